@@ -1,0 +1,240 @@
+"""Seeded synthetic inputs shared by the CUDA path, the oracle, the tests and the bench.
+
+This module holds *inputs only*: atom geometries, pseudo-atom parameters, occupations,
+random draws (KB energies, jitter) and smooth random starting orbitals.  It contains none
+of the method's arithmetic (no stencil, no potentials on the grid, no Hamiltonian, no
+propagation), so both sides of a parity test start from identical numbers without sharing
+any code that computes a result.
+
+Workloads (units: bohr, hartree, atomic time units):
+
+* ``small``  -- two Z=1 Gaussian-erf wells 1.4 bohr apart on a 24^3 grid at h=0.4,
+  1 doubly occupied orbital + 15 virtual, kick along z (the smallest system the
+  propagation of Algorithm 1 is meaningful for).
+* ``ring``   -- planar hexagonal ring: 6 Z=4 atoms at radius 2.6 and 6 Z=1 atoms at
+  radius 4.6, one s-type Kleinman-Bylander projector per Z=4 atom, 64^3 grid at h=0.35,
+  15 doubly occupied + 15 virtual orbitals, kicks along x, y and z.  A benzene-like
+  stand-in (30 valence electrons) for the paper's benzene benchmark (Section 4.1).
+* ``icosa``  -- 147-atom Mackay icosahedron (shells 1+12+42+92) scaled to a 5.4 bohr
+  minimum distance, Z=1 plus one s-type projector each, 128^3 grid at h=0.4,
+  74 doubly occupied + 74 virtual orbitals: a metal-cluster stand-in for the paper's
+  silver nanoparticles (Section 4.3).
+
+Seeds are ``241009189 + 1000*workload_index + sub_index``.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Optional
+
+import numpy as np
+
+SEED_BASE = 241009189
+
+
+@dataclasses.dataclass
+class System:
+    """Everything that defines one propagation problem (inputs only)."""
+
+    name: str
+    n: tuple                 # (nx, ny, nz) grid points
+    h: float                 # grid spacing (bohr)
+    pos: np.ndarray          # (natoms, 3) atom positions, origin = box centre
+    Z: np.ndarray            # (natoms,) valence charges of the local wells
+    rc_loc: np.ndarray       # (natoms,) erf radius of the local wells
+    proj_atom: np.ndarray    # (nproj,) int atom index of each KB projector
+    proj_l: np.ndarray       # (nproj,) int angular momentum (0 = s, 1 = p)
+    proj_m: np.ndarray       # (nproj,) int component for l=1 (0=x, 1=y, 2=z)
+    proj_rc: np.ndarray      # (nproj,) Gaussian radius of each projector
+    E_kb: np.ndarray         # (nproj,) KB energies (hartree), seeded draws
+    nocc: int
+    nvirt: int
+    dt: float = 0.05
+    kappa: float = 1e-3
+    kick_axes: tuple = (2,)
+    nsteps: int = 200
+    hartree_xc: bool = True  # False: independent electrons in V_loc (+ v_ext)
+    v_ext_omega: float = 0.0  # >0 adds a harmonic well 0.5*omega^2*r^2 (test mode)
+    seed: int = SEED_BASE
+
+    @property
+    def N(self) -> int:
+        return self.nocc + self.nvirt
+
+    @property
+    def Ng(self) -> int:
+        return int(self.n[0] * self.n[1] * self.n[2])
+
+    @property
+    def nproj(self) -> int:
+        return int(len(self.proj_atom))
+
+    @property
+    def occupations(self) -> np.ndarray:
+        """f_i = 2 for the doubly occupied orbitals, 0 for the virtual ones."""
+        f = np.zeros(self.N)
+        f[: self.nocc] = 2.0
+        return f
+
+    @property
+    def n_electrons(self) -> float:
+        return 2.0 * self.nocc
+
+
+def _no_proj():
+    return (np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0, np.int32),
+            np.zeros(0), np.zeros(0))
+
+
+def small(n: int = 24, h: float = 0.4, nvirt: int = 15) -> System:
+    """Two Z=1 wells at (0,0,+-0.7) with r_c=0.5, no nonlocal part."""
+    pos = np.array([[0.0, 0.0, -0.7], [0.0, 0.0, 0.7]])
+    pa, pl, pm, prc, ekb = _no_proj()
+    return System("small", (n, n, n), h, pos, np.ones(2), np.full(2, 0.5),
+                  pa, pl, pm, prc, ekb, nocc=1, nvirt=nvirt, kick_axes=(2,),
+                  nsteps=200, seed=SEED_BASE + 1000 * 1)
+
+
+def ring(n: int = 64, h: float = 0.35, nvirt: int = 15) -> System:
+    """Hexagonal ring of 6 Z=4 and 6 Z=1 wells; s-type KB on the Z=4 atoms."""
+    seed = SEED_BASE + 1000 * 2
+    rng = np.random.default_rng(seed)
+    ang = np.arange(6) * (math.pi / 3.0)
+    heavy = np.stack([2.6 * np.cos(ang), 2.6 * np.sin(ang), np.zeros(6)], axis=1)
+    light = np.stack([4.6 * np.cos(ang), 4.6 * np.sin(ang), np.zeros(6)], axis=1)
+    pos = np.concatenate([heavy, light])
+    Z = np.concatenate([np.full(6, 4.0), np.ones(6)])
+    ekb = rng.uniform(0.5, 2.0, size=6)
+    return System("ring", (n, n, n), h, pos, Z, np.full(12, 0.5),
+                  np.arange(6, dtype=np.int32), np.zeros(6, np.int32),
+                  np.zeros(6, np.int32), np.full(6, 1.2), ekb,
+                  nocc=15, nvirt=nvirt, kick_axes=(0, 1, 2), nsteps=2000, seed=seed)
+
+
+def _icosahedron_vertices() -> np.ndarray:
+    phi = (1.0 + math.sqrt(5.0)) / 2.0
+    v = []
+    for a in (-1.0, 1.0):
+        for b in (-phi, phi):
+            v += [(0.0, a, b), (a, b, 0.0), (b, 0.0, a)]
+    return np.array(v)
+
+
+def mackay_icosahedron(shells: int) -> np.ndarray:
+    """Centre atom plus `shells` Mackay shells (10k^2+2 sites in shell k)."""
+    V = _icosahedron_vertices()
+    edge = np.min([np.linalg.norm(V[i] - V[j]) for i in range(12) for j in range(i)])
+    faces = []
+    for i in range(12):
+        for j in range(i + 1, 12):
+            for k in range(j + 1, 12):
+                if (abs(np.linalg.norm(V[i] - V[j]) - edge) < 1e-9
+                        and abs(np.linalg.norm(V[j] - V[k]) - edge) < 1e-9
+                        and abs(np.linalg.norm(V[i] - V[k]) - edge) < 1e-9):
+                    faces.append((i, j, k))
+    pts = [np.zeros(3)]
+    for s in range(1, shells + 1):
+        shell = []
+        for (a, b, c) in faces:
+            for i in range(s + 1):
+                for j in range(s + 1 - i):
+                    l = s - i - j
+                    shell.append((i * V[a] + j * V[b] + l * V[c]))
+        shell = np.array(shell)
+        keys = {}
+        for p in shell:
+            keys[tuple(np.round(p, 8))] = p
+        pts += list(keys.values())
+    return np.array(pts)
+
+
+def icosa(n: int = 128, h: float = 0.4, nvirt: int = 74, shells: int = 3) -> System:
+    """147-atom Mackay icosahedron, min distance 5.4 bohr, Z=1 + s-KB on every atom."""
+    seed = SEED_BASE + 1000 * 3
+    rng = np.random.default_rng(seed)
+    p = mackay_icosahedron(shells)
+    d = np.sqrt(((p[:, None, :] - p[None, :, :]) ** 2).sum(-1))
+    dmin = d[np.triu_indices(len(p), 1)].min()
+    pos = p * (5.4 / dmin)
+    na = len(pos)
+    ekb = rng.uniform(0.5, 2.0, size=na)
+    nocc = (na + 1) // 2
+    return System("icosa", (n, n, n), h, pos, np.ones(na), np.full(na, 0.5),
+                  np.arange(na, dtype=np.int32), np.zeros(na, np.int32),
+                  np.zeros(na, np.int32), np.full(na, 1.2), ekb,
+                  nocc=nocc, nvirt=nvirt, kick_axes=(2,), nsteps=1000, seed=seed)
+
+
+def harmonic(n: int = 32, h: float = 0.4, omega: float = 0.5, nvirt: int = 3) -> System:
+    """Test mode: one doubly occupied orbital in V = 0.5*omega^2*r^2, no Hartree/xc."""
+    pa, pl, pm, prc, ekb = _no_proj()
+    return System("harmonic", (n, n, n), h, np.zeros((0, 3)), np.zeros(0), np.zeros(0),
+                  pa, pl, pm, prc, ekb, nocc=1, nvirt=nvirt, kick_axes=(2,),
+                  nsteps=200, hartree_xc=False, v_ext_omega=omega,
+                  seed=SEED_BASE + 7)
+
+
+def scaled(base: System, n: int, h: Optional[float] = None, nocc: Optional[int] = None,
+           nvirt: Optional[int] = None) -> System:
+    """Same atoms and parameters on another grid / active space (parity-test sizes)."""
+    out = dataclasses.replace(base, n=(n, n, n), h=base.h if h is None else h)
+    if nocc is not None:
+        out.nocc = nocc
+    if nvirt is not None:
+        out.nvirt = nvirt
+    return out
+
+
+def grid_shape(sys: System) -> tuple:
+    """Array shape of a grid function: (nz, ny, nx), x fastest in memory."""
+    return (sys.n[2], sys.n[1], sys.n[0])
+
+
+def smooth_random_orbitals(sys: System, sub_index: int = 0, sigma_pts: float = 2.0,
+                           window_frac: float = 0.8) -> np.ndarray:
+    """Seeded smooth random starting orbitals, shape (N, nz, ny, nx), NOT orthonormal.
+
+    A white-noise field per orbital is smoothed with a Gaussian of `sigma_pts` grid
+    points and multiplied by a smooth window that vanishes at the box faces, so every
+    column is a smooth function that respects the zero boundary condition.  These are
+    random draws, not an eigen-solve: callers orthonormalise them themselves.
+    """
+    from scipy.ndimage import gaussian_filter
+
+    rng = np.random.default_rng(sys.seed + sub_index)
+    shape = grid_shape(sys)
+    out = np.empty((sys.N,) + shape)
+    wins = []
+    for ax, npts in zip((2, 1, 0), sys.n):
+        t = (np.arange(npts) + 0.5) / npts           # (0,1)
+        u = np.clip((t - 0.5) / (0.5 * window_frac), -1.0, 1.0)
+        wins.append(np.cos(0.5 * math.pi * u) ** 2)
+    win = wins[2][:, None, None] * wins[1][None, :, None] * wins[0][None, None, :]
+    for i in range(sys.N):
+        w = rng.standard_normal(shape)
+        out[i] = gaussian_filter(w, sigma_pts, mode="constant") * win
+    return out
+
+
+def random_matrix(n: int, seed: int) -> np.ndarray:
+    """A seeded standard-normal n x n matrix (test inputs for the subspace kernels)."""
+    return np.random.default_rng(seed).standard_normal((n, n))
+
+
+def random_grid(sys: System, seed: int, positive: bool = False) -> np.ndarray:
+    """A seeded random grid function of shape (nz, ny, nx)."""
+    rng = np.random.default_rng(seed)
+    x = rng.standard_normal(grid_shape(sys))
+    return np.abs(x) if positive else x
+
+
+ALL = {"small": small, "ring": ring, "icosa": icosa, "harmonic": harmonic}
+
+
+def by_name(name: str, **kw) -> System:
+    return ALL[name](**kw)
+
+
+def workload_names() -> List[str]:
+    return list(ALL)

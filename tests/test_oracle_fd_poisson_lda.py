@@ -1,0 +1,149 @@
+"""Pins of the oracle's grid operators against closed forms (no GPU).
+
+* FD weights: Fornberg's table (tests/golden) and exactness on monomials of degree <= 12,
+  the property Section 2.1 (Eq. 2) states; degree 14 must NOT be exact (order is 12).
+* 3-D Laplacian: exact on x^a y^b z^c (a+b+c <= 12) at interior points; plane waves.
+* Poisson: potential of a Gaussian charge, Q erf(r/(sqrt(2) sigma))/r.
+* LDA: V = d(rho eps)/d rho, Slater exchange in the k_F form, PZ81 branch continuity.
+* KB: brute-force dense matrix of sum_p beta_p E_p beta_p^T h^3.
+"""
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from oracle import fd, hamiltonian as ham, lda, poisson
+from paper_2410_09189_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def test_fd_weights_match_fornberg_table():
+    rows = [l.strip() for l in open(os.path.join(GOLDEN, "fd12_coefficients.txt"))
+            if l.strip() and not l.startswith("#")]
+    table = [Fraction(r) for r in rows]
+    assert fd.fd_coefficients_exact(6) == table
+
+
+@pytest.mark.parametrize("n", [1, 2, 4, 6])
+def test_fd_exact_on_polynomials(n):
+    h = 0.37
+    L = 4 * n + 9
+    x = (np.arange(L) - (L - 1) / 2) * h
+    inner = slice(n, L - n)
+    for d in range(0, 2 * n + 1):
+        f = x ** d
+        exact = d * (d - 1) * x ** (d - 2) if d >= 2 else np.zeros_like(x)
+        got = fd.laplacian_1d(f, h, n)
+        scale = np.max(np.abs(f[inner])) / h ** 2 + 1.0
+        assert np.max(np.abs(got[inner] - exact[inner])) <= 1e-11 * scale, (n, d)
+    # one degree higher (even) is not exact: the order is exactly 2n
+    d = 2 * n + 2
+    f = x ** d
+    exact = d * (d - 1) * x ** (d - 2)
+    got = fd.laplacian_1d(f, h, n)
+    scale = np.max(np.abs(f[inner])) / h ** 2
+    assert np.max(np.abs(got[inner] - exact[inner])) > 1e-9 * scale
+
+
+def test_laplacian_3d_polynomials_and_plane_wave():
+    s = inputs.small(n=20, h=0.3)
+    x, y, z = ham.full_coords(s)
+    I = (slice(6, -6),) * 3
+    for (a, b, c) in [(12, 0, 0), (0, 7, 5), (4, 4, 4), (2, 3, 6), (0, 0, 11)]:
+        f = x ** a * y ** b * z ** c
+
+        def d2(p, q):
+            return p * (p - 1) * q ** (p - 2) if p >= 2 else 0.0 * q
+        exact = d2(a, x) * y ** b * z ** c + x ** a * d2(b, y) * z ** c + x ** a * y ** b * d2(c, z)
+        got = fd.laplacian(f, s.h)
+        scale = np.max(np.abs(f)) / s.h ** 2
+        assert np.max(np.abs(got[I] - exact[I])) < 1e-11 * scale
+    k = np.array([0.9, -0.6, 1.3])
+    f = np.sin(k[0] * x + k[1] * y + k[2] * z + 0.3)
+    got = fd.laplacian(f, s.h)
+    # continuum -|k|^2 f up to the O((k h)^12) truncation of each axis
+    err_bound = sum((abs(kk) * s.h) ** 12 / s.h ** 2 for kk in k) * 10
+    assert np.max(np.abs(got[I] + (k @ k) * f[I])) < max(err_bound, 1e-11)
+
+
+def test_fd_weight_moments():
+    a = fd.fd_coefficients_exact(6)
+    assert a[0] + 2 * sum(a[1:]) == 0
+    assert sum(Fraction(m * m) * a[m] for m in range(1, 7)) == 1
+
+
+def test_poisson_gaussian_charge():
+    s = inputs.small(n=64, h=0.3)
+    x, y, z = ham.full_coords(s)
+    r = np.sqrt(x * x + y * y + z * z)
+    sigma, Q = 1.0, 2.0
+    rho = Q * (2 * math.pi * sigma ** 2) ** -1.5 * np.exp(-r * r / (2 * sigma ** 2))
+    V, it = poisson.hartree(s, rho, tol=1e-13, return_info=True)
+    from scipy.special import erf
+    with np.errstate(invalid="ignore", divide="ignore"):
+        Vx = np.where(r > 0, Q * erf(r / (math.sqrt(2) * sigma)) / np.where(r > 0, r, 1),
+                      Q * math.sqrt(2 / math.pi) / sigma)
+    assert it < 200
+    assert np.max(np.abs(V - Vx)) < 1e-7
+    # the returned V satisfies the discrete equation it claims to solve
+    gp = poisson.multipole_ghosts(s, rho)
+    gp[6:-6, 6:-6, 6:-6] = V
+    res = fd.laplacian_padded(gp, s.h) + 4 * math.pi * rho
+    assert np.linalg.norm(res) < 1e-11 * np.linalg.norm(4 * math.pi * rho)
+
+
+def test_lda_derivative_and_branches():
+    rho = np.array([1e-5, 1e-3, 0.01, 0.1, 0.5, 2.0, 10.0])
+    v, e = lda.lda(rho)
+    dr = 1e-6 * rho
+    _, ep = lda.lda(rho + dr)
+    _, em = lda.lda(rho - dr)
+    num = ((rho + dr) * ep - (rho - dr) * em) / (2 * dr)
+    assert np.allclose(v, num, rtol=1e-7, atol=1e-10)
+    # Slater exchange written with the Fermi wavevector
+    kf = np.cbrt(3 * math.pi ** 2 * rho)
+    vx, ex = lda.exchange(rho)
+    assert np.allclose(ex, -3 * kf / (4 * math.pi), rtol=1e-14)
+    assert np.allclose(vx, -kf / math.pi, rtol=1e-14)
+    # Gell-Mann-Brueckner: eps_c ~ A ln r_s + ... with A = (1 - ln 2)/pi^2
+    rs = np.array([1e-6, 1e-5])
+    _, ec = lda.correlation(3 / (4 * math.pi * rs ** 3))
+    slope = (ec[1] - ec[0]) / math.log(10.0)
+    assert abs(slope - (1 - math.log(2)) / math.pi ** 2) < 1e-4
+    # eps_c and V_c continuous across r_s = 1 (PZ81's matching conditions)
+    rho1 = 3 / (4 * math.pi)
+    vc_a, ec_a = lda.correlation(np.array([rho1 * (1 + 1e-10)]))
+    vc_b, ec_b = lda.correlation(np.array([rho1 * (1 - 1e-10)]))
+    assert abs(ec_a[0] - ec_b[0]) < 5e-5
+    assert abs(vc_a[0] - vc_b[0]) < 5e-5
+    # floor
+    v0, e0 = lda.lda(np.array([0.0, 1e-15]))
+    assert np.all(v0 == 0) and np.all(e0 == 0)
+
+
+def test_kb_against_dense_matrix():
+    s = inputs.ring(n=16, h=0.9)
+    projs = ham.projectors(s)
+    h3 = s.h ** 3
+    D = np.zeros((s.Ng, s.Ng))
+    for p, (idx, val) in enumerate(projs):
+        b = np.zeros(s.Ng)
+        b[idx] = val
+        assert abs(h3 * b @ b - 1.0) < 1e-13
+        D += s.E_kb[p] * h3 * np.outer(b, b)
+    psi = np.random.default_rng(1).standard_normal((3, s.Ng))
+    assert np.allclose(ham.apply_nonlocal(s, projs, psi), psi @ D.T, atol=1e-12)
+
+
+def test_p_projectors_odd():
+    s = inputs.ring(n=24, h=0.5)
+    s.proj_l = np.array([1, 1, 1, 0, 0, 0], np.int32)
+    s.proj_m = np.array([0, 1, 2, 0, 0, 0], np.int32)
+    projs = ham.projectors(s)
+    x, y, z = (c.ravel() for c in ham.full_coords(s))
+    for m, (idx, val) in enumerate(projs[:3]):
+        q = (x, y, z)[m][idx] - s.pos[s.proj_atom[m], m]
+        assert np.all(val * q >= 0)
