@@ -1,0 +1,212 @@
+/*
+ * rmgtd -- real-time TDDFT density-matrix propagation on one GB300 GPU (C ABI).
+ *
+ * Method: Jakowski et al., "Simulation of 24,000 Electrons Dynamics: Real-Time TDDFT with
+ * the Real-Space Multigrids (RMG)", arXiv:2410.09189.  The library implements the time
+ * loop of Algorithm 1 (Section 3.1) in a fixed active space of N = N_occ + N_virt
+ * orthonormal Kohn-Sham orbitals Phi on a uniform 3-D grid:
+ *   - first-order Magnus operator Omega = -i dt (H_0 + H_1)/2 (Eq. 15),
+ *   - exp(Omega) applied to the density matrix P by the commutator expansion
+ *     dP_k = (Omega dP_{k-1} + dP_{k-1} Omega^dagger)/k until max|dP_k| <= dP_thrs
+ *     (Eqs. 19, 33; real/imaginary split of Eq. 35),
+ *   - Hamiltonian self-consistency: H_1 <- DFT(rho(P_1)) until max|H_new - H_1| <= H_thrs,
+ *     seeded by H_1 = 2 H_0 - H_-1 (Algorithm 1 line 11),
+ *   - DFT(rho) = density rho(r) = sum_ij Re(P)_ij phi_i phi_j, multigrid Poisson solve for
+ *     V_H, LDA exchange-correlation, H = H_core + h^3 Phi^T diag(V_H + V_xc) Phi,
+ *   - dipole d_q = Tr(Re(P) M_q), M_q = h^3 Phi^T q Phi (Algorithm 1 lines 3, 27),
+ *   - delta kick P <- exp(-i kappa M_q) P exp(i kappa M_q) (Eq. 34 with a delta envelope).
+ *
+ * Conventions (atomic units):
+ *   - Grid: point i of an axis with n points sits at (i - (n-1)/2) h (box centre = origin).
+ *     A grid function is an array [nz][ny][nx] (x fastest); Ng = nx*ny*nz.
+ *   - Orbital blocks are orbital-major: column j of the Ng x N block is contiguous,
+ *     element (g, j) at offset j*Ng + g ("Ng x N column-major").
+ *   - N x N matrices are row-major doubles.
+ *   - Inner products carry the grid quadrature h^3 (Eq. 4), so Phi is orthonormal when
+ *     h^3 Phi^T Phi = I.
+ *
+ * Ownership: every pointer passed to rmgtd_create is read during the call only (inputs
+ * are copied).  The context owns all device memory it allocates; host output buffers
+ * belong to the caller.  Device pointers passed to rmgtd_apply_h / rmgtd_hartree /
+ * rmgtd_xc belong to the caller and must stay valid until the work on the context's
+ * stream has finished.
+ *
+ * Errors: every call returns an rmgtd_status and never aborts; rmgtd_last_error() gives a
+ * message.  A failed rmgtd_step leaves the last completed step's state in place.
+ *
+ * Streams: all work is ordered on the context's stream (rmgtd_options.stream, NULL = the
+ * legacy default stream).  Calls that return host data synchronise that stream.
+ */
+#ifndef RMGTD_H
+#define RMGTD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rmgtd_ctx rmgtd_ctx;
+
+typedef enum {
+  RMGTD_OK = 0,
+  RMGTD_EINVAL = -1,         /* bad argument or size */
+  RMGTD_ENOMEM = -2,         /* device allocation failed */
+  RMGTD_ECUDA = -3,          /* a CUDA runtime call failed */
+  RMGTD_ENOTCONVERGED = -4,  /* SCF pass cap or commutator term cap reached */
+  RMGTD_EDIVERGED = -5,      /* non-finite value in the series or the SCF error */
+  RMGTD_ETIMEOUT = -6,       /* a device-side wait gave up after its iteration limit */
+  RMGTD_ESTATE = -7          /* call not valid in the context's current state */
+} rmgtd_status;
+
+/* Arithmetic of the propagation path. */
+typedef enum {
+  RMGTD_PREC_FP64 = 0,   /* every step in float64 */
+  RMGTD_PREC_MIXED = 1   /* float32 orbitals and grid contractions, float64 subspace algebra */
+} rmgtd_precision;
+
+/* Element type of an orbital block passed to rmgtd_apply_h. */
+typedef enum {
+  RMGTD_F64 = 0,   /* double */
+  RMGTD_F32 = 1,   /* float */
+  RMGTD_C128 = 2,  /* complex double, interleaved (re, im) */
+  RMGTD_C64 = 3    /* complex float, interleaved (re, im) */
+} rmgtd_dtype;
+
+/* Device allocator hook: return `bytes` of device memory usable on `stream` (NULL on
+ * failure).  Lets a host framework (e.g. PyTorch's caching allocator) own the memory. */
+typedef void* (*rmgtd_alloc_fn)(size_t bytes, void* stream, void* user);
+typedef void (*rmgtd_free_fn)(void* ptr, void* user);
+
+/* The system: grid, pseudo-atoms, active space and starting orbitals (all host memory). */
+typedef struct {
+  int nx, ny, nz;          /* grid points per axis (each >= 8) */
+  double h;                /* grid spacing (bohr) */
+  int natoms;
+  const double* pos;       /* [natoms][3] positions, origin = box centre */
+  const double* Z;         /* [natoms] local-well charges: V_a = -Z erf(r/rc)/r */
+  const double* rc_loc;    /* [natoms] erf radii */
+  int nproj;               /* Kleinman-Bylander projectors (may be 0) */
+  const int* proj_atom;    /* [nproj] owning atom */
+  const int* proj_l;       /* [nproj] 0 = s: exp(-r^2/rc^2); 1 = p: (q-R_q) exp(-r^2/rc^2) */
+  const int* proj_m;       /* [nproj] p component 0/1/2 = x/y/z (ignored for s) */
+  const double* proj_rc;   /* [nproj] Gaussian radii; the projector is cut at r > 5 rc */
+  const double* E_kb;      /* [nproj] KB energies (hartree) */
+  int nocc, nvirt;         /* active space N = nocc + nvirt */
+  const double* f;         /* [N] occupations (NULL: 2 for the first nocc, 0 after) */
+  const double* phi0;      /* [N][Ng] starting orbitals (orbital-major), required */
+  double v_ext_omega;      /* > 0 adds the harmonic well 0.5 w^2 r^2 (test mode) */
+  int hartree_xc;          /* 1: V_eff includes V_H + V_xc; 0: independent electrons */
+} rmgtd_system;
+
+typedef struct {
+  double dt;               /* time step (a.u.); Algorithm 1 line 4 */
+  double H_thrs;           /* SCF threshold on max|H_new - H_1|; Algorithm 1 line 6 */
+  double dP_thrs;          /* commutator-series threshold on max|dP_k|; line 6 */
+  int max_scf;             /* SCF pass cap per step (exceeded -> RMGTD_ENOTCONVERGED) */
+  int max_terms;           /* commutator-term cap per expansion */
+  int precision;           /* rmgtd_precision */
+  int nrep;                /* independent replicas sharing Phi (e.g. 3 kick directions) */
+  int orthonormalize;      /* 1: Cholesky-orthonormalise phi0 in float64 on the device */
+  double poisson_tol;      /* relative residual of the Hartree solve */
+  int poisson_max_iter;    /* PCG iteration cap per Hartree solve */
+  int use_graph;           /* 1: run each time step as one captured CUDA graph */
+  void* stream;            /* cudaStream_t for all work (NULL = default stream) */
+  rmgtd_alloc_fn alloc;    /* NULL: cudaMalloc */
+  rmgtd_free_fn free;      /* NULL: cudaFree */
+  void* alloc_user;
+} rmgtd_options;
+
+/* Per-step, per-replica statistics written by rmgtd_step. */
+typedef struct {
+  int passes;        /* DFT evaluations (SCF passes) in this step */
+  int terms_max;     /* largest number of commutator terms in one expansion */
+  int terms_sum;     /* commutator terms summed over the passes */
+  int status;        /* rmgtd_status of this replica's step */
+  double H_err;      /* final max|H_new - H_1| */
+} rmgtd_stats;
+
+/* Matrices readable / writable with rmgtd_get_matrix / rmgtd_set_matrix (N x N doubles). */
+typedef enum {
+  RMGTD_MAT_P_RE = 0,   /* Re P of the current state (symmetric) */
+  RMGTD_MAT_P_IM = 1,   /* Im P of the current state (antisymmetric) */
+  RMGTD_MAT_H0 = 2,     /* H at the current time */
+  RMGTD_MAT_HM1 = 3,    /* H one step earlier */
+  RMGTD_MAT_HCORE = 4,  /* h^3 Phi^T (T + V_loc + V_ext + V_NL) Phi (shared, read-only) */
+  RMGTD_MAT_MX = 5,     /* dipole matrices h^3 Phi^T q Phi (shared, read-only) */
+  RMGTD_MAT_MY = 6,
+  RMGTD_MAT_MZ = 7,
+  RMGTD_MAT_S = 8       /* overlap h^3 Phi^T Phi after set-up (shared, read-only) */
+} rmgtd_matrix;
+
+/* Fill `opt` with defaults: dt 0.05, H_thrs 1e-7, dP_thrs 1e-10, max_scf 50,
+ * max_terms 200, FP64, nrep 1, orthonormalize 1, poisson_tol 1e-12, 200 PCG iterations,
+ * graphs on, default stream, cudaMalloc. */
+void rmgtd_default_options(rmgtd_options* opt);
+
+/* Set up a context (Algorithm 1 lines 1-8 given the orbitals): copy Phi, build V_loc and
+ * the KB projectors on the device, orthonormalise Phi (optional), form H_core, M_q and the
+ * ground-state H_0 = H[rho(P_0)] with P_0 = diag(f) for every replica, H_-1 = H_0.
+ * Errors: RMGTD_EINVAL (sizes, NULL required pointers, nrep < 1), RMGTD_ENOMEM,
+ * RMGTD_ECUDA.  On failure *out is NULL. */
+int rmgtd_create(const rmgtd_system* sys, const rmgtd_options* opt, rmgtd_ctx** out);
+
+/* Free every device buffer of the context (NULL is ignored). */
+void rmgtd_destroy(rmgtd_ctx* ctx);
+
+/* hx = H x for `ncols` orbitals on the grid (Eq. 1): -1/2 Lap_12 x + V x + KB part, with
+ * Dirichlet-zero ghosts.  V = V_loc + V_ext, plus V_H + V_xc of replica `rep` when rep >= 0
+ * (rep = -1: the core operator only).  x_dev, hx_dev: device arrays [ncols][Ng] of `dtype`
+ * (rmgtd_dtype), must not overlap.  Errors: RMGTD_EINVAL. */
+int rmgtd_apply_h(rmgtd_ctx* ctx, const void* x_dev, void* hx_dev, int ncols, int dtype,
+                  int rep);
+
+/* Delta kick of replica `rep` along axis q (0 = x, 1 = y, 2 = z):
+ * P <- exp(-i kappa M_q) P exp(i kappa M_q) by the commutator expansion (Eq. 34 with a
+ * delta envelope applied at t = 0+).  Errors: RMGTD_EINVAL, RMGTD_ENOTCONVERGED. */
+int rmgtd_kick(rmgtd_ctx* ctx, int rep, int axis, double kappa);
+
+/* Advance every replica by `nsteps` time steps of Algorithm 1.  `stats` (host, may be
+ * NULL) receives nsteps * nrep entries, step-major.  Returns the first non-OK replica
+ * status; on failure the state of the last completed step is kept. */
+int rmgtd_step(rmgtd_ctx* ctx, int nsteps, rmgtd_stats* stats);
+
+/* rho(r) of replica `rep` for the current P (host array of Ng doubles). */
+int rmgtd_density(rmgtd_ctx* ctx, int rep, double* rho_host);
+
+/* Electronic dipole d_q = Tr(Re(P) M_q), q = x, y, z, of replica `rep` (host double[3]). */
+int rmgtd_dipole(rmgtd_ctx* ctx, int rep, double mu[3]);
+
+/* Total energy Tr(Re P H_core) + 1/2 h^3 sum rho V_H + h^3 sum rho eps_xc + E_ion of
+ * replica `rep` at the last density evaluation. */
+int rmgtd_energy(rmgtd_ctx* ctx, int rep, double* E);
+
+/* Copy an N x N matrix (rmgtd_matrix) of replica `rep` to / from host memory. */
+int rmgtd_get_matrix(rmgtd_ctx* ctx, int which, int rep, double* host_out);
+int rmgtd_set_matrix(rmgtd_ctx* ctx, int which, int rep, const double* host_in);
+
+/* Hartree potential of a device density (Ng doubles) with the context's grid: solves
+ * Lap_12 V = -4 pi rho with monopole + dipole ghost values by multigrid-preconditioned
+ * CG to poisson_tol.  vh_dev is used as the initial guess.  Errors: RMGTD_ENOTCONVERGED. */
+int rmgtd_hartree(rmgtd_ctx* ctx, const double* rho_dev, double* vh_dev);
+
+/* LDA (Slater + PZ81) on n device points: vxc_dev, exc_dev receive V_xc and eps_xc. */
+int rmgtd_xc(rmgtd_ctx* ctx, const double* rho_dev, double* vxc_dev, double* exc_dev,
+             size_t n);
+
+/* Checkpoint / resume of the propagation state (t, step count, P, H_0, H_-1, V_H of every
+ * replica) to a binary file.  rmgtd_load requires a context created for the same system. */
+int rmgtd_save(rmgtd_ctx* ctx, const char* path);
+int rmgtd_load(rmgtd_ctx* ctx, const char* path);
+
+/* Simulation time and completed steps of the context. */
+int rmgtd_time(rmgtd_ctx* ctx, double* t, long long* steps);
+
+/* Message of the last error on `ctx` (thread-local message when ctx is NULL). */
+const char* rmgtd_last_error(const rmgtd_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RMGTD_H */

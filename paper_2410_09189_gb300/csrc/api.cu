@@ -1,0 +1,681 @@
+// The C ABI of include/rmgtd.h: context set-up (Algorithm 1 lines 1-8), the time loop
+// (lines 9-29), kicks, observables, checkpoints.  Host code only orchestrates launches on
+// the context's stream; every arithmetic step of the propagation runs in the kernels of
+// k_grid.cu, k_subspace.cu and k_poisson.cu.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+
+#include "rmgtd_internal.cuh"
+
+static thread_local std::string g_last_error;
+
+namespace rmgtd {
+
+int set_error(rmgtd_ctx* ctx, int code, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  g_last_error = msg;
+  return code;
+}
+
+int cuda_check(rmgtd_ctx* ctx, cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  if (e == cudaErrorMemoryAllocation) return set_error(ctx, RMGTD_ENOMEM, m);
+  return set_error(ctx, RMGTD_ECUDA, m);
+}
+
+void* dev_alloc(rmgtd_ctx* ctx, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  void* p = nullptr;
+  if (ctx->opt.alloc) {
+    p = ctx->opt.alloc(bytes, (void*)ctx->stream, ctx->opt.alloc_user);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    p = nullptr;
+  }
+  if (p) ctx->buffers.push_back(Buffer{p, bytes});
+  return p;
+}
+
+void dev_free(rmgtd_ctx* ctx, void* p) {
+  if (!p) return;
+  for (size_t i = 0; i < ctx->buffers.size(); ++i) {
+    if (ctx->buffers[i].ptr == p) {
+      if (ctx->opt.free)
+        ctx->opt.free(p, ctx->opt.alloc_user);
+      else
+        cudaFree(p);
+      ctx->buffers.erase(ctx->buffers.begin() + i);
+      return;
+    }
+  }
+}
+
+double* kb_coef_buffer(rmgtd_ctx* ctx, int ncols) {
+  if (ncols > ctx->kb_coef_cols) {
+    cudaStreamSynchronize(ctx->stream);
+    dev_free(ctx, ctx->kb_coef);
+    ctx->kb_coef = (double*)dev_alloc(ctx, sizeof(double) * 2 * (size_t)ctx->nproj * ncols);
+    ctx->kb_coef_cols = ctx->kb_coef ? ncols : 0;
+  }
+  return ctx->kb_coef;
+}
+
+// ---- small elementwise kernels ------------------------------------------------------------
+__global__ void k_coords(int nx, int ny, int nz, double h, double* __restrict__ q) {
+  const long Ng = (long)nx * ny * nz;
+  for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < Ng;
+       g += (long)gridDim.x * blockDim.x) {
+    const int ix = (int)(g % nx), iy = (int)((g / nx) % ny), iz = (int)(g / ((long)nx * ny));
+    q[g] = axis_coord(ix, nx, h);
+    q[Ng + g] = axis_coord(iy, ny, h);
+    q[2 * Ng + g] = axis_coord(iz, nz, h);
+  }
+}
+
+__global__ void k_symmetrize(int N, const double* __restrict__ in, double* __restrict__ out) {
+  const long NN = (long)N * N;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < NN;
+       e += (long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / N), j = (int)(e % N);
+    out[e] = 0.5 * (in[e] + in[(long)j * N + i]);
+  }
+}
+
+__global__ void k_diag_init(int N, int nrep, const double* __restrict__ f, double* __restrict__ S,
+                            double* __restrict__ A) {
+  const long NN = (long)N * N;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < NN * nrep;
+       e += (long)gridDim.x * blockDim.x) {
+    const long l = e % NN;
+    const int i = (int)(l / N), j = (int)(l % N);
+    S[e] = (i == j) ? f[i] : 0.0;
+    A[e] = 0.0;
+  }
+}
+
+__global__ void k_set_active(RepCtl* ctl, int nrep, int v) {
+  if (threadIdx.x < nrep) {
+    ctl[threadIdx.x].active = v;
+    ctl[threadIdx.x].status = 0;
+  }
+}
+
+__global__ void k_ion_energy(int natoms, const double* __restrict__ pos, const double* __restrict__ Z,
+                             const double* __restrict__ rc, double* __restrict__ out) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  const long npair = (long)natoms * natoms;
+  for (long e = threadIdx.x; e < npair; e += blockDim.x) {
+    const int a = (int)(e / natoms), b = (int)(e % natoms);
+    if (b >= a) continue;
+    const double dx = pos[3 * a] - pos[3 * b], dy = pos[3 * a + 1] - pos[3 * b + 1],
+                 dz = pos[3 * a + 2] - pos[3 * b + 2];
+    const double R = sqrt(dx * dx + dy * dy + dz * dz);
+    const double sg = sqrt(rc[a] * rc[a] + rc[b] * rc[b]);
+    s += Z[a] * Z[b] * erf(R / sg) / R;
+  }
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) *out = s;
+}
+
+// ---- one density-functional evaluation: H_1 <- DFT(rho(P)) (Algorithm 1 line 26) ------------
+// S: Re P per replica.  Writes rho, vh, vxc, exc, vhxc and H1 (in place) for active
+// replicas and folds max|H_new - H_1| into errbits.
+int dft_eval(rmgtd_ctx* ctx, const double* S, const RepCtl* ctl, unsigned long long* errbits) {
+  const int nrep = ctx->nrep;
+  int rc = rho_dev(ctx, S, ctx->rho, ctl, nrep);
+  if (rc) return rc;
+  if (ctx->hartree_xc) {
+    rc = hartree_dev(ctx, ctx->rho, ctx->vh, ctl, 0, nrep);
+    if (rc) return rc;
+  }
+  rc = launch_lda(ctx, ctx->rho, ctx->hartree_xc ? ctx->vh : nullptr, ctx->vxc, ctx->exc,
+                  ctx->vhxc, ctx->Ng, ctl, nrep, ctx->Ng, ctx->hartree_xc);
+  if (rc) return rc;
+  if (errbits)
+    RMGTD_CUDA(ctx, cudaMemsetAsync(errbits, 0, sizeof(unsigned long long) * nrep, ctx->stream));
+  const long NN = (long)ctx->N * ctx->N;
+  return gram(ctx, ctx->phi, ctx->phi, ctx->vhxc, ctx->Ng, nrep, ctx->h3, ctx->Hcore, ctx->H1,
+              errbits ? ctx->H1 : nullptr, ctl, 1, errbits);
+  (void)NN;
+}
+
+// Refresh rho / V_H / V_xc / eps_xc from the current P_0 of every replica (no H update).
+int refresh_fields(rmgtd_ctx* ctx) {
+  int rc = rho_dev(ctx, ctx->S0, ctx->rho, nullptr, ctx->nrep);
+  if (rc) return rc;
+  if (ctx->hartree_xc) {
+    rc = hartree_dev(ctx, ctx->rho, ctx->vh, nullptr, 0, ctx->nrep);
+    if (rc) return rc;
+  }
+  return launch_lda(ctx, ctx->rho, ctx->hartree_xc ? ctx->vh : nullptr, ctx->vxc, ctx->exc,
+                    ctx->vhxc, ctx->Ng, nullptr, ctx->nrep, ctx->Ng, ctx->hartree_xc);
+}
+
+static int check_status(rmgtd_ctx* ctx, const char* where) {
+  int st = 0;
+  RMGTD_CUDA(ctx, cudaMemcpyAsync(&ctx->ctl_host[ctx->nrep], ctx->status, sizeof(int),
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+  RMGTD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  memcpy(&st, &ctx->ctl_host[ctx->nrep], sizeof(int));
+  if (st != 0) {
+    char buf[160];
+    snprintf(buf, sizeof(buf), "%s: device status %d", where, st);
+    return set_error(ctx, st, buf);
+  }
+  return RMGTD_OK;
+}
+
+}  // namespace rmgtd
+
+using namespace rmgtd;
+
+extern "C" {
+
+void rmgtd_default_options(rmgtd_options* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->dt = 0.05;
+  o->H_thrs = 1e-7;
+  o->dP_thrs = 1e-10;
+  o->max_scf = 50;
+  o->max_terms = 200;
+  o->precision = RMGTD_PREC_FP64;
+  o->nrep = 1;
+  o->orthonormalize = 1;
+  o->poisson_tol = 1e-12;
+  o->poisson_max_iter = 200;
+  o->use_graph = 0;
+}
+
+const char* rmgtd_last_error(const rmgtd_ctx* ctx) {
+  if (ctx) return ctx->err.c_str();
+  return g_last_error.c_str();
+}
+
+void rmgtd_destroy(rmgtd_ctx* ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->stream);
+  if (ctx->step_exec) cudaGraphExecDestroy(ctx->step_exec);
+  if (ctx->step_graph) cudaGraphDestroy(ctx->step_graph);
+  for (auto& b : ctx->buffers) {
+    if (ctx->opt.free)
+      ctx->opt.free(b.ptr, ctx->opt.alloc_user);
+    else
+      cudaFree(b.ptr);
+  }
+  ctx->buffers.clear();
+  if (ctx->ctl_host) cudaFreeHost(ctx->ctl_host);
+  if (ctx->obs_host) cudaFreeHost(ctx->obs_host);
+  if (ctx->pcg_any_host) cudaFreeHost(ctx->pcg_any_host);
+  delete ctx;
+}
+
+static int create_impl(const rmgtd_system* sys, const rmgtd_options* opt, rmgtd_ctx* ctx) {
+  ctx->opt = *opt;
+  ctx->stream = (cudaStream_t)opt->stream;
+  ctx->nx = sys->nx;
+  ctx->ny = sys->ny;
+  ctx->nz = sys->nz;
+  ctx->Ng = (long)sys->nx * sys->ny * sys->nz;
+  ctx->h = sys->h;
+  ctx->h3 = sys->h * sys->h * sys->h;
+  ctx->nocc = sys->nocc;
+  ctx->nvirt = sys->nvirt;
+  ctx->N = sys->nocc + sys->nvirt;
+  ctx->nrep = opt->nrep;
+  ctx->hartree_xc = sys->hartree_xc ? 1 : 0;
+  ctx->v_ext_omega = sys->v_ext_omega;
+  const int N = ctx->N;
+  const long Ng = ctx->Ng;
+  const long NN = (long)N * N;
+  const int nrep = ctx->nrep;
+
+  int dev = 0;
+  RMGTD_CUDA(ctx, cudaGetDevice(&dev));
+  cudaDeviceProp prop;
+  RMGTD_CUDA(ctx, cudaGetDeviceProperties(&prop, dev));
+  ctx->num_sms = prop.multiProcessorCount;
+  ctx->coop_ok = prop.cooperativeLaunch;
+  if (!ctx->coop_ok) return set_error(ctx, RMGTD_ECUDA, "device lacks cooperative launch");
+  ctx->red_blocks = 2 * ctx->num_sms;
+
+  ctx->f.assign(N, 0.0);
+  for (int i = 0; i < N; ++i) ctx->f[i] = sys->f ? sys->f[i] : (i < sys->nocc ? 2.0 : 0.0);
+
+  auto A = [&](size_t bytes) { return dev_alloc(ctx, bytes); };
+  const size_t gsz = sizeof(double) * Ng, msz = sizeof(double) * NN;
+  ctx->phi = (double*)A(gsz * N);
+  ctx->vion = (double*)A(gsz);
+  ctx->f_dev = (double*)A(sizeof(double) * N);
+  ctx->Hcore = (double*)A(msz);
+  ctx->M = (double*)A(3 * msz);
+  ctx->Smat = (double*)A(msz);
+  ctx->S0 = (double*)A(msz * nrep);
+  ctx->A0 = (double*)A(msz * nrep);
+  ctx->S1 = (double*)A(msz * nrep);
+  ctx->A1 = (double*)A(msz * nrep);
+  ctx->H0 = (double*)A(msz * nrep);
+  ctx->Hm1 = (double*)A(msz * nrep);
+  ctx->H1 = (double*)A(msz * nrep);
+  ctx->dbuf = (double*)A(4 * msz * nrep);
+  ctx->rho = (double*)A(gsz * nrep);
+  ctx->vh = (double*)A(gsz * nrep);
+  ctx->vxc = (double*)A(gsz * nrep);
+  ctx->exc = (double*)A(gsz * nrep);
+  ctx->vhxc = (double*)A(gsz * nrep);
+  ctx->pcg_b = (double*)A(gsz * nrep);
+  ctx->pcg_r = (double*)A(gsz * nrep);
+  ctx->pcg_z = (double*)A(gsz * nrep);
+  ctx->pcg_p = (double*)A(gsz * nrep);
+  ctx->pcg_Ap = (double*)A(gsz * nrep);
+  ctx->red_part = (double*)A(sizeof(double) * (size_t)nrep * 8 * ctx->red_blocks);
+  ctx->pcg = (PcgState*)A(sizeof(PcgState) * nrep);
+  ctx->pcg_any = (int*)A(sizeof(int));
+  ctx->ctl = (RepCtl*)A(sizeof(RepCtl) * nrep);
+  ctx->bar = (unsigned*)A(sizeof(unsigned));
+  ctx->errslots = (unsigned long long*)A(sizeof(unsigned long long) * (size_t)nrep * (opt->max_terms + 1));
+  ctx->errbits = (unsigned long long*)A(sizeof(unsigned long long) * nrep);
+  ctx->status = (int*)A(sizeof(int));
+  ctx->obs = (double*)A(sizeof(double) * 8 * nrep);
+  {
+    const long per = std::max(3, nrep) * NN;
+    const long want = per * 4L * ctx->num_sms;
+    const long cap = std::max<long>(per, 64L << 20);
+    ctx->gram_part_elems = (size_t)std::min(want, cap);
+    ctx->gram_part = (double*)A(sizeof(double) * ctx->gram_part_elems);
+  }
+  for (auto& b : ctx->buffers)
+    if (!b.ptr) return set_error(ctx, RMGTD_ENOMEM, "device allocation failed");
+  if (!ctx->phi || !ctx->gram_part || !ctx->pcg_Ap || !ctx->dbuf || !ctx->errslots)
+    return set_error(ctx, RMGTD_ENOMEM, "device allocation failed");
+  RMGTD_CUDA(ctx, cudaMallocHost((void**)&ctx->ctl_host, sizeof(RepCtl) * (nrep + 1)));
+  RMGTD_CUDA(ctx, cudaMallocHost((void**)&ctx->obs_host, sizeof(double) * 8 * nrep));
+  RMGTD_CUDA(ctx, cudaMallocHost((void**)&ctx->pcg_any_host, sizeof(int)));
+  RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream));
+  RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->vh, 0, gsz * nrep, ctx->stream));
+  RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->ctl, 0, sizeof(RepCtl) * nrep, ctx->stream));
+
+  // orbitals, occupations, atoms
+  RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->phi, sys->phi0, gsz * N, cudaMemcpyHostToDevice, ctx->stream));
+  RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->f_dev, ctx->f.data(), sizeof(double) * N,
+                                  cudaMemcpyHostToDevice, ctx->stream));
+  const int na = sys->natoms;
+  double* pos_d = (double*)A(sizeof(double) * 3 * std::max(na, 1));
+  double* Z_d = (double*)A(sizeof(double) * std::max(na, 1));
+  double* rc_d = (double*)A(sizeof(double) * std::max(na, 1));
+  double* eion_d = (double*)A(sizeof(double));
+  if (!pos_d || !Z_d || !rc_d || !eion_d) return set_error(ctx, RMGTD_ENOMEM, "atom arrays");
+  if (na > 0) {
+    RMGTD_CUDA(ctx, cudaMemcpyAsync(pos_d, sys->pos, sizeof(double) * 3 * na, cudaMemcpyHostToDevice, ctx->stream));
+    RMGTD_CUDA(ctx, cudaMemcpyAsync(Z_d, sys->Z, sizeof(double) * na, cudaMemcpyHostToDevice, ctx->stream));
+    RMGTD_CUDA(ctx, cudaMemcpyAsync(rc_d, sys->rc_loc, sizeof(double) * na, cudaMemcpyHostToDevice, ctx->stream));
+  }
+  int rc = launch_vion(ctx, pos_d, Z_d, rc_d, na);
+  if (rc) return rc;
+  k_ion_energy<<<1, 256, 0, ctx->stream>>>(na, pos_d, Z_d, rc_d, eion_d);
+  RMGTD_LAUNCH(ctx, "k_ion_energy");
+  RMGTD_CUDA(ctx, cudaMemcpyAsync(&ctx->obs_host[0], eion_d, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  RMGTD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  ctx->E_ion = ctx->obs_host[0];
+
+  rc = build_projectors(ctx, sys);
+  if (rc) return rc;
+  rc = setup_multigrid(ctx);
+  if (rc) return rc;
+
+  if (opt->orthonormalize) {
+    rc = orthonormalize(ctx);
+    if (rc) return rc;
+  }
+  rc = gram(ctx, ctx->phi, ctx->phi, nullptr, 0, 1, ctx->h3, nullptr, ctx->Smat, nullptr, nullptr,
+            1, nullptr);
+  if (rc) return rc;
+
+  // H_core = h^3 Phi^T (T + V_loc + V_ext + V_NL) Phi, symmetrised
+  {
+    double* hphi = (double*)A(gsz * N);
+    if (!hphi) return set_error(ctx, RMGTD_ENOMEM, "H Phi scratch");
+    rc = apply_h_dev(ctx, ctx->phi, hphi, N, RMGTD_F64, nullptr);
+    if (rc) return rc;
+    rc = gram(ctx, ctx->phi, hphi, nullptr, 0, 1, ctx->h3, nullptr, ctx->H1, nullptr, nullptr, 0,
+              nullptr);
+    if (rc) return rc;
+    k_symmetrize<<<std::max(1, (int)std::min<long>(ceil_div(NN, 256), 1024)), 256, 0, ctx->stream>>>(
+        N, ctx->H1, ctx->Hcore);
+    RMGTD_LAUNCH(ctx, "k_symmetrize");
+    RMGTD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    dev_free(ctx, hphi);
+  }
+  // M_q = h^3 Phi^T q Phi
+  {
+    double* q = (double*)A(3 * gsz);
+    if (!q) return set_error(ctx, RMGTD_ENOMEM, "coordinate scratch");
+    k_coords<<<std::max(1, (int)std::min<long>(ceil_div(Ng, 256), 4096)), 256, 0, ctx->stream>>>(
+        ctx->nx, ctx->ny, ctx->nz, ctx->h, q);
+    RMGTD_LAUNCH(ctx, "k_coords");
+    for (int d = 0; d < 3; ++d) {
+      rc = gram(ctx, ctx->phi, ctx->phi, q + d * Ng, 0, 1, ctx->h3, nullptr, ctx->M + d * NN,
+                nullptr, nullptr, 1, nullptr);
+      if (rc) return rc;
+    }
+    RMGTD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    dev_free(ctx, q);
+  }
+  // P_0 = diag(f), H_0 = H[rho(P_0)], H_-1 = H_0
+  k_diag_init<<<std::max(1, (int)std::min<long>(ceil_div(NN * nrep, 256), 1024)), 256, 0, ctx->stream>>>(
+      N, nrep, ctx->f_dev, ctx->S0, ctx->A0);
+  RMGTD_LAUNCH(ctx, "k_diag_init");
+  k_set_active<<<1, 32, 0, ctx->stream>>>(ctx->ctl, nrep, 1);
+  rc = dft_eval(ctx, ctx->S0, ctx->ctl, nullptr);
+  if (rc) return rc;
+  RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->H0, ctx->H1, msz * nrep, cudaMemcpyDeviceToDevice, ctx->stream));
+  RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->Hm1, ctx->H1, msz * nrep, cudaMemcpyDeviceToDevice, ctx->stream));
+  RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->S1, ctx->S0, msz * nrep, cudaMemcpyDeviceToDevice, ctx->stream));
+  RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->A1, ctx->A0, msz * nrep, cudaMemcpyDeviceToDevice, ctx->stream));
+  k_set_active<<<1, 32, 0, ctx->stream>>>(ctx->ctl, nrep, 0);
+  return check_status(ctx, "create");
+}
+
+int rmgtd_create(const rmgtd_system* sys, const rmgtd_options* opt_in, rmgtd_ctx** out) {
+  if (!out) return set_error(nullptr, RMGTD_EINVAL, "out is NULL");
+  *out = nullptr;
+  rmgtd_options opt;
+  if (opt_in)
+    opt = *opt_in;
+  else
+    rmgtd_default_options(&opt);
+  if (!sys || !sys->phi0) return set_error(nullptr, RMGTD_EINVAL, "system or phi0 is NULL");
+  if (sys->nx < 8 || sys->ny < 8 || sys->nz < 8 || !(sys->h > 0))
+    return set_error(nullptr, RMGTD_EINVAL, "grid must be at least 8^3 with h > 0");
+  if (sys->nocc < 1 || sys->nvirt < 0 || sys->nocc + sys->nvirt > 8192)
+    return set_error(nullptr, RMGTD_EINVAL, "active space must have 1 <= N <= 8192");
+  if (sys->natoms < 0 || (sys->natoms > 0 && (!sys->pos || !sys->Z || !sys->rc_loc)))
+    return set_error(nullptr, RMGTD_EINVAL, "atom arrays missing");
+  if (sys->nproj < 0 ||
+      (sys->nproj > 0 && (!sys->proj_atom || !sys->proj_l || !sys->proj_rc || !sys->E_kb)))
+    return set_error(nullptr, RMGTD_EINVAL, "projector arrays missing");
+  if (opt.nrep < 1 || opt.nrep > 32) return set_error(nullptr, RMGTD_EINVAL, "nrep must be 1..32");
+  if (!(opt.dt > 0) || !(opt.H_thrs > 0) || !(opt.dP_thrs > 0) || opt.max_scf < 1 ||
+      opt.max_terms < 1 || !(opt.poisson_tol > 0) || opt.poisson_max_iter < 1)
+    return set_error(nullptr, RMGTD_EINVAL, "invalid options");
+  if (opt.precision != RMGTD_PREC_FP64 && opt.precision != RMGTD_PREC_MIXED)
+    return set_error(nullptr, RMGTD_EINVAL, "unknown precision");
+  rmgtd_ctx* ctx = new rmgtd_ctx();
+  int rc = create_impl(sys, &opt, ctx);
+  if (rc != RMGTD_OK) {
+    g_last_error = ctx->err;
+    rmgtd_destroy(ctx);
+    return rc;
+  }
+  *out = ctx;
+  return RMGTD_OK;
+}
+
+int rmgtd_apply_h(rmgtd_ctx* ctx, const void* x, void* hx, int ncols, int dtype, int rep) {
+  if (!ctx) return set_error(nullptr, RMGTD_EINVAL, "ctx is NULL");
+  if (!x || !hx || ncols < 1 || rep < -1 || rep >= ctx->nrep)
+    return set_error(ctx, RMGTD_EINVAL, "apply_h: bad arguments");
+  const double* vextra = (rep >= 0) ? ctx->vhxc + (long)rep * ctx->Ng : nullptr;
+  return apply_h_dev(ctx, x, hx, ncols, dtype, vextra);
+}
+
+int rmgtd_kick(rmgtd_ctx* ctx, int rep, int axis, double kappa) {
+  if (!ctx) return set_error(nullptr, RMGTD_EINVAL, "ctx is NULL");
+  if (rep < 0 || rep >= ctx->nrep || axis < 0 || axis > 2)
+    return set_error(ctx, RMGTD_EINVAL, "kick: bad replica or axis");
+  const long NN = (long)ctx->N * ctx->N;
+  RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream));
+  const double* Mq = ctx->M + axis * NN;
+  int rc = eldyn(ctx, Mq, Mq, 0, kappa, ctx->S0 + rep * NN, ctx->A0 + rep * NN,
+                 ctx->S1 + rep * NN, ctx->A1 + rep * NN, nullptr, nullptr, rep, 1);
+  if (rc) return rc;
+  RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->S0 + rep * NN, ctx->S1 + rep * NN, sizeof(double) * NN,
+                                  cudaMemcpyDeviceToDevice, ctx->stream));
+  RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->A0 + rep * NN, ctx->A1 + rep * NN, sizeof(double) * NN,
+                                  cudaMemcpyDeviceToDevice, ctx->stream));
+  rc = refresh_fields(ctx);
+  if (rc) return rc;
+  return check_status(ctx, "kick");
+}
+
+int rmgtd_step(rmgtd_ctx* ctx, int nsteps, rmgtd_stats* stats) {
+  if (!ctx) return set_error(nullptr, RMGTD_EINVAL, "ctx is NULL");
+  if (nsteps < 0) return set_error(ctx, RMGTD_EINVAL, "nsteps < 0");
+  const int nrep = ctx->nrep;
+  const long NN = (long)ctx->N * ctx->N;
+  const size_t msz = sizeof(double) * NN * nrep;
+  for (int s = 0; s < nsteps; ++s) {
+    RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream));
+    int rc = step_begin(ctx);
+    if (rc) return rc;
+    for (int pass = 0; pass < ctx->opt.max_scf; ++pass) {
+      rc = eldyn(ctx, ctx->H0, ctx->H1, NN, ctx->opt.dt, ctx->S0, ctx->A0, ctx->S1, ctx->A1,
+                 ctx->ctl, ctx->ctl, 0, nrep);
+      if (rc) return rc;
+      rc = dft_eval(ctx, ctx->S1, ctx->ctl, ctx->errbits);
+      if (rc) return rc;
+      rc = scf_control(ctx, ctx->errbits);
+      if (rc) return rc;
+      RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->ctl_host, ctx->ctl, sizeof(RepCtl) * nrep,
+                                      cudaMemcpyDeviceToHost, ctx->stream));
+      RMGTD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+      bool any = false;
+      for (int r = 0; r < nrep; ++r) any |= ctx->ctl_host[r].active != 0;
+      if (!any) break;
+    }
+    int worst = RMGTD_OK;
+    for (int r = 0; r < nrep; ++r) {
+      const RepCtl& c = ctx->ctl_host[r];
+      if (stats) {
+        rmgtd_stats& o = stats[(long)s * nrep + r];
+        o.passes = c.passes;
+        o.terms_max = c.terms_max;
+        o.terms_sum = c.terms_sum;
+        o.status = c.status;
+        o.H_err = c.H_err;
+      }
+      if (c.status != 0 && worst == RMGTD_OK) worst = c.status;
+    }
+    if (worst == RMGTD_OK) {
+      int st = check_status(ctx, "step");
+      if (st) return st;
+    }
+    if (worst != RMGTD_OK) {
+      char buf[128];
+      snprintf(buf, sizeof(buf), "step %lld failed with status %d", ctx->steps + 1, worst);
+      return set_error(ctx, worst, buf);
+    }
+    // H_-1 <- H_0, H_0 <- H_1, P_0 <- P_1 (Algorithm 1 line 28)
+    RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->Hm1, ctx->H0, msz, cudaMemcpyDeviceToDevice, ctx->stream));
+    RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->H0, ctx->H1, msz, cudaMemcpyDeviceToDevice, ctx->stream));
+    RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->S0, ctx->S1, msz, cudaMemcpyDeviceToDevice, ctx->stream));
+    RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->A0, ctx->A1, msz, cudaMemcpyDeviceToDevice, ctx->stream));
+    ctx->t += ctx->opt.dt;
+    ctx->steps += 1;
+  }
+  RMGTD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return RMGTD_OK;
+}
+
+int rmgtd_density(rmgtd_ctx* ctx, int rep, double* rho_host) {
+  if (!ctx) return set_error(nullptr, RMGTD_EINVAL, "ctx is NULL");
+  if (rep < 0 || rep >= ctx->nrep || !rho_host) return set_error(ctx, RMGTD_EINVAL, "density: bad arguments");
+  int rc = rho_dev(ctx, ctx->S0, ctx->rho, nullptr, ctx->nrep);
+  if (rc) return rc;
+  RMGTD_CUDA(ctx, cudaMemcpyAsync(rho_host, ctx->rho + (long)rep * ctx->Ng, sizeof(double) * ctx->Ng,
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+  RMGTD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return RMGTD_OK;
+}
+
+static int fetch_obs(rmgtd_ctx* ctx) {
+  int rc = observables(ctx);
+  if (rc) return rc;
+  RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->obs_host, ctx->obs, sizeof(double) * 8 * ctx->nrep,
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+  RMGTD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return RMGTD_OK;
+}
+
+int rmgtd_dipole(rmgtd_ctx* ctx, int rep, double mu[3]) {
+  if (!ctx) return set_error(nullptr, RMGTD_EINVAL, "ctx is NULL");
+  if (rep < 0 || rep >= ctx->nrep || !mu) return set_error(ctx, RMGTD_EINVAL, "dipole: bad arguments");
+  int rc = fetch_obs(ctx);
+  if (rc) return rc;
+  for (int d = 0; d < 3; ++d) mu[d] = ctx->obs_host[8 * rep + d];
+  return RMGTD_OK;
+}
+
+int rmgtd_energy(rmgtd_ctx* ctx, int rep, double* E) {
+  if (!ctx) return set_error(nullptr, RMGTD_EINVAL, "ctx is NULL");
+  if (rep < 0 || rep >= ctx->nrep || !E) return set_error(ctx, RMGTD_EINVAL, "energy: bad arguments");
+  int rc = fetch_obs(ctx);
+  if (rc) return rc;
+  *E = ctx->obs_host[8 * rep + 4];
+  return RMGTD_OK;
+}
+
+static double* matrix_ptr(rmgtd_ctx* ctx, int which, int rep, bool* shared) {
+  const long NN = (long)ctx->N * ctx->N;
+  *shared = false;
+  switch (which) {
+    case RMGTD_MAT_P_RE: return ctx->S0 + rep * NN;
+    case RMGTD_MAT_P_IM: return ctx->A0 + rep * NN;
+    case RMGTD_MAT_H0: return ctx->H0 + rep * NN;
+    case RMGTD_MAT_HM1: return ctx->Hm1 + rep * NN;
+  }
+  *shared = true;
+  switch (which) {
+    case RMGTD_MAT_HCORE: return ctx->Hcore;
+    case RMGTD_MAT_MX: return ctx->M;
+    case RMGTD_MAT_MY: return ctx->M + NN;
+    case RMGTD_MAT_MZ: return ctx->M + 2 * NN;
+    case RMGTD_MAT_S: return ctx->Smat;
+  }
+  return nullptr;
+}
+
+int rmgtd_get_matrix(rmgtd_ctx* ctx, int which, int rep, double* host_out) {
+  if (!ctx) return set_error(nullptr, RMGTD_EINVAL, "ctx is NULL");
+  if (rep < 0 || rep >= ctx->nrep || !host_out) return set_error(ctx, RMGTD_EINVAL, "get_matrix: bad arguments");
+  bool shared;
+  double* p = matrix_ptr(ctx, which, rep, &shared);
+  if (!p) return set_error(ctx, RMGTD_EINVAL, "get_matrix: unknown matrix");
+  RMGTD_CUDA(ctx, cudaMemcpyAsync(host_out, p, sizeof(double) * ctx->N * ctx->N,
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+  RMGTD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return RMGTD_OK;
+}
+
+int rmgtd_set_matrix(rmgtd_ctx* ctx, int which, int rep, const double* host_in) {
+  if (!ctx) return set_error(nullptr, RMGTD_EINVAL, "ctx is NULL");
+  if (rep < 0 || rep >= ctx->nrep || !host_in) return set_error(ctx, RMGTD_EINVAL, "set_matrix: bad arguments");
+  bool shared;
+  double* p = matrix_ptr(ctx, which, rep, &shared);
+  if (!p || shared) return set_error(ctx, RMGTD_EINVAL, "set_matrix: only P, H0, H-1 are writable");
+  RMGTD_CUDA(ctx, cudaMemcpyAsync(p, host_in, sizeof(double) * ctx->N * ctx->N,
+                                  cudaMemcpyHostToDevice, ctx->stream));
+  if (which == RMGTD_MAT_P_RE) {
+    int rc = refresh_fields(ctx);
+    if (rc) return rc;
+  }
+  RMGTD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return RMGTD_OK;
+}
+
+int rmgtd_hartree(rmgtd_ctx* ctx, const double* rho_dev, double* vh_dev) {
+  if (!ctx) return set_error(nullptr, RMGTD_EINVAL, "ctx is NULL");
+  if (!rho_dev || !vh_dev) return set_error(ctx, RMGTD_EINVAL, "hartree: NULL pointer");
+  RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream));
+  int rc = hartree_dev(ctx, rho_dev, vh_dev, nullptr, 0, 1);
+  if (rc) return rc;
+  return check_status(ctx, "hartree");
+}
+
+int rmgtd_xc(rmgtd_ctx* ctx, const double* rho_dev, double* vxc_dev, double* exc_dev, size_t n) {
+  if (!ctx) return set_error(nullptr, RMGTD_EINVAL, "ctx is NULL");
+  if (!rho_dev || !vxc_dev || n == 0) return set_error(ctx, RMGTD_EINVAL, "xc: bad arguments");
+  int rc = launch_lda(ctx, rho_dev, nullptr, vxc_dev, exc_dev, nullptr, (long)n, nullptr, 1, (long)n, 0);
+  if (rc) return rc;
+  RMGTD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return RMGTD_OK;
+}
+
+int rmgtd_time(rmgtd_ctx* ctx, double* t, long long* steps) {
+  if (!ctx) return set_error(nullptr, RMGTD_EINVAL, "ctx is NULL");
+  if (t) *t = ctx->t;
+  if (steps) *steps = ctx->steps;
+  return RMGTD_OK;
+}
+
+static const uint64_t kMagic = 0x31444d54474d52ull;  // "RMGTD1"
+
+int rmgtd_save(rmgtd_ctx* ctx, const char* path) {
+  if (!ctx) return set_error(nullptr, RMGTD_EINVAL, "ctx is NULL");
+  if (!path) return set_error(ctx, RMGTD_EINVAL, "save: path is NULL");
+  const long NN = (long)ctx->N * ctx->N;
+  const size_t mcount = (size_t)NN * ctx->nrep, gcount = (size_t)ctx->Ng * ctx->nrep;
+  std::vector<double> buf(4 * mcount + gcount);
+  double* parts[4] = {ctx->S0, ctx->A0, ctx->H0, ctx->Hm1};
+  for (int i = 0; i < 4; ++i)
+    RMGTD_CUDA(ctx, cudaMemcpyAsync(buf.data() + i * mcount, parts[i], sizeof(double) * mcount,
+                                    cudaMemcpyDeviceToHost, ctx->stream));
+  RMGTD_CUDA(ctx, cudaMemcpyAsync(buf.data() + 4 * mcount, ctx->vh, sizeof(double) * gcount,
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+  RMGTD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  FILE* fp = fopen(path, "wb");
+  if (!fp) return set_error(ctx, RMGTD_EINVAL, std::string("save: cannot open ") + path);
+  const int64_t hdr[6] = {ctx->nx, ctx->ny, ctx->nz, ctx->N, ctx->nrep, ctx->steps};
+  bool ok = fwrite(&kMagic, sizeof(kMagic), 1, fp) == 1 && fwrite(hdr, sizeof(hdr), 1, fp) == 1 &&
+            fwrite(&ctx->t, sizeof(double), 1, fp) == 1 &&
+            fwrite(buf.data(), sizeof(double), buf.size(), fp) == buf.size();
+  fclose(fp);
+  if (!ok) return set_error(ctx, RMGTD_EINVAL, "save: write failed");
+  return RMGTD_OK;
+}
+
+int rmgtd_load(rmgtd_ctx* ctx, const char* path) {
+  if (!ctx) return set_error(nullptr, RMGTD_EINVAL, "ctx is NULL");
+  if (!path) return set_error(ctx, RMGTD_EINVAL, "load: path is NULL");
+  FILE* fp = fopen(path, "rb");
+  if (!fp) return set_error(ctx, RMGTD_EINVAL, std::string("load: cannot open ") + path);
+  uint64_t magic = 0;
+  int64_t hdr[6];
+  double t = 0;
+  bool ok = fread(&magic, sizeof(magic), 1, fp) == 1 && fread(hdr, sizeof(hdr), 1, fp) == 1 &&
+            fread(&t, sizeof(double), 1, fp) == 1;
+  if (!ok || magic != kMagic || hdr[0] != ctx->nx || hdr[1] != ctx->ny || hdr[2] != ctx->nz ||
+      hdr[3] != ctx->N || hdr[4] != ctx->nrep) {
+    fclose(fp);
+    return set_error(ctx, RMGTD_EINVAL, "load: checkpoint does not match this context");
+  }
+  const long NN = (long)ctx->N * ctx->N;
+  const size_t mcount = (size_t)NN * ctx->nrep, gcount = (size_t)ctx->Ng * ctx->nrep;
+  std::vector<double> buf(4 * mcount + gcount);
+  ok = fread(buf.data(), sizeof(double), buf.size(), fp) == buf.size();
+  fclose(fp);
+  if (!ok) return set_error(ctx, RMGTD_EINVAL, "load: truncated checkpoint");
+  double* parts[4] = {ctx->S0, ctx->A0, ctx->H0, ctx->Hm1};
+  for (int i = 0; i < 4; ++i)
+    RMGTD_CUDA(ctx, cudaMemcpyAsync(parts[i], buf.data() + i * mcount, sizeof(double) * mcount,
+                                    cudaMemcpyHostToDevice, ctx->stream));
+  RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->vh, buf.data() + 4 * mcount, sizeof(double) * gcount,
+                                  cudaMemcpyHostToDevice, ctx->stream));
+  RMGTD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  ctx->t = t;
+  ctx->steps = hdr[5];
+  // observables need rho / eps_xc of the restored P; V_H is restored exactly (warm start)
+  int rc = rho_dev(ctx, ctx->S0, ctx->rho, nullptr, ctx->nrep);
+  if (rc) return rc;
+  rc = launch_lda(ctx, ctx->rho, ctx->hartree_xc ? ctx->vh : nullptr, ctx->vxc, ctx->exc,
+                  ctx->vhxc, ctx->Ng, nullptr, ctx->nrep, ctx->Ng, ctx->hartree_xc);
+  if (rc) return rc;
+  RMGTD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return RMGTD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,685 @@
+// Subspace kernels of Algorithm 1: Gram contractions h^3 A^T diag(w) B (H update, H_core,
+// dipole and overlap matrices), the density rho = sum_ij Re(P)_ij phi_i phi_j, the
+// commutator expansion of exp(Omega) P exp(Omega^dagger) (Eqs. 19, 33, 35), observables and
+// the SCF control word.  All float64.
+#include <math.h>
+
+#include "rmgtd_internal.cuh"
+
+namespace rmgtd {
+
+// ---------------------------------------------------------------------------------------
+// Gram contraction, split over the grid (K = Ng).  Output tile TS x TS per block; block
+// (pair, split, rep) accumulates sum_{g in split} A[i][g] w[g] B[j][g] for its tile into
+// part[rep][split][i*N+j].  For sym != 0 only tiles with I <= J are formed.
+constexpr int kGT = 32;
+
+__device__ __forceinline__ void pair_from_index(int p, int T, int sym, int& I, int& J) {
+  if (!sym) {
+    I = p / T;
+    J = p % T;
+    return;
+  }
+  int i = 0, rem = p;
+  while (rem >= T - i) {
+    rem -= T - i;
+    ++i;
+  }
+  I = i;
+  J = i + rem;
+}
+
+__global__ void __launch_bounds__(256)
+k_gram_partial(int N, long Ng, const double* __restrict__ A, const double* __restrict__ B,
+               const double* __restrict__ w, long wstride, int sym, int T, long chunk,
+               double* __restrict__ part, const RepCtl* __restrict__ ctl) {
+  const int rep = blockIdx.z;
+  if (ctl && !ctl[rep].active) return;
+  __shared__ double As[kGT][kGT + 1];
+  __shared__ double Bs[kGT][kGT + 1];
+  int I, J;
+  pair_from_index(blockIdx.x, T, sym, I, J);
+  const int split = blockIdx.y, nsplit = gridDim.y;
+  const long g_beg = (long)split * chunk;
+  const long g_end = min(Ng, g_beg + chunk);
+  const double* wr = w ? w + rep * wstride : nullptr;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  double acc00 = 0, acc01 = 0, acc10 = 0, acc11 = 0;
+  for (long g0 = g_beg; g0 < g_end; g0 += kGT) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int idx = tid + 256 * e;
+      const int r = idx >> 5, c = idx & 31;
+      const long g = g0 + c;
+      const int ia = I * kGT + r, jb = J * kGT + r;
+      double av = 0.0, bv = 0.0;
+      if (g < g_end) {
+        if (ia < N) av = A[(long)ia * Ng + g];
+        if (jb < N) {
+          bv = B[(long)jb * Ng + g];
+          if (wr) bv *= wr[g];
+        }
+      }
+      As[c][r] = av;
+      Bs[c][r] = bv;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int k = 0; k < kGT; ++k) {
+      const double a0 = As[k][ty], a1 = As[k][ty + 16];
+      const double b0 = Bs[k][tx], b1 = Bs[k][tx + 16];
+      acc00 = fma(a0, b0, acc00);
+      acc01 = fma(a0, b1, acc01);
+      acc10 = fma(a1, b0, acc10);
+      acc11 = fma(a1, b1, acc11);
+    }
+    __syncthreads();
+  }
+  double* out = part + ((long)rep * nsplit + split) * (long)N * N;
+  const int i0 = I * kGT + ty, i1 = i0 + 16, j0 = J * kGT + tx, j1 = j0 + 16;
+  if (i0 < N && j0 < N) out[(long)i0 * N + j0] = acc00;
+  if (i0 < N && j1 < N) out[(long)i0 * N + j1] = acc01;
+  if (i1 < N && j0 < N) out[(long)i1 * N + j0] = acc10;
+  if (i1 < N && j1 < N) out[(long)i1 * N + j1] = acc11;
+}
+
+// out[rep] = base + scale * sum_split part; symmetric outputs are mirrored.  When `prev`
+// is given, max_ij |out - prev| is folded into errbits[rep] (prev may alias out: every
+// element is read and written by the same thread).
+__global__ void k_gram_reduce(int N, int nsplit, const double* __restrict__ part, double scale,
+                              const double* __restrict__ base, double* out, long ostride,
+                              const double* prev, int sym, unsigned long long* errbits,
+                              const RepCtl* __restrict__ ctl) {
+  const int rep = blockIdx.y;
+  if (ctl && !ctl[rep].active) return;
+  __shared__ double sh[32];
+  const long NN = (long)N * N;
+  double emax = 0.0;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < NN;
+       e += (long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / N), j = (int)(e % N);
+    if (sym && j < i) continue;
+    double s = 0.0;
+    const double* p = part + (long)rep * nsplit * NN + e;
+    for (int k = 0; k < nsplit; ++k) s += p[(long)k * NN];
+    double v = scale * s;
+    if (base) v += base[e];
+    double* o = out + rep * ostride;
+    if (prev) emax = fmax(emax, fabs(v - prev[rep * ostride + e]));
+    o[e] = v;
+    if (sym && i != j) o[(long)j * N + i] = v;
+  }
+  if (errbits) {
+    emax = block_max(emax, sh);
+    if (threadIdx.x == 0) atomic_max_nonneg(&errbits[rep], emax);
+  }
+}
+
+static int gram_nsplit(rmgtd_ctx* ctx, int ntiles, int nrep) {
+  const long target = 4L * ctx->num_sms;
+  long ns = (target + (long)ntiles * nrep - 1) / ((long)ntiles * nrep);
+  ns = std::max<long>(1, std::min<long>(ns, ctx->Ng / 256 + 1));
+  // partial buffer bound
+  const long per = (long)nrep * ctx->N * ctx->N;
+  ns = std::min<long>(ns, (long)(ctx->gram_part_elems / std::max<long>(per, 1)));
+  return (int)std::max<long>(ns, 1);
+}
+
+int gram(rmgtd_ctx* ctx, const double* A, const double* B, const double* w, long wstride,
+         int nw, double scale, const double* base, double* out, const double* prev,
+         const RepCtl* ctl, int sym, unsigned long long* errbits) {
+  const int N = ctx->N;
+  const int T = ceil_div(N, kGT);
+  const int ntiles = sym ? T * (T + 1) / 2 : T * T;
+  const int nsplit = gram_nsplit(ctx, ntiles, nw);
+  const long chunk = ((ctx->Ng + nsplit - 1) / nsplit + kGT - 1) / kGT * kGT;
+  dim3 grid(ntiles, nsplit, nw);
+  k_gram_partial<<<grid, 256, 0, ctx->stream>>>(N, ctx->Ng, A, B, w, wstride, sym, T, chunk,
+                                                 ctx->gram_part, ctl);
+  RMGTD_LAUNCH(ctx, "k_gram_partial");
+  const long NN = (long)N * N;
+  const int rb = (int)std::min<long>(ceil_div(NN, 256), 2L * ctx->num_sms);
+  k_gram_reduce<<<dim3(rb, nw), 256, 0, ctx->stream>>>(N, nsplit, ctx->gram_part, scale, base,
+                                                        out, NN, prev, sym, errbits, ctl);
+  RMGTD_LAUNCH(ctx, "k_gram_reduce");
+  return RMGTD_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Density rho(g) = sum_ij S_ij phi_i(g) phi_j(g) with S = Re P symmetric, evaluated as
+// sum_j phi_j(g) X_j(g), X_j = sum_{k<=j} Shat_kj phi_k(g), Shat_kj = 2 S_kj (k<j), S_jj
+// (k=j): half of the N^2 products.  One thread per grid point, 32 columns j at a time.
+constexpr int kRhoJ = 32, kRhoK = 64, kRhoThreads = 128;
+
+__global__ void __launch_bounds__(kRhoThreads)
+k_rho(int N, long Ng, const double* __restrict__ phi, const double* __restrict__ S,
+      long sstride, double* __restrict__ rho, long rstride, const RepCtl* __restrict__ ctl) {
+  const int rep = blockIdx.y;
+  if (ctl && !ctl[rep].active) return;
+  __shared__ double Sh[kRhoK][kRhoJ];
+  const double* Sr = S + rep * sstride;
+  const long g = blockIdx.x * (long)kRhoThreads + threadIdx.x;
+  const bool ok = g < Ng;
+  double r = 0.0;
+  for (int jb = 0; jb < N; jb += kRhoJ) {
+    double acc[kRhoJ];
+#pragma unroll
+    for (int jj = 0; jj < kRhoJ; ++jj) acc[jj] = 0.0;
+    const int kend = min(N, jb + kRhoJ);
+    for (int k0 = 0; k0 < kend; k0 += kRhoK) {
+      __syncthreads();
+      for (int e = threadIdx.x; e < kRhoK * kRhoJ; e += kRhoThreads) {
+        const int kk = e / kRhoJ, jj = e % kRhoJ;
+        const int k = k0 + kk, j = jb + jj;
+        double v = 0.0;
+        if (k < N && j < N) {
+          if (k < j)
+            v = 2.0 * Sr[(long)k * N + j];
+          else if (k == j)
+            v = Sr[(long)j * N + j];
+        }
+        Sh[kk][jj] = v;
+      }
+      __syncthreads();
+      const int kn = min(kRhoK, kend - k0);
+      if (ok) {
+        for (int kk = 0; kk < kn; ++kk) {
+          const double pk = phi[(long)(k0 + kk) * Ng + g];
+#pragma unroll
+          for (int jj = 0; jj < kRhoJ; ++jj) acc[jj] = fma(Sh[kk][jj], pk, acc[jj]);
+        }
+      }
+    }
+    if (ok) {
+#pragma unroll
+      for (int jj = 0; jj < kRhoJ; ++jj)
+        if (jb + jj < N) r = fma(phi[(long)(jb + jj) * Ng + g], acc[jj], r);
+    }
+  }
+  if (ok) rho[rep * rstride + g] = r;
+}
+
+int rho_dev(rmgtd_ctx* ctx, const double* S, double* rho, const RepCtl* ctl, int nrep) {
+  dim3 grid(ceil_div(ctx->Ng, kRhoThreads), nrep);
+  k_rho<<<grid, kRhoThreads, 0, ctx->stream>>>(ctx->N, ctx->Ng, ctx->phi, S,
+                                                (long)ctx->N * ctx->N, rho, ctx->Ng, ctl);
+  RMGTD_LAUNCH(ctx, "k_rho");
+  return RMGTD_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Commutator expansion (Algorithm 1, lines 15-22) in the real split of Eq. 35.  With
+// P = S + iA (S symmetric, A antisymmetric), Hbar real symmetric and Omega = -i tau Hbar:
+//   S_k =  (tau/k) [Hbar, A_{k-1}] = (tau/k) (T1 + T1^T),  T1 = Hbar A_{k-1}
+//   A_k = -(tau/k) [Hbar, S_{k-1}] = -(tau/k) (T2 - T2^T), T2 = Hbar S_{k-1}
+// starting from (S_0, A_0) = P_0, P_1 = sum_k (S_k, A_k), stopped when
+// max_ij |S_k + i A_k| <= thrs.  One cooperative launch runs the whole series for every
+// replica: each block owns symmetric tile pairs (I <= J) and forms T1, T2 for (I,J) and
+// (J,I), so the transpose in the commutator never leaves the block; one grid barrier per
+// term publishes the new terms and the per-term maxima.
+struct EldynArgs {
+  int N;
+  int nrep;            // replicas in this launch
+  int rep0;            // first replica index (for ctl / slots)
+  const double* Ha;    // Hbar = (Ha + Hb)/2, replica stride hstride
+  const double* Hb;
+  long hstride;
+  double tau;
+  const double* S0;    // [rep][N*N] inputs
+  const double* A0;
+  double* S1;          // [rep][N*N] outputs
+  double* A1;
+  double* dbuf;        // [rep][2][2][N*N]
+  const RepCtl* ctl_in;   // active flags (NULL: all active)
+  RepCtl* ctl_out;        // term statistics (NULL: none)
+  unsigned long long* slots;  // [rep][max_terms+1]
+  int max_terms;
+  double thrs;
+  unsigned* bar;
+  int* status;
+};
+
+template <int TS>
+__global__ void __launch_bounds__(256) k_eldyn(EldynArgs a) {
+  constexpr int KC = 32;
+  constexpr int TSP = TS + 1;
+  constexpr int OPT = (4 * TS * TS) / 256;
+  extern __shared__ double smem[];
+  double* Hi = smem;                 // [TS][KC+1]
+  double* Hj = Hi + TS * (KC + 1);
+  double* Ai = Hj + TS * (KC + 1);   // [KC][TSP]
+  double* Aj = Ai + KC * TSP;
+  double* Si = Aj + KC * TSP;
+  double* Sj = Si + KC * TSP;
+  double* Tt = Sj + KC * TSP;        // [4][TS][TSP]
+  __shared__ double sh[32];
+  __shared__ int conv[32];
+  __shared__ int all_done;
+
+  const int N = a.N;
+  const long NN = (long)N * N;
+  const int T = (N + TS - 1) / TS;
+  const int npairs = T * (T + 1) / 2;
+  const int total = npairs * a.nrep;
+  const int tid = threadIdx.x;
+
+  if (tid < 32) {
+    int c = 1;
+    if (tid < a.nrep) c = (a.ctl_in && !a.ctl_in[a.rep0 + tid].active) ? 1 : 0;
+    conv[tid] = c;
+  }
+  __syncthreads();
+
+  // P_1 <- P_0 on the owned tiles
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    const int rep = item / npairs;
+    if (conv[rep]) continue;
+    int I, J;
+    pair_from_index(item % npairs, T, 1, I, J);
+    for (int e = tid; e < TS * TS; e += 256) {
+      const int i = I * TS + e / TS, j = J * TS + e % TS;
+      if (i < N && j < N) {
+        const long o = rep * NN + (long)i * N + j, ot = rep * NN + (long)j * N + i;
+        a.S1[o] = a.S0[o];
+        a.A1[o] = a.A0[o];
+        if (I != J) {
+          a.S1[ot] = a.S0[ot];
+          a.A1[ot] = a.A0[ot];
+        }
+      }
+    }
+  }
+
+  int k = 0;
+  while (true) {
+    ++k;
+    const double c = a.tau / (double)k;
+    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+      const int rep = item / npairs;
+      if (conv[rep]) continue;
+      int I, J;
+      pair_from_index(item % npairs, T, 1, I, J);
+      const double* dS = (k == 1) ? a.S0 + rep * NN : a.dbuf + ((long)rep * 4 + ((k - 1) & 1) * 2) * NN;
+      const double* dA = (k == 1) ? a.A0 + rep * NN : dS + NN;
+      double* oS = a.dbuf + ((long)rep * 4 + (k & 1) * 2) * NN;
+      double* oA = oS + NN;
+      const double* Ha = a.Ha + rep * a.hstride;
+      const double* Hb = a.Hb + rep * a.hstride;
+      double acc[OPT];
+#pragma unroll
+      for (int u = 0; u < OPT; ++u) acc[u] = 0.0;
+      for (int k0 = 0; k0 < N; k0 += KC) {
+        for (int e = tid; e < TS * KC; e += 256) {
+          const int r = e / KC, kk = e % KC;
+          const int kg = k0 + kk;
+          const int ri = I * TS + r, rj = J * TS + r;
+          double hi = 0.0, hj = 0.0;
+          if (kg < N) {
+            if (ri < N) hi = 0.5 * (Ha[(long)ri * N + kg] + Hb[(long)ri * N + kg]);
+            if (rj < N) hj = 0.5 * (Ha[(long)rj * N + kg] + Hb[(long)rj * N + kg]);
+          }
+          Hi[r * (KC + 1) + kk] = hi;
+          Hj[r * (KC + 1) + kk] = hj;
+        }
+        for (int e = tid; e < KC * TS; e += 256) {
+          const int kk = e / TS, b = e % TS;
+          const int kg = k0 + kk;
+          const int ci = I * TS + b, cj = J * TS + b;
+          double ai = 0, aj = 0, si = 0, sj = 0;
+          if (kg < N) {
+            if (ci < N) {
+              ai = dA[(long)kg * N + ci];
+              si = dS[(long)kg * N + ci];
+            }
+            if (cj < N) {
+              aj = dA[(long)kg * N + cj];
+              sj = dS[(long)kg * N + cj];
+            }
+          }
+          Ai[kk * TSP + b] = ai;
+          Aj[kk * TSP + b] = aj;
+          Si[kk * TSP + b] = si;
+          Sj[kk * TSP + b] = sj;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < OPT; ++u) {
+          const int o = tid + 256 * u;
+          const int q = o / (TS * TS), e = o % (TS * TS);
+          const int ra = e / TS, cb = e % TS;
+          const double* Hx = (q == 0 || q == 2) ? Hi : Hj;
+          const double* Dx = (q == 0) ? Aj : (q == 1) ? Ai : (q == 2) ? Sj : Si;
+          double s = acc[u];
+#pragma unroll 8
+          for (int kk = 0; kk < KC; ++kk) s = fma(Hx[ra * (KC + 1) + kk], Dx[kk * TSP + cb], s);
+          acc[u] = s;
+        }
+        __syncthreads();
+      }
+#pragma unroll
+      for (int u = 0; u < OPT; ++u) {
+        const int o = tid + 256 * u;
+        const int q = o / (TS * TS), e = o % (TS * TS);
+        Tt[q * TS * TSP + (e / TS) * TSP + (e % TS)] = acc[u];
+      }
+      __syncthreads();
+      double emax = 0.0;
+      for (int e = tid; e < TS * TS; e += 256) {
+        const int ra = e / TS, cb = e % TS;
+        const int i = I * TS + ra, j = J * TS + cb;
+        if (i >= N || j >= N) continue;
+        const double t1ij = Tt[0 * TS * TSP + ra * TSP + cb];
+        const double t1ji = Tt[1 * TS * TSP + cb * TSP + ra];
+        const double t2ij = Tt[2 * TS * TSP + ra * TSP + cb];
+        const double t2ji = Tt[3 * TS * TSP + cb * TSP + ra];
+        const double ns = c * (t1ij + t1ji);
+        const double na = -c * (t2ij - t2ji);
+        const long o = (long)i * N + j;
+        oS[o] = ns;
+        oA[o] = na;
+        a.S1[rep * NN + o] += ns;
+        a.A1[rep * NN + o] += na;
+        if (I != J) {
+          const long ot = (long)j * N + i;
+          oS[ot] = ns;
+          oA[ot] = -na;
+          a.S1[rep * NN + ot] += ns;
+          a.A1[rep * NN + ot] -= na;
+        }
+        emax = fmax(emax, sqrt(ns * ns + na * na));
+      }
+      emax = block_max(emax, sh);
+      if (tid == 0) atomic_max_nonneg(&a.slots[(long)rep * (a.max_terms + 1) + k], emax);
+      __syncthreads();
+    }
+    if (!grid_barrier(a.bar, gridDim.x * (unsigned)k, a.status)) return;
+    if (tid == 0) {
+      int done = 1;
+      for (int r = 0; r < a.nrep; ++r) {
+        if (conv[r]) continue;
+        const unsigned long long bits = *((volatile unsigned long long*)&a.slots[(long)r * (a.max_terms + 1) + k]);
+        const double err = __longlong_as_double((long long)bits);
+        bool finished = false;
+        if (!(err <= 1e300)) {  // NaN or inf
+          if (blockIdx.x == 0) atomicCAS(a.status, 0, (int)RMGTD_EDIVERGED);
+          if (blockIdx.x == 0 && a.ctl_out) a.ctl_out[a.rep0 + r].status = RMGTD_EDIVERGED;
+          finished = true;
+        } else if (err <= a.thrs) {
+          finished = true;
+        } else if (k >= a.max_terms) {
+          if (blockIdx.x == 0) atomicCAS(a.status, 0, (int)RMGTD_ENOTCONVERGED);
+          if (blockIdx.x == 0 && a.ctl_out) a.ctl_out[a.rep0 + r].status = RMGTD_ENOTCONVERGED;
+          finished = true;
+        }
+        if (finished) {
+          conv[r] = 1;
+          if (blockIdx.x == 0 && a.ctl_out) {
+            RepCtl& cr = a.ctl_out[a.rep0 + r];
+            cr.terms_last = k;
+            cr.terms_sum += k;
+            cr.terms_max = max(cr.terms_max, k);
+          }
+        } else {
+          done = 0;
+        }
+      }
+      all_done = done;
+    }
+    __syncthreads();
+    if (all_done) break;
+  }
+}
+
+template <int TS>
+static int launch_eldyn_ts(rmgtd_ctx* ctx, EldynArgs& a) {
+  const int KC = 32;
+  const size_t smem = sizeof(double) * (2 * TS * (KC + 1) + 4 * KC * (TS + 1) + 4 * TS * (TS + 1));
+  static bool attr_set = false;
+  if (!attr_set) {
+    RMGTD_CUDA(ctx, cudaFuncSetAttribute(k_eldyn<TS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem));
+    attr_set = true;
+  }
+  int per_sm = 0;
+  RMGTD_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_eldyn<TS>, 256, smem));
+  if (per_sm < 1) return set_error(ctx, RMGTD_ECUDA, "commutator kernel does not fit on an SM");
+  const int T = (a.N + TS - 1) / TS;
+  const int total = T * (T + 1) / 2 * a.nrep;
+  const int grid = std::max(1, std::min(total, per_sm * ctx->num_sms));
+  RMGTD_CUDA(ctx, cudaMemsetAsync(a.bar, 0, sizeof(unsigned), ctx->stream));
+  RMGTD_CUDA(ctx, cudaMemsetAsync(a.slots, 0,
+                                  sizeof(unsigned long long) * (size_t)a.nrep * (a.max_terms + 1),
+                                  ctx->stream));
+  void* args[] = {&a};
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = ctx->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  RMGTD_CUDA(ctx, cudaLaunchKernelExC(&cfg, (const void*)k_eldyn<TS>, args));
+  return RMGTD_OK;
+}
+
+int eldyn(rmgtd_ctx* ctx, const double* Ha, const double* Hb, long hstride, double tau,
+          const double* S0, const double* A0, double* S1, double* A1, const RepCtl* ctl_in,
+          RepCtl* ctl_out, int rep0, int nreps) {
+  if (nreps > 32) return set_error(ctx, RMGTD_EINVAL, "at most 32 replicas per expansion");
+  EldynArgs a;
+  a.N = ctx->N;
+  a.nrep = nreps;
+  a.rep0 = rep0;
+  a.Ha = Ha;
+  a.Hb = Hb;
+  a.hstride = hstride;
+  a.tau = tau;
+  a.S0 = S0;
+  a.A0 = A0;
+  a.S1 = S1;
+  a.A1 = A1;
+  a.dbuf = ctx->dbuf;
+  a.ctl_in = ctl_in;
+  a.ctl_out = ctl_out;
+  a.slots = ctx->errslots;
+  a.max_terms = ctx->opt.max_terms;
+  a.thrs = ctx->opt.dP_thrs;
+  a.bar = ctx->bar;
+  a.status = ctx->status;
+  if (ctx->N <= 64) return launch_eldyn_ts<8>(ctx, a);
+  if (ctx->N <= 512) return launch_eldyn_ts<16>(ctx, a);
+  return launch_eldyn_ts<32>(ctx, a);
+}
+
+// ---------------------------------------------------------------------------------------
+// Step bookkeeping.
+// H_1 <- 2 H_0 - H_-1 (Algorithm 1 line 11) for every replica; reset the control blocks.
+__global__ void k_step_begin(long n, const double* __restrict__ H0, const double* __restrict__ Hm1,
+                             double* __restrict__ H1, RepCtl* ctl, int nrep) {
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n;
+       e += (long)gridDim.x * blockDim.x)
+    H1[e] = 2.0 * H0[e] - Hm1[e];
+  if (blockIdx.x == 0 && threadIdx.x < nrep) {
+    RepCtl& c = ctl[threadIdx.x];
+    c.active = 1;
+    c.passes = 0;
+    c.terms_last = c.terms_max = c.terms_sum = 0;
+    c.status = 0;
+    c.H_err = 0.0;
+  }
+}
+
+// After one DFT evaluation: H_err = max|H_new - H_1| (already in errbits), decide per
+// replica whether the SCF loop continues.
+__global__ void k_scf_control(RepCtl* ctl, int nrep, const unsigned long long* errbits,
+                              double H_thrs, int max_scf, int* status) {
+  const int r = threadIdx.x;
+  if (r >= nrep) return;
+  RepCtl& c = ctl[r];
+  if (!c.active) return;
+  c.passes += 1;
+  const double err = __longlong_as_double((long long)errbits[r]);
+  c.H_err = err;
+  if (c.status != 0) {
+    c.active = 0;
+  } else if (!(err <= 1e300)) {
+    c.status = RMGTD_EDIVERGED;
+    c.active = 0;
+    atomicCAS(status, 0, (int)RMGTD_EDIVERGED);
+  } else if (err <= H_thrs) {
+    c.active = 0;
+  } else if (c.passes >= max_scf) {
+    c.status = RMGTD_ENOTCONVERGED;
+    c.active = 0;
+    atomicCAS(status, 0, (int)RMGTD_ENOTCONVERGED);
+  }
+}
+
+int step_begin(rmgtd_ctx* ctx) {
+  const long n = (long)ctx->nrep * ctx->N * ctx->N;
+  const int blocks = (int)std::min<long>(ceil_div(n, 256), 2L * ctx->num_sms);
+  k_step_begin<<<std::max(blocks, 1), 256, 0, ctx->stream>>>(n, ctx->H0, ctx->Hm1, ctx->H1,
+                                                              ctx->ctl, ctx->nrep);
+  RMGTD_LAUNCH(ctx, "k_step_begin");
+  return RMGTD_OK;
+}
+
+int scf_control(rmgtd_ctx* ctx, const unsigned long long* errbits) {
+  k_scf_control<<<1, 32, 0, ctx->stream>>>(ctx->ctl, ctx->nrep, errbits, ctx->opt.H_thrs,
+                                           ctx->opt.max_scf, ctx->status);
+  RMGTD_LAUNCH(ctx, "k_scf_control");
+  return RMGTD_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Observables per replica: d_q = Tr(S M_q) (q = x,y,z), Tr(S H_core), Tr(S),
+// h^3 sum rho V_H, h^3 sum rho eps_xc.  Two stages with fixed-order sums (deterministic).
+constexpr int kObs = 7;
+
+__global__ void k_obs_partial(int N, long Ng, const double* __restrict__ S,
+                              const double* __restrict__ M, const double* __restrict__ Hc,
+                              const double* __restrict__ rho, const double* __restrict__ vh,
+                              const double* __restrict__ exc, double* __restrict__ part) {
+  const int rep = blockIdx.y;
+  const long NN = (long)N * N;
+  const double* Sr = S + rep * NN;
+  const double* rr = rho + rep * Ng;
+  const double* vr = vh + rep * Ng;
+  const double* er = exc + rep * Ng;
+  double q[kObs] = {0, 0, 0, 0, 0, 0, 0};
+  const long stride = (long)gridDim.x * blockDim.x;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < NN; e += stride) {
+    const double s = Sr[e];
+    q[0] += s * M[e];
+    q[1] += s * M[NN + e];
+    q[2] += s * M[2 * NN + e];
+    q[3] += s * Hc[e];
+    const int i = (int)(e / N), j = (int)(e % N);
+    if (i == j) q[4] += s;
+  }
+  for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < Ng; g += stride) {
+    const double r = rr[g];
+    q[5] += r * vr[g];
+    q[6] += r * er[g];
+  }
+  __shared__ double sh[32];
+  for (int t = 0; t < kObs; ++t) {
+    const double v = block_sum(q[t], sh);
+    if (threadIdx.x == 0) part[((long)rep * kObs + t) * gridDim.x + blockIdx.x] = v;
+    __syncthreads();
+  }
+}
+
+__global__ void k_obs_final(int nblk, const double* __restrict__ part, double h3, double E_ion,
+                            double* __restrict__ obs) {
+  const int rep = blockIdx.x;
+  __shared__ double sh[32];
+  double v[kObs];
+  for (int t = 0; t < kObs; ++t) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += part[((long)rep * kObs + t) * nblk + b];
+    v[t] = block_sum(s, sh);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double* o = obs + 8 * rep;
+    o[0] = v[0];
+    o[1] = v[1];
+    o[2] = v[2];
+    o[3] = v[4];                                             // Tr(Re P)
+    o[4] = v[3] + 0.5 * h3 * v[5] + h3 * v[6] + E_ion;       // total energy
+    o[5] = v[3];                                             // Tr(Re P H_core)
+    o[6] = 0.5 * h3 * v[5];                                  // Hartree energy
+    o[7] = h3 * v[6];                                        // xc energy
+  }
+}
+
+int observables(rmgtd_ctx* ctx) {
+  const int nblk = ctx->red_blocks;
+  k_obs_partial<<<dim3(nblk, ctx->nrep), 256, 0, ctx->stream>>>(
+      ctx->N, ctx->Ng, ctx->S0, ctx->M, ctx->Hcore, ctx->rho, ctx->vh, ctx->exc, ctx->red_part);
+  RMGTD_LAUNCH(ctx, "k_obs_partial");
+  k_obs_final<<<ctx->nrep, 256, 0, ctx->stream>>>(nblk, ctx->red_part, ctx->h3, ctx->E_ion,
+                                                  ctx->obs);
+  RMGTD_LAUNCH(ctx, "k_obs_final");
+  return RMGTD_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Orthonormalisation of the starting orbitals: S = h^3 Phi^T Phi = L L^T (Cholesky, one
+// block, float64), then Phi <- L^{-1} Phi by forward substitution at every grid point.
+__global__ void k_cholesky(int N, double* __restrict__ S, int* status) {
+  for (int k = 0; k < N; ++k) {
+    __shared__ double d;
+    if (threadIdx.x == 0) {
+      const double v = S[(long)k * N + k];
+      if (!(v > 0.0)) atomicCAS(status, 0, (int)RMGTD_EINVAL);
+      d = sqrt(fmax(v, 1e-300));
+      S[(long)k * N + k] = d;
+    }
+    __syncthreads();
+    for (int i = k + 1 + threadIdx.x; i < N; i += blockDim.x) S[(long)i * N + k] /= d;
+    __syncthreads();
+    const long rem = (long)(N - k - 1);
+    for (long e = threadIdx.x; e < rem * rem; e += blockDim.x) {
+      const int i = k + 1 + (int)(e / rem), j = k + 1 + (int)(e % rem);
+      if (j <= i) S[(long)i * N + j] -= S[(long)i * N + k] * S[(long)j * N + k];
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_forward_subst(int N, long Ng, const double* __restrict__ L,
+                                double* __restrict__ phi, double* __restrict__ work) {
+  const long g = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (g >= Ng) return;
+  double* y = work;  // column-wise scratch [N][Ng] stored at y[i*Ng + g]
+  for (int i = 0; i < N; ++i) {
+    double s = phi[(long)i * Ng + g];
+    for (int j = 0; j < i; ++j) s -= L[(long)i * N + j] * y[(long)j * Ng + g];
+    y[(long)i * Ng + g] = s / L[(long)i * N + i];
+  }
+  for (int i = 0; i < N; ++i) phi[(long)i * Ng + g] = y[(long)i * Ng + g];
+}
+
+int orthonormalize(rmgtd_ctx* ctx) {
+  const int N = ctx->N;
+  int rc = gram(ctx, ctx->phi, ctx->phi, nullptr, 0, 1, ctx->h3, nullptr, ctx->Smat, nullptr,
+                nullptr, 1, nullptr);
+  if (rc) return rc;
+  k_cholesky<<<1, 1024, 0, ctx->stream>>>(N, ctx->Smat, ctx->status);
+  RMGTD_LAUNCH(ctx, "k_cholesky");
+  double* work = (double*)dev_alloc(ctx, sizeof(double) * (size_t)N * ctx->Ng);
+  if (!work) return set_error(ctx, RMGTD_ENOMEM, "orthonormalisation scratch");
+  k_forward_subst<<<ceil_div(ctx->Ng, 128), 128, 0, ctx->stream>>>(N, ctx->Ng, ctx->Smat,
+                                                                    ctx->phi, work);
+  RMGTD_LAUNCH(ctx, "k_forward_subst");
+  RMGTD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  dev_free(ctx, work);
+  return RMGTD_OK;
+}
+
+}  // namespace rmgtd

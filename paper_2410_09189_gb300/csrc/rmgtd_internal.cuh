@@ -1,0 +1,288 @@
+// Internal definitions shared by the translation units of librmgtd (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/rmgtd.h"
+
+namespace rmgtd {
+
+constexpr int kThreads = 256;
+constexpr int kFdRadius = 6;             // 12th-order central stencil (Section 2.1, Eq. 2)
+constexpr double kRhoFloor = 1e-14;      // LDA floor
+constexpr unsigned kSpinLimit = 20000000u;  // bounded device-side waits (~2 s)
+
+// 12th-order second-derivative weights a_0..a_6 (Fornberg closed form, exact rationals).
+__host__ __device__ inline double fd_coef(int m) {
+  switch (m) {
+    case 0: return -5369.0 / 1800.0;
+    case 1: return 12.0 / 7.0;
+    case 2: return -15.0 / 56.0;
+    case 3: return 10.0 / 189.0;
+    case 4: return -1.0 / 112.0;
+    case 5: return 2.0 / 1925.0;
+    case 6: return -1.0 / 16632.0;
+  }
+  return 0.0;
+}
+
+// Per-replica control block living in device memory.
+struct RepCtl {
+  int active;      // SCF loop still running for this replica in the current step
+  int passes;      // DFT evaluations in the current step
+  int terms_last;  // terms of the last commutator expansion
+  int terms_max;
+  int terms_sum;
+  int status;      // rmgtd_status of the current step
+  double H_err;    // last max|H_new - H_1|
+};
+
+// Per-replica state of the preconditioned CG Hartree solve.
+struct PcgState {
+  double rz[2];    // (r, z) of the previous iteration, double-buffered by `cur`
+  double bb;       // (b, b)
+  double rr;       // last (r, r)
+  int cur;
+  int it;
+  int done;
+  int status;
+};
+
+struct MgLevel {
+  int nx, ny, nz;
+  long n;
+  double h;
+  double* x;   // [nrep][n]
+  double* b;   // [nrep][n]
+  double* r;   // [nrep][n]
+};
+
+struct Buffer {
+  void* ptr;
+  size_t bytes;
+};
+
+}  // namespace rmgtd
+
+struct rmgtd_ctx {
+  // sizes
+  int nx = 0, ny = 0, nz = 0;
+  long Ng = 0;
+  int N = 0, nocc = 0, nvirt = 0, nrep = 1;
+  double h = 0, h3 = 0;
+  int hartree_xc = 1;
+  double v_ext_omega = 0;
+  rmgtd_options opt{};
+  cudaStream_t stream = nullptr;
+  int num_sms = 0;
+  int coop_ok = 0;
+
+  // host copies
+  std::vector<double> f;
+  double E_ion = 0;
+  double t = 0;
+  long long steps = 0;
+  std::string err;
+
+  // orbitals and potentials
+  double* phi = nullptr;       // [N][Ng]
+  float* phi32 = nullptr;      // [N][Ng] (mixed precision)
+  double* vion = nullptr;      // [Ng] V_loc + V_ext
+  double* f_dev = nullptr;     // [N]
+
+  // Kleinman-Bylander projectors as dense boxes
+  int nproj = 0;
+  int* pbox = nullptr;         // [nproj][6] x0,y0,z0,bx,by,bz
+  long long* poff = nullptr;   // [nproj+1] offsets into pval
+  double* pval = nullptr;      // box values (normalised)
+  double* Ekb = nullptr;       // [nproj]
+  double* kb_coef = nullptr;   // [2][ncols][nproj] projections (re, im)
+  int kb_coef_cols = 0;
+  std::vector<int> h_pbox;
+  std::vector<long long> h_poff;
+  std::vector<double> h_Ekb;
+
+  // shared N x N matrices
+  double* Hcore = nullptr;
+  double* M = nullptr;         // [3][N*N]
+  double* Smat = nullptr;
+  double* Href = nullptr;      // H_core + h^3 Phi^T V_ref Phi (mixed reference)
+
+  // replica N x N matrices [nrep][N*N]
+  double *S0 = nullptr, *A0 = nullptr, *S1 = nullptr, *A1 = nullptr;
+  double *H0 = nullptr, *Hm1 = nullptr, *H1 = nullptr, *Hnew = nullptr;
+  double* dbuf = nullptr;      // [nrep][4][N*N] commutator-series work
+  double* Sref = nullptr;      // [N*N] reference Re P for the mixed path (diag f)
+
+  // grid fields [nrep][Ng]
+  double *rho = nullptr, *vh = nullptr, *vxc = nullptr, *exc = nullptr, *vhxc = nullptr;
+  double* rho_ref = nullptr;   // [Ng] density of Sref (mixed)
+  double* vref = nullptr;      // [Ng] reference V_Hxc (mixed)
+  float* dv32 = nullptr;       // [nrep][Ng] V_Hxc - vref (mixed)
+
+  // split-K partials of the Gram contractions
+  double* gram_part = nullptr;
+  size_t gram_part_elems = 0;
+
+  // Hartree solve
+  double *pcg_b = nullptr, *pcg_r = nullptr, *pcg_z = nullptr, *pcg_p = nullptr,
+         *pcg_Ap = nullptr;    // [nrep][Ng]
+  double* red_part = nullptr;  // reduction partials
+  int red_blocks = 0;
+  rmgtd::PcgState* pcg = nullptr;   // [nrep]
+  int* pcg_any = nullptr;           // device flag: some replica still iterating
+  int* pcg_any_host = nullptr;      // pinned
+  double* mpole = nullptr;          // [nrep][4] Q, px, py, pz
+  std::vector<rmgtd::MgLevel> mg;   // multi-CTA levels (level 0 = fine grid)
+  int mg_tail_level = -1;           // first level solved inside one CTA
+  size_t mg_tail_smem = 0;
+
+  // control
+  rmgtd::RepCtl* ctl = nullptr;     // [nrep]
+  rmgtd::RepCtl* ctl_host = nullptr;  // pinned host mirror
+  unsigned int* bar = nullptr;      // grid-barrier counter
+  unsigned long long* errslots = nullptr;  // [nrep][max_terms+1]
+  unsigned long long* errbits = nullptr;   // [nrep] SCF error max
+  int* status = nullptr;            // device-wide status word
+  double* obs = nullptr;            // [nrep][8] observables
+  double* obs_host = nullptr;       // pinned
+
+  // CUDA graph of one time step
+  cudaGraphExec_t step_exec = nullptr;
+  cudaGraph_t step_graph = nullptr;
+
+  std::vector<rmgtd::Buffer> buffers;
+};
+
+namespace rmgtd {
+
+// ---- error helpers -----------------------------------------------------------------
+int set_error(rmgtd_ctx* ctx, int code, const std::string& msg);
+int cuda_check(rmgtd_ctx* ctx, cudaError_t e, const char* what);
+#define RMGTD_CUDA(ctx, call)                                  \
+  do {                                                         \
+    cudaError_t _e = (call);                                   \
+    if (_e != cudaSuccess) return rmgtd::cuda_check(ctx, _e, #call); \
+  } while (0)
+#define RMGTD_LAUNCH(ctx, what)                                \
+  do {                                                         \
+    cudaError_t _e = cudaGetLastError();                       \
+    if (_e != cudaSuccess) return rmgtd::cuda_check(ctx, _e, what); \
+  } while (0)
+
+void* dev_alloc(rmgtd_ctx* ctx, size_t bytes);
+
+// ---- device helpers ----------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sumf(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Block-wide sum of `v` (blockDim.x a multiple of 32, <= 1024); result valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    v = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : 0.0;
+    v = warp_sum(v);
+  }
+  return v;
+}
+__device__ __forceinline__ double block_max(double v, double* sh) {
+  v = warp_max(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    v = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : 0.0;
+    v = warp_max(v);
+  }
+  return v;
+}
+
+// max of non-negative doubles via their IEEE bit patterns (NaN sorts above +inf).
+__device__ __forceinline__ void atomic_max_nonneg(unsigned long long* addr, double v) {
+  atomicMax(addr, (unsigned long long)__double_as_longlong(v));
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Grid-wide barrier for cooperative launches.  `count` is zeroed before the launch and
+// only grows; `target` = gridDim.x * (number of this barrier, counting from 1).  The wait
+// gives up after kSpinLimit polls and records RMGTD_ETIMEOUT in *status; returns false then.
+__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned target, int* status) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    __threadfence();
+    atomicAdd(count, 1u);
+    unsigned spins = 0;
+    while (ld_acquire_u32(count) < target) {
+      if (++spins > kSpinLimit) {
+        atomicCAS(status, 0, (int)RMGTD_ETIMEOUT);
+        ok = 0;
+        break;
+      }
+      __nanosleep(64);
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+__host__ __device__ inline double axis_coord(int i, int n, double h) {
+  return ((double)i - 0.5 * (double)(n - 1)) * h;
+}
+
+inline int ceil_div(long a, long b) { return (int)((a + b - 1) / b); }
+
+// ---- launchers -------------------------------------------------------------------------
+void dev_free(rmgtd_ctx* ctx, void* p);
+double* kb_coef_buffer(rmgtd_ctx* ctx, int ncols);
+// k_grid.cu
+int launch_vion(rmgtd_ctx* ctx, const double* pos_dev, const double* Z_dev,
+                const double* rc_dev, int natoms);
+int build_projectors(rmgtd_ctx* ctx, const rmgtd_system* sys);
+int apply_h_dev(rmgtd_ctx* ctx, const void* x, void* hx, int ncols, int dtype,
+                const double* vextra);
+int launch_lda(rmgtd_ctx* ctx, const double* rho, const double* vh, double* vxc, double* exc,
+               double* vhxc, long n, const RepCtl* ctl, int nrep, long stride, int with_xc);
+// k_subspace.cu
+int gram(rmgtd_ctx* ctx, const double* A, const double* B, const double* w, long wstride,
+         int nw, double scale, const double* base, double* out, const double* prev,
+         const RepCtl* ctl, int sym, unsigned long long* errbits);
+int rho_dev(rmgtd_ctx* ctx, const double* S, double* rho, const RepCtl* ctl, int nrep);
+int eldyn(rmgtd_ctx* ctx, const double* Ha, const double* Hb, long hstride, double tau,
+          const double* S0, const double* A0, double* S1, double* A1, const RepCtl* ctl_in,
+          RepCtl* ctl_out, int rep0, int nreps);
+int step_begin(rmgtd_ctx* ctx);
+int scf_control(rmgtd_ctx* ctx, const unsigned long long* errbits);
+int observables(rmgtd_ctx* ctx);
+int orthonormalize(rmgtd_ctx* ctx);
+// k_poisson.cu
+int setup_multigrid(rmgtd_ctx* ctx);
+int hartree_dev(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* ctl, int zero_bc,
+                int nrep);
+
+}  // namespace rmgtd

@@ -1,0 +1,293 @@
+"""Thin ctypes binding of librmgtd (the C ABI of include/rmgtd.h).
+
+Argument marshalling only: every step of the propagation runs in the CUDA library.  If the
+library is missing the binding raises -- there is no CPU fallback.  Device memory for the
+context comes from PyTorch's caching allocator (through the ABI's allocator hook) and work
+runs on the current PyTorch CUDA stream unless another stream is given.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+from .inputs import System
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "librmgtd.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ENOTCONVERGED, EDIVERGED, ETIMEOUT, ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
+PREC_FP64, PREC_MIXED = 0, 1
+F64, F32, C128, C64 = 0, 1, 2, 3
+MAT_P_RE, MAT_P_IM, MAT_H0, MAT_HM1, MAT_HCORE, MAT_MX, MAT_MY, MAT_MZ, MAT_S = range(9)
+
+_c_double_p = ctypes.POINTER(ctypes.c_double)
+_c_int_p = ctypes.POINTER(ctypes.c_int)
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class RmgtdError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"rmgtd error {code}: {msg}")
+        self.code = code
+
+
+class CSystem(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("h", ctypes.c_double),
+        ("natoms", ctypes.c_int), ("pos", _c_double_p), ("Z", _c_double_p),
+        ("rc_loc", _c_double_p),
+        ("nproj", ctypes.c_int), ("proj_atom", _c_int_p), ("proj_l", _c_int_p),
+        ("proj_m", _c_int_p), ("proj_rc", _c_double_p), ("E_kb", _c_double_p),
+        ("nocc", ctypes.c_int), ("nvirt", ctypes.c_int), ("f", _c_double_p),
+        ("phi0", _c_double_p), ("v_ext_omega", ctypes.c_double), ("hartree_xc", ctypes.c_int),
+    ]
+
+
+class COptions(ctypes.Structure):
+    _fields_ = [
+        ("dt", ctypes.c_double), ("H_thrs", ctypes.c_double), ("dP_thrs", ctypes.c_double),
+        ("max_scf", ctypes.c_int), ("max_terms", ctypes.c_int), ("precision", ctypes.c_int),
+        ("nrep", ctypes.c_int), ("orthonormalize", ctypes.c_int),
+        ("poisson_tol", ctypes.c_double), ("poisson_max_iter", ctypes.c_int),
+        ("use_graph", ctypes.c_int), ("stream", ctypes.c_void_p),
+        ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", ctypes.c_void_p),
+    ]
+
+
+class CStats(ctypes.Structure):
+    _fields_ = [("passes", ctypes.c_int), ("terms_max", ctypes.c_int),
+                ("terms_sum", ctypes.c_int), ("status", ctypes.c_int), ("H_err", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load_library(path: Optional[str] = None):
+    """Load librmgtd.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} not found: build it with `python -m paper_2410_09189_gb300.build`")
+    lib = ctypes.CDLL(path)
+    vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    sig = {
+        "rmgtd_default_options": (None, [ctypes.POINTER(COptions)]),
+        "rmgtd_create": (i, [ctypes.POINTER(CSystem), ctypes.POINTER(COptions), ctypes.POINTER(vp)]),
+        "rmgtd_destroy": (None, [vp]),
+        "rmgtd_apply_h": (i, [vp, vp, vp, i, i, i]),
+        "rmgtd_kick": (i, [vp, i, i, d]),
+        "rmgtd_step": (i, [vp, i, ctypes.POINTER(CStats)]),
+        "rmgtd_density": (i, [vp, i, _c_double_p]),
+        "rmgtd_dipole": (i, [vp, i, _c_double_p]),
+        "rmgtd_energy": (i, [vp, i, _c_double_p]),
+        "rmgtd_get_matrix": (i, [vp, i, i, _c_double_p]),
+        "rmgtd_set_matrix": (i, [vp, i, i, _c_double_p]),
+        "rmgtd_hartree": (i, [vp, vp, vp]),
+        "rmgtd_xc": (i, [vp, vp, vp, vp, ctypes.c_size_t]),
+        "rmgtd_save": (i, [vp, ctypes.c_char_p]),
+        "rmgtd_load": (i, [vp, ctypes.c_char_p]),
+        "rmgtd_time": (i, [vp, _c_double_p, ctypes.POINTER(ctypes.c_longlong)]),
+        "rmgtd_last_error": (ctypes.c_char_p, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(_c_double_p)
+
+
+def _iptr(a: np.ndarray):
+    return a.ctypes.data_as(_c_int_p)
+
+
+class Context:
+    """One propagation context on the current CUDA device (owns its device memory)."""
+
+    def __init__(self, sys: System, phi0: np.ndarray, *, dt: Optional[float] = None,
+                 H_thrs: float = 1e-7, dP_thrs: float = 1e-10, max_scf: int = 50,
+                 max_terms: int = 200, precision: int = PREC_FP64, nrep: int = 1,
+                 orthonormalize: bool = True, poisson_tol: float = 1e-12,
+                 poisson_max_iter: int = 200, use_graph: bool = False,
+                 stream: Optional[int] = None, torch_alloc: bool = True):
+        import torch
+
+        lib = load_library()
+        self._lib = lib
+        self._torch = torch
+        self.sys = sys
+        self.N = sys.N
+        self.Ng = sys.Ng
+        self.nrep = nrep
+        self._keep = []
+        phi = np.ascontiguousarray(phi0, dtype=np.float64).reshape(sys.N, sys.Ng)
+        arrs = {
+            "pos": np.ascontiguousarray(sys.pos, dtype=np.float64).reshape(-1),
+            "Z": np.ascontiguousarray(sys.Z, dtype=np.float64),
+            "rc": np.ascontiguousarray(sys.rc_loc, dtype=np.float64),
+            "pa": np.ascontiguousarray(sys.proj_atom, dtype=np.int32),
+            "pl": np.ascontiguousarray(sys.proj_l, dtype=np.int32),
+            "pm": np.ascontiguousarray(sys.proj_m, dtype=np.int32),
+            "prc": np.ascontiguousarray(sys.proj_rc, dtype=np.float64),
+            "ekb": np.ascontiguousarray(sys.E_kb, dtype=np.float64),
+            "f": np.ascontiguousarray(sys.occupations, dtype=np.float64),
+            "phi": phi,
+        }
+        self._keep.append(arrs)
+        cs = CSystem()
+        cs.nx, cs.ny, cs.nz = (int(v) for v in sys.n)
+        cs.h = float(sys.h)
+        cs.natoms = int(len(sys.Z))
+        cs.pos, cs.Z, cs.rc_loc = _dptr(arrs["pos"]), _dptr(arrs["Z"]), _dptr(arrs["rc"])
+        cs.nproj = int(sys.nproj)
+        cs.proj_atom, cs.proj_l, cs.proj_m = _iptr(arrs["pa"]), _iptr(arrs["pl"]), _iptr(arrs["pm"])
+        cs.proj_rc, cs.E_kb = _dptr(arrs["prc"]), _dptr(arrs["ekb"])
+        cs.nocc, cs.nvirt = int(sys.nocc), int(sys.nvirt)
+        cs.f = _dptr(arrs["f"])
+        cs.phi0 = _dptr(phi)
+        cs.v_ext_omega = float(sys.v_ext_omega)
+        cs.hartree_xc = 1 if sys.hartree_xc else 0
+        opt = COptions()
+        lib.rmgtd_default_options(ctypes.byref(opt))
+        opt.dt = float(sys.dt if dt is None else dt)
+        opt.H_thrs, opt.dP_thrs = float(H_thrs), float(dP_thrs)
+        opt.max_scf, opt.max_terms = int(max_scf), int(max_terms)
+        opt.precision, opt.nrep = int(precision), int(nrep)
+        opt.orthonormalize = 1 if orthonormalize else 0
+        opt.poisson_tol, opt.poisson_max_iter = float(poisson_tol), int(poisson_max_iter)
+        opt.use_graph = 1 if use_graph else 0
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        self.stream = int(stream)
+        opt.stream = ctypes.c_void_p(self.stream)
+        if torch_alloc:
+            dev = torch.cuda.current_device()
+
+            def _alloc(nbytes, strm, user):
+                try:
+                    return int(torch.cuda.caching_allocator_alloc(int(nbytes), dev, int(strm or 0)))
+                except Exception:  # reported to the library as an allocation failure
+                    return None
+
+            def _free(ptr, user):
+                torch.cuda.caching_allocator_delete(int(ptr))
+
+            self._alloc_cb = ALLOC_FN(_alloc)
+            self._free_cb = FREE_FN(_free)
+            opt.alloc, opt.free = self._alloc_cb, self._free_cb
+        self._ctx = ctypes.c_void_p()
+        rc = lib.rmgtd_create(ctypes.byref(cs), ctypes.byref(opt), ctypes.byref(self._ctx))
+        if rc != OK:
+            msg = lib.rmgtd_last_error(None).decode()
+            raise RmgtdError(rc, msg)
+
+    # --- helpers -----------------------------------------------------------------------
+    def _check(self, rc: int):
+        if rc != OK:
+            raise RmgtdError(rc, self._lib.rmgtd_last_error(self._ctx).decode())
+
+    def close(self):
+        if getattr(self, "_ctx", None) and self._ctx.value:
+            self._lib.rmgtd_destroy(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # --- ABI -----------------------------------------------------------------------------
+    def kick(self, rep: int, axis: int, kappa: float):
+        self._check(self._lib.rmgtd_kick(self._ctx, rep, axis, float(kappa)))
+
+    def step(self, nsteps: int = 1, stats: bool = True, raise_on_error: bool = True):
+        st = (CStats * max(1, nsteps * self.nrep))() if stats else None
+        rc = self._lib.rmgtd_step(self._ctx, int(nsteps), st)
+        if raise_on_error:
+            self._check(rc)
+        if not stats:
+            return rc
+        out = np.zeros((nsteps, self.nrep), dtype=[("passes", "i4"), ("terms_max", "i4"),
+                                                   ("terms_sum", "i4"), ("status", "i4"),
+                                                   ("H_err", "f8")])
+        for s in range(nsteps):
+            for r in range(self.nrep):
+                c = st[s * self.nrep + r]
+                out[s, r] = (c.passes, c.terms_max, c.terms_sum, c.status, c.H_err)
+        return out if raise_on_error else (rc, out)
+
+    def density(self, rep: int = 0) -> np.ndarray:
+        out = np.empty(self.Ng)
+        self._check(self._lib.rmgtd_density(self._ctx, rep, _dptr(out)))
+        return out
+
+    def dipole(self, rep: int = 0) -> np.ndarray:
+        out = np.empty(3)
+        self._check(self._lib.rmgtd_dipole(self._ctx, rep, _dptr(out)))
+        return out
+
+    def energy(self, rep: int = 0) -> float:
+        out = np.empty(1)
+        self._check(self._lib.rmgtd_energy(self._ctx, rep, _dptr(out)))
+        return float(out[0])
+
+    def get_matrix(self, which: int, rep: int = 0) -> np.ndarray:
+        out = np.empty((self.N, self.N))
+        self._check(self._lib.rmgtd_get_matrix(self._ctx, which, rep, _dptr(out)))
+        return out
+
+    def set_matrix(self, which: int, rep: int, M: np.ndarray):
+        a = np.ascontiguousarray(M, dtype=np.float64)
+        self._check(self._lib.rmgtd_set_matrix(self._ctx, which, rep, _dptr(a)))
+
+    def density_matrix(self, rep: int = 0) -> np.ndarray:
+        return self.get_matrix(MAT_P_RE, rep) + 1j * self.get_matrix(MAT_P_IM, rep)
+
+    def apply_h(self, x, hx, rep: int = -1):
+        """hx = H x for CUDA tensors of shape (ncols, Ng) (float64/float32/complex128/complex64)."""
+        torch = self._torch
+        codes = {torch.float64: F64, torch.float32: F32, torch.complex128: C128,
+                 torch.complex64: C64}
+        assert x.is_cuda and hx.is_cuda and x.dtype == hx.dtype and x.is_contiguous()
+        ncols = x.numel() // self.Ng
+        self._check(self._lib.rmgtd_apply_h(self._ctx, ctypes.c_void_p(x.data_ptr()),
+                                            ctypes.c_void_p(hx.data_ptr()), ncols,
+                                            codes[x.dtype], rep))
+
+    def hartree(self, rho, vh):
+        self._check(self._lib.rmgtd_hartree(self._ctx, ctypes.c_void_p(rho.data_ptr()),
+                                            ctypes.c_void_p(vh.data_ptr())))
+
+    def xc(self, rho, vxc, exc):
+        self._check(self._lib.rmgtd_xc(self._ctx, ctypes.c_void_p(rho.data_ptr()),
+                                       ctypes.c_void_p(vxc.data_ptr()),
+                                       ctypes.c_void_p(exc.data_ptr()), rho.numel()))
+
+    def save(self, path: str):
+        self._check(self._lib.rmgtd_save(self._ctx, path.encode()))
+
+    def load(self, path: str):
+        self._check(self._lib.rmgtd_load(self._ctx, path.encode()))
+
+    def time(self):
+        t = ctypes.c_double()
+        n = ctypes.c_longlong()
+        self._check(self._lib.rmgtd_time(self._ctx, ctypes.byref(t), ctypes.byref(n)))
+        return t.value, n.value

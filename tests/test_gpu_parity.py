@@ -1,0 +1,264 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, element by element.
+
+Tolerances (float64 path): grid operators and set-up matrices to 1e-10 relative (rounding
+order of 37-term stencils and grid sums of up to 10^6 terms), Hartree to the CG tolerance,
+dipole time series to 1e-6 of the dipole variation -- the target the method states for the
+float64 path -- with the SCF and series thresholds tightened so that the iteration history
+does not dominate.
+"""
+import dataclasses
+import os
+import tempfile
+
+import numpy as np
+import pytest
+
+from oracle import groundstate, hamiltonian as oham, lda as olda, poisson as opoisson, tddft
+from paper_2410_09189_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_dev():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    return torch
+
+
+def _rmgtd():
+    from paper_2410_09189_gb300 import rmgtd
+    return rmgtd
+
+
+def _ring_small(n=(30, 34, 38), h=0.5, nvirt=15):
+    s = inputs.ring(n=32, h=h, nvirt=nvirt)
+    return dataclasses.replace(s, n=tuple(n))
+
+
+def _rel(a, b):
+    return np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)
+
+
+# ----------------------------------------------------------------------------------------
+def test_apply_h_all_dtypes(torch_dev):
+    torch = torch_dev
+    rmgtd = _rmgtd()
+    s = _ring_small(n=(37, 41, 43), h=0.45)
+    s.proj_l = s.proj_l.copy()
+    s.proj_m = s.proj_m.copy()
+    s.proj_l[1], s.proj_m[1] = 1, 2      # one p-type projector
+    s.proj_l[4], s.proj_m[4] = 1, 0
+    raw = inputs.smooth_random_orbitals(s).reshape(s.N, s.Ng)
+    x = np.random.default_rng(5).standard_normal((3, s.Ng))
+    v_ion = (oham.v_local(s) + oham.v_external(s)).ravel()
+    ref = oham.apply_h(s, v_ion, x)
+    with rmgtd.Context(s, raw) as ctx:
+        xd = torch.from_numpy(x).cuda()
+        hx = torch.empty_like(xd)
+        ctx.apply_h(xd, hx, rep=-1)
+        assert _rel(hx.cpu().numpy(), ref) < 1e-12
+        x32 = xd.float()
+        h32 = torch.empty_like(x32)
+        ctx.apply_h(x32, h32, rep=-1)
+        assert _rel(h32.double().cpu().numpy(), ref) < 2e-5
+        y = np.random.default_rng(6).standard_normal((3, s.Ng))
+        refy = oham.apply_h(s, v_ion, y)
+        z = torch.complex(xd, torch.from_numpy(y).cuda()).contiguous()
+        hz = torch.empty_like(z)
+        ctx.apply_h(z, hz, rep=-1)
+        got = hz.cpu().numpy()
+        assert _rel(got.real, ref) < 1e-12 and _rel(got.imag, refy) < 1e-12
+        z64 = z.to(torch.complex64)
+        hz64 = torch.empty_like(z64)
+        ctx.apply_h(z64, hz64, rep=-1)
+        got = hz64.cpu().numpy()
+        assert _rel(got.real, ref) < 2e-5 and _rel(got.imag, refy) < 2e-5
+
+
+def test_setup_matrices(torch_dev):
+    rmgtd = _rmgtd()
+    s = _ring_small(n=(30, 34, 38), h=0.5, nvirt=22)     # N = 37: ragged against every tile
+    raw = inputs.smooth_random_orbitals(s).reshape(s.N, s.Ng)
+    phi = oham.orthonormalize(s, raw)
+    pr = tddft.Propagator(s, phi, tddft.Options(poisson_tol=1e-13))
+    st = pr.initial_state()
+    with rmgtd.Context(s, raw, poisson_tol=1e-13) as ctx:
+        S = ctx.get_matrix(rmgtd.MAT_S)
+        assert np.max(np.abs(S - np.eye(s.N))) < 1e-12
+        assert np.max(np.abs(ctx.get_matrix(rmgtd.MAT_HCORE) - pr.Hcore)) < 1e-10
+        for q, which in enumerate((rmgtd.MAT_MX, rmgtd.MAT_MY, rmgtd.MAT_MZ)):
+            assert np.max(np.abs(ctx.get_matrix(which) - pr.M[q])) < 1e-10
+        H0 = ctx.get_matrix(rmgtd.MAT_H0)
+        assert np.max(np.abs(H0 - st["H0"])) < 1e-9
+        assert np.max(np.abs(H0 - H0.T)) == 0.0
+        rho = ctx.density(0)
+        assert _rel(rho, pr.density(st["P0"])) < 1e-12
+        assert abs(ctx.energy(0) - pr.energy(st["P0"], st["aux"])) < 1e-9
+
+
+def test_hartree_and_xc(torch_dev):
+    torch = torch_dev
+    rmgtd = _rmgtd()
+    s = _ring_small(n=(40, 36, 44), h=0.4)
+    raw = inputs.smooth_random_orbitals(s).reshape(s.N, s.Ng)
+    x, y, z = oham.full_coords(s)
+    rho = (np.exp(-((x - 1.1) ** 2 + (y + 0.4) ** 2 + z ** 2) / 2.0)
+           + 0.5 * np.exp(-((x + 2.0) ** 2 + (y - 1.0) ** 2 + (z - 0.7) ** 2) / 1.5))
+    ref = opoisson.hartree(s, rho, tol=1e-13)
+    vref, eref = olda.lda(rho.ravel())
+    with rmgtd.Context(s, raw, poisson_tol=1e-13) as ctx:
+        rd = torch.from_numpy(rho.ravel()).cuda()
+        vh = torch.zeros_like(rd)
+        ctx.hartree(rd, vh)
+        assert _rel(vh.cpu().numpy(), ref.ravel()) < 1e-10
+        vxc = torch.empty_like(rd)
+        exc = torch.empty_like(rd)
+        ctx.xc(rd, vxc, exc)
+        assert _rel(vxc.cpu().numpy(), vref) < 1e-13
+        assert _rel(exc.cpu().numpy(), eref) < 1e-13
+        # a second solve warm-started from the answer converges at once to the same V
+        ctx.hartree(rd, vh)
+        assert _rel(vh.cpu().numpy(), ref.ravel()) < 1e-10
+
+
+def test_kick_matches_oracle(torch_dev):
+    rmgtd = _rmgtd()
+    s = _ring_small(n=(30, 30, 30), h=0.55, nvirt=20)
+    raw = inputs.smooth_random_orbitals(s).reshape(s.N, s.Ng)
+    phi = oham.orthonormalize(s, raw)
+    pr = tddft.Propagator(s, phi, tddft.Options(dP_thrs=1e-14))
+    P = np.diag(s.occupations).astype(complex)
+    with rmgtd.Context(s, raw, dP_thrs=1e-14) as ctx:
+        for axis, kappa in ((2, 0.05), (0, 0.3)):
+            P = pr.kick(P, axis, kappa)
+            ctx.kick(0, axis, kappa)
+            Pg = ctx.density_matrix(0)
+            assert np.max(np.abs(Pg - P)) < 1e-12
+        assert abs(np.trace(Pg).real - s.n_electrons) < 1e-12
+
+
+@pytest.fixture(scope="module")
+def small_gs():
+    s = inputs.small()
+    gs = groundstate.ground_state(s, tol=1e-10)
+    return s, gs
+
+
+def test_trajectory_small_system(torch_dev, small_gs):
+    rmgtd = _rmgtd()
+    s, gs = small_gs
+    nsteps = 40
+    o = tddft.Options(H_thrs=1e-10, dP_thrs=1e-13, poisson_tol=1e-13)
+    orc = tddft.run(s, gs["phi"], o, nsteps=nsteps, axis=2, kappa=s.kappa)
+    with rmgtd.Context(s, gs["phi"], H_thrs=1e-10, dP_thrs=1e-13, poisson_tol=1e-13,
+                       orthonormalize=False) as ctx:
+        ctx.kick(0, 2, s.kappa)
+        d = [ctx.dipole(0)]
+        e = [ctx.energy(0)]
+        passes = []
+        for _ in range(nsteps):
+            st = ctx.step(1)
+            passes.append(int(st["passes"][0, 0]))
+            d.append(ctx.dipole(0))
+            e.append(ctx.energy(0))
+        P = ctx.density_matrix(0)
+    d, e = np.array(d), np.array(e)
+    scale = np.max(np.abs(orc["dipole"][:, 2] - orc["dipole"][0, 2]))
+    assert np.max(np.abs(d - orc["dipole"])) / scale < 1e-6
+    assert np.max(np.abs(e - orc["energy"])) < 1e-9
+    assert abs(np.trace(P).real - s.n_electrons) < 1e-11
+    assert np.max(np.abs(P - P.conj().T)) < 1e-14
+    assert abs(np.mean(passes) - np.mean(orc["passes"])) <= 0.5
+
+
+def test_trajectory_three_kicks_ragged(torch_dev):
+    """Three replicas (kicks x, y, z) in one context on a ragged grid and N = 37."""
+    rmgtd = _rmgtd()
+    s = _ring_small(n=(30, 34, 38), h=0.5, nvirt=22)
+    raw = inputs.smooth_random_orbitals(s).reshape(s.N, s.Ng)
+    phi = oham.orthonormalize(s, raw)
+    nsteps, dt, kap = 5, 0.02, 1e-2
+    o = tddft.Options(dt=dt, H_thrs=1e-10, dP_thrs=1e-13, poisson_tol=1e-13)
+    refs = [tddft.run(s, phi, o, nsteps=nsteps, axis=a, kappa=kap) for a in range(3)]
+    with rmgtd.Context(s, raw, dt=dt, H_thrs=1e-10, dP_thrs=1e-13, poisson_tol=1e-13,
+                       nrep=3) as ctx:
+        for a in range(3):
+            ctx.kick(a, a, kap)
+        d = [[ctx.dipole(a) for a in range(3)]]
+        for _ in range(nsteps):
+            ctx.step(1)
+            d.append([ctx.dipole(a) for a in range(3)])
+    d = np.array(d)  # (t, rep, q)
+    for a in range(3):
+        ref = refs[a]["dipole"]
+        scale = np.max(np.abs(ref - ref[0]))
+        assert np.max(np.abs(d[:, a, :] - ref)) / scale < 1e-6
+
+
+def test_checkpoint_resume_is_bitwise(torch_dev, small_gs):
+    rmgtd = _rmgtd()
+    s, gs = small_gs
+    kw = dict(H_thrs=1e-9, dP_thrs=1e-12, orthonormalize=False)
+    with tempfile.TemporaryDirectory() as td:
+        path = os.path.join(td, "ck.bin")
+        with rmgtd.Context(s, gs["phi"], **kw) as a:
+            a.kick(0, 2, 0.01)
+            a.step(3)
+            a.save(path)
+            a.step(3)
+            Pa = a.density_matrix(0)
+            ta = a.time()
+        with rmgtd.Context(s, gs["phi"], **kw) as b:
+            b.load(path)
+            b.step(3)
+            Pb = b.density_matrix(0)
+            tb = b.time()
+    assert ta == tb
+    assert np.array_equal(Pa, Pb)
+
+
+def test_error_paths_keep_state(torch_dev, small_gs):
+    rmgtd = _rmgtd()
+    s, gs = small_gs
+    with rmgtd.Context(s, gs["phi"], H_thrs=1e-16, max_scf=1, orthonormalize=False) as ctx:
+        ctx.kick(0, 2, 0.01)
+        P_before = ctx.density_matrix(0)
+        with pytest.raises(rmgtd.RmgtdError) as ei:
+            ctx.step(1)
+        assert ei.value.code == rmgtd.ENOTCONVERGED
+        assert np.array_equal(ctx.density_matrix(0), P_before)
+        assert ctx.time() == (0.0, 0)
+        with pytest.raises(rmgtd.RmgtdError) as ei:
+            ctx.kick(0, 3, 0.01)
+        assert ei.value.code == rmgtd.EINVAL
+
+
+def test_full_size_ring_workload(torch_dev):
+    """The benchmarked workload (64^3, N = 30, kicks x/y/z) at full size: the oracle
+    re-evaluates H = DFT(rho(P)) from the GPU's own P after the steps, and the invariants
+    of the propagation hold."""
+    rmgtd = _rmgtd()
+    s = inputs.ring()
+    raw = inputs.smooth_random_orbitals(s).reshape(s.N, s.Ng)
+    phi = oham.orthonormalize(s, raw)
+    with rmgtd.Context(s, raw, nrep=3, poisson_tol=1e-13, H_thrs=1e-9) as ctx:
+        for a in range(3):
+            ctx.kick(a, a, s.kappa)
+        e0 = [ctx.energy(a) for a in range(3)]
+        st = ctx.step(3)
+        assert np.all(st["status"] == 0)
+        P = [ctx.density_matrix(a) for a in range(3)]
+        H0 = [ctx.get_matrix(rmgtd.MAT_H0, a) for a in range(3)]
+        e1 = [ctx.energy(a) for a in range(3)]
+    pr = tddft.Propagator(s, phi, tddft.Options(poisson_tol=1e-13, full_apply=False))
+    for a in range(3):
+        assert abs(np.trace(P[a]).real - s.n_electrons) < 1e-10
+        assert np.max(np.abs(P[a] - P[a].conj().T)) < 1e-14
+        H, _ = pr.dft(P[a])
+        assert np.max(np.abs(H - H0[a])) < 1e-8
+        assert abs(e1[a] - e0[a]) < 1e-4
