@@ -599,7 +599,7 @@ int rmgtd_hartree(rmgtd_ctx* ctx, const double* rho_dev, double* vh_dev) {
 int rmgtd_xc(rmgtd_ctx* ctx, const double* rho_dev, double* vxc_dev, double* exc_dev, size_t n) {
   if (!ctx) return set_error(nullptr, RMGTD_EINVAL, "ctx is NULL");
   if (!rho_dev || !vxc_dev || n == 0) return set_error(ctx, RMGTD_EINVAL, "xc: bad arguments");
-  int rc = launch_lda(ctx, rho_dev, nullptr, vxc_dev, exc_dev, nullptr, (long)n, nullptr, 1, (long)n, 0);
+  int rc = launch_lda(ctx, rho_dev, nullptr, vxc_dev, exc_dev, nullptr, (long)n, nullptr, 1, (long)n, 1);
   if (rc) return rc;
   RMGTD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   return RMGTD_OK;
