@@ -1,0 +1,331 @@
+#!/usr/bin/env python
+"""Benchmark of the RT-TDDFT time step (Algorithm 1) on GB300.
+
+Workload: the benzene-like ring (12 pseudo-atoms, s-type KB on the 6 heavy atoms), 64^3 grid
+at h = 0.35 bohr, N = 15 occupied + 15 virtual orbitals, three replicas kicked along x, y, z
+(kappa = 1e-3) propagated together, dt = 0.05 a.u., H_thrs = 1e-7, dP_thrs = 1e-10.  One
+"step" advances all three replicas by one time step, SCF passes included.  Orbitals are
+seeded smooth random fields orthonormalised on the device (synthetic data).
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle on the same
+workload instead (a bounded sample per step).  Under torchrun every rank propagates its own
+replica set (independent problems, no data-path collective): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "RT-TDDFT time-steps/sec and grid-point·orbital updates/sec, mixed vs FP64 GPU"
+UNIT = "time-steps/s"
+FP64_PEAK_GFLOPS = 1250.0   # GB300 float64 rate (nominal 1.25 TFLOP/s)
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-i", str(self.device), "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) >= 9:
+                rows.append(p)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def _workload():
+    from paper_2410_09189_gb300 import inputs
+    s = inputs.ring()
+    raw = inputs.smooth_random_orbitals(s).reshape(s.N, s.Ng)
+    return s, raw
+
+
+def _config(s, precision):
+    return {"workload": "ring-12-atoms-64^3-N30-kicks-xyz", "grid": list(s.n), "h": s.h,
+            "N": s.N, "nocc": s.nocc, "replicas": 3, "dt": s.dt, "kappa": s.kappa,
+            "H_thrs": 1e-7, "dP_thrs": 1e-10, "precision": precision,
+            "orbitals": "seeded smooth random fields, orthonormalised on the device",
+            "l2": "flushed (256 MiB write) between timed steps"}
+
+
+# ---------------------------------------------------------------------------------------
+def run_reference(args):
+    """The FP64 CPU oracle on the same workload: each step is one time step of ONE replica
+    (a bounded sample), reported in the 3-replica unit."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from oracle import hamiltonian as oham, tddft
+    s, raw = _workload()
+    phi = oham.orthonormalize(s, raw)
+    pr = tddft.Propagator(s, phi, tddft.Options(dt=s.dt))
+    st = pr.initial_state()
+    st["P0"] = pr.kick(st["P0"], 2, s.kappa)
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        pr.step(st)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    per_rep = statistics.mean(times)
+    value = 1.0 / (3.0 * per_rep)
+    cores = os.cpu_count()
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max([d.get("num_threads", 1) for d in threadpool_info()] or [cores])
+    except Exception:
+        pass
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 3.0 * per_rep * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": _config(s, "fp64-cpu-oracle"),
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": "one time step of one of the three replicas per timed "
+                                      "step, scaled x3"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def cpu_baseline_sample(budget_s: float = 20.0):
+    """Time the oracle as it stands on a bounded sample of the workload (host cores)."""
+    from oracle import hamiltonian as oham, tddft
+    s, raw = _workload()
+    phi = oham.orthonormalize(s, raw)
+    pr = tddft.Propagator(s, phi, tddft.Options(dt=s.dt))
+    st = pr.initial_state()
+    st["P0"] = pr.kick(st["P0"], 2, s.kappa)
+    times = []
+    t_start = time.perf_counter()
+    while True:
+        t0 = time.perf_counter()
+        pr.step(st)
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() - t_start > budget_s or len(times) >= 4:
+            break
+    per_rep = statistics.mean(times)
+    cores = os.cpu_count()
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max([d.get("num_threads", 1) for d in threadpool_info()] or [cores])
+    except Exception:
+        pass
+    return {"value": 1.0 / (3.0 * per_rep), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{len(times)} time step(s) of one replica (x3 for the 3-replica unit)"}
+
+
+# ---------------------------------------------------------------------------------------
+def _flops_per_phase(N, Ng, rep_passes, terms_total):
+    """Algorithmic work of the float64 phases (per whole timed region)."""
+    return {
+        # rho = sum_ij S_ij phi_i phi_j with S symmetric: N(N+1)/2 multiply-adds per point
+        "rho": float(rep_passes) * Ng * N * (N + 1),
+        # H_ij = h^3 sum_g phi_i V phi_j, j >= i: N(N+1)/2 multiply-adds per point (+ V)
+        "hupdate": float(rep_passes) * Ng * (N * (N + 1) + N),
+        # two N x N x N products per commutator term
+        "eldyn": float(terms_total) * 4.0 * N ** 3,
+    }
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    __graft_entry__.build()
+    from paper_2410_09189_gb300 import rmgtd
+
+    prec = rmgtd.PREC_MIXED if args.precision == "mixed" else rmgtd.PREC_FP64
+    s, raw = _workload()
+    ctx = rmgtd.Context(s, raw, nrep=3, precision=prec, H_thrs=1e-7, dP_thrs=1e-10,
+                        poisson_tol=1e-12)
+    for a in range(3):
+        ctx.kick(a, a, s.kappa)
+    for _ in range(args.warmup):
+        ctx.step(1)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    sampler = ClockSampler(local)
+    ctx.profile(True)
+    sampler.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    stats = []
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        stats.append(ctx.step(1))
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    wall = time.perf_counter() - wall0
+    clocks = sampler.stop()
+    phase_ms, phase_calls, launches = ctx.profile_read()
+    ctx.profile(False)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    st = np.concatenate(stats)          # (steps, 3)
+    rep_passes = int(st["passes"].sum())
+    terms_total = int(st["terms_sum"].sum())
+    value = world * args.steps / (total_ms * 1e-3)
+    ms_per_step = total_ms / args.steps
+
+    # roofline of the dominant phase (event-timed on the library's stream)
+    peaks, peak_kind = _peaks()
+    flops = _flops_per_phase(s.N, s.Ng, rep_passes, terms_total)
+    dom = max(phase_ms, key=lambda k: phase_ms[k])
+    roof = {"phase": dom, "phase_ms_total": phase_ms[dom], "calls": phase_calls[dom]}
+    if dom in flops and phase_ms[dom] > 0:
+        calls = max(phase_calls[dom], 1)
+        per_launch = flops[dom] / calls
+        achieved = per_launch / (phase_ms[dom] / calls * 1e-3) / 1e12
+        if prec == rmgtd.PREC_FP64 or dom == "eldyn":
+            peak = FP64_PEAK_GFLOPS / 1e3
+            roof.update({"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "peak_source": "nominal GB300 float64 rate 1.25 TFLOP/s"})
+    else:
+        roof.update({"bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs"),
+                     "unit": "GB/s", "frac": None, "traffic": None})
+
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == rmgtd.PREC_FP64 else "f32+f64",
+        "data": "synthetic", "config": _config(s, args.precision),
+        "grid_point_orbital_updates_per_s": value * s.Ng * s.N * 3,
+        "scf_passes_per_replica_step": rep_passes / (3.0 * args.steps),
+        "commutator_terms_per_expansion": terms_total / max(rep_passes, 1),
+        "phase_ms_per_step": {k: v / args.steps for k, v in phase_ms.items()},
+        "gpu_launches": launches, "roofline": roof, "clocks": clocks,
+        "wall_s_timed_region": wall,
+    }
+    ctx.close()
+
+    # end to end through the public API: host orbitals in, dipoles out every step
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    c2 = rmgtd.Context(s, raw, nrep=3, precision=prec, H_thrs=1e-7, dP_thrs=1e-10,
+                       poisson_tol=1e-12)
+    for a in range(3):
+        c2.kick(a, a, s.kappa)
+    for _ in range(args.steps):
+        c2.step(1)
+        for a in range(3):
+            c2.dipole(a)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    c2.close()
+    h2d = raw.nbytes + s.pos.nbytes * 3
+    result["e2e"] = {"value": world * args.steps / e2e_s, "unit": UNIT,
+                     "h2d_bytes_per_step": h2d / args.steps,
+                     "d2h_bytes_per_step": 3 * 3 * 8 + 3 * 24,
+                     "includes": "context creation from host orbitals (upload, set-up, "
+                                 "initial SCF), 3 kicks, steps, dipole read-back per step"}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline_sample()
+    if world > 1:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -203,6 +203,21 @@ int rmgtd_load(rmgtd_ctx* ctx, const char* path);
 /* Simulation time and completed steps of the context. */
 int rmgtd_time(rmgtd_ctx* ctx, double* t, long long* steps);
 
+/* Phases of a time step reported by rmgtd_profile_read, in the paper's Table 1 names:
+ * 0 commutator expansion ("ELDYN"), 1 density ("Rho"), 2 Hartree solve ("Vh"),
+ * 3 exchange-correlation, 4 Hamiltonian update ("Hupdate"), 5 other (bookkeeping). */
+#define RMGTD_NPHASES 6
+
+/* Start (enable = 1) or stop per-phase timing with CUDA events recorded on the context's
+ * stream around each phase of rmgtd_step; resets the phase totals and the launch count. */
+int rmgtd_profile(rmgtd_ctx* ctx, int enable);
+
+/* Accumulated milliseconds and calls per phase since the last rmgtd_profile call
+ * (host arrays of RMGTD_NPHASES, may be NULL) and the number of kernels the library has
+ * launched since then.  Synchronises the stream. */
+int rmgtd_profile_read(rmgtd_ctx* ctx, double* phase_ms, long long* phase_calls,
+                       long long* launches);
+
 /* Message of the last error on `ctx` (thread-local message when ctx is NULL). */
 const char* rmgtd_last_error(const rmgtd_ctx* ctx);
 

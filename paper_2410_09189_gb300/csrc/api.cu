@@ -63,6 +63,35 @@ double* kb_coef_buffer(rmgtd_ctx* ctx, int ncols) {
   return ctx->kb_coef;
 }
 
+// ---- per-phase event timing ---------------------------------------------------------------
+constexpr int kEvPairs = 512;
+
+void ph_begin(rmgtd_ctx* ctx, int phase) {
+  if (!ctx->profile) return;
+  if (ctx->ev_n >= kEvPairs) ph_flush(ctx);
+  cudaEventRecord(ctx->ev_pool[2 * ctx->ev_n], ctx->stream);
+  ctx->ev_phase[ctx->ev_n] = phase;
+}
+
+void ph_end(rmgtd_ctx* ctx) {
+  if (!ctx->profile) return;
+  cudaEventRecord(ctx->ev_pool[2 * ctx->ev_n + 1], ctx->stream);
+  ctx->ev_n += 1;
+}
+
+int ph_flush(rmgtd_ctx* ctx) {
+  if (ctx->ev_n == 0) return RMGTD_OK;
+  RMGTD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  for (int i = 0; i < ctx->ev_n; ++i) {
+    float ms = 0.f;
+    RMGTD_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->ev_pool[2 * i], ctx->ev_pool[2 * i + 1]));
+    ctx->phase_ms[ctx->ev_phase[i]] += ms;
+    ctx->phase_calls[ctx->ev_phase[i]] += 1;
+  }
+  ctx->ev_n = 0;
+  return RMGTD_OK;
+}
+
 // ---- small elementwise kernels ------------------------------------------------------------
 __global__ void k_coords(int nx, int ny, int nz, double h, double* __restrict__ q) {
   const long Ng = (long)nx * ny * nz;
@@ -126,21 +155,28 @@ __global__ void k_ion_energy(int natoms, const double* __restrict__ pos, const d
 // replicas and folds max|H_new - H_1| into errbits.
 int dft_eval(rmgtd_ctx* ctx, const double* S, const RepCtl* ctl, unsigned long long* errbits) {
   const int nrep = ctx->nrep;
+  ph_begin(ctx, PH_RHO);
   int rc = rho_dev(ctx, S, ctx->rho, ctl, nrep);
+  ph_end(ctx);
   if (rc) return rc;
   if (ctx->hartree_xc) {
+    ph_begin(ctx, PH_HARTREE);
     rc = hartree_dev(ctx, ctx->rho, ctx->vh, ctl, 0, nrep);
+    ph_end(ctx);
     if (rc) return rc;
   }
+  ph_begin(ctx, PH_XC);
   rc = launch_lda(ctx, ctx->rho, ctx->hartree_xc ? ctx->vh : nullptr, ctx->vxc, ctx->exc,
                   ctx->vhxc, ctx->Ng, ctl, nrep, ctx->Ng, ctx->hartree_xc);
+  ph_end(ctx);
   if (rc) return rc;
   if (errbits)
     RMGTD_CUDA(ctx, cudaMemsetAsync(errbits, 0, sizeof(unsigned long long) * nrep, ctx->stream));
-  const long NN = (long)ctx->N * ctx->N;
-  return gram(ctx, ctx->phi, ctx->phi, ctx->vhxc, ctx->Ng, nrep, ctx->h3, ctx->Hcore, ctx->H1,
-              errbits ? ctx->H1 : nullptr, ctl, 1, errbits);
-  (void)NN;
+  ph_begin(ctx, PH_HUPDATE);
+  rc = gram(ctx, ctx->phi, ctx->phi, ctx->vhxc, ctx->Ng, nrep, ctx->h3, ctx->Hcore, ctx->H1,
+            errbits ? ctx->H1 : nullptr, ctl, 1, errbits);
+  ph_end(ctx);
+  return rc;
 }
 
 // Refresh rho / V_H / V_xc / eps_xc from the current P_0 of every replica (no H update).
@@ -211,6 +247,7 @@ void rmgtd_destroy(rmgtd_ctx* ctx) {
   if (ctx->ctl_host) cudaFreeHost(ctx->ctl_host);
   if (ctx->obs_host) cudaFreeHost(ctx->obs_host);
   if (ctx->pcg_any_host) cudaFreeHost(ctx->pcg_any_host);
+  for (auto& e : ctx->ev_pool) cudaEventDestroy(e);
   delete ctx;
 }
 
@@ -317,6 +354,7 @@ static int create_impl(const rmgtd_system* sys, const rmgtd_options* opt, rmgtd_
   int rc = launch_vion(ctx, pos_d, Z_d, rc_d, na);
   if (rc) return rc;
   k_ion_energy<<<1, 256, 0, ctx->stream>>>(na, pos_d, Z_d, rc_d, eion_d);
+  ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_ion_energy");
   RMGTD_CUDA(ctx, cudaMemcpyAsync(&ctx->obs_host[0], eion_d, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   RMGTD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
@@ -346,6 +384,7 @@ static int create_impl(const rmgtd_system* sys, const rmgtd_options* opt, rmgtd_
     if (rc) return rc;
     k_symmetrize<<<std::max(1, (int)std::min<long>(ceil_div(NN, 256), 1024)), 256, 0, ctx->stream>>>(
         N, ctx->H1, ctx->Hcore);
+    ++ctx->launches;
     RMGTD_LAUNCH(ctx, "k_symmetrize");
     RMGTD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     dev_free(ctx, hphi);
@@ -356,6 +395,7 @@ static int create_impl(const rmgtd_system* sys, const rmgtd_options* opt, rmgtd_
     if (!q) return set_error(ctx, RMGTD_ENOMEM, "coordinate scratch");
     k_coords<<<std::max(1, (int)std::min<long>(ceil_div(Ng, 256), 4096)), 256, 0, ctx->stream>>>(
         ctx->nx, ctx->ny, ctx->nz, ctx->h, q);
+    ++ctx->launches;
     RMGTD_LAUNCH(ctx, "k_coords");
     for (int d = 0; d < 3; ++d) {
       rc = gram(ctx, ctx->phi, ctx->phi, q + d * Ng, 0, 1, ctx->h3, nullptr, ctx->M + d * NN,
@@ -368,8 +408,10 @@ static int create_impl(const rmgtd_system* sys, const rmgtd_options* opt, rmgtd_
   // P_0 = diag(f), H_0 = H[rho(P_0)], H_-1 = H_0
   k_diag_init<<<std::max(1, (int)std::min<long>(ceil_div(NN * nrep, 256), 1024)), 256, 0, ctx->stream>>>(
       N, nrep, ctx->f_dev, ctx->S0, ctx->A0);
+  ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_diag_init");
   k_set_active<<<1, 32, 0, ctx->stream>>>(ctx->ctl, nrep, 1);
+  ++ctx->launches;
   rc = dft_eval(ctx, ctx->S0, ctx->ctl, nullptr);
   if (rc) return rc;
   RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->H0, ctx->H1, msz * nrep, cudaMemcpyDeviceToDevice, ctx->stream));
@@ -377,6 +419,7 @@ static int create_impl(const rmgtd_system* sys, const rmgtd_options* opt, rmgtd_
   RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->S1, ctx->S0, msz * nrep, cudaMemcpyDeviceToDevice, ctx->stream));
   RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->A1, ctx->A0, msz * nrep, cudaMemcpyDeviceToDevice, ctx->stream));
   k_set_active<<<1, 32, 0, ctx->stream>>>(ctx->ctl, nrep, 0);
+  ++ctx->launches;
   return check_status(ctx, "create");
 }
 
@@ -450,15 +493,21 @@ int rmgtd_step(rmgtd_ctx* ctx, int nsteps, rmgtd_stats* stats) {
   const size_t msz = sizeof(double) * NN * nrep;
   for (int s = 0; s < nsteps; ++s) {
     RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream));
+    ph_begin(ctx, PH_OTHER);
     int rc = step_begin(ctx);
+    ph_end(ctx);
     if (rc) return rc;
     for (int pass = 0; pass < ctx->opt.max_scf; ++pass) {
+      ph_begin(ctx, PH_ELDYN);
       rc = eldyn(ctx, ctx->H0, ctx->H1, NN, ctx->opt.dt, ctx->S0, ctx->A0, ctx->S1, ctx->A1,
                  ctx->ctl, ctx->ctl, 0, nrep);
+      ph_end(ctx);
       if (rc) return rc;
       rc = dft_eval(ctx, ctx->S1, ctx->ctl, ctx->errbits);
       if (rc) return rc;
+      ph_begin(ctx, PH_OTHER);
       rc = scf_control(ctx, ctx->errbits);
+      ph_end(ctx);
       if (rc) return rc;
       RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->ctl_host, ctx->ctl, sizeof(RepCtl) * nrep,
                                       cudaMemcpyDeviceToHost, ctx->stream));
@@ -498,6 +547,37 @@ int rmgtd_step(rmgtd_ctx* ctx, int nsteps, rmgtd_stats* stats) {
     ctx->steps += 1;
   }
   RMGTD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return ph_flush(ctx);
+}
+
+int rmgtd_profile(rmgtd_ctx* ctx, int enable) {
+  if (!ctx) return set_error(nullptr, RMGTD_EINVAL, "ctx is NULL");
+  int rc = ph_flush(ctx);
+  if (rc) return rc;
+  if (enable && ctx->ev_pool.empty()) {
+    ctx->ev_pool.resize(2 * kEvPairs);
+    ctx->ev_phase.resize(kEvPairs);
+    for (auto& e : ctx->ev_pool) RMGTD_CUDA(ctx, cudaEventCreate(&e));
+  }
+  ctx->profile = enable ? 1 : 0;
+  for (int i = 0; i < 8; ++i) {
+    ctx->phase_ms[i] = 0;
+    ctx->phase_calls[i] = 0;
+  }
+  ctx->launches = 0;
+  return RMGTD_OK;
+}
+
+int rmgtd_profile_read(rmgtd_ctx* ctx, double* phase_ms, long long* phase_calls,
+                       long long* launches) {
+  if (!ctx) return set_error(nullptr, RMGTD_EINVAL, "ctx is NULL");
+  int rc = ph_flush(ctx);
+  if (rc) return rc;
+  for (int i = 0; i < RMGTD_NPHASES; ++i) {
+    if (phase_ms) phase_ms[i] = ctx->phase_ms[i];
+    if (phase_calls) phase_calls[i] = ctx->phase_calls[i];
+  }
+  if (launches) *launches = ctx->launches;
   return RMGTD_OK;
 }
 

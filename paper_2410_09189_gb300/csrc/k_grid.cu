@@ -38,6 +38,7 @@ int launch_vion(rmgtd_ctx* ctx, const double* pos, const double* Z, const double
   const int blocks = (int)std::min<long>(ceil_div(ctx->Ng, kThreads), 8L * ctx->num_sms);
   k_vion<<<blocks, kThreads, 0, ctx->stream>>>(ctx->nx, ctx->ny, ctx->nz, ctx->h, natoms, pos,
                                                Z, rc, ctx->v_ext_omega, ctx->vion);
+  ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_vion");
   return RMGTD_OK;
 }
@@ -137,6 +138,7 @@ int build_projectors(rmgtd_ctx* ctx, const rmgtd_system* sys) {
                                   cudaMemcpyHostToDevice, ctx->stream));
   k_proj_values<<<np, kThreads, 0, ctx->stream>>>(ctx->nx, ctx->ny, ctx->nz, ctx->h, ctx->pbox,
                                                   ctx->poff, cen_d, lm_d, rc_d, ctx->pval);
+  ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_proj_values");
   RMGTD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   return RMGTD_OK;
@@ -317,6 +319,7 @@ static int apply_h_t(rmgtd_ctx* ctx, const T* x, T* hx, int ncols, const double*
   k_hstencil<T, BX, BY><<<grid, dim3(BX, BY), 0, ctx->stream>>>(
       x, hx, ctx->vion, vextra, ctx->nx, ctx->ny, ctx->nz, zchunk, nzc,
       -0.5 / (ctx->h * ctx->h), ctx->Ng);
+  ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_hstencil");
   if (ctx->nproj > 0) {
     const int np = ctx->nproj;
@@ -324,6 +327,7 @@ static int apply_h_t(rmgtd_ctx* ctx, const T* x, T* hx, int ncols, const double*
     if (!coef) return set_error(ctx, RMGTD_ENOMEM, "KB coefficient buffer");
     k_kb_project<T><<<dim3(np, ncols), kThreads, 0, ctx->stream>>>(
         x, ncols, ctx->Ng, ctx->nx, ctx->ny, ctx->pbox, ctx->poff, ctx->pval, ctx->h3, coef);
+    ++ctx->launches;
     RMGTD_LAUNCH(ctx, "k_kb_project");
     for (int p = 0; p < np; ++p) {
       const long long nb = ctx->h_poff[p + 1] - ctx->h_poff[p];
@@ -332,6 +336,7 @@ static int apply_h_t(rmgtd_ctx* ctx, const T* x, T* hx, int ncols, const double*
       k_kb_apply<T><<<dim3(bl, ncols), kThreads, 0, ctx->stream>>>(
           hx, ncols, ctx->Ng, ctx->nx, ctx->ny, p, np, ctx->pbox, ctx->poff, ctx->pval,
           ctx->Ekb, coef);
+      ++ctx->launches;
       RMGTD_LAUNCH(ctx, "k_kb_apply");
     }
   }
@@ -400,6 +405,7 @@ int launch_lda(rmgtd_ctx* ctx, const double* rho, const double* vh, double* vxc,
   const int blocks = (int)std::min<long>(ceil_div(n, kThreads), 4L * ctx->num_sms);
   k_lda<<<dim3(std::max(blocks, 1), nrep), kThreads, 0, ctx->stream>>>(
       rho, vh, vxc, exc, vhxc, n, ctl, stride, with_xc);
+  ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_lda");
   return RMGTD_OK;
 }

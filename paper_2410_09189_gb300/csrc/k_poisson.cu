@@ -576,14 +576,17 @@ static int vcycle(rmgtd_ctx* ctx, const double* r0, double* z0, int nrep) {
       double* out = bufs[cur];
       const double* in = bufs[cur ^ 1];
       k_mg_jacobi<<<dim3(bl, nrep), kThreads, 0, ctx->stream>>>(G, in, out, b, s == 0, st);
+      ++ctx->launches;
       cur ^= 1;
     }
     RMGTD_LAUNCH(ctx, "k_mg_jacobi");
     if (coarsest) break;
     k_mg_residual<<<dim3(bl, nrep), kThreads, 0, ctx->stream>>>(G, x, b, L.r, st);
+    ++ctx->launches;
     MgLevel& C = ctx->mg[l + 1];
     k_mg_restrict<<<dim3(grid_blocks(ctx, C.n), nrep), kThreads, 0, ctx->stream>>>(
         G, grid_of(C), L.r, C.b, st);
+    ++ctx->launches;
     RMGTD_LAUNCH(ctx, "k_mg_restrict");
   }
   if (tail >= 0) {
@@ -597,6 +600,7 @@ static int vcycle(rmgtd_ctx* ctx, const double* r0, double* z0, int nrep) {
     }
     k_mg_tail<<<nrep, 1024, ctx->mg_tail_smem, ctx->stream>>>(T, ctx->mg[tail].b,
                                                                ctx->mg[tail].x, st);
+    ++ctx->launches;
     RMGTD_LAUNCH(ctx, "k_mg_tail");
   }
   // ascend on multi-block levels
@@ -608,12 +612,14 @@ static int vcycle(rmgtd_ctx* ctx, const double* r0, double* z0, int nrep) {
     double* x = (l == 0) ? z0 : L.x;
     const int bl = grid_blocks(ctx, L.n);
     k_mg_prolong<<<dim3(bl, nrep), kThreads, 0, ctx->stream>>>(G, grid_of(C), C.x, x, st);
+    ++ctx->launches;
     double* bufs[2] = {x, L.r};
     int cur = 1;
     for (int s = 0; s < kPost; ++s) {
       double* out = bufs[cur];
       const double* in = bufs[cur ^ 1];
       k_mg_jacobi<<<dim3(bl, nrep), kThreads, 0, ctx->stream>>>(G, in, out, b, 0, st);
+      ++ctx->launches;
       cur ^= 1;
     }
     RMGTD_LAUNCH(ctx, "k_mg_post");
@@ -679,35 +685,47 @@ int hartree_dev(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* ctl
   const dim3 grid(nb, nrep);
   double* part = ctx->red_part;
   k_moments<<<grid, kThreads, 0, ctx->stream>>>(G, rho, part, ctl);
+  ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_moments");
   k_hartree_rhs<<<grid, kThreads, 0, ctx->stream>>>(G, rho, part, nb, ctx->pcg_b, zero_bc, ctl);
+  ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_hartree_rhs");
   // separate partial area for the CG scalars (moments are consumed above)
   double* cg = part;
   k_pcg_init<<<grid, kThreads, 0, ctx->stream>>>(G, vh, ctx->pcg_b, ctx->pcg_r, cg, ctl);
+  ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_pcg_init");
   k_pcg_state_init<<<1, 32 * nrep, 0, ctx->stream>>>(ctx->pcg, cg, nb, ctx->opt.poisson_tol, ctl,
                                                      nrep);
+  ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_pcg_state_init");
   int rc = vcycle(ctx, ctx->pcg_r, ctx->pcg_z, nrep);
   if (rc) return rc;
   k_pcg_rz<<<grid, kThreads, 0, ctx->stream>>>(Ng, ctx->pcg_r, ctx->pcg_z, ctx->pcg_p, 1, cg,
                                                ctx->pcg);
+  ++ctx->launches;
   k_pcg_rz_store<<<1, 32 * nrep, 0, ctx->stream>>>(ctx->pcg, cg, nb, nrep);
+  ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_pcg_rz");
   for (int it = 0; it < ctx->opt.poisson_max_iter; ++it) {
     k_pcg_Ap<<<grid, kThreads, 0, ctx->stream>>>(G, ctx->pcg_p, ctx->pcg_Ap, cg, ctx->pcg);
+    ++ctx->launches;
     k_pcg_xr<<<grid, kThreads, 0, ctx->stream>>>(Ng, vh, ctx->pcg_r, ctx->pcg_p, ctx->pcg_Ap, cg,
                                                  ctx->pcg);
+    ++ctx->launches;
     k_pcg_check<<<1, 32 * nrep, 0, ctx->stream>>>(ctx->pcg, cg, nb, ctx->opt.poisson_tol,
                                                   ctx->opt.poisson_max_iter, nrep, ctx->status);
+    ++ctx->launches;
     RMGTD_LAUNCH(ctx, "k_pcg_iteration");
     rc = vcycle(ctx, ctx->pcg_r, ctx->pcg_z, nrep);
     if (rc) return rc;
     k_pcg_rz<<<grid, kThreads, 0, ctx->stream>>>(Ng, ctx->pcg_r, ctx->pcg_z, ctx->pcg_p, 0, cg,
                                                  ctx->pcg);
+    ++ctx->launches;
     k_pcg_p<<<grid, kThreads, 0, ctx->stream>>>(Ng, ctx->pcg_z, ctx->pcg_p, cg, ctx->pcg);
+    ++ctx->launches;
     k_pcg_end<<<1, 32 * nrep, 0, ctx->stream>>>(ctx->pcg, cg, nb, nrep, ctx->pcg_any);
+    ++ctx->launches;
     RMGTD_LAUNCH(ctx, "k_pcg_end");
     // eager mode: peek at the convergence flag every few iterations to stop launching
     if ((it & 3) == 3) {

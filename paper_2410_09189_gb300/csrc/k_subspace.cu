@@ -136,11 +136,13 @@ int gram(rmgtd_ctx* ctx, const double* A, const double* B, const double* w, long
   dim3 grid(ntiles, nsplit, nw);
   k_gram_partial<<<grid, 256, 0, ctx->stream>>>(N, ctx->Ng, A, B, w, wstride, sym, T, chunk,
                                                  ctx->gram_part, ctl);
+  ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_gram_partial");
   const long NN = (long)N * N;
   const int rb = (int)std::min<long>(ceil_div(NN, 256), 2L * ctx->num_sms);
   k_gram_reduce<<<dim3(rb, nw), 256, 0, ctx->stream>>>(N, nsplit, ctx->gram_part, scale, base,
                                                         out, NN, prev, sym, errbits, ctl);
+  ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_gram_reduce");
   return RMGTD_OK;
 }
@@ -203,6 +205,7 @@ int rho_dev(rmgtd_ctx* ctx, const double* S, double* rho, const RepCtl* ctl, int
   dim3 grid(ceil_div(ctx->Ng, kRhoThreads), nrep);
   k_rho<<<grid, kRhoThreads, 0, ctx->stream>>>(ctx->N, ctx->Ng, ctx->phi, S,
                                                 (long)ctx->N * ctx->N, rho, ctx->Ng, ctl);
+  ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_rho");
   return RMGTD_OK;
 }
@@ -462,6 +465,7 @@ static int launch_eldyn_ts(rmgtd_ctx* ctx, EldynArgs& a) {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   RMGTD_CUDA(ctx, cudaLaunchKernelExC(&cfg, (const void*)k_eldyn<TS>, args));
+  ++ctx->launches;
   return RMGTD_OK;
 }
 
@@ -543,6 +547,7 @@ int step_begin(rmgtd_ctx* ctx) {
   const int blocks = (int)std::min<long>(ceil_div(n, 256), 2L * ctx->num_sms);
   k_step_begin<<<std::max(blocks, 1), 256, 0, ctx->stream>>>(n, ctx->H0, ctx->Hm1, ctx->H1,
                                                               ctx->ctl, ctx->nrep);
+  ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_step_begin");
   return RMGTD_OK;
 }
@@ -550,6 +555,7 @@ int step_begin(rmgtd_ctx* ctx) {
 int scf_control(rmgtd_ctx* ctx, const unsigned long long* errbits) {
   k_scf_control<<<1, 32, 0, ctx->stream>>>(ctx->ctl, ctx->nrep, errbits, ctx->opt.H_thrs,
                                            ctx->opt.max_scf, ctx->status);
+  ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_scf_control");
   return RMGTD_OK;
 }
@@ -621,9 +627,11 @@ int observables(rmgtd_ctx* ctx) {
   const int nblk = ctx->red_blocks;
   k_obs_partial<<<dim3(nblk, ctx->nrep), 256, 0, ctx->stream>>>(
       ctx->N, ctx->Ng, ctx->S0, ctx->M, ctx->Hcore, ctx->rho, ctx->vh, ctx->exc, ctx->red_part);
+  ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_obs_partial");
   k_obs_final<<<ctx->nrep, 256, 0, ctx->stream>>>(nblk, ctx->red_part, ctx->h3, ctx->E_ion,
                                                   ctx->obs);
+  ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_obs_final");
   return RMGTD_OK;
 }
@@ -671,11 +679,13 @@ int orthonormalize(rmgtd_ctx* ctx) {
                 nullptr, 1, nullptr);
   if (rc) return rc;
   k_cholesky<<<1, 1024, 0, ctx->stream>>>(N, ctx->Smat, ctx->status);
+  ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_cholesky");
   double* work = (double*)dev_alloc(ctx, sizeof(double) * (size_t)N * ctx->Ng);
   if (!work) return set_error(ctx, RMGTD_ENOMEM, "orthonormalisation scratch");
   k_forward_subst<<<ceil_div(ctx->Ng, 128), 128, 0, ctx->stream>>>(N, ctx->Ng, ctx->Smat,
                                                                     ctx->phi, work);
+  ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_forward_subst");
   RMGTD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   dev_free(ctx, work);

@@ -150,6 +150,15 @@ struct rmgtd_ctx {
   double* obs = nullptr;            // [nrep][8] observables
   double* obs_host = nullptr;       // pinned
 
+  // counters and per-phase event timing
+  long long launches = 0;
+  int profile = 0;
+  std::vector<cudaEvent_t> ev_pool;   // pairs (begin, end)
+  std::vector<int> ev_phase;
+  int ev_n = 0;
+  double phase_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  long long phase_calls[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+
   // CUDA graph of one time step
   cudaGraphExec_t step_exec = nullptr;
   cudaGraph_t step_graph = nullptr;
@@ -174,6 +183,12 @@ int cuda_check(rmgtd_ctx* ctx, cudaError_t e, const char* what);
   } while (0)
 
 void* dev_alloc(rmgtd_ctx* ctx, size_t bytes);
+
+// Phases of one SCF pass (event timing when profiling is on).
+enum Phase { PH_ELDYN = 0, PH_RHO = 1, PH_HARTREE = 2, PH_XC = 3, PH_HUPDATE = 4, PH_OTHER = 5 };
+void ph_begin(rmgtd_ctx* ctx, int phase);
+void ph_end(rmgtd_ctx* ctx);
+int ph_flush(rmgtd_ctx* ctx);
 
 // ---- device helpers ----------------------------------------------------------------
 __device__ __forceinline__ double warp_sum(double v) {

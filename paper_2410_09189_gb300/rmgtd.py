@@ -22,6 +22,8 @@ OK, EINVAL, ENOMEM, ECUDA, ENOTCONVERGED, EDIVERGED, ETIMEOUT, ESTATE = 0, -1, -
 PREC_FP64, PREC_MIXED = 0, 1
 F64, F32, C128, C64 = 0, 1, 2, 3
 MAT_P_RE, MAT_P_IM, MAT_H0, MAT_HM1, MAT_HCORE, MAT_MX, MAT_MY, MAT_MZ, MAT_S = range(9)
+NPHASES = 6
+PHASES = ("eldyn", "rho", "hartree", "xc", "hupdate", "other")
 
 _c_double_p = ctypes.POINTER(ctypes.c_double)
 _c_int_p = ctypes.POINTER(ctypes.c_int)
@@ -94,6 +96,9 @@ def load_library(path: Optional[str] = None):
         "rmgtd_load": (i, [vp, ctypes.c_char_p]),
         "rmgtd_time": (i, [vp, _c_double_p, ctypes.POINTER(ctypes.c_longlong)]),
         "rmgtd_last_error": (ctypes.c_char_p, [vp]),
+        "rmgtd_profile": (i, [vp, i]),
+        "rmgtd_profile_read": (i, [vp, _c_double_p, ctypes.POINTER(ctypes.c_longlong),
+                                   ctypes.POINTER(ctypes.c_longlong)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -285,6 +290,18 @@ class Context:
 
     def load(self, path: str):
         self._check(self._lib.rmgtd_load(self._ctx, path.encode()))
+
+    def profile(self, enable: bool = True):
+        """Start / stop per-phase CUDA-event timing (resets totals and the launch count)."""
+        self._check(self._lib.rmgtd_profile(self._ctx, 1 if enable else 0))
+
+    def profile_read(self):
+        """(phase -> ms, phase -> calls, kernel launches) since the last profile() call."""
+        ms = np.zeros(NPHASES)
+        calls = (ctypes.c_longlong * NPHASES)()
+        n = ctypes.c_longlong()
+        self._check(self._lib.rmgtd_profile_read(self._ctx, _dptr(ms), calls, ctypes.byref(n)))
+        return (dict(zip(PHASES, ms.tolist())), dict(zip(PHASES, list(calls))), int(n.value))
 
     def time(self):
         t = ctypes.c_double()
