@@ -142,7 +142,8 @@ typedef enum {
 
 /* Fill `opt` with defaults: dt 0.05, H_thrs 1e-7, dP_thrs 1e-10, max_scf 50,
  * max_terms 200, FP64, nrep 1, orthonormalize 1, poisson_tol 1e-12, 200 PCG iterations,
- * graphs on, default stream, cudaMalloc. */
+ * use_graph 1 (each time step is one CUDA graph with device-side while loops for the SCF
+ * passes and the Hartree iterations), default stream, cudaMalloc. */
 void rmgtd_default_options(rmgtd_options* opt);
 
 /* Set up a context (Algorithm 1 lines 1-8 given the orbitals): copy Phi, build V_loc and
@@ -214,7 +215,9 @@ int rmgtd_profile(rmgtd_ctx* ctx, int enable);
 
 /* Accumulated milliseconds and calls per phase since the last rmgtd_profile call
  * (host arrays of RMGTD_NPHASES, may be NULL) and the number of kernels the library has
- * launched since then.  Synchronises the stream. */
+ * launched since then (for graph steps: kernel nodes executed, counting each iteration of
+ * the device-side loops).  Phase times are recorded for host-driven steps only
+ * (use_graph = 0): a captured step has no per-phase events.  Synchronises the stream. */
 int rmgtd_profile_read(rmgtd_ctx* ctx, double* phase_ms, long long* phase_calls,
                        long long* launches);
 

@@ -67,14 +67,14 @@ double* kb_coef_buffer(rmgtd_ctx* ctx, int ncols) {
 constexpr int kEvPairs = 512;
 
 void ph_begin(rmgtd_ctx* ctx, int phase) {
-  if (!ctx->profile) return;
+  if (!ctx->profile || ctx->capturing) return;
   if (ctx->ev_n >= kEvPairs) ph_flush(ctx);
   cudaEventRecord(ctx->ev_pool[2 * ctx->ev_n], ctx->stream);
   ctx->ev_phase[ctx->ev_n] = phase;
 }
 
 void ph_end(rmgtd_ctx* ctx) {
-  if (!ctx->profile) return;
+  if (!ctx->profile || ctx->capturing) return;
   cudaEventRecord(ctx->ev_pool[2 * ctx->ev_n + 1], ctx->stream);
   ctx->ev_n += 1;
 }
@@ -150,6 +150,55 @@ __global__ void k_ion_energy(int natoms, const double* __restrict__ pos, const d
   if (threadIdx.x == 0) *out = s;
 }
 
+// ---- CUDA-graph helpers -----------------------------------------------------------------------
+// Add a while-loop node at the current capture position of ctx->stream; returns its body
+// graph and handle.  The handle starts each launch of the node at 1 (the body runs at least
+// once) and the body's last kernel sets it.
+static int add_while(rmgtd_ctx* ctx, cudaGraphConditionalHandle* h, cudaGraph_t* body) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  RMGTD_CUDA(ctx, cudaStreamGetCaptureInfo(ctx->stream, &cs, nullptr, &g, &deps, nullptr, &nd));
+  if (cs != cudaStreamCaptureStatusActive) return set_error(ctx, RMGTD_ECUDA, "stream not capturing");
+  RMGTD_CUDA(ctx, cudaGraphConditionalHandleCreate(h, g, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams p = {};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = *h;
+  p.conditional.type = cudaGraphCondTypeWhile;
+  p.conditional.size = 1;
+  cudaGraphNode_t node;
+  RMGTD_CUDA(ctx, cudaGraphAddNode(&node, g, deps, nullptr, nd, &p));
+  *body = p.conditional.phGraph_out[0];
+  RMGTD_CUDA(ctx, cudaStreamUpdateCaptureDependencies(ctx->stream, &node, nullptr, 1,
+                                                      cudaStreamSetCaptureDependencies));
+  return RMGTD_OK;
+}
+
+// Hartree solve inside a captured graph: prologue, then a device-side while loop of CG
+// iterations (captured on the second auxiliary stream).
+int hartree_graph(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* ctl, int nrep) {
+  int rc = hartree_begin(ctx, rho, vh, ctl, 0, nrep);
+  if (rc) return rc;
+  cudaGraphConditionalHandle hp;
+  cudaGraph_t body;
+  rc = add_while(ctx, &hp, &body);
+  if (rc) return rc;
+  cudaStream_t saved = ctx->stream;
+  RMGTD_CUDA(ctx, cudaStreamBeginCaptureToGraph(ctx->aux[1], body, nullptr, nullptr, 0,
+                                                cudaStreamCaptureModeRelaxed));
+  ctx->stream = ctx->aux[1];
+  const long long l0 = ctx->launches;
+  rc = hartree_iteration(ctx, vh, nrep, hp, 1);
+  ctx->cap_pcg = (int)(ctx->launches - l0);
+  ctx->stream = saved;
+  cudaGraph_t out;
+  cudaError_t e = cudaStreamEndCapture(ctx->aux[1], &out);
+  if (rc) return rc;
+  RMGTD_CUDA(ctx, e);
+  return RMGTD_OK;
+}
+
 // ---- one density-functional evaluation: H_1 <- DFT(rho(P)) (Algorithm 1 line 26) ------------
 // S: Re P per replica.  Writes rho, vh, vxc, exc, vhxc and H1 (in place) for active
 // replicas and folds max|H_new - H_1| into errbits.
@@ -161,7 +210,8 @@ int dft_eval(rmgtd_ctx* ctx, const double* S, const RepCtl* ctl, unsigned long l
   if (rc) return rc;
   if (ctx->hartree_xc) {
     ph_begin(ctx, PH_HARTREE);
-    rc = hartree_dev(ctx, ctx->rho, ctx->vh, ctl, 0, nrep);
+    rc = ctx->capturing ? hartree_graph(ctx, ctx->rho, ctx->vh, ctl, nrep)
+                        : hartree_dev(ctx, ctx->rho, ctx->vh, ctl, 0, nrep);
     ph_end(ctx);
     if (rc) return rc;
   }
@@ -224,7 +274,7 @@ void rmgtd_default_options(rmgtd_options* o) {
   o->orthonormalize = 1;
   o->poisson_tol = 1e-12;
   o->poisson_max_iter = 200;
-  o->use_graph = 0;
+  o->use_graph = 1;
 }
 
 const char* rmgtd_last_error(const rmgtd_ctx* ctx) {
@@ -247,7 +297,10 @@ void rmgtd_destroy(rmgtd_ctx* ctx) {
   if (ctx->ctl_host) cudaFreeHost(ctx->ctl_host);
   if (ctx->obs_host) cudaFreeHost(ctx->obs_host);
   if (ctx->pcg_any_host) cudaFreeHost(ctx->pcg_any_host);
+  if (ctx->stats_host) cudaFreeHost(ctx->stats_host);
   for (auto& e : ctx->ev_pool) cudaEventDestroy(e);
+  for (int i = 0; i < 2; ++i)
+    if (ctx->aux[i]) cudaStreamDestroy(ctx->aux[i]);
   delete ctx;
 }
 
@@ -318,6 +371,11 @@ static int create_impl(const rmgtd_system* sys, const rmgtd_options* opt, rmgtd_
   ctx->errbits = (unsigned long long*)A(sizeof(unsigned long long) * nrep);
   ctx->status = (int*)A(sizeof(int));
   ctx->obs = (double*)A(sizeof(double) * 8 * nrep);
+  ctx->failed = (int*)A(sizeof(int));
+  ctx->kexec = (unsigned long long*)A(2 * sizeof(unsigned long long));
+  ctx->done_steps = (int*)A(sizeof(int));
+  ctx->stats_cap = 256;
+  ctx->stats_dev = (RepCtl*)A(sizeof(RepCtl) * ctx->stats_cap * nrep);
   {
     const long per = std::max(3, nrep) * NN;
     const long want = per * 4L * ctx->num_sms;
@@ -329,9 +387,12 @@ static int create_impl(const rmgtd_system* sys, const rmgtd_options* opt, rmgtd_
     if (!b.ptr) return set_error(ctx, RMGTD_ENOMEM, "device allocation failed");
   if (!ctx->phi || !ctx->gram_part || !ctx->pcg_Ap || !ctx->dbuf || !ctx->errslots)
     return set_error(ctx, RMGTD_ENOMEM, "device allocation failed");
-  RMGTD_CUDA(ctx, cudaMallocHost((void**)&ctx->ctl_host, sizeof(RepCtl) * (nrep + 1)));
+  RMGTD_CUDA(ctx, cudaMallocHost((void**)&ctx->ctl_host, sizeof(RepCtl) * (nrep + 2)));
   RMGTD_CUDA(ctx, cudaMallocHost((void**)&ctx->obs_host, sizeof(double) * 8 * nrep));
   RMGTD_CUDA(ctx, cudaMallocHost((void**)&ctx->pcg_any_host, sizeof(int)));
+  RMGTD_CUDA(ctx, cudaMallocHost((void**)&ctx->stats_host, sizeof(RepCtl) * ctx->stats_cap * nrep));
+  RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->failed, 0, sizeof(int), ctx->stream));
+  RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->kexec, 0, 2 * sizeof(unsigned long long), ctx->stream));
   RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream));
   RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->vh, 0, gsz * nrep, ctx->stream));
   RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->ctl, 0, sizeof(RepCtl) * nrep, ctx->stream));
@@ -485,66 +546,143 @@ int rmgtd_kick(rmgtd_ctx* ctx, int rep, int axis, double kappa) {
   return check_status(ctx, "kick");
 }
 
+// One SCF pass of Algorithm 1 (lines 14-26) for every active replica.
+static int enqueue_pass(rmgtd_ctx* ctx, cudaGraphConditionalHandle cond, int use_cond) {
+  const long NN = (long)ctx->N * ctx->N;
+  ph_begin(ctx, PH_ELDYN);
+  int rc = eldyn(ctx, ctx->H0, ctx->H1, NN, ctx->opt.dt, ctx->S0, ctx->A0, ctx->S1, ctx->A1,
+                 ctx->ctl, ctx->ctl, 0, ctx->nrep);
+  ph_end(ctx);
+  if (rc) return rc;
+  rc = dft_eval(ctx, ctx->S1, ctx->ctl, ctx->errbits);
+  if (rc) return rc;
+  ph_begin(ctx, PH_OTHER);
+  rc = scf_control(ctx, ctx->errbits, cond, use_cond);
+  ph_end(ctx);
+  return rc;
+}
+
+// Capture one whole time step as a graph: H_1 extrapolation, a device-side while loop of
+// SCF passes (each containing the Hartree CG while loop), then the shift.
+static int build_step_graph(rmgtd_ctx* ctx) {
+  for (int i = 0; i < 2; ++i)
+    if (!ctx->aux[i]) RMGTD_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->aux[i], cudaStreamNonBlocking));
+  cudaStream_t main = ctx->stream;
+  RMGTD_CUDA(ctx, cudaStreamBeginCapture(main, cudaStreamCaptureModeRelaxed));
+  ctx->capturing = 1;
+  const long long saved_launches = ctx->launches;
+  int rc = step_begin(ctx);
+  cudaGraphConditionalHandle hs = 0;
+  cudaGraph_t body = nullptr;
+  if (!rc) rc = add_while(ctx, &hs, &body);
+  if (!rc) {
+    cudaError_t e = cudaStreamBeginCaptureToGraph(ctx->aux[0], body, nullptr, nullptr, 0,
+                                                  cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) {
+      rc = cuda_check(ctx, e, "cudaStreamBeginCaptureToGraph");
+    } else {
+      ctx->stream = ctx->aux[0];
+      const long long l0 = ctx->launches;
+      rc = enqueue_pass(ctx, hs, 1);
+      ctx->cap_scf = (int)(ctx->launches - l0) - ctx->cap_pcg;
+      ctx->stream = main;
+      cudaGraph_t out;
+      e = cudaStreamEndCapture(ctx->aux[0], &out);
+      if (!rc && e != cudaSuccess) rc = cuda_check(ctx, e, "end of SCF body capture");
+    }
+  }
+  if (!rc) rc = step_end(ctx);
+  ctx->cap_top = 2;  // step_begin, step_end
+  ctx->launches = saved_launches;
+  ctx->capturing = 0;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(main, &g);
+  if (rc) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  RMGTD_CUDA(ctx, e);
+  ctx->step_graph = g;
+  RMGTD_CUDA(ctx, cudaGraphInstantiate(&ctx->step_exec, g, 0));
+  return RMGTD_OK;
+}
+
+// Eager step: the host reads the control blocks after every pass.
+static int eager_step(rmgtd_ctx* ctx) {
+  int rc = step_begin(ctx);
+  if (rc) return rc;
+  for (int pass = 0; pass < ctx->opt.max_scf; ++pass) {
+    rc = enqueue_pass(ctx, 0, 0);
+    if (rc) return rc;
+    RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->ctl_host, ctx->ctl, sizeof(RepCtl) * ctx->nrep,
+                                    cudaMemcpyDeviceToHost, ctx->stream));
+    RMGTD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    bool any = false;
+    for (int r = 0; r < ctx->nrep; ++r) any |= ctx->ctl_host[r].active != 0;
+    if (!any) break;
+  }
+  ph_begin(ctx, PH_OTHER);
+  rc = step_end(ctx);
+  ph_end(ctx);
+  return rc;
+}
+
 int rmgtd_step(rmgtd_ctx* ctx, int nsteps, rmgtd_stats* stats) {
   if (!ctx) return set_error(nullptr, RMGTD_EINVAL, "ctx is NULL");
   if (nsteps < 0) return set_error(ctx, RMGTD_EINVAL, "nsteps < 0");
   const int nrep = ctx->nrep;
-  const long NN = (long)ctx->N * ctx->N;
-  const size_t msz = sizeof(double) * NN * nrep;
-  for (int s = 0; s < nsteps; ++s) {
-    RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream));
-    ph_begin(ctx, PH_OTHER);
-    int rc = step_begin(ctx);
-    ph_end(ctx);
+  if (ctx->opt.use_graph && !ctx->step_exec) {
+    int rc = build_step_graph(ctx);
     if (rc) return rc;
-    for (int pass = 0; pass < ctx->opt.max_scf; ++pass) {
-      ph_begin(ctx, PH_ELDYN);
-      rc = eldyn(ctx, ctx->H0, ctx->H1, NN, ctx->opt.dt, ctx->S0, ctx->A0, ctx->S1, ctx->A1,
-                 ctx->ctl, ctx->ctl, 0, nrep);
-      ph_end(ctx);
-      if (rc) return rc;
-      rc = dft_eval(ctx, ctx->S1, ctx->ctl, ctx->errbits);
-      if (rc) return rc;
-      ph_begin(ctx, PH_OTHER);
-      rc = scf_control(ctx, ctx->errbits);
-      ph_end(ctx);
-      if (rc) return rc;
-      RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->ctl_host, ctx->ctl, sizeof(RepCtl) * nrep,
-                                      cudaMemcpyDeviceToHost, ctx->stream));
-      RMGTD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-      bool any = false;
-      for (int r = 0; r < nrep; ++r) any |= ctx->ctl_host[r].active != 0;
-      if (!any) break;
-    }
-    int worst = RMGTD_OK;
-    for (int r = 0; r < nrep; ++r) {
-      const RepCtl& c = ctx->ctl_host[r];
-      if (stats) {
-        rmgtd_stats& o = stats[(long)s * nrep + r];
-        o.passes = c.passes;
-        o.terms_max = c.terms_max;
-        o.terms_sum = c.terms_sum;
-        o.status = c.status;
-        o.H_err = c.H_err;
+  }
+  RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->failed, 0, sizeof(int), ctx->stream));
+  int done_total = 0;
+  while (done_total < nsteps) {
+    const int chunk = std::min(nsteps - done_total, ctx->stats_cap);
+    RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->done_steps, 0, sizeof(int), ctx->stream));
+    for (int i = 0; i < chunk; ++i) {
+      if (ctx->step_exec) {
+        RMGTD_CUDA(ctx, cudaGraphLaunch(ctx->step_exec, ctx->stream));
+        ctx->graph_steps += 1;
+      } else {
+        int rc = eager_step(ctx);
+        if (rc) return rc;
       }
-      if (c.status != 0 && worst == RMGTD_OK) worst = c.status;
     }
-    if (worst == RMGTD_OK) {
-      int st = check_status(ctx, "step");
-      if (st) return st;
+    int* hdr = (int*)&ctx->ctl_host[nrep];  // scratch: done, failed, status
+    RMGTD_CUDA(ctx, cudaMemcpyAsync(&hdr[0], ctx->done_steps, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    RMGTD_CUDA(ctx, cudaMemcpyAsync(&hdr[1], ctx->failed, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    RMGTD_CUDA(ctx, cudaMemcpyAsync(&hdr[2], ctx->status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->stats_host, ctx->stats_dev, sizeof(RepCtl) * chunk * nrep,
+                                    cudaMemcpyDeviceToHost, ctx->stream));
+    RMGTD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    const int done = hdr[0], failed = hdr[1], gstatus = hdr[2];
+    const int recorded = std::min(chunk, done + (failed ? 1 : 0));
+    int worst = RMGTD_OK;
+    for (int k = 0; k < recorded; ++k) {
+      for (int r = 0; r < nrep; ++r) {
+        const RepCtl& c = ctx->stats_host[(long)k * nrep + r];
+        if (stats) {
+          rmgtd_stats& o = stats[(long)(done_total + k) * nrep + r];
+          o.passes = c.passes;
+          o.terms_max = c.terms_max;
+          o.terms_sum = c.terms_sum;
+          o.status = c.status;
+          o.H_err = c.H_err;
+        }
+        if (k == done && c.status != 0 && worst == RMGTD_OK) worst = c.status;
+      }
     }
-    if (worst != RMGTD_OK) {
+    ctx->steps += done;
+    ctx->t += done * ctx->opt.dt;
+    done_total += done;
+    if (failed) {
+      if (worst == RMGTD_OK) worst = gstatus ? gstatus : RMGTD_ENOTCONVERGED;
       char buf[128];
       snprintf(buf, sizeof(buf), "step %lld failed with status %d", ctx->steps + 1, worst);
+      ph_flush(ctx);
       return set_error(ctx, worst, buf);
     }
-    // H_-1 <- H_0, H_0 <- H_1, P_0 <- P_1 (Algorithm 1 line 28)
-    RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->Hm1, ctx->H0, msz, cudaMemcpyDeviceToDevice, ctx->stream));
-    RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->H0, ctx->H1, msz, cudaMemcpyDeviceToDevice, ctx->stream));
-    RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->S0, ctx->S1, msz, cudaMemcpyDeviceToDevice, ctx->stream));
-    RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->A0, ctx->A1, msz, cudaMemcpyDeviceToDevice, ctx->stream));
-    ctx->t += ctx->opt.dt;
-    ctx->steps += 1;
   }
   RMGTD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   return ph_flush(ctx);
@@ -565,6 +703,8 @@ int rmgtd_profile(rmgtd_ctx* ctx, int enable) {
     ctx->phase_calls[i] = 0;
   }
   ctx->launches = 0;
+  ctx->graph_steps = 0;
+  RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->kexec, 0, 2 * sizeof(unsigned long long), ctx->stream));
   return RMGTD_OK;
 }
 
@@ -577,7 +717,12 @@ int rmgtd_profile_read(rmgtd_ctx* ctx, double* phase_ms, long long* phase_calls,
     if (phase_ms) phase_ms[i] = ctx->phase_ms[i];
     if (phase_calls) phase_calls[i] = ctx->phase_calls[i];
   }
-  if (launches) *launches = ctx->launches;
+  if (launches) {
+    unsigned long long kx[2] = {0, 0};
+    RMGTD_CUDA(ctx, cudaMemcpy(kx, ctx->kexec, sizeof(kx), cudaMemcpyDeviceToHost));
+    *launches = ctx->launches + ctx->graph_steps * ctx->cap_top +
+                (long long)kx[0] * ctx->cap_scf + (long long)kx[1] * ctx->cap_pcg;
+  }
   return RMGTD_OK;
 }
 

@@ -3,12 +3,18 @@
 // Discrete problem (the same one the kinetic stencil defines): interior unknowns, ghost
 // layers holding the monopole + dipole field of rho about the box centre,
 //   (-Lap_12^0) V = 4 pi rho + L_ghost(V_b),  V_b(r) = Q/|r| + p.r/|r|^3.
-// Solved by conjugate gradients preconditioned with one symmetric multigrid V-cycle
-// (the paper's multigrid, Section 2.1): cell-centred coarsening by 2, 7-point operators
-// at spacing 2^l h, damped Jacobi smoothing (2 pre, 2 post), trilinear prolongation and
-// its transpose/8 as restriction; the levels with <= 4096 points run inside one block.
+// The ghost term is linear in (Q, p): L_ghost(V_b) = Q G0 + px Gx + py Gy + pz Gz with four
+// grid fields G fixed by the grid, formed once at set-up.
+//
+// Solver: flexible (Polak-Ribiere) conjugate gradients in float64, preconditioned by one
+// symmetric multigrid V-cycle in float32 (the paper's multigrid, Section 2.1): cell-centred
+// coarsening by 2, 7-point operators at spacing 2^l h, damped Jacobi smoothing (2 pre,
+// 2 post), trilinear prolongation and its transpose/8 as restriction; the levels with
+// <= 4096 points run inside one block.  The preconditioner's precision changes only the
+// iteration count: the residual, the iterates and the stopping test are float64.
 // Every kernel carries a replica index and returns at once for replicas whose solve has
-// converged, so a fixed launch sequence (eager or captured in a graph) stays correct.
+// converged, so a fixed launch sequence (eager or inside a CUDA-graph while loop) is
+// correct.
 #include <math.h>
 
 #include "rmgtd_internal.cuh"
@@ -16,7 +22,7 @@
 namespace rmgtd {
 
 constexpr double kPi = 3.14159265358979323846;
-constexpr double kJacobiW = 6.0 / 7.0;
+constexpr float kJacobiW = 6.0f / 7.0f;
 constexpr int kTailMax = 4096;
 constexpr int kPre = 2, kPost = 2, kCoarseSweeps = 40;
 
@@ -27,7 +33,51 @@ struct Grid3 {
 
 __device__ __forceinline__ bool pcg_skip(const PcgState* st, int rep) { return st[rep].done != 0; }
 
-// ---- multipole moments (partials) ------------------------------------------------------
+__device__ __forceinline__ double sum_partials(const double* p, int n) {
+  // every lane of the calling warp returns the same fixed-order sum
+  double s = 0.0;
+  for (int b = (threadIdx.x & 31); b < n; b += 32) s += p[b];
+  return warp_sum(s);
+}
+
+// ---- set-up: ghost response fields G0, Gx, Gy, Gz ------------------------------------------
+__global__ void k_ghost_fields(Grid3 G, double* __restrict__ gf) {
+  const long Ng = (long)G.nx * G.ny * G.nz;
+  const double ih2 = 1.0 / (G.h * G.h);
+  for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < Ng;
+       g += (long)gridDim.x * blockDim.x) {
+    const int ix = (int)(g % G.nx), iy = (int)((g / G.nx) % G.ny), iz = (int)(g / ((long)G.nx * G.ny));
+    const int idx[3] = {ix, iy, iz};
+    const int nn[3] = {G.nx, G.ny, G.nz};
+    double g0 = 0, gx = 0, gy = 0, gz = 0;
+    for (int ax = 0; ax < 3; ++ax) {
+      for (int m = 1; m <= kFdRadius; ++m) {
+        for (int sgn = -1; sgn <= 1; sgn += 2) {
+          const int t = idx[ax] + sgn * m;
+          if (t >= 0 && t < nn[ax]) continue;
+          int gi[3] = {ix, iy, iz};
+          gi[ax] = t;
+          const double x = axis_coord(gi[0], G.nx, G.h), y = axis_coord(gi[1], G.ny, G.h),
+                       z = axis_coord(gi[2], G.nz, G.h);
+          const double r2 = x * x + y * y + z * z;
+          const double r = sqrt(r2);
+          const double c = fd_coef(m) * ih2;
+          g0 += c / r;
+          const double c3 = c / (r2 * r);
+          gx += c3 * x;
+          gy += c3 * y;
+          gz += c3 * z;
+        }
+      }
+    }
+    gf[g] = g0;
+    gf[Ng + g] = gx;
+    gf[2 * Ng + g] = gy;
+    gf[3 * Ng + g] = gz;
+  }
+}
+
+// ---- multipole moments (partials into slots 4..7) ------------------------------------------
 __global__ void k_moments(Grid3 G, const double* __restrict__ rho, double* __restrict__ part,
                           const RepCtl* __restrict__ ctl) {
   const int rep = blockIdx.y;
@@ -47,61 +97,8 @@ __global__ void k_moments(Grid3 G, const double* __restrict__ rho, double* __res
   __shared__ double sh[32];
   for (int t = 0; t < 4; ++t) {
     const double s = block_sum(q[t], sh);
-    if (threadIdx.x == 0) part[((long)rep * 4 + t) * gridDim.x + blockIdx.x] = s;
+    if (threadIdx.x == 0) part[((long)rep * 8 + 4 + t) * gridDim.x + blockIdx.x] = s;
     __syncthreads();
-  }
-}
-
-__device__ __forceinline__ double sum_partials(const double* p, int n) {
-  // every thread of warp 0 of the block returns the same fixed-order sum
-  double s = 0.0;
-  for (int b = (threadIdx.x & 31); b < n; b += 32) s += p[b];
-  return warp_sum(s);
-}
-
-// ---- right-hand side with the ghost contribution ----------------------------------------
-__global__ void k_hartree_rhs(Grid3 G, const double* __restrict__ rho,
-                              const double* __restrict__ mpart, int nblk, double* __restrict__ b,
-                              int zero_bc, const RepCtl* __restrict__ ctl) {
-  const int rep = blockIdx.y;
-  if (ctl && !ctl[rep].active) return;
-  __shared__ double mom[4];
-  if (threadIdx.x < 32) {
-    for (int t = 0; t < 4; ++t) {
-      const double s = sum_partials(mpart + ((long)rep * 4 + t) * nblk, nblk);
-      if (threadIdx.x == 0) mom[t] = s;
-    }
-  }
-  __syncthreads();
-  const double h3 = G.h * G.h * G.h;
-  const double Q = h3 * mom[0], px = h3 * mom[1], py = h3 * mom[2], pz = h3 * mom[3];
-  const long Ng = (long)G.nx * G.ny * G.nz;
-  const double ih2 = 1.0 / (G.h * G.h);
-  for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < Ng;
-       g += (long)gridDim.x * blockDim.x) {
-    const int ix = (int)(g % G.nx), iy = (int)((g / G.nx) % G.ny), iz = (int)(g / ((long)G.nx * G.ny));
-    double v = 4.0 * kPi * rho[rep * Ng + g];
-    if (!zero_bc) {
-      const int idx[3] = {ix, iy, iz};
-      const int nn[3] = {G.nx, G.ny, G.nz};
-      for (int ax = 0; ax < 3; ++ax) {
-        for (int m = 1; m <= kFdRadius; ++m) {
-          for (int sgn = -1; sgn <= 1; sgn += 2) {
-            const int t = idx[ax] + sgn * m;
-            if (t >= 0 && t < nn[ax]) continue;
-            int gi[3] = {ix, iy, iz};
-            gi[ax] = t;
-            const double x = axis_coord(gi[0], G.nx, G.h), y = axis_coord(gi[1], G.ny, G.h),
-                         z = axis_coord(gi[2], G.nz, G.h);
-            const double r2 = x * x + y * y + z * z;
-            const double r = sqrt(r2);
-            const double vb = Q / r + (px * x + py * y + pz * z) / (r2 * r);
-            v += fd_coef(m) * ih2 * vb;
-          }
-        }
-      }
-    }
-    b[rep * Ng + g] = v;
   }
 }
 
@@ -125,12 +122,25 @@ __device__ __forceinline__ double apply_A12(const double* __restrict__ x, int ix
   return -s * ih2;
 }
 
-// r = b - A x, partials of (b,b) and (r,r)
-__global__ void k_pcg_init(Grid3 G, const double* __restrict__ x, const double* __restrict__ b,
-                           double* __restrict__ r, double* __restrict__ part,
+// b = 4 pi rho + Q G0 + p.G ; r = b - A x ; partials of (b,b) (slot 0), (r,r) (slot 1)
+__global__ void k_pcg_init(Grid3 G, const double* __restrict__ rho, const double* __restrict__ gf,
+                           const double* __restrict__ x, double* __restrict__ b,
+                           double* __restrict__ r, double* __restrict__ part, int zero_bc,
                            const RepCtl* __restrict__ ctl) {
   const int rep = blockIdx.y;
   if (ctl && !ctl[rep].active) return;
+  const int nblk = gridDim.x;
+  __shared__ double mom[4];
+  if (threadIdx.x < 32) {
+    for (int t = 0; t < 4; ++t) {
+      const double s = sum_partials(part + ((long)rep * 8 + 4 + t) * nblk, nblk);
+      if (threadIdx.x == 0) mom[t] = s;
+    }
+  }
+  __syncthreads();
+  const double h3 = G.h * G.h * G.h;
+  const double Q = zero_bc ? 0.0 : h3 * mom[0], px = zero_bc ? 0.0 : h3 * mom[1],
+               py = zero_bc ? 0.0 : h3 * mom[2], pz = zero_bc ? 0.0 : h3 * mom[3];
   const long Ng = (long)G.nx * G.ny * G.nz;
   const double ih2 = 1.0 / (G.h * G.h);
   const double* xr = x + rep * Ng;
@@ -138,7 +148,9 @@ __global__ void k_pcg_init(Grid3 G, const double* __restrict__ x, const double* 
   for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < Ng;
        g += (long)gridDim.x * blockDim.x) {
     const int ix = (int)(g % G.nx), iy = (int)((g / G.nx) % G.ny), iz = (int)(g / ((long)G.nx * G.ny));
-    const double bv = b[rep * Ng + g];
+    double bv = 4.0 * kPi * rho[rep * Ng + g];
+    bv += Q * gf[g] + px * gf[Ng + g] + py * gf[2 * Ng + g] + pz * gf[3 * Ng + g];
+    b[rep * Ng + g] = bv;
     const double rv = bv - apply_A12(xr, ix, iy, iz, G.nx, G.ny, G.nz, ih2);
     r[rep * Ng + g] = rv;
     bb += bv * bv;
@@ -146,20 +158,19 @@ __global__ void k_pcg_init(Grid3 G, const double* __restrict__ x, const double* 
   }
   __shared__ double sh[32];
   bb = block_sum(bb, sh);
-  if (threadIdx.x == 0) part[((long)rep * 4 + 0) * gridDim.x + blockIdx.x] = bb;
+  if (threadIdx.x == 0) part[((long)rep * 8 + 0) * nblk + blockIdx.x] = bb;
   __syncthreads();
   rr = block_sum(rr, sh);
-  if (threadIdx.x == 0) part[((long)rep * 4 + 1) * gridDim.x + blockIdx.x] = rr;
+  if (threadIdx.x == 0) part[((long)rep * 8 + 1) * nblk + blockIdx.x] = rr;
 }
 
 __global__ void k_pcg_state_init(PcgState* st, const double* __restrict__ part, int nblk,
                                  double tol, const RepCtl* __restrict__ ctl, int nrep) {
-  // one warp per replica
-  const int rep = threadIdx.x >> 5;
+  const int rep = threadIdx.x >> 5;  // one warp per replica
   if (rep >= nrep) return;
   const bool act = !ctl || ctl[rep].active;
-  const double bb = sum_partials(part + ((long)rep * 4 + 0) * nblk, nblk);
-  const double rr = sum_partials(part + ((long)rep * 4 + 1) * nblk, nblk);
+  const double bb = sum_partials(part + ((long)rep * 8 + 0) * nblk, nblk);
+  const double rr = sum_partials(part + ((long)rep * 8 + 1) * nblk, nblk);
   if ((threadIdx.x & 31) == 0) {
     PcgState& s = st[rep];
     s.bb = bb;
@@ -172,7 +183,7 @@ __global__ void k_pcg_state_init(PcgState* st, const double* __restrict__ part, 
   }
 }
 
-// (r, z) partials; p = z when `first`
+// (r, z) partials into slot 2; p = z when `first`
 __global__ void k_pcg_rz(long Ng, const double* __restrict__ r, const double* __restrict__ z,
                          double* __restrict__ p, int first, double* __restrict__ part,
                          const PcgState* __restrict__ st) {
@@ -187,18 +198,17 @@ __global__ void k_pcg_rz(long Ng, const double* __restrict__ r, const double* __
   }
   __shared__ double sh[32];
   s = block_sum(s, sh);
-  if (threadIdx.x == 0) part[((long)rep * 4 + 2) * gridDim.x + blockIdx.x] = s;
+  if (threadIdx.x == 0) part[((long)rep * 8 + 2) * gridDim.x + blockIdx.x] = s;
 }
 
-// first (r,z): store into rz[cur]
 __global__ void k_pcg_rz_store(PcgState* st, const double* __restrict__ part, int nblk, int nrep) {
   const int rep = threadIdx.x >> 5;
   if (rep >= nrep || st[rep].done) return;
-  const double s = sum_partials(part + ((long)rep * 4 + 2) * nblk, nblk);
+  const double s = sum_partials(part + ((long)rep * 8 + 2) * nblk, nblk);
   if ((threadIdx.x & 31) == 0) st[rep].rz[st[rep].cur] = s;
 }
 
-// Ap = A p and partials of (p, Ap)
+// Ap = A p and partials of (p, Ap) into slot 3
 __global__ void k_pcg_Ap(Grid3 G, const double* __restrict__ p, double* __restrict__ Ap,
                          double* __restrict__ part, const PcgState* __restrict__ st) {
   const int rep = blockIdx.y;
@@ -216,24 +226,26 @@ __global__ void k_pcg_Ap(Grid3 G, const double* __restrict__ p, double* __restri
   }
   __shared__ double sh[32];
   s = block_sum(s, sh);
-  if (threadIdx.x == 0) part[((long)rep * 4 + 3) * gridDim.x + blockIdx.x] = s;
+  if (threadIdx.x == 0) part[((long)rep * 8 + 3) * gridDim.x + blockIdx.x] = s;
 }
 
-// alpha = rz/(p,Ap); x += alpha p; r -= alpha Ap; partials of (r,r)
+// alpha = rz/(p,Ap); x += alpha p; r -= alpha Ap; partials of (r,r) (slot 1) and of
+// (r_new, z_old) (slot 5) for the flexible beta
 __global__ void k_pcg_xr(long Ng, double* __restrict__ x, double* __restrict__ r,
                          const double* __restrict__ p, const double* __restrict__ Ap,
-                         double* __restrict__ part, const PcgState* __restrict__ st) {
+                         const double* __restrict__ z, double* __restrict__ part,
+                         const PcgState* __restrict__ st) {
   const int rep = blockIdx.y;
   if (pcg_skip(st, rep)) return;
   __shared__ double alpha;
   const int nblk = gridDim.x;
   if (threadIdx.x < 32) {
-    const double pAp = sum_partials(part + ((long)rep * 4 + 3) * nblk, nblk);
+    const double pAp = sum_partials(part + ((long)rep * 8 + 3) * nblk, nblk);
     if (threadIdx.x == 0) alpha = st[rep].rz[st[rep].cur] / pAp;
   }
   __syncthreads();
   const double a = alpha;
-  double s = 0.0;
+  double s = 0.0, t = 0.0;
   for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < Ng;
        g += (long)gridDim.x * blockDim.x) {
     const long e = rep * Ng + g;
@@ -241,18 +253,21 @@ __global__ void k_pcg_xr(long Ng, double* __restrict__ x, double* __restrict__ r
     const double rv = fma(-a, Ap[e], r[e]);
     r[e] = rv;
     s += rv * rv;
+    t += rv * z[e];
   }
   __shared__ double sh[32];
   s = block_sum(s, sh);
-  if (threadIdx.x == 0) part[((long)rep * 4 + 1) * gridDim.x + blockIdx.x] = s;
+  if (threadIdx.x == 0) part[((long)rep * 8 + 1) * nblk + blockIdx.x] = s;
+  __syncthreads();
+  t = block_sum(t, sh);
+  if (threadIdx.x == 0) part[((long)rep * 8 + 5) * nblk + blockIdx.x] = t;
 }
 
-// convergence test after the update of r
 __global__ void k_pcg_check(PcgState* st, const double* __restrict__ part, int nblk, double tol,
                             int max_it, int nrep, int* status) {
   const int rep = threadIdx.x >> 5;
   if (rep >= nrep || st[rep].done) return;
-  const double rr = sum_partials(part + ((long)rep * 4 + 1) * nblk, nblk);
+  const double rr = sum_partials(part + ((long)rep * 8 + 1) * nblk, nblk);
   if ((threadIdx.x & 31) == 0) {
     PcgState& s = st[rep];
     s.rr = rr;
@@ -270,7 +285,7 @@ __global__ void k_pcg_check(PcgState* st, const double* __restrict__ part, int n
   }
 }
 
-// beta = (r,z)_new/(r,z)_old; p = z + beta p
+// beta = ((r,z_new) - (r,z_old)) / rz_old (Polak-Ribiere); p = z + beta p
 __global__ void k_pcg_p(long Ng, const double* __restrict__ z, double* __restrict__ p,
                         const double* __restrict__ part, const PcgState* __restrict__ st) {
   const int rep = blockIdx.y;
@@ -278,8 +293,9 @@ __global__ void k_pcg_p(long Ng, const double* __restrict__ z, double* __restric
   __shared__ double beta;
   const int nblk = gridDim.x;
   if (threadIdx.x < 32) {
-    const double rz = sum_partials(part + ((long)rep * 4 + 2) * nblk, nblk);
-    if (threadIdx.x == 0) beta = rz / st[rep].rz[st[rep].cur];
+    const double rzn = sum_partials(part + ((long)rep * 8 + 2) * nblk, nblk);
+    const double rzo = sum_partials(part + ((long)rep * 8 + 5) * nblk, nblk);
+    if (threadIdx.x == 0) beta = (rzn - rzo) / st[rep].rz[st[rep].cur];
   }
   __syncthreads();
   const double bt = beta;
@@ -290,11 +306,13 @@ __global__ void k_pcg_p(long Ng, const double* __restrict__ z, double* __restric
   }
 }
 
+// end of one CG iteration: store (r,z), advance, and (inside a graph) set the while flag
 __global__ void k_pcg_end(PcgState* st, const double* __restrict__ part, int nblk, int nrep,
-                          int* any_active) {
+                          int* any_active, cudaGraphConditionalHandle cond, int use_cond,
+                          unsigned long long* kexec) {
   const int rep = threadIdx.x >> 5;
   if (rep < nrep && !st[rep].done) {
-    const double rz = sum_partials(part + ((long)rep * 4 + 2) * nblk, nblk);
+    const double rz = sum_partials(part + ((long)rep * 8 + 2) * nblk, nblk);
     if ((threadIdx.x & 31) == 0) {
       PcgState& s = st[rep];
       s.cur ^= 1;
@@ -302,20 +320,25 @@ __global__ void k_pcg_end(PcgState* st, const double* __restrict__ part, int nbl
       s.it += 1;
     }
   }
-  if (any_active && threadIdx.x == 0) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
     int a = 0;
-    for (int r = 0; r < nrep; ++r) a |= (st[r].done == 0);
-    *any_active = a;
+    for (int r = 0; r < nrep; ++r) a |= (*((volatile int*)&st[r].done) == 0);
+    if (any_active) *any_active = a;
+    if (use_cond) {
+      cudaGraphSetConditional(cond, a ? 1u : 0u);
+      atomicAdd(&kexec[1], 1ull);
+    }
   }
 }
 
-// ---- multigrid V-cycle (7-point operators, zero Dirichlet ghosts) -------------------------
-__device__ __forceinline__ double lap7(const double* __restrict__ x, int ix, int iy, int iz,
-                                       int nx, int ny, int nz, double* center) {
+// ---- multigrid V-cycle in float32 (7-point operators, zero Dirichlet ghosts) ---------------
+__device__ __forceinline__ float lap7f(const float* __restrict__ x, int ix, int iy, int iz,
+                                       int nx, int ny, int nz, float* center) {
   const long plane = (long)nx * ny;
   const long g = (long)iz * plane + (long)iy * nx + ix;
-  const double c = x[g];
-  double s = 0.0;
+  const float c = x[g];
+  float s = 0.0f;
   if (ix + 1 < nx) s += x[g + 1];
   if (ix > 0) s += x[g - 1];
   if (iy + 1 < ny) s += x[g + nx];
@@ -323,115 +346,134 @@ __device__ __forceinline__ double lap7(const double* __restrict__ x, int ix, int
   if (iz + 1 < nz) s += x[g + plane];
   if (iz > 0) s += x[g - plane];
   *center = c;
-  return 6.0 * c - s;  // h^2 * (-Lap_7 x)
+  return 6.0f * c - s;  // h^2 * (-Lap_7 x)
 }
 
-// one damped-Jacobi sweep: xo = xi + w h^2/6 (b - A xi); `first`: xi = 0
-__global__ void k_mg_jacobi(Grid3 G, const double* __restrict__ xi, double* __restrict__ xo,
-                            const double* __restrict__ b, int first,
-                            const PcgState* __restrict__ st) {
+// one damped-Jacobi sweep on level data: xo = xi + w h^2/6 (b - A xi).
+// first: xi = 0; b64 != NULL: b is read from the float64 residual and stored as float in
+// bf; out64 != NULL: the result goes to that float64 array instead of xo.
+__global__ void k_mg_jacobi(Grid3 G, const float* __restrict__ xi, float* __restrict__ xo,
+                            float* __restrict__ bf, const double* __restrict__ b64, int first,
+                            double* __restrict__ out64, const PcgState* __restrict__ st) {
   const int rep = blockIdx.y;
   if (pcg_skip(st, rep)) return;
   const long n = (long)G.nx * G.ny * G.nz;
-  const double h2 = G.h * G.h, ih2 = 1.0 / h2;
-  const double* xr = xi + rep * n;
+  const float h2 = (float)(G.h * G.h), ih2 = 1.0f / h2;
+  const float* xr = xi + rep * n;
   for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < n;
        g += (long)gridDim.x * blockDim.x) {
-    const double bv = b[rep * n + g];
+    const long e = rep * n + g;
+    float bv;
+    if (b64) {
+      bv = (float)b64[e];
+      bf[e] = bv;
+    } else {
+      bv = bf[e];
+    }
+    float v;
     if (first) {
-      xo[rep * n + g] = kJacobiW * h2 / 6.0 * bv;
+      v = kJacobiW * h2 / 6.0f * bv;
     } else {
       const int ix = (int)(g % G.nx), iy = (int)((g / G.nx) % G.ny), iz = (int)(g / ((long)G.nx * G.ny));
-      double c;
-      const double ax = lap7(xr, ix, iy, iz, G.nx, G.ny, G.nz, &c) * ih2;
-      xo[rep * n + g] = c + kJacobiW * h2 / 6.0 * (bv - ax);
+      float c;
+      const float ax = lap7f(xr, ix, iy, iz, G.nx, G.ny, G.nz, &c) * ih2;
+      v = c + kJacobiW * h2 / 6.0f * (bv - ax);
     }
+    if (out64)
+      out64[e] = (double)v;
+    else
+      xo[e] = v;
   }
 }
 
-__global__ void k_mg_residual(Grid3 G, const double* __restrict__ x, const double* __restrict__ b,
-                              double* __restrict__ r, const PcgState* __restrict__ st) {
+__global__ void k_mg_residual(Grid3 G, const float* __restrict__ x, const float* __restrict__ b,
+                              float* __restrict__ r, const PcgState* __restrict__ st) {
   const int rep = blockIdx.y;
   if (pcg_skip(st, rep)) return;
   const long n = (long)G.nx * G.ny * G.nz;
-  const double ih2 = 1.0 / (G.h * G.h);
-  const double* xr = x + rep * n;
+  const float ih2 = (float)(1.0 / (G.h * G.h));
+  const float* xr = x + rep * n;
   for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < n;
        g += (long)gridDim.x * blockDim.x) {
     const int ix = (int)(g % G.nx), iy = (int)((g / G.nx) % G.ny), iz = (int)(g / ((long)G.nx * G.ny));
-    double c;
-    r[rep * n + g] = b[rep * n + g] - lap7(xr, ix, iy, iz, G.nx, G.ny, G.nz, &c) * ih2;
+    float c;
+    r[rep * n + g] = b[rep * n + g] - lap7f(xr, ix, iy, iz, G.nx, G.ny, G.nz, &c) * ih2;
   }
 }
 
 // trilinear (cell-centred) weights along one axis: fine child f = 2I + a takes 3/4 from I
 // and 1/4 from I-1 (a = 0) or I+1 (a = 1)
-__device__ __forceinline__ void tri_w(int f, int nc, int* c0, int* c1, double* w0, double* w1) {
+__device__ __forceinline__ void tri_w(int f, int nc, int* c0, int* c1, float* w0, float* w1) {
   const int I = f >> 1;
   *c0 = I;
-  *w0 = 0.75;
+  *w0 = 0.75f;
   const int nb = (f & 1) ? I + 1 : I - 1;
   if (nb >= 0 && nb < nc) {
     *c1 = nb;
-    *w1 = 0.25;
+    *w1 = 0.25f;
   } else {
     *c1 = I;
-    *w1 = 0.0;
+    *w1 = 0.0f;
   }
 }
 
-// coarse b = (1/8) P^T r
-__global__ void k_mg_restrict(Grid3 F, Grid3 C, const double* __restrict__ rf,
-                              double* __restrict__ bc, const PcgState* __restrict__ st) {
+__device__ __forceinline__ float restrict_point(const float* __restrict__ r, int I, int J, int K,
+                                                int nx, int ny, int nz) {
+  float s = 0.0f;
+  for (int dz = -1; dz <= 2; ++dz) {
+    const int fz = 2 * K + dz;
+    if (fz < 0 || fz >= nz) continue;
+    const float wz = (dz == 0 || dz == 1) ? 0.75f : 0.25f;
+    for (int dy = -1; dy <= 2; ++dy) {
+      const int fy = 2 * J + dy;
+      if (fy < 0 || fy >= ny) continue;
+      const float wy = (dy == 0 || dy == 1) ? 0.75f : 0.25f;
+      for (int dx = -1; dx <= 2; ++dx) {
+        const int fx = 2 * I + dx;
+        if (fx < 0 || fx >= nx) continue;
+        const float wx = (dx == 0 || dx == 1) ? 0.75f : 0.25f;
+        s += wx * wy * wz * r[((long)fz * ny + fy) * nx + fx];
+      }
+    }
+  }
+  return 0.125f * s;
+}
+
+__device__ __forceinline__ float prolong_point(const float* __restrict__ xc, int fx, int fy, int fz,
+                                               int cx, int cy, int cz) {
+  int x0, x1, y0, y1, z0, z1;
+  float wx0, wx1, wy0, wy1, wz0, wz1;
+  tri_w(fx, cx, &x0, &x1, &wx0, &wx1);
+  tri_w(fy, cy, &y0, &y1, &wy0, &wy1);
+  tri_w(fz, cz, &z0, &z1, &wz0, &wz1);
+  auto at = [&](int i, int j, int k) { return xc[((long)k * cy + j) * cx + i]; };
+  return wz0 * (wy0 * (wx0 * at(x0, y0, z0) + wx1 * at(x1, y0, z0)) +
+                wy1 * (wx0 * at(x0, y1, z0) + wx1 * at(x1, y1, z0))) +
+         wz1 * (wy0 * (wx0 * at(x0, y0, z1) + wx1 * at(x1, y0, z1)) +
+                wy1 * (wx0 * at(x0, y1, z1) + wx1 * at(x1, y1, z1)));
+}
+
+__global__ void k_mg_restrict(Grid3 F, Grid3 C, const float* __restrict__ rf,
+                              float* __restrict__ bc, const PcgState* __restrict__ st) {
   const int rep = blockIdx.y;
   if (pcg_skip(st, rep)) return;
   const long nf = (long)F.nx * F.ny * F.nz, nc = (long)C.nx * C.ny * C.nz;
-  const double* r = rf + rep * nf;
   for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < nc;
        g += (long)gridDim.x * blockDim.x) {
     const int I = (int)(g % C.nx), J = (int)((g / C.nx) % C.ny), K = (int)(g / ((long)C.nx * C.ny));
-    double s = 0.0;
-    for (int dz = -1; dz <= 2; ++dz) {
-      const int fz = 2 * K + dz;
-      if (fz < 0 || fz >= F.nz) continue;
-      const double wz = (dz == 0 || dz == 1) ? 0.75 : 0.25;
-      for (int dy = -1; dy <= 2; ++dy) {
-        const int fy = 2 * J + dy;
-        if (fy < 0 || fy >= F.ny) continue;
-        const double wy = (dy == 0 || dy == 1) ? 0.75 : 0.25;
-        for (int dx = -1; dx <= 2; ++dx) {
-          const int fx = 2 * I + dx;
-          if (fx < 0 || fx >= F.nx) continue;
-          const double wx = (dx == 0 || dx == 1) ? 0.75 : 0.25;
-          s += wx * wy * wz * r[((long)fz * F.ny + fy) * F.nx + fx];
-        }
-      }
-    }
-    bc[rep * nc + g] = 0.125 * s;
+    bc[rep * nc + g] = restrict_point(rf + rep * nf, I, J, K, F.nx, F.ny, F.nz);
   }
 }
 
-// x_fine += P x_coarse
-__global__ void k_mg_prolong(Grid3 F, Grid3 C, const double* __restrict__ xc,
-                             double* __restrict__ xf, const PcgState* __restrict__ st) {
+__global__ void k_mg_prolong(Grid3 F, Grid3 C, const float* __restrict__ xc,
+                             float* __restrict__ xf, const PcgState* __restrict__ st) {
   const int rep = blockIdx.y;
   if (pcg_skip(st, rep)) return;
   const long nf = (long)F.nx * F.ny * F.nz, nc = (long)C.nx * C.ny * C.nz;
-  const double* x = xc + rep * nc;
   for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < nf;
        g += (long)gridDim.x * blockDim.x) {
     const int fx = (int)(g % F.nx), fy = (int)((g / F.nx) % F.ny), fz = (int)(g / ((long)F.nx * F.ny));
-    int x0, x1, y0, y1, z0, z1;
-    double wx0, wx1, wy0, wy1, wz0, wz1;
-    tri_w(fx, C.nx, &x0, &x1, &wx0, &wx1);
-    tri_w(fy, C.ny, &y0, &y1, &wy0, &wy1);
-    tri_w(fz, C.nz, &z0, &z1, &wz0, &wz1);
-    auto at = [&](int i, int j, int k) { return x[((long)k * C.ny + j) * C.nx + i]; };
-    const double v = wz0 * (wy0 * (wx0 * at(x0, y0, z0) + wx1 * at(x1, y0, z0)) +
-                            wy1 * (wx0 * at(x0, y1, z0) + wx1 * at(x1, y1, z0))) +
-                     wz1 * (wy0 * (wx0 * at(x0, y0, z1) + wx1 * at(x1, y0, z1)) +
-                            wy1 * (wx0 * at(x0, y1, z1) + wx1 * at(x1, y1, z1)));
-    xf[rep * nf + g] += v;
+    xf[rep * nf + g] += prolong_point(xc + rep * nc, fx, fy, fz, C.nx, C.ny, C.nz);
   }
 }
 
@@ -439,22 +481,22 @@ __global__ void k_mg_prolong(Grid3 F, Grid3 C, const double* __restrict__ xc,
 struct TailLevels {
   int nl;
   int nx[12], ny[12], nz[12];
-  double h[12];
+  float h[12];
 };
 
-__device__ void tail_jacobi(const TailLevels& L, int l, double* x, double* t, const double* b,
+__device__ void tail_jacobi(const TailLevels& L, int l, float* x, float* t, const float* b,
                             int first) {
   const int nx = L.nx[l], ny = L.ny[l], nz = L.nz[l];
   const long n = (long)nx * ny * nz;
-  const double h2 = L.h[l] * L.h[l];
+  const float h2 = L.h[l] * L.h[l];
   for (long g = threadIdx.x; g < n; g += blockDim.x) {
     if (first) {
-      t[g] = kJacobiW * h2 / 6.0 * b[g];
+      t[g] = kJacobiW * h2 / 6.0f * b[g];
     } else {
       const int ix = (int)(g % nx), iy = (int)((g / nx) % ny), iz = (int)(g / ((long)nx * ny));
-      double c;
-      const double ax = lap7(x, ix, iy, iz, nx, ny, nz, &c) / h2;
-      t[g] = c + kJacobiW * h2 / 6.0 * (b[g] - ax);
+      float c;
+      const float ax = lap7f(x, ix, iy, iz, nx, ny, nz, &c) / h2;
+      t[g] = c + kJacobiW * h2 / 6.0f * (b[g] - ax);
     }
   }
   __syncthreads();
@@ -462,14 +504,14 @@ __device__ void tail_jacobi(const TailLevels& L, int l, double* x, double* t, co
   __syncthreads();
 }
 
-__global__ void k_mg_tail(TailLevels L, const double* __restrict__ b_in, double* __restrict__ x_out,
+__global__ void k_mg_tail(TailLevels L, const float* __restrict__ b_in, float* __restrict__ x_out,
                           const PcgState* __restrict__ st) {
   const int rep = blockIdx.x;
   if (pcg_skip(st, rep)) return;
-  extern __shared__ double sm[];
-  double* xs[12];
-  double* bs[12];
-  double* ts[12];
+  extern __shared__ float sm[];
+  float* xs[12];
+  float* bs[12];
+  float* ts[12];
   long off = 0;
   for (int l = 0; l < L.nl; ++l) {
     const long n = (long)L.nx[l] * L.ny[l] * L.nz[l];
@@ -481,65 +523,35 @@ __global__ void k_mg_tail(TailLevels L, const double* __restrict__ b_in, double*
   const long n0 = (long)L.nx[0] * L.ny[0] * L.nz[0];
   for (long g = threadIdx.x; g < n0; g += blockDim.x) bs[0][g] = b_in[rep * n0 + g];
   __syncthreads();
-  // descend
   for (int l = 0; l < L.nl; ++l) {
     const bool coarsest = (l == L.nl - 1);
     const int sweeps = coarsest ? kCoarseSweeps : kPre;
     for (int s = 0; s < sweeps; ++s) tail_jacobi(L, l, xs[l], ts[l], bs[l], s == 0);
     if (coarsest) break;
-    // residual into ts[l], restrict into bs[l+1]
     const int nx = L.nx[l], ny = L.ny[l], nz = L.nz[l];
     const long n = (long)nx * ny * nz;
-    const double ih2 = 1.0 / (L.h[l] * L.h[l]);
+    const float ih2 = 1.0f / (L.h[l] * L.h[l]);
     for (long g = threadIdx.x; g < n; g += blockDim.x) {
       const int ix = (int)(g % nx), iy = (int)((g / nx) % ny), iz = (int)(g / ((long)nx * ny));
-      double c;
-      ts[l][g] = bs[l][g] - lap7(xs[l], ix, iy, iz, nx, ny, nz, &c) * ih2;
+      float c;
+      ts[l][g] = bs[l][g] - lap7f(xs[l], ix, iy, iz, nx, ny, nz, &c) * ih2;
     }
     __syncthreads();
     const int cx = L.nx[l + 1], cy = L.ny[l + 1], cz = L.nz[l + 1];
     const long nc = (long)cx * cy * cz;
     for (long g = threadIdx.x; g < nc; g += blockDim.x) {
       const int I = (int)(g % cx), J = (int)((g / cx) % cy), K = (int)(g / ((long)cx * cy));
-      double s = 0.0;
-      for (int dz = -1; dz <= 2; ++dz) {
-        const int fz = 2 * K + dz;
-        if (fz < 0 || fz >= nz) continue;
-        const double wz = (dz == 0 || dz == 1) ? 0.75 : 0.25;
-        for (int dy = -1; dy <= 2; ++dy) {
-          const int fy = 2 * J + dy;
-          if (fy < 0 || fy >= ny) continue;
-          const double wy = (dy == 0 || dy == 1) ? 0.75 : 0.25;
-          for (int dx = -1; dx <= 2; ++dx) {
-            const int fx = 2 * I + dx;
-            if (fx < 0 || fx >= nx) continue;
-            const double wx = (dx == 0 || dx == 1) ? 0.75 : 0.25;
-            s += wx * wy * wz * ts[l][((long)fz * ny + fy) * nx + fx];
-          }
-        }
-      }
-      bs[l + 1][g] = 0.125 * s;
+      bs[l + 1][g] = restrict_point(ts[l], I, J, K, nx, ny, nz);
     }
     __syncthreads();
   }
-  // ascend
   for (int l = L.nl - 2; l >= 0; --l) {
     const int nx = L.nx[l], ny = L.ny[l], nz = L.nz[l];
     const int cx = L.nx[l + 1], cy = L.ny[l + 1], cz = L.nz[l + 1];
     const long n = (long)nx * ny * nz;
-    const double* xc = xs[l + 1];
     for (long g = threadIdx.x; g < n; g += blockDim.x) {
       const int fx = (int)(g % nx), fy = (int)((g / nx) % ny), fz = (int)(g / ((long)nx * ny));
-      int x0, x1, y0, y1, z0, z1;
-      double wx0, wx1, wy0, wy1, wz0, wz1;
-      tri_w(fx, cx, &x0, &x1, &wx0, &wx1);
-      tri_w(fy, cy, &y0, &y1, &wy0, &wy1);
-      tri_w(fz, cz, &z0, &z1, &wz0, &wz1);
-      auto at = [&](int i, int j, int k) { return xc[((long)k * cy + j) * cx + i]; };
-      xs[l][g] += wz0 * (wy0 * (wx0 * at(x0, y0, z0) + wx1 * at(x1, y0, z0)) +
-                         wy1 * (wx0 * at(x0, y1, z0) + wx1 * at(x1, y1, z0))) +
-                  wz1 * (wy0 * (wx0 * at(x0, y0, z1) + wx1 * at(x1, y0, z1)) +
-                         wy1 * (wx0 * at(x0, y1, z1) + wx1 * at(x1, y1, z1)));
+      xs[l][g] += prolong_point(xs[l + 1], fx, fy, fz, cx, cy, cz);
     }
     __syncthreads();
     for (int s = 0; s < kPost; ++s) tail_jacobi(L, l, xs[l], ts[l], bs[l], 0);
@@ -554,38 +566,35 @@ static int grid_blocks(rmgtd_ctx* ctx, long n) {
   return (int)std::max<long>(1, std::min<long>(ceil_div(n, kThreads), ctx->red_blocks));
 }
 
-// z = M r on level 0 (M = one V-cycle); level arrays: mg[l].x / .b / .r
-static int vcycle(rmgtd_ctx* ctx, const double* r0, double* z0, int nrep) {
+// z (float64) = M r (float64), M = one float32 V-cycle
+static int vcycle(rmgtd_ctx* ctx, const double* r64, double* z64, int nrep) {
   const PcgState* st = ctx->pcg;
   const int nl = (int)ctx->mg.size();
   const int tail = ctx->mg_tail_level;  // first tail level (>= 1) or -1
   const int nmulti = (tail >= 0) ? tail : nl;
-  // descend on multi-block levels
+  cudaStream_t s = ctx->stream;
   for (int l = 0; l < nmulti; ++l) {
     MgLevel& L = ctx->mg[l];
     const Grid3 G = grid_of(L);
-    const double* b = (l == 0) ? r0 : L.b;
-    double* x = (l == 0) ? z0 : L.x;
     const int bl = grid_blocks(ctx, L.n);
     const bool coarsest = (l == nl - 1);
     const int sweeps = coarsest ? kCoarseSweeps : kPre;
-    // ping-pong between x and r for the sweeps, ending in x
-    double* bufs[2] = {x, L.r};
-    int cur = (sweeps % 2 == 1) ? 0 : 1;  // so that the last sweep writes x
-    for (int s = 0; s < sweeps; ++s) {
-      double* out = bufs[cur];
-      const double* in = bufs[cur ^ 1];
-      k_mg_jacobi<<<dim3(bl, nrep), kThreads, 0, ctx->stream>>>(G, in, out, b, s == 0, st);
+    float* bufs[2] = {L.x, L.t};
+    int cur = (sweeps % 2 == 1) ? 0 : 1;  // the last sweep writes x
+    for (int sw = 0; sw < sweeps; ++sw) {
+      const bool last_out64 = (coarsest && l == 0 && sw == sweeps - 1);
+      k_mg_jacobi<<<dim3(bl, nrep), kThreads, 0, s>>>(
+          G, bufs[cur ^ 1], bufs[cur], L.b, (l == 0 && sw == 0) ? r64 : nullptr, sw == 0,
+          last_out64 ? z64 : nullptr, st);
       ++ctx->launches;
       cur ^= 1;
     }
     RMGTD_LAUNCH(ctx, "k_mg_jacobi");
     if (coarsest) break;
-    k_mg_residual<<<dim3(bl, nrep), kThreads, 0, ctx->stream>>>(G, x, b, L.r, st);
+    k_mg_residual<<<dim3(bl, nrep), kThreads, 0, s>>>(G, L.x, L.b, L.t, st);
     ++ctx->launches;
     MgLevel& C = ctx->mg[l + 1];
-    k_mg_restrict<<<dim3(grid_blocks(ctx, C.n), nrep), kThreads, 0, ctx->stream>>>(
-        G, grid_of(C), L.r, C.b, st);
+    k_mg_restrict<<<dim3(grid_blocks(ctx, C.n), nrep), kThreads, 0, s>>>(G, grid_of(C), L.t, C.b, st);
     ++ctx->launches;
     RMGTD_LAUNCH(ctx, "k_mg_restrict");
   }
@@ -596,29 +605,25 @@ static int vcycle(rmgtd_ctx* ctx, const double* r0, double* z0, int nrep) {
       T.nx[l - tail] = ctx->mg[l].nx;
       T.ny[l - tail] = ctx->mg[l].ny;
       T.nz[l - tail] = ctx->mg[l].nz;
-      T.h[l - tail] = ctx->mg[l].h;
+      T.h[l - tail] = (float)ctx->mg[l].h;
     }
-    k_mg_tail<<<nrep, 1024, ctx->mg_tail_smem, ctx->stream>>>(T, ctx->mg[tail].b,
-                                                               ctx->mg[tail].x, st);
+    k_mg_tail<<<nrep, 1024, ctx->mg_tail_smem, s>>>(T, ctx->mg[tail].b, ctx->mg[tail].x, st);
     ++ctx->launches;
     RMGTD_LAUNCH(ctx, "k_mg_tail");
   }
-  // ascend on multi-block levels
   for (int l = std::min(nmulti, nl - 1) - 1; l >= 0; --l) {
     MgLevel& L = ctx->mg[l];
     MgLevel& C = ctx->mg[l + 1];
     const Grid3 G = grid_of(L);
-    const double* b = (l == 0) ? r0 : L.b;
-    double* x = (l == 0) ? z0 : L.x;
     const int bl = grid_blocks(ctx, L.n);
-    k_mg_prolong<<<dim3(bl, nrep), kThreads, 0, ctx->stream>>>(G, grid_of(C), C.x, x, st);
+    k_mg_prolong<<<dim3(bl, nrep), kThreads, 0, s>>>(G, grid_of(C), C.x, L.x, st);
     ++ctx->launches;
-    double* bufs[2] = {x, L.r};
+    float* bufs[2] = {L.x, L.t};
     int cur = 1;
-    for (int s = 0; s < kPost; ++s) {
-      double* out = bufs[cur];
-      const double* in = bufs[cur ^ 1];
-      k_mg_jacobi<<<dim3(bl, nrep), kThreads, 0, ctx->stream>>>(G, in, out, b, 0, st);
+    for (int sw = 0; sw < kPost; ++sw) {
+      const bool out64 = (l == 0 && sw == kPost - 1);
+      k_mg_jacobi<<<dim3(bl, nrep), kThreads, 0, s>>>(G, bufs[cur ^ 1], bufs[cur], L.b, nullptr,
+                                                      0, out64 ? z64 : nullptr, st);
       ++ctx->launches;
       cur ^= 1;
     }
@@ -638,7 +643,7 @@ int setup_multigrid(rmgtd_ctx* ctx) {
     L.nz = nz;
     L.n = (long)nx * ny * nz;
     L.h = h;
-    L.x = L.b = L.r = nullptr;
+    L.x = L.b = L.t = nullptr;
     ctx->mg.push_back(L);
     if (ctx->mg.size() >= 12) break;
     if ((nx & 1) || (ny & 1) || (nz & 1) || nx < 4 || ny < 4 || nz < 4) break;
@@ -656,7 +661,7 @@ int setup_multigrid(rmgtd_ctx* ctx) {
     }
   size_t smem = 0;
   if (ctx->mg_tail_level >= 0)
-    for (int l = ctx->mg_tail_level; l < nl; ++l) smem += 3 * sizeof(double) * ctx->mg[l].n;
+    for (int l = ctx->mg_tail_level; l < nl; ++l) smem += 3 * sizeof(float) * ctx->mg[l].n;
   ctx->mg_tail_smem = smem;
   if (smem > 48 * 1024) {
     RMGTD_CUDA(ctx, cudaFuncSetAttribute(k_mg_tail, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -664,77 +669,93 @@ int setup_multigrid(rmgtd_ctx* ctx) {
   }
   for (int l = 0; l < nl; ++l) {
     MgLevel& L = ctx->mg[l];
-    const size_t bytes = sizeof(double) * (size_t)ctx->nrep * L.n;
-    if (l > 0) {
-      L.x = (double*)dev_alloc(ctx, bytes);
-      L.b = (double*)dev_alloc(ctx, bytes);
-    }
-    L.r = (double*)dev_alloc(ctx, bytes);
-    if ((l > 0 && (!L.x || !L.b)) || !L.r) return set_error(ctx, RMGTD_ENOMEM, "multigrid levels");
+    const size_t bytes = sizeof(float) * (size_t)ctx->nrep * L.n;
+    L.x = (float*)dev_alloc(ctx, bytes);
+    L.b = (float*)dev_alloc(ctx, bytes);
+    L.t = (float*)dev_alloc(ctx, bytes);
+    if (!L.x || !L.b || !L.t) return set_error(ctx, RMGTD_ENOMEM, "multigrid levels");
   }
+  ctx->ghost = (double*)dev_alloc(ctx, sizeof(double) * 4 * (size_t)ctx->Ng);
+  if (!ctx->ghost) return set_error(ctx, RMGTD_ENOMEM, "ghost fields");
+  const Grid3 G{ctx->nx, ctx->ny, ctx->nz, ctx->h};
+  k_ghost_fields<<<grid_blocks(ctx, ctx->Ng), kThreads, 0, ctx->stream>>>(G, ctx->ghost);
+  ++ctx->launches;
+  RMGTD_LAUNCH(ctx, "k_ghost_fields");
   return RMGTD_OK;
 }
 
-// Hartree solve for every active replica: vh (initial guess in, solution out).
-int hartree_dev(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* ctl, int zero_bc,
-                int nrep) {
-  const MgLevel& F = ctx->mg[0];
-  const Grid3 G = grid_of(F);
+// Start of a Hartree solve: moments, right-hand side, initial residual, first V-cycle.
+int hartree_begin(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* ctl, int zero_bc,
+                  int nrep) {
+  const Grid3 G{ctx->nx, ctx->ny, ctx->nz, ctx->h};
   const long Ng = ctx->Ng;
   const int nb = ctx->red_blocks;
   const dim3 grid(nb, nrep);
+  cudaStream_t s = ctx->stream;
   double* part = ctx->red_part;
-  k_moments<<<grid, kThreads, 0, ctx->stream>>>(G, rho, part, ctl);
+  k_moments<<<grid, kThreads, 0, s>>>(G, rho, part, ctl);
   ++ctx->launches;
-  RMGTD_LAUNCH(ctx, "k_moments");
-  k_hartree_rhs<<<grid, kThreads, 0, ctx->stream>>>(G, rho, part, nb, ctx->pcg_b, zero_bc, ctl);
+  k_pcg_init<<<grid, kThreads, 0, s>>>(G, rho, ctx->ghost, vh, ctx->pcg_b, ctx->pcg_r, part,
+                                       zero_bc, ctl);
   ++ctx->launches;
-  RMGTD_LAUNCH(ctx, "k_hartree_rhs");
-  // separate partial area for the CG scalars (moments are consumed above)
-  double* cg = part;
-  k_pcg_init<<<grid, kThreads, 0, ctx->stream>>>(G, vh, ctx->pcg_b, ctx->pcg_r, cg, ctl);
+  k_pcg_state_init<<<1, 32 * nrep, 0, s>>>(ctx->pcg, part, nb, ctx->opt.poisson_tol, ctl, nrep);
   ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_pcg_init");
-  k_pcg_state_init<<<1, 32 * nrep, 0, ctx->stream>>>(ctx->pcg, cg, nb, ctx->opt.poisson_tol, ctl,
-                                                     nrep);
-  ++ctx->launches;
-  RMGTD_LAUNCH(ctx, "k_pcg_state_init");
   int rc = vcycle(ctx, ctx->pcg_r, ctx->pcg_z, nrep);
   if (rc) return rc;
-  k_pcg_rz<<<grid, kThreads, 0, ctx->stream>>>(Ng, ctx->pcg_r, ctx->pcg_z, ctx->pcg_p, 1, cg,
-                                               ctx->pcg);
+  k_pcg_rz<<<grid, kThreads, 0, s>>>(Ng, ctx->pcg_r, ctx->pcg_z, ctx->pcg_p, 1, part, ctx->pcg);
   ++ctx->launches;
-  k_pcg_rz_store<<<1, 32 * nrep, 0, ctx->stream>>>(ctx->pcg, cg, nb, nrep);
+  k_pcg_rz_store<<<1, 32 * nrep, 0, s>>>(ctx->pcg, part, nb, nrep);
   ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_pcg_rz");
+  return RMGTD_OK;
+}
+
+// One flexible-CG iteration for every replica still iterating; `cond` is the graph
+// while-handle to update (use_cond = 0 outside a graph).
+int hartree_iteration(rmgtd_ctx* ctx, double* vh, int nrep, cudaGraphConditionalHandle cond,
+                      int use_cond) {
+  const Grid3 G{ctx->nx, ctx->ny, ctx->nz, ctx->h};
+  const long Ng = ctx->Ng;
+  const int nb = ctx->red_blocks;
+  const dim3 grid(nb, nrep);
+  cudaStream_t s = ctx->stream;
+  double* part = ctx->red_part;
+  k_pcg_Ap<<<grid, kThreads, 0, s>>>(G, ctx->pcg_p, ctx->pcg_Ap, part, ctx->pcg);
+  ++ctx->launches;
+  k_pcg_xr<<<grid, kThreads, 0, s>>>(Ng, vh, ctx->pcg_r, ctx->pcg_p, ctx->pcg_Ap, ctx->pcg_z, part,
+                                     ctx->pcg);
+  ++ctx->launches;
+  k_pcg_check<<<1, 32 * nrep, 0, s>>>(ctx->pcg, part, nb, ctx->opt.poisson_tol,
+                                      ctx->opt.poisson_max_iter, nrep, ctx->status);
+  ++ctx->launches;
+  RMGTD_LAUNCH(ctx, "k_pcg_iteration");
+  int rc = vcycle(ctx, ctx->pcg_r, ctx->pcg_z, nrep);
+  if (rc) return rc;
+  k_pcg_rz<<<grid, kThreads, 0, s>>>(Ng, ctx->pcg_r, ctx->pcg_z, ctx->pcg_p, 0, part, ctx->pcg);
+  ++ctx->launches;
+  k_pcg_p<<<grid, kThreads, 0, s>>>(Ng, ctx->pcg_z, ctx->pcg_p, part, ctx->pcg);
+  ++ctx->launches;
+  k_pcg_end<<<1, 32 * nrep, 0, s>>>(ctx->pcg, part, nb, nrep, ctx->pcg_any, cond, use_cond,
+                                     ctx->kexec);
+  ++ctx->launches;
+  RMGTD_LAUNCH(ctx, "k_pcg_end");
+  return RMGTD_OK;
+}
+
+// Eager Hartree solve (host-driven loop, peeking at the convergence flag).
+int hartree_dev(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* ctl, int zero_bc,
+                int nrep) {
+  int rc = hartree_begin(ctx, rho, vh, ctl, zero_bc, nrep);
+  if (rc) return rc;
   for (int it = 0; it < ctx->opt.poisson_max_iter; ++it) {
-    k_pcg_Ap<<<grid, kThreads, 0, ctx->stream>>>(G, ctx->pcg_p, ctx->pcg_Ap, cg, ctx->pcg);
-    ++ctx->launches;
-    k_pcg_xr<<<grid, kThreads, 0, ctx->stream>>>(Ng, vh, ctx->pcg_r, ctx->pcg_p, ctx->pcg_Ap, cg,
-                                                 ctx->pcg);
-    ++ctx->launches;
-    k_pcg_check<<<1, 32 * nrep, 0, ctx->stream>>>(ctx->pcg, cg, nb, ctx->opt.poisson_tol,
-                                                  ctx->opt.poisson_max_iter, nrep, ctx->status);
-    ++ctx->launches;
-    RMGTD_LAUNCH(ctx, "k_pcg_iteration");
-    rc = vcycle(ctx, ctx->pcg_r, ctx->pcg_z, nrep);
+    rc = hartree_iteration(ctx, vh, nrep, 0, 0);
     if (rc) return rc;
-    k_pcg_rz<<<grid, kThreads, 0, ctx->stream>>>(Ng, ctx->pcg_r, ctx->pcg_z, ctx->pcg_p, 0, cg,
-                                                 ctx->pcg);
-    ++ctx->launches;
-    k_pcg_p<<<grid, kThreads, 0, ctx->stream>>>(Ng, ctx->pcg_z, ctx->pcg_p, cg, ctx->pcg);
-    ++ctx->launches;
-    k_pcg_end<<<1, 32 * nrep, 0, ctx->stream>>>(ctx->pcg, cg, nb, nrep, ctx->pcg_any);
-    ++ctx->launches;
-    RMGTD_LAUNCH(ctx, "k_pcg_end");
-    // eager mode: peek at the convergence flag every few iterations to stop launching
     if ((it & 3) == 3) {
-      int any = 1;
       RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->pcg_any_host, ctx->pcg_any, sizeof(int),
                                       cudaMemcpyDeviceToHost, ctx->stream));
       RMGTD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-      any = *ctx->pcg_any_host;
-      if (!any) break;
+      if (!*ctx->pcg_any_host) break;
     }
   }
   return RMGTD_OK;

@@ -501,44 +501,94 @@ int eldyn(rmgtd_ctx* ctx, const double* Ha, const double* Hb, long hstride, doub
 // ---------------------------------------------------------------------------------------
 // Step bookkeeping.
 // H_1 <- 2 H_0 - H_-1 (Algorithm 1 line 11) for every replica; reset the control blocks.
+// After a failed step of the same rmgtd_step call (sticky `failed`), every replica is
+// left inactive so the remaining steps do nothing.
 __global__ void k_step_begin(long n, const double* __restrict__ H0, const double* __restrict__ Hm1,
-                             double* __restrict__ H1, RepCtl* ctl, int nrep) {
-  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n;
-       e += (long)gridDim.x * blockDim.x)
-    H1[e] = 2.0 * H0[e] - Hm1[e];
+                             double* __restrict__ H1, RepCtl* ctl, int nrep,
+                             const int* __restrict__ failed, int* status) {
+  const int f = *failed;
+  if (!f) {
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n;
+         e += (long)gridDim.x * blockDim.x)
+      H1[e] = 2.0 * H0[e] - Hm1[e];
+  }
   if (blockIdx.x == 0 && threadIdx.x < nrep) {
     RepCtl& c = ctl[threadIdx.x];
-    c.active = 1;
+    c.active = f ? 0 : 1;
     c.passes = 0;
     c.terms_last = c.terms_max = c.terms_sum = 0;
     c.status = 0;
     c.H_err = 0.0;
   }
+  if (!f && blockIdx.x == 0 && threadIdx.x == 0) *status = 0;
 }
 
 // After one DFT evaluation: H_err = max|H_new - H_1| (already in errbits), decide per
-// replica whether the SCF loop continues.
+// replica whether the SCF loop continues; inside a graph, set the loop's while flag.
 __global__ void k_scf_control(RepCtl* ctl, int nrep, const unsigned long long* errbits,
-                              double H_thrs, int max_scf, int* status) {
+                              double H_thrs, int max_scf, int* status,
+                              cudaGraphConditionalHandle cond, int use_cond,
+                              unsigned long long* kexec) {
   const int r = threadIdx.x;
-  if (r >= nrep) return;
-  RepCtl& c = ctl[r];
-  if (!c.active) return;
-  c.passes += 1;
-  const double err = __longlong_as_double((long long)errbits[r]);
-  c.H_err = err;
-  if (c.status != 0) {
-    c.active = 0;
-  } else if (!(err <= 1e300)) {
-    c.status = RMGTD_EDIVERGED;
-    c.active = 0;
-    atomicCAS(status, 0, (int)RMGTD_EDIVERGED);
-  } else if (err <= H_thrs) {
-    c.active = 0;
-  } else if (c.passes >= max_scf) {
-    c.status = RMGTD_ENOTCONVERGED;
-    c.active = 0;
-    atomicCAS(status, 0, (int)RMGTD_ENOTCONVERGED);
+  if (r < nrep) {
+    RepCtl& c = ctl[r];
+    if (c.active) {
+      c.passes += 1;
+      const double err = __longlong_as_double((long long)errbits[r]);
+      c.H_err = err;
+      if (c.status != 0) {
+        c.active = 0;
+      } else if (!(err <= 1e300)) {
+        c.status = RMGTD_EDIVERGED;
+        c.active = 0;
+        atomicCAS(status, 0, (int)RMGTD_EDIVERGED);
+      } else if (err <= H_thrs) {
+        c.active = 0;
+      } else if (c.passes >= max_scf) {
+        c.status = RMGTD_ENOTCONVERGED;
+        c.active = 0;
+        atomicCAS(status, 0, (int)RMGTD_ENOTCONVERGED);
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && use_cond) {
+    int a = 0;
+    for (int q = 0; q < nrep; ++q) a |= ctl[q].active;
+    cudaGraphSetConditional(cond, a ? 1u : 0u);
+    atomicAdd(&kexec[0], 1ull);
+  }
+}
+
+// End of a step: if every replica succeeded, H_-1 <- H_0, H_0 <- H_1, P_0 <- P_1
+// (Algorithm 1 line 28) and count the step; otherwise raise the sticky failure flag.
+// Block 0 appends the control blocks to the per-call statistics.
+__global__ void k_step_end(long n, double* __restrict__ Hm1, double* __restrict__ H0,
+                           const double* __restrict__ H1, double* __restrict__ S0,
+                           double* __restrict__ A0, const double* __restrict__ S1,
+                           const double* __restrict__ A1, const RepCtl* __restrict__ ctl, int nrep,
+                           int* failed, int* done_steps, RepCtl* stats, int stats_cap,
+                           const int* __restrict__ status) {
+  if (*failed) return;
+  int ok = (*status == 0);
+  for (int r = 0; r < nrep; ++r) ok &= (ctl[r].status == 0);
+  if (ok) {
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n;
+         e += (long)gridDim.x * blockDim.x) {
+      Hm1[e] = H0[e];
+      H0[e] = H1[e];
+      S0[e] = S1[e];
+      A0[e] = A1[e];
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const int k = *done_steps;
+    if (k < stats_cap)
+      for (int r = 0; r < nrep; ++r) stats[(long)k * nrep + r] = ctl[r];
+    if (ok)
+      *done_steps = k + 1;
+    else
+      *failed = 1;
   }
 }
 
@@ -546,17 +596,31 @@ int step_begin(rmgtd_ctx* ctx) {
   const long n = (long)ctx->nrep * ctx->N * ctx->N;
   const int blocks = (int)std::min<long>(ceil_div(n, 256), 2L * ctx->num_sms);
   k_step_begin<<<std::max(blocks, 1), 256, 0, ctx->stream>>>(n, ctx->H0, ctx->Hm1, ctx->H1,
-                                                              ctx->ctl, ctx->nrep);
+                                                              ctx->ctl, ctx->nrep, ctx->failed,
+                                                              ctx->status);
   ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_step_begin");
   return RMGTD_OK;
 }
 
-int scf_control(rmgtd_ctx* ctx, const unsigned long long* errbits) {
+int scf_control(rmgtd_ctx* ctx, const unsigned long long* errbits,
+                cudaGraphConditionalHandle cond, int use_cond) {
   k_scf_control<<<1, 32, 0, ctx->stream>>>(ctx->ctl, ctx->nrep, errbits, ctx->opt.H_thrs,
-                                           ctx->opt.max_scf, ctx->status);
+                                           ctx->opt.max_scf, ctx->status, cond, use_cond,
+                                           ctx->kexec);
   ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_scf_control");
+  return RMGTD_OK;
+}
+
+int step_end(rmgtd_ctx* ctx) {
+  const long n = (long)ctx->nrep * ctx->N * ctx->N;
+  const int blocks = (int)std::min<long>(ceil_div(n, 256), 2L * ctx->num_sms);
+  k_step_end<<<std::max(blocks, 1), 256, 0, ctx->stream>>>(
+      n, ctx->Hm1, ctx->H0, ctx->H1, ctx->S0, ctx->A0, ctx->S1, ctx->A1, ctx->ctl, ctx->nrep,
+      ctx->failed, ctx->done_steps, ctx->stats_dev, ctx->stats_cap, ctx->status);
+  ++ctx->launches;
+  RMGTD_LAUNCH(ctx, "k_step_end");
   return RMGTD_OK;
 }
 

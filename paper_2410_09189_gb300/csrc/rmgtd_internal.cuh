@@ -55,9 +55,9 @@ struct MgLevel {
   int nx, ny, nz;
   long n;
   double h;
-  double* x;   // [nrep][n]
-  double* b;   // [nrep][n]
-  double* r;   // [nrep][n]
+  float* x;   // [nrep][n] iterate
+  float* b;   // [nrep][n] right-hand side
+  float* t;   // [nrep][n] sweep / residual scratch
 };
 
 struct Buffer {
@@ -135,7 +135,7 @@ struct rmgtd_ctx {
   rmgtd::PcgState* pcg = nullptr;   // [nrep]
   int* pcg_any = nullptr;           // device flag: some replica still iterating
   int* pcg_any_host = nullptr;      // pinned
-  double* mpole = nullptr;          // [nrep][4] Q, px, py, pz
+  double* ghost = nullptr;          // [4][Ng] ghost response fields G0, Gx, Gy, Gz
   std::vector<rmgtd::MgLevel> mg;   // multi-CTA levels (level 0 = fine grid)
   int mg_tail_level = -1;           // first level solved inside one CTA
   size_t mg_tail_smem = 0;
@@ -162,6 +162,18 @@ struct rmgtd_ctx {
   // CUDA graph of one time step
   cudaGraphExec_t step_exec = nullptr;
   cudaGraph_t step_graph = nullptr;
+  cudaStream_t aux[2] = {nullptr, nullptr};
+  int capturing = 0;
+  int* failed = nullptr;            // sticky: a step of the current rmgtd_step call failed
+  int* done_steps = nullptr;        // steps completed in the current rmgtd_step call
+  rmgtd::RepCtl* stats_dev = nullptr;  // [stats_cap][nrep]
+  rmgtd::RepCtl* stats_host = nullptr; // pinned mirror
+  int stats_cap = 0;
+  // kernel counts of the captured step: top level, SCF-pass body, Hartree-iteration body;
+  // executions of the bodies are counted on the device (kexec[0], kexec[1])
+  int cap_top = 0, cap_scf = 0, cap_pcg = 0;
+  long long graph_steps = 0;
+  unsigned long long* kexec = nullptr;
 
   std::vector<rmgtd::Buffer> buffers;
 };
@@ -292,12 +304,20 @@ int eldyn(rmgtd_ctx* ctx, const double* Ha, const double* Hb, long hstride, doub
           const double* S0, const double* A0, double* S1, double* A1, const RepCtl* ctl_in,
           RepCtl* ctl_out, int rep0, int nreps);
 int step_begin(rmgtd_ctx* ctx);
-int scf_control(rmgtd_ctx* ctx, const unsigned long long* errbits);
+int scf_control(rmgtd_ctx* ctx, const unsigned long long* errbits,
+                cudaGraphConditionalHandle cond, int use_cond);
+// launches counted while the SCF body was captured, minus the Hartree-iteration body
+int step_end(rmgtd_ctx* ctx);
 int observables(rmgtd_ctx* ctx);
 int orthonormalize(rmgtd_ctx* ctx);
 // k_poisson.cu
 int setup_multigrid(rmgtd_ctx* ctx);
 int hartree_dev(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* ctl, int zero_bc,
                 int nrep);
+int hartree_graph(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* ctl, int nrep);
+int hartree_begin(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* ctl, int zero_bc,
+                  int nrep);
+int hartree_iteration(rmgtd_ctx* ctx, double* vh, int nrep, cudaGraphConditionalHandle cond,
+                      int use_cond);
 
 }  // namespace rmgtd

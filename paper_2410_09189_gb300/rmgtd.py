@@ -123,7 +123,7 @@ class Context:
                  H_thrs: float = 1e-7, dP_thrs: float = 1e-10, max_scf: int = 50,
                  max_terms: int = 200, precision: int = PREC_FP64, nrep: int = 1,
                  orthonormalize: bool = True, poisson_tol: float = 1e-12,
-                 poisson_max_iter: int = 200, use_graph: bool = False,
+                 poisson_max_iter: int = 200, use_graph: bool = True,
                  stream: Optional[int] = None, torch_alloc: bool = True):
         import torch
 

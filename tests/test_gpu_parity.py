@@ -262,3 +262,38 @@ def test_full_size_ring_workload(torch_dev):
         H, _ = pr.dft(P[a])
         assert np.max(np.abs(H - H0[a])) < 1e-8
         assert abs(e1[a] - e0[a]) < 1e-4
+
+
+def test_graph_step_matches_eager_bitwise(torch_dev):
+    """The captured step (device-side SCF and Hartree while loops) runs the same kernels in
+    the same order as the host-driven step: identical results."""
+    rmgtd = _rmgtd()
+    s = _ring_small(n=(30, 34, 38), h=0.5, nvirt=22)
+    raw = inputs.smooth_random_orbitals(s).reshape(s.N, s.Ng)
+    out = {}
+    for mode in (False, True):
+        with rmgtd.Context(s, raw, dt=0.02, nrep=3, use_graph=mode, H_thrs=1e-9) as ctx:
+            for a in range(3):
+                ctx.kick(a, a, 1e-2)
+            st = ctx.step(4)
+            out[mode] = ([ctx.density_matrix(a) for a in range(3)], st, ctx.time())
+    for a in range(3):
+        assert np.array_equal(out[False][0][a], out[True][0][a])
+    assert np.array_equal(out[False][1]["passes"], out[True][1]["passes"])
+    assert out[False][2] == out[True][2]
+
+
+def test_graph_step_failure_keeps_last_completed_state(torch_dev, small_gs):
+    rmgtd = _rmgtd()
+    s, gs = small_gs
+    with rmgtd.Context(s, gs["phi"], H_thrs=1e-9, orthonormalize=False, use_graph=True) as ctx:
+        ctx.kick(0, 2, 0.01)
+        ctx.step(2)
+        P2 = ctx.density_matrix(0)
+    with rmgtd.Context(s, gs["phi"], H_thrs=1e-9, orthonormalize=False, use_graph=True,
+                       max_scf=1) as ctx:
+        ctx.kick(0, 2, 0.01)
+        with pytest.raises(rmgtd.RmgtdError) as ei:
+            ctx.step(3)
+        assert ei.value.code == rmgtd.ENOTCONVERGED
+        assert ctx.time() == (0.0, 0)
