@@ -154,17 +154,34 @@ __global__ void k_ion_energy(int natoms, const double* __restrict__ pos, const d
 // Add a while-loop node at the current capture position of ctx->stream; returns its body
 // graph and handle.  The handle starts each launch of the node at 1 (the body runs at least
 // once) and the body's last kernel sets it.
-static int add_while(rmgtd_ctx* ctx, cudaGraphConditionalHandle* h, cudaGraph_t* body) {
+// Handle for a while loop that will be added to the graph being captured on ctx->stream.
+// The top-level loop uses default value 1 (reset at every launch of the step graph); a
+// nested loop gets no default and is armed by a kernel just before it.
+static int new_handle(rmgtd_ctx* ctx, cudaGraphConditionalHandle* h, bool with_default) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g;
+  RMGTD_CUDA(ctx, cudaStreamGetCaptureInfo(ctx->stream, &cs, nullptr, &g, nullptr, nullptr, nullptr));
+  if (cs != cudaStreamCaptureStatusActive) return set_error(ctx, RMGTD_ECUDA, "stream not capturing");
+  if (with_default) {
+    RMGTD_CUDA(ctx, cudaGraphConditionalHandleCreate(h, g, 1, cudaGraphCondAssignDefault));
+  } else {
+    RMGTD_CUDA(ctx, cudaGraphConditionalHandleCreate(h, g, 0, 0));
+  }
+  return RMGTD_OK;
+}
+
+// Add a while-loop node driven by `h` at the current capture position of ctx->stream and
+// return its body graph.
+static int add_while(rmgtd_ctx* ctx, cudaGraphConditionalHandle h, cudaGraph_t* body) {
   cudaStreamCaptureStatus cs;
   cudaGraph_t g;
   const cudaGraphNode_t* deps = nullptr;
   size_t nd = 0;
   RMGTD_CUDA(ctx, cudaStreamGetCaptureInfo(ctx->stream, &cs, nullptr, &g, &deps, nullptr, &nd));
   if (cs != cudaStreamCaptureStatusActive) return set_error(ctx, RMGTD_ECUDA, "stream not capturing");
-  RMGTD_CUDA(ctx, cudaGraphConditionalHandleCreate(h, g, 1, cudaGraphCondAssignDefault));
   cudaGraphNodeParams p = {};
   p.type = cudaGraphNodeTypeConditional;
-  p.conditional.handle = *h;
+  p.conditional.handle = h;
   p.conditional.type = cudaGraphCondTypeWhile;
   p.conditional.size = 1;
   cudaGraphNode_t node;
@@ -175,14 +192,16 @@ static int add_while(rmgtd_ctx* ctx, cudaGraphConditionalHandle* h, cudaGraph_t*
   return RMGTD_OK;
 }
 
-// Hartree solve inside a captured graph: prologue, then a device-side while loop of CG
-// iterations (captured on the second auxiliary stream).
+// Hartree solve inside a captured graph: prologue (which arms the loop), then a device-side
+// while loop of CG iterations captured on the second auxiliary stream.
 int hartree_graph(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* ctl, int nrep) {
-  int rc = hartree_begin(ctx, rho, vh, ctl, 0, nrep);
-  if (rc) return rc;
   cudaGraphConditionalHandle hp;
+  int rc = new_handle(ctx, &hp, false);
+  if (rc) return rc;
+  rc = hartree_begin(ctx, rho, vh, ctl, 0, nrep, hp, 1);
+  if (rc) return rc;
   cudaGraph_t body;
-  rc = add_while(ctx, &hp, &body);
+  rc = add_while(ctx, hp, &body);
   if (rc) return rc;
   cudaStream_t saved = ctx->stream;
   RMGTD_CUDA(ctx, cudaStreamBeginCaptureToGraph(ctx->aux[1], body, nullptr, nullptr, 0,
@@ -299,7 +318,7 @@ void rmgtd_destroy(rmgtd_ctx* ctx) {
   if (ctx->pcg_any_host) cudaFreeHost(ctx->pcg_any_host);
   if (ctx->stats_host) cudaFreeHost(ctx->stats_host);
   for (auto& e : ctx->ev_pool) cudaEventDestroy(e);
-  for (int i = 0; i < 2; ++i)
+  for (int i = 0; i < 3; ++i)
     if (ctx->aux[i]) cudaStreamDestroy(ctx->aux[i]);
   delete ctx;
 }
@@ -565,16 +584,25 @@ static int enqueue_pass(rmgtd_ctx* ctx, cudaGraphConditionalHandle cond, int use
 // Capture one whole time step as a graph: H_1 extrapolation, a device-side while loop of
 // SCF passes (each containing the Hartree CG while loop), then the shift.
 static int build_step_graph(rmgtd_ctx* ctx) {
-  for (int i = 0; i < 2; ++i)
+  for (int i = 0; i < 3; ++i)
     if (!ctx->aux[i]) RMGTD_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->aux[i], cudaStreamNonBlocking));
-  cudaStream_t main = ctx->stream;
-  RMGTD_CUDA(ctx, cudaStreamBeginCapture(main, cudaStreamCaptureModeRelaxed));
+  // capture on a library-owned stream (the caller's stream may be the legacy default
+  // stream, which cannot be captured); the graph is launched on the caller's stream
+  cudaStream_t user = ctx->stream;
+  cudaStream_t main = ctx->aux[2];
+  ctx->stream = main;
+  cudaError_t be = cudaStreamBeginCapture(main, cudaStreamCaptureModeRelaxed);
+  if (be != cudaSuccess) {
+    ctx->stream = user;
+    return cuda_check(ctx, be, "cudaStreamBeginCapture");
+  }
   ctx->capturing = 1;
   const long long saved_launches = ctx->launches;
   int rc = step_begin(ctx);
   cudaGraphConditionalHandle hs = 0;
   cudaGraph_t body = nullptr;
-  if (!rc) rc = add_while(ctx, &hs, &body);
+  if (!rc) rc = new_handle(ctx, &hs, true);
+  if (!rc) rc = add_while(ctx, hs, &body);
   if (!rc) {
     cudaError_t e = cudaStreamBeginCaptureToGraph(ctx->aux[0], body, nullptr, nullptr, 0,
                                                   cudaStreamCaptureModeRelaxed);
@@ -597,6 +625,7 @@ static int build_step_graph(rmgtd_ctx* ctx) {
   ctx->capturing = 0;
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(main, &g);
+  ctx->stream = user;
   if (rc) {
     if (g) cudaGraphDestroy(g);
     return rc;

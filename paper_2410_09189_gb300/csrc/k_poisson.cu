@@ -201,11 +201,21 @@ __global__ void k_pcg_rz(long Ng, const double* __restrict__ r, const double* __
   if (threadIdx.x == 0) part[((long)rep * 8 + 2) * gridDim.x + blockIdx.x] = s;
 }
 
-__global__ void k_pcg_rz_store(PcgState* st, const double* __restrict__ part, int nblk, int nrep) {
+// store the first (r, z); inside a graph, arm the CG while loop that follows (a nested
+// loop's flag is not reset between executions of the enclosing body)
+__global__ void k_pcg_rz_store(PcgState* st, const double* __restrict__ part, int nblk, int nrep,
+                               cudaGraphConditionalHandle cond, int use_cond) {
   const int rep = threadIdx.x >> 5;
-  if (rep >= nrep || st[rep].done) return;
-  const double s = sum_partials(part + ((long)rep * 8 + 2) * nblk, nblk);
-  if ((threadIdx.x & 31) == 0) st[rep].rz[st[rep].cur] = s;
+  if (rep < nrep && !st[rep].done) {
+    const double s = sum_partials(part + ((long)rep * 8 + 2) * nblk, nblk);
+    if ((threadIdx.x & 31) == 0) st[rep].rz[st[rep].cur] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && use_cond) {
+    int a = 0;
+    for (int r = 0; r < nrep; ++r) a |= (st[r].done == 0);
+    cudaGraphSetConditional(cond, a ? 1u : 0u);
+  }
 }
 
 // Ap = A p and partials of (p, Ap) into slot 3
@@ -686,7 +696,7 @@ int setup_multigrid(rmgtd_ctx* ctx) {
 
 // Start of a Hartree solve: moments, right-hand side, initial residual, first V-cycle.
 int hartree_begin(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* ctl, int zero_bc,
-                  int nrep) {
+                  int nrep, cudaGraphConditionalHandle cond, int use_cond) {
   const Grid3 G{ctx->nx, ctx->ny, ctx->nz, ctx->h};
   const long Ng = ctx->Ng;
   const int nb = ctx->red_blocks;
@@ -705,7 +715,7 @@ int hartree_begin(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* c
   if (rc) return rc;
   k_pcg_rz<<<grid, kThreads, 0, s>>>(Ng, ctx->pcg_r, ctx->pcg_z, ctx->pcg_p, 1, part, ctx->pcg);
   ++ctx->launches;
-  k_pcg_rz_store<<<1, 32 * nrep, 0, s>>>(ctx->pcg, part, nb, nrep);
+  k_pcg_rz_store<<<1, 32 * nrep, 0, s>>>(ctx->pcg, part, nb, nrep, cond, use_cond);
   ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_pcg_rz");
   return RMGTD_OK;
@@ -746,7 +756,7 @@ int hartree_iteration(rmgtd_ctx* ctx, double* vh, int nrep, cudaGraphConditional
 // Eager Hartree solve (host-driven loop, peeking at the convergence flag).
 int hartree_dev(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* ctl, int zero_bc,
                 int nrep) {
-  int rc = hartree_begin(ctx, rho, vh, ctl, zero_bc, nrep);
+  int rc = hartree_begin(ctx, rho, vh, ctl, zero_bc, nrep, 0, 0);
   if (rc) return rc;
   for (int it = 0; it < ctx->opt.poisson_max_iter; ++it) {
     rc = hartree_iteration(ctx, vh, nrep, 0, 0);

@@ -162,7 +162,7 @@ struct rmgtd_ctx {
   // CUDA graph of one time step
   cudaGraphExec_t step_exec = nullptr;
   cudaGraph_t step_graph = nullptr;
-  cudaStream_t aux[2] = {nullptr, nullptr};
+  cudaStream_t aux[3] = {nullptr, nullptr, nullptr};  // SCF body, CG body, top-level capture
   int capturing = 0;
   int* failed = nullptr;            // sticky: a step of the current rmgtd_step call failed
   int* done_steps = nullptr;        // steps completed in the current rmgtd_step call
@@ -316,7 +316,7 @@ int hartree_dev(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* ctl
                 int nrep);
 int hartree_graph(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* ctl, int nrep);
 int hartree_begin(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* ctl, int zero_bc,
-                  int nrep);
+                  int nrep, cudaGraphConditionalHandle cond, int use_cond);
 int hartree_iteration(rmgtd_ctx* ctx, double* vh, int nrep, cudaGraphConditionalHandle cond,
                       int use_cond);
 
