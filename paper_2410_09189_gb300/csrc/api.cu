@@ -194,11 +194,12 @@ static int add_while(rmgtd_ctx* ctx, cudaGraphConditionalHandle h, cudaGraph_t* 
 
 // Hartree solve inside a captured graph: prologue (which arms the loop), then a device-side
 // while loop of CG iterations captured on the second auxiliary stream.
-int hartree_graph(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* ctl, int nrep) {
+int hartree_graph(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* ctl, int nrep,
+                  int f32) {
   cudaGraphConditionalHandle hp;
   int rc = new_handle(ctx, &hp, false);
   if (rc) return rc;
-  rc = hartree_begin(ctx, rho, vh, ctl, 0, nrep, hp, 1);
+  rc = hartree_begin(ctx, rho, vh, ctl, 0, nrep, hp, 1, f32);
   if (rc) return rc;
   cudaGraph_t body;
   rc = add_while(ctx, hp, &body);
@@ -208,7 +209,7 @@ int hartree_graph(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* c
                                                 cudaStreamCaptureModeRelaxed));
   ctx->stream = ctx->aux[1];
   const long long l0 = ctx->launches;
-  rc = hartree_iteration(ctx, vh, nrep, hp, 1);
+  rc = hartree_iteration(ctx, vh, nrep, hp, 1, f32);
   ctx->cap_pcg = (int)(ctx->launches - l0);
   ctx->stream = saved;
   cudaGraph_t out;
@@ -223,41 +224,50 @@ int hartree_graph(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* c
 // replicas and folds max|H_new - H_1| into errbits.
 int dft_eval(rmgtd_ctx* ctx, const double* S, const RepCtl* ctl, unsigned long long* errbits) {
   const int nrep = ctx->nrep;
+  const int mixed = ctx->mixed;
   ph_begin(ctx, PH_RHO);
-  int rc = rho_dev(ctx, S, ctx->rho, ctl, nrep);
+  int rc = mixed ? rho_dev_mixed(ctx, S, ctx->rho, ctl, nrep) : rho_dev(ctx, S, ctx->rho, ctl, nrep);
   ph_end(ctx);
   if (rc) return rc;
   if (ctx->hartree_xc) {
     ph_begin(ctx, PH_HARTREE);
-    rc = ctx->capturing ? hartree_graph(ctx, ctx->rho, ctx->vh, ctl, nrep)
-                        : hartree_dev(ctx, ctx->rho, ctx->vh, ctl, 0, nrep);
+    rc = ctx->capturing ? hartree_graph(ctx, ctx->rho, ctx->vh, ctl, nrep, mixed)
+                        : hartree_dev(ctx, ctx->rho, ctx->vh, ctl, 0, nrep, mixed);
     ph_end(ctx);
     if (rc) return rc;
   }
   ph_begin(ctx, PH_XC);
-  rc = launch_lda(ctx, ctx->rho, ctx->hartree_xc ? ctx->vh : nullptr, ctx->vxc, ctx->exc,
-                  ctx->vhxc, ctx->Ng, ctl, nrep, ctx->Ng, ctx->hartree_xc);
+  rc = launch_lda(ctx, ctx->rho, ctx->hartree_xc ? ctx->vh : nullptr,
+                  (mixed && ctx->hartree_xc) ? 1 : 0, ctx->vxc, ctx->exc, ctx->vhxc,
+                  mixed ? ctx->dv32 : nullptr, ctx->Ng, ctl, nrep, ctx->Ng, ctx->hartree_xc);
   ph_end(ctx);
   if (rc) return rc;
   if (errbits)
     RMGTD_CUDA(ctx, cudaMemsetAsync(errbits, 0, sizeof(unsigned long long) * nrep, ctx->stream));
   ph_begin(ctx, PH_HUPDATE);
-  rc = gram(ctx, ctx->phi, ctx->phi, ctx->vhxc, ctx->Ng, nrep, ctx->h3, ctx->Hcore, ctx->H1,
-            errbits ? ctx->H1 : nullptr, ctl, 1, errbits);
+  if (mixed)
+    rc = gram_mixed(ctx, ctx->dv32, ctx->Ng, nrep, ctx->h3, ctx->Href, ctx->H1, ctl, errbits);
+  else
+    rc = gram(ctx, ctx->phi, ctx->phi, ctx->vhxc, ctx->Ng, nrep, ctx->h3, ctx->Hcore, ctx->H1,
+              errbits ? ctx->H1 : nullptr, ctl, 1, errbits);
   ph_end(ctx);
   return rc;
 }
 
-// Refresh rho / V_H / V_xc / eps_xc from the current P_0 of every replica (no H update).
+// Refresh rho / V_H / V_xc / eps_xc from the current P_0 of every replica (no H update),
+// in float64 (kicks, loads, set_matrix); in the mixed path the float32 corrections are
+// re-derived from the float64 fields.
 int refresh_fields(rmgtd_ctx* ctx) {
   int rc = rho_dev(ctx, ctx->S0, ctx->rho, nullptr, ctx->nrep);
   if (rc) return rc;
   if (ctx->hartree_xc) {
-    rc = hartree_dev(ctx, ctx->rho, ctx->vh, nullptr, 0, ctx->nrep);
+    rc = hartree_dev(ctx, ctx->rho, ctx->vh, nullptr, 0, ctx->nrep, 0);
     if (rc) return rc;
   }
-  return launch_lda(ctx, ctx->rho, ctx->hartree_xc ? ctx->vh : nullptr, ctx->vxc, ctx->exc,
-                    ctx->vhxc, ctx->Ng, nullptr, ctx->nrep, ctx->Ng, ctx->hartree_xc);
+  return launch_lda(ctx, ctx->rho, ctx->hartree_xc ? ctx->vh : nullptr,
+                    (ctx->mixed && ctx->hartree_xc) ? 2 : 0, ctx->vxc, ctx->exc, ctx->vhxc,
+                    ctx->mixed ? ctx->dv32 : nullptr, ctx->Ng, nullptr, ctx->nrep, ctx->Ng,
+                    ctx->hartree_xc);
 }
 
 static int check_status(rmgtd_ctx* ctx, const char* where) {
@@ -500,6 +510,35 @@ static int create_impl(const rmgtd_system* sys, const rmgtd_options* opt, rmgtd_
   RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->A1, ctx->A0, msz * nrep, cudaMemcpyDeviceToDevice, ctx->stream));
   k_set_active<<<1, 32, 0, ctx->stream>>>(ctx->ctl, nrep, 0);
   ++ctx->launches;
+  if (opt->precision == RMGTD_PREC_MIXED) {
+    // reference state of the mixed path: the float64 set-up state (all replicas start in it)
+    const size_t fsz = sizeof(float) * Ng;
+    ctx->phi32 = (float*)A(fsz * N);
+    ctx->Sref = (double*)A(msz);
+    ctx->Href = (double*)A(msz);
+    ctx->rho_ref = (double*)A(gsz);
+    ctx->vref = (double*)A(gsz);
+    ctx->vh_ref = (double*)A(gsz);
+    ctx->dv32 = (float*)A(fsz * nrep);
+    ctx->dvh32 = (float*)A(fsz * nrep);
+    ctx->pcg32_b = (float*)A(fsz * nrep);
+    ctx->pcg32_r = (float*)A(fsz * nrep);
+    ctx->pcg32_z = (float*)A(fsz * nrep);
+    ctx->pcg32_p = (float*)A(fsz * nrep);
+    ctx->pcg32_Ap = (float*)A(fsz * nrep);
+    if (!ctx->phi32 || !ctx->pcg32_Ap || !ctx->dvh32 || !ctx->Href || !ctx->vh_ref)
+      return set_error(ctx, RMGTD_ENOMEM, "mixed-precision buffers");
+    rc = to_float(ctx, ctx->phi, ctx->phi32, (long)N * Ng);
+    if (rc) return rc;
+    RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->Sref, ctx->S0, msz, cudaMemcpyDeviceToDevice, ctx->stream));
+    RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->Href, ctx->H0, msz, cudaMemcpyDeviceToDevice, ctx->stream));
+    RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->rho_ref, ctx->rho, gsz, cudaMemcpyDeviceToDevice, ctx->stream));
+    RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->vh_ref, ctx->vh, gsz, cudaMemcpyDeviceToDevice, ctx->stream));
+    RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->vref, ctx->vhxc, gsz, cudaMemcpyDeviceToDevice, ctx->stream));
+    RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->dvh32, 0, fsz * nrep, ctx->stream));
+    RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->dv32, 0, fsz * nrep, ctx->stream));
+    ctx->mixed = 1;
+  }
   return check_status(ctx, "create");
 }
 
@@ -845,7 +884,7 @@ int rmgtd_hartree(rmgtd_ctx* ctx, const double* rho_dev, double* vh_dev) {
   if (!ctx) return set_error(nullptr, RMGTD_EINVAL, "ctx is NULL");
   if (!rho_dev || !vh_dev) return set_error(ctx, RMGTD_EINVAL, "hartree: NULL pointer");
   RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream));
-  int rc = hartree_dev(ctx, rho_dev, vh_dev, nullptr, 0, 1);
+  int rc = hartree_dev(ctx, rho_dev, vh_dev, nullptr, 0, 1, 0);
   if (rc) return rc;
   return check_status(ctx, "hartree");
 }
@@ -853,7 +892,8 @@ int rmgtd_hartree(rmgtd_ctx* ctx, const double* rho_dev, double* vh_dev) {
 int rmgtd_xc(rmgtd_ctx* ctx, const double* rho_dev, double* vxc_dev, double* exc_dev, size_t n) {
   if (!ctx) return set_error(nullptr, RMGTD_EINVAL, "ctx is NULL");
   if (!rho_dev || !vxc_dev || n == 0) return set_error(ctx, RMGTD_EINVAL, "xc: bad arguments");
-  int rc = launch_lda(ctx, rho_dev, nullptr, vxc_dev, exc_dev, nullptr, (long)n, nullptr, 1, (long)n, 1);
+  int rc = launch_lda(ctx, rho_dev, nullptr, 0, vxc_dev, exc_dev, nullptr, nullptr, (long)n, nullptr,
+                      1, (long)n, 1);
   if (rc) return rc;
   RMGTD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   return RMGTD_OK;
@@ -883,10 +923,15 @@ int rmgtd_save(rmgtd_ctx* ctx, const char* path) {
   RMGTD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   FILE* fp = fopen(path, "wb");
   if (!fp) return set_error(ctx, RMGTD_EINVAL, std::string("save: cannot open ") + path);
-  const int64_t hdr[6] = {ctx->nx, ctx->ny, ctx->nz, ctx->N, ctx->nrep, ctx->steps};
+  const int64_t hdr[7] = {ctx->nx, ctx->ny, ctx->nz, ctx->N, ctx->nrep, ctx->steps, ctx->mixed};
   bool ok = fwrite(&kMagic, sizeof(kMagic), 1, fp) == 1 && fwrite(hdr, sizeof(hdr), 1, fp) == 1 &&
             fwrite(&ctx->t, sizeof(double), 1, fp) == 1 &&
             fwrite(buf.data(), sizeof(double), buf.size(), fp) == buf.size();
+  if (ok && ctx->mixed) {
+    std::vector<float> d32(gcount);
+    RMGTD_CUDA(ctx, cudaMemcpy(d32.data(), ctx->dvh32, sizeof(float) * gcount, cudaMemcpyDeviceToHost));
+    ok = fwrite(d32.data(), sizeof(float), gcount, fp) == gcount;
+  }
   fclose(fp);
   if (!ok) return set_error(ctx, RMGTD_EINVAL, "save: write failed");
   return RMGTD_OK;
@@ -898,12 +943,12 @@ int rmgtd_load(rmgtd_ctx* ctx, const char* path) {
   FILE* fp = fopen(path, "rb");
   if (!fp) return set_error(ctx, RMGTD_EINVAL, std::string("load: cannot open ") + path);
   uint64_t magic = 0;
-  int64_t hdr[6];
+  int64_t hdr[7];
   double t = 0;
   bool ok = fread(&magic, sizeof(magic), 1, fp) == 1 && fread(hdr, sizeof(hdr), 1, fp) == 1 &&
             fread(&t, sizeof(double), 1, fp) == 1;
   if (!ok || magic != kMagic || hdr[0] != ctx->nx || hdr[1] != ctx->ny || hdr[2] != ctx->nz ||
-      hdr[3] != ctx->N || hdr[4] != ctx->nrep) {
+      hdr[3] != ctx->N || hdr[4] != ctx->nrep || hdr[6] != ctx->mixed) {
     fclose(fp);
     return set_error(ctx, RMGTD_EINVAL, "load: checkpoint does not match this context");
   }
@@ -911,8 +956,15 @@ int rmgtd_load(rmgtd_ctx* ctx, const char* path) {
   const size_t mcount = (size_t)NN * ctx->nrep, gcount = (size_t)ctx->Ng * ctx->nrep;
   std::vector<double> buf(4 * mcount + gcount);
   ok = fread(buf.data(), sizeof(double), buf.size(), fp) == buf.size();
+  std::vector<float> d32;
+  if (ok && ctx->mixed) {
+    d32.resize(gcount);
+    ok = fread(d32.data(), sizeof(float), gcount, fp) == gcount;
+  }
   fclose(fp);
   if (!ok) return set_error(ctx, RMGTD_EINVAL, "load: truncated checkpoint");
+  if (ctx->mixed)
+    RMGTD_CUDA(ctx, cudaMemcpy(ctx->dvh32, d32.data(), sizeof(float) * gcount, cudaMemcpyHostToDevice));
   double* parts[4] = {ctx->S0, ctx->A0, ctx->H0, ctx->Hm1};
   for (int i = 0; i < 4; ++i)
     RMGTD_CUDA(ctx, cudaMemcpyAsync(parts[i], buf.data() + i * mcount, sizeof(double) * mcount,
@@ -925,8 +977,9 @@ int rmgtd_load(rmgtd_ctx* ctx, const char* path) {
   // observables need rho / eps_xc of the restored P; V_H is restored exactly (warm start)
   int rc = rho_dev(ctx, ctx->S0, ctx->rho, nullptr, ctx->nrep);
   if (rc) return rc;
-  rc = launch_lda(ctx, ctx->rho, ctx->hartree_xc ? ctx->vh : nullptr, ctx->vxc, ctx->exc,
-                  ctx->vhxc, ctx->Ng, nullptr, ctx->nrep, ctx->Ng, ctx->hartree_xc);
+  rc = launch_lda(ctx, ctx->rho, ctx->hartree_xc ? ctx->vh : nullptr, 0, ctx->vxc, ctx->exc,
+                  ctx->vhxc, ctx->mixed ? ctx->dv32 : nullptr, ctx->Ng, nullptr, ctx->nrep,
+                  ctx->Ng, ctx->hartree_xc);
   if (rc) return rc;
   RMGTD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   return RMGTD_OK;

@@ -381,9 +381,11 @@ __device__ __forceinline__ void lda_point(double rho, double& vxc, double& exc) 
   exc = ex + ec;
 }
 
-__global__ void k_lda(const double* __restrict__ rho, const double* __restrict__ vh,
+__global__ void k_lda(const double* __restrict__ rho, double* __restrict__ vh, int vh_mode,
+                      const double* __restrict__ vh_ref, float* __restrict__ dvh32,
                       double* __restrict__ vxc, double* __restrict__ exc,
-                      double* __restrict__ vhxc, long n, const RepCtl* __restrict__ ctl,
+                      double* __restrict__ vhxc, const double* __restrict__ vref,
+                      float* __restrict__ dv32, long n, const RepCtl* __restrict__ ctl,
                       long stride, int with_xc) {
   const int rep = blockIdx.y;
   if (ctl && !ctl[rep].active) return;
@@ -394,17 +396,28 @@ __global__ void k_lda(const double* __restrict__ rho, const double* __restrict__
     if (with_xc) lda_point(rho[o + g], v, e);
     vxc[o + g] = v;
     if (exc) exc[o + g] = e;
-    if (vhxc) vhxc[o + g] = (vh ? vh[o + g] : 0.0) + v;
+    double vhv = 0.0;
+    if (vh) {
+      if (vh_mode == 1) {
+        vhv = vh_ref[g] + (double)dvh32[o + g];
+        vh[o + g] = vhv;
+      } else {
+        vhv = vh[o + g];
+        if (vh_mode == 2) dvh32[o + g] = (float)(vhv - vh_ref[g]);
+      }
+    }
+    if (vhxc) vhxc[o + g] = vhv + v;
+    if (dv32) dv32[o + g] = (float)(vhv + v - vref[g]);
   }
 }
 
-// V_xc, eps_xc (and V_H + V_xc when vhxc is given) for `nrep` fields of `n` points.
-// with_xc = 0 gives zero exchange-correlation (independent-electron test mode).
-int launch_lda(rmgtd_ctx* ctx, const double* rho, const double* vh, double* vxc, double* exc,
-               double* vhxc, long n, const RepCtl* ctl, int nrep, long stride, int with_xc) {
+int launch_lda(rmgtd_ctx* ctx, const double* rho, double* vh, int vh_mode, double* vxc,
+               double* exc, double* vhxc, float* dv32, long n, const RepCtl* ctl, int nrep,
+               long stride, int with_xc) {
   const int blocks = (int)std::min<long>(ceil_div(n, kThreads), 4L * ctx->num_sms);
   k_lda<<<dim3(std::max(blocks, 1), nrep), kThreads, 0, ctx->stream>>>(
-      rho, vh, vxc, exc, vhxc, n, ctl, stride, with_xc);
+      rho, vh, vh_mode, ctx->vh_ref, ctx->dvh32, vxc, exc, vhxc, ctx->vref, dv32, n, ctl, stride,
+      with_xc);
   ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_lda");
   return RMGTD_OK;

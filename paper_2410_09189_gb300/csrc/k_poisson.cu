@@ -25,6 +25,9 @@ constexpr double kPi = 3.14159265358979323846;
 constexpr float kJacobiW = 6.0f / 7.0f;
 constexpr int kTailMax = 4096;
 constexpr int kPre = 2, kPost = 2, kCoarseSweeps = 40;
+// relative residual of the float32 correction solve of the mixed path (float32 CG reaches
+// ~1e-6-1e-7; the correction is small next to the float64 reference potential)
+constexpr double kMixedPoissonTol = 1e-6;
 
 struct Grid3 {
   int nx, ny, nz;
@@ -78,7 +81,8 @@ __global__ void k_ghost_fields(Grid3 G, double* __restrict__ gf) {
 }
 
 // ---- multipole moments (partials into slots 4..7) ------------------------------------------
-__global__ void k_moments(Grid3 G, const double* __restrict__ rho, double* __restrict__ part,
+__global__ void k_moments(Grid3 G, const double* __restrict__ rho,
+                          const double* __restrict__ rho_ref, double* __restrict__ part,
                           const RepCtl* __restrict__ ctl) {
   const int rep = blockIdx.y;
   if (ctl && !ctl[rep].active) return;
@@ -88,7 +92,7 @@ __global__ void k_moments(Grid3 G, const double* __restrict__ rho, double* __res
   for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < Ng;
        g += (long)gridDim.x * blockDim.x) {
     const int ix = (int)(g % G.nx), iy = (int)((g / G.nx) % G.ny), iz = (int)(g / ((long)G.nx * G.ny));
-    const double v = r[g];
+    const double v = rho_ref ? r[g] - rho_ref[g] : r[g];
     q[0] += v;
     q[1] += v * axis_coord(ix, G.nx, G.h);
     q[2] += v * axis_coord(iy, G.ny, G.h);
@@ -103,30 +107,33 @@ __global__ void k_moments(Grid3 G, const double* __restrict__ rho, double* __res
 }
 
 // ---- the 12th-order operator A = -Lap_12 with zero ghosts -------------------------------
-__device__ __forceinline__ double apply_A12(const double* __restrict__ x, int ix, int iy, int iz,
-                                            int nx, int ny, int nz, double ih2) {
+template <typename V>
+__device__ __forceinline__ V apply_A12(const V* __restrict__ x, int ix, int iy, int iz, int nx,
+                                       int ny, int nz, V ih2) {
   const long plane = (long)nx * ny;
   const long g = (long)iz * plane + (long)iy * nx + ix;
-  double s = 3.0 * fd_coef(0) * x[g];
+  V s = (V)(3.0 * fd_coef(0)) * x[g];
 #pragma unroll
   for (int m = 1; m <= kFdRadius; ++m) {
-    double t = 0.0;
+    V t = 0;
     if (ix + m < nx) t += x[g + m];
     if (ix - m >= 0) t += x[g - m];
     if (iy + m < ny) t += x[g + (long)m * nx];
     if (iy - m >= 0) t += x[g - (long)m * nx];
     if (iz + m < nz) t += x[g + (long)m * plane];
     if (iz - m >= 0) t += x[g - (long)m * plane];
-    s = fma(fd_coef(m), t, s);
+    s = fma((V)fd_coef(m), t, s);
   }
   return -s * ih2;
 }
 
-// b = 4 pi rho + Q G0 + p.G ; r = b - A x ; partials of (b,b) (slot 0), (r,r) (slot 1)
-__global__ void k_pcg_init(Grid3 G, const double* __restrict__ rho, const double* __restrict__ gf,
-                           const double* __restrict__ x, double* __restrict__ b,
-                           double* __restrict__ r, double* __restrict__ part, int zero_bc,
-                           const RepCtl* __restrict__ ctl) {
+// b = 4 pi (rho - rho_ref) + Q G0 + p.G (moments of rho - rho_ref; rho_ref may be NULL);
+// r = b - A x; partials of (b,b) (slot 0), (r,r) (slot 1)
+template <typename V>
+__global__ void k_pcg_init(Grid3 G, const double* __restrict__ rho,
+                           const double* __restrict__ rho_ref, const double* __restrict__ gf,
+                           const V* __restrict__ x, V* __restrict__ b, V* __restrict__ r,
+                           double* __restrict__ part, int zero_bc, const RepCtl* __restrict__ ctl) {
   const int rep = blockIdx.y;
   if (ctl && !ctl[rep].active) return;
   const int nblk = gridDim.x;
@@ -142,19 +149,21 @@ __global__ void k_pcg_init(Grid3 G, const double* __restrict__ rho, const double
   const double Q = zero_bc ? 0.0 : h3 * mom[0], px = zero_bc ? 0.0 : h3 * mom[1],
                py = zero_bc ? 0.0 : h3 * mom[2], pz = zero_bc ? 0.0 : h3 * mom[3];
   const long Ng = (long)G.nx * G.ny * G.nz;
-  const double ih2 = 1.0 / (G.h * G.h);
-  const double* xr = x + rep * Ng;
+  const V ih2 = (V)(1.0 / (G.h * G.h));
+  const V* xr = x + rep * Ng;
   double bb = 0.0, rr = 0.0;
   for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < Ng;
        g += (long)gridDim.x * blockDim.x) {
     const int ix = (int)(g % G.nx), iy = (int)((g / G.nx) % G.ny), iz = (int)(g / ((long)G.nx * G.ny));
-    double bv = 4.0 * kPi * rho[rep * Ng + g];
-    bv += Q * gf[g] + px * gf[Ng + g] + py * gf[2 * Ng + g] + pz * gf[3 * Ng + g];
+    const double dr = rho_ref ? rho[rep * Ng + g] - rho_ref[g] : rho[rep * Ng + g];
+    double bd = 4.0 * kPi * dr;
+    bd += Q * gf[g] + px * gf[Ng + g] + py * gf[2 * Ng + g] + pz * gf[3 * Ng + g];
+    const V bv = (V)bd;
     b[rep * Ng + g] = bv;
-    const double rv = bv - apply_A12(xr, ix, iy, iz, G.nx, G.ny, G.nz, ih2);
+    const V rv = bv - apply_A12<V>(xr, ix, iy, iz, G.nx, G.ny, G.nz, ih2);
     r[rep * Ng + g] = rv;
-    bb += bv * bv;
-    rr += rv * rv;
+    bb += (double)bv * (double)bv;
+    rr += (double)rv * (double)rv;
   }
   __shared__ double sh[32];
   bb = block_sum(bb, sh);
@@ -184,16 +193,17 @@ __global__ void k_pcg_state_init(PcgState* st, const double* __restrict__ part, 
 }
 
 // (r, z) partials into slot 2; p = z when `first`
-__global__ void k_pcg_rz(long Ng, const double* __restrict__ r, const double* __restrict__ z,
-                         double* __restrict__ p, int first, double* __restrict__ part,
+template <typename V>
+__global__ void k_pcg_rz(long Ng, const V* __restrict__ r, const V* __restrict__ z,
+                         V* __restrict__ p, int first, double* __restrict__ part,
                          const PcgState* __restrict__ st) {
   const int rep = blockIdx.y;
   if (pcg_skip(st, rep)) return;
   double s = 0.0;
   for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < Ng;
        g += (long)gridDim.x * blockDim.x) {
-    const double zv = z[rep * Ng + g];
-    s += r[rep * Ng + g] * zv;
+    const V zv = z[rep * Ng + g];
+    s += (double)r[rep * Ng + g] * (double)zv;
     if (first) p[rep * Ng + g] = zv;
   }
   __shared__ double sh[32];
@@ -219,20 +229,21 @@ __global__ void k_pcg_rz_store(PcgState* st, const double* __restrict__ part, in
 }
 
 // Ap = A p and partials of (p, Ap) into slot 3
-__global__ void k_pcg_Ap(Grid3 G, const double* __restrict__ p, double* __restrict__ Ap,
+template <typename V>
+__global__ void k_pcg_Ap(Grid3 G, const V* __restrict__ p, V* __restrict__ Ap,
                          double* __restrict__ part, const PcgState* __restrict__ st) {
   const int rep = blockIdx.y;
   if (pcg_skip(st, rep)) return;
   const long Ng = (long)G.nx * G.ny * G.nz;
-  const double ih2 = 1.0 / (G.h * G.h);
-  const double* pr = p + rep * Ng;
+  const V ih2 = (V)(1.0 / (G.h * G.h));
+  const V* pr = p + rep * Ng;
   double s = 0.0;
   for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < Ng;
        g += (long)gridDim.x * blockDim.x) {
     const int ix = (int)(g % G.nx), iy = (int)((g / G.nx) % G.ny), iz = (int)(g / ((long)G.nx * G.ny));
-    const double a = apply_A12(pr, ix, iy, iz, G.nx, G.ny, G.nz, ih2);
+    const V a = apply_A12<V>(pr, ix, iy, iz, G.nx, G.ny, G.nz, ih2);
     Ap[rep * Ng + g] = a;
-    s += pr[g] * a;
+    s += (double)pr[g] * (double)a;
   }
   __shared__ double sh[32];
   s = block_sum(s, sh);
@@ -241,10 +252,10 @@ __global__ void k_pcg_Ap(Grid3 G, const double* __restrict__ p, double* __restri
 
 // alpha = rz/(p,Ap); x += alpha p; r -= alpha Ap; partials of (r,r) (slot 1) and of
 // (r_new, z_old) (slot 5) for the flexible beta
-__global__ void k_pcg_xr(long Ng, double* __restrict__ x, double* __restrict__ r,
-                         const double* __restrict__ p, const double* __restrict__ Ap,
-                         const double* __restrict__ z, double* __restrict__ part,
-                         const PcgState* __restrict__ st) {
+template <typename V>
+__global__ void k_pcg_xr(long Ng, V* __restrict__ x, V* __restrict__ r, const V* __restrict__ p,
+                         const V* __restrict__ Ap, const V* __restrict__ z,
+                         double* __restrict__ part, const PcgState* __restrict__ st) {
   const int rep = blockIdx.y;
   if (pcg_skip(st, rep)) return;
   __shared__ double alpha;
@@ -254,16 +265,16 @@ __global__ void k_pcg_xr(long Ng, double* __restrict__ x, double* __restrict__ r
     if (threadIdx.x == 0) alpha = st[rep].rz[st[rep].cur] / pAp;
   }
   __syncthreads();
-  const double a = alpha;
+  const V a = (V)alpha;
   double s = 0.0, t = 0.0;
   for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < Ng;
        g += (long)gridDim.x * blockDim.x) {
     const long e = rep * Ng + g;
     x[e] = fma(a, p[e], x[e]);
-    const double rv = fma(-a, Ap[e], r[e]);
+    const V rv = fma(-a, Ap[e], r[e]);
     r[e] = rv;
-    s += rv * rv;
-    t += rv * z[e];
+    s += (double)rv * (double)rv;
+    t += (double)rv * (double)z[e];
   }
   __shared__ double sh[32];
   s = block_sum(s, sh);
@@ -296,7 +307,8 @@ __global__ void k_pcg_check(PcgState* st, const double* __restrict__ part, int n
 }
 
 // beta = ((r,z_new) - (r,z_old)) / rz_old (Polak-Ribiere); p = z + beta p
-__global__ void k_pcg_p(long Ng, const double* __restrict__ z, double* __restrict__ p,
+template <typename V>
+__global__ void k_pcg_p(long Ng, const V* __restrict__ z, V* __restrict__ p,
                         const double* __restrict__ part, const PcgState* __restrict__ st) {
   const int rep = blockIdx.y;
   if (pcg_skip(st, rep)) return;
@@ -308,7 +320,7 @@ __global__ void k_pcg_p(long Ng, const double* __restrict__ z, double* __restric
     if (threadIdx.x == 0) beta = (rzn - rzo) / st[rep].rz[st[rep].cur];
   }
   __syncthreads();
-  const double bt = beta;
+  const V bt = (V)beta;
   for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < Ng;
        g += (long)gridDim.x * blockDim.x) {
     const long e = rep * Ng + g;
@@ -576,8 +588,10 @@ static int grid_blocks(rmgtd_ctx* ctx, long n) {
   return (int)std::max<long>(1, std::min<long>(ceil_div(n, kThreads), ctx->red_blocks));
 }
 
-// z (float64) = M r (float64), M = one float32 V-cycle
-static int vcycle(rmgtd_ctx* ctx, const double* r64, double* z64, int nrep) {
+// z = M r, M = one float32 V-cycle.  Level-0 input / output are float64 (r64, z64) or
+// float32 (r32, z32: the V-cycle then iterates directly in z32).
+static int vcycle(rmgtd_ctx* ctx, const double* r64, double* z64, const float* r32, float* z32,
+                  int nrep) {
   const PcgState* st = ctx->pcg;
   const int nl = (int)ctx->mg.size();
   const int tail = ctx->mg_tail_level;  // first tail level (>= 1) or -1
@@ -589,19 +603,23 @@ static int vcycle(rmgtd_ctx* ctx, const double* r64, double* z64, int nrep) {
     const int bl = grid_blocks(ctx, L.n);
     const bool coarsest = (l == nl - 1);
     const int sweeps = coarsest ? kCoarseSweeps : kPre;
-    float* bufs[2] = {L.x, L.t};
+    float* lx = (l == 0 && z32) ? z32 : L.x;
+    float* lb = (l == 0 && r32) ? const_cast<float*>(r32) : L.b;
+    const double* in64 = (l == 0 && !r32) ? r64 : nullptr;
+    double* out64 = (l == 0 && !z32) ? z64 : nullptr;
+    float* bufs[2] = {lx, L.t};
     int cur = (sweeps % 2 == 1) ? 0 : 1;  // the last sweep writes x
     for (int sw = 0; sw < sweeps; ++sw) {
-      const bool last_out64 = (coarsest && l == 0 && sw == sweeps - 1);
+      const bool last_out64 = (coarsest && out64 && sw == sweeps - 1);
       k_mg_jacobi<<<dim3(bl, nrep), kThreads, 0, s>>>(
-          G, bufs[cur ^ 1], bufs[cur], L.b, (l == 0 && sw == 0) ? r64 : nullptr, sw == 0,
-          last_out64 ? z64 : nullptr, st);
+          G, bufs[cur ^ 1], bufs[cur], lb, sw == 0 ? in64 : nullptr, sw == 0,
+          last_out64 ? out64 : nullptr, st);
       ++ctx->launches;
       cur ^= 1;
     }
     RMGTD_LAUNCH(ctx, "k_mg_jacobi");
     if (coarsest) break;
-    k_mg_residual<<<dim3(bl, nrep), kThreads, 0, s>>>(G, L.x, L.b, L.t, st);
+    k_mg_residual<<<dim3(bl, nrep), kThreads, 0, s>>>(G, lx, lb, L.t, st);
     ++ctx->launches;
     MgLevel& C = ctx->mg[l + 1];
     k_mg_restrict<<<dim3(grid_blocks(ctx, C.n), nrep), kThreads, 0, s>>>(G, grid_of(C), L.t, C.b, st);
@@ -626,14 +644,17 @@ static int vcycle(rmgtd_ctx* ctx, const double* r64, double* z64, int nrep) {
     MgLevel& C = ctx->mg[l + 1];
     const Grid3 G = grid_of(L);
     const int bl = grid_blocks(ctx, L.n);
-    k_mg_prolong<<<dim3(bl, nrep), kThreads, 0, s>>>(G, grid_of(C), C.x, L.x, st);
+    float* lx = (l == 0 && z32) ? z32 : L.x;
+    float* lb = (l == 0 && r32) ? const_cast<float*>(r32) : L.b;
+    double* out64 = (l == 0 && !z32) ? z64 : nullptr;
+    k_mg_prolong<<<dim3(bl, nrep), kThreads, 0, s>>>(G, grid_of(C), C.x, lx, st);
     ++ctx->launches;
-    float* bufs[2] = {L.x, L.t};
+    float* bufs[2] = {lx, L.t};
     int cur = 1;
     for (int sw = 0; sw < kPost; ++sw) {
-      const bool out64 = (l == 0 && sw == kPost - 1);
-      k_mg_jacobi<<<dim3(bl, nrep), kThreads, 0, s>>>(G, bufs[cur ^ 1], bufs[cur], L.b, nullptr,
-                                                      0, out64 ? z64 : nullptr, st);
+      const bool last = (sw == kPost - 1);
+      k_mg_jacobi<<<dim3(bl, nrep), kThreads, 0, s>>>(G, bufs[cur ^ 1], bufs[cur], lb, nullptr,
+                                                      0, (last && out64) ? out64 : nullptr, st);
       ++ctx->launches;
       cur ^= 1;
     }
@@ -694,26 +715,72 @@ int setup_multigrid(rmgtd_ctx* ctx) {
   return RMGTD_OK;
 }
 
+// Buffers of one Hartree solve: float64 (the solve of rho itself) or float32 (the change
+// of V_H relative to the reference potential, mixed path).
+struct PcgBufs {
+  bool f32;
+  void *x, *b, *r, *z, *p, *Ap;
+  const double* rho_ref;
+  double tol;
+};
+
+static PcgBufs pcg_bufs(rmgtd_ctx* ctx, double* vh, int f32) {
+  PcgBufs B;
+  B.f32 = f32 != 0;
+  if (B.f32) {
+    B.x = ctx->dvh32;
+    B.b = ctx->pcg32_b;
+    B.r = ctx->pcg32_r;
+    B.z = ctx->pcg32_z;
+    B.p = ctx->pcg32_p;
+    B.Ap = ctx->pcg32_Ap;
+    B.rho_ref = ctx->rho_ref;
+    B.tol = std::max(ctx->opt.poisson_tol, kMixedPoissonTol);
+  } else {
+    B.x = vh;
+    B.b = ctx->pcg_b;
+    B.r = ctx->pcg_r;
+    B.z = ctx->pcg_z;
+    B.p = ctx->pcg_p;
+    B.Ap = ctx->pcg_Ap;
+    B.rho_ref = nullptr;
+    B.tol = ctx->opt.poisson_tol;
+  }
+  return B;
+}
+
 // Start of a Hartree solve: moments, right-hand side, initial residual, first V-cycle.
 int hartree_begin(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* ctl, int zero_bc,
-                  int nrep, cudaGraphConditionalHandle cond, int use_cond) {
+                  int nrep, cudaGraphConditionalHandle cond, int use_cond, int f32) {
   const Grid3 G{ctx->nx, ctx->ny, ctx->nz, ctx->h};
   const long Ng = ctx->Ng;
   const int nb = ctx->red_blocks;
   const dim3 grid(nb, nrep);
   cudaStream_t s = ctx->stream;
   double* part = ctx->red_part;
-  k_moments<<<grid, kThreads, 0, s>>>(G, rho, part, ctl);
+  const PcgBufs B = pcg_bufs(ctx, vh, f32);
+  k_moments<<<grid, kThreads, 0, s>>>(G, rho, B.rho_ref, part, ctl);
   ++ctx->launches;
-  k_pcg_init<<<grid, kThreads, 0, s>>>(G, rho, ctx->ghost, vh, ctx->pcg_b, ctx->pcg_r, part,
-                                       zero_bc, ctl);
+  if (B.f32) {
+    k_pcg_init<float><<<grid, kThreads, 0, s>>>(G, rho, B.rho_ref, ctx->ghost, (float*)B.x,
+                                                (float*)B.b, (float*)B.r, part, zero_bc, ctl);
+  } else {
+    k_pcg_init<double><<<grid, kThreads, 0, s>>>(G, rho, nullptr, ctx->ghost, (double*)B.x,
+                                                 (double*)B.b, (double*)B.r, part, zero_bc, ctl);
+  }
   ++ctx->launches;
-  k_pcg_state_init<<<1, 32 * nrep, 0, s>>>(ctx->pcg, part, nb, ctx->opt.poisson_tol, ctl, nrep);
+  k_pcg_state_init<<<1, 32 * nrep, 0, s>>>(ctx->pcg, part, nb, B.tol, ctl, nrep);
   ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_pcg_init");
-  int rc = vcycle(ctx, ctx->pcg_r, ctx->pcg_z, nrep);
+  int rc = B.f32 ? vcycle(ctx, nullptr, nullptr, (float*)B.r, (float*)B.z, nrep)
+                 : vcycle(ctx, (double*)B.r, (double*)B.z, nullptr, nullptr, nrep);
   if (rc) return rc;
-  k_pcg_rz<<<grid, kThreads, 0, s>>>(Ng, ctx->pcg_r, ctx->pcg_z, ctx->pcg_p, 1, part, ctx->pcg);
+  if (B.f32)
+    k_pcg_rz<float><<<grid, kThreads, 0, s>>>(Ng, (float*)B.r, (float*)B.z, (float*)B.p, 1, part,
+                                              ctx->pcg);
+  else
+    k_pcg_rz<double><<<grid, kThreads, 0, s>>>(Ng, (double*)B.r, (double*)B.z, (double*)B.p, 1,
+                                               part, ctx->pcg);
   ++ctx->launches;
   k_pcg_rz_store<<<1, 32 * nrep, 0, s>>>(ctx->pcg, part, nb, nrep, cond, use_cond);
   ++ctx->launches;
@@ -724,28 +791,47 @@ int hartree_begin(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* c
 // One flexible-CG iteration for every replica still iterating; `cond` is the graph
 // while-handle to update (use_cond = 0 outside a graph).
 int hartree_iteration(rmgtd_ctx* ctx, double* vh, int nrep, cudaGraphConditionalHandle cond,
-                      int use_cond) {
+                      int use_cond, int f32) {
   const Grid3 G{ctx->nx, ctx->ny, ctx->nz, ctx->h};
   const long Ng = ctx->Ng;
   const int nb = ctx->red_blocks;
   const dim3 grid(nb, nrep);
   cudaStream_t s = ctx->stream;
   double* part = ctx->red_part;
-  k_pcg_Ap<<<grid, kThreads, 0, s>>>(G, ctx->pcg_p, ctx->pcg_Ap, part, ctx->pcg);
-  ++ctx->launches;
-  k_pcg_xr<<<grid, kThreads, 0, s>>>(Ng, vh, ctx->pcg_r, ctx->pcg_p, ctx->pcg_Ap, ctx->pcg_z, part,
-                                     ctx->pcg);
-  ++ctx->launches;
-  k_pcg_check<<<1, 32 * nrep, 0, s>>>(ctx->pcg, part, nb, ctx->opt.poisson_tol,
-                                      ctx->opt.poisson_max_iter, nrep, ctx->status);
+  const PcgBufs B = pcg_bufs(ctx, vh, f32);
+  if (B.f32) {
+    k_pcg_Ap<float><<<grid, kThreads, 0, s>>>(G, (float*)B.p, (float*)B.Ap, part, ctx->pcg);
+    ++ctx->launches;
+    k_pcg_xr<float><<<grid, kThreads, 0, s>>>(Ng, (float*)B.x, (float*)B.r, (float*)B.p,
+                                              (float*)B.Ap, (float*)B.z, part, ctx->pcg);
+    ++ctx->launches;
+  } else {
+    k_pcg_Ap<double><<<grid, kThreads, 0, s>>>(G, (double*)B.p, (double*)B.Ap, part, ctx->pcg);
+    ++ctx->launches;
+    k_pcg_xr<double><<<grid, kThreads, 0, s>>>(Ng, (double*)B.x, (double*)B.r, (double*)B.p,
+                                               (double*)B.Ap, (double*)B.z, part, ctx->pcg);
+    ++ctx->launches;
+  }
+  k_pcg_check<<<1, 32 * nrep, 0, s>>>(ctx->pcg, part, nb, B.tol, ctx->opt.poisson_max_iter, nrep,
+                                      ctx->status);
   ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_pcg_iteration");
-  int rc = vcycle(ctx, ctx->pcg_r, ctx->pcg_z, nrep);
+  int rc = B.f32 ? vcycle(ctx, nullptr, nullptr, (float*)B.r, (float*)B.z, nrep)
+                 : vcycle(ctx, (double*)B.r, (double*)B.z, nullptr, nullptr, nrep);
   if (rc) return rc;
-  k_pcg_rz<<<grid, kThreads, 0, s>>>(Ng, ctx->pcg_r, ctx->pcg_z, ctx->pcg_p, 0, part, ctx->pcg);
-  ++ctx->launches;
-  k_pcg_p<<<grid, kThreads, 0, s>>>(Ng, ctx->pcg_z, ctx->pcg_p, part, ctx->pcg);
-  ++ctx->launches;
+  if (B.f32) {
+    k_pcg_rz<float><<<grid, kThreads, 0, s>>>(Ng, (float*)B.r, (float*)B.z, (float*)B.p, 0, part,
+                                              ctx->pcg);
+    ++ctx->launches;
+    k_pcg_p<float><<<grid, kThreads, 0, s>>>(Ng, (float*)B.z, (float*)B.p, part, ctx->pcg);
+    ++ctx->launches;
+  } else {
+    k_pcg_rz<double><<<grid, kThreads, 0, s>>>(Ng, (double*)B.r, (double*)B.z, (double*)B.p, 0,
+                                               part, ctx->pcg);
+    ++ctx->launches;
+    k_pcg_p<double><<<grid, kThreads, 0, s>>>(Ng, (double*)B.z, (double*)B.p, part, ctx->pcg);
+    ++ctx->launches;
+  }
   k_pcg_end<<<1, 32 * nrep, 0, s>>>(ctx->pcg, part, nb, nrep, ctx->pcg_any, cond, use_cond,
                                      ctx->kexec);
   ++ctx->launches;
@@ -755,11 +841,11 @@ int hartree_iteration(rmgtd_ctx* ctx, double* vh, int nrep, cudaGraphConditional
 
 // Eager Hartree solve (host-driven loop, peeking at the convergence flag).
 int hartree_dev(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* ctl, int zero_bc,
-                int nrep) {
-  int rc = hartree_begin(ctx, rho, vh, ctl, zero_bc, nrep, 0, 0);
+                int nrep, int f32) {
+  int rc = hartree_begin(ctx, rho, vh, ctl, zero_bc, nrep, 0, 0, f32);
   if (rc) return rc;
   for (int it = 0; it < ctx->opt.poisson_max_iter; ++it) {
-    rc = hartree_iteration(ctx, vh, nrep, 0, 0);
+    rc = hartree_iteration(ctx, vh, nrep, 0, 0, f32);
     if (rc) return rc;
     if ((it & 3) == 3) {
       RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->pcg_any_host, ctx->pcg_any, sizeof(int),

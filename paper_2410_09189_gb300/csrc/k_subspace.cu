@@ -211,6 +211,158 @@ int rho_dev(rmgtd_ctx* ctx, const double* S, double* rho, const RepCtl* ctl, int
 }
 
 // ---------------------------------------------------------------------------------------
+// Mixed-precision contractions around the float64 reference state (P_ref, V_ref):
+//   rho = rho_ref + sum_ij (S - S_ref)_ij phi_i phi_j      (float32 products and sums)
+//   H   = H_ref + h^3 Phi^T diag(V - V_ref) Phi            (float32 per block, float64 across)
+// Rounding then scales with the perturbation P - P_ref, not with P.
+__global__ void __launch_bounds__(kRhoThreads)
+k_rho32(int N, long Ng, const float* __restrict__ phi, const double* __restrict__ S,
+        const double* __restrict__ Sref, long sstride, const double* __restrict__ rho_ref,
+        double* __restrict__ rho, long rstride, const RepCtl* __restrict__ ctl) {
+  const int rep = blockIdx.y;
+  if (ctl && !ctl[rep].active) return;
+  __shared__ float Sh[kRhoK][kRhoJ];
+  const double* Sr = S + rep * sstride;
+  const long g = blockIdx.x * (long)kRhoThreads + threadIdx.x;
+  const bool ok = g < Ng;
+  float r = 0.0f;
+  for (int jb = 0; jb < N; jb += kRhoJ) {
+    float acc[kRhoJ];
+#pragma unroll
+    for (int jj = 0; jj < kRhoJ; ++jj) acc[jj] = 0.0f;
+    const int kend = min(N, jb + kRhoJ);
+    for (int k0 = 0; k0 < kend; k0 += kRhoK) {
+      __syncthreads();
+      for (int e = threadIdx.x; e < kRhoK * kRhoJ; e += kRhoThreads) {
+        const int kk = e / kRhoJ, jj = e % kRhoJ;
+        const int k = k0 + kk, j = jb + jj;
+        double v = 0.0;
+        if (k < N && j < N) {
+          const long o = (long)k * N + j;
+          if (k < j)
+            v = 2.0 * (Sr[o] - Sref[o]);
+          else if (k == j)
+            v = Sr[o] - Sref[o];
+        }
+        Sh[kk][jj] = (float)v;
+      }
+      __syncthreads();
+      const int kn = min(kRhoK, kend - k0);
+      if (ok) {
+        for (int kk = 0; kk < kn; ++kk) {
+          const float pk = phi[(long)(k0 + kk) * Ng + g];
+#pragma unroll
+          for (int jj = 0; jj < kRhoJ; ++jj) acc[jj] = fmaf(Sh[kk][jj], pk, acc[jj]);
+        }
+      }
+    }
+    if (ok) {
+#pragma unroll
+      for (int jj = 0; jj < kRhoJ; ++jj)
+        if (jb + jj < N) r = fmaf(phi[(long)(jb + jj) * Ng + g], acc[jj], r);
+    }
+  }
+  if (ok) rho[rep * rstride + g] = rho_ref[g] + (double)r;
+}
+
+int rho_dev_mixed(rmgtd_ctx* ctx, const double* S, double* rho, const RepCtl* ctl, int nrep) {
+  dim3 grid(ceil_div(ctx->Ng, kRhoThreads), nrep);
+  k_rho32<<<grid, kRhoThreads, 0, ctx->stream>>>(ctx->N, ctx->Ng, ctx->phi32, S, ctx->Sref,
+                                                  (long)ctx->N * ctx->N, ctx->rho_ref, rho,
+                                                  ctx->Ng, ctl);
+  ++ctx->launches;
+  RMGTD_LAUNCH(ctx, "k_rho32");
+  return RMGTD_OK;
+}
+
+// float32 Gram partials: per block sum_{g in split} phi_i(g) dv(g) phi_j(g), symmetric tiles
+__global__ void __launch_bounds__(256)
+k_gram_partial32(int N, long Ng, const float* __restrict__ A, const float* __restrict__ w,
+                 long wstride, int T, long chunk, double* __restrict__ part,
+                 const RepCtl* __restrict__ ctl) {
+  const int rep = blockIdx.z;
+  if (ctl && !ctl[rep].active) return;
+  __shared__ float As[kGT][kGT + 1];
+  __shared__ float Bs[kGT][kGT + 1];
+  int I, J;
+  pair_from_index(blockIdx.x, T, 1, I, J);
+  const int split = blockIdx.y, nsplit = gridDim.y;
+  const long g_beg = (long)split * chunk;
+  const long g_end = min(Ng, g_beg + chunk);
+  const float* wr = w + rep * wstride;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  float acc00 = 0, acc01 = 0, acc10 = 0, acc11 = 0;
+  for (long g0 = g_beg; g0 < g_end; g0 += kGT) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int idx = tid + 256 * e;
+      const int r = idx >> 5, c = idx & 31;
+      const long g = g0 + c;
+      const int ia = I * kGT + r, jb = J * kGT + r;
+      float av = 0.0f, bv = 0.0f;
+      if (g < g_end) {
+        if (ia < N) av = A[(long)ia * Ng + g];
+        if (jb < N) bv = A[(long)jb * Ng + g] * wr[g];
+      }
+      As[c][r] = av;
+      Bs[c][r] = bv;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int k = 0; k < kGT; ++k) {
+      const float a0 = As[k][ty], a1 = As[k][ty + 16];
+      const float b0 = Bs[k][tx], b1 = Bs[k][tx + 16];
+      acc00 = fmaf(a0, b0, acc00);
+      acc01 = fmaf(a0, b1, acc01);
+      acc10 = fmaf(a1, b0, acc10);
+      acc11 = fmaf(a1, b1, acc11);
+    }
+    __syncthreads();
+  }
+  double* out = part + ((long)rep * nsplit + split) * (long)N * N;
+  const int i0 = I * kGT + ty, i1 = i0 + 16, j0 = J * kGT + tx, j1 = j0 + 16;
+  if (i0 < N && j0 < N) out[(long)i0 * N + j0] = acc00;
+  if (i0 < N && j1 < N) out[(long)i0 * N + j1] = acc01;
+  if (i1 < N && j0 < N) out[(long)i1 * N + j0] = acc10;
+  if (i1 < N && j1 < N) out[(long)i1 * N + j1] = acc11;
+}
+
+int gram_mixed(rmgtd_ctx* ctx, const float* w, long wstride, int nw, double scale,
+               const double* base, double* out, const RepCtl* ctl, unsigned long long* errbits) {
+  const int N = ctx->N;
+  const int T = ceil_div(N, kGT);
+  const int ntiles = T * (T + 1) / 2;
+  const int nsplit = gram_nsplit(ctx, ntiles, nw);
+  const long chunk = ((ctx->Ng + nsplit - 1) / nsplit + kGT - 1) / kGT * kGT;
+  dim3 grid(ntiles, nsplit, nw);
+  k_gram_partial32<<<grid, 256, 0, ctx->stream>>>(N, ctx->Ng, ctx->phi32, w, wstride, T, chunk,
+                                                   ctx->gram_part, ctl);
+  ++ctx->launches;
+  RMGTD_LAUNCH(ctx, "k_gram_partial32");
+  const long NN = (long)N * N;
+  const int rb = (int)std::min<long>(ceil_div(NN, 256), 2L * ctx->num_sms);
+  k_gram_reduce<<<dim3(rb, nw), 256, 0, ctx->stream>>>(N, nsplit, ctx->gram_part, scale, base, out,
+                                                        NN, out, 1, errbits, ctl);
+  ++ctx->launches;
+  RMGTD_LAUNCH(ctx, "k_gram_reduce");
+  return RMGTD_OK;
+}
+
+__global__ void k_to_float(long n, const double* __restrict__ in, float* __restrict__ out) {
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n;
+       e += (long)gridDim.x * blockDim.x)
+    out[e] = (float)in[e];
+}
+
+int to_float(rmgtd_ctx* ctx, const double* in, float* out, long n) {
+  const int blocks = (int)std::max<long>(1, std::min<long>(ceil_div(n, 256), 8L * ctx->num_sms));
+  k_to_float<<<blocks, 256, 0, ctx->stream>>>(n, in, out);
+  ++ctx->launches;
+  RMGTD_LAUNCH(ctx, "k_to_float");
+  return RMGTD_OK;
+}
+
+// ---------------------------------------------------------------------------------------
 // Commutator expansion (Algorithm 1, lines 15-22) in the real split of Eq. 35.  With
 // P = S + iA (S symmetric, A antisymmetric), Hbar real symmetric and Omega = -i tau Hbar:
 //   S_k =  (tau/k) [Hbar, A_{k-1}] = (tau/k) (T1 + T1^T),  T1 = Hbar A_{k-1}

@@ -121,7 +121,12 @@ struct rmgtd_ctx {
   double *rho = nullptr, *vh = nullptr, *vxc = nullptr, *exc = nullptr, *vhxc = nullptr;
   double* rho_ref = nullptr;   // [Ng] density of Sref (mixed)
   double* vref = nullptr;      // [Ng] reference V_Hxc (mixed)
+  double* vh_ref = nullptr;    // [Ng] reference V_H (mixed)
   float* dv32 = nullptr;       // [nrep][Ng] V_Hxc - vref (mixed)
+  float* dvh32 = nullptr;      // [nrep][Ng] V_H - vh_ref (mixed, Hartree correction unknown)
+  float *pcg32_b = nullptr, *pcg32_r = nullptr, *pcg32_z = nullptr, *pcg32_p = nullptr,
+        *pcg32_Ap = nullptr;   // [nrep][Ng] float32 CG vectors (mixed)
+  int mixed = 0;               // mixed-precision step active (after set-up)
 
   // split-K partials of the Gram contractions
   double* gram_part = nullptr;
@@ -293,13 +298,20 @@ int launch_vion(rmgtd_ctx* ctx, const double* pos_dev, const double* Z_dev,
 int build_projectors(rmgtd_ctx* ctx, const rmgtd_system* sys);
 int apply_h_dev(rmgtd_ctx* ctx, const void* x, void* hx, int ncols, int dtype,
                 const double* vextra);
-int launch_lda(rmgtd_ctx* ctx, const double* rho, const double* vh, double* vxc, double* exc,
-               double* vhxc, long n, const RepCtl* ctl, int nrep, long stride, int with_xc);
+// vh_mode: 0 = vh is an input; 1 = vh <- vh_ref + dvh32 (mixed step); 2 = vh is an input
+// and dvh32 <- vh - vh_ref (mixed refresh).  dv32 (if given) <- V_H + V_xc - vref.
+int launch_lda(rmgtd_ctx* ctx, const double* rho, double* vh, int vh_mode, double* vxc,
+               double* exc, double* vhxc, float* dv32, long n, const RepCtl* ctl, int nrep,
+               long stride, int with_xc);
 // k_subspace.cu
 int gram(rmgtd_ctx* ctx, const double* A, const double* B, const double* w, long wstride,
          int nw, double scale, const double* base, double* out, const double* prev,
          const RepCtl* ctl, int sym, unsigned long long* errbits);
 int rho_dev(rmgtd_ctx* ctx, const double* S, double* rho, const RepCtl* ctl, int nrep);
+int rho_dev_mixed(rmgtd_ctx* ctx, const double* S, double* rho, const RepCtl* ctl, int nrep);
+int gram_mixed(rmgtd_ctx* ctx, const float* w, long wstride, int nw, double scale,
+               const double* base, double* out, const RepCtl* ctl, unsigned long long* errbits);
+int to_float(rmgtd_ctx* ctx, const double* in, float* out, long n);
 int eldyn(rmgtd_ctx* ctx, const double* Ha, const double* Hb, long hstride, double tau,
           const double* S0, const double* A0, double* S1, double* A1, const RepCtl* ctl_in,
           RepCtl* ctl_out, int rep0, int nreps);
@@ -313,11 +325,12 @@ int orthonormalize(rmgtd_ctx* ctx);
 // k_poisson.cu
 int setup_multigrid(rmgtd_ctx* ctx);
 int hartree_dev(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* ctl, int zero_bc,
-                int nrep);
-int hartree_graph(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* ctl, int nrep);
+                int nrep, int f32);
+int hartree_graph(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* ctl, int nrep,
+                  int f32);
 int hartree_begin(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* ctl, int zero_bc,
-                  int nrep, cudaGraphConditionalHandle cond, int use_cond);
+                  int nrep, cudaGraphConditionalHandle cond, int use_cond, int f32);
 int hartree_iteration(rmgtd_ctx* ctx, double* vh, int nrep, cudaGraphConditionalHandle cond,
-                      int use_cond);
+                      int use_cond, int f32);
 
 }  // namespace rmgtd

@@ -297,3 +297,79 @@ def test_graph_step_failure_keeps_last_completed_state(torch_dev, small_gs):
             ctx.step(3)
         assert ei.value.code == rmgtd.ENOTCONVERGED
         assert ctx.time() == (0.0, 0)
+
+
+# ---- mixed-precision path: float32 contractions around the float64 reference state ------
+def test_mixed_trajectory_small_system(torch_dev, small_gs):
+    """Mixed path vs the FP64 oracle: the stated target is 1e-4 of the dipole variation."""
+    rmgtd = _rmgtd()
+    s, gs = small_gs
+    nsteps = 40
+    o = tddft.Options(H_thrs=1e-9, dP_thrs=1e-12, poisson_tol=1e-13)
+    orc = tddft.run(s, gs["phi"], o, nsteps=nsteps, axis=2, kappa=s.kappa)
+    with rmgtd.Context(s, gs["phi"], H_thrs=1e-9, dP_thrs=1e-12, orthonormalize=False,
+                       precision=rmgtd.PREC_MIXED) as ctx:
+        ctx.kick(0, 2, s.kappa)
+        d = [ctx.dipole(0)]
+        e = [ctx.energy(0)]
+        for _ in range(nsteps):
+            ctx.step(1)
+            d.append(ctx.dipole(0))
+            e.append(ctx.energy(0))
+        P = ctx.density_matrix(0)
+    d, e = np.array(d), np.array(e)
+    scale = np.max(np.abs(orc["dipole"][:, 2] - orc["dipole"][0, 2]))
+    err = np.max(np.abs(d - orc["dipole"])) / scale
+    assert err < 1e-4, err
+    assert np.max(np.abs(e - orc["energy"])) < 1e-7
+    assert abs(np.trace(P).real - s.n_electrons) < 1e-11
+
+
+def test_mixed_three_kicks_ragged(torch_dev):
+    rmgtd = _rmgtd()
+    s = _ring_small(n=(30, 34, 38), h=0.5, nvirt=22)
+    raw = inputs.smooth_random_orbitals(s).reshape(s.N, s.Ng)
+    phi = oham.orthonormalize(s, raw)
+    nsteps, dt, kap = 5, 0.02, 1e-2
+    o = tddft.Options(dt=dt, H_thrs=1e-9, dP_thrs=1e-12, poisson_tol=1e-13)
+    refs = [tddft.run(s, phi, o, nsteps=nsteps, axis=a, kappa=kap) for a in range(3)]
+    with rmgtd.Context(s, raw, dt=dt, H_thrs=1e-9, dP_thrs=1e-12, nrep=3,
+                       precision=rmgtd.PREC_MIXED) as ctx:
+        for a in range(3):
+            ctx.kick(a, a, kap)
+        d = [[ctx.dipole(a) for a in range(3)]]
+        for _ in range(nsteps):
+            ctx.step(1)
+            d.append([ctx.dipole(a) for a in range(3)])
+    d = np.array(d)
+    for a in range(3):
+        ref = refs[a]["dipole"]
+        scale = np.max(np.abs(ref - ref[0]))
+        assert np.max(np.abs(d[:, a, :] - ref)) / scale < 1e-4
+
+
+def test_mixed_graph_matches_eager_and_resumes_bitwise(torch_dev, small_gs):
+    rmgtd = _rmgtd()
+    s, gs = small_gs
+    kw = dict(H_thrs=1e-9, dP_thrs=1e-12, orthonormalize=False, precision=rmgtd.PREC_MIXED)
+    out = {}
+    for mode in (False, True):
+        with rmgtd.Context(s, gs["phi"], use_graph=mode, **kw) as ctx:
+            ctx.kick(0, 2, 0.01)
+            ctx.step(4)
+            out[mode] = ctx.density_matrix(0)
+    assert np.array_equal(out[False], out[True])
+    with tempfile.TemporaryDirectory() as td:
+        path = os.path.join(td, "ck.bin")
+        with rmgtd.Context(s, gs["phi"], **kw) as a:
+            a.kick(0, 2, 0.01)
+            a.step(2)
+            a.save(path)
+            a.step(2)
+            Pa = a.density_matrix(0)
+        with rmgtd.Context(s, gs["phi"], **kw) as b:
+            b.load(path)
+            b.step(2)
+            Pb = b.density_matrix(0)
+    assert np.array_equal(Pa, Pb)
+    assert np.array_equal(Pa, out[True])
