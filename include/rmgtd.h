@@ -116,6 +116,11 @@ typedef struct {
   rmgtd_alloc_fn alloc;    /* NULL: cudaMalloc */
   rmgtd_free_fn free;      /* NULL: cudaFree */
   void* alloc_user;
+  int subspace_scf;        /* > 0: up to this many SCF iterations inside the orbital block
+                              before t = 0 (P_0 = aufbau projector of H[rho(P_0)], N <= 1024);
+                              0: P_0 = diag(f) (the orbitals are taken as the ground state) */
+  double subspace_mix;     /* linear mixing of P in those iterations (default 0.3) */
+  double subspace_tol;     /* stop when max|P_new - P| <= subspace_tol (default 1e-10) */
 } rmgtd_options;
 
 /* Per-step, per-replica statistics written by rmgtd_step. */

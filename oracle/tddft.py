@@ -153,10 +153,35 @@ class Propagator:
         return e + self.E_ion
 
     # --- driver ----------------------------------------------------------------------
-    def initial_state(self):
+    def subspace_ground_state(self, iters: int, mix: float = 0.3, tol: float = 1e-10):
+        """SCF inside the orbital block: P <- (1-mix) P + mix P_aufbau(H[rho(P)]).
+
+        P_aufbau = sum_n f_n w_n w_n^T over the eigenvectors of H in ascending order
+        (scipy eigh), i.e. the ground-state density matrix of Algorithm 1 lines 1-3 restricted
+        to the active space.  Returns (P, H, aux, iterations, last max|P_new - P|).
+        """
         f = self.sys.occupations
-        P0 = np.diag(f).astype(np.complex128)
-        H0, aux = self.dft(P0)
+        P = np.diag(f).astype(np.float64)
+        H, aux = self.dft(P)
+        err, it = np.inf, 0
+        for it in range(1, iters + 1):
+            w, W = _eigh(H)
+            Pn = (W * f) @ W.T
+            err = float(np.max(np.abs(Pn - P)))
+            P = (1.0 - mix) * P + mix * Pn
+            H, aux = self.dft(P)
+            if err <= tol:
+                break
+        return P, H, aux, it, err
+
+    def initial_state(self, subspace_scf: int = 0, mix: float = 0.3, tol: float = 1e-10):
+        if subspace_scf > 0:
+            P, H0, aux, _, _ = self.subspace_ground_state(subspace_scf, mix, tol)
+            P0 = P.astype(np.complex128)
+        else:
+            f = self.sys.occupations
+            P0 = np.diag(f).astype(np.complex128)
+            H0, aux = self.dft(P0)
         return {"P0": P0, "H0": H0, "Hm1": H0.copy(), "aux": aux, "t": 0.0, "j": 0}
 
     def step(self, st):
@@ -181,10 +206,10 @@ class Propagator:
 
 
 def run(sys, phi, opts: Optional[Options] = None, nsteps: int = 10, axis: int = 2,
-        kappa: Optional[float] = None):
+        kappa: Optional[float] = None, subspace_scf: int = 0, subspace_mix: float = 0.3):
     """Kick along `axis` and propagate; returns per-step dipole, energy, trace, stats."""
     pr = Propagator(sys, phi, opts)
-    st = pr.initial_state()
+    st = pr.initial_state(subspace_scf, subspace_mix)
     kap = sys.kappa if kappa is None else kappa
     out = {"dipole_gs": pr.dipole(st["P0"]), "energy_gs": pr.energy(st["P0"], st["aux"])}
     if kap != 0.0:

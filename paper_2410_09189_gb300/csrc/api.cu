@@ -304,6 +304,9 @@ void rmgtd_default_options(rmgtd_options* o) {
   o->poisson_tol = 1e-12;
   o->poisson_max_iter = 200;
   o->use_graph = 1;
+  o->subspace_scf = 0;
+  o->subspace_mix = 0.3;
+  o->subspace_tol = 1e-10;
 }
 
 const char* rmgtd_last_error(const rmgtd_ctx* ctx) {
@@ -504,6 +507,24 @@ static int create_impl(const rmgtd_system* sys, const rmgtd_options* opt, rmgtd_
   ++ctx->launches;
   rc = dft_eval(ctx, ctx->S0, ctx->ctl, nullptr);
   if (rc) return rc;
+  if (opt->subspace_scf > 0) {
+    // SCF inside the orbital block: P <- mix(P, aufbau(H[rho(P)])) until stationary
+    double* err_d = (double*)A(sizeof(double) * nrep);
+    if (!err_d) return set_error(ctx, RMGTD_ENOMEM, "subspace SCF");
+    std::vector<double> err_h(nrep);
+    for (int it = 0; it < opt->subspace_scf; ++it) {
+      rc = subspace_update(ctx, opt->subspace_mix, err_d);
+      if (rc) return rc;
+      rc = dft_eval(ctx, ctx->S0, ctx->ctl, nullptr);
+      if (rc) return rc;
+      RMGTD_CUDA(ctx, cudaMemcpyAsync(err_h.data(), err_d, sizeof(double) * nrep,
+                                      cudaMemcpyDeviceToHost, ctx->stream));
+      RMGTD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+      ctx->subspace_iters = it + 1;
+      ctx->subspace_err = *std::max_element(err_h.begin(), err_h.end());
+      if (ctx->subspace_err <= opt->subspace_tol) break;
+    }
+  }
   RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->H0, ctx->H1, msz * nrep, cudaMemcpyDeviceToDevice, ctx->stream));
   RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->Hm1, ctx->H1, msz * nrep, cudaMemcpyDeviceToDevice, ctx->stream));
   RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->S1, ctx->S0, msz * nrep, cudaMemcpyDeviceToDevice, ctx->stream));

@@ -853,6 +853,140 @@ int observables(rmgtd_ctx* ctx) {
 }
 
 // ---------------------------------------------------------------------------------------
+// Subspace ground state (set-up): one SCF update of the density matrix inside the orbital
+// block.  H (float64, per replica) is diagonalised by parallel cyclic Jacobi rotations
+// (round-robin pairing: N/2 disjoint rotations per round, applied to rows, then columns),
+// the aufbau density matrix P_new = sum_n f_n w_n w_n^T of the ascending eigenvectors is
+// formed, max|P_new - P| is recorded and P <- (1 - alpha) P + alpha P_new.  One block per
+// replica; work arrays in global memory (set-up only).
+__global__ void __launch_bounds__(1024)
+k_subspace_update(int N, const double* __restrict__ H, double* __restrict__ S,
+                  const double* __restrict__ f, double alpha, double* __restrict__ work,
+                  double* __restrict__ err) {
+  const int rep = blockIdx.x;
+  const long NN = (long)N * N;
+  const double* Hr = H + rep * NN;
+  double* Sr = S + rep * NN;
+  double* A = work + (long)rep * 3 * NN;
+  double* V = A + NN;
+  double* Pn = V + NN;
+  __shared__ int pp[512], qq[512];
+  __shared__ double cc[512], ss[512];
+  __shared__ double sh[32];
+  __shared__ int ord[1024];
+  __shared__ double stop;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (long e = tid; e < NN; e += nt) {
+    A[e] = Hr[e];
+    V[e] = ((e / N) == (e % N)) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  const int n2 = N + (N & 1);
+  const int np = n2 / 2;
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (long e = tid; e < NN; e += nt) {
+      const double a = A[e];
+      tot += a * a;
+      if ((e / N) != (e % N)) off += a * a;
+    }
+    off = block_sum(off, sh);
+    __syncthreads();
+    tot = block_sum(tot, sh);
+    if (tid == 0) stop = (off <= 1e-28 * tot) ? 1.0 : 0.0;
+    __syncthreads();
+    if (stop != 0.0) break;
+    for (int r = 0; r < n2 - 1; ++r) {
+      for (int i = tid; i < np; i += nt) {
+        const int a0 = (i == 0) ? 0 : ((i - 1 + r) % (n2 - 1)) + 1;
+        const int b0 = ((n2 - 2 - i + r) % (n2 - 1)) + 1;
+        int p = min(a0, b0), q = max(a0, b0);
+        double c = 1.0, sn = 0.0;
+        if (q < N) {
+          const double apq = A[(long)p * N + q];
+          if (fabs(apq) > 1e-300) {
+            const double tau = (A[(long)q * N + q] - A[(long)p * N + p]) / (2.0 * apq);
+            double t;
+            if (fabs(tau) > 1e150)
+              t = 0.5 / tau;
+            else
+              t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            c = 1.0 / sqrt(1.0 + t * t);
+            sn = t * c;
+          }
+        } else {
+          p = q = -1;
+        }
+        pp[i] = p;
+        qq[i] = q;
+        cc[i] = c;
+        ss[i] = sn;
+      }
+      __syncthreads();
+      for (long e = tid; e < (long)np * N; e += nt) {  // rows: A <- J^T A
+        const int i = (int)(e / N), k = (int)(e % N);
+        const int p = pp[i], q = qq[i];
+        if (p < 0) continue;
+        const double ap = A[(long)p * N + k], aq = A[(long)q * N + k];
+        A[(long)p * N + k] = cc[i] * ap - ss[i] * aq;
+        A[(long)q * N + k] = ss[i] * ap + cc[i] * aq;
+      }
+      __syncthreads();
+      for (long e = tid; e < (long)np * N; e += nt) {  // columns: A <- A J, V <- V J
+        const int i = (int)(e / N), k = (int)(e % N);
+        const int p = pp[i], q = qq[i];
+        if (p < 0) continue;
+        const double ap = A[(long)k * N + p], aq = A[(long)k * N + q];
+        A[(long)k * N + p] = cc[i] * ap - ss[i] * aq;
+        A[(long)k * N + q] = ss[i] * ap + cc[i] * aq;
+        const double vp = V[(long)k * N + p], vq = V[(long)k * N + q];
+        V[(long)k * N + p] = cc[i] * vp - ss[i] * vq;
+        V[(long)k * N + q] = ss[i] * vp + cc[i] * vq;
+      }
+      __syncthreads();
+    }
+  }
+  if (tid == 0) {  // ascending eigenvalue order (insertion sort, N <= 1024)
+    for (int i = 0; i < N; ++i) ord[i] = i;
+    for (int i = 1; i < N; ++i) {
+      const int o = ord[i];
+      const double d = A[(long)o * N + o];
+      int j = i - 1;
+      while (j >= 0 && A[(long)ord[j] * N + ord[j]] > d) {
+        ord[j + 1] = ord[j];
+        --j;
+      }
+      ord[j + 1] = o;
+    }
+  }
+  __syncthreads();
+  double emax = 0.0;
+  for (long e = tid; e < NN; e += nt) {
+    const int i = (int)(e / N), j = (int)(e % N);
+    double v = 0.0;
+    for (int n = 0; n < N; ++n) {
+      const double fn = f[n];
+      if (fn != 0.0) v += fn * V[(long)i * N + ord[n]] * V[(long)j * N + ord[n]];
+    }
+    Pn[e] = v;
+    emax = fmax(emax, fabs(v - Sr[e]));
+  }
+  emax = block_max(emax, sh);
+  if (tid == 0) err[rep] = emax;
+  __syncthreads();
+  for (long e = tid; e < NN; e += nt) Sr[e] = (1.0 - alpha) * Sr[e] + alpha * Pn[e];
+}
+
+int subspace_update(rmgtd_ctx* ctx, double alpha, double* err_dev) {
+  if (ctx->N > 1024) return set_error(ctx, RMGTD_EINVAL, "subspace ground state needs N <= 1024");
+  k_subspace_update<<<ctx->nrep, 1024, 0, ctx->stream>>>(ctx->N, ctx->H1, ctx->S0, ctx->f_dev,
+                                                         alpha, ctx->dbuf, err_dev);
+  ++ctx->launches;
+  RMGTD_LAUNCH(ctx, "k_subspace_update");
+  return RMGTD_OK;
+}
+
+// ---------------------------------------------------------------------------------------
 // Orthonormalisation of the starting orbitals: S = h^3 Phi^T Phi = L L^T (Cholesky, one
 // block, float64), then Phi <- L^{-1} Phi by forward substitution at every grid point.
 __global__ void k_cholesky(int N, double* __restrict__ S, int* status) {

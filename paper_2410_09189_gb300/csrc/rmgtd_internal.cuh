@@ -127,6 +127,8 @@ struct rmgtd_ctx {
   float *pcg32_b = nullptr, *pcg32_r = nullptr, *pcg32_z = nullptr, *pcg32_p = nullptr,
         *pcg32_Ap = nullptr;   // [nrep][Ng] float32 CG vectors (mixed)
   int mixed = 0;               // mixed-precision step active (after set-up)
+  int subspace_iters = 0;      // subspace SCF iterations done at set-up
+  double subspace_err = 0;     // last max|P_new - P| of the subspace SCF
 
   // split-K partials of the Gram contractions
   double* gram_part = nullptr;
@@ -321,6 +323,7 @@ int scf_control(rmgtd_ctx* ctx, const unsigned long long* errbits,
 // launches counted while the SCF body was captured, minus the Hartree-iteration body
 int step_end(rmgtd_ctx* ctx);
 int observables(rmgtd_ctx* ctx);
+int subspace_update(rmgtd_ctx* ctx, double alpha, double* err_dev);
 int orthonormalize(rmgtd_ctx* ctx);
 // k_poisson.cu
 int setup_multigrid(rmgtd_ctx* ctx);

@@ -57,6 +57,8 @@ class COptions(ctypes.Structure):
         ("poisson_tol", ctypes.c_double), ("poisson_max_iter", ctypes.c_int),
         ("use_graph", ctypes.c_int), ("stream", ctypes.c_void_p),
         ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", ctypes.c_void_p),
+        ("subspace_scf", ctypes.c_int), ("subspace_mix", ctypes.c_double),
+        ("subspace_tol", ctypes.c_double),
     ]
 
 
@@ -124,7 +126,8 @@ class Context:
                  max_terms: int = 200, precision: int = PREC_FP64, nrep: int = 1,
                  orthonormalize: bool = True, poisson_tol: float = 1e-12,
                  poisson_max_iter: int = 200, use_graph: bool = True,
-                 stream: Optional[int] = None, torch_alloc: bool = True):
+                 stream: Optional[int] = None, torch_alloc: bool = True,
+                 subspace_scf: int = 0, subspace_mix: float = 0.3, subspace_tol: float = 1e-10):
         import torch
 
         lib = load_library()
@@ -171,6 +174,8 @@ class Context:
         opt.orthonormalize = 1 if orthonormalize else 0
         opt.poisson_tol, opt.poisson_max_iter = float(poisson_tol), int(poisson_max_iter)
         opt.use_graph = 1 if use_graph else 0
+        opt.subspace_scf, opt.subspace_mix = int(subspace_scf), float(subspace_mix)
+        opt.subspace_tol = float(subspace_tol)
         if stream is None:
             stream = torch.cuda.current_stream().cuda_stream
         self.stream = int(stream)

@@ -373,3 +373,23 @@ def test_mixed_graph_matches_eager_and_resumes_bitwise(torch_dev, small_gs):
             Pb = b.density_matrix(0)
     assert np.array_equal(Pa, Pb)
     assert np.array_equal(Pa, out[True])
+
+
+def test_subspace_ground_state_matches_oracle(torch_dev):
+    """Set-up SCF inside the orbital block (Jacobi eigensolver on the GPU, eigh in the
+    oracle): same stationary P_0 and H_0; a step without a kick leaves P_0 in place."""
+    rmgtd = _rmgtd()
+    s = _ring_small(n=(30, 34, 38), h=0.5, nvirt=22)
+    raw = inputs.smooth_random_orbitals(s).reshape(s.N, s.Ng)
+    phi = oham.orthonormalize(s, raw)
+    pr = tddft.Propagator(s, phi, tddft.Options(poisson_tol=1e-13, H_thrs=1e-9))
+    P, H, _, it, err = pr.subspace_ground_state(300, 0.3, 1e-10)
+    assert err <= 1e-10
+    for prec in (rmgtd.PREC_FP64, rmgtd.PREC_MIXED):
+        with rmgtd.Context(s, raw, poisson_tol=1e-13, subspace_scf=300, H_thrs=1e-9,
+                           precision=prec, nrep=2) as ctx:
+            for rep in range(2):
+                assert np.max(np.abs(ctx.get_matrix(rmgtd.MAT_P_RE, rep) - P)) < 1e-8
+                assert np.max(np.abs(ctx.get_matrix(rmgtd.MAT_H0, rep) - H)) < 1e-8
+            ctx.step(2)
+            assert np.max(np.abs(ctx.density_matrix(0) - P)) < 1e-7

@@ -142,3 +142,24 @@ def test_trk_slope_complete_basis():
     trk = np.trace(P0 @ dc)
     assert abs(slope + kappa * trk) < 1e-5 * kappa * abs(trk)
     assert abs(trk / s.n_electrons - 1.0) < 2e-2
+
+
+def test_subspace_ground_state_is_stationary_projector():
+    """Subspace SCF: the result is idempotent, commutes with its own H, and with independent
+    electrons one undamped iteration is exactly the eigh projector."""
+    s = inputs.scaled(inputs.ring(), n=24, h=0.7, nvirt=10)
+    raw = inputs.smooth_random_orbitals(s).reshape(s.N, s.Ng)
+    phi = ham.orthonormalize(s, raw)
+    pr = tddft.Propagator(s, phi, tddft.Options(poisson_tol=1e-13))
+    P, H, _, it, err = pr.subspace_ground_state(200, 0.3, 1e-10)
+    assert err <= 1e-10 and it < 200
+    Q = P / 2
+    assert np.max(np.abs(Q @ Q - Q)) < 1e-9
+    assert np.max(np.abs(H @ P - P @ H)) < 1e-8
+    assert abs(np.trace(P) - s.n_electrons) < 1e-10
+    h = inputs.harmonic(n=16, h=0.6, omega=0.8, nvirt=4)
+    rawh = inputs.smooth_random_orbitals(h).reshape(h.N, h.Ng)
+    prh = tddft.Propagator(h, ham.orthonormalize(h, rawh), tddft.Options())
+    P1, H1, _, _, _ = prh.subspace_ground_state(1, 1.0, 0.0)
+    w, W = np.linalg.eigh(prh.Hcore)
+    assert np.max(np.abs(P1 - 2.0 * np.outer(W[:, 0], W[:, 0]))) < 1e-12
