@@ -215,7 +215,7 @@ def run_ours(args):
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB
     stream = torch.cuda.current_stream()
 
-    def timed_steps(ctx, nsteps, profile):
+    def timed_steps(ctx, nsteps, profile, nvtx_name="rmgtd_other"):
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(nsteps)]
         if profile:
@@ -225,11 +225,13 @@ def run_ours(args):
         torch.cuda.synchronize()
         w0 = time.perf_counter()
         st = []
+        torch.cuda.nvtx.range_push(nvtx_name)
         for i in range(nsteps):
             flush.zero_()
             ev[i][0].record(stream)
             st.append(ctx.step(1))
             ev[i][1].record(stream)
+        torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
@@ -246,7 +248,8 @@ def run_ours(args):
         smp = ClockSampler(local)
         if with_clocks:
             smp.start()
-        ms, stt, wl, prof = timed_steps(c, nsteps, profile=True)
+        ms, stt, wl, prof = timed_steps(c, nsteps, profile=True,
+                                        nvtx_name="rmgtd_timed" if with_clocks else "rmgtd_other")
         clk = smp.stop() if with_clocks else None
         c.close()
         tot = float(sum(ms))
@@ -276,7 +279,8 @@ def run_ours(args):
         pctx.kick(a, a, s.kappa)
     for _ in range(args.warmup):
         pctx.step(1)
-    p_ms, p_st, _, (phase_ms, phase_calls, _) = timed_steps(pctx, args.steps, profile=True)
+    p_ms, p_st, _, (phase_ms, phase_calls, _) = timed_steps(pctx, args.steps, profile=True,
+                                                            nvtx_name="rmgtd_host_driven")
     pctx.close()
     p_rep_passes = int(p_st["passes"].sum())
     p_terms = int(p_st["terms_sum"].sum())

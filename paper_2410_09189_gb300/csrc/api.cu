@@ -264,10 +264,12 @@ int refresh_fields(rmgtd_ctx* ctx) {
     rc = hartree_dev(ctx, ctx->rho, ctx->vh, nullptr, 0, ctx->nrep, 0);
     if (rc) return rc;
   }
-  return launch_lda(ctx, ctx->rho, ctx->hartree_xc ? ctx->vh : nullptr,
-                    (ctx->mixed && ctx->hartree_xc) ? 2 : 0, ctx->vxc, ctx->exc, ctx->vhxc,
-                    ctx->mixed ? ctx->dv32 : nullptr, ctx->Ng, nullptr, ctx->nrep, ctx->Ng,
-                    ctx->hartree_xc);
+  rc = launch_lda(ctx, ctx->rho, ctx->hartree_xc ? ctx->vh : nullptr,
+                  (ctx->mixed && ctx->hartree_xc) ? 2 : 0, ctx->vxc, ctx->exc, ctx->vhxc,
+                  ctx->mixed ? ctx->dv32 : nullptr, ctx->Ng, nullptr, ctx->nrep, ctx->Ng,
+                  ctx->hartree_xc);
+  if (rc) return rc;
+  return hartree_reset_history(ctx);
 }
 
 static int check_status(rmgtd_ctx* ctx, const char* where) {
@@ -363,7 +365,8 @@ static int create_impl(const rmgtd_system* sys, const rmgtd_options* opt, rmgtd_
   ctx->num_sms = prop.multiProcessorCount;
   ctx->coop_ok = prop.cooperativeLaunch;
   if (!ctx->coop_ok) return set_error(ctx, RMGTD_ECUDA, "device lacks cooperative launch");
-  ctx->red_blocks = 2 * ctx->num_sms;
+  // blocks of the grid-stride reduction kernels: about one point per thread up to 2048
+  ctx->red_blocks = (int)std::max<long>(1, std::min<long>(2048, rmgtd::ceil_div(ctx->Ng, kThreads)));
 
   ctx->f.assign(N, 0.0);
   for (int i = 0; i < N; ++i) ctx->f[i] = sys->f ? sys->f[i] : (i < sys->nocc ? 2.0 : 0.0);
@@ -386,6 +389,7 @@ static int create_impl(const rmgtd_system* sys, const rmgtd_options* opt, rmgtd_
   ctx->dbuf = (double*)A(4 * msz * nrep);
   ctx->rho = (double*)A(gsz * nrep);
   ctx->vh = (double*)A(gsz * nrep);
+  ctx->vh_prev = (double*)A(gsz * nrep);
   ctx->vxc = (double*)A(gsz * nrep);
   ctx->exc = (double*)A(gsz * nrep);
   ctx->vhxc = (double*)A(gsz * nrep);
@@ -542,6 +546,11 @@ static int create_impl(const rmgtd_system* sys, const rmgtd_options* opt, rmgtd_
     ctx->vh_ref = (double*)A(gsz);
     ctx->dv32 = (float*)A(fsz * nrep);
     ctx->dvh32 = (float*)A(fsz * nrep);
+    ctx->dvh_prev32 = (float*)A(fsz * nrep);
+    {
+      const long Np = ((N + 31) / 32) * 32;
+      ctx->shat32 = (float*)A(sizeof(float) * Np * Np * nrep);
+    }
     ctx->pcg32_b = (float*)A(fsz * nrep);
     ctx->pcg32_r = (float*)A(fsz * nrep);
     ctx->pcg32_z = (float*)A(fsz * nrep);
@@ -560,6 +569,8 @@ static int create_impl(const rmgtd_system* sys, const rmgtd_options* opt, rmgtd_
     RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->dv32, 0, fsz * nrep, ctx->stream));
     ctx->mixed = 1;
   }
+  rc = hartree_reset_history(ctx);
+  if (rc) return rc;
   return check_status(ctx, "create");
 }
 
@@ -659,6 +670,7 @@ static int build_step_graph(rmgtd_ctx* ctx) {
   ctx->capturing = 1;
   const long long saved_launches = ctx->launches;
   int rc = step_begin(ctx);
+  if (!rc) rc = hartree_extrapolate(ctx);
   cudaGraphConditionalHandle hs = 0;
   cudaGraph_t body = nullptr;
   if (!rc) rc = new_handle(ctx, &hs, true);
@@ -680,7 +692,7 @@ static int build_step_graph(rmgtd_ctx* ctx) {
     }
   }
   if (!rc) rc = step_end(ctx);
-  ctx->cap_top = 2;  // step_begin, step_end
+  ctx->cap_top = ctx->hartree_xc ? 3 : 2;  // step_begin, [extrapolation], step_end
   ctx->launches = saved_launches;
   ctx->capturing = 0;
   cudaGraph_t g = nullptr;
@@ -699,6 +711,7 @@ static int build_step_graph(rmgtd_ctx* ctx) {
 // Eager step: the host reads the control blocks after every pass.
 static int eager_step(rmgtd_ctx* ctx) {
   int rc = step_begin(ctx);
+  if (!rc) rc = hartree_extrapolate(ctx);
   if (rc) return rc;
   for (int pass = 0; pass < ctx->opt.max_scf; ++pass) {
     rc = enqueue_pass(ctx, 0, 0);
@@ -948,10 +961,17 @@ int rmgtd_save(rmgtd_ctx* ctx, const char* path) {
   bool ok = fwrite(&kMagic, sizeof(kMagic), 1, fp) == 1 && fwrite(hdr, sizeof(hdr), 1, fp) == 1 &&
             fwrite(&ctx->t, sizeof(double), 1, fp) == 1 &&
             fwrite(buf.data(), sizeof(double), buf.size(), fp) == buf.size();
+  if (ok) {
+    std::vector<double> vp(gcount);
+    RMGTD_CUDA(ctx, cudaMemcpy(vp.data(), ctx->vh_prev, sizeof(double) * gcount, cudaMemcpyDeviceToHost));
+    ok = fwrite(vp.data(), sizeof(double), gcount, fp) == gcount;
+  }
   if (ok && ctx->mixed) {
-    std::vector<float> d32(gcount);
+    std::vector<float> d32(2 * gcount);
     RMGTD_CUDA(ctx, cudaMemcpy(d32.data(), ctx->dvh32, sizeof(float) * gcount, cudaMemcpyDeviceToHost));
-    ok = fwrite(d32.data(), sizeof(float), gcount, fp) == gcount;
+    RMGTD_CUDA(ctx, cudaMemcpy(d32.data() + gcount, ctx->dvh_prev32, sizeof(float) * gcount,
+                               cudaMemcpyDeviceToHost));
+    ok = fwrite(d32.data(), sizeof(float), 2 * gcount, fp) == 2 * gcount;
   }
   fclose(fp);
   if (!ok) return set_error(ctx, RMGTD_EINVAL, "save: write failed");
@@ -977,15 +997,21 @@ int rmgtd_load(rmgtd_ctx* ctx, const char* path) {
   const size_t mcount = (size_t)NN * ctx->nrep, gcount = (size_t)ctx->Ng * ctx->nrep;
   std::vector<double> buf(4 * mcount + gcount);
   ok = fread(buf.data(), sizeof(double), buf.size(), fp) == buf.size();
+  std::vector<double> vp(gcount);
+  if (ok) ok = fread(vp.data(), sizeof(double), gcount, fp) == gcount;
   std::vector<float> d32;
   if (ok && ctx->mixed) {
-    d32.resize(gcount);
-    ok = fread(d32.data(), sizeof(float), gcount, fp) == gcount;
+    d32.resize(2 * gcount);
+    ok = fread(d32.data(), sizeof(float), 2 * gcount, fp) == 2 * gcount;
   }
   fclose(fp);
   if (!ok) return set_error(ctx, RMGTD_EINVAL, "load: truncated checkpoint");
-  if (ctx->mixed)
+  RMGTD_CUDA(ctx, cudaMemcpy(ctx->vh_prev, vp.data(), sizeof(double) * gcount, cudaMemcpyHostToDevice));
+  if (ctx->mixed) {
     RMGTD_CUDA(ctx, cudaMemcpy(ctx->dvh32, d32.data(), sizeof(float) * gcount, cudaMemcpyHostToDevice));
+    RMGTD_CUDA(ctx, cudaMemcpy(ctx->dvh_prev32, d32.data() + gcount, sizeof(float) * gcount,
+                               cudaMemcpyHostToDevice));
+  }
   double* parts[4] = {ctx->S0, ctx->A0, ctx->H0, ctx->Hm1};
   for (int i = 0; i < 4; ++i)
     RMGTD_CUDA(ctx, cudaMemcpyAsync(parts[i], buf.data() + i * mcount, sizeof(double) * mcount,

@@ -357,27 +357,46 @@ int apply_h_dev(rmgtd_ctx* ctx, const void* x, void* hx, int ncols, int dtype,
 
 // ---------------------------------------------------------------------------------------
 // LDA (Slater exchange + Perdew-Zunger 1981 correlation, spin-unpolarised), float64.
+// The roots and the reciprocal are Newton iterations in float64 seeded from float32:
+//   z = rho^(-1/3):   z <- z (4 - rho z^3) / 3        (two steps from rcbrtf)
+//   u = r_s^(-1/2):   u <- u (3 - r_s u^2) / 2        (two steps from rsqrtf)
+//   q = 1/den:        q <- q (2 - den q)              (two steps from 1/float)
+// each step squares the relative error, so two steps from ~1e-7 reach float64 rounding.
+// Then rho^(1/3) = rho z^2, r_s = (3/(4 pi))^(1/3) z, 1/r_s = rho z^2 / (3/(4 pi))^(1/3).
 __device__ __forceinline__ void lda_point(double rho, double& vxc, double& exc) {
   if (!(rho >= kRhoFloor)) {
     vxc = 0.0;
     exc = 0.0;
     return;
   }
-  const double t = cbrt(3.0 * rho / 3.14159265358979323846);
+  constexpr double kC3pi = 0.98474502184269641;   // (3/pi)^(1/3)
+  constexpr double kCrs = 0.62035049089940009;    // (3/(4 pi))^(1/3)
+  double z = (double)rcbrtf((float)rho);
+  z = z * (4.0 - rho * z * z * z) * (1.0 / 3.0);
+  z = z * (4.0 - rho * z * z * z) * (1.0 / 3.0);
+  const double c13 = rho * z * z;                 // rho^(1/3)
+  const double t = kC3pi * c13;
   const double ex = -0.75 * t, vx = -t;
-  const double rs = cbrt(3.0 / (4.0 * 3.14159265358979323846 * rho));
+  const double rs = kCrs * z;
   double ec, dec;
   if (rs >= 1.0) {
-    const double sq = sqrt(rs);
+    double u = (double)rsqrtf((float)rs);
+    u = u * (3.0 - rs * u * u) * 0.5;
+    u = u * (3.0 - rs * u * u) * 0.5;
+    const double sq = rs * u;                     // sqrt(r_s)
     const double den = 1.0 + 1.0529 * sq + 0.3334 * rs;
-    ec = -0.1423 / den;
-    dec = 0.1423 * (0.5 * 1.0529 / sq + 0.3334) / (den * den);
+    double q = (double)(1.0f / (float)den);
+    q = q * (2.0 - den * q);
+    q = q * (2.0 - den * q);
+    ec = -0.1423 * q;
+    dec = 0.1423 * (0.5 * 1.0529 * u + 0.3334) * q * q;
   } else {
     const double lr = log(rs);
+    const double irs = c13 * (1.0 / kCrs);        // 1 / r_s
     ec = 0.0311 * lr - 0.048 + 0.0020 * rs * lr - 0.0116 * rs;
-    dec = 0.0311 / rs + 0.0020 * (lr + 1.0) - 0.0116;
+    dec = 0.0311 * irs + 0.0020 * (lr + 1.0) - 0.0116;
   }
-  vxc = vx + ec - rs / 3.0 * dec;
+  vxc = vx + ec - rs * (1.0 / 3.0) * dec;
   exc = ex + ec;
 }
 

@@ -408,6 +408,49 @@ __global__ void k_mg_jacobi(Grid3 G, const float* __restrict__ xi, float* __rest
   }
 }
 
+// Two damped-Jacobi sweeps from x = 0 in one pass: x1 = c b, x2 = x1 + c (b - A x1) with
+// c = w h^2/6, i.e. x2 = c (2 b - c A b); reads b at the 7-point neighbourhood.  b64: the
+// fine-level float64 residual, also stored as float into bf.
+__global__ void k_mg_pre2(Grid3 G, float* __restrict__ xo, float* __restrict__ bf,
+                          const double* __restrict__ b64, const PcgState* __restrict__ st) {
+  const int rep = blockIdx.y;
+  if (pcg_skip(st, rep)) return;
+  const long n = (long)G.nx * G.ny * G.nz;
+  const float h2 = (float)(G.h * G.h), ih2 = 1.0f / h2;
+  const float c = kJacobiW * h2 / 6.0f;
+  const long plane = (long)G.nx * G.ny;
+  for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < n;
+       g += (long)gridDim.x * blockDim.x) {
+    const int ix = (int)(g % G.nx), iy = (int)((g / G.nx) % G.ny), iz = (int)(g / plane);
+    const long e = rep * n + g;
+    float bc, s;
+    if (b64) {
+      const double* b = b64 + rep * n;
+      bc = (float)b[g];
+      s = 0.0f;
+      if (ix + 1 < G.nx) s += (float)b[g + 1];
+      if (ix > 0) s += (float)b[g - 1];
+      if (iy + 1 < G.ny) s += (float)b[g + G.nx];
+      if (iy > 0) s += (float)b[g - G.nx];
+      if (iz + 1 < G.nz) s += (float)b[g + plane];
+      if (iz > 0) s += (float)b[g - plane];
+      bf[e] = bc;
+    } else {
+      const float* b = bf + rep * n;
+      bc = b[g];
+      s = 0.0f;
+      if (ix + 1 < G.nx) s += b[g + 1];
+      if (ix > 0) s += b[g - 1];
+      if (iy + 1 < G.ny) s += b[g + G.nx];
+      if (iy > 0) s += b[g - G.nx];
+      if (iz + 1 < G.nz) s += b[g + plane];
+      if (iz > 0) s += b[g - plane];
+    }
+    const float Ab = (6.0f * bc - s) * ih2;
+    xo[e] = c * (2.0f * bc - c * Ab);
+  }
+}
+
 __global__ void k_mg_residual(Grid3 G, const float* __restrict__ x, const float* __restrict__ b,
                               float* __restrict__ r, const PcgState* __restrict__ st) {
   const int rep = blockIdx.y;
@@ -475,6 +518,37 @@ __device__ __forceinline__ float prolong_point(const float* __restrict__ xc, int
                 wy1 * (wx0 * at(x0, y1, z1) + wx1 * at(x1, y1, z1)));
 }
 
+// x <- x + P xc, then one damped-Jacobi sweep on the corrected x, in one pass: the
+// corrected values of the 6 neighbours are formed on the fly.  Result into xo.
+__global__ void k_mg_prolong_sweep(Grid3 F, Grid3 C, const float* __restrict__ xc,
+                                   const float* __restrict__ x, float* __restrict__ xo,
+                                   const float* __restrict__ b, const PcgState* __restrict__ st) {
+  const int rep = blockIdx.y;
+  if (pcg_skip(st, rep)) return;
+  const long nf = (long)F.nx * F.ny * F.nz, nc = (long)C.nx * C.ny * C.nz;
+  const float* xcr = xc + rep * nc;
+  const float* xr = x + rep * nf;
+  const float h2 = (float)(F.h * F.h);
+  const long plane = (long)F.nx * F.ny;
+  for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < nf;
+       g += (long)gridDim.x * blockDim.x) {
+    const int fx = (int)(g % F.nx), fy = (int)((g / F.nx) % F.ny), fz = (int)(g / plane);
+    auto corr = [&](int ax, int ay, int az, long gg) {
+      return xr[gg] + prolong_point(xcr, ax, ay, az, C.nx, C.ny, C.nz);
+    };
+    const float c0 = corr(fx, fy, fz, g);
+    float s = 0.0f;
+    if (fx + 1 < F.nx) s += corr(fx + 1, fy, fz, g + 1);
+    if (fx > 0) s += corr(fx - 1, fy, fz, g - 1);
+    if (fy + 1 < F.ny) s += corr(fx, fy + 1, fz, g + F.nx);
+    if (fy > 0) s += corr(fx, fy - 1, fz, g - F.nx);
+    if (fz + 1 < F.nz) s += corr(fx, fy, fz + 1, g + plane);
+    if (fz > 0) s += corr(fx, fy, fz - 1, g - plane);
+    const float ax = (6.0f * c0 - s) / h2;
+    xo[rep * nf + g] = c0 + kJacobiW * h2 / 6.0f * (b[rep * nf + g] - ax);
+  }
+}
+
 __global__ void k_mg_restrict(Grid3 F, Grid3 C, const float* __restrict__ rf,
                               float* __restrict__ bc, const PcgState* __restrict__ st) {
   const int rep = blockIdx.y;
@@ -527,7 +601,7 @@ __device__ void tail_jacobi(const TailLevels& L, int l, float* x, float* t, cons
 }
 
 __global__ void k_mg_tail(TailLevels L, const float* __restrict__ b_in, float* __restrict__ x_out,
-                          const PcgState* __restrict__ st) {
+                          const float* __restrict__ cinv, const PcgState* __restrict__ st) {
   const int rep = blockIdx.x;
   if (pcg_skip(st, rep)) return;
   extern __shared__ float sm[];
@@ -547,6 +621,17 @@ __global__ void k_mg_tail(TailLevels L, const float* __restrict__ b_in, float* _
   __syncthreads();
   for (int l = 0; l < L.nl; ++l) {
     const bool coarsest = (l == L.nl - 1);
+    if (coarsest && cinv) {
+      // exact solve with the precomputed inverse of the coarsest operator
+      const int nc = L.nx[l] * L.ny[l] * L.nz[l];
+      for (int i = threadIdx.x; i < nc; i += blockDim.x) {
+        float a = 0.0f;
+        for (int j = 0; j < nc; ++j) a = fmaf(cinv[(long)i * nc + j], bs[l][j], a);
+        xs[l][i] = a;
+      }
+      __syncthreads();
+      break;
+    }
     const int sweeps = coarsest ? kCoarseSweeps : kPre;
     for (int s = 0; s < sweeps; ++s) tail_jacobi(L, l, xs[l], ts[l], bs[l], s == 0);
     if (coarsest) break;
@@ -581,11 +666,50 @@ __global__ void k_mg_tail(TailLevels L, const float* __restrict__ b_in, float* _
   for (long g = threadIdx.x; g < n0; g += blockDim.x) x_out[rep * n0 + g] = xs[0][g];
 }
 
+// ---- set-up: inverse of the coarsest 7-point operator (one block, Gauss-Jordan, float64) ----
+__global__ void k_coarse_inverse(int nx, int ny, int nz, double h, double* __restrict__ M,
+                                 double* __restrict__ Minv, float* __restrict__ out) {
+  const int n = nx * ny * nz;
+  for (long e = threadIdx.x; e < (long)n * n; e += blockDim.x) {
+    const int i = (int)(e / n), j = (int)(e % n);
+    const int ix = i % nx, iy = (i / nx) % ny, iz = i / (nx * ny);
+    const int jx = j % nx, jy = (j / nx) % ny, jz = j / (nx * ny);
+    const int d = abs(ix - jx) + abs(iy - jy) + abs(iz - jz);
+    M[e] = (i == j) ? 6.0 / (h * h) : (d == 1 ? -1.0 / (h * h) : 0.0);
+    Minv[e] = (i == j) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  __shared__ double piv;
+  for (int k = 0; k < n; ++k) {  // SPD: no pivoting needed
+    if (threadIdx.x == 0) piv = M[(long)k * n + k];
+    __syncthreads();
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      M[(long)k * n + j] /= piv;
+      Minv[(long)k * n + j] /= piv;
+    }
+    __syncthreads();
+    for (long e = threadIdx.x; e < (long)n * n; e += blockDim.x) {
+      const int i = (int)(e / n), j = (int)(e % n);
+      if (i == k) continue;
+      const double f = M[(long)i * n + k];
+      if (j != k) M[e] -= f * M[(long)k * n + j];
+      Minv[e] -= f * Minv[(long)k * n + j];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+      if (i != k) M[(long)i * n + k] = 0.0;
+    __syncthreads();
+  }
+  for (long e = threadIdx.x; e < (long)n * n; e += blockDim.x) out[e] = (float)Minv[e];
+}
+
 // ---- host orchestration ------------------------------------------------------------------
 static Grid3 grid_of(const MgLevel& L) { return Grid3{L.nx, L.ny, L.nz, L.h}; }
 
+// one thread per point (grid-stride beyond 65535 blocks) for the pointwise multigrid kernels
 static int grid_blocks(rmgtd_ctx* ctx, long n) {
-  return (int)std::max<long>(1, std::min<long>(ceil_div(n, kThreads), ctx->red_blocks));
+  (void)ctx;
+  return (int)std::max<long>(1, std::min<long>(ceil_div(n, kThreads), 65535L));
 }
 
 // z = M r, M = one float32 V-cycle.  Level-0 input / output are float64 (r64, z64) or
@@ -602,15 +726,28 @@ static int vcycle(rmgtd_ctx* ctx, const double* r64, double* z64, const float* r
     const Grid3 G = grid_of(L);
     const int bl = grid_blocks(ctx, L.n);
     const bool coarsest = (l == nl - 1);
-    const int sweeps = coarsest ? kCoarseSweeps : kPre;
     float* lx = (l == 0 && z32) ? z32 : L.x;
     float* lb = (l == 0 && r32) ? const_cast<float*>(r32) : L.b;
     const double* in64 = (l == 0 && !r32) ? r64 : nullptr;
     double* out64 = (l == 0 && !z32) ? z64 : nullptr;
+    if (!coarsest) {
+      // pre-smoothing: two sweeps from zero in one kernel
+      k_mg_pre2<<<dim3(bl, nrep), kThreads, 0, s>>>(G, lx, lb, in64, st);
+      ++ctx->launches;
+      k_mg_residual<<<dim3(bl, nrep), kThreads, 0, s>>>(G, lx, lb, L.t, st);
+      ++ctx->launches;
+      MgLevel& C = ctx->mg[l + 1];
+      k_mg_restrict<<<dim3(grid_blocks(ctx, C.n), nrep), kThreads, 0, s>>>(G, grid_of(C), L.t,
+                                                                            C.b, st);
+      ++ctx->launches;
+      RMGTD_LAUNCH(ctx, "k_mg_descend");
+      continue;
+    }
+    // coarsest level handled by multi-block sweeps (no single-block tail)
     float* bufs[2] = {lx, L.t};
-    int cur = (sweeps % 2 == 1) ? 0 : 1;  // the last sweep writes x
-    for (int sw = 0; sw < sweeps; ++sw) {
-      const bool last_out64 = (coarsest && out64 && sw == sweeps - 1);
+    int cur = (kCoarseSweeps % 2 == 1) ? 0 : 1;  // the last sweep writes x
+    for (int sw = 0; sw < kCoarseSweeps; ++sw) {
+      const bool last_out64 = (out64 && sw == kCoarseSweeps - 1);
       k_mg_jacobi<<<dim3(bl, nrep), kThreads, 0, s>>>(
           G, bufs[cur ^ 1], bufs[cur], lb, sw == 0 ? in64 : nullptr, sw == 0,
           last_out64 ? out64 : nullptr, st);
@@ -618,13 +755,6 @@ static int vcycle(rmgtd_ctx* ctx, const double* r64, double* z64, const float* r
       cur ^= 1;
     }
     RMGTD_LAUNCH(ctx, "k_mg_jacobi");
-    if (coarsest) break;
-    k_mg_residual<<<dim3(bl, nrep), kThreads, 0, s>>>(G, lx, lb, L.t, st);
-    ++ctx->launches;
-    MgLevel& C = ctx->mg[l + 1];
-    k_mg_restrict<<<dim3(grid_blocks(ctx, C.n), nrep), kThreads, 0, s>>>(G, grid_of(C), L.t, C.b, st);
-    ++ctx->launches;
-    RMGTD_LAUNCH(ctx, "k_mg_restrict");
   }
   if (tail >= 0) {
     TailLevels T;
@@ -635,7 +765,8 @@ static int vcycle(rmgtd_ctx* ctx, const double* r64, double* z64, const float* r
       T.nz[l - tail] = ctx->mg[l].nz;
       T.h[l - tail] = (float)ctx->mg[l].h;
     }
-    k_mg_tail<<<nrep, 1024, ctx->mg_tail_smem, s>>>(T, ctx->mg[tail].b, ctx->mg[tail].x, st);
+    k_mg_tail<<<nrep, 1024, ctx->mg_tail_smem, s>>>(T, ctx->mg[tail].b, ctx->mg[tail].x,
+                                                     ctx->mg_cinv, st);
     ++ctx->launches;
     RMGTD_LAUNCH(ctx, "k_mg_tail");
   }
@@ -647,18 +778,13 @@ static int vcycle(rmgtd_ctx* ctx, const double* r64, double* z64, const float* r
     float* lx = (l == 0 && z32) ? z32 : L.x;
     float* lb = (l == 0 && r32) ? const_cast<float*>(r32) : L.b;
     double* out64 = (l == 0 && !z32) ? z64 : nullptr;
-    k_mg_prolong<<<dim3(bl, nrep), kThreads, 0, s>>>(G, grid_of(C), C.x, lx, st);
+    // coarse correction and the first post-sweep in one kernel (result in L.t), then the
+    // second post-sweep back into x (or the float64 output)
+    k_mg_prolong_sweep<<<dim3(bl, nrep), kThreads, 0, s>>>(G, grid_of(C), C.x, lx, L.t, lb, st);
     ++ctx->launches;
-    float* bufs[2] = {lx, L.t};
-    int cur = 1;
-    for (int sw = 0; sw < kPost; ++sw) {
-      const bool last = (sw == kPost - 1);
-      k_mg_jacobi<<<dim3(bl, nrep), kThreads, 0, s>>>(G, bufs[cur ^ 1], bufs[cur], lb, nullptr,
-                                                      0, (last && out64) ? out64 : nullptr, st);
-      ++ctx->launches;
-      cur ^= 1;
-    }
-    RMGTD_LAUNCH(ctx, "k_mg_post");
+    k_mg_jacobi<<<dim3(bl, nrep), kThreads, 0, s>>>(G, L.t, lx, lb, nullptr, 0, out64, st);
+    ++ctx->launches;
+    RMGTD_LAUNCH(ctx, "k_mg_ascend");
   }
   return RMGTD_OK;
 }
@@ -705,6 +831,23 @@ int setup_multigrid(rmgtd_ctx* ctx) {
     L.b = (float*)dev_alloc(ctx, bytes);
     L.t = (float*)dev_alloc(ctx, bytes);
     if (!L.x || !L.b || !L.t) return set_error(ctx, RMGTD_ENOMEM, "multigrid levels");
+  }
+  ctx->mg_cinv = nullptr;
+  if (ctx->mg_tail_level >= 0) {
+    const MgLevel& Lc = ctx->mg[nl - 1];
+    if (Lc.n <= 512) {
+      const size_t n2 = (size_t)Lc.n * Lc.n;
+      double* M = (double*)dev_alloc(ctx, sizeof(double) * n2);
+      double* Mi = (double*)dev_alloc(ctx, sizeof(double) * n2);
+      ctx->mg_cinv = (float*)dev_alloc(ctx, sizeof(float) * n2);
+      if (!M || !Mi || !ctx->mg_cinv) return set_error(ctx, RMGTD_ENOMEM, "coarse inverse");
+      k_coarse_inverse<<<1, 1024, 0, ctx->stream>>>(Lc.nx, Lc.ny, Lc.nz, Lc.h, M, Mi, ctx->mg_cinv);
+      ++ctx->launches;
+      RMGTD_LAUNCH(ctx, "k_coarse_inverse");
+      RMGTD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+      dev_free(ctx, M);
+      dev_free(ctx, Mi);
+    }
   }
   ctx->ghost = (double*)dev_alloc(ctx, sizeof(double) * 4 * (size_t)ctx->Ng);
   if (!ctx->ghost) return set_error(ctx, RMGTD_ENOMEM, "ghost fields");
@@ -836,6 +979,44 @@ int hartree_iteration(rmgtd_ctx* ctx, double* vh, int nrep, cudaGraphConditional
                                      ctx->kexec);
   ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_pcg_end");
+  return RMGTD_OK;
+}
+
+// Initial guess of the first Hartree solve of a step: linear extrapolation in time,
+// x <- 2 x(t) - x(t - dt), prev <- x(t).  Only the CG starting point changes.
+template <typename T>
+__global__ void k_extrap(long n, T* __restrict__ x, T* __restrict__ prev,
+                         const int* __restrict__ failed) {
+  if (*failed) return;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n;
+       e += (long)gridDim.x * blockDim.x) {
+    const T t = x[e];
+    x[e] = (T)2 * t - prev[e];
+    prev[e] = t;
+  }
+}
+
+int hartree_extrapolate(rmgtd_ctx* ctx) {
+  if (!ctx->hartree_xc) return RMGTD_OK;
+  const long n = (long)ctx->nrep * ctx->Ng;
+  const int bl = grid_blocks(ctx, n);
+  if (ctx->mixed)
+    k_extrap<float><<<bl, kThreads, 0, ctx->stream>>>(n, ctx->dvh32, ctx->dvh_prev32, ctx->failed);
+  else
+    k_extrap<double><<<bl, kThreads, 0, ctx->stream>>>(n, ctx->vh, ctx->vh_prev, ctx->failed);
+  ++ctx->launches;
+  RMGTD_LAUNCH(ctx, "k_extrap");
+  return RMGTD_OK;
+}
+
+// prev <- current (no history yet: the first extrapolation reproduces the current guess)
+int hartree_reset_history(rmgtd_ctx* ctx) {
+  const long n = (long)ctx->nrep * ctx->Ng;
+  RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->vh_prev, ctx->vh, sizeof(double) * n,
+                                  cudaMemcpyDeviceToDevice, ctx->stream));
+  if (ctx->mixed)
+    RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->dvh_prev32, ctx->dvh32, sizeof(float) * n,
+                                    cudaMemcpyDeviceToDevice, ctx->stream));
   return RMGTD_OK;
 }
 

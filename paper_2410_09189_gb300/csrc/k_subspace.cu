@@ -75,17 +75,19 @@ k_gram_partial(int N, long Ng, const double* __restrict__ A, const double* __res
     }
     __syncthreads();
   }
-  double* out = part + ((long)rep * nsplit + split) * (long)N * N;
+  // element-major partials [rep][i*N+j][split]: the reduction reads them contiguously
+  double* out = part + (long)rep * N * N * nsplit + split;
   const int i0 = I * kGT + ty, i1 = i0 + 16, j0 = J * kGT + tx, j1 = j0 + 16;
-  if (i0 < N && j0 < N) out[(long)i0 * N + j0] = acc00;
-  if (i0 < N && j1 < N) out[(long)i0 * N + j1] = acc01;
-  if (i1 < N && j0 < N) out[(long)i1 * N + j0] = acc10;
-  if (i1 < N && j1 < N) out[(long)i1 * N + j1] = acc11;
+  if (i0 < N && j0 < N) out[((long)i0 * N + j0) * nsplit] = acc00;
+  if (i0 < N && j1 < N) out[((long)i0 * N + j1) * nsplit] = acc01;
+  if (i1 < N && j0 < N) out[((long)i1 * N + j0) * nsplit] = acc10;
+  if (i1 < N && j1 < N) out[((long)i1 * N + j1) * nsplit] = acc11;
 }
 
-// out[rep] = base + scale * sum_split part; symmetric outputs are mirrored.  When `prev`
-// is given, max_ij |out - prev| is folded into errbits[rep] (prev may alias out: every
-// element is read and written by the same thread).
+// out[rep] = base + scale * sum_split part; symmetric outputs are mirrored.  One warp per
+// output element sums its split partials (contiguous, fixed order).  When `prev` is given,
+// max_ij |out - prev| is folded into errbits[rep] (prev may alias out: every element is read
+// and written by the same warp).
 __global__ void k_gram_reduce(int N, int nsplit, const double* __restrict__ part, double scale,
                               const double* __restrict__ base, double* out, long ostride,
                               const double* prev, int sym, unsigned long long* errbits,
@@ -94,20 +96,24 @@ __global__ void k_gram_reduce(int N, int nsplit, const double* __restrict__ part
   if (ctl && !ctl[rep].active) return;
   __shared__ double sh[32];
   const long NN = (long)N * N;
+  const int lane = threadIdx.x & 31;
+  const long warps = (long)gridDim.x * (blockDim.x >> 5);
   double emax = 0.0;
-  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < NN;
-       e += (long)gridDim.x * blockDim.x) {
+  for (long e = blockIdx.x * (long)(blockDim.x >> 5) + (threadIdx.x >> 5); e < NN; e += warps) {
     const int i = (int)(e / N), j = (int)(e % N);
     if (sym && j < i) continue;
-    double s = 0.0;
-    const double* p = part + (long)rep * nsplit * NN + e;
-    for (int k = 0; k < nsplit; ++k) s += p[(long)k * NN];
-    double v = scale * s;
-    if (base) v += base[e];
-    double* o = out + rep * ostride;
-    if (prev) emax = fmax(emax, fabs(v - prev[rep * ostride + e]));
-    o[e] = v;
-    if (sym && i != j) o[(long)j * N + i] = v;
+    const double* p = part + ((long)rep * NN + e) * nsplit;
+    double sacc = 0.0;
+    for (int k = lane; k < nsplit; k += 32) sacc += p[k];
+    sacc = warp_sum(sacc);
+    if (lane == 0) {
+      double v = scale * sacc;
+      if (base) v += base[e];
+      double* o = out + rep * ostride;
+      if (prev) emax = fmax(emax, fabs(v - prev[rep * ostride + e]));
+      o[e] = v;
+      if (sym && i != j) o[(long)j * N + i] = v;
+    }
   }
   if (errbits) {
     emax = block_max(emax, sh);
@@ -139,7 +145,7 @@ int gram(rmgtd_ctx* ctx, const double* A, const double* B, const double* w, long
   ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_gram_partial");
   const long NN = (long)N * N;
-  const int rb = (int)std::min<long>(ceil_div(NN, 256), 2L * ctx->num_sms);
+  const int rb = (int)std::min<long>(ceil_div(NN, 8), 4L * ctx->num_sms);
   k_gram_reduce<<<dim3(rb, nw), 256, 0, ctx->stream>>>(N, nsplit, ctx->gram_part, scale, base,
                                                         out, NN, prev, sym, errbits, ctl);
   ++ctx->launches;
@@ -215,87 +221,153 @@ int rho_dev(rmgtd_ctx* ctx, const double* S, double* rho, const RepCtl* ctl, int
 //   rho = rho_ref + sum_ij (S - S_ref)_ij phi_i phi_j      (float32 products and sums)
 //   H   = H_ref + h^3 Phi^T diag(V - V_ref) Phi            (float32 per block, float64 across)
 // Rounding then scales with the perturbation P - P_ref, not with P.
-__global__ void __launch_bounds__(kRhoThreads)
-k_rho32(int N, long Ng, const float* __restrict__ phi, const double* __restrict__ S,
-        const double* __restrict__ Sref, long sstride, const double* __restrict__ rho_ref,
-        double* __restrict__ rho, long rstride, const RepCtl* __restrict__ ctl) {
+// Density of the change of P: the float32 matrix Shat_kj = 2 dS_kj (k < j), dS_jj (k = j),
+// 0 (k > j), dS = S - S_ref, zero-padded to Np x Np (Np = N rounded up to 32), formed once
+// per pass by k_shat32 and streamed by k_rho32.
+__global__ void k_shat32(int N, int Np, const double* __restrict__ S, const double* __restrict__ Sref,
+                         long sstride, float* __restrict__ shat, const RepCtl* __restrict__ ctl) {
   const int rep = blockIdx.y;
   if (ctl && !ctl[rep].active) return;
-  __shared__ float Sh[kRhoK][kRhoJ];
   const double* Sr = S + rep * sstride;
-  const long g = blockIdx.x * (long)kRhoThreads + threadIdx.x;
-  const bool ok = g < Ng;
-  float r = 0.0f;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < (long)Np * Np;
+       e += (long)gridDim.x * blockDim.x) {
+    const int k = (int)(e / Np), j = (int)(e % Np);
+    double v = 0.0;
+    if (k < N && j < N && k <= j) {
+      const long o = (long)k * N + j;
+      v = (k < j) ? 2.0 * (Sr[o] - Sref[o]) : (Sr[o] - Sref[o]);
+    }
+    shat[(long)rep * Np * Np + e] = (float)v;
+  }
+}
+
+// rho = rho_ref + sum_j phi_j X_j, X_j = sum_{k<=j} Shat_kj phi_k: each thread two grid
+// points (g, g + 128), 32 columns j at a time, Shat rows read as float4 broadcasts.
+constexpr int kRho32Pts = 2;
+__global__ void __launch_bounds__(kRhoThreads)
+k_rho32(int N, int Np, long Ng, const float* __restrict__ phi, const float* __restrict__ shat,
+        const double* __restrict__ rho_ref, double* __restrict__ rho, long rstride,
+        const RepCtl* __restrict__ ctl) {
+  const int rep = blockIdx.y;
+  if (ctl && !ctl[rep].active) return;
+  __shared__ __align__(16) float Sh[kRhoK][kRhoJ];
+  const float* shr = shat + (long)rep * Np * Np;
+  const long g0 = blockIdx.x * (long)(kRhoThreads * kRho32Pts) + threadIdx.x;
+  const long g1 = g0 + kRhoThreads;
+  const bool ok0 = g0 < Ng, ok1 = g1 < Ng;
+  float r0 = 0.0f, r1 = 0.0f;
   for (int jb = 0; jb < N; jb += kRhoJ) {
-    float acc[kRhoJ];
+    float a0[kRhoJ], a1[kRhoJ];
 #pragma unroll
-    for (int jj = 0; jj < kRhoJ; ++jj) acc[jj] = 0.0f;
+    for (int jj = 0; jj < kRhoJ; ++jj) a0[jj] = a1[jj] = 0.0f;
     const int kend = min(N, jb + kRhoJ);
     for (int k0 = 0; k0 < kend; k0 += kRhoK) {
       __syncthreads();
-      for (int e = threadIdx.x; e < kRhoK * kRhoJ; e += kRhoThreads) {
-        const int kk = e / kRhoJ, jj = e % kRhoJ;
-        const int k = k0 + kk, j = jb + jj;
-        double v = 0.0;
-        if (k < N && j < N) {
-          const long o = (long)k * N + j;
-          if (k < j)
-            v = 2.0 * (Sr[o] - Sref[o]);
-          else if (k == j)
-            v = Sr[o] - Sref[o];
-        }
-        Sh[kk][jj] = (float)v;
+      // stage Shat[k0 .. k0+63][jb .. jb+31] (float4, coalesced; padded rows are zero)
+      for (int e = threadIdx.x; e < kRhoK * kRhoJ / 4; e += kRhoThreads) {
+        const int kk = e / (kRhoJ / 4), q = e % (kRhoJ / 4);
+        const int k = k0 + kk;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (k < Np) v = *reinterpret_cast<const float4*>(shr + (long)k * Np + jb + 4 * q);
+        *reinterpret_cast<float4*>(&Sh[kk][4 * q]) = v;
       }
       __syncthreads();
       const int kn = min(kRhoK, kend - k0);
-      if (ok) {
-        for (int kk = 0; kk < kn; ++kk) {
-          const float pk = phi[(long)(k0 + kk) * Ng + g];
+      int kk = 0;
+      for (; kk + 1 < kn; kk += 2) {
+        const long ka = (long)(k0 + kk) * Ng, kb = ka + Ng;
+        const float pa0 = ok0 ? phi[ka + g0] : 0.f, pa1 = ok1 ? phi[ka + g1] : 0.f;
+        const float pb0 = ok0 ? phi[kb + g0] : 0.f, pb1 = ok1 ? phi[kb + g1] : 0.f;
+        const float4* ra = reinterpret_cast<const float4*>(&Sh[kk][0]);
+        const float4* rb = reinterpret_cast<const float4*>(&Sh[kk + 1][0]);
 #pragma unroll
-          for (int jj = 0; jj < kRhoJ; ++jj) acc[jj] = fmaf(Sh[kk][jj], pk, acc[jj]);
+        for (int q = 0; q < kRhoJ / 4; ++q) {
+          const float4 u = ra[q], w = rb[q];
+          a0[4 * q + 0] = fmaf(w.x, pb0, fmaf(u.x, pa0, a0[4 * q + 0]));
+          a0[4 * q + 1] = fmaf(w.y, pb0, fmaf(u.y, pa0, a0[4 * q + 1]));
+          a0[4 * q + 2] = fmaf(w.z, pb0, fmaf(u.z, pa0, a0[4 * q + 2]));
+          a0[4 * q + 3] = fmaf(w.w, pb0, fmaf(u.w, pa0, a0[4 * q + 3]));
+          a1[4 * q + 0] = fmaf(w.x, pb1, fmaf(u.x, pa1, a1[4 * q + 0]));
+          a1[4 * q + 1] = fmaf(w.y, pb1, fmaf(u.y, pa1, a1[4 * q + 1]));
+          a1[4 * q + 2] = fmaf(w.z, pb1, fmaf(u.z, pa1, a1[4 * q + 2]));
+          a1[4 * q + 3] = fmaf(w.w, pb1, fmaf(u.w, pa1, a1[4 * q + 3]));
+        }
+      }
+      if (kk < kn) {
+        const long ka = (long)(k0 + kk) * Ng;
+        const float pa0 = ok0 ? phi[ka + g0] : 0.f, pa1 = ok1 ? phi[ka + g1] : 0.f;
+        const float4* ra = reinterpret_cast<const float4*>(&Sh[kk][0]);
+#pragma unroll
+        for (int q = 0; q < kRhoJ / 4; ++q) {
+          const float4 u = ra[q];
+          a0[4 * q + 0] = fmaf(u.x, pa0, a0[4 * q + 0]);
+          a0[4 * q + 1] = fmaf(u.y, pa0, a0[4 * q + 1]);
+          a0[4 * q + 2] = fmaf(u.z, pa0, a0[4 * q + 2]);
+          a0[4 * q + 3] = fmaf(u.w, pa0, a0[4 * q + 3]);
+          a1[4 * q + 0] = fmaf(u.x, pa1, a1[4 * q + 0]);
+          a1[4 * q + 1] = fmaf(u.y, pa1, a1[4 * q + 1]);
+          a1[4 * q + 2] = fmaf(u.z, pa1, a1[4 * q + 2]);
+          a1[4 * q + 3] = fmaf(u.w, pa1, a1[4 * q + 3]);
         }
       }
     }
-    if (ok) {
 #pragma unroll
-      for (int jj = 0; jj < kRhoJ; ++jj)
-        if (jb + jj < N) r = fmaf(phi[(long)(jb + jj) * Ng + g], acc[jj], r);
+    for (int jj = 0; jj < kRhoJ; ++jj) {
+      if (jb + jj < N) {
+        const long kj = (long)(jb + jj) * Ng;
+        if (ok0) r0 = fmaf(phi[kj + g0], a0[jj], r0);
+        if (ok1) r1 = fmaf(phi[kj + g1], a1[jj], r1);
+      }
     }
   }
-  if (ok) rho[rep * rstride + g] = rho_ref[g] + (double)r;
+  if (ok0) rho[rep * rstride + g0] = rho_ref[g0] + (double)r0;
+  if (ok1) rho[rep * rstride + g1] = rho_ref[g1] + (double)r1;
 }
 
 int rho_dev_mixed(rmgtd_ctx* ctx, const double* S, double* rho, const RepCtl* ctl, int nrep) {
-  dim3 grid(ceil_div(ctx->Ng, kRhoThreads), nrep);
-  k_rho32<<<grid, kRhoThreads, 0, ctx->stream>>>(ctx->N, ctx->Ng, ctx->phi32, S, ctx->Sref,
-                                                  (long)ctx->N * ctx->N, ctx->rho_ref, rho,
-                                                  ctx->Ng, ctl);
+  const int N = ctx->N, Np = ((N + 31) / 32) * 32;
+  const long NpNp = (long)Np * Np;
+  k_shat32<<<dim3(std::max(1, (int)std::min<long>(ceil_div(NpNp, 256), 1024)), nrep), 256, 0,
+             ctx->stream>>>(N, Np, S, ctx->Sref, (long)N * N, ctx->shat32, ctl);
+  ++ctx->launches;
+  dim3 grid(ceil_div(ctx->Ng, kRhoThreads * kRho32Pts), nrep);
+  k_rho32<<<grid, kRhoThreads, 0, ctx->stream>>>(N, Np, ctx->Ng, ctx->phi32, ctx->shat32,
+                                                  ctx->rho_ref, rho, ctx->Ng, ctl);
   ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_rho32");
   return RMGTD_OK;
 }
 
-// float32 Gram partials: per block sum_{g in split} phi_i(g) dv(g) phi_j(g), symmetric tiles
-__global__ void __launch_bounds__(256)
+// float32 Gram partials h-free sums sum_{g in split} phi_i(g) dv(g) phi_j(g) for one 32 x 32
+// output tile (symmetric pairs I <= J): 64 threads, each a 4 x 4 register tile; the k-slab
+// of 32 points is staged transposed in shared memory and read as float4 (1 LDS.128 per 4
+// values, 2 per 16 FFMA).
+constexpr int kG32Threads = 64;
+__global__ void __launch_bounds__(kG32Threads)
 k_gram_partial32(int N, long Ng, const float* __restrict__ A, const float* __restrict__ w,
                  long wstride, int T, long chunk, double* __restrict__ part,
                  const RepCtl* __restrict__ ctl) {
   const int rep = blockIdx.z;
   if (ctl && !ctl[rep].active) return;
-  __shared__ float As[kGT][kGT + 1];
-  __shared__ float Bs[kGT][kGT + 1];
+  __shared__ __align__(16) float As[kGT][kGT + 4];
+  __shared__ __align__(16) float Bs[kGT][kGT + 4];
   int I, J;
   pair_from_index(blockIdx.x, T, 1, I, J);
   const int split = blockIdx.y, nsplit = gridDim.y;
   const long g_beg = (long)split * chunk;
   const long g_end = min(Ng, g_beg + chunk);
   const float* wr = w + rep * wstride;
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  float acc00 = 0, acc01 = 0, acc10 = 0, acc11 = 0;
-  for (long g0 = g_beg; g0 < g_end; g0 += kGT) {
+  const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;   // 8 x 8 threads
+  float acc[4][4];
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int idx = tid + 256 * e;
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0f;
+  for (long g0 = g_beg; g0 < g_end; g0 += kGT) {
+    // stage: 32 rows x 32 points of A (rows of tile I) and of w*A (rows of tile J)
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+      const int idx = tid + kG32Threads * e;  // 0 .. 1023
       const int r = idx >> 5, c = idx & 31;
       const long g = g0 + c;
       const int ia = I * kGT + r, jb = J * kGT + r;
@@ -310,21 +382,27 @@ k_gram_partial32(int N, long Ng, const float* __restrict__ A, const float* __res
     __syncthreads();
 #pragma unroll 8
     for (int k = 0; k < kGT; ++k) {
-      const float a0 = As[k][ty], a1 = As[k][ty + 16];
-      const float b0 = Bs[k][tx], b1 = Bs[k][tx + 16];
-      acc00 = fmaf(a0, b0, acc00);
-      acc01 = fmaf(a0, b1, acc01);
-      acc10 = fmaf(a1, b0, acc10);
-      acc11 = fmaf(a1, b1, acc11);
+      const float4 a = *reinterpret_cast<const float4*>(&As[k][4 * ty]);
+      const float4 b = *reinterpret_cast<const float4*>(&Bs[k][4 * tx]);
+      const float av[4] = {a.x, a.y, a.z, a.w};
+      const float bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(av[p], bv[q], acc[p][q]);
     }
     __syncthreads();
   }
-  double* out = part + ((long)rep * nsplit + split) * (long)N * N;
-  const int i0 = I * kGT + ty, i1 = i0 + 16, j0 = J * kGT + tx, j1 = j0 + 16;
-  if (i0 < N && j0 < N) out[(long)i0 * N + j0] = acc00;
-  if (i0 < N && j1 < N) out[(long)i0 * N + j1] = acc01;
-  if (i1 < N && j0 < N) out[(long)i1 * N + j0] = acc10;
-  if (i1 < N && j1 < N) out[(long)i1 * N + j1] = acc11;
+  double* out = part + (long)rep * N * N * nsplit + split;
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    const int i = I * kGT + 4 * ty + p;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = J * kGT + 4 * tx + q;
+      if (i < N && j < N) out[((long)i * N + j) * nsplit] = acc[p][q];
+    }
+  }
 }
 
 int gram_mixed(rmgtd_ctx* ctx, const float* w, long wstride, int nw, double scale,
@@ -332,15 +410,19 @@ int gram_mixed(rmgtd_ctx* ctx, const float* w, long wstride, int nw, double scal
   const int N = ctx->N;
   const int T = ceil_div(N, kGT);
   const int ntiles = T * (T + 1) / 2;
-  const int nsplit = gram_nsplit(ctx, ntiles, nw);
+  // 64-thread blocks: aim at ~16 resident warps per SM
+  long ns = (16L * ctx->num_sms + (long)ntiles * nw - 1) / ((long)ntiles * nw);
+  ns = std::max<long>(1, std::min<long>(ns, ctx->Ng / 256 + 1));
+  ns = std::min<long>(ns, (long)(ctx->gram_part_elems / std::max<long>((long)nw * N * N, 1)));
+  const int nsplit = (int)std::max<long>(ns, 1);
   const long chunk = ((ctx->Ng + nsplit - 1) / nsplit + kGT - 1) / kGT * kGT;
   dim3 grid(ntiles, nsplit, nw);
-  k_gram_partial32<<<grid, 256, 0, ctx->stream>>>(N, ctx->Ng, ctx->phi32, w, wstride, T, chunk,
-                                                   ctx->gram_part, ctl);
+  k_gram_partial32<<<grid, kG32Threads, 0, ctx->stream>>>(N, ctx->Ng, ctx->phi32, w, wstride, T,
+                                                           chunk, ctx->gram_part, ctl);
   ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_gram_partial32");
   const long NN = (long)N * N;
-  const int rb = (int)std::min<long>(ceil_div(NN, 256), 2L * ctx->num_sms);
+  const int rb = (int)std::min<long>(ceil_div(NN, 8), 4L * ctx->num_sms);
   k_gram_reduce<<<dim3(rb, nw), 256, 0, ctx->stream>>>(N, nsplit, ctx->gram_part, scale, base, out,
                                                         NN, out, 1, errbits, ctl);
   ++ctx->launches;

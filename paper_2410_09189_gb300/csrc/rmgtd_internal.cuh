@@ -124,6 +124,9 @@ struct rmgtd_ctx {
   double* vh_ref = nullptr;    // [Ng] reference V_H (mixed)
   float* dv32 = nullptr;       // [nrep][Ng] V_Hxc - vref (mixed)
   float* dvh32 = nullptr;      // [nrep][Ng] V_H - vh_ref (mixed, Hartree correction unknown)
+  float* dvh_prev32 = nullptr; // [nrep][Ng] dvh32 one step earlier (initial-guess history)
+  float* shat32 = nullptr;     // [nrep][Np][Np] float32 density-change matrix (mixed)
+  double* vh_prev = nullptr;   // [nrep][Ng] V_H one step earlier (initial-guess history)
   float *pcg32_b = nullptr, *pcg32_r = nullptr, *pcg32_z = nullptr, *pcg32_p = nullptr,
         *pcg32_Ap = nullptr;   // [nrep][Ng] float32 CG vectors (mixed)
   int mixed = 0;               // mixed-precision step active (after set-up)
@@ -146,6 +149,7 @@ struct rmgtd_ctx {
   std::vector<rmgtd::MgLevel> mg;   // multi-CTA levels (level 0 = fine grid)
   int mg_tail_level = -1;           // first level solved inside one CTA
   size_t mg_tail_smem = 0;
+  float* mg_cinv = nullptr;         // inverse of the coarsest operator (tail), or NULL
 
   // control
   rmgtd::RepCtl* ctl = nullptr;     // [nrep]
@@ -333,6 +337,8 @@ int hartree_graph(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* c
                   int f32);
 int hartree_begin(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* ctl, int zero_bc,
                   int nrep, cudaGraphConditionalHandle cond, int use_cond, int f32);
+int hartree_extrapolate(rmgtd_ctx* ctx);
+int hartree_reset_history(rmgtd_ctx* ctx);
 int hartree_iteration(rmgtd_ctx* ctx, double* vh, int nrep, cudaGraphConditionalHandle cond,
                       int use_cond, int f32);
 
