@@ -366,7 +366,8 @@ static int create_impl(const rmgtd_system* sys, const rmgtd_options* opt, rmgtd_
   ctx->coop_ok = prop.cooperativeLaunch;
   if (!ctx->coop_ok) return set_error(ctx, RMGTD_ECUDA, "device lacks cooperative launch");
   // blocks of the grid-stride reduction kernels: about one point per thread up to 2048
-  ctx->red_blocks = (int)std::max<long>(1, std::min<long>(2048, rmgtd::ceil_div(ctx->Ng, kThreads)));
+  ctx->red_blocks = 2 * ctx->num_sms;
+  ctx->red_cap = poisson_red_cap(ctx->nx, ctx->ny, ctx->nz, ctx->red_blocks);
 
   ctx->f.assign(N, 0.0);
   for (int i = 0; i < N; ++i) ctx->f[i] = sys->f ? sys->f[i] : (i < sys->nocc ? 2.0 : 0.0);
@@ -398,7 +399,7 @@ static int create_impl(const rmgtd_system* sys, const rmgtd_options* opt, rmgtd_
   ctx->pcg_z = (double*)A(gsz * nrep);
   ctx->pcg_p = (double*)A(gsz * nrep);
   ctx->pcg_Ap = (double*)A(gsz * nrep);
-  ctx->red_part = (double*)A(sizeof(double) * (size_t)nrep * 8 * ctx->red_blocks);
+  ctx->red_part = (double*)A(sizeof(double) * (size_t)nrep * 8 * ctx->red_cap);
   ctx->pcg = (PcgState*)A(sizeof(PcgState) * nrep);
   ctx->pcg_any = (int*)A(sizeof(int));
   ctx->ctl = (RepCtl*)A(sizeof(RepCtl) * nrep);
@@ -593,6 +594,8 @@ int rmgtd_create(const rmgtd_system* sys, const rmgtd_options* opt_in, rmgtd_ctx
       (sys->nproj > 0 && (!sys->proj_atom || !sys->proj_l || !sys->proj_rc || !sys->E_kb)))
     return set_error(nullptr, RMGTD_EINVAL, "projector arrays missing");
   if (opt.nrep < 1 || opt.nrep > 32) return set_error(nullptr, RMGTD_EINVAL, "nrep must be 1..32");
+  if ((long)sys->nz * opt.nrep > 65535)
+    return set_error(nullptr, RMGTD_EINVAL, "nz * nrep must not exceed 65535");
   if (!(opt.dt > 0) || !(opt.H_thrs > 0) || !(opt.dP_thrs > 0) || opt.max_scf < 1 ||
       opt.max_terms < 1 || !(opt.poisson_tol > 0) || opt.poisson_max_iter < 1)
     return set_error(nullptr, RMGTD_EINVAL, "invalid options");

@@ -6,15 +6,19 @@
 // The ghost term is linear in (Q, p): L_ghost(V_b) = Q G0 + px Gx + py Gy + pz Gz with four
 // grid fields G fixed by the grid, formed once at set-up.
 //
-// Solver: flexible (Polak-Ribiere) conjugate gradients in float64, preconditioned by one
-// symmetric multigrid V-cycle in float32 (the paper's multigrid, Section 2.1): cell-centred
-// coarsening by 2, 7-point operators at spacing 2^l h, damped Jacobi smoothing (2 pre,
-// 2 post), trilinear prolongation and its transpose/8 as restriction; the levels with
-// <= 4096 points run inside one block.  The preconditioner's precision changes only the
-// iteration count: the residual, the iterates and the stopping test are float64.
-// Every kernel carries a replica index and returns at once for replicas whose solve has
-// converged, so a fixed launch sequence (eager or inside a CUDA-graph while loop) is
-// correct.
+// Solver: flexible (Polak-Ribiere) conjugate gradients, preconditioned by one symmetric
+// multigrid V-cycle in float32 (the paper's multigrid, Section 2.1): cell-centred coarsening
+// by 2, 7-point operators at spacing 2^l h, damped Jacobi smoothing (2 pre, 2 post),
+// trilinear prolongation and its transpose/8 as restriction; the levels with <= 4096 points
+// run inside one block, whose coarsest level is solved exactly.  The float64 path iterates
+// on V itself; the mixed path iterates in float32 on the change of V relative to the
+// reference potential.  Stopping test, scalars and reductions are float64.
+//
+// Layout of the launches: stencil kernels run one thread per grid point on a 3-D launch
+// grid (32 x 8 threads per x-y tile, blockIdx.z = plane + nz * replica), so no index is
+// divided; pointwise vector updates run a fixed number of grid-stride blocks.  Every kernel
+// returns at once for replicas whose solve has converged, so a fixed launch sequence (eager
+// or inside a CUDA-graph while loop) is correct.
 #include <math.h>
 
 #include "rmgtd_internal.cuh"
@@ -28,11 +32,22 @@ constexpr int kPre = 2, kPost = 2, kCoarseSweeps = 40;
 // relative residual of the float32 correction solve of the mixed path (float32 CG reaches
 // ~1e-6-1e-7; the correction is small next to the float64 reference potential)
 constexpr double kMixedPoissonTol = 1e-6;
+constexpr int kBX = 32, kBY = 8;   // x-y tile of the 3-D launches
 
 struct Grid3 {
   int nx, ny, nz;
   double h;
 };
+
+// Reduction partials: slot s of replica r starts at part + (r * 8 + s) * cap.
+//   0 (b,b)  1 (r,r)  2 (r,z)  3 (p,Ap)  4..7 moments of rho   5 also (r_new, z_old)
+struct Red {
+  double* part;
+  int cap;
+};
+__device__ __forceinline__ double* slot(Red R, int rep, int s) {
+  return R.part + ((long)rep * 8 + s) * R.cap;
+}
 
 __device__ __forceinline__ bool pcg_skip(const PcgState* st, int rep) { return st[rep].done != 0; }
 
@@ -41,6 +56,38 @@ __device__ __forceinline__ double sum_partials(const double* p, int n) {
   double s = 0.0;
   for (int b = (threadIdx.x & 31); b < n; b += 32) s += p[b];
   return warp_sum(s);
+}
+
+// 3-D launch helpers: thread (ix, iy) of plane iz of replica rep
+struct Pt3 {
+  int ix, iy, iz, rep;
+  bool in;
+  int blin;   // linear block id within the replica
+  int nblk;   // blocks per replica
+};
+__device__ __forceinline__ Pt3 pt3(int nx, int ny, int nz) {
+  Pt3 p;
+  p.ix = blockIdx.x * kBX + threadIdx.x;
+  p.iy = blockIdx.y * kBY + threadIdx.y;
+  p.iz = blockIdx.z % nz;
+  p.rep = blockIdx.z / nz;
+  p.in = (p.ix < nx) && (p.iy < ny);
+  p.blin = (p.iz * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+  p.nblk = gridDim.x * gridDim.y * nz;
+  return p;
+}
+// block sum for 32 x 8 blocks (each y-row is one warp); valid in thread (0, 0)
+__device__ __forceinline__ double block_sum_2d(double v, double* sh) {
+  v = warp_sum(v);
+  __syncthreads();
+  if (threadIdx.x == 0) sh[threadIdx.y] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.y == 0) {
+    s = (threadIdx.x < kBY) ? sh[threadIdx.x] : 0.0;
+    s = warp_sum(s);
+  }
+  return s;
 }
 
 // ---- set-up: ghost response fields G0, Gx, Gy, Gz ------------------------------------------
@@ -80,29 +127,26 @@ __global__ void k_ghost_fields(Grid3 G, double* __restrict__ gf) {
   }
 }
 
-// ---- multipole moments (partials into slots 4..7) ------------------------------------------
-__global__ void k_moments(Grid3 G, const double* __restrict__ rho,
-                          const double* __restrict__ rho_ref, double* __restrict__ part,
-                          const RepCtl* __restrict__ ctl) {
-  const int rep = blockIdx.y;
-  if (ctl && !ctl[rep].active) return;
-  const long Ng = (long)G.nx * G.ny * G.nz;
-  const double* r = rho + rep * Ng;
+// ---- multipole moments of rho (or rho - rho_ref): partials into slots 4..7 ------------------
+__global__ void __launch_bounds__(kBX* kBY)
+k_moments(Grid3 G, const double* __restrict__ rho, const double* __restrict__ rho_ref, Red R,
+          const RepCtl* __restrict__ ctl) {
+  const Pt3 p = pt3(G.nx, G.ny, G.nz);
+  if (ctl && !ctl[p.rep].active) return;
   double q[4] = {0, 0, 0, 0};
-  for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < Ng;
-       g += (long)gridDim.x * blockDim.x) {
-    const int ix = (int)(g % G.nx), iy = (int)((g / G.nx) % G.ny), iz = (int)(g / ((long)G.nx * G.ny));
-    const double v = rho_ref ? r[g] - rho_ref[g] : r[g];
-    q[0] += v;
-    q[1] += v * axis_coord(ix, G.nx, G.h);
-    q[2] += v * axis_coord(iy, G.ny, G.h);
-    q[3] += v * axis_coord(iz, G.nz, G.h);
+  if (p.in) {
+    const long Ng = (long)G.nx * G.ny * G.nz;
+    const long g = ((long)p.iz * G.ny + p.iy) * G.nx + p.ix;
+    const double v = rho_ref ? rho[p.rep * Ng + g] - rho_ref[g] : rho[p.rep * Ng + g];
+    q[0] = v;
+    q[1] = v * axis_coord(p.ix, G.nx, G.h);
+    q[2] = v * axis_coord(p.iy, G.ny, G.h);
+    q[3] = v * axis_coord(p.iz, G.nz, G.h);
   }
-  __shared__ double sh[32];
+  __shared__ double sh[kBY];
   for (int t = 0; t < 4; ++t) {
-    const double s = block_sum(q[t], sh);
-    if (threadIdx.x == 0) part[((long)rep * 8 + 4 + t) * gridDim.x + blockIdx.x] = s;
-    __syncthreads();
+    const double s = block_sum_2d(q[t], sh);
+    if (threadIdx.x == 0 && threadIdx.y == 0) slot(R, p.rep, 4 + t)[p.blin] = s;
   }
 }
 
@@ -127,20 +171,20 @@ __device__ __forceinline__ V apply_A12(const V* __restrict__ x, int ix, int iy, 
   return -s * ih2;
 }
 
-// b = 4 pi (rho - rho_ref) + Q G0 + p.G (moments of rho - rho_ref; rho_ref may be NULL);
-// r = b - A x; partials of (b,b) (slot 0), (r,r) (slot 1)
+// b = 4 pi (rho - rho_ref) + Q G0 + p.G (moments from k_moments, `nmom` partials); r = b - A x;
+// partials of (b,b) (slot 0) and (r,r) (slot 1)
 template <typename V>
-__global__ void k_pcg_init(Grid3 G, const double* __restrict__ rho,
-                           const double* __restrict__ rho_ref, const double* __restrict__ gf,
-                           const V* __restrict__ x, V* __restrict__ b, V* __restrict__ r,
-                           double* __restrict__ part, int zero_bc, const RepCtl* __restrict__ ctl) {
-  const int rep = blockIdx.y;
-  if (ctl && !ctl[rep].active) return;
-  const int nblk = gridDim.x;
+__global__ void __launch_bounds__(kBX* kBY)
+k_pcg_init(Grid3 G, const double* __restrict__ rho, const double* __restrict__ rho_ref,
+           const double* __restrict__ gf, const V* __restrict__ x, V* __restrict__ b,
+           V* __restrict__ r, Red R, int nmom, int zero_bc, const RepCtl* __restrict__ ctl) {
+  const Pt3 p = pt3(G.nx, G.ny, G.nz);
+  if (ctl && !ctl[p.rep].active) return;
   __shared__ double mom[4];
-  if (threadIdx.x < 32) {
+  __shared__ double sh[kBY];
+  if (threadIdx.y == 0) {
     for (int t = 0; t < 4; ++t) {
-      const double s = sum_partials(part + ((long)rep * 8 + 4 + t) * nblk, nblk);
+      const double s = sum_partials(slot(R, p.rep, 4 + t), nmom);
       if (threadIdx.x == 0) mom[t] = s;
     }
   }
@@ -149,37 +193,54 @@ __global__ void k_pcg_init(Grid3 G, const double* __restrict__ rho,
   const double Q = zero_bc ? 0.0 : h3 * mom[0], px = zero_bc ? 0.0 : h3 * mom[1],
                py = zero_bc ? 0.0 : h3 * mom[2], pz = zero_bc ? 0.0 : h3 * mom[3];
   const long Ng = (long)G.nx * G.ny * G.nz;
-  const V ih2 = (V)(1.0 / (G.h * G.h));
-  const V* xr = x + rep * Ng;
   double bb = 0.0, rr = 0.0;
-  for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < Ng;
-       g += (long)gridDim.x * blockDim.x) {
-    const int ix = (int)(g % G.nx), iy = (int)((g / G.nx) % G.ny), iz = (int)(g / ((long)G.nx * G.ny));
-    const double dr = rho_ref ? rho[rep * Ng + g] - rho_ref[g] : rho[rep * Ng + g];
+  if (p.in) {
+    const long g = ((long)p.iz * G.ny + p.iy) * G.nx + p.ix;
+    const double dr = rho_ref ? rho[p.rep * Ng + g] - rho_ref[g] : rho[p.rep * Ng + g];
     double bd = 4.0 * kPi * dr;
     bd += Q * gf[g] + px * gf[Ng + g] + py * gf[2 * Ng + g] + pz * gf[3 * Ng + g];
     const V bv = (V)bd;
-    b[rep * Ng + g] = bv;
-    const V rv = bv - apply_A12<V>(xr, ix, iy, iz, G.nx, G.ny, G.nz, ih2);
-    r[rep * Ng + g] = rv;
-    bb += (double)bv * (double)bv;
-    rr += (double)rv * (double)rv;
+    b[p.rep * Ng + g] = bv;
+    const V rv = bv - apply_A12<V>(x + p.rep * Ng, p.ix, p.iy, p.iz, G.nx, G.ny, G.nz,
+                                   (V)(1.0 / (G.h * G.h)));
+    r[p.rep * Ng + g] = rv;
+    bb = (double)bv * (double)bv;
+    rr = (double)rv * (double)rv;
   }
-  __shared__ double sh[32];
-  bb = block_sum(bb, sh);
-  if (threadIdx.x == 0) part[((long)rep * 8 + 0) * nblk + blockIdx.x] = bb;
-  __syncthreads();
-  rr = block_sum(rr, sh);
-  if (threadIdx.x == 0) part[((long)rep * 8 + 1) * nblk + blockIdx.x] = rr;
+  bb = block_sum_2d(bb, sh);
+  if (threadIdx.x == 0 && threadIdx.y == 0) slot(R, p.rep, 0)[p.blin] = bb;
+  rr = block_sum_2d(rr, sh);
+  if (threadIdx.x == 0 && threadIdx.y == 0) slot(R, p.rep, 1)[p.blin] = rr;
 }
 
-__global__ void k_pcg_state_init(PcgState* st, const double* __restrict__ part, int nblk,
-                                 double tol, const RepCtl* __restrict__ ctl, int nrep) {
+// Ap = A p and partials of (p, Ap) into slot 3
+template <typename V>
+__global__ void __launch_bounds__(kBX* kBY)
+k_pcg_Ap(Grid3 G, const V* __restrict__ pv, V* __restrict__ Ap, Red R,
+         const PcgState* __restrict__ st) {
+  const Pt3 p = pt3(G.nx, G.ny, G.nz);
+  if (pcg_skip(st, p.rep)) return;
+  __shared__ double sh[kBY];
+  double s = 0.0;
+  if (p.in) {
+    const long Ng = (long)G.nx * G.ny * G.nz;
+    const long g = ((long)p.iz * G.ny + p.iy) * G.nx + p.ix;
+    const V* pr = pv + p.rep * Ng;
+    const V a = apply_A12<V>(pr, p.ix, p.iy, p.iz, G.nx, G.ny, G.nz, (V)(1.0 / (G.h * G.h)));
+    Ap[p.rep * Ng + g] = a;
+    s = (double)pr[g] * (double)a;
+  }
+  s = block_sum_2d(s, sh);
+  if (threadIdx.x == 0 && threadIdx.y == 0) slot(R, p.rep, 3)[p.blin] = s;
+}
+
+__global__ void k_pcg_state_init(PcgState* st, Red R, int nblk, double tol,
+                                 const RepCtl* __restrict__ ctl, int nrep) {
   const int rep = threadIdx.x >> 5;  // one warp per replica
   if (rep >= nrep) return;
   const bool act = !ctl || ctl[rep].active;
-  const double bb = sum_partials(part + ((long)rep * 8 + 0) * nblk, nblk);
-  const double rr = sum_partials(part + ((long)rep * 8 + 1) * nblk, nblk);
+  const double bb = sum_partials(slot(R, rep, 0), nblk);
+  const double rr = sum_partials(slot(R, rep, 1), nblk);
   if ((threadIdx.x & 31) == 0) {
     PcgState& s = st[rep];
     s.bb = bb;
@@ -192,11 +253,10 @@ __global__ void k_pcg_state_init(PcgState* st, const double* __restrict__ part, 
   }
 }
 
-// (r, z) partials into slot 2; p = z when `first`
+// (r, z) partials into slot 2 (grid-stride, gridDim.x partials); p = z when `first`
 template <typename V>
 __global__ void k_pcg_rz(long Ng, const V* __restrict__ r, const V* __restrict__ z,
-                         V* __restrict__ p, int first, double* __restrict__ part,
-                         const PcgState* __restrict__ st) {
+                         V* __restrict__ p, int first, Red R, const PcgState* __restrict__ st) {
   const int rep = blockIdx.y;
   if (pcg_skip(st, rep)) return;
   double s = 0.0;
@@ -208,16 +268,16 @@ __global__ void k_pcg_rz(long Ng, const V* __restrict__ r, const V* __restrict__
   }
   __shared__ double sh[32];
   s = block_sum(s, sh);
-  if (threadIdx.x == 0) part[((long)rep * 8 + 2) * gridDim.x + blockIdx.x] = s;
+  if (threadIdx.x == 0) slot(R, rep, 2)[blockIdx.x] = s;
 }
 
 // store the first (r, z); inside a graph, arm the CG while loop that follows (a nested
 // loop's flag is not reset between executions of the enclosing body)
-__global__ void k_pcg_rz_store(PcgState* st, const double* __restrict__ part, int nblk, int nrep,
+__global__ void k_pcg_rz_store(PcgState* st, Red R, int nblk, int nrep,
                                cudaGraphConditionalHandle cond, int use_cond) {
   const int rep = threadIdx.x >> 5;
   if (rep < nrep && !st[rep].done) {
-    const double s = sum_partials(part + ((long)rep * 8 + 2) * nblk, nblk);
+    const double s = sum_partials(slot(R, rep, 2), nblk);
     if ((threadIdx.x & 31) == 0) st[rep].rz[st[rep].cur] = s;
   }
   __syncthreads();
@@ -228,40 +288,17 @@ __global__ void k_pcg_rz_store(PcgState* st, const double* __restrict__ part, in
   }
 }
 
-// Ap = A p and partials of (p, Ap) into slot 3
-template <typename V>
-__global__ void k_pcg_Ap(Grid3 G, const V* __restrict__ p, V* __restrict__ Ap,
-                         double* __restrict__ part, const PcgState* __restrict__ st) {
-  const int rep = blockIdx.y;
-  if (pcg_skip(st, rep)) return;
-  const long Ng = (long)G.nx * G.ny * G.nz;
-  const V ih2 = (V)(1.0 / (G.h * G.h));
-  const V* pr = p + rep * Ng;
-  double s = 0.0;
-  for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < Ng;
-       g += (long)gridDim.x * blockDim.x) {
-    const int ix = (int)(g % G.nx), iy = (int)((g / G.nx) % G.ny), iz = (int)(g / ((long)G.nx * G.ny));
-    const V a = apply_A12<V>(pr, ix, iy, iz, G.nx, G.ny, G.nz, ih2);
-    Ap[rep * Ng + g] = a;
-    s += (double)pr[g] * (double)a;
-  }
-  __shared__ double sh[32];
-  s = block_sum(s, sh);
-  if (threadIdx.x == 0) part[((long)rep * 8 + 3) * gridDim.x + blockIdx.x] = s;
-}
-
-// alpha = rz/(p,Ap); x += alpha p; r -= alpha Ap; partials of (r,r) (slot 1) and of
-// (r_new, z_old) (slot 5) for the flexible beta
+// alpha = rz / (p,Ap) (slot 3, `nap` partials); x += alpha p; r -= alpha Ap; partials of
+// (r,r) (slot 1) and (r_new, z_old) (slot 5), gridDim.x each
 template <typename V>
 __global__ void k_pcg_xr(long Ng, V* __restrict__ x, V* __restrict__ r, const V* __restrict__ p,
-                         const V* __restrict__ Ap, const V* __restrict__ z,
-                         double* __restrict__ part, const PcgState* __restrict__ st) {
+                         const V* __restrict__ Ap, const V* __restrict__ z, Red R, int nap,
+                         const PcgState* __restrict__ st) {
   const int rep = blockIdx.y;
   if (pcg_skip(st, rep)) return;
   __shared__ double alpha;
-  const int nblk = gridDim.x;
   if (threadIdx.x < 32) {
-    const double pAp = sum_partials(part + ((long)rep * 8 + 3) * nblk, nblk);
+    const double pAp = sum_partials(slot(R, rep, 3), nap);
     if (threadIdx.x == 0) alpha = st[rep].rz[st[rep].cur] / pAp;
   }
   __syncthreads();
@@ -278,17 +315,17 @@ __global__ void k_pcg_xr(long Ng, V* __restrict__ x, V* __restrict__ r, const V*
   }
   __shared__ double sh[32];
   s = block_sum(s, sh);
-  if (threadIdx.x == 0) part[((long)rep * 8 + 1) * nblk + blockIdx.x] = s;
+  if (threadIdx.x == 0) slot(R, rep, 1)[blockIdx.x] = s;
   __syncthreads();
   t = block_sum(t, sh);
-  if (threadIdx.x == 0) part[((long)rep * 8 + 5) * nblk + blockIdx.x] = t;
+  if (threadIdx.x == 0) slot(R, rep, 5)[blockIdx.x] = t;
 }
 
-__global__ void k_pcg_check(PcgState* st, const double* __restrict__ part, int nblk, double tol,
-                            int max_it, int nrep, int* status) {
+__global__ void k_pcg_check(PcgState* st, Red R, int nblk, double tol, int max_it, int nrep,
+                            int* status) {
   const int rep = threadIdx.x >> 5;
   if (rep >= nrep || st[rep].done) return;
-  const double rr = sum_partials(part + ((long)rep * 8 + 1) * nblk, nblk);
+  const double rr = sum_partials(slot(R, rep, 1), nblk);
   if ((threadIdx.x & 31) == 0) {
     PcgState& s = st[rep];
     s.rr = rr;
@@ -308,15 +345,14 @@ __global__ void k_pcg_check(PcgState* st, const double* __restrict__ part, int n
 
 // beta = ((r,z_new) - (r,z_old)) / rz_old (Polak-Ribiere); p = z + beta p
 template <typename V>
-__global__ void k_pcg_p(long Ng, const V* __restrict__ z, V* __restrict__ p,
-                        const double* __restrict__ part, const PcgState* __restrict__ st) {
+__global__ void k_pcg_p(long Ng, const V* __restrict__ z, V* __restrict__ p, Red R, int nblk,
+                        const PcgState* __restrict__ st) {
   const int rep = blockIdx.y;
   if (pcg_skip(st, rep)) return;
   __shared__ double beta;
-  const int nblk = gridDim.x;
   if (threadIdx.x < 32) {
-    const double rzn = sum_partials(part + ((long)rep * 8 + 2) * nblk, nblk);
-    const double rzo = sum_partials(part + ((long)rep * 8 + 5) * nblk, nblk);
+    const double rzn = sum_partials(slot(R, rep, 2), nblk);
+    const double rzo = sum_partials(slot(R, rep, 5), nblk);
     if (threadIdx.x == 0) beta = (rzn - rzo) / st[rep].rz[st[rep].cur];
   }
   __syncthreads();
@@ -329,12 +365,12 @@ __global__ void k_pcg_p(long Ng, const V* __restrict__ z, V* __restrict__ p,
 }
 
 // end of one CG iteration: store (r,z), advance, and (inside a graph) set the while flag
-__global__ void k_pcg_end(PcgState* st, const double* __restrict__ part, int nblk, int nrep,
-                          int* any_active, cudaGraphConditionalHandle cond, int use_cond,
+__global__ void k_pcg_end(PcgState* st, Red R, int nblk, int nrep, int* any_active,
+                          cudaGraphConditionalHandle cond, int use_cond,
                           unsigned long long* kexec) {
   const int rep = threadIdx.x >> 5;
   if (rep < nrep && !st[rep].done) {
-    const double rz = sum_partials(part + ((long)rep * 8 + 2) * nblk, nblk);
+    const double rz = sum_partials(slot(R, rep, 2), nblk);
     if ((threadIdx.x & 31) == 0) {
       PcgState& s = st[rep];
       s.cur ^= 1;
@@ -371,99 +407,87 @@ __device__ __forceinline__ float lap7f(const float* __restrict__ x, int ix, int 
   return 6.0f * c - s;  // h^2 * (-Lap_7 x)
 }
 
-// one damped-Jacobi sweep on level data: xo = xi + w h^2/6 (b - A xi).
-// first: xi = 0; b64 != NULL: b is read from the float64 residual and stored as float in
-// bf; out64 != NULL: the result goes to that float64 array instead of xo.
-__global__ void k_mg_jacobi(Grid3 G, const float* __restrict__ xi, float* __restrict__ xo,
-                            float* __restrict__ bf, const double* __restrict__ b64, int first,
-                            double* __restrict__ out64, const PcgState* __restrict__ st) {
-  const int rep = blockIdx.y;
-  if (pcg_skip(st, rep)) return;
+// one damped-Jacobi sweep: xo = xi + w h^2/6 (b - A xi); first: xi = 0; b64 != NULL: b is
+// read from the float64 residual and stored as float in bf; out64 != NULL: result to it
+__global__ void __launch_bounds__(kBX* kBY)
+k_mg_jacobi(Grid3 G, const float* __restrict__ xi, float* __restrict__ xo, float* __restrict__ bf,
+            const double* __restrict__ b64, int first, double* __restrict__ out64,
+            const PcgState* __restrict__ st) {
+  const Pt3 p = pt3(G.nx, G.ny, G.nz);
+  if (pcg_skip(st, p.rep) || !p.in) return;
   const long n = (long)G.nx * G.ny * G.nz;
   const float h2 = (float)(G.h * G.h), ih2 = 1.0f / h2;
-  const float* xr = xi + rep * n;
-  for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < n;
-       g += (long)gridDim.x * blockDim.x) {
-    const long e = rep * n + g;
-    float bv;
-    if (b64) {
-      bv = (float)b64[e];
-      bf[e] = bv;
-    } else {
-      bv = bf[e];
-    }
-    float v;
-    if (first) {
-      v = kJacobiW * h2 / 6.0f * bv;
-    } else {
-      const int ix = (int)(g % G.nx), iy = (int)((g / G.nx) % G.ny), iz = (int)(g / ((long)G.nx * G.ny));
-      float c;
-      const float ax = lap7f(xr, ix, iy, iz, G.nx, G.ny, G.nz, &c) * ih2;
-      v = c + kJacobiW * h2 / 6.0f * (bv - ax);
-    }
-    if (out64)
-      out64[e] = (double)v;
-    else
-      xo[e] = v;
+  const long g = ((long)p.iz * G.ny + p.iy) * G.nx + p.ix;
+  const long e = p.rep * n + g;
+  float bv;
+  if (b64) {
+    bv = (float)b64[e];
+    bf[e] = bv;
+  } else {
+    bv = bf[e];
   }
+  float v;
+  if (first) {
+    v = kJacobiW * h2 / 6.0f * bv;
+  } else {
+    float c;
+    const float ax = lap7f(xi + p.rep * n, p.ix, p.iy, p.iz, G.nx, G.ny, G.nz, &c) * ih2;
+    v = c + kJacobiW * h2 / 6.0f * (bv - ax);
+  }
+  if (out64)
+    out64[e] = (double)v;
+  else
+    xo[e] = v;
 }
 
-// Two damped-Jacobi sweeps from x = 0 in one pass: x1 = c b, x2 = x1 + c (b - A x1) with
-// c = w h^2/6, i.e. x2 = c (2 b - c A b); reads b at the 7-point neighbourhood.  b64: the
-// fine-level float64 residual, also stored as float into bf.
-__global__ void k_mg_pre2(Grid3 G, float* __restrict__ xo, float* __restrict__ bf,
-                          const double* __restrict__ b64, const PcgState* __restrict__ st) {
-  const int rep = blockIdx.y;
-  if (pcg_skip(st, rep)) return;
+// Two damped-Jacobi sweeps from x = 0 in one pass: x2 = c (2 b - c A b), c = w h^2/6.
+// b64: the fine-level float64 residual, also stored as float into bf.
+__global__ void __launch_bounds__(kBX* kBY)
+k_mg_pre2(Grid3 G, float* __restrict__ xo, float* __restrict__ bf, const double* __restrict__ b64,
+          const PcgState* __restrict__ st) {
+  const Pt3 p = pt3(G.nx, G.ny, G.nz);
+  if (pcg_skip(st, p.rep) || !p.in) return;
   const long n = (long)G.nx * G.ny * G.nz;
   const float h2 = (float)(G.h * G.h), ih2 = 1.0f / h2;
   const float c = kJacobiW * h2 / 6.0f;
   const long plane = (long)G.nx * G.ny;
-  for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < n;
-       g += (long)gridDim.x * blockDim.x) {
-    const int ix = (int)(g % G.nx), iy = (int)((g / G.nx) % G.ny), iz = (int)(g / plane);
-    const long e = rep * n + g;
-    float bc, s;
-    if (b64) {
-      const double* b = b64 + rep * n;
-      bc = (float)b[g];
-      s = 0.0f;
-      if (ix + 1 < G.nx) s += (float)b[g + 1];
-      if (ix > 0) s += (float)b[g - 1];
-      if (iy + 1 < G.ny) s += (float)b[g + G.nx];
-      if (iy > 0) s += (float)b[g - G.nx];
-      if (iz + 1 < G.nz) s += (float)b[g + plane];
-      if (iz > 0) s += (float)b[g - plane];
-      bf[e] = bc;
-    } else {
-      const float* b = bf + rep * n;
-      bc = b[g];
-      s = 0.0f;
-      if (ix + 1 < G.nx) s += b[g + 1];
-      if (ix > 0) s += b[g - 1];
-      if (iy + 1 < G.ny) s += b[g + G.nx];
-      if (iy > 0) s += b[g - G.nx];
-      if (iz + 1 < G.nz) s += b[g + plane];
-      if (iz > 0) s += b[g - plane];
-    }
-    const float Ab = (6.0f * bc - s) * ih2;
-    xo[e] = c * (2.0f * bc - c * Ab);
+  const long g = (long)p.iz * plane + (long)p.iy * G.nx + p.ix;
+  const long e = p.rep * n + g;
+  float bc, s = 0.0f;
+  if (b64) {
+    const double* b = b64 + p.rep * n;
+    bc = (float)b[g];
+    if (p.ix + 1 < G.nx) s += (float)b[g + 1];
+    if (p.ix > 0) s += (float)b[g - 1];
+    if (p.iy + 1 < G.ny) s += (float)b[g + G.nx];
+    if (p.iy > 0) s += (float)b[g - G.nx];
+    if (p.iz + 1 < G.nz) s += (float)b[g + plane];
+    if (p.iz > 0) s += (float)b[g - plane];
+    bf[e] = bc;
+  } else {
+    const float* b = bf + p.rep * n;
+    bc = b[g];
+    if (p.ix + 1 < G.nx) s += b[g + 1];
+    if (p.ix > 0) s += b[g - 1];
+    if (p.iy + 1 < G.ny) s += b[g + G.nx];
+    if (p.iy > 0) s += b[g - G.nx];
+    if (p.iz + 1 < G.nz) s += b[g + plane];
+    if (p.iz > 0) s += b[g - plane];
   }
+  const float Ab = (6.0f * bc - s) * ih2;
+  xo[e] = c * (2.0f * bc - c * Ab);
 }
 
-__global__ void k_mg_residual(Grid3 G, const float* __restrict__ x, const float* __restrict__ b,
-                              float* __restrict__ r, const PcgState* __restrict__ st) {
-  const int rep = blockIdx.y;
-  if (pcg_skip(st, rep)) return;
+__global__ void __launch_bounds__(kBX* kBY)
+k_mg_residual(Grid3 G, const float* __restrict__ x, const float* __restrict__ b,
+              float* __restrict__ r, const PcgState* __restrict__ st) {
+  const Pt3 p = pt3(G.nx, G.ny, G.nz);
+  if (pcg_skip(st, p.rep) || !p.in) return;
   const long n = (long)G.nx * G.ny * G.nz;
   const float ih2 = (float)(1.0 / (G.h * G.h));
-  const float* xr = x + rep * n;
-  for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < n;
-       g += (long)gridDim.x * blockDim.x) {
-    const int ix = (int)(g % G.nx), iy = (int)((g / G.nx) % G.ny), iz = (int)(g / ((long)G.nx * G.ny));
-    float c;
-    r[rep * n + g] = b[rep * n + g] - lap7f(xr, ix, iy, iz, G.nx, G.ny, G.nz, &c) * ih2;
-  }
+  const long g = ((long)p.iz * G.ny + p.iy) * G.nx + p.ix;
+  float c;
+  r[p.rep * n + g] = b[p.rep * n + g] - lap7f(x + p.rep * n, p.ix, p.iy, p.iz, G.nx, G.ny, G.nz, &c) * ih2;
 }
 
 // trilinear (cell-centred) weights along one axis: fine child f = 2I + a takes 3/4 from I
@@ -520,57 +544,43 @@ __device__ __forceinline__ float prolong_point(const float* __restrict__ xc, int
 
 // x <- x + P xc, then one damped-Jacobi sweep on the corrected x, in one pass: the
 // corrected values of the 6 neighbours are formed on the fly.  Result into xo.
-__global__ void k_mg_prolong_sweep(Grid3 F, Grid3 C, const float* __restrict__ xc,
-                                   const float* __restrict__ x, float* __restrict__ xo,
-                                   const float* __restrict__ b, const PcgState* __restrict__ st) {
-  const int rep = blockIdx.y;
-  if (pcg_skip(st, rep)) return;
+__global__ void __launch_bounds__(kBX* kBY)
+k_mg_prolong_sweep(Grid3 F, Grid3 C, const float* __restrict__ xc, const float* __restrict__ x,
+                   float* __restrict__ xo, const float* __restrict__ b,
+                   const PcgState* __restrict__ st) {
+  const Pt3 p = pt3(F.nx, F.ny, F.nz);
+  if (pcg_skip(st, p.rep) || !p.in) return;
   const long nf = (long)F.nx * F.ny * F.nz, nc = (long)C.nx * C.ny * C.nz;
-  const float* xcr = xc + rep * nc;
-  const float* xr = x + rep * nf;
+  const float* xcr = xc + p.rep * nc;
+  const float* xr = x + p.rep * nf;
   const float h2 = (float)(F.h * F.h);
   const long plane = (long)F.nx * F.ny;
-  for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < nf;
-       g += (long)gridDim.x * blockDim.x) {
-    const int fx = (int)(g % F.nx), fy = (int)((g / F.nx) % F.ny), fz = (int)(g / plane);
-    auto corr = [&](int ax, int ay, int az, long gg) {
-      return xr[gg] + prolong_point(xcr, ax, ay, az, C.nx, C.ny, C.nz);
-    };
-    const float c0 = corr(fx, fy, fz, g);
-    float s = 0.0f;
-    if (fx + 1 < F.nx) s += corr(fx + 1, fy, fz, g + 1);
-    if (fx > 0) s += corr(fx - 1, fy, fz, g - 1);
-    if (fy + 1 < F.ny) s += corr(fx, fy + 1, fz, g + F.nx);
-    if (fy > 0) s += corr(fx, fy - 1, fz, g - F.nx);
-    if (fz + 1 < F.nz) s += corr(fx, fy, fz + 1, g + plane);
-    if (fz > 0) s += corr(fx, fy, fz - 1, g - plane);
-    const float ax = (6.0f * c0 - s) / h2;
-    xo[rep * nf + g] = c0 + kJacobiW * h2 / 6.0f * (b[rep * nf + g] - ax);
-  }
+  const int fx = p.ix, fy = p.iy, fz = p.iz;
+  const long g = (long)fz * plane + (long)fy * F.nx + fx;
+  auto corr = [&](int ax, int ay, int az, long gg) {
+    return xr[gg] + prolong_point(xcr, ax, ay, az, C.nx, C.ny, C.nz);
+  };
+  const float c0 = corr(fx, fy, fz, g);
+  float s = 0.0f;
+  if (fx + 1 < F.nx) s += corr(fx + 1, fy, fz, g + 1);
+  if (fx > 0) s += corr(fx - 1, fy, fz, g - 1);
+  if (fy + 1 < F.ny) s += corr(fx, fy + 1, fz, g + F.nx);
+  if (fy > 0) s += corr(fx, fy - 1, fz, g - F.nx);
+  if (fz + 1 < F.nz) s += corr(fx, fy, fz + 1, g + plane);
+  if (fz > 0) s += corr(fx, fy, fz - 1, g - plane);
+  const float ax = (6.0f * c0 - s) / h2;
+  xo[p.rep * nf + g] = c0 + kJacobiW * h2 / 6.0f * (b[p.rep * nf + g] - ax);
 }
 
-__global__ void k_mg_restrict(Grid3 F, Grid3 C, const float* __restrict__ rf,
-                              float* __restrict__ bc, const PcgState* __restrict__ st) {
-  const int rep = blockIdx.y;
-  if (pcg_skip(st, rep)) return;
+// coarse b = (1/8) P^T r (launched over the coarse grid)
+__global__ void __launch_bounds__(kBX* kBY)
+k_mg_restrict(Grid3 F, Grid3 C, const float* __restrict__ rf, float* __restrict__ bc,
+              const PcgState* __restrict__ st) {
+  const Pt3 p = pt3(C.nx, C.ny, C.nz);
+  if (pcg_skip(st, p.rep) || !p.in) return;
   const long nf = (long)F.nx * F.ny * F.nz, nc = (long)C.nx * C.ny * C.nz;
-  for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < nc;
-       g += (long)gridDim.x * blockDim.x) {
-    const int I = (int)(g % C.nx), J = (int)((g / C.nx) % C.ny), K = (int)(g / ((long)C.nx * C.ny));
-    bc[rep * nc + g] = restrict_point(rf + rep * nf, I, J, K, F.nx, F.ny, F.nz);
-  }
-}
-
-__global__ void k_mg_prolong(Grid3 F, Grid3 C, const float* __restrict__ xc,
-                             float* __restrict__ xf, const PcgState* __restrict__ st) {
-  const int rep = blockIdx.y;
-  if (pcg_skip(st, rep)) return;
-  const long nf = (long)F.nx * F.ny * F.nz, nc = (long)C.nx * C.ny * C.nz;
-  for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < nf;
-       g += (long)gridDim.x * blockDim.x) {
-    const int fx = (int)(g % F.nx), fy = (int)((g / F.nx) % F.ny), fz = (int)(g / ((long)F.nx * F.ny));
-    xf[rep * nf + g] += prolong_point(xc + rep * nc, fx, fy, fz, C.nx, C.ny, C.nz);
-  }
+  const long g = ((long)p.iz * C.ny + p.iy) * C.nx + p.ix;
+  bc[p.rep * nc + g] = restrict_point(rf + p.rep * nf, p.ix, p.iy, p.iz, F.nx, F.ny, F.nz);
 }
 
 // ---- coarse tail of the V-cycle inside one block (levels with <= kTailMax points) ---------
@@ -706,11 +716,13 @@ __global__ void k_coarse_inverse(int nx, int ny, int nz, double h, double* __res
 // ---- host orchestration ------------------------------------------------------------------
 static Grid3 grid_of(const MgLevel& L) { return Grid3{L.nx, L.ny, L.nz, L.h}; }
 
-// one thread per point (grid-stride beyond 65535 blocks) for the pointwise multigrid kernels
-static int grid_blocks(rmgtd_ctx* ctx, long n) {
-  (void)ctx;
-  return (int)std::max<long>(1, std::min<long>(ceil_div(n, kThreads), 65535L));
+static dim3 grid3(int nx, int ny, int nz, int nrep) {
+  return dim3(ceil_div(nx, kBX), ceil_div(ny, kBY), nz * nrep);
 }
+static int nblk3(int nx, int ny, int nz) { return ceil_div(nx, kBX) * ceil_div(ny, kBY) * nz; }
+static const dim3 kBlock3(kBX, kBY, 1);
+
+static Red red_of(rmgtd_ctx* ctx) { return Red{ctx->red_part, ctx->red_cap}; }
 
 // z = M r, M = one float32 V-cycle.  Level-0 input / output are float64 (r64, z64) or
 // float32 (r32, z32: the V-cycle then iterates directly in z32).
@@ -724,21 +736,19 @@ static int vcycle(rmgtd_ctx* ctx, const double* r64, double* z64, const float* r
   for (int l = 0; l < nmulti; ++l) {
     MgLevel& L = ctx->mg[l];
     const Grid3 G = grid_of(L);
-    const int bl = grid_blocks(ctx, L.n);
+    const dim3 gr = grid3(L.nx, L.ny, L.nz, nrep);
     const bool coarsest = (l == nl - 1);
     float* lx = (l == 0 && z32) ? z32 : L.x;
     float* lb = (l == 0 && r32) ? const_cast<float*>(r32) : L.b;
     const double* in64 = (l == 0 && !r32) ? r64 : nullptr;
     double* out64 = (l == 0 && !z32) ? z64 : nullptr;
     if (!coarsest) {
-      // pre-smoothing: two sweeps from zero in one kernel
-      k_mg_pre2<<<dim3(bl, nrep), kThreads, 0, s>>>(G, lx, lb, in64, st);
+      k_mg_pre2<<<gr, kBlock3, 0, s>>>(G, lx, lb, in64, st);
       ++ctx->launches;
-      k_mg_residual<<<dim3(bl, nrep), kThreads, 0, s>>>(G, lx, lb, L.t, st);
+      k_mg_residual<<<gr, kBlock3, 0, s>>>(G, lx, lb, L.t, st);
       ++ctx->launches;
       MgLevel& C = ctx->mg[l + 1];
-      k_mg_restrict<<<dim3(grid_blocks(ctx, C.n), nrep), kThreads, 0, s>>>(G, grid_of(C), L.t,
-                                                                            C.b, st);
+      k_mg_restrict<<<grid3(C.nx, C.ny, C.nz, nrep), kBlock3, 0, s>>>(G, grid_of(C), L.t, C.b, st);
       ++ctx->launches;
       RMGTD_LAUNCH(ctx, "k_mg_descend");
       continue;
@@ -748,9 +758,9 @@ static int vcycle(rmgtd_ctx* ctx, const double* r64, double* z64, const float* r
     int cur = (kCoarseSweeps % 2 == 1) ? 0 : 1;  // the last sweep writes x
     for (int sw = 0; sw < kCoarseSweeps; ++sw) {
       const bool last_out64 = (out64 && sw == kCoarseSweeps - 1);
-      k_mg_jacobi<<<dim3(bl, nrep), kThreads, 0, s>>>(
-          G, bufs[cur ^ 1], bufs[cur], lb, sw == 0 ? in64 : nullptr, sw == 0,
-          last_out64 ? out64 : nullptr, st);
+      k_mg_jacobi<<<gr, kBlock3, 0, s>>>(G, bufs[cur ^ 1], bufs[cur], lb,
+                                         sw == 0 ? in64 : nullptr, sw == 0,
+                                         last_out64 ? out64 : nullptr, st);
       ++ctx->launches;
       cur ^= 1;
     }
@@ -774,15 +784,15 @@ static int vcycle(rmgtd_ctx* ctx, const double* r64, double* z64, const float* r
     MgLevel& L = ctx->mg[l];
     MgLevel& C = ctx->mg[l + 1];
     const Grid3 G = grid_of(L);
-    const int bl = grid_blocks(ctx, L.n);
+    const dim3 gr = grid3(L.nx, L.ny, L.nz, nrep);
     float* lx = (l == 0 && z32) ? z32 : L.x;
     float* lb = (l == 0 && r32) ? const_cast<float*>(r32) : L.b;
     double* out64 = (l == 0 && !z32) ? z64 : nullptr;
     // coarse correction and the first post-sweep in one kernel (result in L.t), then the
     // second post-sweep back into x (or the float64 output)
-    k_mg_prolong_sweep<<<dim3(bl, nrep), kThreads, 0, s>>>(G, grid_of(C), C.x, lx, L.t, lb, st);
+    k_mg_prolong_sweep<<<gr, kBlock3, 0, s>>>(G, grid_of(C), C.x, lx, L.t, lb, st);
     ++ctx->launches;
-    k_mg_jacobi<<<dim3(bl, nrep), kThreads, 0, s>>>(G, L.t, lx, lb, nullptr, 0, out64, st);
+    k_mg_jacobi<<<gr, kBlock3, 0, s>>>(G, L.t, lx, lb, nullptr, 0, out64, st);
     ++ctx->launches;
     RMGTD_LAUNCH(ctx, "k_mg_ascend");
   }
@@ -852,10 +862,17 @@ int setup_multigrid(rmgtd_ctx* ctx) {
   ctx->ghost = (double*)dev_alloc(ctx, sizeof(double) * 4 * (size_t)ctx->Ng);
   if (!ctx->ghost) return set_error(ctx, RMGTD_ENOMEM, "ghost fields");
   const Grid3 G{ctx->nx, ctx->ny, ctx->nz, ctx->h};
-  k_ghost_fields<<<grid_blocks(ctx, ctx->Ng), kThreads, 0, ctx->stream>>>(G, ctx->ghost);
+  const int bl = (int)std::max<long>(1, std::min<long>(ceil_div(ctx->Ng, kThreads), 65535L));
+  k_ghost_fields<<<bl, kThreads, 0, ctx->stream>>>(G, ctx->ghost);
   ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_ghost_fields");
   return RMGTD_OK;
+}
+
+// slot capacity of the reduction partials: the larger of the 3-D fine-grid block count and
+// the grid-stride block count
+int poisson_red_cap(int nx, int ny, int nz, int red_blocks) {
+  return std::max(nblk3(nx, ny, nz), red_blocks);
 }
 
 // Buffers of one Hartree solve: float64 (the solve of rho itself) or float32 (the change
@@ -897,35 +914,37 @@ int hartree_begin(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* c
                   int nrep, cudaGraphConditionalHandle cond, int use_cond, int f32) {
   const Grid3 G{ctx->nx, ctx->ny, ctx->nz, ctx->h};
   const long Ng = ctx->Ng;
-  const int nb = ctx->red_blocks;
-  const dim3 grid(nb, nrep);
+  const int rb = ctx->red_blocks;
+  const dim3 g3 = grid3(ctx->nx, ctx->ny, ctx->nz, nrep);
+  const int nb3 = nblk3(ctx->nx, ctx->ny, ctx->nz);
   cudaStream_t s = ctx->stream;
-  double* part = ctx->red_part;
+  const Red R = red_of(ctx);
   const PcgBufs B = pcg_bufs(ctx, vh, f32);
-  k_moments<<<grid, kThreads, 0, s>>>(G, rho, B.rho_ref, part, ctl);
+  k_moments<<<g3, kBlock3, 0, s>>>(G, rho, B.rho_ref, R, ctl);
   ++ctx->launches;
   if (B.f32) {
-    k_pcg_init<float><<<grid, kThreads, 0, s>>>(G, rho, B.rho_ref, ctx->ghost, (float*)B.x,
-                                                (float*)B.b, (float*)B.r, part, zero_bc, ctl);
+    k_pcg_init<float><<<g3, kBlock3, 0, s>>>(G, rho, B.rho_ref, ctx->ghost, (float*)B.x,
+                                             (float*)B.b, (float*)B.r, R, nb3, zero_bc, ctl);
   } else {
-    k_pcg_init<double><<<grid, kThreads, 0, s>>>(G, rho, nullptr, ctx->ghost, (double*)B.x,
-                                                 (double*)B.b, (double*)B.r, part, zero_bc, ctl);
+    k_pcg_init<double><<<g3, kBlock3, 0, s>>>(G, rho, nullptr, ctx->ghost, (double*)B.x,
+                                              (double*)B.b, (double*)B.r, R, nb3, zero_bc, ctl);
   }
   ++ctx->launches;
-  k_pcg_state_init<<<1, 32 * nrep, 0, s>>>(ctx->pcg, part, nb, B.tol, ctl, nrep);
+  k_pcg_state_init<<<1, 32 * nrep, 0, s>>>(ctx->pcg, R, nb3, B.tol, ctl, nrep);
   ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_pcg_init");
   int rc = B.f32 ? vcycle(ctx, nullptr, nullptr, (float*)B.r, (float*)B.z, nrep)
                  : vcycle(ctx, (double*)B.r, (double*)B.z, nullptr, nullptr, nrep);
   if (rc) return rc;
+  const dim3 gf(rb, nrep);
   if (B.f32)
-    k_pcg_rz<float><<<grid, kThreads, 0, s>>>(Ng, (float*)B.r, (float*)B.z, (float*)B.p, 1, part,
-                                              ctx->pcg);
+    k_pcg_rz<float><<<gf, kThreads, 0, s>>>(Ng, (float*)B.r, (float*)B.z, (float*)B.p, 1, R,
+                                            ctx->pcg);
   else
-    k_pcg_rz<double><<<grid, kThreads, 0, s>>>(Ng, (double*)B.r, (double*)B.z, (double*)B.p, 1,
-                                               part, ctx->pcg);
+    k_pcg_rz<double><<<gf, kThreads, 0, s>>>(Ng, (double*)B.r, (double*)B.z, (double*)B.p, 1, R,
+                                             ctx->pcg);
   ++ctx->launches;
-  k_pcg_rz_store<<<1, 32 * nrep, 0, s>>>(ctx->pcg, part, nb, nrep, cond, use_cond);
+  k_pcg_rz_store<<<1, 32 * nrep, 0, s>>>(ctx->pcg, R, rb, nrep, cond, use_cond);
   ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_pcg_rz");
   return RMGTD_OK;
@@ -937,25 +956,27 @@ int hartree_iteration(rmgtd_ctx* ctx, double* vh, int nrep, cudaGraphConditional
                       int use_cond, int f32) {
   const Grid3 G{ctx->nx, ctx->ny, ctx->nz, ctx->h};
   const long Ng = ctx->Ng;
-  const int nb = ctx->red_blocks;
-  const dim3 grid(nb, nrep);
+  const int rb = ctx->red_blocks;
+  const dim3 g3 = grid3(ctx->nx, ctx->ny, ctx->nz, nrep);
+  const int nb3 = nblk3(ctx->nx, ctx->ny, ctx->nz);
+  const dim3 gf(rb, nrep);
   cudaStream_t s = ctx->stream;
-  double* part = ctx->red_part;
+  const Red R = red_of(ctx);
   const PcgBufs B = pcg_bufs(ctx, vh, f32);
   if (B.f32) {
-    k_pcg_Ap<float><<<grid, kThreads, 0, s>>>(G, (float*)B.p, (float*)B.Ap, part, ctx->pcg);
+    k_pcg_Ap<float><<<g3, kBlock3, 0, s>>>(G, (float*)B.p, (float*)B.Ap, R, ctx->pcg);
     ++ctx->launches;
-    k_pcg_xr<float><<<grid, kThreads, 0, s>>>(Ng, (float*)B.x, (float*)B.r, (float*)B.p,
-                                              (float*)B.Ap, (float*)B.z, part, ctx->pcg);
+    k_pcg_xr<float><<<gf, kThreads, 0, s>>>(Ng, (float*)B.x, (float*)B.r, (float*)B.p,
+                                            (float*)B.Ap, (float*)B.z, R, nb3, ctx->pcg);
     ++ctx->launches;
   } else {
-    k_pcg_Ap<double><<<grid, kThreads, 0, s>>>(G, (double*)B.p, (double*)B.Ap, part, ctx->pcg);
+    k_pcg_Ap<double><<<g3, kBlock3, 0, s>>>(G, (double*)B.p, (double*)B.Ap, R, ctx->pcg);
     ++ctx->launches;
-    k_pcg_xr<double><<<grid, kThreads, 0, s>>>(Ng, (double*)B.x, (double*)B.r, (double*)B.p,
-                                               (double*)B.Ap, (double*)B.z, part, ctx->pcg);
+    k_pcg_xr<double><<<gf, kThreads, 0, s>>>(Ng, (double*)B.x, (double*)B.r, (double*)B.p,
+                                             (double*)B.Ap, (double*)B.z, R, nb3, ctx->pcg);
     ++ctx->launches;
   }
-  k_pcg_check<<<1, 32 * nrep, 0, s>>>(ctx->pcg, part, nb, B.tol, ctx->opt.poisson_max_iter, nrep,
+  k_pcg_check<<<1, 32 * nrep, 0, s>>>(ctx->pcg, R, rb, B.tol, ctx->opt.poisson_max_iter, nrep,
                                       ctx->status);
   ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_pcg_iteration");
@@ -963,19 +984,19 @@ int hartree_iteration(rmgtd_ctx* ctx, double* vh, int nrep, cudaGraphConditional
                  : vcycle(ctx, (double*)B.r, (double*)B.z, nullptr, nullptr, nrep);
   if (rc) return rc;
   if (B.f32) {
-    k_pcg_rz<float><<<grid, kThreads, 0, s>>>(Ng, (float*)B.r, (float*)B.z, (float*)B.p, 0, part,
-                                              ctx->pcg);
+    k_pcg_rz<float><<<gf, kThreads, 0, s>>>(Ng, (float*)B.r, (float*)B.z, (float*)B.p, 0, R,
+                                            ctx->pcg);
     ++ctx->launches;
-    k_pcg_p<float><<<grid, kThreads, 0, s>>>(Ng, (float*)B.z, (float*)B.p, part, ctx->pcg);
+    k_pcg_p<float><<<gf, kThreads, 0, s>>>(Ng, (float*)B.z, (float*)B.p, R, rb, ctx->pcg);
     ++ctx->launches;
   } else {
-    k_pcg_rz<double><<<grid, kThreads, 0, s>>>(Ng, (double*)B.r, (double*)B.z, (double*)B.p, 0,
-                                               part, ctx->pcg);
+    k_pcg_rz<double><<<gf, kThreads, 0, s>>>(Ng, (double*)B.r, (double*)B.z, (double*)B.p, 0, R,
+                                             ctx->pcg);
     ++ctx->launches;
-    k_pcg_p<double><<<grid, kThreads, 0, s>>>(Ng, (double*)B.z, (double*)B.p, part, ctx->pcg);
+    k_pcg_p<double><<<gf, kThreads, 0, s>>>(Ng, (double*)B.z, (double*)B.p, R, rb, ctx->pcg);
     ++ctx->launches;
   }
-  k_pcg_end<<<1, 32 * nrep, 0, s>>>(ctx->pcg, part, nb, nrep, ctx->pcg_any, cond, use_cond,
+  k_pcg_end<<<1, 32 * nrep, 0, s>>>(ctx->pcg, R, rb, nrep, ctx->pcg_any, cond, use_cond,
                                      ctx->kexec);
   ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_pcg_end");
@@ -999,7 +1020,7 @@ __global__ void k_extrap(long n, T* __restrict__ x, T* __restrict__ prev,
 int hartree_extrapolate(rmgtd_ctx* ctx) {
   if (!ctx->hartree_xc) return RMGTD_OK;
   const long n = (long)ctx->nrep * ctx->Ng;
-  const int bl = grid_blocks(ctx, n);
+  const int bl = (int)std::max<long>(1, std::min<long>(ceil_div(n, kThreads), 65535L));
   if (ctx->mixed)
     k_extrap<float><<<bl, kThreads, 0, ctx->stream>>>(n, ctx->dvh32, ctx->dvh_prev32, ctx->failed);
   else

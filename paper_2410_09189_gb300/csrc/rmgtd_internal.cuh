@@ -141,7 +141,8 @@ struct rmgtd_ctx {
   double *pcg_b = nullptr, *pcg_r = nullptr, *pcg_z = nullptr, *pcg_p = nullptr,
          *pcg_Ap = nullptr;    // [nrep][Ng]
   double* red_part = nullptr;  // reduction partials
-  int red_blocks = 0;
+  int red_blocks = 0;                // blocks of the grid-stride reduction kernels
+  int red_cap = 0;                   // capacity of one partial slot
   rmgtd::PcgState* pcg = nullptr;   // [nrep]
   int* pcg_any = nullptr;           // device flag: some replica still iterating
   int* pcg_any_host = nullptr;      // pinned
@@ -331,6 +332,7 @@ int subspace_update(rmgtd_ctx* ctx, double alpha, double* err_dev);
 int orthonormalize(rmgtd_ctx* ctx);
 // k_poisson.cu
 int setup_multigrid(rmgtd_ctx* ctx);
+int poisson_red_cap(int nx, int ny, int nz, int red_blocks);
 int hartree_dev(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* ctl, int zero_bc,
                 int nrep, int f32);
 int hartree_graph(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* ctl, int nrep,
