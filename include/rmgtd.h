@@ -226,6 +226,26 @@ int rmgtd_profile(rmgtd_ctx* ctx, int enable);
 int rmgtd_profile_read(rmgtd_ctx* ctx, double* phase_ms, long long* phase_calls,
                        long long* launches);
 
+/* Allocation-free Gram contraction  C = scale * A^T diag(w) B  (N x N, row-major) for two
+ * orbital blocks A, B of n_orb columns of n_grid points each (orbital-major device arrays,
+ * as in rmgtd_system.phi0), w (n_grid device doubles) or NULL for w = 1; c_dev receives
+ * n_orb * n_orb doubles.  With A = B = Phi, w = V and scale = h^3 this is the Hamiltonian
+ * update matrix; with w = x, y, z the dipole matrices; with w = NULL the overlap.
+ *
+ * The paper has no counterpart: this entry point exists for callers that cannot allocate
+ * device memory when they call -- code that runs while a stream is being captured into a
+ * CUDA graph, hosts that own all device memory through their own arena, loops that cannot
+ * take cudaMalloc's implicit synchronisation.  It allocates nothing: its scratch is a fixed
+ * 8 MiB array of float64 inside the library (held on every GPU that loads the library until
+ * the process exits), so n_orb must satisfy n_orb^2 <= 1048576 (n_orb <= 1024); larger sizes
+ * return RMGTD_EINVAL.  The first call on a device looks up the array's address on that
+ * device (make that first call before any stream capture).  All calls share the array:
+ * calls whose work overlaps on the device race; serialise them on one stream.  Work is
+ * enqueued on `stream` (cudaStream_t, NULL = default stream) and the call does not wait.
+ * Errors (message through rmgtd_last_error(NULL)): RMGTD_EINVAL, RMGTD_ECUDA. */
+int rmgtd_gram_noalloc(const double* a_dev, const double* b_dev, const double* w_dev,
+                       int n_orb, long long n_grid, double scale, double* c_dev, void* stream);
+
 /* Message of the last error on `ctx` (thread-local message when ctx is NULL). */
 const char* rmgtd_last_error(const rmgtd_ctx* ctx);
 

@@ -99,6 +99,7 @@ def load_library(path: Optional[str] = None):
         "rmgtd_time": (i, [vp, _c_double_p, ctypes.POINTER(ctypes.c_longlong)]),
         "rmgtd_last_error": (ctypes.c_char_p, [vp]),
         "rmgtd_profile": (i, [vp, i]),
+        "rmgtd_gram_noalloc": (i, [vp, vp, vp, i, ctypes.c_longlong, d, vp, vp]),
         "rmgtd_profile_read": (i, [vp, _c_double_p, ctypes.POINTER(ctypes.c_longlong),
                                    ctypes.POINTER(ctypes.c_longlong)]),
     }
