@@ -192,32 +192,6 @@ static int add_while(rmgtd_ctx* ctx, cudaGraphConditionalHandle h, cudaGraph_t* 
   return RMGTD_OK;
 }
 
-// Hartree solve inside a captured graph: prologue (which arms the loop), then a device-side
-// while loop of CG iterations captured on the second auxiliary stream.
-int hartree_graph(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* ctl, int nrep,
-                  int f32) {
-  cudaGraphConditionalHandle hp;
-  int rc = new_handle(ctx, &hp, false);
-  if (rc) return rc;
-  rc = hartree_begin(ctx, rho, vh, ctl, 0, nrep, hp, 1, f32);
-  if (rc) return rc;
-  cudaGraph_t body;
-  rc = add_while(ctx, hp, &body);
-  if (rc) return rc;
-  cudaStream_t saved = ctx->stream;
-  RMGTD_CUDA(ctx, cudaStreamBeginCaptureToGraph(ctx->aux[1], body, nullptr, nullptr, 0,
-                                                cudaStreamCaptureModeRelaxed));
-  ctx->stream = ctx->aux[1];
-  const long long l0 = ctx->launches;
-  rc = hartree_iteration(ctx, vh, nrep, hp, 1, f32);
-  ctx->cap_pcg = (int)(ctx->launches - l0);
-  ctx->stream = saved;
-  cudaGraph_t out;
-  cudaError_t e = cudaStreamEndCapture(ctx->aux[1], &out);
-  if (rc) return rc;
-  RMGTD_CUDA(ctx, e);
-  return RMGTD_OK;
-}
 
 // ---- one density-functional evaluation: H_1 <- DFT(rho(P)) (Algorithm 1 line 26) ------------
 // S: Re P per replica.  Writes rho, vh, vxc, exc, vhxc and H1 (in place) for active
@@ -231,8 +205,7 @@ int dft_eval(rmgtd_ctx* ctx, const double* S, const RepCtl* ctl, unsigned long l
   if (rc) return rc;
   if (ctx->hartree_xc) {
     ph_begin(ctx, PH_HARTREE);
-    rc = ctx->capturing ? hartree_graph(ctx, ctx->rho, ctx->vh, ctl, nrep, mixed)
-                        : hartree_dev(ctx, ctx->rho, ctx->vh, ctl, 0, nrep, mixed);
+    rc = hartree_coop(ctx, ctx->rho, ctx->vh, ctl, 0, nrep, mixed);
     ph_end(ctx);
     if (rc) return rc;
   }
@@ -261,7 +234,7 @@ int refresh_fields(rmgtd_ctx* ctx) {
   int rc = rho_dev(ctx, ctx->S0, ctx->rho, nullptr, ctx->nrep);
   if (rc) return rc;
   if (ctx->hartree_xc) {
-    rc = hartree_dev(ctx, ctx->rho, ctx->vh, nullptr, 0, ctx->nrep, 0);
+    rc = hartree_coop(ctx, ctx->rho, ctx->vh, nullptr, 0, ctx->nrep, 0);
     if (rc) return rc;
   }
   rc = launch_lda(ctx, ctx->rho, ctx->hartree_xc ? ctx->vh : nullptr,
@@ -330,7 +303,6 @@ void rmgtd_destroy(rmgtd_ctx* ctx) {
   ctx->buffers.clear();
   if (ctx->ctl_host) cudaFreeHost(ctx->ctl_host);
   if (ctx->obs_host) cudaFreeHost(ctx->obs_host);
-  if (ctx->pcg_any_host) cudaFreeHost(ctx->pcg_any_host);
   if (ctx->stats_host) cudaFreeHost(ctx->stats_host);
   for (auto& e : ctx->ev_pool) cudaEventDestroy(e);
   for (int i = 0; i < 3; ++i)
@@ -367,7 +339,7 @@ static int create_impl(const rmgtd_system* sys, const rmgtd_options* opt, rmgtd_
   if (!ctx->coop_ok) return set_error(ctx, RMGTD_ECUDA, "device lacks cooperative launch");
   // blocks of the grid-stride reduction kernels: about one point per thread up to 2048
   ctx->red_blocks = 2 * ctx->num_sms;
-  ctx->red_cap = poisson_red_cap(ctx->nx, ctx->ny, ctx->nz, ctx->red_blocks);
+  ctx->red_cap = poisson_red_cap(ctx->num_sms, ctx->red_blocks);
 
   ctx->f.assign(N, 0.0);
   for (int i = 0; i < N; ++i) ctx->f[i] = sys->f ? sys->f[i] : (i < sys->nocc ? 2.0 : 0.0);
@@ -399,9 +371,10 @@ static int create_impl(const rmgtd_system* sys, const rmgtd_options* opt, rmgtd_
   ctx->pcg_z = (double*)A(gsz * nrep);
   ctx->pcg_p = (double*)A(gsz * nrep);
   ctx->pcg_Ap = (double*)A(gsz * nrep);
+  ctx->pcg_Az = (double*)A(gsz * nrep);
+  ctx->bar2 = (unsigned*)A(sizeof(unsigned));
   ctx->red_part = (double*)A(sizeof(double) * (size_t)nrep * 8 * ctx->red_cap);
   ctx->pcg = (PcgState*)A(sizeof(PcgState) * nrep);
-  ctx->pcg_any = (int*)A(sizeof(int));
   ctx->ctl = (RepCtl*)A(sizeof(RepCtl) * nrep);
   ctx->bar = (unsigned*)A(sizeof(unsigned));
   ctx->errslots = (unsigned long long*)A(sizeof(unsigned long long) * (size_t)nrep * (opt->max_terms + 1));
@@ -426,7 +399,6 @@ static int create_impl(const rmgtd_system* sys, const rmgtd_options* opt, rmgtd_
     return set_error(ctx, RMGTD_ENOMEM, "device allocation failed");
   RMGTD_CUDA(ctx, cudaMallocHost((void**)&ctx->ctl_host, sizeof(RepCtl) * (nrep + 2)));
   RMGTD_CUDA(ctx, cudaMallocHost((void**)&ctx->obs_host, sizeof(double) * 8 * nrep));
-  RMGTD_CUDA(ctx, cudaMallocHost((void**)&ctx->pcg_any_host, sizeof(int)));
   RMGTD_CUDA(ctx, cudaMallocHost((void**)&ctx->stats_host, sizeof(RepCtl) * ctx->stats_cap * nrep));
   RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->failed, 0, sizeof(int), ctx->stream));
   RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->kexec, 0, 2 * sizeof(unsigned long long), ctx->stream));
@@ -557,9 +529,15 @@ static int create_impl(const rmgtd_system* sys, const rmgtd_options* opt, rmgtd_
     ctx->pcg32_z = (float*)A(fsz * nrep);
     ctx->pcg32_p = (float*)A(fsz * nrep);
     ctx->pcg32_Ap = (float*)A(fsz * nrep);
-    if (!ctx->phi32 || !ctx->pcg32_Ap || !ctx->dvh32 || !ctx->Href || !ctx->vh_ref)
+    ctx->pcg32_Az = (float*)A(fsz * nrep);
+    ctx->drho32 = (float*)A(fsz * nrep);
+    ctx->ghost32 = (float*)A(fsz * 4);
+    if (!ctx->phi32 || !ctx->pcg32_Az || !ctx->dvh32 || !ctx->Href || !ctx->vh_ref ||
+        !ctx->drho32 || !ctx->ghost32)
       return set_error(ctx, RMGTD_ENOMEM, "mixed-precision buffers");
     rc = to_float(ctx, ctx->phi, ctx->phi32, (long)N * Ng);
+    if (rc) return rc;
+    rc = to_float(ctx, ctx->ghost, ctx->ghost32, 4L * Ng);
     if (rc) return rc;
     RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->Sref, ctx->S0, msz, cudaMemcpyDeviceToDevice, ctx->stream));
     RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->Href, ctx->H0, msz, cudaMemcpyDeviceToDevice, ctx->stream));
@@ -594,8 +572,8 @@ int rmgtd_create(const rmgtd_system* sys, const rmgtd_options* opt_in, rmgtd_ctx
       (sys->nproj > 0 && (!sys->proj_atom || !sys->proj_l || !sys->proj_rc || !sys->E_kb)))
     return set_error(nullptr, RMGTD_EINVAL, "projector arrays missing");
   if (opt.nrep < 1 || opt.nrep > 32) return set_error(nullptr, RMGTD_EINVAL, "nrep must be 1..32");
-  if ((long)sys->nz * opt.nrep > 65535)
-    return set_error(nullptr, RMGTD_EINVAL, "nz * nrep must not exceed 65535");
+  if ((long long)sys->nx * sys->ny * sys->nz * opt.nrep >= (1ll << 31) - (1ll << 22))
+    return set_error(nullptr, RMGTD_EINVAL, "nx * ny * nz * nrep must be below 2^31 - 2^22");
   if (!(opt.dt > 0) || !(opt.H_thrs > 0) || !(opt.dP_thrs > 0) || opt.max_scf < 1 ||
       opt.max_terms < 1 || !(opt.poisson_tol > 0) || opt.poisson_max_iter < 1)
     return set_error(nullptr, RMGTD_EINVAL, "invalid options");
@@ -687,7 +665,7 @@ static int build_step_graph(rmgtd_ctx* ctx) {
       ctx->stream = ctx->aux[0];
       const long long l0 = ctx->launches;
       rc = enqueue_pass(ctx, hs, 1);
-      ctx->cap_scf = (int)(ctx->launches - l0) - ctx->cap_pcg;
+      ctx->cap_scf = (int)(ctx->launches - l0);
       ctx->stream = main;
       cudaGraph_t out;
       e = cudaStreamEndCapture(ctx->aux[0], &out);
@@ -825,8 +803,7 @@ int rmgtd_profile_read(rmgtd_ctx* ctx, double* phase_ms, long long* phase_calls,
   if (launches) {
     unsigned long long kx[2] = {0, 0};
     RMGTD_CUDA(ctx, cudaMemcpy(kx, ctx->kexec, sizeof(kx), cudaMemcpyDeviceToHost));
-    *launches = ctx->launches + ctx->graph_steps * ctx->cap_top +
-                (long long)kx[0] * ctx->cap_scf + (long long)kx[1] * ctx->cap_pcg;
+    *launches = ctx->launches + ctx->graph_steps * ctx->cap_top + (long long)kx[0] * ctx->cap_scf;
   }
   return RMGTD_OK;
 }
@@ -921,7 +898,7 @@ int rmgtd_hartree(rmgtd_ctx* ctx, const double* rho_dev, double* vh_dev) {
   if (!ctx) return set_error(nullptr, RMGTD_EINVAL, "ctx is NULL");
   if (!rho_dev || !vh_dev) return set_error(ctx, RMGTD_EINVAL, "hartree: NULL pointer");
   RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream));
-  int rc = hartree_dev(ctx, rho_dev, vh_dev, nullptr, 0, 1, 0);
+  int rc = hartree_coop(ctx, rho_dev, vh_dev, nullptr, 0, 1, 0);
   if (rc) return rc;
   return check_status(ctx, "hartree");
 }

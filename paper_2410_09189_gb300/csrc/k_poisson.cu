@@ -12,13 +12,16 @@
 // trilinear prolongation and its transpose/8 as restriction; the levels with <= 4096 points
 // run inside one block, whose coarsest level is solved exactly.  The float64 path iterates
 // on V itself; the mixed path iterates in float32 on the change of V relative to the
-// reference potential.  Stopping test, scalars and reductions are float64.
+// reference potential, with float32 right-hand side and dot products summed per warp in
+// float32 and across warps and blocks in float64 (float64 runs at a small fraction of the
+// float32 rate on this GPU, so no per-point float64 work remains in that solve).
 //
-// Layout of the launches: stencil kernels run one thread per grid point on a 3-D launch
-// grid (32 x 8 threads per x-y tile, blockIdx.z = plane + nz * replica), so no index is
-// divided; pointwise vector updates run a fixed number of grid-stride blocks.  Every kernel
-// returns at once for replicas whose solve has converged, so a fixed launch sequence (eager
-// or inside a CUDA-graph while loop) is correct.
+// One cooperative launch runs the whole solve: prologue, every CG iteration and every
+// V-cycle phase, separated by grid barriers (15 per iteration at 64^3).  A p = A z +
+// beta A p_old is carried as a vector, so the 37-point operator is applied once per
+// iteration to z, and (p, A p) follows from four dot products taken with A z.  Every block
+// sums the per-block partials of a reduction in the same order, so all blocks take the
+// same decisions and the result does not depend on timing.
 #include <math.h>
 
 #include "rmgtd_internal.cuh"
@@ -32,62 +35,62 @@ constexpr int kPre = 2, kPost = 2, kCoarseSweeps = 40;
 // relative residual of the float32 correction solve of the mixed path (float32 CG reaches
 // ~1e-6-1e-7; the correction is small next to the float64 reference potential)
 constexpr double kMixedPoissonTol = 1e-6;
-constexpr int kBX = 32, kBY = 8;   // x-y tile of the 3-D launches
 
 struct Grid3 {
   int nx, ny, nz;
   double h;
 };
 
-// Reduction partials: slot s of replica r starts at part + (r * 8 + s) * cap.
-//   0 (b,b)  1 (r,r)  2 (r,z)  3 (p,Ap)  4..7 moments of rho   5 also (r_new, z_old)
-struct Red {
-  double* part;
-  int cap;
+// Division of 0 <= x < 2^31 by a fixed d >= 1 with one multiply-high (Granlund & Montgomery,
+// "Division by invariant integers using multiplication", 1994): with l = ceil(log2 d) and
+// m = ceil(2^(31+l) / d), floor(x / d) = (x m) >> (31 + l) exactly, because
+// x m / 2^(31+l) - x / d < x / 2^(31+l) < 2^-l <= 1 / d.
+struct FastDiv {
+  unsigned long long m;
+  int s;
+  int d;
 };
-__device__ __forceinline__ double* slot(Red R, int rep, int s) {
-  return R.part + ((long)rep * 8 + s) * R.cap;
+inline FastDiv make_fastdiv(int d) {
+  int l = 0;
+  while ((1ll << l) < d) ++l;
+  FastDiv f;
+  f.s = 31 + l;
+  f.m = ((1ull << f.s) + (unsigned long long)d - 1) / (unsigned long long)d;
+  f.d = d;
+  return f;
+}
+__host__ __device__ __forceinline__ int fdiv(int x, const FastDiv& f) {
+  return (int)(((unsigned long long)(unsigned)x * f.m) >> f.s);
 }
 
-__device__ __forceinline__ bool pcg_skip(const PcgState* st, int rep) { return st[rep].done != 0; }
-
-__device__ __forceinline__ double sum_partials(const double* p, int n) {
-  // every lane of the calling warp returns the same fixed-order sum
-  double s = 0.0;
-  for (int b = (threadIdx.x & 31); b < n; b += 32) s += p[b];
-  return warp_sum(s);
-}
-
-// 3-D launch helpers: thread (ix, iy) of plane iz of replica rep
-struct Pt3 {
-  int ix, iy, iz, rep;
-  bool in;
-  int blin;   // linear block id within the replica
-  int nblk;   // blocks per replica
+constexpr int kMaxLevels = 12;
+// one multi-block level of the hierarchy, replicas stacked: [rep][n]
+struct Level {
+  int nx, ny, nz, n;
+  float h2;
+  FastDiv dx, dy, dn;     // division by nx, ny, n
+  float *x, *b, *t;
 };
-__device__ __forceinline__ Pt3 pt3(int nx, int ny, int nz) {
-  Pt3 p;
-  p.ix = blockIdx.x * kBX + threadIdx.x;
-  p.iy = blockIdx.y * kBY + threadIdx.y;
-  p.iz = blockIdx.z % nz;
-  p.rep = blockIdx.z / nz;
-  p.in = (p.ix < nx) && (p.iy < ny);
-  p.blin = (p.iz * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-  p.nblk = gridDim.x * gridDim.y * nz;
-  return p;
-}
-// block sum for 32 x 8 blocks (each y-row is one warp); valid in thread (0, 0)
-__device__ __forceinline__ double block_sum_2d(double v, double* sh) {
-  v = warp_sum(v);
-  __syncthreads();
-  if (threadIdx.x == 0) sh[threadIdx.y] = v;
-  __syncthreads();
-  double s = 0.0;
-  if (threadIdx.y == 0) {
-    s = (threadIdx.x < kBY) ? sh[threadIdx.x] : 0.0;
-    s = warp_sum(s);
-  }
-  return s;
+// levels solved inside one block (no replica stride: one block per replica)
+struct Tail {
+  int nl;
+  int nx[kMaxLevels], ny[kMaxLevels], nz[kMaxLevels], n[kMaxLevels];
+  float h2[kMaxLevels];
+  FastDiv dx[kMaxLevels], dy[kMaxLevels];
+};
+struct LevelTable {
+  int nl;       // all levels
+  int nmulti;   // levels [0, nmulti) run across the grid; [nmulti, nl) inside one block
+  Level L[kMaxLevels];
+  Tail T;
+};
+
+__device__ __forceinline__ void xyz_of(int g, int nx, int ny, const FastDiv& dx,
+                                       const FastDiv& dy, int& ix, int& iy, int& iz) {
+  const int q = fdiv(g, dx);
+  ix = g - q * nx;
+  iz = fdiv(q, dy);
+  iy = q - iz * ny;
 }
 
 // ---- set-up: ghost response fields G0, Gx, Gy, Gz ------------------------------------------
@@ -127,274 +130,32 @@ __global__ void k_ghost_fields(Grid3 G, double* __restrict__ gf) {
   }
 }
 
-// ---- multipole moments of rho (or rho - rho_ref): partials into slots 4..7 ------------------
-__global__ void __launch_bounds__(kBX* kBY)
-k_moments(Grid3 G, const double* __restrict__ rho, const double* __restrict__ rho_ref, Red R,
-          const RepCtl* __restrict__ ctl) {
-  const Pt3 p = pt3(G.nx, G.ny, G.nz);
-  if (ctl && !ctl[p.rep].active) return;
-  double q[4] = {0, 0, 0, 0};
-  if (p.in) {
-    const long Ng = (long)G.nx * G.ny * G.nz;
-    const long g = ((long)p.iz * G.ny + p.iy) * G.nx + p.ix;
-    const double v = rho_ref ? rho[p.rep * Ng + g] - rho_ref[g] : rho[p.rep * Ng + g];
-    q[0] = v;
-    q[1] = v * axis_coord(p.ix, G.nx, G.h);
-    q[2] = v * axis_coord(p.iy, G.ny, G.h);
-    q[3] = v * axis_coord(p.iz, G.nz, G.h);
-  }
-  __shared__ double sh[kBY];
-  for (int t = 0; t < 4; ++t) {
-    const double s = block_sum_2d(q[t], sh);
-    if (threadIdx.x == 0 && threadIdx.y == 0) slot(R, p.rep, 4 + t)[p.blin] = s;
-  }
-}
-
 // ---- the 12th-order operator A = -Lap_12 with zero ghosts -------------------------------
 template <typename V>
 __device__ __forceinline__ V apply_A12(const V* __restrict__ x, int ix, int iy, int iz, int nx,
                                        int ny, int nz, V ih2) {
-  const long plane = (long)nx * ny;
-  const long g = (long)iz * plane + (long)iy * nx + ix;
+  const int plane = nx * ny;
+  const int g = iz * plane + iy * nx + ix;
   V s = (V)(3.0 * fd_coef(0)) * x[g];
 #pragma unroll
   for (int m = 1; m <= kFdRadius; ++m) {
     V t = 0;
     if (ix + m < nx) t += x[g + m];
     if (ix - m >= 0) t += x[g - m];
-    if (iy + m < ny) t += x[g + (long)m * nx];
-    if (iy - m >= 0) t += x[g - (long)m * nx];
-    if (iz + m < nz) t += x[g + (long)m * plane];
-    if (iz - m >= 0) t += x[g - (long)m * plane];
+    if (iy + m < ny) t += x[g + m * nx];
+    if (iy - m >= 0) t += x[g - m * nx];
+    if (iz + m < nz) t += x[g + m * plane];
+    if (iz - m >= 0) t += x[g - m * plane];
     s = fma((V)fd_coef(m), t, s);
   }
   return -s * ih2;
 }
 
-// b = 4 pi (rho - rho_ref) + Q G0 + p.G (moments from k_moments, `nmom` partials); r = b - A x;
-// partials of (b,b) (slot 0) and (r,r) (slot 1)
-template <typename V>
-__global__ void __launch_bounds__(kBX* kBY)
-k_pcg_init(Grid3 G, const double* __restrict__ rho, const double* __restrict__ rho_ref,
-           const double* __restrict__ gf, const V* __restrict__ x, V* __restrict__ b,
-           V* __restrict__ r, Red R, int nmom, int zero_bc, const RepCtl* __restrict__ ctl) {
-  const Pt3 p = pt3(G.nx, G.ny, G.nz);
-  if (ctl && !ctl[p.rep].active) return;
-  __shared__ double mom[4];
-  __shared__ double sh[kBY];
-  if (threadIdx.y == 0) {
-    for (int t = 0; t < 4; ++t) {
-      const double s = sum_partials(slot(R, p.rep, 4 + t), nmom);
-      if (threadIdx.x == 0) mom[t] = s;
-    }
-  }
-  __syncthreads();
-  const double h3 = G.h * G.h * G.h;
-  const double Q = zero_bc ? 0.0 : h3 * mom[0], px = zero_bc ? 0.0 : h3 * mom[1],
-               py = zero_bc ? 0.0 : h3 * mom[2], pz = zero_bc ? 0.0 : h3 * mom[3];
-  const long Ng = (long)G.nx * G.ny * G.nz;
-  double bb = 0.0, rr = 0.0;
-  if (p.in) {
-    const long g = ((long)p.iz * G.ny + p.iy) * G.nx + p.ix;
-    const double dr = rho_ref ? rho[p.rep * Ng + g] - rho_ref[g] : rho[p.rep * Ng + g];
-    double bd = 4.0 * kPi * dr;
-    bd += Q * gf[g] + px * gf[Ng + g] + py * gf[2 * Ng + g] + pz * gf[3 * Ng + g];
-    const V bv = (V)bd;
-    b[p.rep * Ng + g] = bv;
-    const V rv = bv - apply_A12<V>(x + p.rep * Ng, p.ix, p.iy, p.iz, G.nx, G.ny, G.nz,
-                                   (V)(1.0 / (G.h * G.h)));
-    r[p.rep * Ng + g] = rv;
-    bb = (double)bv * (double)bv;
-    rr = (double)rv * (double)rv;
-  }
-  bb = block_sum_2d(bb, sh);
-  if (threadIdx.x == 0 && threadIdx.y == 0) slot(R, p.rep, 0)[p.blin] = bb;
-  rr = block_sum_2d(rr, sh);
-  if (threadIdx.x == 0 && threadIdx.y == 0) slot(R, p.rep, 1)[p.blin] = rr;
-}
-
-// Ap = A p and partials of (p, Ap) into slot 3
-template <typename V>
-__global__ void __launch_bounds__(kBX* kBY)
-k_pcg_Ap(Grid3 G, const V* __restrict__ pv, V* __restrict__ Ap, Red R,
-         const PcgState* __restrict__ st) {
-  const Pt3 p = pt3(G.nx, G.ny, G.nz);
-  if (pcg_skip(st, p.rep)) return;
-  __shared__ double sh[kBY];
-  double s = 0.0;
-  if (p.in) {
-    const long Ng = (long)G.nx * G.ny * G.nz;
-    const long g = ((long)p.iz * G.ny + p.iy) * G.nx + p.ix;
-    const V* pr = pv + p.rep * Ng;
-    const V a = apply_A12<V>(pr, p.ix, p.iy, p.iz, G.nx, G.ny, G.nz, (V)(1.0 / (G.h * G.h)));
-    Ap[p.rep * Ng + g] = a;
-    s = (double)pr[g] * (double)a;
-  }
-  s = block_sum_2d(s, sh);
-  if (threadIdx.x == 0 && threadIdx.y == 0) slot(R, p.rep, 3)[p.blin] = s;
-}
-
-__global__ void k_pcg_state_init(PcgState* st, Red R, int nblk, double tol,
-                                 const RepCtl* __restrict__ ctl, int nrep) {
-  const int rep = threadIdx.x >> 5;  // one warp per replica
-  if (rep >= nrep) return;
-  const bool act = !ctl || ctl[rep].active;
-  const double bb = sum_partials(slot(R, rep, 0), nblk);
-  const double rr = sum_partials(slot(R, rep, 1), nblk);
-  if ((threadIdx.x & 31) == 0) {
-    PcgState& s = st[rep];
-    s.bb = bb;
-    s.rr = rr;
-    s.cur = 0;
-    s.it = 0;
-    s.status = 0;
-    s.done = (!act || rr <= tol * tol * bb) ? 1 : 0;
-    s.rz[0] = s.rz[1] = 0.0;
-  }
-}
-
-// (r, z) partials into slot 2 (grid-stride, gridDim.x partials); p = z when `first`
-template <typename V>
-__global__ void k_pcg_rz(long Ng, const V* __restrict__ r, const V* __restrict__ z,
-                         V* __restrict__ p, int first, Red R, const PcgState* __restrict__ st) {
-  const int rep = blockIdx.y;
-  if (pcg_skip(st, rep)) return;
-  double s = 0.0;
-  for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < Ng;
-       g += (long)gridDim.x * blockDim.x) {
-    const V zv = z[rep * Ng + g];
-    s += (double)r[rep * Ng + g] * (double)zv;
-    if (first) p[rep * Ng + g] = zv;
-  }
-  __shared__ double sh[32];
-  s = block_sum(s, sh);
-  if (threadIdx.x == 0) slot(R, rep, 2)[blockIdx.x] = s;
-}
-
-// store the first (r, z); inside a graph, arm the CG while loop that follows (a nested
-// loop's flag is not reset between executions of the enclosing body)
-__global__ void k_pcg_rz_store(PcgState* st, Red R, int nblk, int nrep,
-                               cudaGraphConditionalHandle cond, int use_cond) {
-  const int rep = threadIdx.x >> 5;
-  if (rep < nrep && !st[rep].done) {
-    const double s = sum_partials(slot(R, rep, 2), nblk);
-    if ((threadIdx.x & 31) == 0) st[rep].rz[st[rep].cur] = s;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0 && use_cond) {
-    int a = 0;
-    for (int r = 0; r < nrep; ++r) a |= (st[r].done == 0);
-    cudaGraphSetConditional(cond, a ? 1u : 0u);
-  }
-}
-
-// alpha = rz / (p,Ap) (slot 3, `nap` partials); x += alpha p; r -= alpha Ap; partials of
-// (r,r) (slot 1) and (r_new, z_old) (slot 5), gridDim.x each
-template <typename V>
-__global__ void k_pcg_xr(long Ng, V* __restrict__ x, V* __restrict__ r, const V* __restrict__ p,
-                         const V* __restrict__ Ap, const V* __restrict__ z, Red R, int nap,
-                         const PcgState* __restrict__ st) {
-  const int rep = blockIdx.y;
-  if (pcg_skip(st, rep)) return;
-  __shared__ double alpha;
-  if (threadIdx.x < 32) {
-    const double pAp = sum_partials(slot(R, rep, 3), nap);
-    if (threadIdx.x == 0) alpha = st[rep].rz[st[rep].cur] / pAp;
-  }
-  __syncthreads();
-  const V a = (V)alpha;
-  double s = 0.0, t = 0.0;
-  for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < Ng;
-       g += (long)gridDim.x * blockDim.x) {
-    const long e = rep * Ng + g;
-    x[e] = fma(a, p[e], x[e]);
-    const V rv = fma(-a, Ap[e], r[e]);
-    r[e] = rv;
-    s += (double)rv * (double)rv;
-    t += (double)rv * (double)z[e];
-  }
-  __shared__ double sh[32];
-  s = block_sum(s, sh);
-  if (threadIdx.x == 0) slot(R, rep, 1)[blockIdx.x] = s;
-  __syncthreads();
-  t = block_sum(t, sh);
-  if (threadIdx.x == 0) slot(R, rep, 5)[blockIdx.x] = t;
-}
-
-__global__ void k_pcg_check(PcgState* st, Red R, int nblk, double tol, int max_it, int nrep,
-                            int* status) {
-  const int rep = threadIdx.x >> 5;
-  if (rep >= nrep || st[rep].done) return;
-  const double rr = sum_partials(slot(R, rep, 1), nblk);
-  if ((threadIdx.x & 31) == 0) {
-    PcgState& s = st[rep];
-    s.rr = rr;
-    if (!(rr <= 1e300)) {
-      s.done = 1;
-      s.status = RMGTD_EDIVERGED;
-      atomicCAS(status, 0, (int)RMGTD_EDIVERGED);
-    } else if (rr <= tol * tol * s.bb) {
-      s.done = 1;
-    } else if (s.it + 1 >= max_it) {
-      s.done = 1;
-      s.status = RMGTD_ENOTCONVERGED;
-      atomicCAS(status, 0, (int)RMGTD_ENOTCONVERGED);
-    }
-  }
-}
-
-// beta = ((r,z_new) - (r,z_old)) / rz_old (Polak-Ribiere); p = z + beta p
-template <typename V>
-__global__ void k_pcg_p(long Ng, const V* __restrict__ z, V* __restrict__ p, Red R, int nblk,
-                        const PcgState* __restrict__ st) {
-  const int rep = blockIdx.y;
-  if (pcg_skip(st, rep)) return;
-  __shared__ double beta;
-  if (threadIdx.x < 32) {
-    const double rzn = sum_partials(slot(R, rep, 2), nblk);
-    const double rzo = sum_partials(slot(R, rep, 5), nblk);
-    if (threadIdx.x == 0) beta = (rzn - rzo) / st[rep].rz[st[rep].cur];
-  }
-  __syncthreads();
-  const V bt = (V)beta;
-  for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < Ng;
-       g += (long)gridDim.x * blockDim.x) {
-    const long e = rep * Ng + g;
-    p[e] = fma(bt, p[e], z[e]);
-  }
-}
-
-// end of one CG iteration: store (r,z), advance, and (inside a graph) set the while flag
-__global__ void k_pcg_end(PcgState* st, Red R, int nblk, int nrep, int* any_active,
-                          cudaGraphConditionalHandle cond, int use_cond,
-                          unsigned long long* kexec) {
-  const int rep = threadIdx.x >> 5;
-  if (rep < nrep && !st[rep].done) {
-    const double rz = sum_partials(slot(R, rep, 2), nblk);
-    if ((threadIdx.x & 31) == 0) {
-      PcgState& s = st[rep];
-      s.cur ^= 1;
-      s.rz[s.cur] = rz;
-      s.it += 1;
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int a = 0;
-    for (int r = 0; r < nrep; ++r) a |= (*((volatile int*)&st[r].done) == 0);
-    if (any_active) *any_active = a;
-    if (use_cond) {
-      cudaGraphSetConditional(cond, a ? 1u : 0u);
-      atomicAdd(&kexec[1], 1ull);
-    }
-  }
-}
-
-// ---- multigrid V-cycle in float32 (7-point operators, zero Dirichlet ghosts) ---------------
+// ---- multigrid in float32 (7-point operators, zero Dirichlet ghosts) ----------------------
 __device__ __forceinline__ float lap7f(const float* __restrict__ x, int ix, int iy, int iz,
                                        int nx, int ny, int nz, float* center) {
-  const long plane = (long)nx * ny;
-  const long g = (long)iz * plane + (long)iy * nx + ix;
+  const int plane = nx * ny;
+  const int g = iz * plane + iy * nx + ix;
   const float c = x[g];
   float s = 0.0f;
   if (ix + 1 < nx) s += x[g + 1];
@@ -407,91 +168,6 @@ __device__ __forceinline__ float lap7f(const float* __restrict__ x, int ix, int 
   return 6.0f * c - s;  // h^2 * (-Lap_7 x)
 }
 
-// one damped-Jacobi sweep: xo = xi + w h^2/6 (b - A xi); first: xi = 0; b64 != NULL: b is
-// read from the float64 residual and stored as float in bf; out64 != NULL: result to it
-__global__ void __launch_bounds__(kBX* kBY)
-k_mg_jacobi(Grid3 G, const float* __restrict__ xi, float* __restrict__ xo, float* __restrict__ bf,
-            const double* __restrict__ b64, int first, double* __restrict__ out64,
-            const PcgState* __restrict__ st) {
-  const Pt3 p = pt3(G.nx, G.ny, G.nz);
-  if (pcg_skip(st, p.rep) || !p.in) return;
-  const long n = (long)G.nx * G.ny * G.nz;
-  const float h2 = (float)(G.h * G.h), ih2 = 1.0f / h2;
-  const long g = ((long)p.iz * G.ny + p.iy) * G.nx + p.ix;
-  const long e = p.rep * n + g;
-  float bv;
-  if (b64) {
-    bv = (float)b64[e];
-    bf[e] = bv;
-  } else {
-    bv = bf[e];
-  }
-  float v;
-  if (first) {
-    v = kJacobiW * h2 / 6.0f * bv;
-  } else {
-    float c;
-    const float ax = lap7f(xi + p.rep * n, p.ix, p.iy, p.iz, G.nx, G.ny, G.nz, &c) * ih2;
-    v = c + kJacobiW * h2 / 6.0f * (bv - ax);
-  }
-  if (out64)
-    out64[e] = (double)v;
-  else
-    xo[e] = v;
-}
-
-// Two damped-Jacobi sweeps from x = 0 in one pass: x2 = c (2 b - c A b), c = w h^2/6.
-// b64: the fine-level float64 residual, also stored as float into bf.
-__global__ void __launch_bounds__(kBX* kBY)
-k_mg_pre2(Grid3 G, float* __restrict__ xo, float* __restrict__ bf, const double* __restrict__ b64,
-          const PcgState* __restrict__ st) {
-  const Pt3 p = pt3(G.nx, G.ny, G.nz);
-  if (pcg_skip(st, p.rep) || !p.in) return;
-  const long n = (long)G.nx * G.ny * G.nz;
-  const float h2 = (float)(G.h * G.h), ih2 = 1.0f / h2;
-  const float c = kJacobiW * h2 / 6.0f;
-  const long plane = (long)G.nx * G.ny;
-  const long g = (long)p.iz * plane + (long)p.iy * G.nx + p.ix;
-  const long e = p.rep * n + g;
-  float bc, s = 0.0f;
-  if (b64) {
-    const double* b = b64 + p.rep * n;
-    bc = (float)b[g];
-    if (p.ix + 1 < G.nx) s += (float)b[g + 1];
-    if (p.ix > 0) s += (float)b[g - 1];
-    if (p.iy + 1 < G.ny) s += (float)b[g + G.nx];
-    if (p.iy > 0) s += (float)b[g - G.nx];
-    if (p.iz + 1 < G.nz) s += (float)b[g + plane];
-    if (p.iz > 0) s += (float)b[g - plane];
-    bf[e] = bc;
-  } else {
-    const float* b = bf + p.rep * n;
-    bc = b[g];
-    if (p.ix + 1 < G.nx) s += b[g + 1];
-    if (p.ix > 0) s += b[g - 1];
-    if (p.iy + 1 < G.ny) s += b[g + G.nx];
-    if (p.iy > 0) s += b[g - G.nx];
-    if (p.iz + 1 < G.nz) s += b[g + plane];
-    if (p.iz > 0) s += b[g - plane];
-  }
-  const float Ab = (6.0f * bc - s) * ih2;
-  xo[e] = c * (2.0f * bc - c * Ab);
-}
-
-__global__ void __launch_bounds__(kBX* kBY)
-k_mg_residual(Grid3 G, const float* __restrict__ x, const float* __restrict__ b,
-              float* __restrict__ r, const PcgState* __restrict__ st) {
-  const Pt3 p = pt3(G.nx, G.ny, G.nz);
-  if (pcg_skip(st, p.rep) || !p.in) return;
-  const long n = (long)G.nx * G.ny * G.nz;
-  const float ih2 = (float)(1.0 / (G.h * G.h));
-  const long g = ((long)p.iz * G.ny + p.iy) * G.nx + p.ix;
-  float c;
-  r[p.rep * n + g] = b[p.rep * n + g] - lap7f(x + p.rep * n, p.ix, p.iy, p.iz, G.nx, G.ny, G.nz, &c) * ih2;
-}
-
-// trilinear (cell-centred) weights along one axis: fine child f = 2I + a takes 3/4 from I
-// and 1/4 from I-1 (a = 0) or I+1 (a = 1)
 __device__ __forceinline__ void tri_w(int f, int nc, int* c0, int* c1, float* w0, float* w1) {
   const int I = f >> 1;
   *c0 = I;
@@ -521,7 +197,7 @@ __device__ __forceinline__ float restrict_point(const float* __restrict__ r, int
         const int fx = 2 * I + dx;
         if (fx < 0 || fx >= nx) continue;
         const float wx = (dx == 0 || dx == 1) ? 0.75f : 0.25f;
-        s += wx * wy * wz * r[((long)fz * ny + fy) * nx + fx];
+        s += wx * wy * wz * r[(fz * ny + fy) * nx + fx];
       }
     }
   }
@@ -535,145 +211,97 @@ __device__ __forceinline__ float prolong_point(const float* __restrict__ xc, int
   tri_w(fx, cx, &x0, &x1, &wx0, &wx1);
   tri_w(fy, cy, &y0, &y1, &wy0, &wy1);
   tri_w(fz, cz, &z0, &z1, &wz0, &wz1);
-  auto at = [&](int i, int j, int k) { return xc[((long)k * cy + j) * cx + i]; };
+  auto at = [&](int i, int j, int k) { return xc[(k * cy + j) * cx + i]; };
   return wz0 * (wy0 * (wx0 * at(x0, y0, z0) + wx1 * at(x1, y0, z0)) +
                 wy1 * (wx0 * at(x0, y1, z0) + wx1 * at(x1, y1, z0))) +
          wz1 * (wy0 * (wx0 * at(x0, y0, z1) + wx1 * at(x1, y0, z1)) +
                 wy1 * (wx0 * at(x0, y1, z1) + wx1 * at(x1, y1, z1)));
 }
 
-// x <- x + P xc, then one damped-Jacobi sweep on the corrected x, in one pass: the
-// corrected values of the 6 neighbours are formed on the fly.  Result into xo.
-__global__ void __launch_bounds__(kBX* kBY)
-k_mg_prolong_sweep(Grid3 F, Grid3 C, const float* __restrict__ xc, const float* __restrict__ x,
-                   float* __restrict__ xo, const float* __restrict__ b,
-                   const PcgState* __restrict__ st) {
-  const Pt3 p = pt3(F.nx, F.ny, F.nz);
-  if (pcg_skip(st, p.rep) || !p.in) return;
-  const long nf = (long)F.nx * F.ny * F.nz, nc = (long)C.nx * C.ny * C.nz;
-  const float* xcr = xc + p.rep * nc;
-  const float* xr = x + p.rep * nf;
-  const float h2 = (float)(F.h * F.h);
-  const long plane = (long)F.nx * F.ny;
-  const int fx = p.ix, fy = p.iy, fz = p.iz;
-  const long g = (long)fz * plane + (long)fy * F.nx + fx;
-  auto corr = [&](int ax, int ay, int az, long gg) {
-    return xr[gg] + prolong_point(xcr, ax, ay, az, C.nx, C.ny, C.nz);
-  };
-  const float c0 = corr(fx, fy, fz, g);
-  float s = 0.0f;
-  if (fx + 1 < F.nx) s += corr(fx + 1, fy, fz, g + 1);
-  if (fx > 0) s += corr(fx - 1, fy, fz, g - 1);
-  if (fy + 1 < F.ny) s += corr(fx, fy + 1, fz, g + F.nx);
-  if (fy > 0) s += corr(fx, fy - 1, fz, g - F.nx);
-  if (fz + 1 < F.nz) s += corr(fx, fy, fz + 1, g + plane);
-  if (fz > 0) s += corr(fx, fy, fz - 1, g - plane);
-  const float ax = (6.0f * c0 - s) / h2;
-  xo[p.rep * nf + g] = c0 + kJacobiW * h2 / 6.0f * (b[p.rep * nf + g] - ax);
-}
-
-// coarse b = (1/8) P^T r (launched over the coarse grid)
-__global__ void __launch_bounds__(kBX* kBY)
-k_mg_restrict(Grid3 F, Grid3 C, const float* __restrict__ rf, float* __restrict__ bc,
-              const PcgState* __restrict__ st) {
-  const Pt3 p = pt3(C.nx, C.ny, C.nz);
-  if (pcg_skip(st, p.rep) || !p.in) return;
-  const long nf = (long)F.nx * F.ny * F.nz, nc = (long)C.nx * C.ny * C.nz;
-  const long g = ((long)p.iz * C.ny + p.iy) * C.nx + p.ix;
-  bc[p.rep * nc + g] = restrict_point(rf + p.rep * nf, p.ix, p.iy, p.iz, F.nx, F.ny, F.nz);
-}
-
 // ---- coarse tail of the V-cycle inside one block (levels with <= kTailMax points) ---------
-struct TailLevels {
-  int nl;
-  int nx[12], ny[12], nz[12];
-  float h[12];
-};
-
-__device__ void tail_jacobi(const TailLevels& L, int l, float* x, float* t, const float* b,
+__device__ void tail_jacobi(const Tail& L, int l, float* x, float* t, const float* b,
                             int first) {
-  const int nx = L.nx[l], ny = L.ny[l], nz = L.nz[l];
-  const long n = (long)nx * ny * nz;
-  const float h2 = L.h[l] * L.h[l];
-  for (long g = threadIdx.x; g < n; g += blockDim.x) {
+  const int nx = L.nx[l], ny = L.ny[l], nz = L.nz[l], n = L.n[l];
+  const float h2 = L.h2[l], c = kJacobiW * h2 / 6.0f, ih2 = 1.0f / h2;
+  for (int g = threadIdx.x; g < n; g += blockDim.x) {
     if (first) {
-      t[g] = kJacobiW * h2 / 6.0f * b[g];
+      t[g] = c * b[g];
     } else {
-      const int ix = (int)(g % nx), iy = (int)((g / nx) % ny), iz = (int)(g / ((long)nx * ny));
-      float c;
-      const float ax = lap7f(x, ix, iy, iz, nx, ny, nz, &c) / h2;
-      t[g] = c + kJacobiW * h2 / 6.0f * (b[g] - ax);
+      int ix, iy, iz;
+      xyz_of(g, nx, ny, L.dx[l], L.dy[l], ix, iy, iz);
+      float cc;
+      const float ax = lap7f(x, ix, iy, iz, nx, ny, nz, &cc) * ih2;
+      t[g] = cc + c * (b[g] - ax);
     }
   }
   __syncthreads();
-  for (long g = threadIdx.x; g < n; g += blockDim.x) x[g] = t[g];
+  for (int g = threadIdx.x; g < n; g += blockDim.x) x[g] = t[g];
   __syncthreads();
 }
 
-__global__ void k_mg_tail(TailLevels L, const float* __restrict__ b_in, float* __restrict__ x_out,
-                          const float* __restrict__ cinv, const PcgState* __restrict__ st) {
-  const int rep = blockIdx.x;
-  if (pcg_skip(st, rep)) return;
-  extern __shared__ float sm[];
-  float* xs[12];
-  float* bs[12];
-  float* ts[12];
-  long off = 0;
+// V-cycle of the tail levels for one replica inside one block (all threads of the block):
+// b_in / x_out are that replica's arrays of the first tail level, sm the dynamic shared memory.
+__device__ void tail_vcycle(const Tail& L, const float* __restrict__ b_in,
+                            float* __restrict__ x_out, const float* __restrict__ cinv, float* sm) {
+  float* xs[kMaxLevels];
+  float* bs[kMaxLevels];
+  float* ts[kMaxLevels];
+  int off = 0;
   for (int l = 0; l < L.nl; ++l) {
-    const long n = (long)L.nx[l] * L.ny[l] * L.nz[l];
     xs[l] = sm + off;
-    bs[l] = sm + off + n;
-    ts[l] = sm + off + 2 * n;
-    off += 3 * n;
+    bs[l] = sm + off + L.n[l];
+    ts[l] = sm + off + 2 * L.n[l];
+    off += 3 * L.n[l];
   }
-  const long n0 = (long)L.nx[0] * L.ny[0] * L.nz[0];
-  for (long g = threadIdx.x; g < n0; g += blockDim.x) bs[0][g] = b_in[rep * n0 + g];
+  const int n0 = L.n[0];
+  for (int g = threadIdx.x; g < n0; g += blockDim.x) bs[0][g] = b_in[g];
   __syncthreads();
   for (int l = 0; l < L.nl; ++l) {
     const bool coarsest = (l == L.nl - 1);
     if (coarsest && cinv) {
       // exact solve with the precomputed inverse of the coarsest operator
-      const int nc = L.nx[l] * L.ny[l] * L.nz[l];
+      const int nc = L.n[l];
       for (int i = threadIdx.x; i < nc; i += blockDim.x) {
         float a = 0.0f;
-        for (int j = 0; j < nc; ++j) a = fmaf(cinv[(long)i * nc + j], bs[l][j], a);
+        for (int j = 0; j < nc; ++j) a = fmaf(cinv[i * nc + j], bs[l][j], a);
         xs[l][i] = a;
       }
       __syncthreads();
       break;
     }
     const int sweeps = coarsest ? kCoarseSweeps : kPre;
-    for (int s = 0; s < sweeps; ++s) tail_jacobi(L, l, xs[l], ts[l], bs[l], s == 0);
+    for (int sw = 0; sw < sweeps; ++sw) tail_jacobi(L, l, xs[l], ts[l], bs[l], sw == 0);
     if (coarsest) break;
-    const int nx = L.nx[l], ny = L.ny[l], nz = L.nz[l];
-    const long n = (long)nx * ny * nz;
-    const float ih2 = 1.0f / (L.h[l] * L.h[l]);
-    for (long g = threadIdx.x; g < n; g += blockDim.x) {
-      const int ix = (int)(g % nx), iy = (int)((g / nx) % ny), iz = (int)(g / ((long)nx * ny));
+    const int nx = L.nx[l], ny = L.ny[l], nz = L.nz[l], n = L.n[l];
+    const float ih2 = 1.0f / L.h2[l];
+    for (int g = threadIdx.x; g < n; g += blockDim.x) {
+      int ix, iy, iz;
+      xyz_of(g, nx, ny, L.dx[l], L.dy[l], ix, iy, iz);
       float c;
       ts[l][g] = bs[l][g] - lap7f(xs[l], ix, iy, iz, nx, ny, nz, &c) * ih2;
     }
     __syncthreads();
-    const int cx = L.nx[l + 1], cy = L.ny[l + 1], cz = L.nz[l + 1];
-    const long nc = (long)cx * cy * cz;
-    for (long g = threadIdx.x; g < nc; g += blockDim.x) {
-      const int I = (int)(g % cx), J = (int)((g / cx) % cy), K = (int)(g / ((long)cx * cy));
+    const int cx = L.nx[l + 1], cy = L.ny[l + 1], nc = L.n[l + 1];
+    for (int g = threadIdx.x; g < nc; g += blockDim.x) {
+      int I, J, K;
+      xyz_of(g, cx, cy, L.dx[l + 1], L.dy[l + 1], I, J, K);
       bs[l + 1][g] = restrict_point(ts[l], I, J, K, nx, ny, nz);
     }
     __syncthreads();
   }
   for (int l = L.nl - 2; l >= 0; --l) {
-    const int nx = L.nx[l], ny = L.ny[l], nz = L.nz[l];
+    const int nx = L.nx[l], ny = L.ny[l], n = L.n[l];
     const int cx = L.nx[l + 1], cy = L.ny[l + 1], cz = L.nz[l + 1];
-    const long n = (long)nx * ny * nz;
-    for (long g = threadIdx.x; g < n; g += blockDim.x) {
-      const int fx = (int)(g % nx), fy = (int)((g / nx) % ny), fz = (int)(g / ((long)nx * ny));
+    for (int g = threadIdx.x; g < n; g += blockDim.x) {
+      int fx, fy, fz;
+      xyz_of(g, nx, ny, L.dx[l], L.dy[l], fx, fy, fz);
       xs[l][g] += prolong_point(xs[l + 1], fx, fy, fz, cx, cy, cz);
     }
     __syncthreads();
-    for (int s = 0; s < kPost; ++s) tail_jacobi(L, l, xs[l], ts[l], bs[l], 0);
+    for (int sw = 0; sw < kPost; ++sw) tail_jacobi(L, l, xs[l], ts[l], bs[l], 0);
   }
-  for (long g = threadIdx.x; g < n0; g += blockDim.x) x_out[rep * n0 + g] = xs[0][g];
+  for (int g = threadIdx.x; g < n0; g += blockDim.x) x_out[g] = xs[0][g];
+  __syncthreads();
 }
 
 // ---- set-up: inverse of the coarsest 7-point operator (one block, Gauss-Jordan, float64) ----
@@ -713,92 +341,7 @@ __global__ void k_coarse_inverse(int nx, int ny, int nz, double h, double* __res
   for (long e = threadIdx.x; e < (long)n * n; e += blockDim.x) out[e] = (float)Minv[e];
 }
 
-// ---- host orchestration ------------------------------------------------------------------
-static Grid3 grid_of(const MgLevel& L) { return Grid3{L.nx, L.ny, L.nz, L.h}; }
-
-static dim3 grid3(int nx, int ny, int nz, int nrep) {
-  return dim3(ceil_div(nx, kBX), ceil_div(ny, kBY), nz * nrep);
-}
-static int nblk3(int nx, int ny, int nz) { return ceil_div(nx, kBX) * ceil_div(ny, kBY) * nz; }
-static const dim3 kBlock3(kBX, kBY, 1);
-
-static Red red_of(rmgtd_ctx* ctx) { return Red{ctx->red_part, ctx->red_cap}; }
-
-// z = M r, M = one float32 V-cycle.  Level-0 input / output are float64 (r64, z64) or
-// float32 (r32, z32: the V-cycle then iterates directly in z32).
-static int vcycle(rmgtd_ctx* ctx, const double* r64, double* z64, const float* r32, float* z32,
-                  int nrep) {
-  const PcgState* st = ctx->pcg;
-  const int nl = (int)ctx->mg.size();
-  const int tail = ctx->mg_tail_level;  // first tail level (>= 1) or -1
-  const int nmulti = (tail >= 0) ? tail : nl;
-  cudaStream_t s = ctx->stream;
-  for (int l = 0; l < nmulti; ++l) {
-    MgLevel& L = ctx->mg[l];
-    const Grid3 G = grid_of(L);
-    const dim3 gr = grid3(L.nx, L.ny, L.nz, nrep);
-    const bool coarsest = (l == nl - 1);
-    float* lx = (l == 0 && z32) ? z32 : L.x;
-    float* lb = (l == 0 && r32) ? const_cast<float*>(r32) : L.b;
-    const double* in64 = (l == 0 && !r32) ? r64 : nullptr;
-    double* out64 = (l == 0 && !z32) ? z64 : nullptr;
-    if (!coarsest) {
-      k_mg_pre2<<<gr, kBlock3, 0, s>>>(G, lx, lb, in64, st);
-      ++ctx->launches;
-      k_mg_residual<<<gr, kBlock3, 0, s>>>(G, lx, lb, L.t, st);
-      ++ctx->launches;
-      MgLevel& C = ctx->mg[l + 1];
-      k_mg_restrict<<<grid3(C.nx, C.ny, C.nz, nrep), kBlock3, 0, s>>>(G, grid_of(C), L.t, C.b, st);
-      ++ctx->launches;
-      RMGTD_LAUNCH(ctx, "k_mg_descend");
-      continue;
-    }
-    // coarsest level handled by multi-block sweeps (no single-block tail)
-    float* bufs[2] = {lx, L.t};
-    int cur = (kCoarseSweeps % 2 == 1) ? 0 : 1;  // the last sweep writes x
-    for (int sw = 0; sw < kCoarseSweeps; ++sw) {
-      const bool last_out64 = (out64 && sw == kCoarseSweeps - 1);
-      k_mg_jacobi<<<gr, kBlock3, 0, s>>>(G, bufs[cur ^ 1], bufs[cur], lb,
-                                         sw == 0 ? in64 : nullptr, sw == 0,
-                                         last_out64 ? out64 : nullptr, st);
-      ++ctx->launches;
-      cur ^= 1;
-    }
-    RMGTD_LAUNCH(ctx, "k_mg_jacobi");
-  }
-  if (tail >= 0) {
-    TailLevels T;
-    T.nl = nl - tail;
-    for (int l = tail; l < nl; ++l) {
-      T.nx[l - tail] = ctx->mg[l].nx;
-      T.ny[l - tail] = ctx->mg[l].ny;
-      T.nz[l - tail] = ctx->mg[l].nz;
-      T.h[l - tail] = (float)ctx->mg[l].h;
-    }
-    k_mg_tail<<<nrep, 1024, ctx->mg_tail_smem, s>>>(T, ctx->mg[tail].b, ctx->mg[tail].x,
-                                                     ctx->mg_cinv, st);
-    ++ctx->launches;
-    RMGTD_LAUNCH(ctx, "k_mg_tail");
-  }
-  for (int l = std::min(nmulti, nl - 1) - 1; l >= 0; --l) {
-    MgLevel& L = ctx->mg[l];
-    MgLevel& C = ctx->mg[l + 1];
-    const Grid3 G = grid_of(L);
-    const dim3 gr = grid3(L.nx, L.ny, L.nz, nrep);
-    float* lx = (l == 0 && z32) ? z32 : L.x;
-    float* lb = (l == 0 && r32) ? const_cast<float*>(r32) : L.b;
-    double* out64 = (l == 0 && !z32) ? z64 : nullptr;
-    // coarse correction and the first post-sweep in one kernel (result in L.t), then the
-    // second post-sweep back into x (or the float64 output)
-    k_mg_prolong_sweep<<<gr, kBlock3, 0, s>>>(G, grid_of(C), C.x, lx, L.t, lb, st);
-    ++ctx->launches;
-    k_mg_jacobi<<<gr, kBlock3, 0, s>>>(G, L.t, lx, lb, nullptr, 0, out64, st);
-    ++ctx->launches;
-    RMGTD_LAUNCH(ctx, "k_mg_ascend");
-  }
-  return RMGTD_OK;
-}
-
+// ---- host set-up ---------------------------------------------------------------------------
 int setup_multigrid(rmgtd_ctx* ctx) {
   ctx->mg.clear();
   int nx = ctx->nx, ny = ctx->ny, nz = ctx->nz;
@@ -812,7 +355,7 @@ int setup_multigrid(rmgtd_ctx* ctx) {
     L.h = h;
     L.x = L.b = L.t = nullptr;
     ctx->mg.push_back(L);
-    if (ctx->mg.size() >= 12) break;
+    if ((int)ctx->mg.size() >= kMaxLevels) break;
     if ((nx & 1) || (ny & 1) || (nz & 1) || nx < 4 || ny < 4 || nz < 4) break;
     nx /= 2;
     ny /= 2;
@@ -830,10 +373,6 @@ int setup_multigrid(rmgtd_ctx* ctx) {
   if (ctx->mg_tail_level >= 0)
     for (int l = ctx->mg_tail_level; l < nl; ++l) smem += 3 * sizeof(float) * ctx->mg[l].n;
   ctx->mg_tail_smem = smem;
-  if (smem > 48 * 1024) {
-    RMGTD_CUDA(ctx, cudaFuncSetAttribute(k_mg_tail, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem));
-  }
   for (int l = 0; l < nl; ++l) {
     MgLevel& L = ctx->mg[l];
     const size_t bytes = sizeof(float) * (size_t)ctx->nrep * L.n;
@@ -859,6 +398,44 @@ int setup_multigrid(rmgtd_ctx* ctx) {
       dev_free(ctx, Mi);
     }
   }
+  // level table of the persistent solve (device copy, read once per launch)
+  LevelTable lt;
+  memset(&lt, 0, sizeof(lt));
+  lt.nl = nl;
+  lt.nmulti = ctx->mg_tail_level >= 0 ? ctx->mg_tail_level : nl;
+  for (int l = 0; l < nl; ++l) {
+    const MgLevel& M = ctx->mg[l];
+    Level& L = lt.L[l];
+    L.nx = M.nx;
+    L.ny = M.ny;
+    L.nz = M.nz;
+    L.n = (int)M.n;
+    L.h2 = (float)(M.h * M.h);
+    L.dx = make_fastdiv(M.nx);
+    L.dy = make_fastdiv(M.ny);
+    L.dn = make_fastdiv((int)M.n);
+    L.x = M.x;
+    L.b = M.b;
+    L.t = M.t;
+  }
+  if (ctx->mg_tail_level >= 0) {
+    lt.T.nl = nl - lt.nmulti;
+    for (int l = lt.nmulti; l < nl; ++l) {
+      const MgLevel& M = ctx->mg[l];
+      const int k = l - lt.nmulti;
+      lt.T.nx[k] = M.nx;
+      lt.T.ny[k] = M.ny;
+      lt.T.nz[k] = M.nz;
+      lt.T.n[k] = (int)M.n;
+      lt.T.h2[k] = (float)(M.h * M.h);
+      lt.T.dx[k] = make_fastdiv(M.nx);
+      lt.T.dy[k] = make_fastdiv(M.ny);
+    }
+  }
+  ctx->mg_table = dev_alloc(ctx, sizeof(LevelTable));
+  if (!ctx->mg_table) return set_error(ctx, RMGTD_ENOMEM, "level table");
+  RMGTD_CUDA(ctx, cudaMemcpy(ctx->mg_table, &lt, sizeof(LevelTable), cudaMemcpyHostToDevice));
+
   ctx->ghost = (double*)dev_alloc(ctx, sizeof(double) * 4 * (size_t)ctx->Ng);
   if (!ctx->ghost) return set_error(ctx, RMGTD_ENOMEM, "ghost fields");
   const Grid3 G{ctx->nx, ctx->ny, ctx->nz, ctx->h};
@@ -869,137 +446,536 @@ int setup_multigrid(rmgtd_ctx* ctx) {
   return RMGTD_OK;
 }
 
-// slot capacity of the reduction partials: the larger of the 3-D fine-grid block count and
-// the grid-stride block count
-int poisson_red_cap(int nx, int ny, int nz, int red_blocks) {
-  return std::max(nblk3(nx, ny, nz), red_blocks);
-}
+// slot capacity of the reduction partials (grid-stride kernels and the persistent solve)
+int poisson_red_cap(int num_sms, int red_blocks) { return std::max(num_sms, red_blocks); }
 
-// Buffers of one Hartree solve: float64 (the solve of rho itself) or float32 (the change
-// of V_H relative to the reference potential, mixed path).
-struct PcgBufs {
-  bool f32;
-  void *x, *b, *r, *z, *p, *Ap;
-  const double* rho_ref;
+// ---- the persistent solve ---------------------------------------------------------------
+namespace coop {
+
+constexpr int kThreadsC = 1024;
+constexpr int kWarps = kThreadsC / 32;
+constexpr int kMaxRep = 32;
+constexpr int kMaxDots = 4;     // dot products reduced together in one phase
+constexpr int kSlots = 8;
+// reduction slots per replica: 0 (b,b)  1 (r,r)  2 (r,z)  3 (z,Az)  4 (z,Ap_old) / Q
+// 5 (p_old,Az) / px  6 (r_new,z_old) / py  7 pz   (moments only in the prologue)
+
+template <typename V>
+struct Args {
+  const LevelTable* lt;   // device copy of the level table
+  int nrep;
+  double h;
+  const double* rho;      // float64 path: density [rep][n0]
+  const float* drho;      // mixed path: density change rho - rho_ref [rep][n0]
+  const double* gf;       // float64 ghost response fields [4][n0]
+  const float* gf32;      // float32 copy (mixed path)
+  const float* cinv;
+  int zero_bc;
+  V* x;                   // unknown (initial guess in, solution out) [rep][n0]
+  V *b, *r, *z, *p, *Ap, *Az;
+  double* part;           // [rep][kSlots][gridDim.x] per-block partial sums
+  PcgState* st;
+  const RepCtl* ctl;
   double tol;
+  int max_it;
+  unsigned* bar;
+  int* status;
 };
 
-static PcgBufs pcg_bufs(rmgtd_ctx* ctx, double* vh, int f32) {
-  PcgBufs B;
-  B.f32 = f32 != 0;
-  if (B.f32) {
-    B.x = ctx->dvh32;
-    B.b = ctx->pcg32_b;
-    B.r = ctx->pcg32_r;
-    B.z = ctx->pcg32_z;
-    B.p = ctx->pcg32_p;
-    B.Ap = ctx->pcg32_Ap;
-    B.rho_ref = ctx->rho_ref;
-    B.tol = std::max(ctx->opt.poisson_tol, kMixedPoissonTol);
-  } else {
-    B.x = vh;
-    B.b = ctx->pcg_b;
-    B.r = ctx->pcg_r;
-    B.z = ctx->pcg_z;
-    B.p = ctx->pcg_p;
-    B.Ap = ctx->pcg_Ap;
-    B.rho_ref = nullptr;
-    B.tol = ctx->opt.poisson_tol;
-  }
-  return B;
+__device__ __forceinline__ float wsum(float v) { return warp_sumf(v); }
+__device__ __forceinline__ double wsum(double v) { return warp_sum(v); }
+
+template <typename V>
+__device__ __forceinline__ double* pslot(const Args<V>& a, int rep, int s) {
+  return a.part + ((long)rep * kSlots + s) * gridDim.x;
 }
 
-// Start of a Hartree solve: moments, right-hand side, initial residual, first V-cycle.
-int hartree_begin(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* ctl, int zero_bc,
-                  int nrep, cudaGraphConditionalHandle cond, int use_cond, int f32) {
-  const Grid3 G{ctx->nx, ctx->ny, ctx->nz, ctx->h};
-  const long Ng = ctx->Ng;
-  const int rb = ctx->red_blocks;
-  const dim3 g3 = grid3(ctx->nx, ctx->ny, ctx->nz, nrep);
-  const int nb3 = nblk3(ctx->nx, ctx->ny, ctx->nz);
-  cudaStream_t s = ctx->stream;
-  const Red R = red_of(ctx);
-  const PcgBufs B = pcg_bufs(ctx, vh, f32);
-  k_moments<<<g3, kBlock3, 0, s>>>(G, rho, B.rho_ref, R, ctl);
-  ++ctx->launches;
-  if (B.f32) {
-    k_pcg_init<float><<<g3, kBlock3, 0, s>>>(G, rho, B.rho_ref, ctx->ghost, (float*)B.x,
-                                             (float*)B.b, (float*)B.r, R, nb3, zero_bc, ctl);
-  } else {
-    k_pcg_init<double><<<g3, kBlock3, 0, s>>>(G, rho, nullptr, ctx->ghost, (double*)B.x,
-                                              (double*)B.b, (double*)B.r, R, nb3, zero_bc, ctl);
-  }
-  ++ctx->launches;
-  k_pcg_state_init<<<1, 32 * nrep, 0, s>>>(ctx->pcg, R, nb3, B.tol, ctl, nrep);
-  ++ctx->launches;
-  RMGTD_LAUNCH(ctx, "k_pcg_init");
-  int rc = B.f32 ? vcycle(ctx, nullptr, nullptr, (float*)B.r, (float*)B.z, nrep)
-                 : vcycle(ctx, (double*)B.r, (double*)B.z, nullptr, nullptr, nrep);
-  if (rc) return rc;
-  const dim3 gf(rb, nrep);
-  if (B.f32)
-    k_pcg_rz<float><<<gf, kThreads, 0, s>>>(Ng, (float*)B.r, (float*)B.z, (float*)B.p, 1, R,
-                                            ctx->pcg);
-  else
-    k_pcg_rz<double><<<gf, kThreads, 0, s>>>(Ng, (double*)B.r, (double*)B.z, (double*)B.p, 1, R,
-                                             ctx->pcg);
-  ++ctx->launches;
-  k_pcg_rz_store<<<1, 32 * nrep, 0, s>>>(ctx->pcg, R, rb, nrep, cond, use_cond);
-  ++ctx->launches;
-  RMGTD_LAUNCH(ctx, "k_pcg_rz");
-  return RMGTD_OK;
+template <typename V>
+__device__ __forceinline__ V dens(const Args<V>& a, int i) {
+  if constexpr (sizeof(V) == 4) return a.drho[i];
+  else return a.rho[i];
+}
+template <typename V>
+__device__ __forceinline__ V ghost(const Args<V>& a, int k, int n0, int g) {
+  if constexpr (sizeof(V) == 4) return a.gf32[k * n0 + g];
+  else return a.gf[k * n0 + g];
 }
 
-// One flexible-CG iteration for every replica still iterating; `cond` is the graph
-// while-handle to update (use_cond = 0 outside a graph).
-int hartree_iteration(rmgtd_ctx* ctx, double* vh, int nrep, cudaGraphConditionalHandle cond,
-                      int use_cond, int f32) {
-  const Grid3 G{ctx->nx, ctx->ny, ctx->nz, ctx->h};
-  const long Ng = ctx->Ng;
-  const int rb = ctx->red_blocks;
-  const dim3 g3 = grid3(ctx->nx, ctx->ny, ctx->nz, nrep);
-  const int nb3 = nblk3(ctx->nx, ctx->ny, ctx->nz);
-  const dim3 gf(rb, nrep);
-  cudaStream_t s = ctx->stream;
-  const Red R = red_of(ctx);
-  const PcgBufs B = pcg_bufs(ctx, vh, f32);
-  if (B.f32) {
-    k_pcg_Ap<float><<<g3, kBlock3, 0, s>>>(G, (float*)B.p, (float*)B.Ap, R, ctx->pcg);
-    ++ctx->launches;
-    k_pcg_xr<float><<<gf, kThreads, 0, s>>>(Ng, (float*)B.x, (float*)B.r, (float*)B.p,
-                                            (float*)B.Ap, (float*)B.z, R, nb3, ctx->pcg);
-    ++ctx->launches;
-  } else {
-    k_pcg_Ap<double><<<g3, kBlock3, 0, s>>>(G, (double*)B.p, (double*)B.Ap, R, ctx->pcg);
-    ++ctx->launches;
-    k_pcg_xr<double><<<gf, kThreads, 0, s>>>(Ng, (double*)B.x, (double*)B.r, (double*)B.p,
-                                             (double*)B.Ap, (double*)B.z, R, nb3, ctx->pcg);
-    ++ctx->launches;
+template <typename V>
+__global__ void __launch_bounds__(kThreadsC, 1) k_hartree_coop(Args<V> a) {
+  extern __shared__ float smem_tail[];
+  __shared__ LevelTable T;
+  __shared__ double wpart[kMaxDots][kMaxRep][kWarps];   // per-warp partials of one phase
+  __shared__ double sc[kSlots][kMaxRep];                // grid-wide sums
+  __shared__ double rz_old[kMaxRep], pAp_old[kMaxRep], beta[kMaxRep], alpha[kMaxRep];
+  __shared__ double bbv[kMaxRep];
+  __shared__ int act[kMaxRep];   // replica still iterating
+  __shared__ int any_act;
+  const int G = gridDim.x;
+  const int gstride = G * blockDim.x;
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned nbar = 0;
+#define COOP_BAR()                                                        \
+  do {                                                                    \
+    if (!grid_barrier(a.bar, (unsigned)G * (++nbar), a.status)) return; \
+  } while (0)
+  // per-warp partial of dot d for replica rp (whole warp calls)
+  auto put = [&](int d, int rp, V v) {
+    v = wsum(v);
+    if (lane == 0) wpart[d][rp][warp] = (double)v;
+  };
+  // block partials of dots 0..nd-1 into slots sl[0..nd-1] (fixed order over warps)
+  auto flush = [&](int nd, int s0, int s1, int s2, int s3) {
+    __syncthreads();
+    const int t = threadIdx.x;
+    if (t < nd * a.nrep) {
+      const int d = t / a.nrep, rp = t - d * a.nrep;
+      const int s = d == 0 ? s0 : d == 1 ? s1 : d == 2 ? s2 : s3;
+      double acc = 0.0;
+      for (int w = 0; w < kWarps; ++w) acc += wpart[d][rp][w];
+      pslot(a, rp, s)[blockIdx.x] = acc;
+    }
+  };
+  // grid-wide sums of slots s0..s(ns-1) into sc (every block, same order)
+  auto gsum = [&](int ns, int s0, int s1, int s2, int s3) {
+    for (int q = warp; q < ns * a.nrep; q += kWarps) {
+      const int k = q / a.nrep, rp = q - k * a.nrep;
+      const int s = k == 0 ? s0 : k == 1 ? s1 : k == 2 ? s2 : s3;
+      const double* src = pslot(a, rp, s);
+      double acc = 0.0;
+      for (int b = lane; b < G; b += 32) acc += src[b];
+      acc = warp_sum(acc);
+      if (lane == 0) sc[s][rp] = acc;
+    }
+    __syncthreads();
+  };
+
+  {  // level table into shared memory
+    const int* src = reinterpret_cast<const int*>(a.lt);
+    int* dst = reinterpret_cast<int*>(&T);
+    for (int i = threadIdx.x; i < (int)(sizeof(LevelTable) / sizeof(int)); i += blockDim.x)
+      dst[i] = src[i];
   }
-  k_pcg_check<<<1, 32 * nrep, 0, s>>>(ctx->pcg, R, rb, B.tol, ctx->opt.poisson_max_iter, nrep,
-                                      ctx->status);
-  ++ctx->launches;
-  RMGTD_LAUNCH(ctx, "k_pcg_iteration");
-  int rc = B.f32 ? vcycle(ctx, nullptr, nullptr, (float*)B.r, (float*)B.z, nrep)
-                 : vcycle(ctx, (double*)B.r, (double*)B.z, nullptr, nullptr, nrep);
-  if (rc) return rc;
-  if (B.f32) {
-    k_pcg_rz<float><<<gf, kThreads, 0, s>>>(Ng, (float*)B.r, (float*)B.z, (float*)B.p, 0, R,
-                                            ctx->pcg);
-    ++ctx->launches;
-    k_pcg_p<float><<<gf, kThreads, 0, s>>>(Ng, (float*)B.z, (float*)B.p, R, rb, ctx->pcg);
-    ++ctx->launches;
-  } else {
-    k_pcg_rz<double><<<gf, kThreads, 0, s>>>(Ng, (double*)B.r, (double*)B.z, (double*)B.p, 0, R,
-                                             ctx->pcg);
-    ++ctx->launches;
-    k_pcg_p<double><<<gf, kThreads, 0, s>>>(Ng, (double*)B.z, (double*)B.p, R, rb, ctx->pcg);
-    ++ctx->launches;
+  const int nrep = a.nrep;
+  if (threadIdx.x < kMaxRep)
+    act[threadIdx.x] = (threadIdx.x < nrep) && (!a.ctl || a.ctl[threadIdx.x].active);
+  __syncthreads();
+  const int nl = T.nl, nmulti = T.nmulti;
+  const int nx = T.L[0].nx, ny = T.L[0].ny, nz = T.L[0].nz, n0 = T.L[0].n;
+  const V ih2 = (V)(1.0 / (a.h * a.h));
+  const V hv = (V)a.h;
+
+  // ---- prologue: multipole moments of the density (change) ----------------------------
+  for (int rp = 0; rp < nrep; ++rp) {
+    V q0 = 0, q1 = 0, q2 = 0, q3 = 0;
+    if (act[rp] && !a.zero_bc) {
+      for (int g = gtid; g < n0; g += gstride) {
+        int ix, iy, iz;
+        xyz_of(g, nx, ny, T.L[0].dx, T.L[0].dy, ix, iy, iz);
+        const V v = dens(a, rp * n0 + g);
+        q0 += v;
+        q1 += v * (((V)ix - (V)0.5 * (V)(nx - 1)) * hv);
+        q2 += v * (((V)iy - (V)0.5 * (V)(ny - 1)) * hv);
+        q3 += v * (((V)iz - (V)0.5 * (V)(nz - 1)) * hv);
+      }
+    }
+    put(0, rp, q0);
+    put(1, rp, q1);
+    put(2, rp, q2);
+    put(3, rp, q3);
   }
-  k_pcg_end<<<1, 32 * nrep, 0, s>>>(ctx->pcg, R, rb, nrep, ctx->pcg_any, cond, use_cond,
-                                     ctx->kexec);
+  flush(4, 4, 5, 6, 7);
+  COOP_BAR();
+  gsum(4, 4, 5, 6, 7);
+
+  // ---- right-hand side b = 4 pi rho + ghost term, residual r = b - A x -----------------
+  {
+    const double h3 = a.h * a.h * a.h;
+    for (int rp = 0; rp < nrep; ++rp) {
+      V bb = 0, rr = 0;
+      if (act[rp]) {
+        const V Q = (V)(h3 * sc[4][rp]), px = (V)(h3 * sc[5][rp]);
+        const V py = (V)(h3 * sc[6][rp]), pz = (V)(h3 * sc[7][rp]);
+        const int base = rp * n0;
+        for (int g = gtid; g < n0; g += gstride) {
+          int ix, iy, iz;
+          xyz_of(g, nx, ny, T.L[0].dx, T.L[0].dy, ix, iy, iz);
+          V bv = (V)(4.0 * kPi) * dens(a, base + g);
+          if (!a.zero_bc)
+            bv += Q * ghost(a, 0, n0, g) + px * ghost(a, 1, n0, g) + py * ghost(a, 2, n0, g) +
+                  pz * ghost(a, 3, n0, g);
+          a.b[base + g] = bv;
+          const V rv = bv - apply_A12<V>(a.x + base, ix, iy, iz, nx, ny, nz, ih2);
+          a.r[base + g] = rv;
+          bb += bv * bv;
+          rr += rv * rv;
+        }
+      }
+      put(0, rp, bb);
+      put(1, rp, rr);
+    }
+  }
+  flush(2, 0, 1, 0, 0);
+  COOP_BAR();
+  gsum(2, 0, 1, 0, 0);
+  if (threadIdx.x < nrep) {
+    const int rp = threadIdx.x;
+    bbv[rp] = sc[0][rp];
+    if (act[rp] && blockIdx.x == 0) {
+      a.st[rp].it = 0;
+      a.st[rp].rr = sc[1][rp];
+      a.st[rp].status = 0;
+    }
+  }
+  __syncthreads();
+  // b = 0: the solution is 0 (CG from a non-zero guess would never meet a relative test)
+  for (int rp = 0; rp < nrep; ++rp)
+    if (act[rp] && bbv[rp] == 0.0)
+      for (int g = gtid; g < n0; g += gstride) a.x[rp * n0 + g] = (V)0;
+  __syncthreads();
+  if (threadIdx.x < nrep) {
+    const int rp = threadIdx.x;
+    if (act[rp] && (bbv[rp] == 0.0 || sc[1][rp] <= a.tol * a.tol * bbv[rp])) act[rp] = 0;
+  }
+  __syncthreads();
+
+  int it = 0;
+  while (true) {
+    if (threadIdx.x == 0) {
+      int an = 0;
+      for (int rp = 0; rp < nrep; ++rp) an |= act[rp];
+      any_act = an;
+    }
+    __syncthreads();
+    if (!any_act) break;
+
+    // ---- V-cycle z = M r: down leg over the multi-block levels --------------------------
+    for (int l = 0; l < nmulti; ++l) {
+      const Level& L = T.L[l];
+      const int Nl = L.n * nrep;
+      const float ih2f = 1.0f / L.h2, c = kJacobiW * L.h2 / 6.0f;
+      if (l == nl - 1) {
+        // coarsest level without a tail: damped-Jacobi sweeps from zero, X <-> T
+        for (int sw = 0; sw < kCoarseSweeps; ++sw) {
+          const float* in = (sw & 1) ? L.t : L.x;
+          float* out = (sw & 1) ? L.x : L.t;
+          for (int e = gtid; e < Nl; e += gstride) {
+            const int rep = fdiv(e, L.dn);
+            if (!act[rep]) continue;
+            float bv;
+            if (l == 0) {
+              bv = (float)a.r[e];
+              if (sw == 0) L.b[e] = bv;
+            } else {
+              bv = L.b[e];
+            }
+            float v;
+            if (sw == 0) {
+              v = c * bv;
+            } else {
+              int ix, iy, iz;
+              xyz_of(e - rep * L.n, L.nx, L.ny, L.dx, L.dy, ix, iy, iz);
+              float cc;
+              const float ax = lap7f(in + rep * L.n, ix, iy, iz, L.nx, L.ny, L.nz, &cc) * ih2f;
+              v = cc + c * (bv - ax);
+            }
+            out[e] = v;
+          }
+          COOP_BAR();
+        }
+        if (kCoarseSweeps & 1) {
+          for (int e = gtid; e < Nl; e += gstride) L.x[e] = L.t[e];
+          COOP_BAR();
+        }
+        continue;
+      }
+      // two pre-sweeps from zero in one pass: x = c (2 b - c A b); level 0 reads b from r
+      for (int e = gtid; e < Nl; e += gstride) {
+        const int rep = fdiv(e, L.dn);
+        if (!act[rep]) continue;
+        int ix, iy, iz;
+        xyz_of(e - rep * L.n, L.nx, L.ny, L.dx, L.dy, ix, iy, iz);
+        const int plane = L.nx * L.ny;
+        float bc, sn = 0.0f;
+        if (l == 0) {
+          const V* rr = a.r;
+          bc = (float)rr[e];
+          if (ix + 1 < L.nx) sn += (float)rr[e + 1];
+          if (ix > 0) sn += (float)rr[e - 1];
+          if (iy + 1 < L.ny) sn += (float)rr[e + L.nx];
+          if (iy > 0) sn += (float)rr[e - L.nx];
+          if (iz + 1 < L.nz) sn += (float)rr[e + plane];
+          if (iz > 0) sn += (float)rr[e - plane];
+          L.b[e] = bc;
+        } else {
+          const float* bb = L.b;
+          bc = bb[e];
+          if (ix + 1 < L.nx) sn += bb[e + 1];
+          if (ix > 0) sn += bb[e - 1];
+          if (iy + 1 < L.ny) sn += bb[e + L.nx];
+          if (iy > 0) sn += bb[e - L.nx];
+          if (iz + 1 < L.nz) sn += bb[e + plane];
+          if (iz > 0) sn += bb[e - plane];
+        }
+        L.x[e] = c * (2.0f * bc - c * (6.0f * bc - sn) * ih2f);
+      }
+      COOP_BAR();
+      // residual t = b - A x
+      for (int e = gtid; e < Nl; e += gstride) {
+        const int rep = fdiv(e, L.dn);
+        if (!act[rep]) continue;
+        int ix, iy, iz;
+        xyz_of(e - rep * L.n, L.nx, L.ny, L.dx, L.dy, ix, iy, iz);
+        float cc;
+        L.t[e] = L.b[e] - lap7f(L.x + rep * L.n, ix, iy, iz, L.nx, L.ny, L.nz, &cc) * ih2f;
+      }
+      COOP_BAR();
+      // restriction to the next level
+      {
+        const Level& C = T.L[l + 1];
+        const int Nc = C.n * nrep;
+        for (int e = gtid; e < Nc; e += gstride) {
+          const int rep = fdiv(e, C.dn);
+          if (!act[rep]) continue;
+          int I, J, K;
+          xyz_of(e - rep * C.n, C.nx, C.ny, C.dx, C.dy, I, J, K);
+          C.b[e] = restrict_point(L.t + rep * L.n, I, J, K, L.nx, L.ny, L.nz);
+        }
+      }
+      COOP_BAR();
+    }
+    // ---- tail levels: one block per replica ---------------------------------------------
+    if (nmulti < nl) {
+      const Level& Lt = T.L[nmulti];
+      for (int rp = blockIdx.x; rp < nrep; rp += G)
+        if (act[rp]) tail_vcycle(T.T, Lt.b + rp * Lt.n, Lt.x + rp * Lt.n, a.cinv, smem_tail);
+      COOP_BAR();
+    }
+    // ---- up leg: x += P x_coarse, two post-sweeps (the last one writes z) ---------------
+    for (int l = min(nmulti, nl - 1) - 1; l >= 0; --l) {
+      const Level& L = T.L[l];
+      const Level& C = T.L[l + 1];
+      const int Nl = L.n * nrep;
+      const float ih2f = 1.0f / L.h2, c = kJacobiW * L.h2 / 6.0f;
+      for (int e = gtid; e < Nl; e += gstride) {
+        const int rep = fdiv(e, L.dn);
+        if (!act[rep]) continue;
+        int ix, iy, iz;
+        xyz_of(e - rep * L.n, L.nx, L.ny, L.dx, L.dy, ix, iy, iz);
+        L.x[e] += prolong_point(C.x + rep * C.n, ix, iy, iz, C.nx, C.ny, C.nz);
+      }
+      COOP_BAR();
+      for (int e = gtid; e < Nl; e += gstride) {
+        const int rep = fdiv(e, L.dn);
+        if (!act[rep]) continue;
+        int ix, iy, iz;
+        xyz_of(e - rep * L.n, L.nx, L.ny, L.dx, L.dy, ix, iy, iz);
+        float cc;
+        const float ax = lap7f(L.x + rep * L.n, ix, iy, iz, L.nx, L.ny, L.nz, &cc) * ih2f;
+        L.t[e] = cc + c * (L.b[e] - ax);
+      }
+      COOP_BAR();
+      for (int e = gtid; e < Nl; e += gstride) {
+        const int rep = fdiv(e, L.dn);
+        if (!act[rep]) continue;
+        int ix, iy, iz;
+        xyz_of(e - rep * L.n, L.nx, L.ny, L.dx, L.dy, ix, iy, iz);
+        float cc;
+        const float ax = lap7f(L.t + rep * L.n, ix, iy, iz, L.nx, L.ny, L.nz, &cc) * ih2f;
+        const float v = cc + c * (L.b[e] - ax);
+        if (l == 0)
+          a.z[e] = (V)v;
+        else
+          L.x[e] = v;
+      }
+      COOP_BAR();
+    }
+    if (nl == 1) {  // the fine level is the coarsest: z = its sweeps' result
+      const int N0 = n0 * nrep;
+      for (int e = gtid; e < N0; e += gstride)
+        if (act[fdiv(e, T.L[0].dn)]) a.z[e] = (V)T.L[0].x[e];
+      COOP_BAR();
+    }
+
+    // ---- A z and the dot products (r,z), (z,Az), (z,Ap_old), (p_old,Az) ------------------
+    const bool first = (it == 0);
+    for (int rp = 0; rp < nrep; ++rp) {
+      V d0 = 0, d1 = 0, d2 = 0, d3 = 0;
+      if (act[rp]) {
+        const int base = rp * n0;
+        const V* zr = a.z + base;
+        for (int g = gtid; g < n0; g += gstride) {
+          int ix, iy, iz;
+          xyz_of(g, nx, ny, T.L[0].dx, T.L[0].dy, ix, iy, iz);
+          const V zc = zr[g];
+          const V az = apply_A12<V>(zr, ix, iy, iz, nx, ny, nz, ih2);
+          a.Az[base + g] = az;
+          d0 += a.r[base + g] * zc;
+          d1 += zc * az;
+          if (!first) {
+            d2 += zc * a.Ap[base + g];
+            d3 += a.p[base + g] * az;
+          }
+        }
+      }
+      put(0, rp, d0);
+      put(1, rp, d1);
+      put(2, rp, d2);
+      put(3, rp, d3);
+    }
+    flush(4, 2, 3, 4, 5);
+    COOP_BAR();
+    gsum(4, 2, 3, 4, 5);
+    // beta (Polak-Ribiere), (p, Ap) with p = z + beta p_old, Ap = Az + beta Ap_old, alpha
+    if (threadIdx.x < nrep && act[threadIdx.x]) {
+      const int rp = threadIdx.x;
+      const double rz = sc[2][rp];
+      double bt = 0.0, pAp = sc[3][rp];
+      if (!first) {
+        bt = (rz - sc[6][rp]) / rz_old[rp];
+        pAp = sc[3][rp] + bt * (sc[4][rp] + sc[5][rp]) + bt * bt * pAp_old[rp];
+      }
+      beta[rp] = bt;
+      alpha[rp] = rz / pAp;
+      rz_old[rp] = rz;
+      pAp_old[rp] = pAp;
+    }
+    __syncthreads();
+
+    // ---- p, Ap, x, r updates; partials of (r,r) and (r_new, z_old) ----------------------
+    for (int rp = 0; rp < nrep; ++rp) {
+      V d0 = 0, d1 = 0;
+      if (act[rp]) {
+        const int base = rp * n0;
+        const V al = (V)alpha[rp], bt = (V)beta[rp];
+        for (int g = gtid; g < n0; g += gstride) {
+          const int e = base + g;
+          const V zc = a.z[e], az = a.Az[e];
+          const V pv = first ? zc : fma(bt, a.p[e], zc);
+          const V apv = first ? az : fma(bt, a.Ap[e], az);
+          a.p[e] = pv;
+          a.Ap[e] = apv;
+          a.x[e] = fma(al, pv, a.x[e]);
+          const V rv = fma(-al, apv, a.r[e]);
+          a.r[e] = rv;
+          d0 += rv * rv;
+          d1 += rv * zc;
+        }
+      }
+      put(0, rp, d0);
+      put(1, rp, d1);
+    }
+    flush(2, 1, 6, 0, 0);
+    COOP_BAR();
+    gsum(2, 1, 6, 0, 0);
+    ++it;
+    if (threadIdx.x < nrep && act[threadIdx.x]) {
+      const int rp = threadIdx.x;
+      const double rr = sc[1][rp];
+      int st = 0;
+      if (!(rr <= 1e300)) {
+        st = RMGTD_EDIVERGED;
+        act[rp] = 0;
+      } else if (rr <= a.tol * a.tol * bbv[rp]) {
+        act[rp] = 0;
+      } else if (it >= a.max_it) {
+        st = RMGTD_ENOTCONVERGED;
+        act[rp] = 0;
+      }
+      if (blockIdx.x == 0) {
+        if (st) {
+          atomicCAS(a.status, 0, st);
+          a.st[rp].status = st;
+        }
+        a.st[rp].it = it;
+        a.st[rp].rr = rr;
+      }
+    }
+    __syncthreads();
+  }
+#undef COOP_BAR
+}
+
+}  // namespace coop
+
+// host launcher of the persistent solve; f32 selects the mixed-path correction solve
+int hartree_coop(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* ctl, int zero_bc,
+                 int nrep, int f32) {
+  if (nrep > coop::kMaxRep) return set_error(ctx, RMGTD_EINVAL, "too many replicas");
+  if (f32 && (!ctx->drho32 || !ctx->ghost32))
+    return set_error(ctx, RMGTD_ESTATE, "mixed Hartree solve without float32 buffers");
+  const size_t smem = ctx->mg_tail_smem;
+  auto fill = [&](auto& a) {
+    a.lt = (const LevelTable*)ctx->mg_table;
+    a.nrep = nrep;
+    a.h = ctx->h;
+    a.rho = rho;
+    a.drho = ctx->drho32;
+    a.gf = ctx->ghost;
+    a.gf32 = ctx->ghost32;
+    a.cinv = ctx->mg_cinv;
+    a.zero_bc = zero_bc;
+    a.part = ctx->red_part;
+    a.st = ctx->pcg;
+    a.ctl = ctl;
+    a.max_it = ctx->opt.poisson_max_iter;
+    a.bar = ctx->bar2;
+    a.status = ctx->status;
+  };
+  const void* fn;
+  void* args[1];
+  coop::Args<float> af;
+  coop::Args<double> ad;
+  if (f32) {
+    fill(af);
+    af.x = ctx->dvh32;
+    af.b = ctx->pcg32_b;
+    af.r = ctx->pcg32_r;
+    af.z = ctx->pcg32_z;
+    af.p = ctx->pcg32_p;
+    af.Ap = ctx->pcg32_Ap;
+    af.Az = ctx->pcg32_Az;
+    af.tol = std::max(ctx->opt.poisson_tol, kMixedPoissonTol);
+    fn = (const void*)coop::k_hartree_coop<float>;
+    args[0] = &af;
+  } else {
+    fill(ad);
+    ad.x = vh;
+    ad.b = ctx->pcg_b;
+    ad.r = ctx->pcg_r;
+    ad.z = ctx->pcg_z;
+    ad.p = ctx->pcg_p;
+    ad.Ap = ctx->pcg_Ap;
+    ad.Az = ctx->pcg_Az;
+    ad.tol = ctx->opt.poisson_tol;
+    fn = (const void*)coop::k_hartree_coop<double>;
+    args[0] = &ad;
+  }
+  const int k = f32 ? 1 : 0;
+  if (!ctx->coop_attr_set[k]) {
+    RMGTD_CUDA(ctx, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)std::max<size_t>(smem, 1)));
+    int per_sm = 0;
+    RMGTD_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, coop::kThreadsC, smem));
+    if (per_sm < 1) return set_error(ctx, RMGTD_ECUDA, "persistent Hartree kernel does not fit on an SM");
+    ctx->coop_grid[k] = std::min(per_sm * ctx->num_sms, ctx->red_cap);
+    ctx->coop_attr_set[k] = 1;
+  }
+  RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->bar2, 0, sizeof(unsigned), ctx->stream));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(ctx->coop_grid[k]);
+  cfg.blockDim = dim3(coop::kThreadsC);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = ctx->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  RMGTD_CUDA(ctx, cudaLaunchKernelExC(&cfg, fn, args));
   ++ctx->launches;
-  RMGTD_LAUNCH(ctx, "k_pcg_end");
+  RMGTD_LAUNCH(ctx, "k_hartree_coop");
   return RMGTD_OK;
 }
 
@@ -1038,24 +1014,6 @@ int hartree_reset_history(rmgtd_ctx* ctx) {
   if (ctx->mixed)
     RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->dvh_prev32, ctx->dvh32, sizeof(float) * n,
                                     cudaMemcpyDeviceToDevice, ctx->stream));
-  return RMGTD_OK;
-}
-
-// Eager Hartree solve (host-driven loop, peeking at the convergence flag).
-int hartree_dev(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* ctl, int zero_bc,
-                int nrep, int f32) {
-  int rc = hartree_begin(ctx, rho, vh, ctl, zero_bc, nrep, 0, 0, f32);
-  if (rc) return rc;
-  for (int it = 0; it < ctx->opt.poisson_max_iter; ++it) {
-    rc = hartree_iteration(ctx, vh, nrep, 0, 0, f32);
-    if (rc) return rc;
-    if ((it & 3) == 3) {
-      RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->pcg_any_host, ctx->pcg_any, sizeof(int),
-                                      cudaMemcpyDeviceToHost, ctx->stream));
-      RMGTD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-      if (!*ctx->pcg_any_host) break;
-    }
-  }
   return RMGTD_OK;
 }
 

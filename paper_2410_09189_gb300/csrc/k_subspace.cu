@@ -241,13 +241,14 @@ __global__ void k_shat32(int N, int Np, const double* __restrict__ S, const doub
   }
 }
 
-// rho = rho_ref + sum_j phi_j X_j, X_j = sum_{k<=j} Shat_kj phi_k: each thread two grid
+// rho = rho_ref + drho, drho = sum_j phi_j X_j (also stored in float32 for the Hartree
+// solve), X_j = sum_{k<=j} Shat_kj phi_k: each thread two grid
 // points (g, g + 128), 32 columns j at a time, Shat rows read as float4 broadcasts.
 constexpr int kRho32Pts = 2;
 __global__ void __launch_bounds__(kRhoThreads)
 k_rho32(int N, int Np, long Ng, const float* __restrict__ phi, const float* __restrict__ shat,
-        const double* __restrict__ rho_ref, double* __restrict__ rho, long rstride,
-        const RepCtl* __restrict__ ctl) {
+        const double* __restrict__ rho_ref, double* __restrict__ rho, float* __restrict__ drho,
+        long rstride, const RepCtl* __restrict__ ctl) {
   const int rep = blockIdx.y;
   if (ctl && !ctl[rep].active) return;
   __shared__ __align__(16) float Sh[kRhoK][kRhoJ];
@@ -320,8 +321,14 @@ k_rho32(int N, int Np, long Ng, const float* __restrict__ phi, const float* __re
       }
     }
   }
-  if (ok0) rho[rep * rstride + g0] = rho_ref[g0] + (double)r0;
-  if (ok1) rho[rep * rstride + g1] = rho_ref[g1] + (double)r1;
+  if (ok0) {
+    rho[rep * rstride + g0] = rho_ref[g0] + (double)r0;
+    drho[rep * rstride + g0] = r0;
+  }
+  if (ok1) {
+    rho[rep * rstride + g1] = rho_ref[g1] + (double)r1;
+    drho[rep * rstride + g1] = r1;
+  }
 }
 
 int rho_dev_mixed(rmgtd_ctx* ctx, const double* S, double* rho, const RepCtl* ctl, int nrep) {
@@ -332,7 +339,7 @@ int rho_dev_mixed(rmgtd_ctx* ctx, const double* S, double* rho, const RepCtl* ct
   ++ctx->launches;
   dim3 grid(ceil_div(ctx->Ng, kRhoThreads * kRho32Pts), nrep);
   k_rho32<<<grid, kRhoThreads, 0, ctx->stream>>>(N, Np, ctx->Ng, ctx->phi32, ctx->shat32,
-                                                  ctx->rho_ref, rho, ctx->Ng, ctl);
+                                                  ctx->rho_ref, rho, ctx->drho32, ctx->Ng, ctl);
   ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_rho32");
   return RMGTD_OK;

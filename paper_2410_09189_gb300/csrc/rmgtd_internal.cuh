@@ -128,7 +128,9 @@ struct rmgtd_ctx {
   float* shat32 = nullptr;     // [nrep][Np][Np] float32 density-change matrix (mixed)
   double* vh_prev = nullptr;   // [nrep][Ng] V_H one step earlier (initial-guess history)
   float *pcg32_b = nullptr, *pcg32_r = nullptr, *pcg32_z = nullptr, *pcg32_p = nullptr,
-        *pcg32_Ap = nullptr;   // [nrep][Ng] float32 CG vectors (mixed)
+        *pcg32_Ap = nullptr, *pcg32_Az = nullptr;   // [nrep][Ng] float32 CG vectors (mixed)
+  float* drho32 = nullptr;     // [nrep][Ng] rho - rho_ref in float32 (mixed)
+  float* ghost32 = nullptr;    // [4][Ng] float32 copy of the ghost response fields (mixed)
   int mixed = 0;               // mixed-precision step active (after set-up)
   int subspace_iters = 0;      // subspace SCF iterations done at set-up
   double subspace_err = 0;     // last max|P_new - P| of the subspace SCF
@@ -139,18 +141,20 @@ struct rmgtd_ctx {
 
   // Hartree solve
   double *pcg_b = nullptr, *pcg_r = nullptr, *pcg_z = nullptr, *pcg_p = nullptr,
-         *pcg_Ap = nullptr;    // [nrep][Ng]
+         *pcg_Ap = nullptr, *pcg_Az = nullptr;    // [nrep][Ng]
+  unsigned* bar2 = nullptr;          // grid-barrier counter of the persistent Hartree solve
+  int coop_attr_set[2] = {0, 0};     // persistent Hartree kernel configured (float64, float32)
+  int coop_grid[2] = {0, 0};
   double* red_part = nullptr;  // reduction partials
   int red_blocks = 0;                // blocks of the grid-stride reduction kernels
   int red_cap = 0;                   // capacity of one partial slot
   rmgtd::PcgState* pcg = nullptr;   // [nrep]
-  int* pcg_any = nullptr;           // device flag: some replica still iterating
-  int* pcg_any_host = nullptr;      // pinned
   double* ghost = nullptr;          // [4][Ng] ghost response fields G0, Gx, Gy, Gz
   std::vector<rmgtd::MgLevel> mg;   // multi-CTA levels (level 0 = fine grid)
   int mg_tail_level = -1;           // first level solved inside one CTA
   size_t mg_tail_smem = 0;
   float* mg_cinv = nullptr;         // inverse of the coarsest operator (tail), or NULL
+  void* mg_table = nullptr;         // device level table of the persistent solve
 
   // control
   rmgtd::RepCtl* ctl = nullptr;     // [nrep]
@@ -181,9 +185,9 @@ struct rmgtd_ctx {
   rmgtd::RepCtl* stats_dev = nullptr;  // [stats_cap][nrep]
   rmgtd::RepCtl* stats_host = nullptr; // pinned mirror
   int stats_cap = 0;
-  // kernel counts of the captured step: top level, SCF-pass body, Hartree-iteration body;
-  // executions of the bodies are counted on the device (kexec[0], kexec[1])
-  int cap_top = 0, cap_scf = 0, cap_pcg = 0;
+  // kernel counts of the captured step: top level and SCF-pass body; executions of the
+  // body are counted on the device (kexec[0])
+  int cap_top = 0, cap_scf = 0;
   long long graph_steps = 0;
   unsigned long long* kexec = nullptr;
 
@@ -332,16 +336,12 @@ int subspace_update(rmgtd_ctx* ctx, double alpha, double* err_dev);
 int orthonormalize(rmgtd_ctx* ctx);
 // k_poisson.cu
 int setup_multigrid(rmgtd_ctx* ctx);
-int poisson_red_cap(int nx, int ny, int nz, int red_blocks);
-int hartree_dev(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* ctl, int zero_bc,
-                int nrep, int f32);
-int hartree_graph(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* ctl, int nrep,
-                  int f32);
-int hartree_begin(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* ctl, int zero_bc,
-                  int nrep, cudaGraphConditionalHandle cond, int use_cond, int f32);
+int poisson_red_cap(int num_sms, int red_blocks);
 int hartree_extrapolate(rmgtd_ctx* ctx);
+// Hartree solve of every active replica in one cooperative launch; f32 = 1: float32
+// correction solve of the mixed path (reads drho32, writes dvh32)
+int hartree_coop(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* ctl, int zero_bc,
+                 int nrep, int f32);
 int hartree_reset_history(rmgtd_ctx* ctx);
-int hartree_iteration(rmgtd_ctx* ctx, double* vh, int nrep, cudaGraphConditionalHandle cond,
-                      int use_cond, int f32);
 
 }  // namespace rmgtd
