@@ -226,6 +226,13 @@ int rmgtd_profile(rmgtd_ctx* ctx, int enable);
 int rmgtd_profile_read(rmgtd_ctx* ctx, double* phase_ms, long long* phase_calls,
                        long long* launches);
 
+/* Work counters of the Hartree solve since the last rmgtd_profile call, for host-driven and
+ * graph steps alike: replica solves (Section 2.1's Poisson problem, one per replica per DFT
+ * evaluation) and conjugate-gradient iterations summed over them.  Either pointer may be
+ * NULL.  Synchronises the stream. */
+int rmgtd_profile_counters(rmgtd_ctx* ctx, long long* hartree_solves,
+                           long long* hartree_iterations);
+
 /* Allocation-free Gram contraction  C = scale * A^T diag(w) B  (N x N, row-major) for two
  * orbital blocks A, B of n_orb columns of n_grid points each (orbital-major device arrays,
  * as in rmgtd_system.phi0), w (n_grid device doubles) or NULL for w = 1; c_dev receives

@@ -382,7 +382,7 @@ static int create_impl(const rmgtd_system* sys, const rmgtd_options* opt, rmgtd_
   ctx->status = (int*)A(sizeof(int));
   ctx->obs = (double*)A(sizeof(double) * 8 * nrep);
   ctx->failed = (int*)A(sizeof(int));
-  ctx->kexec = (unsigned long long*)A(2 * sizeof(unsigned long long));
+  ctx->kexec = (unsigned long long*)A(4 * sizeof(unsigned long long));
   ctx->done_steps = (int*)A(sizeof(int));
   ctx->stats_cap = 256;
   ctx->stats_dev = (RepCtl*)A(sizeof(RepCtl) * ctx->stats_cap * nrep);
@@ -401,7 +401,7 @@ static int create_impl(const rmgtd_system* sys, const rmgtd_options* opt, rmgtd_
   RMGTD_CUDA(ctx, cudaMallocHost((void**)&ctx->obs_host, sizeof(double) * 8 * nrep));
   RMGTD_CUDA(ctx, cudaMallocHost((void**)&ctx->stats_host, sizeof(RepCtl) * ctx->stats_cap * nrep));
   RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->failed, 0, sizeof(int), ctx->stream));
-  RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->kexec, 0, 2 * sizeof(unsigned long long), ctx->stream));
+  RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->kexec, 0, 4 * sizeof(unsigned long long), ctx->stream));
   RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream));
   RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->vh, 0, gsz * nrep, ctx->stream));
   RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->ctl, 0, sizeof(RepCtl) * nrep, ctx->stream));
@@ -787,7 +787,7 @@ int rmgtd_profile(rmgtd_ctx* ctx, int enable) {
   }
   ctx->launches = 0;
   ctx->graph_steps = 0;
-  RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->kexec, 0, 2 * sizeof(unsigned long long), ctx->stream));
+  RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->kexec, 0, 4 * sizeof(unsigned long long), ctx->stream));
   return RMGTD_OK;
 }
 
@@ -805,6 +805,17 @@ int rmgtd_profile_read(rmgtd_ctx* ctx, double* phase_ms, long long* phase_calls,
     RMGTD_CUDA(ctx, cudaMemcpy(kx, ctx->kexec, sizeof(kx), cudaMemcpyDeviceToHost));
     *launches = ctx->launches + ctx->graph_steps * ctx->cap_top + (long long)kx[0] * ctx->cap_scf;
   }
+  return RMGTD_OK;
+}
+
+int rmgtd_profile_counters(rmgtd_ctx* ctx, long long* hartree_solves,
+                           long long* hartree_iterations) {
+  if (!ctx) return set_error(nullptr, RMGTD_EINVAL, "ctx is NULL");
+  unsigned long long kx[4] = {0, 0, 0, 0};
+  RMGTD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  RMGTD_CUDA(ctx, cudaMemcpy(kx, ctx->kexec, sizeof(kx), cudaMemcpyDeviceToHost));
+  if (hartree_solves) *hartree_solves = (long long)kx[2];
+  if (hartree_iterations) *hartree_iterations = (long long)kx[3];
   return RMGTD_OK;
 }
 

@@ -32,6 +32,7 @@ constexpr double kPi = 3.14159265358979323846;
 constexpr float kJacobiW = 6.0f / 7.0f;
 constexpr int kTailMax = 4096;
 constexpr int kPre = 2, kPost = 2, kCoarseSweeps = 40;
+static_assert(kPre == 2, "the pre-smoothing pass fuses exactly two sweeps from zero");
 // relative residual of the float32 correction solve of the mixed path (float32 CG reaches
 // ~1e-6-1e-7; the correction is small next to the float64 reference potential)
 constexpr double kMixedPoissonTol = 1e-6;
@@ -240,7 +241,9 @@ __device__ void tail_jacobi(const Tail& L, int l, float* x, float* t, const floa
 }
 
 // V-cycle of the tail levels for one replica inside one block (all threads of the block):
-// b_in / x_out are that replica's arrays of the first tail level, sm the dynamic shared memory.
+// b_in / x_out are that replica's arrays of the first tail level, sm the dynamic shared
+// memory.  Down: both pre-sweeps from zero in one pass, residual, restriction; up:
+// prolongation, two post-sweeps ping-ponging between x and t.
 __device__ void tail_vcycle(const Tail& L, const float* __restrict__ b_in,
                             float* __restrict__ x_out, const float* __restrict__ cinv, float* sm) {
   float* xs[kMaxLevels];
@@ -269,16 +272,25 @@ __device__ void tail_vcycle(const Tail& L, const float* __restrict__ b_in,
       __syncthreads();
       break;
     }
-    const int sweeps = coarsest ? kCoarseSweeps : kPre;
-    for (int sw = 0; sw < sweeps; ++sw) tail_jacobi(L, l, xs[l], ts[l], bs[l], sw == 0);
-    if (coarsest) break;
+    if (coarsest) {
+      for (int sw = 0; sw < kCoarseSweeps; ++sw) tail_jacobi(L, l, xs[l], ts[l], bs[l], sw == 0);
+      break;
+    }
     const int nx = L.nx[l], ny = L.ny[l], nz = L.nz[l], n = L.n[l];
-    const float ih2 = 1.0f / L.h2[l];
-    for (int g = threadIdx.x; g < n; g += blockDim.x) {
+    const float h2 = L.h2[l], ih2 = 1.0f / h2, c = kJacobiW * h2 / 6.0f;
+    for (int g = threadIdx.x; g < n; g += blockDim.x) {   // x = c (2 b - c A b)
       int ix, iy, iz;
       xyz_of(g, nx, ny, L.dx[l], L.dy[l], ix, iy, iz);
-      float c;
-      ts[l][g] = bs[l][g] - lap7f(xs[l], ix, iy, iz, nx, ny, nz, &c) * ih2;
+      float bc;
+      const float ab = lap7f(bs[l], ix, iy, iz, nx, ny, nz, &bc) * ih2;
+      xs[l][g] = c * (2.0f * bc - c * ab);
+    }
+    __syncthreads();
+    for (int g = threadIdx.x; g < n; g += blockDim.x) {   // t = b - A x
+      int ix, iy, iz;
+      xyz_of(g, nx, ny, L.dx[l], L.dy[l], ix, iy, iz);
+      float cc;
+      ts[l][g] = bs[l][g] - lap7f(xs[l], ix, iy, iz, nx, ny, nz, &cc) * ih2;
     }
     __syncthreads();
     const int cx = L.nx[l + 1], cy = L.ny[l + 1], nc = L.n[l + 1];
@@ -290,15 +302,30 @@ __device__ void tail_vcycle(const Tail& L, const float* __restrict__ b_in,
     __syncthreads();
   }
   for (int l = L.nl - 2; l >= 0; --l) {
-    const int nx = L.nx[l], ny = L.ny[l], n = L.n[l];
+    const int nx = L.nx[l], ny = L.ny[l], nz = L.nz[l], n = L.n[l];
     const int cx = L.nx[l + 1], cy = L.ny[l + 1], cz = L.nz[l + 1];
+    const float h2 = L.h2[l], ih2 = 1.0f / h2, c = kJacobiW * h2 / 6.0f;
     for (int g = threadIdx.x; g < n; g += blockDim.x) {
       int fx, fy, fz;
       xyz_of(g, nx, ny, L.dx[l], L.dy[l], fx, fy, fz);
       xs[l][g] += prolong_point(xs[l + 1], fx, fy, fz, cx, cy, cz);
     }
     __syncthreads();
-    for (int sw = 0; sw < kPost; ++sw) tail_jacobi(L, l, xs[l], ts[l], bs[l], 0);
+    for (int sw = 0; sw < kPost; ++sw) {
+      const float* in = (sw & 1) ? ts[l] : xs[l];
+      float* out = (sw & 1) ? xs[l] : ts[l];
+      for (int g = threadIdx.x; g < n; g += blockDim.x) {
+        int ix, iy, iz;
+        xyz_of(g, nx, ny, L.dx[l], L.dy[l], ix, iy, iz);
+        float cc;
+        const float ax = lap7f(in, ix, iy, iz, nx, ny, nz, &cc) * ih2;
+        out[g] = cc + c * (bs[l][g] - ax);
+      }
+      __syncthreads();
+    }
+    if (kPost & 1)
+      for (int g = threadIdx.x; g < n; g += blockDim.x) xs[l][g] = ts[l][g];
+    __syncthreads();
   }
   for (int g = threadIdx.x; g < n0; g += blockDim.x) x_out[g] = xs[0][g];
   __syncthreads();
@@ -480,6 +507,7 @@ struct Args {
   int max_it;
   unsigned* bar;
   int* status;
+  unsigned long long* counters;   // [0] solves, [1] CG iterations (summed over replicas)
 };
 
 __device__ __forceinline__ float wsum(float v) { return warp_sumf(v); }
@@ -510,6 +538,7 @@ __global__ void __launch_bounds__(kThreadsC, 1) k_hartree_coop(Args<V> a) {
   __shared__ double rz_old[kMaxRep], pAp_old[kMaxRep], beta[kMaxRep], alpha[kMaxRep];
   __shared__ double bbv[kMaxRep];
   __shared__ int act[kMaxRep];   // replica still iterating
+  __shared__ int act0[kMaxRep];  // replica solved by this launch
   __shared__ int any_act;
   const int G = gridDim.x;
   const int gstride = G * blockDim.x;
@@ -558,8 +587,10 @@ __global__ void __launch_bounds__(kThreadsC, 1) k_hartree_coop(Args<V> a) {
       dst[i] = src[i];
   }
   const int nrep = a.nrep;
-  if (threadIdx.x < kMaxRep)
+  if (threadIdx.x < kMaxRep) {
     act[threadIdx.x] = (threadIdx.x < nrep) && (!a.ctl || a.ctl[threadIdx.x].active);
+    act0[threadIdx.x] = act[threadIdx.x];
+  }
   __syncthreads();
   const int nl = T.nl, nmulti = T.nmulti;
   const int nx = T.L[0].nx, ny = T.L[0].ny, nz = T.L[0].nz, n0 = T.L[0].n;
@@ -894,6 +925,10 @@ __global__ void __launch_bounds__(kThreadsC, 1) k_hartree_coop(Args<V> a) {
     }
     __syncthreads();
   }
+  if (a.counters && blockIdx.x == 0 && threadIdx.x < nrep && act0[threadIdx.x]) {
+    atomicAdd(&a.counters[0], 1ull);
+    atomicAdd(&a.counters[1], (unsigned long long)a.st[threadIdx.x].it);
+  }
 #undef COOP_BAR
 }
 
@@ -922,6 +957,7 @@ int hartree_coop(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* ct
     a.max_it = ctx->opt.poisson_max_iter;
     a.bar = ctx->bar2;
     a.status = ctx->status;
+    a.counters = ctx->kexec + 2;
   };
   const void* fn;
   void* args[1];

@@ -345,69 +345,195 @@ int rho_dev_mixed(rmgtd_ctx* ctx, const double* S, double* rho, const RepCtl* ct
   return RMGTD_OK;
 }
 
-// float32 Gram partials h-free sums sum_{g in split} phi_i(g) dv(g) phi_j(g) for one 32 x 32
-// output tile (symmetric pairs I <= J): 64 threads, each a 4 x 4 register tile; the k-slab
-// of 32 points is staged transposed in shared memory and read as float4 (1 LDS.128 per 4
-// values, 2 per 16 FFMA).
-constexpr int kG32Threads = 64;
+// float32 H update of the mixed path: C_r = sum_g phi_i(g) w_r(g) phi_j(g) for every replica
+// r, i <= j.  Block = 4 k-groups x 128 threads; each k-group takes 32 of the 128 grid points
+// staged per slab.  A thread owns one 4 x 4 sub-tile of the 32 x 32 output tile pair
+// (It, Jt) for one replica: in a diagonal tile pair only the 36 sub-tiles on or above the
+// diagonal are formed (3 replicas per block), otherwise all 64 (2 replicas per block).  The
+// staged orbital slab serves every replica of the block.  The 4 k-groups are summed in
+// shared memory and each block writes its float32 partial tile [split][rep][Np][Np].
+constexpr int kG32Slab = 128;               // grid points staged per slab
+constexpr int kG32Groups = 4;               // k-groups per block
+constexpr int kG32Group = 128;              // threads per k-group
+constexpr int kG32Threads = kG32Groups * kG32Group;
+constexpr int kG32Pad = kGT + 4;   // 144-byte rows: float4 reads, conflict-free staging
+
+struct Gram32Smem {
+  union {
+    struct {
+      float A[kG32Slab][kG32Pad];   // [k][i] rows of tile It
+      float B[kG32Slab][kG32Pad];   // [k][j] rows of tile Jt
+      float W[kG32Slab][4];         // [k][replica of the block]
+    } s;
+    float red[kG32Groups - 1][kG32Group][16];
+  };
+};
+
+// sub-tile (I4, J4) of item s: diagonal pair -> upper-triangle enumeration of the 8 x 8 grid
+__device__ __forceinline__ void subtile_of(int s, bool diag, int& I4, int& J4) {
+  if (!diag) {
+    I4 = s >> 3;
+    J4 = s & 7;
+    return;
+  }
+  int i = 0, rem = s;
+  while (rem >= 8 - i) {
+    rem -= 8 - i;
+    ++i;
+  }
+  I4 = i;
+  J4 = i + rem;
+}
+
 __global__ void __launch_bounds__(kG32Threads)
-k_gram_partial32(int N, long Ng, const float* __restrict__ A, const float* __restrict__ w,
-                 long wstride, int T, long chunk, double* __restrict__ part,
-                 const RepCtl* __restrict__ ctl) {
-  const int rep = blockIdx.z;
-  if (ctl && !ctl[rep].active) return;
-  __shared__ __align__(16) float As[kGT][kGT + 4];
-  __shared__ __align__(16) float Bs[kGT][kGT + 4];
-  int I, J;
-  pair_from_index(blockIdx.x, T, 1, I, J);
-  const int split = blockIdx.y, nsplit = gridDim.y;
-  const long g_beg = (long)split * chunk;
-  const long g_end = min(Ng, g_beg + chunk);
-  const float* wr = w + rep * wstride;
-  const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;   // 8 x 8 threads
+k_gram32(int N, int Np, int Ng, const float* __restrict__ phi, const float* __restrict__ w,
+         int nrep, int T, int chunk, float* __restrict__ part, const RepCtl* __restrict__ ctl) {
+  __shared__ __align__(16) Gram32Smem sm;
+  int It, Jt;
+  pair_from_index(blockIdx.y, T, 1, It, Jt);
+  const bool diag = (It == Jt);
+  const int per_rep = diag ? 36 : 64;
+  const int R = diag ? 3 : 2;                  // replicas per block
+  const int rep0 = blockIdx.z * R;
+  if (rep0 >= nrep) return;
+  const int nr = min(R, nrep - rep0);
+  const int split = blockIdx.x;
+  const int g_beg = split * chunk;
+  const int g_end = min(Ng, g_beg + chunk);
+  const int tid = threadIdx.x, kg = tid / kG32Group, u = tid % kG32Group;
+  const bool work = u < nr * per_rep;
+  const int rl = work ? u % nr : 0;           // replica (minor) and sub-tile (major)
+  int I4 = 0, J4 = 0;
+  if (work) subtile_of(u / nr, diag, I4, J4);
+  const bool rep_on = work && (!ctl || ctl[rep0 + rl].active);
   float acc[4][4];
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int p = 0; p < 4; ++p)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0f;
-  for (long g0 = g_beg; g0 < g_end; g0 += kGT) {
-    // stage: 32 rows x 32 points of A (rows of tile I) and of w*A (rows of tile J)
+    for (int q = 0; q < 4; ++q) acc[p][q] = 0.0f;
+  for (int g0 = g_beg; g0 < g_end; g0 += kG32Slab) {
+    __syncthreads();
+    // stage: lane <-> orbital row (conflict-free transposed stores), 4 points per load
+    for (int e = tid; e < 2 * kGT * (kG32Slab / 4); e += kG32Threads) {
+      const int which = e / (kGT * (kG32Slab / 4));     // 0: tile It, 1: tile Jt
+      const int r = e % kGT, q = (e / kGT) % (kG32Slab / 4);
+      if (which == 1 && diag) continue;
+      const int row = (which ? Jt : It) * kGT + r;
+      const int g = g0 + 4 * q;
+      float v[4] = {0.f, 0.f, 0.f, 0.f};
+      if (row < N) {
+        const float* src = phi + (long)row * Ng + g;
+        if (g + 3 < g_end && ((((long)row * Ng + g) & 3) == 0)) {
+          const float4 t = *reinterpret_cast<const float4*>(src);
+          v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+        } else {
 #pragma unroll
-    for (int e = 0; e < 16; ++e) {
-      const int idx = tid + kG32Threads * e;  // 0 .. 1023
-      const int r = idx >> 5, c = idx & 31;
-      const long g = g0 + c;
-      const int ia = I * kGT + r, jb = J * kGT + r;
-      float av = 0.0f, bv = 0.0f;
-      if (g < g_end) {
-        if (ia < N) av = A[(long)ia * Ng + g];
-        if (jb < N) bv = A[(long)jb * Ng + g] * wr[g];
+          for (int c = 0; c < 4; ++c)
+            if (g + c < g_end) v[c] = src[c];
+        }
       }
-      As[c][r] = av;
-      Bs[c][r] = bv;
+      float(*dst)[kG32Pad] = which ? sm.s.B : sm.s.A;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) dst[4 * q + c][r] = v[c];
+    }
+    for (int e = tid; e < kG32Slab * 4; e += kG32Threads) {
+      const int k = e >> 2, rr = e & 3;
+      const int g = g0 + k;
+      sm.s.W[k][rr] = (rr < nr && g < g_end) ? w[(long)(rep0 + rr) * Ng + g] : 0.0f;
     }
     __syncthreads();
-#pragma unroll 8
-    for (int k = 0; k < kGT; ++k) {
-      const float4 a = *reinterpret_cast<const float4*>(&As[k][4 * ty]);
-      const float4 b = *reinterpret_cast<const float4*>(&Bs[k][4 * tx]);
-      const float av[4] = {a.x, a.y, a.z, a.w};
-      const float bv[4] = {b.x, b.y, b.z, b.w};
+    if (rep_on) {
+      const float(*Bt)[kG32Pad] = diag ? sm.s.A : sm.s.B;
+#pragma unroll 4
+      for (int kk = 0; kk < kG32Slab / kG32Groups; ++kk) {
+        const int k = kg * (kG32Slab / kG32Groups) + kk;
+        const float4 a = *reinterpret_cast<const float4*>(&sm.s.A[k][4 * I4]);
+        const float4 b = *reinterpret_cast<const float4*>(&Bt[k][4 * J4]);
+        const float wv = sm.s.W[k][rl];
+        const float av[4] = {a.x, a.y, a.z, a.w};
+        const float bv[4] = {b.x * wv, b.y * wv, b.z * wv, b.w * wv};
 #pragma unroll
-      for (int p = 0; p < 4; ++p)
+        for (int p = 0; p < 4; ++p)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(av[p], bv[q], acc[p][q]);
+          for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(av[p], bv[q], acc[p][q]);
+      }
     }
-    __syncthreads();
   }
-  double* out = part + (long)rep * N * N * nsplit + split;
+  // sum the k-groups (fixed order), then write this block's partial tile
+  __syncthreads();
+  if (kg > 0) {
 #pragma unroll
-  for (int p = 0; p < 4; ++p) {
-    const int i = I * kGT + 4 * ty + p;
+    for (int p = 0; p < 4; ++p)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int j = J * kGT + 4 * tx + q;
-      if (i < N && j < N) out[((long)i * N + j) * nsplit] = acc[p][q];
+      for (int q = 0; q < 4; ++q) sm.red[kg - 1][u][4 * p + q] = acc[p][q];
+  }
+  __syncthreads();
+  if (kg == 0 && work) {
+    const long NpNp = (long)Np * Np;
+    float* out = part + ((long)split * nrep + rep0 + rl) * NpNp;
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      const int i = It * kGT + 4 * I4 + p;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        float v = acc[p][q];
+        for (int g = 0; g < kG32Groups - 1; ++g) v += sm.red[g][u][4 * p + q];
+        out[(long)i * Np + Jt * kGT + 4 * J4 + q] = rep_on ? v : 0.0f;
+      }
+    }
+  }
+}
+
+// out[rep] = base + scale * sum_split part (float64, fixed order), mirrored to i > j;
+// max_ij |out - prev| folded into errbits.  Block = 8 warps x 32 consecutive elements of
+// one replica; warp w sums the splits s = w, w + 8, ...
+__global__ void __launch_bounds__(256)
+k_gram32_reduce(int N, int Np, int nsplit, int nrep, const float* __restrict__ part,
+                double scale, const double* __restrict__ base, double* out, const double* prev,
+                unsigned long long* errbits, const RepCtl* __restrict__ ctl) {
+  const int rep = blockIdx.y;
+  if (ctl && !ctl[rep].active) return;
+  __shared__ double sh[8][33];
+  __shared__ double shm[32];
+  const long NpNp = (long)Np * Np;
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  const long e = (long)blockIdx.x * 32 + lane;
+  double s = 0.0;
+  if (e < NpNp) {
+    // eight independent loads in flight per step, summed in split order
+    for (int k0 = wp; k0 < nsplit; k0 += 64) {
+      float v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int k = k0 + 8 * u;
+        v[u] = k < nsplit ? part[((long)k * nrep + rep) * NpNp + e] : 0.0f;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) s += (double)v[u];
+    }
+  }
+  sh[wp][lane] = s;
+  __syncthreads();
+  double emax = 0.0;
+  if (wp == 0 && e < NpNp) {
+    double t = 0.0;
+    for (int k = 0; k < 8; ++k) t += sh[k][lane];
+    const int i = (int)(e / Np), j = (int)(e % Np);
+    if (i < N && j < N && i <= j) {
+      const long NN = (long)N * N;
+      const long o = (long)i * N + j;
+      double v = scale * t;
+      if (base) v += base[o];
+      double* orow = out + rep * NN;
+      if (prev) emax = fmax(emax, fabs(v - prev[rep * NN + o]));
+      orow[o] = v;
+      if (i != j) orow[(long)j * N + i] = v;
+    }
+  }
+  if (errbits) {
+    if (wp == 0) {
+      emax = warp_max(emax);
+      if (lane == 0) atomic_max_nonneg(&errbits[rep], emax);
     }
   }
 }
@@ -416,24 +542,27 @@ int gram_mixed(rmgtd_ctx* ctx, const float* w, long wstride, int nw, double scal
                const double* base, double* out, const RepCtl* ctl, unsigned long long* errbits) {
   const int N = ctx->N;
   const int T = ceil_div(N, kGT);
-  const int ntiles = T * (T + 1) / 2;
-  // 64-thread blocks: aim at ~16 resident warps per SM
-  long ns = (16L * ctx->num_sms + (long)ntiles * nw - 1) / ((long)ntiles * nw);
-  ns = std::max<long>(1, std::min<long>(ns, ctx->Ng / 256 + 1));
-  ns = std::min<long>(ns, (long)(ctx->gram_part_elems / std::max<long>((long)nw * N * N, 1)));
-  const int nsplit = (int)std::max<long>(ns, 1);
-  const long chunk = ((ctx->Ng + nsplit - 1) / nsplit + kGT - 1) / kGT * kGT;
-  dim3 grid(ntiles, nsplit, nw);
-  k_gram_partial32<<<grid, kG32Threads, 0, ctx->stream>>>(N, ctx->Ng, ctx->phi32, w, wstride, T,
-                                                           chunk, ctx->gram_part, ctl);
+  const int Np = T * kGT;
+  const int npairs = T * (T + 1) / 2;
+  if (wstride != ctx->Ng) return set_error(ctx, RMGTD_EINVAL, "gram_mixed: replica stride must be Ng");
+  const int ngroups = ceil_div(nw, 2);   // replica groups of off-diagonal pairs (diagonal: 3)
+  // about two blocks per SM over the (pair, replica-group) units, bounded by the partials
+  long ns = ceil_div(2L * ctx->num_sms, (long)npairs * ceil_div(nw, 3));
+  ns = std::max<long>(1, std::min<long>(ns, ceil_div(ctx->Ng, (long)kG32Slab)));
+  const long per = (long)nw * Np * Np;   // floats per split
+  ns = std::min<long>(ns, (long)(2 * ctx->gram_part_elems) / std::max<long>(per, 1));
+  if (ns < 1) return set_error(ctx, RMGTD_ENOMEM, "gram_mixed: partial buffer too small");
+  const int nsplit = (int)ns;
+  const int chunk = (int)(ceil_div(ceil_div(ctx->Ng, (long)nsplit), (long)kG32Slab) * kG32Slab);
+  float* part = reinterpret_cast<float*>(ctx->gram_part);
+  k_gram32<<<dim3(nsplit, npairs, ngroups), kG32Threads, 0, ctx->stream>>>(
+      N, Np, (int)ctx->Ng, ctx->phi32, w, nw, T, chunk, part, ctl);
   ++ctx->launches;
-  RMGTD_LAUNCH(ctx, "k_gram_partial32");
-  const long NN = (long)N * N;
-  const int rb = (int)std::min<long>(ceil_div(NN, 8), 4L * ctx->num_sms);
-  k_gram_reduce<<<dim3(rb, nw), 256, 0, ctx->stream>>>(N, nsplit, ctx->gram_part, scale, base, out,
-                                                        NN, out, 1, errbits, ctl);
+  RMGTD_LAUNCH(ctx, "k_gram32");
+  k_gram32_reduce<<<dim3(ceil_div((long)Np * Np, 32L), nw), 256, 0, ctx->stream>>>(
+      N, Np, nsplit, nw, part, scale, base, out, out, errbits, ctl);
   ++ctx->launches;
-  RMGTD_LAUNCH(ctx, "k_gram_reduce");
+  RMGTD_LAUNCH(ctx, "k_gram32_reduce");
   return RMGTD_OK;
 }
 

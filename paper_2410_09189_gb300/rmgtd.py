@@ -99,6 +99,8 @@ def load_library(path: Optional[str] = None):
         "rmgtd_time": (i, [vp, _c_double_p, ctypes.POINTER(ctypes.c_longlong)]),
         "rmgtd_last_error": (ctypes.c_char_p, [vp]),
         "rmgtd_profile": (i, [vp, i]),
+        "rmgtd_profile_counters": (i, [vp, ctypes.POINTER(ctypes.c_longlong),
+                                       ctypes.POINTER(ctypes.c_longlong)]),
         "rmgtd_gram_noalloc": (i, [vp, vp, vp, i, ctypes.c_longlong, d, vp, vp]),
         "rmgtd_profile_read": (i, [vp, _c_double_p, ctypes.POINTER(ctypes.c_longlong),
                                    ctypes.POINTER(ctypes.c_longlong)]),
@@ -308,6 +310,13 @@ class Context:
         n = ctypes.c_longlong()
         self._check(self._lib.rmgtd_profile_read(self._ctx, _dptr(ms), calls, ctypes.byref(n)))
         return (dict(zip(PHASES, ms.tolist())), dict(zip(PHASES, list(calls))), int(n.value))
+
+    def profile_counters(self):
+        """(Hartree replica solves, CG iterations summed over them) since profile()."""
+        ns = ctypes.c_longlong()
+        ni = ctypes.c_longlong()
+        self._check(self._lib.rmgtd_profile_counters(self._ctx, ctypes.byref(ns), ctypes.byref(ni)))
+        return int(ns.value), int(ni.value)
 
     def time(self):
         t = ctypes.c_double()
