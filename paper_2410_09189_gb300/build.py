@@ -39,7 +39,7 @@ def build(verbose: bool = False, force: bool = False, extra_flags=()) -> str:
     os.makedirs(LIBDIR, exist_ok=True)
     os.makedirs(OBJDIR, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
-    hdrs = glob.glob(os.path.join(CSRC, "*.cuh")) + [os.path.join(ROOT, "include", "rmgtd.h")]
+    hdrs = glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) + [os.path.join(ROOT, "include", "rmgtd.h")]
     hdr_time = _newest(hdrs)
     cc = nvcc()
 

@@ -24,6 +24,7 @@
 // same decisions and the result does not depend on timing.
 #include <math.h>
 
+#include "fastdiv.h"
 #include "rmgtd_internal.cuh"
 
 namespace rmgtd {
@@ -41,28 +42,6 @@ struct Grid3 {
   int nx, ny, nz;
   double h;
 };
-
-// Division of 0 <= x < 2^31 by a fixed d >= 1 with one multiply-high (Granlund & Montgomery,
-// "Division by invariant integers using multiplication", 1994): with l = ceil(log2 d) and
-// m = ceil(2^(31+l) / d), floor(x / d) = (x m) >> (31 + l) exactly, because
-// x m / 2^(31+l) - x / d < x / 2^(31+l) < 2^-l <= 1 / d.
-struct FastDiv {
-  unsigned long long m;
-  int s;
-  int d;
-};
-inline FastDiv make_fastdiv(int d) {
-  int l = 0;
-  while ((1ll << l) < d) ++l;
-  FastDiv f;
-  f.s = 31 + l;
-  f.m = ((1ull << f.s) + (unsigned long long)d - 1) / (unsigned long long)d;
-  f.d = d;
-  return f;
-}
-__host__ __device__ __forceinline__ int fdiv(int x, const FastDiv& f) {
-  return (int)(((unsigned long long)(unsigned)x * f.m) >> f.s);
-}
 
 constexpr int kMaxLevels = 12;
 // one multi-block level of the hierarchy, replicas stacked: [rep][n]
