@@ -215,17 +215,24 @@ def hartree_bytes(n, solves, iters, mixed):
     return float(iters) * per_it + float(solves) * (prologue - 4 * sv * lv[0])
 
 
+def kernel_source_sha(source, begin, end):
+    """sha256 of the kernel's source text: the lines from the first one starting with
+    `begin` to the first later one starting with `end` (inclusive) of csrc/`source`."""
+    import hashlib
+    lines = open(os.path.join(ROOT, "paper_2410_09189_gb300", "csrc", source)).read().splitlines()
+    i = next(k for k, l in enumerate(lines) if l.startswith(begin))
+    j = next(k for k in range(i + 1, len(lines)) if lines[k].startswith(end))
+    return hashlib.sha256("\n".join(lines[i:j + 1]).encode()).hexdigest()
+
+
 def _traffic(kernel, workload):
     """dram bytes per launch from the committed ncu summary, if it was taken on the current
-    source of the kernel (sha256 of its translation unit), else None."""
-    import hashlib
+    source of the kernel (sha256 of the kernel's source region), else None."""
     path = os.path.join(ROOT, "profiles", f"traffic_{kernel}_{workload}.txt")
     try:
         kv = dict(line.strip().split("=", 1) for line in open(path)
                   if "=" in line and not line.startswith("#"))
-        src = os.path.join(ROOT, "paper_2410_09189_gb300", "csrc", kv["source"])
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-        if sha != kv["sha256"]:
+        if kernel_source_sha(kv["source"], kv["begin"], kv["end"]) != kv["sha256"]:
             return None
         return float(kv["dram_bytes_per_launch"])
     except Exception:

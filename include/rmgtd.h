@@ -233,6 +233,82 @@ int rmgtd_profile_read(rmgtd_ctx* ctx, double* phase_ms, long long* phase_calls,
 int rmgtd_profile_counters(rmgtd_ctx* ctx, long long* hartree_solves,
                            long long* hartree_iterations);
 
+/* ---- Launch autotuning and batched systems -------------------------------------------------
+ * rmgtd_autotune times the launch alternatives of the mixed path's density (tensor-core CTAs
+ * per SM), Hamiltonian update (tensor-core or SIMT kernel x CTAs per SM) and the persistent
+ * Hartree solve (all SMs, 1/2 or 1/4 of them) on this context's shapes, on scratch outputs,
+ * and keeps the fastest; the state is not changed, but later results may differ at rounding
+ * level (other reduction orders).  choice (may be NULL) receives {density CTAs per SM, Gram
+ * on tensor cores (0/1), Gram CTAs per SM, Hartree block divisor}.  Synchronises. */
+int rmgtd_autotune(rmgtd_ctx* ctx, int choice[4]);
+
+/* Several contexts (different systems, each with its replicas) stepped by one CUDA graph per
+ * time step: their steps are captured back to back into a single graph, launched once per
+ * step on the contexts' common stream.  All contexts must use the same stream; attach the
+ * learned seed and autotune before creating the batch.  While in a batch a context refuses
+ * rmgtd_step, rmgtd_attach_net and rmgtd_autotune (RMGTD_ESTATE); other calls work.
+ * Errors: RMGTD_EINVAL (NULL, repeated or already-batched contexts, different streams). */
+typedef struct rmgtd_batch rmgtd_batch;
+int rmgtd_batch_create(rmgtd_ctx* const* ctxs, int n, rmgtd_batch** out);
+void rmgtd_batch_destroy(rmgtd_batch* batch);
+/* nsteps steps of every context; stats (may be NULL) holds one array per context, each of
+ * nsteps x nrep records (as rmgtd_step).  On a failed step the error names the context. */
+int rmgtd_batch_step(rmgtd_batch* batch, int nsteps, rmgtd_stats* const* stats);
+
+/* ---- Learned seed of the SCF loop (Algorithm 1 line 11) ------------------------------------
+ * The paper seeds each step's Hamiltonian SCF loop with H_1 = 2 H_0 - H_-1 = H[2 V_0 - V_-1].
+ * An attached network adds dV = s_out * y to that potential, y = net(x) with features
+ *   x[0] = rho_t / s_0,  x[1] = (rho_t - rho_{t-dt}) / s_1,  x[2] = (rho_t - 2 rho_{t-dt} + rho_{t-2dt}) / s_2,
+ * i.e. H_1 += h^3 Phi^T diag(dV) Phi before the first pass.  The SCF loop still decides
+ * convergence (H_thrs), so the converged step does not depend on the network; only the
+ * number of passes does.  Network: four 3x3x3 cross-correlations with zero padding,
+ * 3 -> 16 -> 16 -> 16 -> 1 channels, SiLU after the first three; bfloat16 weights, float32
+ * biases and accumulation.  Parameters (float32, RMGTD_NET_PARAMS of them): per layer W
+ * [cout][cin][kz][ky][kx] then b [cout].  Training target: (V_{t+dt} - 2 V_t + V_{t-dt}) / s_out
+ * (V = V_H + V_xc of converged steps); loss = mean squared error over the points at least 4
+ * from every face; Adam (beta1 0.9, beta2 0.999, eps 1e-8) on float32 master parameters.
+ * A network is not thread-safe; do not train one while an attached context steps. */
+typedef struct rmgtd_net rmgtd_net;
+#define RMGTD_NET_PARAMS 15601
+
+long long rmgtd_net_num_params(void);
+/* Network with workspace for batches of up to max_batch samples on an nx x ny x nz grid, its
+ * calls ordered on `stream` (cudaStream_t, NULL = legacy default).  Parameters start at 0
+ * (the paper's seed), scales at 1.  Errors: RMGTD_EINVAL, RMGTD_ENOMEM. */
+int rmgtd_net_create(int nx, int ny, int nz, int max_batch, void* stream, rmgtd_net** out);
+void rmgtd_net_destroy(rmgtd_net* net);
+/* Copy the float32 parameter vector in from / out to host memory; set resets Adam. */
+int rmgtd_net_set_params(rmgtd_net* net, const float* theta_host);
+int rmgtd_net_get_params(rmgtd_net* net, float* theta_host);
+/* Feature scales s_0..s_2 and output scale s_out (positive, finite). */
+int rmgtd_net_set_scales(rmgtd_net* net, const double in_scales[3], double out_scale);
+int rmgtd_net_get_scales(rmgtd_net* net, double in_scales[3], double* out_scale);
+/* One sample's features x_dev [3][Ng] (float32) from three float64 densities, and its target
+ * t_dev [Ng] from three float64 potentials V_{t+dt}, V_t, V_{t-dt} (all device pointers). */
+int rmgtd_net_features(rmgtd_net* net, const double* rho_t, const double* rho_tm1,
+                       const double* rho_tm2, float* x_dev);
+int rmgtd_net_targets(rmgtd_net* net, const double* v_tp1, const double* v_t, const double* v_tm1,
+                      float* t_dev);
+/* y_dev [batch][Ng] = net(x_dev [batch][3][Ng]) (device pointers); synchronises the stream. */
+int rmgtd_net_forward(rmgtd_net* net, const float* x_dev, float* y_dev, int batch);
+/* Loss and gradient at the current parameters for targets t_dev [batch][Ng]; the gradient
+ * stays on the device for rmgtd_net_adam and is copied to grad_host (RMGTD_NET_PARAMS
+ * floats) when that is not NULL.  The grid needs interior points (every side > 8). */
+int rmgtd_net_backward(rmgtd_net* net, const float* x_dev, const float* t_dev, int batch,
+                       double* loss, float* grad_host);
+/* One Adam step with learning rate lr from the last gradient. */
+int rmgtd_net_adam(rmgtd_net* net, double lr);
+/* Attach (net != NULL) or detach the learned seed; the network's grid must match the
+ * context's and its max_batch must be >= nrep.  The density history restarts (no history:
+ * rho_{t-dt} = rho_{t-2dt} = rho_t).  Errors: RMGTD_EINVAL. */
+int rmgtd_attach_net(rmgtd_ctx* ctx, rmgtd_net* net);
+
+/* Fields of replica `rep` of the current state copied to a device array of Ng doubles:
+ * which = 0 rho, 1 V_H + V_xc (of the last DFT evaluation). */
+#define RMGTD_FIELD_RHO 0
+#define RMGTD_FIELD_VHXC 1
+int rmgtd_get_field(rmgtd_ctx* ctx, int which, int rep, double* dev_out);
+
 /* Allocation-free Gram contraction  C = scale * A^T diag(w) B  (N x N, row-major) for two
  * orbital blocks A, B of n_orb columns of n_grid points each (orbital-major device arrays,
  * as in rmgtd_system.phi0), w (n_grid device doubles) or NULL for w = 1; c_dev receives

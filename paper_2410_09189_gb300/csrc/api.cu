@@ -242,6 +242,10 @@ int refresh_fields(rmgtd_ctx* ctx) {
                   ctx->mixed ? ctx->dv32 : nullptr, ctx->Ng, nullptr, ctx->nrep, ctx->Ng,
                   ctx->hartree_xc);
   if (rc) return rc;
+  if (ctx->net) {
+    rc = net_history_reset(ctx);
+    if (rc) return rc;
+  }
   return hartree_reset_history(ctx);
 }
 
@@ -363,6 +367,7 @@ static int create_impl(const rmgtd_system* sys, const rmgtd_options* opt, rmgtd_
   ctx->rho = (double*)A(gsz * nrep);
   ctx->vh = (double*)A(gsz * nrep);
   ctx->vh_prev = (double*)A(gsz * nrep);
+  ctx->vh_prev2 = (double*)A(gsz * nrep);
   ctx->vxc = (double*)A(gsz * nrep);
   ctx->exc = (double*)A(gsz * nrep);
   ctx->vhxc = (double*)A(gsz * nrep);
@@ -520,6 +525,7 @@ static int create_impl(const rmgtd_system* sys, const rmgtd_options* opt, rmgtd_
     ctx->dv32 = (float*)A(fsz * nrep);
     ctx->dvh32 = (float*)A(fsz * nrep);
     ctx->dvh_prev32 = (float*)A(fsz * nrep);
+    ctx->dvh_prev2_32 = (float*)A(fsz * nrep);
     {
       const long Np = ((N + 31) / 32) * 32;
       ctx->shat32 = (float*)A(sizeof(float) * Np * Np * nrep);
@@ -635,22 +641,18 @@ static int enqueue_pass(rmgtd_ctx* ctx, cudaGraphConditionalHandle cond, int use
 
 // Capture one whole time step as a graph: H_1 extrapolation, a device-side while loop of
 // SCF passes (each containing the Hartree CG while loop), then the shift.
-static int build_step_graph(rmgtd_ctx* ctx) {
+// Record one time step of `ctx` into the capture active on `main` (ctx->stream is switched
+// to it meanwhile): extrapolation [and the learned seed], a device-side while loop of SCF
+// passes whose body is captured on ctx->aux[0], the shift [and the density history].
+static int capture_step(rmgtd_ctx* ctx, cudaStream_t main) {
   for (int i = 0; i < 3; ++i)
     if (!ctx->aux[i]) RMGTD_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->aux[i], cudaStreamNonBlocking));
-  // capture on a library-owned stream (the caller's stream may be the legacy default
-  // stream, which cannot be captured); the graph is launched on the caller's stream
   cudaStream_t user = ctx->stream;
-  cudaStream_t main = ctx->aux[2];
   ctx->stream = main;
-  cudaError_t be = cudaStreamBeginCapture(main, cudaStreamCaptureModeRelaxed);
-  if (be != cudaSuccess) {
-    ctx->stream = user;
-    return cuda_check(ctx, be, "cudaStreamBeginCapture");
-  }
   ctx->capturing = 1;
   const long long saved_launches = ctx->launches;
   int rc = step_begin(ctx);
+  if (!rc && ctx->net) rc = net_predict(ctx);
   if (!rc) rc = hartree_extrapolate(ctx);
   cudaGraphConditionalHandle hs = 0;
   cudaGraph_t body = nullptr;
@@ -673,16 +675,26 @@ static int build_step_graph(rmgtd_ctx* ctx) {
     }
   }
   if (!rc) rc = step_end(ctx);
-  ctx->cap_top = ctx->hartree_xc ? 3 : 2;  // step_begin, [extrapolation], step_end
+  if (!rc && ctx->net) rc = net_history_shift(ctx);
+  // kernels of the top level: everything captured outside the SCF body
+  ctx->cap_top = (int)(ctx->launches - saved_launches) - ctx->cap_scf;
   ctx->launches = saved_launches;
   ctx->capturing = 0;
+  ctx->stream = user;
+  return rc;
+}
+
+// Capture one whole time step as a graph (on a library-owned stream: the caller's stream
+// may be the legacy default stream, which cannot be captured); launched on the caller's.
+static int build_step_graph(rmgtd_ctx* ctx) {
+  for (int i = 0; i < 3; ++i)
+    if (!ctx->aux[i]) RMGTD_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->aux[i], cudaStreamNonBlocking));
+  cudaStream_t main = ctx->aux[2];
+  RMGTD_CUDA(ctx, cudaStreamBeginCapture(main, cudaStreamCaptureModeRelaxed));
+  const int rc = capture_step(ctx, main);
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(main, &g);
-  ctx->stream = user;
-  if (rc) {
-    if (g) cudaGraphDestroy(g);
-    return rc;
-  }
+  if (rc) return rc;   // a part-way capture is not destroyed (see rmgtd_batch_create)
   RMGTD_CUDA(ctx, e);
   ctx->step_graph = g;
   RMGTD_CUDA(ctx, cudaGraphInstantiate(&ctx->step_exec, g, 0));
@@ -692,6 +704,7 @@ static int build_step_graph(rmgtd_ctx* ctx) {
 // Eager step: the host reads the control blocks after every pass.
 static int eager_step(rmgtd_ctx* ctx) {
   int rc = step_begin(ctx);
+  if (!rc && ctx->net) rc = net_predict(ctx);
   if (!rc) rc = hartree_extrapolate(ctx);
   if (rc) return rc;
   for (int pass = 0; pass < ctx->opt.max_scf; ++pass) {
@@ -706,14 +719,56 @@ static int eager_step(rmgtd_ctx* ctx) {
   }
   ph_begin(ctx, PH_OTHER);
   rc = step_end(ctx);
+  if (!rc && ctx->net) rc = net_history_shift(ctx);
   ph_end(ctx);
   return rc;
+}
+
+// After a chunk of `chunk` launched steps: copy the per-step statistics out (to
+// stats[done_total ..] when given), advance time and step count, report a failed step.
+static int finish_chunk(rmgtd_ctx* ctx, int chunk, int done_total, rmgtd_stats* stats, int* done_out) {
+  const int nrep = ctx->nrep;
+  int* hdr = (int*)&ctx->ctl_host[nrep];  // scratch: done, failed, status
+  RMGTD_CUDA(ctx, cudaMemcpyAsync(&hdr[0], ctx->done_steps, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  RMGTD_CUDA(ctx, cudaMemcpyAsync(&hdr[1], ctx->failed, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  RMGTD_CUDA(ctx, cudaMemcpyAsync(&hdr[2], ctx->status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->stats_host, ctx->stats_dev, sizeof(RepCtl) * chunk * nrep,
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+  RMGTD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  const int done = hdr[0], failed = hdr[1], gstatus = hdr[2];
+  const int recorded = std::min(chunk, done + (failed ? 1 : 0));
+  int worst = RMGTD_OK;
+  for (int k = 0; k < recorded; ++k) {
+    for (int r = 0; r < nrep; ++r) {
+      const RepCtl& c = ctx->stats_host[(long)k * nrep + r];
+      if (stats) {
+        rmgtd_stats& o = stats[(long)(done_total + k) * nrep + r];
+        o.passes = c.passes;
+        o.terms_max = c.terms_max;
+        o.terms_sum = c.terms_sum;
+        o.status = c.status;
+        o.H_err = c.H_err;
+      }
+      if (k == done && c.status != 0 && worst == RMGTD_OK) worst = c.status;
+    }
+  }
+  ctx->steps += done;
+  ctx->t += done * ctx->opt.dt;
+  *done_out = done;
+  if (failed) {
+    if (worst == RMGTD_OK) worst = gstatus ? gstatus : RMGTD_ENOTCONVERGED;
+    char buf[128];
+    snprintf(buf, sizeof(buf), "step %lld failed with status %d", ctx->steps + 1, worst);
+    ph_flush(ctx);
+    return set_error(ctx, worst, buf);
+  }
+  return RMGTD_OK;
 }
 
 int rmgtd_step(rmgtd_ctx* ctx, int nsteps, rmgtd_stats* stats) {
   if (!ctx) return set_error(nullptr, RMGTD_EINVAL, "ctx is NULL");
   if (nsteps < 0) return set_error(ctx, RMGTD_EINVAL, "nsteps < 0");
-  const int nrep = ctx->nrep;
+  if (ctx->in_batch) return set_error(ctx, RMGTD_ESTATE, "context belongs to a batch: step the batch");
   if (ctx->opt.use_graph && !ctx->step_exec) {
     int rc = build_step_graph(ctx);
     if (rc) return rc;
@@ -732,44 +787,238 @@ int rmgtd_step(rmgtd_ctx* ctx, int nsteps, rmgtd_stats* stats) {
         if (rc) return rc;
       }
     }
-    int* hdr = (int*)&ctx->ctl_host[nrep];  // scratch: done, failed, status
-    RMGTD_CUDA(ctx, cudaMemcpyAsync(&hdr[0], ctx->done_steps, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-    RMGTD_CUDA(ctx, cudaMemcpyAsync(&hdr[1], ctx->failed, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-    RMGTD_CUDA(ctx, cudaMemcpyAsync(&hdr[2], ctx->status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-    RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->stats_host, ctx->stats_dev, sizeof(RepCtl) * chunk * nrep,
-                                    cudaMemcpyDeviceToHost, ctx->stream));
-    RMGTD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    const int done = hdr[0], failed = hdr[1], gstatus = hdr[2];
-    const int recorded = std::min(chunk, done + (failed ? 1 : 0));
-    int worst = RMGTD_OK;
-    for (int k = 0; k < recorded; ++k) {
-      for (int r = 0; r < nrep; ++r) {
-        const RepCtl& c = ctx->stats_host[(long)k * nrep + r];
-        if (stats) {
-          rmgtd_stats& o = stats[(long)(done_total + k) * nrep + r];
-          o.passes = c.passes;
-          o.terms_max = c.terms_max;
-          o.terms_sum = c.terms_sum;
-          o.status = c.status;
-          o.H_err = c.H_err;
-        }
-        if (k == done && c.status != 0 && worst == RMGTD_OK) worst = c.status;
-      }
-    }
-    ctx->steps += done;
-    ctx->t += done * ctx->opt.dt;
+    int done = 0;
+    int rc = finish_chunk(ctx, chunk, done_total, stats, &done);
+    if (rc) return rc;
     done_total += done;
-    if (failed) {
-      if (worst == RMGTD_OK) worst = gstatus ? gstatus : RMGTD_ENOTCONVERGED;
-      char buf[128];
-      snprintf(buf, sizeof(buf), "step %lld failed with status %d", ctx->steps + 1, worst);
-      ph_flush(ctx);
-      return set_error(ctx, worst, buf);
-    }
   }
   RMGTD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   return ph_flush(ctx);
 }
+
+// ---- autotuner: time the launch alternatives on this context's shapes ----------------------
+// Each candidate runs on scratch outputs (state untouched): 2 warm-up and 5 timed calls with
+// CUDA events on the context's stream; the smallest median wins.  The Hartree candidates
+// solve from a zero initial guess into a scratch unknown.
+int rmgtd_autotune(rmgtd_ctx* ctx, int choice[4]) {
+  if (!ctx) return set_error(nullptr, RMGTD_EINVAL, "ctx is NULL");
+  if (ctx->in_batch) return set_error(ctx, RMGTD_ESTATE, "autotune: context belongs to a batch");
+  const int nrep = ctx->nrep;
+  const long Ng = ctx->Ng, NN = (long)ctx->N * ctx->N;
+  RMGTD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  double* rho_s = (double*)dev_alloc(ctx, sizeof(double) * Ng * nrep);
+  float* drho_s = (float*)dev_alloc(ctx, sizeof(float) * Ng * nrep);
+  double* gram_s = (double*)dev_alloc(ctx, sizeof(double) * NN * nrep);
+  void* x_s = dev_alloc(ctx, sizeof(double) * Ng * nrep);
+  if (!rho_s || !drho_s || !gram_s || !x_s) return set_error(ctx, RMGTD_ENOMEM, "autotune scratch");
+  cudaEvent_t e0, e1;
+  RMGTD_CUDA(ctx, cudaEventCreate(&e0));
+  RMGTD_CUDA(ctx, cudaEventCreate(&e1));
+  int rc = RMGTD_OK;
+  // median of 5 timed calls of `fn` (after 2 untimed); `prep` runs before each call, untimed
+  auto timed = [&](auto fn, auto prep, float* ms) -> int {
+    float t[5];
+    for (int it = 0; it < 7; ++it) {
+      int r = prep();
+      if (r) return r;
+      RMGTD_CUDA(ctx, cudaEventRecord(e0, ctx->stream));
+      r = fn();
+      if (r) return r;
+      RMGTD_CUDA(ctx, cudaEventRecord(e1, ctx->stream));
+      RMGTD_CUDA(ctx, cudaEventSynchronize(e1));
+      if (it >= 2) RMGTD_CUDA(ctx, cudaEventElapsedTime(&t[it - 2], e0, e1));
+    }
+    std::sort(t, t + 5);
+    *ms = t[2];
+    return RMGTD_OK;
+  };
+  auto none = [&]() { return RMGTD_OK; };
+  const int launches0 = (int)ctx->launches;
+  if (ctx->mixed) {
+    // density: CTAs per SM of the tensor-core kernel (also leaves valid Shat / drho inputs)
+    rc = rho_dev_mixed(ctx, ctx->S0, rho_s, nullptr, nrep);
+    const int keep_rho = ctx->tune_rho_blocks;
+    float best = 1e30f;
+    int best_b = keep_rho;
+    for (int b : {1, 2, 3, 4}) {
+      if (rc) break;
+      ctx->tune_rho_blocks = b;
+      float ms;
+      int r = timed([&]() { return rho_tc(ctx, rho_s, drho_s, nullptr, nrep); }, none, &ms);
+      if (r > 0) break;   // shape outside the tensor-core kernel
+      if (r < 0) {
+        rc = r;
+        break;
+      }
+      if (ms < best) best = ms, best_b = b;
+    }
+    ctx->tune_rho_blocks = best_b;
+    // Gram: kernel x CTAs per SM
+    best = 1e30f;
+    int best_tc = ctx->tune_gram_tc, best_gb = ctx->tune_gram_blocks;
+    for (int tcv : {0, 1})
+      for (int b : {1, 2, 4, 8}) {
+        if (rc) break;
+        ctx->tune_gram_tc = tcv;
+        ctx->tune_gram_blocks = b;
+        float ms;
+        rc = timed([&]() { return gram_mixed(ctx, ctx->dv32, Ng, nrep, ctx->h3, ctx->Href, gram_s,
+                                             nullptr, nullptr); }, none, &ms);
+        if (!rc && ms < best) best = ms, best_tc = tcv, best_gb = b;
+      }
+    ctx->tune_gram_tc = best_tc;
+    ctx->tune_gram_blocks = best_gb;
+  }
+  // Hartree: blocks of the persistent solve (SMs / div), from a zero guess
+  {
+    float best = 1e30f;
+    int best_d = ctx->tune_coop_div;
+    ctx->tune_x = x_s;
+    const size_t xb = (ctx->mixed ? sizeof(float) : sizeof(double)) * Ng * nrep;
+    for (int d : {1, 2, 4}) {
+      if (rc) break;
+      ctx->tune_coop_div = d;
+      float ms;
+      rc = timed([&]() { return hartree_coop(ctx, ctx->rho, ctx->vh, nullptr, 0, nrep, ctx->mixed); },
+                 [&]() {
+                   const cudaError_t me = cudaMemsetAsync(x_s, 0, xb, ctx->stream);
+                   return me == cudaSuccess ? (int)RMGTD_OK : cuda_check(ctx, me, "memset");
+                 },
+                 &ms);
+      if (!rc && ms < best) best = ms, best_d = d;
+    }
+    ctx->tune_x = nullptr;
+    ctx->tune_coop_div = best_d;
+  }
+  ctx->launches = launches0;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  // the candidates may have flagged their scratch solves; the state is untouched
+  RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream));
+  RMGTD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  dev_free(ctx, rho_s);
+  dev_free(ctx, drho_s);
+  dev_free(ctx, gram_s);
+  dev_free(ctx, x_s);
+  if (rc) return rc;
+  // launch configurations are baked into the step graph: rebuild it
+  if (ctx->step_exec) cudaGraphExecDestroy(ctx->step_exec);
+  if (ctx->step_graph) cudaGraphDestroy(ctx->step_graph);
+  ctx->step_exec = nullptr;
+  ctx->step_graph = nullptr;
+  if (choice) {
+    choice[0] = ctx->tune_rho_blocks;
+    choice[1] = ctx->tune_gram_tc;
+    choice[2] = ctx->tune_gram_blocks;
+    choice[3] = ctx->tune_coop_div;
+  }
+  return RMGTD_OK;
+}
+
+// ---- several systems in one graph per step (SURVEY a14's batched launch) --------------------
+struct rmgtd_batch {
+  std::vector<rmgtd_ctx*> ctxs;
+  cudaStream_t stream = nullptr;     // the contexts' common stream (launch stream)
+  cudaStream_t capture = nullptr;    // library-owned capture stream
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+int rmgtd_batch_create(rmgtd_ctx* const* ctxs, int n, rmgtd_batch** out) {
+  if (!out) return set_error(nullptr, RMGTD_EINVAL, "batch_create: out is NULL");
+  *out = nullptr;
+  if (!ctxs || n < 1) return set_error(nullptr, RMGTD_EINVAL, "batch_create: no contexts");
+  for (int i = 0; i < n; ++i) {
+    if (!ctxs[i]) return set_error(nullptr, RMGTD_EINVAL, "batch_create: NULL context");
+    if (ctxs[i]->in_batch) return set_error(nullptr, RMGTD_EINVAL, "batch_create: context already in a batch");
+    if (ctxs[i]->stream != ctxs[0]->stream)
+      return set_error(nullptr, RMGTD_EINVAL, "batch_create: contexts must share one stream");
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i]) return set_error(nullptr, RMGTD_EINVAL, "batch_create: context repeated");
+  }
+  rmgtd_batch* b = new rmgtd_batch();
+  b->ctxs.assign(ctxs, ctxs + n);
+  b->stream = ctxs[0]->stream;
+  auto fail = [&](int code, const std::string& msg) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->capture) cudaStreamDestroy(b->capture);
+    delete b;
+    return set_error(nullptr, code, msg);
+  };
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking) != cudaSuccess)
+    return fail(RMGTD_ECUDA, "batch_create: stream");
+  if (cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeRelaxed) != cudaSuccess)
+    return fail(RMGTD_ECUDA, "batch_create: begin capture");
+  int rc = RMGTD_OK;
+  int bad = -1;
+  for (int i = 0; i < n && !rc; ++i) {
+    rc = capture_step(b->ctxs[i], b->capture);
+    if (rc) bad = i;
+  }
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(b->capture, &g);
+  // a graph whose capture failed part-way (inside a conditional body) is left to the driver
+  // rather than destroyed: it is never instantiated or launched
+  if (rc) {
+    b->graph = nullptr;
+    return fail(rc, std::string("batch_create: context ") + std::to_string(bad) + ": " +
+                        b->ctxs[bad]->err);
+  }
+  b->graph = g;
+  if (e != cudaSuccess) return fail(RMGTD_ECUDA, std::string("batch_create: ") + cudaGetErrorString(e));
+  if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess)
+    return fail(RMGTD_ECUDA, "batch_create: graph instantiation");
+  for (auto* c : b->ctxs) c->in_batch = 1;
+  *out = b;
+  return RMGTD_OK;
+}
+
+void rmgtd_batch_destroy(rmgtd_batch* b) {
+  if (!b) return;
+  cudaStreamSynchronize(b->stream);
+  for (auto* c : b->ctxs) c->in_batch = 0;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->capture) cudaStreamDestroy(b->capture);
+  delete b;
+}
+
+int rmgtd_batch_step(rmgtd_batch* b, int nsteps, rmgtd_stats* const* stats) {
+  if (!b) return set_error(nullptr, RMGTD_EINVAL, "batch_step: NULL batch");
+  if (nsteps < 0) return set_error(nullptr, RMGTD_EINVAL, "batch_step: nsteps < 0");
+  int cap = b->ctxs[0]->stats_cap;
+  for (auto* c : b->ctxs) {
+    cap = std::min(cap, c->stats_cap);
+    RMGTD_CUDA(c, cudaMemsetAsync(c->failed, 0, sizeof(int), b->stream));
+  }
+  int done_total = 0;
+  while (done_total < nsteps) {
+    const int chunk = std::min(nsteps - done_total, cap);
+    for (auto* c : b->ctxs) RMGTD_CUDA(c, cudaMemsetAsync(c->done_steps, 0, sizeof(int), b->stream));
+    for (int i = 0; i < chunk; ++i) {
+      const cudaError_t e = cudaGraphLaunch(b->exec, b->stream);
+      if (e != cudaSuccess) return set_error(nullptr, RMGTD_ECUDA, cudaGetErrorString(e));
+    }
+    int done_min = chunk, first_err = RMGTD_OK;
+    for (size_t i = 0; i < b->ctxs.size(); ++i) {
+      rmgtd_ctx* c = b->ctxs[i];
+      c->graph_steps += chunk;
+      int done = 0;
+      const int rc = finish_chunk(c, chunk, done_total, stats ? stats[i] : nullptr, &done);
+      if (rc && first_err == RMGTD_OK) {
+        first_err = rc;
+        set_error(nullptr, rc, std::string("batch_step: context ") + std::to_string(i) + ": " + c->err);
+      }
+      done_min = std::min(done_min, done);
+    }
+    if (first_err) return first_err;
+    done_total += done_min;
+  }
+  return RMGTD_OK;
+}
+
 
 int rmgtd_profile(rmgtd_ctx* ctx, int enable) {
   if (!ctx) return set_error(nullptr, RMGTD_EINVAL, "ctx is NULL");
@@ -816,6 +1065,56 @@ int rmgtd_profile_counters(rmgtd_ctx* ctx, long long* hartree_solves,
   RMGTD_CUDA(ctx, cudaMemcpy(kx, ctx->kexec, sizeof(kx), cudaMemcpyDeviceToHost));
   if (hartree_solves) *hartree_solves = (long long)kx[2];
   if (hartree_iterations) *hartree_iterations = (long long)kx[3];
+  return RMGTD_OK;
+}
+
+int rmgtd_attach_net(rmgtd_ctx* ctx, rmgtd_net* net) {
+  if (!ctx) return set_error(nullptr, RMGTD_EINVAL, "ctx is NULL");
+  if (ctx->in_batch) return set_error(ctx, RMGTD_ESTATE, "attach_net: context belongs to a batch");
+  if (net) {
+    int nx, ny, nz;
+    net_grid_points(net, &nx, &ny, &nz);
+    if (nx != ctx->nx || ny != ctx->ny || nz != ctx->nz)
+      return set_error(ctx, RMGTD_EINVAL, "attach_net: network grid differs from the context's");
+    if (net_batch_cap(net) < ctx->nrep)
+      return set_error(ctx, RMGTD_EINVAL, "attach_net: network max_batch < nrep");
+    if (!ctx->rho_h1) {
+      const size_t g = sizeof(double) * ctx->Ng * ctx->nrep, f = sizeof(float) * ctx->Ng * ctx->nrep;
+      ctx->net_x = (float*)dev_alloc(ctx, 3 * f);
+      ctx->net_y = (float*)dev_alloc(ctx, f);
+      ctx->net_dv32 = (float*)dev_alloc(ctx, f);
+      ctx->net_dv64 = (double*)dev_alloc(ctx, g);
+      ctx->rho_h1 = (double*)dev_alloc(ctx, g);
+      ctx->rho_h2 = (double*)dev_alloc(ctx, g);
+      ctx->rho_start = (double*)dev_alloc(ctx, g);
+      if (!ctx->net_x || !ctx->net_y || !ctx->net_dv32 || !ctx->net_dv64 || !ctx->rho_h1 ||
+          !ctx->rho_h2 || !ctx->rho_start)
+        return set_error(ctx, RMGTD_ENOMEM, "attach_net: predictor buffers");
+    }
+  }
+  RMGTD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  ctx->net = net;
+  // the step graph changes with the predictor: rebuild it on the next step
+  if (ctx->step_exec) cudaGraphExecDestroy(ctx->step_exec);
+  if (ctx->step_graph) cudaGraphDestroy(ctx->step_graph);
+  ctx->step_exec = nullptr;
+  ctx->step_graph = nullptr;
+  if (net) {
+    int rc = net_history_reset(ctx);
+    if (rc) return rc;
+  }
+  RMGTD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return RMGTD_OK;
+}
+
+int rmgtd_get_field(rmgtd_ctx* ctx, int which, int rep, double* dev_out) {
+  if (!ctx) return set_error(nullptr, RMGTD_EINVAL, "ctx is NULL");
+  if (rep < 0 || rep >= ctx->nrep || !dev_out) return set_error(ctx, RMGTD_EINVAL, "get_field: bad arguments");
+  const double* src = which == RMGTD_FIELD_RHO ? ctx->rho : which == RMGTD_FIELD_VHXC ? ctx->vhxc : nullptr;
+  if (!src) return set_error(ctx, RMGTD_EINVAL, "get_field: unknown field");
+  RMGTD_CUDA(ctx, cudaMemcpyAsync(dev_out, src + (long)rep * ctx->Ng, sizeof(double) * ctx->Ng,
+                                  cudaMemcpyDeviceToDevice, ctx->stream));
+  RMGTD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   return RMGTD_OK;
 }
 
@@ -931,7 +1230,7 @@ int rmgtd_time(rmgtd_ctx* ctx, double* t, long long* steps) {
   return RMGTD_OK;
 }
 
-static const uint64_t kMagic = 0x31444d54474d52ull;  // "RMGTD1"
+static const uint64_t kMagic = 0x32444d54474d52ull;  // "RMGTD2"
 
 int rmgtd_save(rmgtd_ctx* ctx, const char* path) {
   if (!ctx) return set_error(nullptr, RMGTD_EINVAL, "ctx is NULL");
@@ -953,16 +1252,20 @@ int rmgtd_save(rmgtd_ctx* ctx, const char* path) {
             fwrite(&ctx->t, sizeof(double), 1, fp) == 1 &&
             fwrite(buf.data(), sizeof(double), buf.size(), fp) == buf.size();
   if (ok) {
-    std::vector<double> vp(gcount);
+    std::vector<double> vp(2 * gcount);
     RMGTD_CUDA(ctx, cudaMemcpy(vp.data(), ctx->vh_prev, sizeof(double) * gcount, cudaMemcpyDeviceToHost));
-    ok = fwrite(vp.data(), sizeof(double), gcount, fp) == gcount;
+    RMGTD_CUDA(ctx, cudaMemcpy(vp.data() + gcount, ctx->vh_prev2, sizeof(double) * gcount,
+                               cudaMemcpyDeviceToHost));
+    ok = fwrite(vp.data(), sizeof(double), 2 * gcount, fp) == 2 * gcount;
   }
   if (ok && ctx->mixed) {
-    std::vector<float> d32(2 * gcount);
+    std::vector<float> d32(3 * gcount);
     RMGTD_CUDA(ctx, cudaMemcpy(d32.data(), ctx->dvh32, sizeof(float) * gcount, cudaMemcpyDeviceToHost));
     RMGTD_CUDA(ctx, cudaMemcpy(d32.data() + gcount, ctx->dvh_prev32, sizeof(float) * gcount,
                                cudaMemcpyDeviceToHost));
-    ok = fwrite(d32.data(), sizeof(float), 2 * gcount, fp) == 2 * gcount;
+    RMGTD_CUDA(ctx, cudaMemcpy(d32.data() + 2 * gcount, ctx->dvh_prev2_32, sizeof(float) * gcount,
+                               cudaMemcpyDeviceToHost));
+    ok = fwrite(d32.data(), sizeof(float), 3 * gcount, fp) == 3 * gcount;
   }
   fclose(fp);
   if (!ok) return set_error(ctx, RMGTD_EINVAL, "save: write failed");
@@ -988,19 +1291,23 @@ int rmgtd_load(rmgtd_ctx* ctx, const char* path) {
   const size_t mcount = (size_t)NN * ctx->nrep, gcount = (size_t)ctx->Ng * ctx->nrep;
   std::vector<double> buf(4 * mcount + gcount);
   ok = fread(buf.data(), sizeof(double), buf.size(), fp) == buf.size();
-  std::vector<double> vp(gcount);
-  if (ok) ok = fread(vp.data(), sizeof(double), gcount, fp) == gcount;
+  std::vector<double> vp(2 * gcount);
+  if (ok) ok = fread(vp.data(), sizeof(double), 2 * gcount, fp) == 2 * gcount;
   std::vector<float> d32;
   if (ok && ctx->mixed) {
-    d32.resize(2 * gcount);
-    ok = fread(d32.data(), sizeof(float), 2 * gcount, fp) == 2 * gcount;
+    d32.resize(3 * gcount);
+    ok = fread(d32.data(), sizeof(float), 3 * gcount, fp) == 3 * gcount;
   }
   fclose(fp);
   if (!ok) return set_error(ctx, RMGTD_EINVAL, "load: truncated checkpoint");
   RMGTD_CUDA(ctx, cudaMemcpy(ctx->vh_prev, vp.data(), sizeof(double) * gcount, cudaMemcpyHostToDevice));
+  RMGTD_CUDA(ctx, cudaMemcpy(ctx->vh_prev2, vp.data() + gcount, sizeof(double) * gcount,
+                             cudaMemcpyHostToDevice));
   if (ctx->mixed) {
     RMGTD_CUDA(ctx, cudaMemcpy(ctx->dvh32, d32.data(), sizeof(float) * gcount, cudaMemcpyHostToDevice));
     RMGTD_CUDA(ctx, cudaMemcpy(ctx->dvh_prev32, d32.data() + gcount, sizeof(float) * gcount,
+                               cudaMemcpyHostToDevice));
+    RMGTD_CUDA(ctx, cudaMemcpy(ctx->dvh_prev2_32, d32.data() + 2 * gcount, sizeof(float) * gcount,
                                cudaMemcpyHostToDevice));
   }
   double* parts[4] = {ctx->S0, ctx->A0, ctx->H0, ctx->Hm1};

@@ -936,7 +936,7 @@ int hartree_coop(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* ct
     a.max_it = ctx->opt.poisson_max_iter;
     a.bar = ctx->bar2;
     a.status = ctx->status;
-    a.counters = ctx->kexec + 2;
+    a.counters = ctx->tune_x ? nullptr : ctx->kexec + 2;
   };
   const void* fn;
   void* args[1];
@@ -944,7 +944,7 @@ int hartree_coop(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* ct
   coop::Args<double> ad;
   if (f32) {
     fill(af);
-    af.x = ctx->dvh32;
+    af.x = ctx->tune_x ? (float*)ctx->tune_x : ctx->dvh32;
     af.b = ctx->pcg32_b;
     af.r = ctx->pcg32_r;
     af.z = ctx->pcg32_z;
@@ -956,7 +956,7 @@ int hartree_coop(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* ct
     args[0] = &af;
   } else {
     fill(ad);
-    ad.x = vh;
+    ad.x = ctx->tune_x ? (double*)ctx->tune_x : vh;
     ad.b = ctx->pcg_b;
     ad.r = ctx->pcg_r;
     ad.z = ctx->pcg_z;
@@ -968,9 +968,16 @@ int hartree_coop(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* ct
     args[0] = &ad;
   }
   const int k = f32 ? 1 : 0;
+  // the shared-memory limit is an attribute of the function, shared by every context of the
+  // process: only ever raise it (contexts of other grids may need more or less)
+  {
+    cudaFuncAttributes fa;
+    RMGTD_CUDA(ctx, cudaFuncGetAttributes(&fa, fn));
+    if ((size_t)fa.maxDynamicSharedSizeBytes < smem)
+      RMGTD_CUDA(ctx, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem));
+  }
   if (!ctx->coop_attr_set[k]) {
-    RMGTD_CUDA(ctx, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)std::max<size_t>(smem, 1)));
     int per_sm = 0;
     RMGTD_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, coop::kThreadsC, smem));
     if (per_sm < 1) return set_error(ctx, RMGTD_ECUDA, "persistent Hartree kernel does not fit on an SM");
@@ -979,7 +986,7 @@ int hartree_coop(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* ct
   }
   RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->bar2, 0, sizeof(unsigned), ctx->stream));
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(ctx->coop_grid[k]);
+  cfg.gridDim = dim3(std::max(1, ctx->coop_grid[k] / std::max(1, ctx->tune_coop_div)));
   cfg.blockDim = dim3(coop::kThreadsC);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = ctx->stream;
@@ -994,17 +1001,20 @@ int hartree_coop(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* ct
   return RMGTD_OK;
 }
 
-// Initial guess of the first Hartree solve of a step: linear extrapolation in time,
-// x <- 2 x(t) - x(t - dt), prev <- x(t).  Only the CG starting point changes.
+// Initial guess of the first Hartree solve of a step: quadratic extrapolation in time of
+// the last three solutions, x <- 3 x(t) - 3 x(t - dt) + x(t - 2 dt) (error O(dt^3) against
+// O(dt^2) for the linear 2 x(t) - x(t - dt)); p2 <- p1, p1 <- x(t).  Only the CG starting
+// point changes, not the solution it converges to.
 template <typename T>
-__global__ void k_extrap(long n, T* __restrict__ x, T* __restrict__ prev,
+__global__ void k_extrap(long n, T* __restrict__ x, T* __restrict__ p1, T* __restrict__ p2,
                          const int* __restrict__ failed) {
   if (*failed) return;
   for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n;
        e += (long)gridDim.x * blockDim.x) {
-    const T t = x[e];
-    x[e] = (T)2 * t - prev[e];
-    prev[e] = t;
+    const T t = x[e], a = p1[e];
+    x[e] = (T)3 * (t - a) + p2[e];
+    p2[e] = a;
+    p1[e] = t;
   }
 }
 
@@ -1013,22 +1023,26 @@ int hartree_extrapolate(rmgtd_ctx* ctx) {
   const long n = (long)ctx->nrep * ctx->Ng;
   const int bl = (int)std::max<long>(1, std::min<long>(ceil_div(n, kThreads), 65535L));
   if (ctx->mixed)
-    k_extrap<float><<<bl, kThreads, 0, ctx->stream>>>(n, ctx->dvh32, ctx->dvh_prev32, ctx->failed);
+    k_extrap<float><<<bl, kThreads, 0, ctx->stream>>>(n, ctx->dvh32, ctx->dvh_prev32,
+                                                      ctx->dvh_prev2_32, ctx->failed);
   else
-    k_extrap<double><<<bl, kThreads, 0, ctx->stream>>>(n, ctx->vh, ctx->vh_prev, ctx->failed);
+    k_extrap<double><<<bl, kThreads, 0, ctx->stream>>>(n, ctx->vh, ctx->vh_prev, ctx->vh_prev2,
+                                                       ctx->failed);
   ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_extrap");
   return RMGTD_OK;
 }
 
-// prev <- current (no history yet: the first extrapolation reproduces the current guess)
+// no history yet: p1 = p2 = current, so the first extrapolations reproduce the current guess
 int hartree_reset_history(rmgtd_ctx* ctx) {
   const long n = (long)ctx->nrep * ctx->Ng;
-  RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->vh_prev, ctx->vh, sizeof(double) * n,
-                                  cudaMemcpyDeviceToDevice, ctx->stream));
+  for (double* p : {ctx->vh_prev, ctx->vh_prev2})
+    RMGTD_CUDA(ctx, cudaMemcpyAsync(p, ctx->vh, sizeof(double) * n, cudaMemcpyDeviceToDevice,
+                                    ctx->stream));
   if (ctx->mixed)
-    RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->dvh_prev32, ctx->dvh32, sizeof(float) * n,
-                                    cudaMemcpyDeviceToDevice, ctx->stream));
+    for (float* p : {ctx->dvh_prev32, ctx->dvh_prev2_32})
+      RMGTD_CUDA(ctx, cudaMemcpyAsync(p, ctx->dvh32, sizeof(float) * n, cudaMemcpyDeviceToDevice,
+                                      ctx->stream));
   return RMGTD_OK;
 }
 

@@ -337,6 +337,9 @@ int rho_dev_mixed(rmgtd_ctx* ctx, const double* S, double* rho, const RepCtl* ct
   k_shat32<<<dim3(std::max(1, (int)std::min<long>(ceil_div(NpNp, 256), 1024)), nrep), 256, 0,
              ctx->stream>>>(N, Np, S, ctx->Sref, (long)N * N, ctx->shat32, ctl);
   ++ctx->launches;
+  RMGTD_LAUNCH(ctx, "k_shat32");
+  const int rc = rho_tc(ctx, rho, ctx->drho32, ctl, nrep);   // tensor cores when N <= 32
+  if (rc <= 0) return rc;
   dim3 grid(ceil_div(ctx->Ng, kRhoThreads * kRho32Pts), nrep);
   k_rho32<<<grid, kRhoThreads, 0, ctx->stream>>>(N, Np, ctx->Ng, ctx->phi32, ctx->shat32,
                                                   ctx->rho_ref, rho, ctx->drho32, ctx->Ng, ctl);
@@ -546,19 +549,27 @@ int gram_mixed(rmgtd_ctx* ctx, const float* w, long wstride, int nw, double scal
   const int npairs = T * (T + 1) / 2;
   if (wstride != ctx->Ng) return set_error(ctx, RMGTD_EINVAL, "gram_mixed: replica stride must be Ng");
   const int ngroups = ceil_div(nw, 2);   // replica groups of off-diagonal pairs (diagonal: 3)
-  // about two blocks per SM over the (pair, replica-group) units, bounded by the partials
-  long ns = ceil_div(2L * ctx->num_sms, (long)npairs * ceil_div(nw, 3));
+  // tune_gram_blocks CTAs per SM over the (pair, replica-group) units: groups of 4 replicas
+  // on the tensor cores, of 3 (diagonal pairs) in the SIMT kernel; bounded by the partials
+  const bool tc = ctx->tune_gram_tc != 0;
+  long ns = ceil_div((long)std::max(1, ctx->tune_gram_blocks) * ctx->num_sms,
+                     (long)npairs * ceil_div(nw, tc ? 4 : 3));
   ns = std::max<long>(1, std::min<long>(ns, ceil_div(ctx->Ng, (long)kG32Slab)));
   const long per = (long)nw * Np * Np;   // floats per split
   ns = std::min<long>(ns, (long)(2 * ctx->gram_part_elems) / std::max<long>(per, 1));
   if (ns < 1) return set_error(ctx, RMGTD_ENOMEM, "gram_mixed: partial buffer too small");
-  const int nsplit = (int)ns;
-  const int chunk = (int)(ceil_div(ceil_div(ctx->Ng, (long)nsplit), (long)kG32Slab) * kG32Slab);
+  int nsplit = (int)ns;
+  int chunk = (int)(ceil_div(ceil_div(ctx->Ng, (long)nsplit), (long)kG32Slab) * kG32Slab);
+  nsplit = (int)ceil_div(ctx->Ng, (long)chunk);   // no empty splits
   float* part = reinterpret_cast<float*>(ctx->gram_part);
-  k_gram32<<<dim3(nsplit, npairs, ngroups), kG32Threads, 0, ctx->stream>>>(
-      N, Np, (int)ctx->Ng, ctx->phi32, w, nw, T, chunk, part, ctl);
-  ++ctx->launches;
-  RMGTD_LAUNCH(ctx, "k_gram32");
+  const int rc = tc ? gram_tc(ctx, w, nw, part, nsplit, chunk, ctl) : 1;
+  if (rc < 0) return rc;
+  if (rc > 0) {
+    k_gram32<<<dim3(nsplit, npairs, ngroups), kG32Threads, 0, ctx->stream>>>(
+        N, Np, (int)ctx->Ng, ctx->phi32, w, nw, T, chunk, part, ctl);
+    ++ctx->launches;
+    RMGTD_LAUNCH(ctx, "k_gram32");
+  }
   k_gram32_reduce<<<dim3(ceil_div((long)Np * Np, 32L), nw), 256, 0, ctx->stream>>>(
       N, Np, nsplit, nw, part, scale, base, out, out, errbits, ctl);
   ++ctx->launches;
@@ -612,11 +623,12 @@ struct EldynArgs {
   int* status;
 };
 
-template <int TS>
-__global__ void __launch_bounds__(256) k_eldyn(EldynArgs a) {
+template <int TS, int NT>
+__global__ void __launch_bounds__(NT) k_eldyn(EldynArgs a) {
   constexpr int KC = 32;
   constexpr int TSP = TS + 1;
-  constexpr int OPT = (4 * TS * TS) / 256;
+  constexpr int OPT = (4 * TS * TS) / NT;
+  static_assert(OPT >= 1 && OPT * NT == 4 * TS * TS, "threads must divide the 4 output tiles");
   extern __shared__ double smem[];
   double* Hi = smem;                 // [TS][KC+1]
   double* Hj = Hi + TS * (KC + 1);
@@ -649,7 +661,7 @@ __global__ void __launch_bounds__(256) k_eldyn(EldynArgs a) {
     if (conv[rep]) continue;
     int I, J;
     pair_from_index(item % npairs, T, 1, I, J);
-    for (int e = tid; e < TS * TS; e += 256) {
+    for (int e = tid; e < TS * TS; e += NT) {
       const int i = I * TS + e / TS, j = J * TS + e % TS;
       if (i < N && j < N) {
         const long o = rep * NN + (long)i * N + j, ot = rep * NN + (long)j * N + i;
@@ -682,7 +694,7 @@ __global__ void __launch_bounds__(256) k_eldyn(EldynArgs a) {
 #pragma unroll
       for (int u = 0; u < OPT; ++u) acc[u] = 0.0;
       for (int k0 = 0; k0 < N; k0 += KC) {
-        for (int e = tid; e < TS * KC; e += 256) {
+        for (int e = tid; e < TS * KC; e += NT) {
           const int r = e / KC, kk = e % KC;
           const int kg = k0 + kk;
           const int ri = I * TS + r, rj = J * TS + r;
@@ -694,7 +706,7 @@ __global__ void __launch_bounds__(256) k_eldyn(EldynArgs a) {
           Hi[r * (KC + 1) + kk] = hi;
           Hj[r * (KC + 1) + kk] = hj;
         }
-        for (int e = tid; e < KC * TS; e += 256) {
+        for (int e = tid; e < KC * TS; e += NT) {
           const int kk = e / TS, b = e % TS;
           const int kg = k0 + kk;
           const int ci = I * TS + b, cj = J * TS + b;
@@ -717,7 +729,7 @@ __global__ void __launch_bounds__(256) k_eldyn(EldynArgs a) {
         __syncthreads();
 #pragma unroll
         for (int u = 0; u < OPT; ++u) {
-          const int o = tid + 256 * u;
+          const int o = tid + NT * u;
           const int q = o / (TS * TS), e = o % (TS * TS);
           const int ra = e / TS, cb = e % TS;
           const double* Hx = (q == 0 || q == 2) ? Hi : Hj;
@@ -731,13 +743,13 @@ __global__ void __launch_bounds__(256) k_eldyn(EldynArgs a) {
       }
 #pragma unroll
       for (int u = 0; u < OPT; ++u) {
-        const int o = tid + 256 * u;
+        const int o = tid + NT * u;
         const int q = o / (TS * TS), e = o % (TS * TS);
         Tt[q * TS * TSP + (e / TS) * TSP + (e % TS)] = acc[u];
       }
       __syncthreads();
       double emax = 0.0;
-      for (int e = tid; e < TS * TS; e += 256) {
+      for (int e = tid; e < TS * TS; e += NT) {
         const int ra = e / TS, cb = e % TS;
         const int i = I * TS + ra, j = J * TS + cb;
         if (i >= N || j >= N) continue;
@@ -759,7 +771,7 @@ __global__ void __launch_bounds__(256) k_eldyn(EldynArgs a) {
           a.S1[rep * NN + ot] += ns;
           a.A1[rep * NN + ot] -= na;
         }
-        emax = fmax(emax, sqrt(ns * ns + na * na));
+        emax = fmax(emax, ns * ns + na * na);   // |dP_ij|^2
       }
       emax = block_max(emax, sh);
       if (tid == 0) atomic_max_nonneg(&a.slots[(long)rep * (a.max_terms + 1) + k], emax);
@@ -771,13 +783,13 @@ __global__ void __launch_bounds__(256) k_eldyn(EldynArgs a) {
       for (int r = 0; r < a.nrep; ++r) {
         if (conv[r]) continue;
         const unsigned long long bits = *((volatile unsigned long long*)&a.slots[(long)r * (a.max_terms + 1) + k]);
-        const double err = __longlong_as_double((long long)bits);
+        const double err = __longlong_as_double((long long)bits);   // max |dP_ij|^2
         bool finished = false;
         if (!(err <= 1e300)) {  // NaN or inf
           if (blockIdx.x == 0) atomicCAS(a.status, 0, (int)RMGTD_EDIVERGED);
           if (blockIdx.x == 0 && a.ctl_out) a.ctl_out[a.rep0 + r].status = RMGTD_EDIVERGED;
           finished = true;
-        } else if (err <= a.thrs) {
+        } else if (err <= a.thrs * a.thrs) {
           finished = true;
         } else if (k >= a.max_terms) {
           if (blockIdx.x == 0) atomicCAS(a.status, 0, (int)RMGTD_ENOTCONVERGED);
@@ -803,18 +815,18 @@ __global__ void __launch_bounds__(256) k_eldyn(EldynArgs a) {
   }
 }
 
-template <int TS>
+template <int TS, int NT>
 static int launch_eldyn_ts(rmgtd_ctx* ctx, EldynArgs& a) {
   const int KC = 32;
   const size_t smem = sizeof(double) * (2 * TS * (KC + 1) + 4 * KC * (TS + 1) + 4 * TS * (TS + 1));
   static bool attr_set = false;
   if (!attr_set) {
-    RMGTD_CUDA(ctx, cudaFuncSetAttribute(k_eldyn<TS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    RMGTD_CUDA(ctx, cudaFuncSetAttribute(k_eldyn<TS, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem));
     attr_set = true;
   }
   int per_sm = 0;
-  RMGTD_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_eldyn<TS>, 256, smem));
+  RMGTD_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_eldyn<TS, NT>, NT, smem));
   if (per_sm < 1) return set_error(ctx, RMGTD_ECUDA, "commutator kernel does not fit on an SM");
   const int T = (a.N + TS - 1) / TS;
   const int total = T * (T + 1) / 2 * a.nrep;
@@ -826,7 +838,7 @@ static int launch_eldyn_ts(rmgtd_ctx* ctx, EldynArgs& a) {
   void* args[] = {&a};
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(256);
+  cfg.blockDim = dim3(NT);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = ctx->stream;
   cudaLaunchAttribute attr[1];
@@ -834,7 +846,7 @@ static int launch_eldyn_ts(rmgtd_ctx* ctx, EldynArgs& a) {
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  RMGTD_CUDA(ctx, cudaLaunchKernelExC(&cfg, (const void*)k_eldyn<TS>, args));
+  RMGTD_CUDA(ctx, cudaLaunchKernelExC(&cfg, (const void*)k_eldyn<TS, NT>, args));
   ++ctx->launches;
   return RMGTD_OK;
 }
@@ -863,9 +875,11 @@ int eldyn(rmgtd_ctx* ctx, const double* Ha, const double* Hb, long hstride, doub
   a.thrs = ctx->opt.dP_thrs;
   a.bar = ctx->bar;
   a.status = ctx->status;
-  if (ctx->N <= 64) return launch_eldyn_ts<8>(ctx, a);
-  if (ctx->N <= 512) return launch_eldyn_ts<16>(ctx, a);
-  return launch_eldyn_ts<32>(ctx, a);
+  // small tiles for small N: the float64 work of a term spreads over more SMs
+  if (ctx->N <= 32) return launch_eldyn_ts<4, 64>(ctx, a);
+  if (ctx->N <= 64) return launch_eldyn_ts<8, 256>(ctx, a);
+  if (ctx->N <= 512) return launch_eldyn_ts<16, 256>(ctx, a);
+  return launch_eldyn_ts<32, 256>(ctx, a);
 }
 
 // ---------------------------------------------------------------------------------------

@@ -1,0 +1,455 @@
+// Tensor-core (tcgen05) kernels of the mixed path.
+//
+// Density change (Algorithm 1 line 26's rho(P_1), Section 3.1's rho = sum_ij Re P_ij phi_i phi_j)
+// as a GEMM on the 5th-generation tensor cores:
+//   Y_r(g, j) = sum_k phi_k(g) Shat_r[k][j]        (M = 128 grid points, N = 32 nrep, K = 32)
+//   drho_r(g) = sum_j phi_j(g) Y_r(g, j)            (epilogue, one thread per grid point)
+// with Shat_r the float32 upper-triangular change matrix (2 (S - S_ref)_kj for k < j,
+// (S - S_ref)_jj on the diagonal).  Operands are float32 split as x = hi + lo with hi = x
+// rounded down to tf32 (low 13 mantissa bits cleared) and lo = x - hi (exact); the three
+// products hi*hi + hi*lo + lo*hi accumulate in float32 in tensor memory (kind::tf32), which
+// keeps about 2^-20 relative accuracy (the dropped lo*lo term and the tf32 truncation of lo).
+//
+// Shared-memory operands use the canonical K-major layout without swizzle: core matrices
+// of 8 rows x 16 bytes (4 floats), the K-adjacent core matrix at +128 bytes (leading byte
+// offset), the next group of 8 rows at +K/4 * 128 bytes (stride byte offset).  One CTA
+// (128 threads) allocates nrep*32 (rounded up to a power of two) TMEM columns, stages the
+// Shat operand once, and loops over 128-point tiles: stage the orbital tile (transposed
+// to point-major), one thread issues 4 K-steps x 3 products, commits to an mbarrier, all
+// threads wait (bounded), each warp reads its 32 TMEM lanes and forms drho for its points.
+#include <stdint.h>
+
+#include "rmgtd_internal.cuh"
+
+namespace rmgtd {
+namespace tc {
+
+constexpr int kM = 128;          // grid points per tile = TMEM lanes
+constexpr int kK = 32;           // orbitals per tile (N <= 32)
+constexpr int kThreadsTc = 128;
+constexpr int kMaxRepTc = 8;     // N = 32 * nrep <= 256
+constexpr uint32_t kSBO = (kK / 4) * 128;             // 1024 B between 8-row groups
+constexpr uint32_t kLBO = 128;                        // K-adjacent core matrices
+
+__device__ __forceinline__ uint32_t saddr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// float index of element (row, k) in a K-major no-swizzle tile with K = kK
+__device__ __forceinline__ int kmaj(int row, int k) {
+  return (row >> 3) * (kSBO / 4) + (k >> 2) * (kLBO / 4) + (row & 7) * 4 + (k & 3);
+}
+
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((kLBO >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((kSBO >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// kind::tf32, D float32, A and B tf32, both K-major, M x N
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
+  hi = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
+  lo = x - hi;
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          saddr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase) {
+  for (uint32_t i = 0; i < kSpinLimit; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(saddr(bar)), "r"(phase)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// 32 consecutive TMEM columns of this warp's 32 lanes
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// dynamic shared memory: a_hi, a_lo (128 x 32 floats each), b_hi, b_lo (nr * 32 rows x kK)
+__global__ void __launch_bounds__(kThreadsTc)
+k_rho_tc(int N, int Np, int Ng, int nr, const float* __restrict__ phi,
+         const float* __restrict__ shat, const double* __restrict__ rho_ref,
+         double* __restrict__ rho, float* __restrict__ drho, const RepCtl* __restrict__ ctl,
+         int* status) {
+  extern __shared__ __align__(128) float sm[];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t tmem_base;
+  float* a_hi = sm;
+  float* a_lo = sm + kM * kK;
+  float* b_hi = sm + 2 * kM * kK;
+  float* b_lo = b_hi + nr * 32 * kK;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int ncols_used = nr * 32;
+  uint32_t ncols = 32;
+  while (ncols < (uint32_t)ncols_used) ncols <<= 1;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     saddr(&tmem_base)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // B operand: row n = r * 32 + j, column k: Shat_r[k][j] (zero beyond N)
+  for (int e = tid; e < ncols_used * kK; e += blockDim.x) {
+    const int n = e / kK, k = e % kK;
+    const int r = n >> 5, j = n & 31;
+    float v = 0.0f;
+    if (j < N && k < N) v = shat[((long)r * Np + k) * Np + j];
+    float hi, lo;
+    split_tf32(v, hi, lo);
+    b_hi[kmaj(n, k)] = hi;
+    b_lo[kmaj(n, k)] = lo;
+  }
+  fence_async_smem();
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tbase = tmem_base;
+  const uint32_t idesc = idesc_tf32(kM, ncols_used);
+  const int ntiles = (Ng + kM - 1) / kM;
+  uint32_t phase = 0;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int g0 = t * kM;
+    // stage the orbital tile: thread <-> point, rows of 4 orbitals as 16-byte stores
+    {
+      const int p = tid;
+      const int g = g0 + p;
+#pragma unroll
+      for (int kc = 0; kc < kK; kc += 4) {
+        float4 h4, l4;
+        float* hp = &h4.x;
+        float* lp = &l4.x;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int k = kc + c;
+          const float v = (k < N && g < Ng) ? phi[(long)k * Ng + g] : 0.0f;
+          split_tf32(v, hp[c], lp[c]);
+        }
+        *reinterpret_cast<float4*>(&a_hi[kmaj(p, kc)]) = h4;
+        *reinterpret_cast<float4*>(&a_lo[kmaj(p, kc)]) = l4;
+      }
+    }
+    fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      fence_after();
+      const uint32_t ah = saddr(a_hi), al = saddr(a_lo), bh = saddr(b_hi), bl = saddr(b_lo);
+#pragma unroll
+      for (int s = 0; s < kK / 8; ++s) {
+        const uint32_t off = s * 2 * kLBO;   // two core matrices (8 tf32) per K-step
+        mma_tf32(tbase, sdesc(ah + off), sdesc(bh + off), idesc, s > 0 ? 1u : 0u);
+        mma_tf32(tbase, sdesc(ah + off), sdesc(bl + off), idesc, 1u);
+        mma_tf32(tbase, sdesc(al + off), sdesc(bh + off), idesc, 1u);
+      }
+      mma_commit(&bar);
+    }
+    const bool ok = mbar_wait(&bar, phase);
+    phase ^= 1u;
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) atomicCAS(status, 0, (int)RMGTD_ETIMEOUT);
+      break;
+    }
+    fence_after();
+    // epilogue: warp w owns TMEM lanes 32w .. 32w + 31 = points g0 + 32w + lane
+    const int p = warp * 32 + lane;
+    const int g = g0 + p;
+    float ph[32];
+#pragma unroll
+    for (int kc = 0; kc < kK; kc += 4) {
+      const float4 h4 = *reinterpret_cast<const float4*>(&a_hi[kmaj(p, kc)]);
+      const float4 l4 = *reinterpret_cast<const float4*>(&a_lo[kmaj(p, kc)]);
+      ph[kc] = h4.x + l4.x;
+      ph[kc + 1] = h4.y + l4.y;
+      ph[kc + 2] = h4.z + l4.z;
+      ph[kc + 3] = h4.w + l4.w;
+    }
+    for (int r = 0; r < nr; ++r) {
+      float y[32];
+      tmem_ld32(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)(r * 32), y);
+      float acc = 0.0f;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) acc = fmaf(ph[j], y[j], acc);
+      if (g < Ng && (!ctl || ctl[r].active)) {
+        rho[(long)r * Ng + g] = rho_ref[g] + (double)acc;
+        drho[(long)r * Ng + g] = acc;
+      }
+    }
+    fence_before();
+    __syncthreads();
+  }
+  __syncthreads();
+  if (warp == 0) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(ncols)
+                 : "memory");
+  }
+}
+
+}  // namespace tc
+
+// Density of the mixed path on the tensor cores (N <= 32, nrep <= 8); returns 1 when the
+// shape is outside that range (the caller then uses the float32 SIMT kernel).
+int rho_tc(rmgtd_ctx* ctx, double* rho, float* drho, const RepCtl* ctl, int nrep) {
+  using namespace tc;
+  const int N = ctx->N, Np = ((N + 31) / 32) * 32;
+  if (Np != kK || nrep > kMaxRepTc || ctx->Ng >= (1l << 31)) return 1;
+  const size_t smem = (size_t)(2 * kM * kK + 2 * nrep * 32 * kK) * sizeof(float);
+  if (!ctx->rho_tc_attr) {
+    RMGTD_CUDA(ctx, cudaFuncSetAttribute(k_rho_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(2 * kM * kK + 2 * kMaxRepTc * 32 * kK) * 4));
+    ctx->rho_tc_attr = 1;
+  }
+  const int ntiles = (int)((ctx->Ng + kM - 1) / kM);
+  const int grid = std::min(ntiles, std::max(1, ctx->tune_rho_blocks) * ctx->num_sms);
+  k_rho_tc<<<grid, kThreadsTc, smem, ctx->stream>>>(N, Np, (int)ctx->Ng, nrep, ctx->phi32,
+                                                     ctx->shat32, ctx->rho_ref, rho, drho, ctl,
+                                                     ctx->status);
+  ++ctx->launches;
+  RMGTD_LAUNCH(ctx, "k_rho_tc");
+  return RMGTD_OK;
+}
+
+// ---- Hamiltonian update of the mixed path on the tensor cores ------------------------------
+// C_r[i][j] = sum_g phi_i(g) w_r(g) phi_j(g) for the 32 x 32 tile pair (It, Jt), It <= Jt,
+// of up to four replicas r (Section 3.1's H = H_ref + h^3 Phi^T diag(dV) Phi):
+//   D[(r, i)][j] += sum_k A[(r, i)][k] B[j][k],  A = phi_i w_r (M = 32 nr <= 128 rows),
+//   B = phi_j (N = 32), K = grid points in slabs of 32.
+// Each CTA (256 threads, 40 KB of shared memory, so several CTAs share an SM and hide each
+// other's load latency) reduces a contiguous range of grid points in tensor memory: stage a
+// slab (float32 split hi + lo as for the density), one thread issues 4 K-steps x 3 products
+// and commits, all wait for the MMAs before the slab buffer is restaged.  The float32
+// partial tile goes to part[split][rep][Np][Np] for the float64 reduction of the SIMT path.
+namespace tc {
+
+constexpr int kGKS = 32;                       // grid points per slab (K)
+constexpr int kGRows = 128;                    // A rows (TMEM lanes)
+constexpr int kGAfl = kGRows * kGKS;           // floats per A operand
+constexpr int kGBfl = 32 * kGKS;               // floats per B operand
+constexpr int kThreadsG = 256;
+
+__global__ void __launch_bounds__(kThreadsG)
+k_gram_tc(int N, int Np, int Ng, const float* __restrict__ phi, const float* __restrict__ w,
+          int nrep, int T, int chunk, float* __restrict__ part, const RepCtl* __restrict__ ctl,
+          int* status) {
+  extern __shared__ __align__(128) float sm[];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t tmem_base;
+  float* ah = sm;
+  float* al = sm + kGAfl;
+  float* bh = sm + 2 * kGAfl;
+  float* bl = sm + 2 * kGAfl + kGBfl;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  int It, Jt;
+  {
+    int i = 0, rem = blockIdx.y;
+    while (rem >= T - i) {
+      rem -= T - i;
+      ++i;
+    }
+    It = i;
+    Jt = i + rem;
+  }
+  const int rep0 = blockIdx.z * 4;
+  const int nr = min(4, nrep - rep0);
+  const int split = blockIdx.x;
+  const int g_beg = split * chunk;
+  const int g_end = min(Ng, g_beg + chunk);
+  const uint32_t ncols = 32;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     saddr(&tmem_base)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // rows of A beyond 32 nr stay zero
+  for (int e = tid; e < 2 * kGAfl + 2 * kGBfl; e += blockDim.x) sm[e] = 0.0f;
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tbase = tmem_base;
+  const uint32_t idesc = idesc_tf32(kGRows, 32);
+  const int nslab = (g_end > g_beg) ? (g_end - g_beg + kGKS - 1) / kGKS : 0;
+  uint32_t phase = 0;
+  bool ok = true;
+  // staging map: warp w stages orbital rows 4 w + (lane >> 3), lane & 7 picks 4 points
+  const int q = lane & 7;
+  const int i = 4 * warp + (lane >> 3);   // 0 .. 31
+  for (int s = 0; s < nslab; ++s) {
+    const int g = g_beg + s * kGKS + 4 * q;
+    float wv[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        wv[r][c] = (r < nr && g + c < g_end) ? w[(long)(rep0 + r) * Ng + g + c] : 0.0f;
+    float va[4], vb[4];
+    {
+      const int ra = It * 32 + i, rb = Jt * 32 + i;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const bool in = g + c < g_end;
+        va[c] = (ra < N && in) ? phi[(long)ra * Ng + g + c] : 0.0f;
+        vb[c] = (rb < N && in) ? phi[(long)rb * Ng + g + c] : 0.0f;
+      }
+    }
+    if (s > 0) {   // the MMAs of slab s - 1 read the buffers
+      ok = mbar_wait(&bar, phase);
+      phase ^= 1u;
+      if (__syncthreads_or(!ok)) break;
+      fence_after();
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      if (r >= nr) break;
+      float4 h4, l4;
+      split_tf32(va[0] * wv[r][0], h4.x, l4.x);
+      split_tf32(va[1] * wv[r][1], h4.y, l4.y);
+      split_tf32(va[2] * wv[r][2], h4.z, l4.z);
+      split_tf32(va[3] * wv[r][3], h4.w, l4.w);
+      *reinterpret_cast<float4*>(&ah[kmaj(r * 32 + i, 4 * q)]) = h4;
+      *reinterpret_cast<float4*>(&al[kmaj(r * 32 + i, 4 * q)]) = l4;
+    }
+    {
+      float4 h4, l4;
+      split_tf32(vb[0], h4.x, l4.x);
+      split_tf32(vb[1], h4.y, l4.y);
+      split_tf32(vb[2], h4.z, l4.z);
+      split_tf32(vb[3], h4.w, l4.w);
+      *reinterpret_cast<float4*>(&bh[kmaj(i, 4 * q)]) = h4;
+      *reinterpret_cast<float4*>(&bl[kmaj(i, 4 * q)]) = l4;
+    }
+    fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      fence_after();
+      const uint32_t sah = saddr(ah), sal = saddr(al), sbh = saddr(bh), sbl = saddr(bl);
+#pragma unroll
+      for (int k = 0; k < kGKS / 8; ++k) {
+        const uint32_t off = k * 2 * kLBO;
+        mma_tf32(tbase, sdesc(sah + off), sdesc(sbh + off), idesc, (s > 0 || k > 0) ? 1u : 0u);
+        mma_tf32(tbase, sdesc(sah + off), sdesc(sbl + off), idesc, 1u);
+        mma_tf32(tbase, sdesc(sal + off), sdesc(sbh + off), idesc, 1u);
+      }
+      mma_commit(&bar);
+    }
+  }
+  if (ok && nslab > 0) {   // the last slab's MMAs
+    ok = mbar_wait(&bar, phase);
+    phase ^= 1u;
+    ok = !__syncthreads_or(!ok);
+  }
+  if (!ok && tid == 0) atomicCAS(status, 0, (int)RMGTD_ETIMEOUT);
+  fence_after();
+  // epilogue: TMEM lane m = 32 warp + lane is A row (r = warp, i = lane)
+  if (ok && warp < nr) {
+    float y[32];
+    if (nslab > 0) {
+      tmem_ld32(tbase + ((uint32_t)(warp * 32) << 16), y);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) y[j] = 0.0f;
+    }
+    const int r = rep0 + warp;
+    const bool on = !ctl || ctl[r].active;
+    const long NpNp = (long)Np * Np;
+    float* out = part + ((long)split * nrep + r) * NpNp + (long)(It * 32 + lane) * Np + Jt * 32;
+#pragma unroll
+    for (int j = 0; j < 32; j += 4)
+      *reinterpret_cast<float4*>(out + j) =
+          on ? make_float4(y[j], y[j + 1], y[j + 2], y[j + 3]) : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(ncols)
+                 : "memory");
+  }
+}
+
+}  // namespace tc
+
+// float32 Gram partials on the tensor cores; returns 1 when the shapes are outside its
+// range (the caller then runs the SIMT kernel), else the status.  Partials as k_gram32.
+int gram_tc(rmgtd_ctx* ctx, const float* w, int nw, float* part, int nsplit, int chunk,
+            const RepCtl* ctl) {
+  using namespace tc;
+  const int N = ctx->N;
+  const int T = ceil_div(N, 32);
+  const int Np = T * 32;
+  if (ctx->Ng >= (1l << 31) || chunk % kGKS) return 1;
+  const size_t smem = (size_t)(2 * kGAfl + 2 * kGBfl) * sizeof(float);
+  if (!ctx->gram_tc_attr) {
+    RMGTD_CUDA(ctx, cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem));
+    ctx->gram_tc_attr = 1;
+  }
+  const dim3 grid(nsplit, T * (T + 1) / 2, ceil_div(nw, 4));
+  k_gram_tc<<<grid, kThreadsG, smem, ctx->stream>>>(N, Np, (int)ctx->Ng, ctx->phi32, w, nw, T,
+                                                      chunk, part, ctl, ctx->status);
+  ++ctx->launches;
+  RMGTD_LAUNCH(ctx, "k_gram_tc");
+  return RMGTD_OK;
+}
+
+}  // namespace rmgtd

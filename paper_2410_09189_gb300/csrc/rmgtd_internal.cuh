@@ -125,8 +125,10 @@ struct rmgtd_ctx {
   float* dv32 = nullptr;       // [nrep][Ng] V_Hxc - vref (mixed)
   float* dvh32 = nullptr;      // [nrep][Ng] V_H - vh_ref (mixed, Hartree correction unknown)
   float* dvh_prev32 = nullptr; // [nrep][Ng] dvh32 one step earlier (initial-guess history)
+  float* dvh_prev2_32 = nullptr; // [nrep][Ng] dvh32 two steps earlier
   float* shat32 = nullptr;     // [nrep][Np][Np] float32 density-change matrix (mixed)
   double* vh_prev = nullptr;   // [nrep][Ng] V_H one step earlier (initial-guess history)
+  double* vh_prev2 = nullptr;  // [nrep][Ng] V_H two steps earlier
   float *pcg32_b = nullptr, *pcg32_r = nullptr, *pcg32_z = nullptr, *pcg32_p = nullptr,
         *pcg32_Ap = nullptr, *pcg32_Az = nullptr;   // [nrep][Ng] float32 CG vectors (mixed)
   float* drho32 = nullptr;     // [nrep][Ng] rho - rho_ref in float32 (mixed)
@@ -145,6 +147,14 @@ struct rmgtd_ctx {
   unsigned* bar2 = nullptr;          // grid-barrier counter of the persistent Hartree solve
   int coop_attr_set[2] = {0, 0};     // persistent Hartree kernel configured (float64, float32)
   int coop_grid[2] = {0, 0};
+  int rho_tc_attr = 0;               // tensor-core density kernel configured
+  // launch choices (defaults, or measured by rmgtd_autotune)
+  int tune_rho_blocks = 3;           // CTAs per SM of the tensor-core density kernel
+  int tune_gram_tc = 0;              // mixed Gram on the tensor cores (1) or SIMT (0)
+  int tune_gram_blocks = 2;          // CTAs per SM over the Gram's (pair, replica-group) units
+  int tune_coop_div = 1;             // persistent Hartree solve on (SMs / div) blocks
+  void* tune_x = nullptr;            // Hartree unknown redirected while timing (autotune)
+  int gram_tc_attr = 0;              // tensor-core Gram kernel configured
   double* red_part = nullptr;  // reduction partials
   int red_blocks = 0;                // blocks of the grid-stride reduction kernels
   int red_cap = 0;                   // capacity of one partial slot
@@ -178,6 +188,17 @@ struct rmgtd_ctx {
   // CUDA graph of one time step
   cudaGraphExec_t step_exec = nullptr;
   cudaGraph_t step_graph = nullptr;
+  int in_batch = 0;             // stepped through an rmgtd_batch (own step calls refused)
+
+  // learned seed of the SCF loop (attached network; buffers allocated at attach)
+  rmgtd_net* net = nullptr;
+  float* net_x = nullptr;       // [nrep][3][Ng] features
+  float* net_y = nullptr;       // [nrep][Ng] network output
+  float* net_dv32 = nullptr;    // [nrep][Ng] predicted dV (mixed path)
+  double* net_dv64 = nullptr;   // [nrep][Ng] predicted dV (float64 path)
+  double* rho_h1 = nullptr;     // [nrep][Ng] rho one step earlier
+  double* rho_h2 = nullptr;     // [nrep][Ng] rho two steps earlier
+  double* rho_start = nullptr;  // [nrep][Ng] rho at the start of the current step
   cudaStream_t aux[3] = {nullptr, nullptr, nullptr};  // SCF body, CG body, top-level capture
   int capturing = 0;
   int* failed = nullptr;            // sticky: a step of the current rmgtd_step call failed
@@ -343,5 +364,16 @@ int hartree_extrapolate(rmgtd_ctx* ctx);
 int hartree_coop(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* ctl, int zero_bc,
                  int nrep, int f32);
 int hartree_reset_history(rmgtd_ctx* ctx);
+// k_tc.cu
+int rho_tc(rmgtd_ctx* ctx, double* rho, float* drho, const RepCtl* ctl, int nrep);
+int gram_tc(rmgtd_ctx* ctx, const float* w, int nw, float* part, int nsplit, int chunk,
+            const RepCtl* ctl);
+// k_surrogate.cu
+int net_forward_on(rmgtd_net* n, const float* x, float* y, int batch, cudaStream_t s, bool keep_pre);
+int net_batch_cap(const rmgtd_net* n);
+long net_grid_points(const rmgtd_net* n, int* nx, int* ny, int* nz);
+int net_predict(rmgtd_ctx* ctx);
+int net_history_shift(rmgtd_ctx* ctx);
+int net_history_reset(rmgtd_ctx* ctx);
 
 }  // namespace rmgtd

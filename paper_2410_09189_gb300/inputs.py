@@ -166,6 +166,45 @@ def icosa(n: int = 128, h: float = 0.4, nvirt: int = 74, shells: int = 3) -> Sys
                   nocc=nocc, nvirt=nvirt, kick_axes=(2,), nsteps=1000, seed=seed)
 
 
+# the eight clusters of the batched workload: atom counts and grids (edge points)
+CLUSTER_ATOMS = (20, 38, 56, 75, 93, 112, 131, 150)
+CLUSTER_GRIDS = (48, 56, 64, 64, 72, 80, 88, 96)
+
+
+def cluster(index: int, natoms: Optional[int] = None, n: Optional[int] = None,
+            h: float = 0.4) -> System:
+    """Cluster `index` (0..7) of the batched workload: atoms uniform in a sphere with a
+    minimum distance of 4.0 bohr (rejection sampling, seeded), Z = 1 local well (r_c = 0.5)
+    plus an s-type KB projector (r_c = 1.2, E_KB ~ U[0.5, 2]) on every atom, h = 0.4,
+    N_occ = ceil(natoms / 2), N = 2 N_occ."""
+    natoms = CLUSTER_ATOMS[index] if natoms is None else natoms
+    n = CLUSTER_GRIDS[index] if n is None else n
+    seed = SEED_BASE + 1000 * 4 + index
+    rng = np.random.default_rng(seed)
+    half = 0.5 * (n - 1) * h
+    # 80 % of the half-width, enlarged (up to 95 %) where the atoms would fill more than a
+    # quarter of the spheres of radius 2 around them (random placement jams near 38 %)
+    radius = min(max(0.8 * half, 2.0 * (4.0 * natoms) ** (1.0 / 3.0) - 2.0), 0.95 * half)
+    pts = []
+    tries = 0
+    while len(pts) < natoms:
+        tries += 1
+        if tries > 200000:
+            raise ValueError("cluster: could not place the atoms at the minimum distance")
+        p = rng.uniform(-radius, radius, 3)
+        if np.linalg.norm(p) > radius:
+            continue
+        if all(np.linalg.norm(p - q) >= 4.0 for q in pts):
+            pts.append(p)
+    pos = np.array(pts)
+    nocc = (natoms + 1) // 2
+    ekb = rng.uniform(0.5, 2.0, size=natoms)
+    return System(f"cluster{index}", (n, n, n), h, pos, np.ones(natoms), np.full(natoms, 0.5),
+                  np.arange(natoms, dtype=np.int32), np.zeros(natoms, np.int32),
+                  np.zeros(natoms, np.int32), np.full(natoms, 1.2), ekb,
+                  nocc=nocc, nvirt=nocc, kick_axes=(0, 1, 2), nsteps=200, seed=seed)
+
+
 def harmonic(n: int = 32, h: float = 0.4, omega: float = 0.5, nvirt: int = 3) -> System:
     """Test mode: one doubly occupied orbital in V = 0.5*omega^2*r^2, no Hartree/xc."""
     pa, pl, pm, prc, ekb = _no_proj()

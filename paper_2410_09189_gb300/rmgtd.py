@@ -102,6 +102,24 @@ def load_library(path: Optional[str] = None):
         "rmgtd_profile_counters": (i, [vp, ctypes.POINTER(ctypes.c_longlong),
                                        ctypes.POINTER(ctypes.c_longlong)]),
         "rmgtd_gram_noalloc": (i, [vp, vp, vp, i, ctypes.c_longlong, d, vp, vp]),
+        "rmgtd_net_num_params": (ctypes.c_longlong, []),
+        "rmgtd_net_create": (i, [i, i, i, i, vp, ctypes.POINTER(vp)]),
+        "rmgtd_net_destroy": (None, [vp]),
+        "rmgtd_net_set_params": (i, [vp, ctypes.POINTER(ctypes.c_float)]),
+        "rmgtd_net_get_params": (i, [vp, ctypes.POINTER(ctypes.c_float)]),
+        "rmgtd_net_set_scales": (i, [vp, _c_double_p, d]),
+        "rmgtd_net_get_scales": (i, [vp, _c_double_p, _c_double_p]),
+        "rmgtd_net_features": (i, [vp, vp, vp, vp, vp]),
+        "rmgtd_net_targets": (i, [vp, vp, vp, vp, vp]),
+        "rmgtd_net_forward": (i, [vp, vp, vp, i]),
+        "rmgtd_net_backward": (i, [vp, vp, vp, i, _c_double_p, ctypes.POINTER(ctypes.c_float)]),
+        "rmgtd_net_adam": (i, [vp, d]),
+        "rmgtd_attach_net": (i, [vp, vp]),
+        "rmgtd_get_field": (i, [vp, i, i, vp]),
+        "rmgtd_autotune": (i, [vp, _c_int_p]),
+        "rmgtd_batch_create": (i, [ctypes.POINTER(vp), i, ctypes.POINTER(vp)]),
+        "rmgtd_batch_destroy": (None, [vp]),
+        "rmgtd_batch_step": (i, [vp, i, ctypes.POINTER(ctypes.POINTER(CStats))]),
         "rmgtd_profile_read": (i, [vp, _c_double_p, ctypes.POINTER(ctypes.c_longlong),
                                    ctypes.POINTER(ctypes.c_longlong)]),
     }
@@ -204,6 +222,16 @@ class Context:
             msg = lib.rmgtd_last_error(None).decode()
             raise RmgtdError(rc, msg)
 
+    def _stats_array(self, st, nsteps):
+        out = np.zeros((nsteps, self.nrep), dtype=[("passes", "i4"), ("terms_max", "i4"),
+                                                   ("terms_sum", "i4"), ("status", "i4"),
+                                                   ("H_err", "f8")])
+        for s in range(nsteps):
+            for r in range(self.nrep):
+                c = st[s * self.nrep + r]
+                out[s, r] = (c.passes, c.terms_max, c.terms_sum, c.status, c.H_err)
+        return out
+
     # --- helpers -----------------------------------------------------------------------
     def _check(self, rc: int):
         if rc != OK:
@@ -245,6 +273,22 @@ class Context:
                 c = st[s * self.nrep + r]
                 out[s, r] = (c.passes, c.terms_max, c.terms_sum, c.status, c.H_err)
         return out if raise_on_error else (rc, out)
+
+    def autotune(self):
+        """Time the launch alternatives and keep the fastest; returns the choice
+        (density CTAs/SM, Gram on tensor cores, Gram CTAs/SM, Hartree block divisor)."""
+        c = np.zeros(4, dtype=np.int32)
+        self._check(self._lib.rmgtd_autotune(self._ctx, _iptr(c)))
+        return tuple(int(v) for v in c)
+
+    def attach_net(self, net: Optional["Net"]):
+        """Seed every step's SCF loop with the network's correction (None detaches)."""
+        self._net = net
+        self._check(self._lib.rmgtd_attach_net(self._ctx, net._net if net is not None else None))
+
+    def field_into(self, which: int, rep: int, dev_ptr: int):
+        """Copy rho (FIELD_RHO) or V_H + V_xc (FIELD_VHXC) of replica `rep` to device memory."""
+        self._check(self._lib.rmgtd_get_field(self._ctx, int(which), int(rep), ctypes.c_void_p(dev_ptr)))
 
     def density(self, rep: int = 0) -> np.ndarray:
         out = np.empty(self.Ng)
@@ -323,3 +367,114 @@ class Context:
         n = ctypes.c_longlong()
         self._check(self._lib.rmgtd_time(self._ctx, ctypes.byref(t), ctypes.byref(n)))
         return t.value, n.value
+
+
+FIELD_RHO, FIELD_VHXC = 0, 1
+
+
+class Net:
+    """The learned SCF-seed network (rmgtd_net): parameters, scales, features, forward,
+    backward and Adam all run in the library; arrays passed as device pointers (ints)."""
+
+    def __init__(self, n, max_batch: int = 1, stream: Optional[int] = None):
+        import torch
+
+        self._lib = load_library()
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        self.n = tuple(int(v) for v in n)
+        self.Ng = self.n[0] * self.n[1] * self.n[2]
+        self.max_batch = int(max_batch)
+        self.P = int(self._lib.rmgtd_net_num_params())
+        self._net = ctypes.c_void_p()
+        self._check(self._lib.rmgtd_net_create(self.n[0], self.n[1], self.n[2], self.max_batch,
+                                               ctypes.c_void_p(int(stream)), ctypes.byref(self._net)))
+
+    def _check(self, rc: int):
+        if rc != OK:
+            raise RmgtdError(rc, self._lib.rmgtd_last_error(None).decode())
+
+    def close(self):
+        if getattr(self, "_net", None) and self._net.value:
+            self._lib.rmgtd_net_destroy(self._net)
+            self._net = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, theta: np.ndarray):
+        t = np.ascontiguousarray(theta, dtype=np.float32)
+        assert t.size == self.P
+        self._check(self._lib.rmgtd_net_set_params(self._net, t.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+
+    def params(self) -> np.ndarray:
+        t = np.empty(self.P, dtype=np.float32)
+        self._check(self._lib.rmgtd_net_get_params(self._net, t.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+        return t
+
+    def set_scales(self, in_scales, out_scale: float):
+        s = np.ascontiguousarray(in_scales, dtype=np.float64)
+        self._check(self._lib.rmgtd_net_set_scales(self._net, _dptr(s), float(out_scale)))
+
+    def scales(self):
+        s = np.empty(3)
+        o = ctypes.c_double()
+        self._check(self._lib.rmgtd_net_get_scales(self._net, _dptr(s), ctypes.byref(o)))
+        return s, float(o.value)
+
+    def features(self, rho_t: int, rho_tm1: int, rho_tm2: int, x: int):
+        v = ctypes.c_void_p
+        self._check(self._lib.rmgtd_net_features(self._net, v(rho_t), v(rho_tm1), v(rho_tm2), v(x)))
+
+    def targets(self, v_tp1: int, v_t: int, v_tm1: int, t: int):
+        v = ctypes.c_void_p
+        self._check(self._lib.rmgtd_net_targets(self._net, v(v_tp1), v(v_t), v(v_tm1), v(t)))
+
+    def forward(self, x: int, y: int, batch: int):
+        self._check(self._lib.rmgtd_net_forward(self._net, ctypes.c_void_p(x), ctypes.c_void_p(y), int(batch)))
+
+    def backward(self, x: int, t: int, batch: int, want_grad: bool = False):
+        loss = ctypes.c_double()
+        g = np.empty(self.P, dtype=np.float32) if want_grad else None
+        gp = g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)) if want_grad else None
+        self._check(self._lib.rmgtd_net_backward(self._net, ctypes.c_void_p(x), ctypes.c_void_p(t),
+                                                 int(batch), ctypes.byref(loss), gp))
+        return (float(loss.value), g) if want_grad else float(loss.value)
+
+    def adam(self, lr: float):
+        self._check(self._lib.rmgtd_net_adam(self._net, float(lr)))
+
+
+class Batch:
+    """Several contexts stepped by one CUDA graph per time step (rmgtd_batch)."""
+
+    def __init__(self, ctxs):
+        self._lib = load_library()
+        self.ctxs = list(ctxs)
+        arr = (ctypes.c_void_p * len(self.ctxs))(*[c._ctx.value for c in self.ctxs])
+        self._b = ctypes.c_void_p()
+        rc = self._lib.rmgtd_batch_create(arr, len(self.ctxs), ctypes.byref(self._b))
+        if rc != OK:
+            raise RmgtdError(rc, self._lib.rmgtd_last_error(None).decode())
+
+    def step(self, nsteps: int = 1):
+        bufs = [(CStats * max(1, nsteps * c.nrep))() for c in self.ctxs]
+        ptrs = (ctypes.POINTER(CStats) * len(bufs))(*[ctypes.cast(b, ctypes.POINTER(CStats)) for b in bufs])
+        rc = self._lib.rmgtd_batch_step(self._b, int(nsteps), ptrs)
+        if rc != OK:
+            raise RmgtdError(rc, self._lib.rmgtd_last_error(None).decode())
+        return [c._stats_array(b, nsteps) for c, b in zip(self.ctxs, bufs)]
+
+    def close(self):
+        if getattr(self, "_b", None) and self._b.value:
+            self._lib.rmgtd_batch_destroy(self._b)
+            self._b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -393,3 +393,27 @@ def test_subspace_ground_state_matches_oracle(torch_dev):
                 assert np.max(np.abs(ctx.get_matrix(rmgtd.MAT_H0, rep) - H)) < 1e-8
             ctx.step(2)
             assert np.max(np.abs(ctx.density_matrix(0) - P)) < 1e-7
+
+
+@pytest.mark.parametrize("nvirt", [15, 22])
+def test_mixed_density_matches_oracle(torch_dev, nvirt):
+    """rho of the mixed path (rho_ref + float32 change; N <= 32 on the tensor cores, larger N
+    on the float32 SIMT kernel) against the oracle's rho of the same P, three replicas with
+    different kicks on a ragged grid (a partial last 128-point tile)."""
+    rmgtd = _rmgtd()
+    s = _ring_small(n=(30, 34, 38), h=0.5, nvirt=nvirt)
+    raw = inputs.smooth_random_orbitals(s).reshape(s.N, s.Ng)
+    phi = oham.orthonormalize(s, raw)
+    pr = tddft.Propagator(s, phi, tddft.Options())
+    torch = torch_dev
+    with rmgtd.Context(s, raw, dt=0.02, H_thrs=1e-9, dP_thrs=1e-12, nrep=3,
+                       precision=rmgtd.PREC_MIXED) as ctx:
+        for a in range(3):
+            ctx.kick(a, a, 1e-2)
+        ctx.step(2)
+        buf = torch.empty(s.Ng, dtype=torch.float64, device="cuda")
+        for a in range(3):
+            ctx.field_into(rmgtd.FIELD_RHO, a, buf.data_ptr())
+            rho = buf.cpu().numpy()
+            ref = pr.density(ctx.density_matrix(a))
+            assert np.max(np.abs(rho - ref)) <= 1e-7 * np.max(np.abs(ref)), (a, np.max(np.abs(rho - ref)))
