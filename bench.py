@@ -199,16 +199,16 @@ def _mg_levels(n):
 def hartree_bytes(n, solves, iters, mixed):
     """Algorithmic bytes of the persistent Hartree solve: each array every phase reads or
     writes, counted once (no stencil re-reads).  Per fine point and CG iteration: level 0 of
-    the V-cycle 53 + 2 s_V bytes (pre-sweeps 8 + s_V, residual 12, restriction 4.5,
-    prolongation 8.5, post-sweeps 12 + 8 + s_V), each coarser multi-block level 57 bytes per
-    own point, the tail 8 bytes per tail point, A z with its dots 5 s_V and the vector update
-    10 s_V (s_V = 4 float32 / 8 float64; the first iteration of a solve reads no p, A p:
-    -4 s_V).  Per solve: moments and right-hand side 2 s_rho + 4 s_ghost + 3 s_V."""
+    the V-cycle 45 + 2 s_V bytes (pre-sweeps 8 + s_V, residual with the box restriction
+    8.5, prolongation 8.5, post-sweeps 12 + 8 + s_V), each coarser multi-block level 49 bytes
+    per own point, the tail 8 bytes per tail point, A z with its dots 5 s_V and the vector
+    update 10 s_V (s_V = 4 float32 / 8 float64; the first iteration of a solve reads no p,
+    A p: -4 s_V).  Per solve: moments and right-hand side 2 s_rho + 4 s_ghost + 3 s_V."""
     sv = 4 if mixed else 8
     lv, tail = _mg_levels(n)
     nmulti = tail if tail is not None else len(lv)
-    per_it = lv[0] * (53 + 2 * sv + 15 * sv)
-    per_it += sum(57 * lv[l] for l in range(1, nmulti))
+    per_it = lv[0] * (45 + 2 * sv + 15 * sv)
+    per_it += sum(49 * lv[l] for l in range(1, nmulti))
     if tail is not None:
         per_it += 8 * lv[tail]
     prologue = lv[0] * (2 * sv + 4 * sv + 3 * sv)

@@ -6,18 +6,20 @@
 // The ghost term is linear in (Q, p): L_ghost(V_b) = Q G0 + px Gx + py Gy + pz Gz with four
 // grid fields G fixed by the grid, formed once at set-up.
 //
-// Solver: flexible (Polak-Ribiere) conjugate gradients, preconditioned by one symmetric
+// Solver: flexible (Polak-Ribiere) conjugate gradients, preconditioned by one
 // multigrid V-cycle in float32 (the paper's multigrid, Section 2.1): cell-centred coarsening
 // by 2, 7-point operators at spacing 2^l h, damped Jacobi smoothing (2 pre, 2 post),
-// trilinear prolongation and its transpose/8 as restriction; the levels with <= 4096 points
-// run inside one block, whose coarsest level is solved exactly.  The float64 path iterates
+// trilinear prolongation and the box restriction (mean over the 8 children, formed in the
+// same pass as the residual; the V-cycle is then not symmetric, which flexible CG
+// tolerates); the levels with <= 4096 points run inside one block, whose coarsest level
+// is solved exactly.  The float64 path iterates
 // on V itself; the mixed path iterates in float32 on the change of V relative to the
 // reference potential, with float32 right-hand side and dot products summed per warp in
 // float32 and across warps and blocks in float64 (float64 runs at a small fraction of the
 // float32 rate on this GPU, so no per-point float64 work remains in that solve).
 //
 // One cooperative launch runs the whole solve: prologue, every CG iteration and every
-// V-cycle phase, separated by grid barriers (15 per iteration at 64^3).  A p = A z +
+// V-cycle phase, separated by grid barriers (13 per iteration at 64^3).  A p = A z +
 // beta A p_old is carried as a vector, so the 37-point operator is applied once per
 // iteration to z, and (p, A p) follows from four dot products taken with A z.  Every block
 // sums the per-block partials of a reduction in the same order, so all blocks take the
@@ -162,24 +164,18 @@ __device__ __forceinline__ void tri_w(int f, int nc, int* c0, int* c1, float* w0
   }
 }
 
-__device__ __forceinline__ float restrict_point(const float* __restrict__ r, int I, int J, int K,
-                                                int nx, int ny, int nz) {
+// Box restriction of the residual: the mean of b - A x over the 8 fine children of coarse
+// point (I, J, K) (cell-centred coarsening by 2; A = 7-point operator / h^2).
+__device__ __forceinline__ float restrict_residual(const float* __restrict__ x,
+                                                   const float* __restrict__ b, int I, int J,
+                                                   int K, int nx, int ny, int nz, float ih2) {
   float s = 0.0f;
-  for (int dz = -1; dz <= 2; ++dz) {
-    const int fz = 2 * K + dz;
-    if (fz < 0 || fz >= nz) continue;
-    const float wz = (dz == 0 || dz == 1) ? 0.75f : 0.25f;
-    for (int dy = -1; dy <= 2; ++dy) {
-      const int fy = 2 * J + dy;
-      if (fy < 0 || fy >= ny) continue;
-      const float wy = (dy == 0 || dy == 1) ? 0.75f : 0.25f;
-      for (int dx = -1; dx <= 2; ++dx) {
-        const int fx = 2 * I + dx;
-        if (fx < 0 || fx >= nx) continue;
-        const float wx = (dx == 0 || dx == 1) ? 0.75f : 0.25f;
-        s += wx * wy * wz * r[(fz * ny + fy) * nx + fx];
-      }
-    }
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int fx = 2 * I + (c & 1), fy = 2 * J + ((c >> 1) & 1), fz = 2 * K + (c >> 2);
+    float cc;
+    const float ax = lap7f(x, fx, fy, fz, nx, ny, nz, &cc) * ih2;
+    s += b[(fz * ny + fy) * nx + fx] - ax;
   }
   return 0.125f * s;
 }
@@ -265,18 +261,11 @@ __device__ void tail_vcycle(const Tail& L, const float* __restrict__ b_in,
       xs[l][g] = c * (2.0f * bc - c * ab);
     }
     __syncthreads();
-    for (int g = threadIdx.x; g < n; g += blockDim.x) {   // t = b - A x
-      int ix, iy, iz;
-      xyz_of(g, nx, ny, L.dx[l], L.dy[l], ix, iy, iz);
-      float cc;
-      ts[l][g] = bs[l][g] - lap7f(xs[l], ix, iy, iz, nx, ny, nz, &cc) * ih2;
-    }
-    __syncthreads();
     const int cx = L.nx[l + 1], cy = L.ny[l + 1], nc = L.n[l + 1];
-    for (int g = threadIdx.x; g < nc; g += blockDim.x) {
+    for (int g = threadIdx.x; g < nc; g += blockDim.x) {   // restricted residual
       int I, J, K;
       xyz_of(g, cx, cy, L.dx[l + 1], L.dy[l + 1], I, J, K);
-      bs[l + 1][g] = restrict_point(ts[l], I, J, K, nx, ny, nz);
+      bs[l + 1][g] = restrict_residual(xs[l], bs[l], I, J, K, nx, ny, nz, ih2);
     }
     __syncthreads();
   }
@@ -731,17 +720,8 @@ __global__ void __launch_bounds__(kThreadsC, 1) k_hartree_coop(Args<V> a) {
         L.x[e] = c * (2.0f * bc - c * (6.0f * bc - sn) * ih2f);
       }
       COOP_BAR();
-      // residual t = b - A x
-      for (int e = gtid; e < Nl; e += gstride) {
-        const int rep = fdiv(e, L.dn);
-        if (!act[rep]) continue;
-        int ix, iy, iz;
-        xyz_of(e - rep * L.n, L.nx, L.ny, L.dx, L.dy, ix, iy, iz);
-        float cc;
-        L.t[e] = L.b[e] - lap7f(L.x + rep * L.n, ix, iy, iz, L.nx, L.ny, L.nz, &cc) * ih2f;
-      }
-      COOP_BAR();
-      // restriction to the next level
+      // residual b - A x of the 8 children of every coarse point, averaged (the box
+      // restriction) into the next level's right-hand side, in one pass
       {
         const Level& C = T.L[l + 1];
         const int Nc = C.n * nrep;
@@ -750,7 +730,8 @@ __global__ void __launch_bounds__(kThreadsC, 1) k_hartree_coop(Args<V> a) {
           if (!act[rep]) continue;
           int I, J, K;
           xyz_of(e - rep * C.n, C.nx, C.ny, C.dx, C.dy, I, J, K);
-          C.b[e] = restrict_point(L.t + rep * L.n, I, J, K, L.nx, L.ny, L.nz);
+          C.b[e] = restrict_residual(L.x + rep * L.n, L.b + rep * L.n, I, J, K, L.nx, L.ny,
+                                     L.nz, ih2f);
         }
       }
       COOP_BAR();

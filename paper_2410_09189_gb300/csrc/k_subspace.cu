@@ -89,9 +89,9 @@ k_gram_partial(int N, long Ng, const double* __restrict__ A, const double* __res
 // max_ij |out - prev| is folded into errbits[rep] (prev may alias out: every element is read
 // and written by the same warp).
 __global__ void k_gram_reduce(int N, int nsplit, const double* __restrict__ part, double scale,
-                              const double* __restrict__ base, double* out, long ostride,
-                              const double* prev, int sym, unsigned long long* errbits,
-                              const RepCtl* __restrict__ ctl) {
+                              const double* __restrict__ base, long bstride, double* out,
+                              long ostride, const double* prev, int sym,
+                              unsigned long long* errbits, const RepCtl* __restrict__ ctl) {
   const int rep = blockIdx.y;
   if (ctl && !ctl[rep].active) return;
   __shared__ double sh[32];
@@ -108,7 +108,7 @@ __global__ void k_gram_reduce(int N, int nsplit, const double* __restrict__ part
     sacc = warp_sum(sacc);
     if (lane == 0) {
       double v = scale * sacc;
-      if (base) v += base[e];
+      if (base) v += base[rep * bstride + e];
       double* o = out + rep * ostride;
       if (prev) emax = fmax(emax, fabs(v - prev[rep * ostride + e]));
       o[e] = v;
@@ -133,7 +133,7 @@ static int gram_nsplit(rmgtd_ctx* ctx, int ntiles, int nrep) {
 
 int gram(rmgtd_ctx* ctx, const double* A, const double* B, const double* w, long wstride,
          int nw, double scale, const double* base, double* out, const double* prev,
-         const RepCtl* ctl, int sym, unsigned long long* errbits) {
+         const RepCtl* ctl, int sym, unsigned long long* errbits, long bstride) {
   const int N = ctx->N;
   const int T = ceil_div(N, kGT);
   const int ntiles = sym ? T * (T + 1) / 2 : T * T;
@@ -147,7 +147,7 @@ int gram(rmgtd_ctx* ctx, const double* A, const double* B, const double* w, long
   const long NN = (long)N * N;
   const int rb = (int)std::min<long>(ceil_div(NN, 8), 4L * ctx->num_sms);
   k_gram_reduce<<<dim3(rb, nw), 256, 0, ctx->stream>>>(N, nsplit, ctx->gram_part, scale, base,
-                                                        out, NN, prev, sym, errbits, ctl);
+                                                        bstride, out, NN, prev, sym, errbits, ctl);
   ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_gram_reduce");
   return RMGTD_OK;
@@ -492,8 +492,8 @@ k_gram32(int N, int Np, int Ng, const float* __restrict__ phi, const float* __re
 // one replica; warp w sums the splits s = w, w + 8, ...
 __global__ void __launch_bounds__(256)
 k_gram32_reduce(int N, int Np, int nsplit, int nrep, const float* __restrict__ part,
-                double scale, const double* __restrict__ base, double* out, const double* prev,
-                unsigned long long* errbits, const RepCtl* __restrict__ ctl) {
+                double scale, const double* __restrict__ base, long bstride, double* out,
+                const double* prev, unsigned long long* errbits, const RepCtl* __restrict__ ctl) {
   const int rep = blockIdx.y;
   if (ctl && !ctl[rep].active) return;
   __shared__ double sh[8][33];
@@ -526,7 +526,7 @@ k_gram32_reduce(int N, int Np, int nsplit, int nrep, const float* __restrict__ p
       const long NN = (long)N * N;
       const long o = (long)i * N + j;
       double v = scale * t;
-      if (base) v += base[o];
+      if (base) v += base[rep * bstride + o];
       double* orow = out + rep * NN;
       if (prev) emax = fmax(emax, fabs(v - prev[rep * NN + o]));
       orow[o] = v;
@@ -542,7 +542,8 @@ k_gram32_reduce(int N, int Np, int nsplit, int nrep, const float* __restrict__ p
 }
 
 int gram_mixed(rmgtd_ctx* ctx, const float* w, long wstride, int nw, double scale,
-               const double* base, double* out, const RepCtl* ctl, unsigned long long* errbits) {
+               const double* base, double* out, const RepCtl* ctl, unsigned long long* errbits,
+               long bstride) {
   const int N = ctx->N;
   const int T = ceil_div(N, kGT);
   const int Np = T * kGT;
@@ -571,7 +572,7 @@ int gram_mixed(rmgtd_ctx* ctx, const float* w, long wstride, int nw, double scal
     RMGTD_LAUNCH(ctx, "k_gram32");
   }
   k_gram32_reduce<<<dim3(ceil_div((long)Np * Np, 32L), nw), 256, 0, ctx->stream>>>(
-      N, Np, nsplit, nw, part, scale, base, out, out, errbits, ctl);
+      N, Np, nsplit, nw, part, scale, base, bstride, out, out, errbits, ctl);
   ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_gram32_reduce");
   return RMGTD_OK;

@@ -430,10 +430,12 @@ int net_predict(rmgtd_ctx* ctx) {
                                         ctx->mixed ? nullptr : ctx->net_dv64, ctx->failed);
   ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_dv_out");
+  // H_1[r] += h^3 Phi^T diag(dV_r) Phi: the base is each replica's own H_1
+  const long NN = (long)ctx->N * ctx->N;
   if (ctx->mixed)
-    return gram_mixed(ctx, ctx->net_dv32, Ng, nrep, ctx->h3, ctx->H1, ctx->H1, ctx->ctl, nullptr);
+    return gram_mixed(ctx, ctx->net_dv32, Ng, nrep, ctx->h3, ctx->H1, ctx->H1, ctx->ctl, nullptr, NN);
   return gram(ctx, ctx->phi, ctx->phi, ctx->net_dv64, Ng, nrep, ctx->h3, ctx->H1, ctx->H1, nullptr,
-              ctx->ctl, 1, nullptr);
+              ctx->ctl, 1, nullptr, NN);
 }
 
 int net_history_shift(rmgtd_ctx* ctx) {

@@ -336,13 +336,15 @@ int launch_lda(rmgtd_ctx* ctx, const double* rho, double* vh, int vh_mode, doubl
                double* exc, double* vhxc, float* dv32, long n, const RepCtl* ctl, int nrep,
                long stride, int with_xc);
 // k_subspace.cu
+// out[r] = base[r * bstride] + scale * A^T diag(w_r) B (bstride 0: one base for all replicas)
 int gram(rmgtd_ctx* ctx, const double* A, const double* B, const double* w, long wstride,
          int nw, double scale, const double* base, double* out, const double* prev,
-         const RepCtl* ctl, int sym, unsigned long long* errbits);
+         const RepCtl* ctl, int sym, unsigned long long* errbits, long bstride = 0);
 int rho_dev(rmgtd_ctx* ctx, const double* S, double* rho, const RepCtl* ctl, int nrep);
 int rho_dev_mixed(rmgtd_ctx* ctx, const double* S, double* rho, const RepCtl* ctl, int nrep);
 int gram_mixed(rmgtd_ctx* ctx, const float* w, long wstride, int nw, double scale,
-               const double* base, double* out, const RepCtl* ctl, unsigned long long* errbits);
+               const double* base, double* out, const RepCtl* ctl, unsigned long long* errbits,
+               long bstride = 0);
 int to_float(rmgtd_ctx* ctx, const double* in, float* out, long n);
 int eldyn(rmgtd_ctx* ctx, const double* Ha, const double* Hb, long hstride, double tau,
           const double* S0, const double* A0, double* S1, double* A1, const RepCtl* ctl_in,

@@ -122,21 +122,22 @@ def test_features_and_targets_match_oracle(lib):
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_zero_network_reproduces_the_paper_seed(lib, small_ground_state, precision):
-    """H_1 += h^3 Phi^T diag(0) Phi leaves H_1 unchanged: bitwise-equal trajectories."""
-    from paper_2410_09189_gb300 import inputs  # noqa: F401
+    """H_1 += h^3 Phi^T diag(0) Phi leaves every replica's H_1 unchanged: bitwise-equal
+    trajectories (three replicas kicked along x, y, z, so a mix-up of replicas shows)."""
     s, gs = small_ground_state
     prec = lib.PREC_FP64 if precision == "fp64" else lib.PREC_MIXED
-    kw = dict(nrep=1, H_thrs=1e-9, dP_thrs=1e-12, precision=prec)
+    kw = dict(nrep=3, H_thrs=1e-9, dP_thrs=1e-12, precision=prec)
     runs = []
     for with_net in (False, True):
         ctx = lib.Context(s, gs["phi"], use_graph=True, **kw)
-        ctx.kick(0, 2, s.kappa)
+        for a in range(3):
+            ctx.kick(a, a, s.kappa)
         if with_net:
-            net = lib.Net(s.n, max_batch=1)
+            net = lib.Net(s.n, max_batch=3)
             net.set_scales([1.0, 1.0, 1.0], 1.0)
             ctx.attach_net(net)
         st = ctx.step(12)
-        runs.append((ctx.dipole(0), st["passes"].copy()))
+        runs.append((np.array([ctx.dipole(a) for a in range(3)]), st["passes"].copy()))
         ctx.close()
     assert np.array_equal(runs[0][0], runs[1][0])
     assert np.array_equal(runs[0][1], runs[1][1])
