@@ -31,6 +31,8 @@ if ROOT not in sys.path:
 METRIC = "RT-TDDFT time-steps/sec and grid-point·orbital updates/sec, mixed vs FP64 GPU"
 UNIT = "time-steps/s"
 SUBSPACE_SCF = 200          # set-up SCF iterations inside the orbital block (stationary start)
+SUR_STEPS = 300             # trajectory steps recorded to train the learned SCF seed
+SUR_ITERS = 2000            # Adam iterations of that training
 FP64_PEAK_GFLOPS = 1250.0   # GB300 float64 rate (nominal 1.25 TFLOP/s)
 
 
@@ -300,10 +302,15 @@ def run_ours(args):
         prof = ctx.profile_read() if profile else None
         return [a.elapsed_time(b) for a, b in ev], np.concatenate(st), wall, prof
 
-    def run_path(p, nsteps, with_clocks):
+    def run_path(p, nsteps, with_clocks, state=None, net=None):
         c = rmgtd.Context(s, raw, use_graph=True, precision=p, **kw)
-        for a in range(3):
-            c.kick(a, a, s.kappa)
+        if state is None:
+            for a in range(3):
+                c.kick(a, a, s.kappa)
+        else:
+            c.load(state)
+        if net is not None:
+            c.attach_net(net)
         for _ in range(args.warmup):
             c.step(1)
         smp = ClockSampler(local)
@@ -332,6 +339,38 @@ def run_ours(args):
                   "value": world * args.steps / (o_ms * 1e-3), "unit": UNIT,
                   "ms_per_step": o_ms / args.steps,
                   "scf_passes_per_replica_step": float(o_st["passes"].sum()) / (3.0 * args.steps)}
+
+    # the mixed path with the learned seed: a network trained (library kernels only) on the
+    # first SUR_STEPS steps of this workload's own trajectory, then the continuation timed
+    # with and without it from the same state (a window the network has not seen)
+    surrogate_path = None
+    if prec == rmgtd.PREC_MIXED and not args.no_surrogate:
+        from paper_2410_09189_gb300 import surrogate
+        tctx = rmgtd.Context(s, raw, use_graph=True, precision=prec, **kw)
+        for a in range(3):
+            tctx.kick(a, a, s.kappa)
+        t0 = time.perf_counter()
+        net, rep = surrogate.train_on_trajectory(tctx, nsteps=SUR_STEPS, iters=SUR_ITERS,
+                                                 batch=8, lr=5e-4)
+        train_s = time.perf_counter() - t0
+        state = os.path.join(tempfile.mkdtemp(), "state.bin")
+        tctx.save(state)
+        tctx.close()
+        p_ms, p_st, _, _, _ = run_path(prec, args.steps, False, state=state)
+        n_ms, n_st, _, _, _ = run_path(prec, args.steps, False, state=state, net=net)
+        surrogate_path = {
+            "value": world * args.steps / (n_ms * 1e-3), "unit": UNIT,
+            "ms_per_step": n_ms / args.steps,
+            "scf_passes_per_replica_step": float(n_st["passes"].sum()) / (3.0 * args.steps),
+            "same_window_without_seed": {
+                "value": world * args.steps / (p_ms * 1e-3), "ms_per_step": p_ms / args.steps,
+                "scf_passes_per_replica_step": float(p_st["passes"].sum()) / (3.0 * args.steps)},
+            "window": f"steps {SUR_STEPS + args.warmup + 1}..{SUR_STEPS + args.warmup + args.steps}"
+                      " after the kicks",
+            "training": {"trajectory_steps": SUR_STEPS, "adam_iterations": SUR_ITERS, "batch": 8,
+                         "lr": 5e-4, "seconds_incl_recording": train_s,
+                         "heldout_seed_rms_ratio": rep["heldout_ratio"],
+                         "samples": rep["train_samples"]}}
 
     # second timed region, host-driven steps with CUDA events around every phase on the
     # library's stream: the per-kernel durations behind the roofline
@@ -391,6 +430,7 @@ def run_ours(args):
         "scf_passes_per_replica_step": rep_passes / (3.0 * args.steps),
         "commutator_terms_per_expansion": terms_total / max(rep_passes, 1),
         "other_path": other_path,
+        "surrogate_path": surrogate_path,
         "phase_ms_per_step_host_driven": {k: v / args.steps for k, v in phase_ms.items()},
         "ms_per_step_host_driven": float(sum(p_ms)) / args.steps,
         "gpu_launches": launches, "roofline": roof, "clocks": clocks,
@@ -433,6 +473,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-surrogate", action="store_true",
+                    help="skip training and timing the learned SCF seed")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

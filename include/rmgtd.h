@@ -291,6 +291,10 @@ int rmgtd_net_targets(rmgtd_net* net, const double* v_tp1, const double* v_t, co
                       float* t_dev);
 /* y_dev [batch][Ng] = net(x_dev [batch][3][Ng]) (device pointers); synchronises the stream. */
 int rmgtd_net_forward(rmgtd_net* net, const float* x_dev, float* y_dev, int batch);
+/* The same with the two 16 -> 16 layers on the tensor cores, activations rounded to
+ * bfloat16 at their inputs (float32 accumulation): the form the propagation's predictor
+ * uses.  Synchronises the stream. */
+int rmgtd_net_forward_tc(rmgtd_net* net, const float* x_dev, float* y_dev, int batch);
 /* Loss and gradient at the current parameters for targets t_dev [batch][Ng]; the gradient
  * stays on the device for rmgtd_net_adam and is copied to grad_host (RMGTD_NET_PARAMS
  * floats) when that is not NULL.  The grid needs interior points (every side > 8). */

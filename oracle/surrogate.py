@@ -117,12 +117,15 @@ def conv3d(x: np.ndarray, W: np.ndarray, b: np.ndarray) -> np.ndarray:
     return y + b[:, None, None, None]
 
 
-def forward(theta: np.ndarray, x: np.ndarray):
+def forward(theta: np.ndarray, x: np.ndarray, bf16_inputs=()):
     """Network output y [Z, Y, X] for one sample x [3, Z, Y, X]; also the per-layer
-    (input, pre-activation) pairs needed by the backward pass."""
+    (input, pre-activation) pairs needed by the backward pass.  Layers listed in
+    `bf16_inputs` see their input rounded to bfloat16 (the tensor-core inference form)."""
     acts = []
     h = x
     for l, (W, b) in enumerate(unpack(theta)):
+        if l in bf16_inputs:
+            h = bf16_round(h)
         z = conv3d(h, W, b)
         acts.append((h, z))
         h = silu(z) if l < NLAYERS - 1 else z

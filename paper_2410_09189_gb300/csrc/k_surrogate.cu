@@ -342,6 +342,7 @@ struct rmgtd_net {
   double* loss_part = nullptr;
   int loss_blocks = 0;
   double* loss_dev = nullptr;
+  int* status = nullptr;             // device status word of the tensor-core forward
   double in_scale[3] = {1.0, 1.0, 1.0};
   double out_scale = 1.0;
   std::vector<void*> bufs;
@@ -379,19 +380,29 @@ namespace rmgtd {
 
 // forward pass of `batch` samples x [batch][3][Ng] -> y [batch][Ng] on `s`; keep_pre stores
 // the pre-activations for a backward pass
-int net_forward_on(rmgtd_net* n, const float* x, float* y, int batch, cudaStream_t s, bool keep_pre) {
+int net_forward_on(rmgtd_net* n, const float* x, float* y, int batch, cudaStream_t s, bool keep_pre,
+                   bool tc_middle, int* status) {
   const Dims& d = n->d;
   const int gr = grid_for(n, (long)batch * d.n, kFwdThreads);
   const __nv_bfloat16* W = n->wbf;
   const float* th = n->theta;
   k_conv_fwd<3, 16, true><<<gr, kFwdThreads, 0, s>>>(d, batch, x, W + kWOff[0], th + kBOff[0],
                                                       n->act[0], keep_pre ? n->pre[0] : nullptr);
-  k_conv_fwd<16, 16, true><<<gr, kFwdThreads, 0, s>>>(d, batch, n->act[0], W + kWOff[1],
-                                                       th + kBOff[1], n->act[1],
-                                                       keep_pre ? n->pre[1] : nullptr);
-  k_conv_fwd<16, 16, true><<<gr, kFwdThreads, 0, s>>>(d, batch, n->act[1], W + kWOff[2],
-                                                       th + kBOff[2], n->act[2],
-                                                       keep_pre ? n->pre[2] : nullptr);
+  if (tc_middle && !keep_pre) {
+    // the two 16 -> 16 layers on the tensor cores (bfloat16 activations)
+    for (int l = 1; l <= 2; ++l) {
+      const int rc = conv16_tc(d.nx, d.ny, d.nz, batch, n->act[l - 1], W + kWOff[l], th + kBOff[l],
+                               n->act[l], 1, status, n->num_sms, s);
+      if (rc) return net_err(rc, "conv16_tc launch failed");
+    }
+  } else {
+    k_conv_fwd<16, 16, true><<<gr, kFwdThreads, 0, s>>>(d, batch, n->act[0], W + kWOff[1],
+                                                         th + kBOff[1], n->act[1],
+                                                         keep_pre ? n->pre[1] : nullptr);
+    k_conv_fwd<16, 16, true><<<gr, kFwdThreads, 0, s>>>(d, batch, n->act[1], W + kWOff[2],
+                                                         th + kBOff[2], n->act[2],
+                                                         keep_pre ? n->pre[2] : nullptr);
+  }
   k_conv_fwd<16, 1, false><<<gr, kFwdThreads, 0, s>>>(d, batch, n->act[2], W + kWOff[3],
                                                        th + kBOff[3], y, nullptr);
   NET_LAUNCH("k_conv_fwd");
@@ -422,7 +433,7 @@ int net_predict(rmgtd_ctx* ctx) {
                                           ctx->net_x, ctx->rho_start);
   ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_features");
-  int rc = net_forward_on(n, ctx->net_x, ctx->net_y, nrep, ctx->stream, false);
+  int rc = net_forward_on(n, ctx->net_x, ctx->net_y, nrep, ctx->stream, false, true, ctx->status);
   if (rc) return set_error(ctx, rc, rmgtd_last_error(nullptr));
   ctx->launches += kLayers;
   k_dv_out<<<bl, 256, 0, ctx->stream>>>(Ng * nrep, ctx->net_y, n->out_scale,
@@ -509,6 +520,7 @@ int rmgtd_net_create(int nx, int ny, int nz, int max_batch, void* stream, rmgtd_
   n->loss_blocks = 2 * n->num_sms;
   n->loss_part = (double*)A(sizeof(double) * n->loss_blocks);
   n->loss_dev = (double*)A(sizeof(double));
+  n->status = (int*)A(sizeof(int));
   if (!ok) {
     rmgtd_net_destroy(n);
     return net_err(RMGTD_ENOMEM, "net_create: device memory");
@@ -592,9 +604,22 @@ int rmgtd_net_targets(rmgtd_net* n, const double* v_tp1, const double* v_t, cons
 int rmgtd_net_forward(rmgtd_net* n, const float* x_dev, float* y_dev, int batch) {
   if (!n || !x_dev || !y_dev) return net_err(RMGTD_EINVAL, "net_forward: NULL argument");
   if (batch < 1 || batch > n->max_batch) return net_err(RMGTD_EINVAL, "net_forward: batch out of range");
-  int rc = net_forward_on(n, x_dev, y_dev, batch, n->stream, false);
+  int rc = net_forward_on(n, x_dev, y_dev, batch, n->stream, false, false, n->status);
   if (rc) return rc;
   NET_CUDA(cudaStreamSynchronize(n->stream));
+  return RMGTD_OK;
+}
+
+int rmgtd_net_forward_tc(rmgtd_net* n, const float* x_dev, float* y_dev, int batch) {
+  if (!n || !x_dev || !y_dev) return net_err(RMGTD_EINVAL, "net_forward_tc: NULL argument");
+  if (batch < 1 || batch > n->max_batch) return net_err(RMGTD_EINVAL, "net_forward_tc: batch out of range");
+  NET_CUDA(cudaMemsetAsync(n->status, 0, sizeof(int), n->stream));
+  int rc = net_forward_on(n, x_dev, y_dev, batch, n->stream, false, true, n->status);
+  if (rc) return rc;
+  int st = 0;
+  NET_CUDA(cudaMemcpyAsync(&st, n->status, sizeof(int), cudaMemcpyDeviceToHost, n->stream));
+  NET_CUDA(cudaStreamSynchronize(n->stream));
+  if (st) return net_err(st, "net_forward_tc: device wait timed out");
   return RMGTD_OK;
 }
 
@@ -610,7 +635,7 @@ int rmgtd_net_backward(rmgtd_net* n, const float* x_dev, const float* t_dev, int
   cudaStream_t s = n->stream;
   // forward with the pre-activations; the output goes to gbuf[1] (reused below)
   float* y = n->gbuf[1];
-  int rc = net_forward_on(n, x_dev, y, batch, s, true);
+  int rc = net_forward_on(n, x_dev, y, batch, s, true, false, n->status);
   if (rc) return rc;
   float* g = n->gbuf[0];
   k_loss<<<n->loss_blocks, 256, 0, s>>>(d, batch, y, t_dev, inv_count, g, n->loss_part);

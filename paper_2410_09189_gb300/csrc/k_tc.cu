@@ -17,7 +17,10 @@
 // Shat operand once, and loops over 128-point tiles: stage the orbital tile (transposed
 // to point-major), one thread issues 4 K-steps x 3 products, commits to an mbarrier, all
 // threads wait (bounded), each warp reads its 32 TMEM lanes and forms drho for its points.
+#include <cuda_bf16.h>
 #include <stdint.h>
+
+#include <algorithm>
 
 #include "rmgtd_internal.cuh"
 
@@ -450,6 +453,221 @@ int gram_tc(rmgtd_ctx* ctx, const float* w, int nw, float* part, int nsplit, int
   ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_gram_tc");
   return RMGTD_OK;
+}
+
+// ---- 16 -> 16 channel 3x3x3 convolution of the learned seed on the tensor cores -------------
+// Inference form of the network's two middle layers (the propagation's predictor): implicit
+// GEMM with M = 128 output points, N = 16 output channels, K = 16 input channels per tap,
+// one kind::f16 MMA per tap (27 taps accumulate in tensor memory).  Activations are rounded
+// to bfloat16 when staged (the weights already are); accumulation is float32.  A tile of 128
+// consecutive points (flat index over samples and points) is staged as K-major operands
+// A_t[p][c] = x_c(p + t) (zero outside the grid), one 16-byte store per 8 channels, nine
+// taps (one z offset) at a time: the 72 loads of a group are in flight together, and the
+// 51 KB of shared memory let four CTAs share an SM.
+namespace tc {
+
+constexpr int kCvM = 128;                  // points per tile
+constexpr int kCvC = 16;                   // channels in and out
+constexpr int kCvThreads = 256;
+constexpr int kCvAbytes = kCvM * kCvC * 2; // one tap's A operand (4 KB)
+constexpr int kCvBbytes = kCvC * kCvC * 2; // one tap's B operand (512 B)
+
+// bf16 index of element (row, k) in a K-major no-swizzle operand with K = 16: core matrices
+// of 8 rows x 8 bf16, K-adjacent at +128 B, 8-row groups at +256 B
+__device__ __forceinline__ int kmaj16(int row, int k) {
+  return (row >> 3) * 128 + (k >> 3) * 64 + (row & 7) * 8 + (k & 7);
+}
+
+// two floats as bfloat16 (round to nearest even), the first in the low half
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+__device__ __forceinline__ uint64_t sdesc_lbo_sbo(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// kind::f16, D float32, A and B bfloat16, both K-major, M x N
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__global__ void __launch_bounds__(kCvThreads)
+k_conv16_tc(int nx, int ny, int nz, int B, const float* __restrict__ in,
+            const __nv_bfloat16* __restrict__ W, const float* __restrict__ bias,
+            float* __restrict__ out, int silu, int* status) {
+  extern __shared__ __align__(128) unsigned char smc[];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t tmem_base;
+  __shared__ float bs[kCvC];
+  // A: one group of 9 taps (a z offset) at a time; B: all 27 taps
+  __nv_bfloat16* A = reinterpret_cast<__nv_bfloat16*>(smc);
+  __nv_bfloat16* Bw = reinterpret_cast<__nv_bfloat16*>(smc + 9 * kCvAbytes);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int n = nx * ny * nz, plane = nx * ny;
+  const int total = B * n;
+  const uint32_t ncols = 32;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     saddr(&tmem_base)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (tid < kCvC) bs[tid] = bias[tid];
+  // B_t[co][ci] = W[co][ci][t]
+  for (int e = tid; e < 27 * kCvC * kCvC; e += blockDim.x) {
+    const int t = e / (kCvC * kCvC), r = e % (kCvC * kCvC), co = r / kCvC, ci = r % kCvC;
+    Bw[t * (kCvBbytes / 2) + kmaj16(co, ci)] = W[(co * kCvC + ci) * 27 + t];
+  }
+  fence_async_smem();
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tbase = tmem_base;
+  const uint32_t idesc = idesc_bf16(kCvM, kCvC);
+  const int ntiles = (total + kCvM - 1) / kCvM;
+  const int p = tid & (kCvM - 1), half = tid >> 7;   // point of the tile, channels 8 half ..
+  uint32_t phase = 0;
+  bool ok_all = true;
+  for (int tile = blockIdx.x; tile < ntiles && ok_all; tile += gridDim.x) {
+    const int idx = tile * kCvM + p;
+    const bool valid = idx < total;
+    int b = 0, g = 0, ix = 0, iy = 0, iz = 0;
+    if (valid) {
+      b = idx / n;
+      g = idx - b * n;
+      ix = g % nx;
+      const int q = g / nx;
+      iy = q % ny;
+      iz = q / ny;
+    }
+    const float* src = in + ((long)b * kCvC + 8 * half) * n;
+    for (int grp = 0; grp < 3; ++grp) {   // taps with z offset grp - 1
+      const int tz = grp - 1;
+      const bool zok = valid && (unsigned)(iz + tz) < (unsigned)nz;
+      float v[9][8];
+#pragma unroll
+      for (int u = 0; u < 9; ++u) {       // all 72 loads of the group in flight together
+        const int ty = u / 3 - 1, tx = u % 3 - 1;
+        const bool ok = zok && (unsigned)(ix + tx) < (unsigned)nx && (unsigned)(iy + ty) < (unsigned)ny;
+        const int off = g + tz * plane + ty * nx + tx;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) v[u][c] = ok ? src[(long)c * n + off] : 0.0f;
+      }
+      if (grp > 0) {   // the MMAs of the previous group read A
+        const bool okw = mbar_wait(&bar, phase);
+        phase ^= 1u;
+        if (__syncthreads_or(!okw)) {
+          ok_all = false;
+          break;
+        }
+        fence_after();
+      }
+#pragma unroll
+      for (int u = 0; u < 9; ++u) {
+        uint4 w4;
+        w4.x = pack_bf16(v[u][0], v[u][1]);
+        w4.y = pack_bf16(v[u][2], v[u][3]);
+        w4.z = pack_bf16(v[u][4], v[u][5]);
+        w4.w = pack_bf16(v[u][6], v[u][7]);
+        *reinterpret_cast<uint4*>(&A[u * (kCvAbytes / 2) + kmaj16(p, 8 * half)]) = w4;
+      }
+      fence_async_smem();
+      __syncthreads();
+      if (tid == 0) {
+        fence_after();
+        const uint32_t a0 = saddr(A), b0 = saddr(Bw);
+        for (int u = 0; u < 9; ++u) {
+          const int t = 9 * grp + u;
+          mma_bf16(tbase, sdesc_lbo_sbo(a0 + u * kCvAbytes, 128, 256),
+                   sdesc_lbo_sbo(b0 + t * kCvBbytes, 128, 256), idesc, t > 0 ? 1u : 0u);
+        }
+        mma_commit(&bar);
+      }
+    }
+    if (!ok_all) break;
+    const bool okw = mbar_wait(&bar, phase);
+    phase ^= 1u;
+    if (__syncthreads_or(!okw)) {
+      ok_all = false;
+      break;
+    }
+    fence_after();
+    if (warp < 4) {   // TMEM lanes 32 warp .. : points of the tile
+      float y[16];
+      tmem_ld16(tbase + ((uint32_t)(warp * 32) << 16), y);
+      const int pi = tile * kCvM + warp * 32 + lane;
+      if (pi < total) {
+        const int bb = pi / n, gg = pi - bb * n;
+#pragma unroll
+        for (int co = 0; co < kCvC; ++co) {
+          const float z = y[co] + bs[co];
+          out[((long)bb * kCvC + co) * n + gg] = silu ? z / (1.0f + expf(-z)) : z;
+        }
+      }
+    }
+    fence_before();
+    __syncthreads();
+  }
+  if (!ok_all && tid == 0) atomicCAS(status, 0, (int)RMGTD_ETIMEOUT);
+  __syncthreads();
+  if (warp == 0) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(ncols)
+                 : "memory");
+  }
+}
+
+}  // namespace tc
+
+// y = conv(x) (+ SiLU) for a 16 -> 16 layer on the tensor cores, on stream s.
+int conv16_tc(int nx, int ny, int nz, int B, const float* x, const __nv_bfloat16* W,
+              const float* bias, float* y, int silu, int* status, int num_sms, cudaStream_t s) {
+  using namespace tc;
+  static bool attr = false;
+  const size_t smem = 9 * (size_t)kCvAbytes + 27 * (size_t)kCvBbytes;
+  if (!attr) {
+    if (cudaFuncSetAttribute(k_conv16_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+      return RMGTD_ECUDA;
+    attr = true;
+  }
+  const long total = (long)B * nx * ny * nz;
+  const int ntiles = (int)((total + kCvM - 1) / kCvM);
+  const int grid = std::min(ntiles, 4 * num_sms);   // 4 CTAs (51 KB each) per SM
+  k_conv16_tc<<<grid, kCvThreads, smem, s>>>(nx, ny, nz, B, x, W, bias, y, silu, status);
+  return cudaGetLastError() == cudaSuccess ? RMGTD_OK : RMGTD_ECUDA;
 }
 
 }  // namespace rmgtd

@@ -1,6 +1,7 @@
 // Internal definitions shared by the translation units of librmgtd (not part of the ABI).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string>
@@ -13,7 +14,7 @@ namespace rmgtd {
 constexpr int kThreads = 256;
 constexpr int kFdRadius = 6;             // 12th-order central stencil (Section 2.1, Eq. 2)
 constexpr double kRhoFloor = 1e-14;      // LDA floor
-constexpr unsigned kSpinLimit = 20000000u;  // bounded device-side waits (~2 s)
+constexpr unsigned kSpinLimit = 20000000u;  // bounded device-side waits (seconds)
 
 // 12th-order second-derivative weights a_0..a_6 (Fornberg closed form, exact rationals).
 __host__ __device__ inline double fd_coef(int m) {
@@ -291,15 +292,17 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
 }
 
 // Grid-wide barrier for cooperative launches.  `count` is zeroed before the launch and
-// only grows; `target` = gridDim.x * (number of this barrier, counting from 1).  The wait
-// gives up after kSpinLimit polls and records RMGTD_ETIMEOUT in *status; returns false then.
+// only grows; `target` = gridDim.x * (number of this barrier, counting from 1).  Thread 0
+// of each block arrives with a release reduction (the block barrier before it orders the
+// block's writes ahead of it) and polls with acquire loads (the block barrier after it
+// orders the block's later reads behind it).  The wait gives up after kSpinLimit polls and
+// records RMGTD_ETIMEOUT in *status; returns false then.
 __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned target, int* status) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     ok = 1;
-    __threadfence();
-    atomicAdd(count, 1u);
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(count) : "memory");
     unsigned spins = 0;
     while (ld_acquire_u32(count) < target) {
       if (++spins > kSpinLimit) {
@@ -307,9 +310,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned target, i
         ok = 0;
         break;
       }
-      __nanosleep(64);
     }
-    __threadfence();
   }
   __syncthreads();
   return ok != 0;
@@ -370,8 +371,11 @@ int hartree_reset_history(rmgtd_ctx* ctx);
 int rho_tc(rmgtd_ctx* ctx, double* rho, float* drho, const RepCtl* ctl, int nrep);
 int gram_tc(rmgtd_ctx* ctx, const float* w, int nw, float* part, int nsplit, int chunk,
             const RepCtl* ctl);
+int conv16_tc(int nx, int ny, int nz, int B, const float* x, const __nv_bfloat16* W,
+              const float* bias, float* y, int silu, int* status, int num_sms, cudaStream_t s);
 // k_surrogate.cu
-int net_forward_on(rmgtd_net* n, const float* x, float* y, int batch, cudaStream_t s, bool keep_pre);
+int net_forward_on(rmgtd_net* n, const float* x, float* y, int batch, cudaStream_t s, bool keep_pre,
+                   bool tc_middle, int* status);
 int net_batch_cap(const rmgtd_net* n);
 long net_grid_points(const rmgtd_net* n, int* nx, int* ny, int* nz);
 int net_predict(rmgtd_ctx* ctx);

@@ -112,6 +112,7 @@ def load_library(path: Optional[str] = None):
         "rmgtd_net_features": (i, [vp, vp, vp, vp, vp]),
         "rmgtd_net_targets": (i, [vp, vp, vp, vp, vp]),
         "rmgtd_net_forward": (i, [vp, vp, vp, i]),
+        "rmgtd_net_forward_tc": (i, [vp, vp, vp, i]),
         "rmgtd_net_backward": (i, [vp, vp, vp, i, _c_double_p, ctypes.POINTER(ctypes.c_float)]),
         "rmgtd_net_adam": (i, [vp, d]),
         "rmgtd_attach_net": (i, [vp, vp]),
@@ -435,6 +436,10 @@ class Net:
 
     def forward(self, x: int, y: int, batch: int):
         self._check(self._lib.rmgtd_net_forward(self._net, ctypes.c_void_p(x), ctypes.c_void_p(y), int(batch)))
+
+    def forward_tc(self, x: int, y: int, batch: int):
+        """Forward with the middle layers on the tensor cores (bfloat16 activations)."""
+        self._check(self._lib.rmgtd_net_forward_tc(self._net, ctypes.c_void_p(x), ctypes.c_void_p(y), int(batch)))
 
     def backward(self, x: int, t: int, batch: int, want_grad: bool = False):
         loss = ctypes.c_double()

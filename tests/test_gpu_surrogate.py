@@ -66,6 +66,36 @@ def test_forward_matches_oracle(lib):
         assert err <= 2e-5 * max(1.0, np.max(np.abs(yr))), err
 
 
+def test_tensor_core_forward_matches_oracle(lib):
+    """The predictor's inference form: the two 16 -> 16 layers on the tensor cores with
+    bfloat16 activations, against the oracle with the same roundings.  Where a float32
+    activation (device) and its float64 counterpart (oracle) fall on different sides of a
+    bfloat16 rounding boundary the two differ by one bfloat16 step (~2^-8 relative); with
+    ~10^3 rounded inputs per output that touches a few percent of the outputs, so the test
+    bounds the fraction of points off by more than 1e-4 and the largest deviation."""
+    th = _theta(9)
+    rng = np.random.default_rng(10)
+    B = 3
+    x = rng.standard_normal((B, 3, N[2], N[1], N[0])).astype(np.float32)
+    net = lib.Net(N, max_batch=B)
+    net.set_params(th)
+    xd = _dev(x, torch.float32)
+    yd = torch.empty((B, N[2] * N[1] * N[0]), dtype=torch.float32, device="cuda")
+    net.forward_tc(xd.data_ptr(), yd.data_ptr(), B)
+    y = yd.cpu().numpy()
+    ref = _as_used(th)
+    for b in range(B):
+        yr, _ = sg.forward(ref, x[b].astype(np.float64), bf16_inputs=(1, 2))
+        err = np.abs(y[b] - yr.ravel())
+        scale = max(1.0, np.max(np.abs(yr)))
+        assert np.mean(err > 1e-4 * scale) <= 0.10, np.mean(err > 1e-4 * scale)
+        assert np.max(err) <= 2e-2 * scale, np.max(err)
+    # and close to the float32 path (the bfloat16 activations cost ~1e-2 relative at most)
+    y32 = torch.empty_like(yd)
+    net.forward(xd.data_ptr(), y32.data_ptr(), B)
+    assert np.max(np.abs(y32.cpu().numpy() - y)) <= 5e-2 * max(1.0, np.max(np.abs(y)))
+
+
 def test_backward_and_adam_match_oracle(lib):
     th = _theta(5)
     rng = np.random.default_rng(6)
