@@ -111,6 +111,24 @@ def _config(s, precision):
 
 
 # ---------------------------------------------------------------------------------------
+def max_over_ranks(value: float, world: int, device: str = "cuda") -> float:
+    """The largest value over all ranks (the timed region's wall on the slowest GPU);
+    torch.distributed must be initialised when world > 1."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(steps: int, world: int, max_ms: float) -> float:
+    """Whole-job time-steps/s: every rank advances its own replica set `steps` steps (weak
+    scaling), and the job takes as long as the slowest rank."""
+    return world * steps / (max_ms * 1e-3)
+
+
 def run_reference(args):
     """The FP64 CPU oracle on the same workload: each step is one time step of ONE replica
     (a bounded sample), reported in the 3-replica unit."""
@@ -320,18 +338,14 @@ def run_ours(args):
                                         nvtx_name="rmgtd_timed" if with_clocks else "rmgtd_other")
         clk = smp.stop() if with_clocks else None
         c.close()
-        tot = float(sum(ms))
-        if world > 1:
-            t = torch.tensor([tot], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            tot = float(t.item())
+        tot = max_over_ranks(float(sum(ms)), world)
         return tot, stt, wl, prof[2], clk
 
     # timed region: every step is one CUDA graph (device-side SCF and Hartree loops)
     total_ms, st, wall, launches, clocks = run_path(prec, args.steps, True)
     rep_passes = int(st["passes"].sum())
     terms_total = int(st["terms_sum"].sum())
-    value = world * args.steps / (total_ms * 1e-3)
+    value = job_throughput(args.steps, world, total_ms)
     ms_per_step = total_ms / args.steps
     other = rmgtd.PREC_FP64 if prec == rmgtd.PREC_MIXED else rmgtd.PREC_MIXED
     o_ms, o_st, _, _, _ = run_path(other, args.steps, False)
@@ -465,6 +479,72 @@ def run_ours(args):
     return 0
 
 
+def run_batch8(args):
+    """The batched workload: eight clusters (20-150 atoms, 48^3-96^3), three kicks each,
+    stepped by one CUDA graph per time step (rmgtd_batch), against the same contexts stepped
+    one after another; mixed path, launch configurations from the autotuner."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2410_09189_gb300 import inputs, rmgtd
+
+    def make():
+        out = []
+        for i in range(8):
+            s = inputs.cluster(i)
+            raw = inputs.smooth_random_orbitals(s).reshape(s.N, s.Ng)
+            c = rmgtd.Context(s, raw, nrep=3, H_thrs=1e-7, dP_thrs=1e-10, poisson_tol=1e-10,
+                              precision=rmgtd.PREC_MIXED, use_graph=True)
+            for a in range(3):
+                c.kick(a, a, 1e-3)
+            out.append(c)
+        return out
+
+    t0 = time.perf_counter()
+    ctxs = make()
+    setup_s = time.perf_counter() - t0
+    choices = [c.autotune() for c in ctxs]
+    stream = torch.cuda.current_stream()
+
+    def timed(step_all):
+        for _ in range(args.warmup):
+            step_all(1)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = step_all(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), st
+
+    seq_ms, seq_st = timed(lambda k: [c.step(k) for c in ctxs])
+    batch = rmgtd.Batch(ctxs)
+    bat_ms, bat_st = timed(lambda k: batch.step(k))
+    batch.close()
+    passes = float(np.mean([st["passes"].mean() for st in bat_st]))
+    for c in ctxs:
+        c.close()
+    grid_pts = sum(inputs.cluster(i).Ng * inputs.cluster(i).N for i in range(8))
+    out = {"metric": "batched RT-TDDFT time-steps/sec (8 clusters x 3 kicks per step)",
+           "value": args.steps / (bat_ms * 1e-3), "unit": "time-steps/s", "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": bat_ms / args.steps,
+           "higher_is_better": True, "dtype": "f32+f64", "data": "synthetic",
+           "config": {"workload": "clusters-8-(20..150 atoms)-(48^3..96^3)-kicks-xyz",
+                      "clusters": [{"atoms": int(len(inputs.cluster(i).Z)),
+                                    "grid": list(inputs.cluster(i).n), "N": inputs.cluster(i).N}
+                                   for i in range(8)],
+                      "precision": "mixed", "H_thrs": 1e-7, "initial_state": "P0 = diag(f)"},
+           "one_graph_per_step": {"value": args.steps / (bat_ms * 1e-3)},
+           "contexts_one_after_another": {"value": args.steps / (seq_ms * 1e-3),
+                                          "ms_per_step": seq_ms / args.steps},
+           "grid_point_orbital_updates_per_s": grid_pts * 3 * args.steps / (bat_ms * 1e-3),
+           "scf_passes_per_replica_step": passes, "setup_s": setup_s,
+           "autotune_choices": choices}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -475,11 +555,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true",
                     help="skip training and timing the learned SCF seed")
+    ap.add_argument("--batch8", action="store_true",
+                    help="time the batched workload of eight clusters instead")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.batch8:
+        return run_batch8(args)
     return run_ours(args)
 
 

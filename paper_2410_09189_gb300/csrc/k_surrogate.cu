@@ -272,28 +272,32 @@ __global__ void k_to_bf16(int P, const float* __restrict__ theta, __nv_bfloat16*
 }
 
 // ---- features and targets ---------------------------------------------------------------
-__global__ void k_features(long n, int nrep, long stride, const double* __restrict__ r0,
+// x = (rho_t / s0, (rho_t - rho_{t-1}) / s1, (rho_t - 2 rho_{t-1} + rho_{t-2}) / s2); the
+// scales arrive as reciprocals (float64 division is slow on this GPU), replica r at r * stride
+__global__ void k_features(int n, int nrep, long stride, const double* __restrict__ r0,
                            const double* __restrict__ r1, const double* __restrict__ r2,
-                           double s0, double s1, double s2, float* __restrict__ x,
+                           double i0, double i1, double i2, float* __restrict__ x,
                            double* __restrict__ save) {
-  const long total = n * nrep;
-  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
-       e += (long)gridDim.x * blockDim.x) {
-    const long rep = e / n, g = e - rep * n;
-    const long o = rep * stride + g;
-    const double a = r0[o], b = r1[o], c = r2[o];
-    float* xr = x + rep * 3 * n;
-    xr[g] = (float)(a / s0);
-    xr[n + g] = (float)((a - b) / s1);
-    xr[2 * n + g] = (float)((a - 2.0 * b + c) / s2);
-    if (save) save[o] = a;
+  for (int rep = blockIdx.y; rep < nrep; rep += gridDim.y) {
+    const double* a0 = r0 + rep * stride;
+    const double* a1 = r1 + rep * stride;
+    const double* a2 = r2 + rep * stride;
+    float* xr = x + (long)rep * 3 * n;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n; g += gridDim.x * blockDim.x) {
+      const double a = a0[g], b = a1[g], c = a2[g];
+      const double d1 = a - b;
+      xr[g] = (float)(a * i0);
+      xr[n + g] = (float)(d1 * i1);
+      xr[2 * n + g] = (float)((d1 - (b - c)) * i2);
+      if (save) save[rep * stride + g] = a;
+    }
   }
 }
 
-__global__ void k_targets(long n, const double* __restrict__ v0, const double* __restrict__ v1,
-                          const double* __restrict__ v2, double s, float* __restrict__ t) {
-  for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < n; g += (long)gridDim.x * blockDim.x)
-    t[g] = (float)((v0[g] - 2.0 * v1[g] + v2[g]) / s);
+__global__ void k_targets(int n, const double* __restrict__ v0, const double* __restrict__ v1,
+                          const double* __restrict__ v2, double inv_s, float* __restrict__ t) {
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n; g += gridDim.x * blockDim.x)
+    t[g] = (float)(((v0[g] - v1[g]) - (v1[g] - v2[g])) * inv_s);
 }
 
 // dV = s_out * y into float32 (mixed path) or float64 (float64 path)
@@ -428,9 +432,9 @@ int net_predict(rmgtd_ctx* ctx) {
   const long Ng = ctx->Ng;
   const int nrep = ctx->nrep;
   const int bl = (int)std::max<long>(1, std::min<long>(ceil_div(Ng * nrep, 256L), 8L * ctx->num_sms));
-  k_features<<<bl, 256, 0, ctx->stream>>>(Ng, nrep, Ng, ctx->rho, ctx->rho_h1, ctx->rho_h2,
-                                          n->in_scale[0], n->in_scale[1], n->in_scale[2],
-                                          ctx->net_x, ctx->rho_start);
+  k_features<<<dim3(std::max(1, bl / nrep), nrep), 256, 0, ctx->stream>>>(
+      (int)Ng, nrep, Ng, ctx->rho, ctx->rho_h1, ctx->rho_h2, 1.0 / n->in_scale[0],
+      1.0 / n->in_scale[1], 1.0 / n->in_scale[2], ctx->net_x, ctx->rho_start);
   ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_features");
   int rc = net_forward_on(n, ctx->net_x, ctx->net_y, nrep, ctx->stream, false, true, ctx->status);
@@ -587,8 +591,8 @@ int rmgtd_net_features(rmgtd_net* n, const double* rho_t, const double* rho_tm1,
   if (!n || !rho_t || !rho_tm1 || !rho_tm2 || !x_dev)
     return net_err(RMGTD_EINVAL, "net_features: NULL argument");
   k_features<<<grid_for(n, n->Ng, 256), 256, 0, n->stream>>>(
-      n->Ng, 1, n->Ng, rho_t, rho_tm1, rho_tm2, n->in_scale[0], n->in_scale[1], n->in_scale[2],
-      x_dev, nullptr);
+      (int)n->Ng, 1, n->Ng, rho_t, rho_tm1, rho_tm2, 1.0 / n->in_scale[0], 1.0 / n->in_scale[1],
+      1.0 / n->in_scale[2], x_dev, nullptr);
   NET_LAUNCH("k_features");
   return RMGTD_OK;
 }
@@ -596,7 +600,8 @@ int rmgtd_net_features(rmgtd_net* n, const double* rho_t, const double* rho_tm1,
 int rmgtd_net_targets(rmgtd_net* n, const double* v_tp1, const double* v_t, const double* v_tm1,
                       float* t_dev) {
   if (!n || !v_tp1 || !v_t || !v_tm1 || !t_dev) return net_err(RMGTD_EINVAL, "net_targets: NULL argument");
-  k_targets<<<grid_for(n, n->Ng, 256), 256, 0, n->stream>>>(n->Ng, v_tp1, v_t, v_tm1, n->out_scale, t_dev);
+  k_targets<<<grid_for(n, n->Ng, 256), 256, 0, n->stream>>>((int)n->Ng, v_tp1, v_t, v_tm1,
+                                                            1.0 / n->out_scale, t_dev);
   NET_LAUNCH("k_targets");
   return RMGTD_OK;
 }

@@ -119,8 +119,9 @@ def test_hartree_and_xc(torch_dev):
         vxc = torch.empty_like(rd)
         exc = torch.empty_like(rd)
         ctx.xc(rd, vxc, exc)
-        assert _rel(vxc.cpu().numpy(), vref) < 1e-13
-        assert _rel(exc.cpu().numpy(), eref) < 1e-13
+        # one float64 Newton step from float32 seeds: <= 2^-43 relative per root (see k_lda)
+        assert _rel(vxc.cpu().numpy(), vref) < 1e-12
+        assert _rel(exc.cpu().numpy(), eref) < 1e-12
         # a second solve warm-started from the answer converges at once to the same V
         ctx.hartree(rd, vh)
         assert _rel(vh.cpu().numpy(), ref.ravel()) < 1e-10
