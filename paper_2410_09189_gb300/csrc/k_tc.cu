@@ -165,23 +165,27 @@ k_rho_tc(int N, int Np, int Ng, int nr, const float* __restrict__ phi,
   const uint32_t idesc = idesc_tf32(kM, ncols_used);
   const int ntiles = (Ng + kM - 1) / kM;
   uint32_t phase = 0;
+  // this thread's point of the next tile, prefetched into registers while the MMAs and the
+  // epilogue of the current tile run
+  float pf[kK];
+  auto load_tile = [&](int t) {
+    const int g = t * kM + tid;
+#pragma unroll
+    for (int k = 0; k < kK; ++k) pf[k] = (k < N && g < Ng) ? phi[(long)k * Ng + g] : 0.0f;
+  };
+  if ((int)blockIdx.x < ntiles) load_tile(blockIdx.x);
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int g0 = t * kM;
     // stage the orbital tile: thread <-> point, rows of 4 orbitals as 16-byte stores
     {
       const int p = tid;
-      const int g = g0 + p;
 #pragma unroll
       for (int kc = 0; kc < kK; kc += 4) {
         float4 h4, l4;
-        float* hp = &h4.x;
-        float* lp = &l4.x;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const int k = kc + c;
-          const float v = (k < N && g < Ng) ? phi[(long)k * Ng + g] : 0.0f;
-          split_tf32(v, hp[c], lp[c]);
-        }
+        split_tf32(pf[kc], h4.x, l4.x);
+        split_tf32(pf[kc + 1], h4.y, l4.y);
+        split_tf32(pf[kc + 2], h4.z, l4.z);
+        split_tf32(pf[kc + 3], h4.w, l4.w);
         *reinterpret_cast<float4*>(&a_hi[kmaj(p, kc)]) = h4;
         *reinterpret_cast<float4*>(&a_lo[kmaj(p, kc)]) = l4;
       }
@@ -200,6 +204,7 @@ k_rho_tc(int N, int Np, int Ng, int nr, const float* __restrict__ phi,
       }
       mma_commit(&bar);
     }
+    if (t + (int)gridDim.x < ntiles) load_tile(t + gridDim.x);
     const bool ok = mbar_wait(&bar, phase);
     phase ^= 1u;
     if (__syncthreads_or(!ok)) {
