@@ -201,6 +201,15 @@ int rmgtd_hartree(rmgtd_ctx* ctx, const double* rho_dev, double* vh_dev);
 int rmgtd_xc(rmgtd_ctx* ctx, const double* rho_dev, double* vxc_dev, double* exc_dev,
              size_t n);
 
+/* The mixed path's xc increment (Algorithm 1 line 26 with the fields kept as float32
+ * increments against the set-up state): dvxc_dev[g] = V_xc(rho0_dev[g] + drho_dev[g]) -
+ * V_xc(rho0_dev[g]) for the LDA of rmgtd_xc, on n device points (rho0 double, drho and the
+ * result float).  Evaluated in float32 arithmetic on the increment, so the error is a few
+ * float32 units of the increment itself; points near the density floor or across r_s = 1 take
+ * two float64 evaluations.  Arrays belong to the caller.  Errors: RMGTD_EINVAL. */
+int rmgtd_xc_increment(rmgtd_ctx* ctx, const double* rho0_dev, const float* drho_dev,
+                       float* dvxc_dev, size_t n);
+
 /* Checkpoint / resume of the propagation state (t, step count, P, H_0, H_-1, V_H of every
  * replica) to a binary file.  rmgtd_load requires a context created for the same system. */
 int rmgtd_save(rmgtd_ctx* ctx, const char* path);
@@ -241,6 +250,14 @@ int rmgtd_profile_counters(rmgtd_ctx* ctx, long long* hartree_solves,
  * level (other reduction orders).  choice (may be NULL) receives {density CTAs per SM, Gram
  * on tensor cores (0/1), Gram CTAs per SM, Hartree block divisor}.  Synchronises. */
 int rmgtd_autotune(rmgtd_ctx* ctx, int choice[4]);
+
+/* Set / read the launch configuration directly, in rmgtd_autotune's order: density CTAs per
+ * SM in 1..4, Gram on tensor cores 0/1 (used when Ng is a multiple of 4, else the SIMT
+ * kernel runs), Gram CTAs per SM in {1, 2, 4, 8} (the tensor-core kernel uses at most 2),
+ * Hartree block divisor in {1, 2, 4}.  Out-of-range values: RMGTD_EINVAL, nothing changed;
+ * a context in a batch: RMGTD_ESTATE.  Results may change at rounding level. */
+int rmgtd_set_tuning(rmgtd_ctx* ctx, const int choice[4]);
+int rmgtd_get_tuning(const rmgtd_ctx* ctx, int choice[4]);
 
 /* Several contexts (different systems, each with its replicas) stepped by one CUDA graph per
  * time step: their steps are captured back to back into a single graph, launched once per

@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <initializer_list>
 #include <string>
 
 #include "rmgtd_internal.cuh"
@@ -200,7 +201,10 @@ int dft_eval(rmgtd_ctx* ctx, const double* S, const RepCtl* ctl, unsigned long l
   const int nrep = ctx->nrep;
   const int mixed = ctx->mixed;
   ph_begin(ctx, PH_RHO);
-  int rc = mixed ? rho_dev_mixed(ctx, S, ctx->rho, ctl, nrep) : rho_dev(ctx, S, ctx->rho, ctl, nrep);
+  // the mixed pass keeps the density as its float32 increment; the float64 copy is written
+  // only for an attached network, whose features read it
+  int rc = mixed ? rho_dev_mixed(ctx, S, ctx->net ? ctx->rho : nullptr, ctl, nrep)
+                 : rho_dev(ctx, S, ctx->rho, ctl, nrep);
   ph_end(ctx);
   if (rc) return rc;
   if (ctx->hartree_xc) {
@@ -210,9 +214,13 @@ int dft_eval(rmgtd_ctx* ctx, const double* S, const RepCtl* ctl, unsigned long l
     if (rc) return rc;
   }
   ph_begin(ctx, PH_XC);
-  rc = launch_lda(ctx, ctx->rho, ctx->hartree_xc ? ctx->vh : nullptr,
-                  (mixed && ctx->hartree_xc) ? 1 : 0, ctx->vxc, ctx->exc, ctx->vhxc,
-                  mixed ? ctx->dv32 : nullptr, ctx->Ng, ctl, nrep, ctx->Ng, ctx->hartree_xc);
+  if (mixed) {
+    rc = launch_xc_mixed(ctx, ctl, nrep);
+    ctx->fields_stale = 1;
+  } else {
+    rc = launch_lda(ctx, ctx->rho, ctx->hartree_xc ? ctx->vh : nullptr, 0, ctx->vxc, ctx->exc,
+                    ctx->vhxc, nullptr, ctx->Ng, ctl, nrep, ctx->Ng, ctx->hartree_xc);
+  }
   ph_end(ctx);
   if (rc) return rc;
   if (errbits)
@@ -225,6 +233,20 @@ int dft_eval(rmgtd_ctx* ctx, const double* S, const RepCtl* ctl, unsigned long l
               errbits ? ctx->H1 : nullptr, ctl, 1, errbits);
   ph_end(ctx);
   return rc;
+}
+
+// Rebuild the float64 fields of the mixed path from the float32 increments of the last pass:
+// rho = rho_ref + drho, V_H = V_H,ref + dV_H, then V_xc, eps_xc, V_Hxc by the float64 LDA.
+int mixed_fields64(rmgtd_ctx* ctx) {
+  if (!ctx->mixed || !ctx->fields_stale) return RMGTD_OK;
+  int rc = rho_from_increment(ctx);
+  if (rc) return rc;
+  rc = launch_lda(ctx, ctx->rho, ctx->hartree_xc ? ctx->vh : nullptr, ctx->hartree_xc ? 1 : 0,
+                  ctx->vxc, ctx->exc, ctx->vhxc, nullptr, ctx->Ng, nullptr, ctx->nrep, ctx->Ng,
+                  ctx->hartree_xc);
+  if (rc) return rc;
+  ctx->fields_stale = 0;
+  return RMGTD_OK;
 }
 
 // Refresh rho / V_H / V_xc / eps_xc from the current P_0 of every replica (no H update),
@@ -242,6 +264,7 @@ int refresh_fields(rmgtd_ctx* ctx) {
                   ctx->mixed ? ctx->dv32 : nullptr, ctx->Ng, nullptr, ctx->nrep, ctx->Ng,
                   ctx->hartree_xc);
   if (rc) return rc;
+  ctx->fields_stale = 0;
   if (ctx->net) {
     rc = net_history_reset(ctx);
     if (rc) return rc;
@@ -517,6 +540,7 @@ static int create_impl(const rmgtd_system* sys, const rmgtd_options* opt, rmgtd_
     // reference state of the mixed path: the float64 set-up state (all replicas start in it)
     const size_t fsz = sizeof(float) * Ng;
     ctx->phi32 = (float*)A(fsz * N);
+    ctx->phi32t = (float*)A(sizeof(float) * 32 * ((N + 31) / 32) * 32 * ((Ng + 31) / 32));
     ctx->Sref = (double*)A(msz);
     ctx->Href = (double*)A(msz);
     ctx->rho_ref = (double*)A(gsz);
@@ -537,17 +561,22 @@ static int create_impl(const rmgtd_system* sys, const rmgtd_options* opt, rmgtd_
     ctx->pcg32_Ap = (float*)A(fsz * nrep);
     ctx->pcg32_Az = (float*)A(fsz * nrep);
     ctx->drho32 = (float*)A(fsz * nrep);
+    ctx->rho_ref32 = (float*)A(fsz);
     ctx->ghost32 = (float*)A(fsz * 4);
-    if (!ctx->phi32 || !ctx->pcg32_Az || !ctx->dvh32 || !ctx->Href || !ctx->vh_ref ||
-        !ctx->drho32 || !ctx->ghost32)
+    if (!ctx->phi32 || !ctx->phi32t || !ctx->pcg32_Az || !ctx->dvh32 || !ctx->Href || !ctx->vh_ref ||
+        !ctx->drho32 || !ctx->ghost32 || !ctx->rho_ref32)
       return set_error(ctx, RMGTD_ENOMEM, "mixed-precision buffers");
     rc = to_float(ctx, ctx->phi, ctx->phi32, (long)N * Ng);
+    if (rc) return rc;
+    rc = tile_orbitals(ctx);
     if (rc) return rc;
     rc = to_float(ctx, ctx->ghost, ctx->ghost32, 4L * Ng);
     if (rc) return rc;
     RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->Sref, ctx->S0, msz, cudaMemcpyDeviceToDevice, ctx->stream));
     RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->Href, ctx->H0, msz, cudaMemcpyDeviceToDevice, ctx->stream));
     RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->rho_ref, ctx->rho, gsz, cudaMemcpyDeviceToDevice, ctx->stream));
+    rc = to_float(ctx, ctx->rho, ctx->rho_ref32, Ng);
+    if (rc) return rc;
     RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->vh_ref, ctx->vh, gsz, cudaMemcpyDeviceToDevice, ctx->stream));
     RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->vref, ctx->vhxc, gsz, cudaMemcpyDeviceToDevice, ctx->stream));
     RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->dvh32, 0, fsz * nrep, ctx->stream));
@@ -600,6 +629,10 @@ int rmgtd_apply_h(rmgtd_ctx* ctx, const void* x, void* hx, int ncols, int dtype,
   if (!ctx) return set_error(nullptr, RMGTD_EINVAL, "ctx is NULL");
   if (!x || !hx || ncols < 1 || rep < -1 || rep >= ctx->nrep)
     return set_error(ctx, RMGTD_EINVAL, "apply_h: bad arguments");
+  if (rep >= 0) {
+    const int rc = mixed_fields64(ctx);
+    if (rc) return rc;
+  }
   const double* vextra = (rep >= 0) ? ctx->vhxc + (long)rep * ctx->Ng : nullptr;
   return apply_h_dev(ctx, x, hx, ncols, dtype, vextra);
 }
@@ -774,6 +807,7 @@ int rmgtd_step(rmgtd_ctx* ctx, int nsteps, rmgtd_stats* stats) {
     if (rc) return rc;
   }
   RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->failed, 0, sizeof(int), ctx->stream));
+  if (ctx->mixed && nsteps > 0) ctx->fields_stale = 1;
   int done_total = 0;
   while (done_total < nsteps) {
     const int chunk = std::min(nsteps - done_total, ctx->stats_cap);
@@ -915,7 +949,42 @@ int rmgtd_autotune(rmgtd_ctx* ctx, int choice[4]) {
   return RMGTD_OK;
 }
 
-// ---- several systems in one graph per step (SURVEY a14's batched launch) --------------------
+int rmgtd_set_tuning(rmgtd_ctx* ctx, const int choice[4]) {
+  if (!ctx) return set_error(nullptr, RMGTD_EINVAL, "ctx is NULL");
+  if (!choice) return set_error(ctx, RMGTD_EINVAL, "set_tuning: choice is NULL");
+  if (ctx->in_batch) return set_error(ctx, RMGTD_ESTATE, "set_tuning: context belongs to a batch");
+  const auto one_of = [](int v, std::initializer_list<int> s) {
+    for (int x : s)
+      if (v == x) return true;
+    return false;
+  };
+  if (choice[0] < 1 || choice[0] > 4 || !one_of(choice[1], {0, 1}) ||
+      !one_of(choice[2], {1, 2, 4, 8}) || !one_of(choice[3], {1, 2, 4}))
+    return set_error(ctx, RMGTD_EINVAL, "set_tuning: value out of range");
+  RMGTD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  ctx->tune_rho_blocks = choice[0];
+  ctx->tune_gram_tc = choice[1];
+  ctx->tune_gram_blocks = choice[2];
+  ctx->tune_coop_div = choice[3];
+  // launch configurations are baked into the step graph: rebuild it
+  if (ctx->step_exec) cudaGraphExecDestroy(ctx->step_exec);
+  if (ctx->step_graph) cudaGraphDestroy(ctx->step_graph);
+  ctx->step_exec = nullptr;
+  ctx->step_graph = nullptr;
+  return RMGTD_OK;
+}
+
+int rmgtd_get_tuning(const rmgtd_ctx* ctx, int choice[4]) {
+  if (!ctx) return set_error(nullptr, RMGTD_EINVAL, "ctx is NULL");
+  if (!choice) return RMGTD_EINVAL;
+  choice[0] = ctx->tune_rho_blocks;
+  choice[1] = ctx->tune_gram_tc;
+  choice[2] = ctx->tune_gram_blocks;
+  choice[3] = ctx->tune_coop_div;
+  return RMGTD_OK;
+}
+
+// ---- several systems in one graph per step (batched launch of independent systems) ---------
 struct rmgtd_batch {
   std::vector<rmgtd_ctx*> ctxs;
   cudaStream_t stream = nullptr;     // the contexts' common stream (launch stream)
@@ -992,6 +1061,7 @@ int rmgtd_batch_step(rmgtd_batch* b, int nsteps, rmgtd_stats* const* stats) {
   for (auto* c : b->ctxs) {
     cap = std::min(cap, c->stats_cap);
     RMGTD_CUDA(c, cudaMemsetAsync(c->failed, 0, sizeof(int), b->stream));
+    if (c->mixed && nsteps > 0) c->fields_stale = 1;
   }
   int done_total = 0;
   while (done_total < nsteps) {
@@ -1100,7 +1170,9 @@ int rmgtd_attach_net(rmgtd_ctx* ctx, rmgtd_net* net) {
   ctx->step_exec = nullptr;
   ctx->step_graph = nullptr;
   if (net) {
-    int rc = net_history_reset(ctx);
+    int rc = mixed_fields64(ctx);   // the history starts from the current float64 density
+    if (rc) return rc;
+    rc = net_history_reset(ctx);
     if (rc) return rc;
   }
   RMGTD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
@@ -1112,6 +1184,8 @@ int rmgtd_get_field(rmgtd_ctx* ctx, int which, int rep, double* dev_out) {
   if (rep < 0 || rep >= ctx->nrep || !dev_out) return set_error(ctx, RMGTD_EINVAL, "get_field: bad arguments");
   const double* src = which == RMGTD_FIELD_RHO ? ctx->rho : which == RMGTD_FIELD_VHXC ? ctx->vhxc : nullptr;
   if (!src) return set_error(ctx, RMGTD_EINVAL, "get_field: unknown field");
+  const int rc = mixed_fields64(ctx);
+  if (rc) return rc;
   RMGTD_CUDA(ctx, cudaMemcpyAsync(dev_out, src + (long)rep * ctx->Ng, sizeof(double) * ctx->Ng,
                                   cudaMemcpyDeviceToDevice, ctx->stream));
   RMGTD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
@@ -1150,7 +1224,9 @@ int rmgtd_dipole(rmgtd_ctx* ctx, int rep, double mu[3]) {
 int rmgtd_energy(rmgtd_ctx* ctx, int rep, double* E) {
   if (!ctx) return set_error(nullptr, RMGTD_EINVAL, "ctx is NULL");
   if (rep < 0 || rep >= ctx->nrep || !E) return set_error(ctx, RMGTD_EINVAL, "energy: bad arguments");
-  int rc = fetch_obs(ctx);
+  int rc = mixed_fields64(ctx);
+  if (rc) return rc;
+  rc = fetch_obs(ctx);
   if (rc) return rc;
   *E = ctx->obs_host[8 * rep + 4];
   return RMGTD_OK;
@@ -1223,6 +1299,17 @@ int rmgtd_xc(rmgtd_ctx* ctx, const double* rho_dev, double* vxc_dev, double* exc
   return RMGTD_OK;
 }
 
+int rmgtd_xc_increment(rmgtd_ctx* ctx, const double* rho0_dev, const float* drho_dev,
+                       float* dvxc_dev, size_t n) {
+  if (!ctx) return set_error(nullptr, RMGTD_EINVAL, "ctx is NULL");
+  if (!rho0_dev || !drho_dev || !dvxc_dev || n == 0)
+    return set_error(ctx, RMGTD_EINVAL, "xc_increment: bad arguments");
+  int rc = launch_xc_increment(ctx, rho0_dev, drho_dev, dvxc_dev, (long)n);
+  if (rc) return rc;
+  RMGTD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return RMGTD_OK;
+}
+
 int rmgtd_time(rmgtd_ctx* ctx, double* t, long long* steps) {
   if (!ctx) return set_error(nullptr, RMGTD_EINVAL, "ctx is NULL");
   if (t) *t = ctx->t;
@@ -1238,6 +1325,8 @@ int rmgtd_save(rmgtd_ctx* ctx, const char* path) {
   const long NN = (long)ctx->N * ctx->N;
   const size_t mcount = (size_t)NN * ctx->nrep, gcount = (size_t)ctx->Ng * ctx->nrep;
   std::vector<double> buf(4 * mcount + gcount);
+  const int rc = mixed_fields64(ctx);
+  if (rc) return rc;
   double* parts[4] = {ctx->S0, ctx->A0, ctx->H0, ctx->Hm1};
   for (int i = 0; i < 4; ++i)
     RMGTD_CUDA(ctx, cudaMemcpyAsync(buf.data() + i * mcount, parts[i], sizeof(double) * mcount,
@@ -1326,6 +1415,7 @@ int rmgtd_load(rmgtd_ctx* ctx, const char* path) {
                   ctx->vhxc, ctx->mixed ? ctx->dv32 : nullptr, ctx->Ng, nullptr, ctx->nrep,
                   ctx->Ng, ctx->hartree_xc);
   if (rc) return rc;
+  ctx->fields_stale = 0;
   RMGTD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   return RMGTD_OK;
 }

@@ -399,6 +399,129 @@ __device__ __forceinline__ void lda_point(double rho, double& vxc, double& exc) 
   exc = ex + ec;
 }
 
+// Increment V_xc(rho0 + d) - V_xc(rho0) of the mixed path in float32 arithmetic on the
+// increment itself.  Every difference of the functional is rewritten as d times a smooth
+// factor, so float32 rounding is relative to the increment, not to V_xc:
+//   c = rho^(1/3):  c - c0 = d / (c^2 + c c0 + c0^2)            (c^3 - c0^3 = d)
+//   r_s = k / c:    r_s - r_s0 = -k (c - c0) / (c c0)
+//   r_s >= 1:  V_c = gamma Nn / Dd^2, Nn = 1 + 7/6 b1 s + 4/3 b2 r_s, Dd = 1 + b1 s + b2 r_s,
+//              s = sqrt(r_s), s - s0 = (r_s - r_s0) / (s + s0),
+//              Nn/Dd^2 - Nn0/Dd0^2 = (dNn Dd0^2 - Nn0 dDd (Dd + Dd0)) / (Dd^2 Dd0^2)
+//   r_s <  1:  V_c = A ln r_s + (B - A/3) + 2/3 C r_s ln r_s + (2D - C)/3 r_s,
+//              ln r_s - ln r_s0 = log1p((r_s - r_s0) / r_s0),
+//              r_s ln r_s - r_s0 ln r_s0 = (r_s - r_s0) ln r_s + r_s0 (ln r_s - ln r_s0)
+// (the PZ81 potential of lda_point, V_c = eps_c - (r_s/3) d eps_c/d r_s, regrouped).  Points
+// within a factor 2 of the density floor or whose two densities sit on different sides of
+// r_s = 1 (or within float32 rounding of it) take both float64 evaluations instead; points
+// whose two densities are both well below the floor give 0.
+// r0 = (float)rho0 (rounded to nearest); rho0 itself is read only on the float64 path.
+__device__ __forceinline__ float dvxc_increment(const double* rho0p, float r0, float d) {
+  constexpr float kC3pi = 0.98474502f, kCrs = 0.62035049f;
+  constexpr float b1 = 1.0529f, b2 = 0.3334f, gam = -0.1423f;
+  constexpr float A = 0.0311f, C = 0.0020f, D = -0.0116f;
+  // the floor decision of float64 is certain outside +-1e-4 of the floor (float32 rounding
+  // of r0 and r1 is ~1e-7 relative)
+  constexpr float kLo = (float)(kRhoFloor * (1.0 - 1e-4)), kHi = (float)(kRhoFloor * (1.0 + 1e-4));
+  const float r1 = r0 + d;
+  // both densities below the floor (vacuum): V_xc = 0 on both sides
+  if (r0 < kLo && r1 < kLo) return 0.0f;
+  bool easy = r0 > kHi && r1 > kHi;
+  float out = 0.0f;
+  if (easy) {
+    const float c0 = cbrtf(r0), c1 = cbrtf(r1);
+    const float dc = d / (c1 * c1 + c1 * c0 + c0 * c0);
+    const float rs0 = kCrs / c0, rs1 = kCrs / c1;
+    const float drs = -kCrs * dc / (c1 * c0);
+    const bool hi0 = rs0 >= 1.0f;
+    easy = (hi0 == (rs1 >= 1.0f)) && fabsf(rs0 - 1.0f) > 1e-5f && fabsf(rs1 - 1.0f) > 1e-5f;
+    float dvc;
+    if (hi0) {
+      const float s0 = sqrtf(rs0), s1 = sqrtf(rs1);
+      const float ds = drs / (s1 + s0);
+      const float D0 = 1.0f + b1 * s0 + b2 * rs0, D1 = 1.0f + b1 * s1 + b2 * rs1;
+      const float N0 = 1.0f + (7.0f / 6.0f) * b1 * s0 + (4.0f / 3.0f) * b2 * rs0;
+      const float dN = (7.0f / 6.0f) * b1 * ds + (4.0f / 3.0f) * b2 * drs;
+      const float dD = b1 * ds + b2 * drs;
+      dvc = gam * (dN * D0 * D0 - N0 * dD * (D1 + D0)) / (D1 * D1 * D0 * D0);
+    } else {
+      const float lr0 = logf(rs0);
+      const float dlr = log1pf(drs / rs0);
+      dvc = A * dlr + (2.0f / 3.0f) * C * (drs * (lr0 + dlr) + rs0 * dlr) +
+            ((2.0f * D - C) / 3.0f) * drs;
+    }
+    out = -kC3pi * dc + dvc;
+  }
+  if (!easy) {
+    const double rho0 = *rho0p;
+    double v1, v0, e;
+    lda_point(rho0 + (double)d, v1, e);
+    lda_point(rho0, v0, e);
+    out = (float)(v1 - v0);
+  }
+  return out;
+}
+
+// Mixed-path potential correction of one pass: dv = dV_H + (V_xc(rho0 + drho) - V_xc(rho0)),
+// float32 throughout (the float64 fields are rebuilt from the increments when read).  The
+// set-up state gives V_ref = V_H,ref + V_xc(rho0) exactly, so no further term enters.
+// rho0f: float32 copy of rho0 (NULL: rounded here).
+__global__ void k_xc_mixed(const double* __restrict__ rho0, const float* __restrict__ rho0f,
+                           const float* __restrict__ drho, const float* __restrict__ dvh,
+                           float* __restrict__ dv32, long n, const RepCtl* __restrict__ ctl,
+                           long stride, int with_xc, int with_h) {
+  const int rep = blockIdx.y;
+  if (ctl && !ctl[rep].active) return;
+  const long o = rep * stride;
+  for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < n;
+       g += (long)gridDim.x * blockDim.x) {
+    float v = 0.0f;
+    if (with_xc) v = dvxc_increment(rho0 + g, rho0f ? rho0f[g] : (float)rho0[g], drho[o + g]);
+    if (with_h) v += dvh[o + g];
+    dv32[o + g] = v;
+  }
+}
+
+int launch_xc_mixed(rmgtd_ctx* ctx, const RepCtl* ctl, int nrep) {
+  const long n = ctx->Ng;
+  const int blocks = (int)std::min<long>(ceil_div(n, kThreads), 4L * ctx->num_sms);
+  k_xc_mixed<<<dim3(std::max(blocks, 1), nrep), kThreads, 0, ctx->stream>>>(
+      ctx->rho_ref, ctx->rho_ref32, ctx->drho32, ctx->dvh32, ctx->dv32, n, ctl, n,
+      ctx->hartree_xc, ctx->hartree_xc);
+  ++ctx->launches;
+  RMGTD_LAUNCH(ctx, "k_xc_mixed");
+  return RMGTD_OK;
+}
+
+// rho[r][g] = rho_ref[g] + drho[r][g] for every replica (the float64 density of the mixed
+// path, rebuilt from its increment; identical to what the density kernels write).
+__global__ void k_rho_from_inc(const double* __restrict__ rho_ref, const float* __restrict__ drho,
+                               double* __restrict__ rho, long n) {
+  const long o = blockIdx.y * n;
+  for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < n;
+       g += (long)gridDim.x * blockDim.x)
+    rho[o + g] = rho_ref[g] + (double)drho[o + g];
+}
+
+int rho_from_increment(rmgtd_ctx* ctx) {
+  const long n = ctx->Ng;
+  const int blocks = (int)std::min<long>(ceil_div(n, kThreads), 4L * ctx->num_sms);
+  k_rho_from_inc<<<dim3(std::max(blocks, 1), ctx->nrep), kThreads, 0, ctx->stream>>>(
+      ctx->rho_ref, ctx->drho32, ctx->rho, n);
+  ++ctx->launches;
+  RMGTD_LAUNCH(ctx, "k_rho_from_inc");
+  return RMGTD_OK;
+}
+
+// Stand-alone increment (parity tests): dv[g] = V_xc(rho0[g] + d[g]) - V_xc(rho0[g]).
+int launch_xc_increment(rmgtd_ctx* ctx, const double* rho0, const float* d, float* dv, long n) {
+  const int blocks = (int)std::min<long>(ceil_div(n, kThreads), 4L * ctx->num_sms);
+  k_xc_mixed<<<dim3(std::max(blocks, 1), 1), kThreads, 0, ctx->stream>>>(
+      rho0, nullptr, d, nullptr, dv, n, nullptr, n, 1, 0);
+  ++ctx->launches;
+  RMGTD_LAUNCH(ctx, "k_xc_mixed");
+  return RMGTD_OK;
+}
+
 __global__ void k_lda(const double* __restrict__ rho, double* __restrict__ vh, int vh_mode,
                       const double* __restrict__ vh_ref, float* __restrict__ dvh32,
                       double* __restrict__ vxc, double* __restrict__ exc,

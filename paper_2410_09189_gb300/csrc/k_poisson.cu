@@ -38,7 +38,7 @@ constexpr int kPre = 2, kPost = 2, kCoarseSweeps = 40;
 static_assert(kPre == 2, "the pre-smoothing pass fuses exactly two sweeps from zero");
 // relative residual of the float32 correction solve of the mixed path: the unknown is the
 // change of V_H relative to the reference potential (|dV_H| ~ 1e-3 after a 1e-3 kick), so
-// 3e-6 of it is ~3e-9 absolute -- far below the SCF threshold H_thrs that judges the step
+// 3e-6 of it is ~3e-9 absolute -- far below the SCF threshold H_thrs that decides the step
 constexpr double kMixedPoissonTol = 3e-6;
 
 struct Grid3 {

@@ -2,6 +2,7 @@
 // dipole and overlap matrices), the density rho = sum_ij Re(P)_ij phi_i phi_j, the
 // commutator expansion of exp(Omega) P exp(Omega^dagger) (Eqs. 19, 33, 35), observables and
 // the SCF control word.  All float64.
+#include <cooperative_groups.h>
 #include <math.h>
 
 #include "rmgtd_internal.cuh"
@@ -322,11 +323,11 @@ k_rho32(int N, int Np, long Ng, const float* __restrict__ phi, const float* __re
     }
   }
   if (ok0) {
-    rho[rep * rstride + g0] = rho_ref[g0] + (double)r0;
+    if (rho) rho[rep * rstride + g0] = rho_ref[g0] + (double)r0;
     drho[rep * rstride + g0] = r0;
   }
   if (ok1) {
-    rho[rep * rstride + g1] = rho_ref[g1] + (double)r1;
+    if (rho) rho[rep * rstride + g1] = rho_ref[g1] + (double)r1;
     drho[rep * rstride + g1] = r1;
   }
 }
@@ -497,7 +498,6 @@ k_gram32_reduce(int N, int Np, int nsplit, int nrep, const float* __restrict__ p
   const int rep = blockIdx.y;
   if (ctl && !ctl[rep].active) return;
   __shared__ double sh[8][33];
-  __shared__ double shm[32];
   const long NpNp = (long)Np * Np;
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   const long e = (long)blockIdx.x * 32 + lane;
@@ -582,6 +582,27 @@ __global__ void k_to_float(long n, const double* __restrict__ in, float* __restr
   for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n;
        e += (long)gridDim.x * blockDim.x)
     out[e] = (float)in[e];
+}
+
+__global__ void k_tile_orbitals(int N, int Np, long Ng, const float* __restrict__ phi,
+                                float* __restrict__ phit, long n) {
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n;
+       e += (long)gridDim.x * blockDim.x) {
+    const long tile = e / (32L * Np);
+    const int k = (int)((e >> 5) % Np);
+    const long g = tile * 32 + (e & 31);
+    phit[e] = (k < N && g < Ng) ? phi[(long)k * Ng + g] : 0.0f;
+  }
+}
+
+int tile_orbitals(rmgtd_ctx* ctx) {
+  const int Np = ((ctx->N + 31) / 32) * 32;
+  const long n = ceil_div(ctx->Ng, 32L) * Np * 32;
+  const int blocks = (int)std::max<long>(1, std::min<long>(ceil_div(n, 256), 8L * ctx->num_sms));
+  k_tile_orbitals<<<blocks, 256, 0, ctx->stream>>>(ctx->N, Np, ctx->Ng, ctx->phi32, ctx->phi32t, n);
+  ++ctx->launches;
+  RMGTD_LAUNCH(ctx, "k_tile_orbitals");
+  return RMGTD_OK;
 }
 
 int to_float(rmgtd_ctx* ctx, const double* in, float* out, long n) {
@@ -852,6 +873,213 @@ static int launch_eldyn_ts(rmgtd_ctx* ctx, EldynArgs& a) {
   return RMGTD_OK;
 }
 
+// Commutator series of one replica on one thread-block cluster (N <= 64).  The C CTAs of the
+// cluster own consecutive row blocks of the N x N matrices; every CTA keeps a full copy of
+// the current term (S_{k-1}, A_{k-1}) in shared memory, forms its rows of T1 = Hbar A_{k-1}
+// and T2 = Hbar S_{k-1}, and after a cluster barrier reads the transposed entries T1[j][i],
+// T2[j][i] from the owning CTA's shared memory (distributed shared memory), forms its rows of
+// S_k, A_k, adds them to P_1 and writes them into every CTA's copy.  Two cluster barriers per
+// term and no global-memory round trip: the series of every replica runs on its own cluster
+// and the replicas' clusters never wait on one another.  Sums run over m = 0..N-1 in order,
+// as in k_eldyn, so both kernels give the same bits.
+namespace cg = cooperative_groups;
+
+template <int C>
+__global__ void __launch_bounds__(256, 1) k_eldyn_cluster(EldynArgs a) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int rep = blockIdx.y;
+  const int N = a.N;
+  const long NN = (long)N * N;
+  const int rows = (N + C - 1) / C;
+  const int r0 = rank * rows;
+  const int nr = max(0, min(rows, N - r0));   // rows owned by this CTA (may be 0)
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (a.ctl_in && !a.ctl_in[a.rep0 + rep].active) return;   // whole cluster leaves together
+
+  extern __shared__ double smem[];
+  double* Sf = smem;                 // [N][N] current term S_{k-1}
+  double* Af = Sf + NN;              // [N][N] current term A_{k-1}
+  double* Hr = Af + NN;              // [rows][N] Hbar rows
+  double* T1 = Hr + rows * N;        // [rows][N]
+  double* T2 = T1 + rows * N;
+  double* S1r = T2 + rows * N;       // [rows][N] running P_1
+  double* A1r = S1r + rows * N;
+  unsigned long long* mx = reinterpret_cast<unsigned long long*>(A1r + rows * N);  // [C]
+  __shared__ unsigned long long shm[8];
+  __shared__ double c_sh;
+
+  const double* Ha = a.Ha + rep * a.hstride;
+  const double* Hb = a.Hb + rep * a.hstride;
+  const double* S0 = a.S0 + rep * NN;
+  const double* A0 = a.A0 + rep * NN;
+  for (long e = tid; e < NN; e += nt) {
+    Sf[e] = S0[e];
+    Af[e] = A0[e];
+  }
+  for (int e = tid; e < nr * N; e += nt) {
+    const long o = (long)r0 * N + e;
+    Hr[e] = 0.5 * (Ha[o] + Hb[o]);
+    S1r[e] = S0[o];
+    A1r[e] = A0[o];
+  }
+  __syncthreads();
+
+  // GB300's float64 rate is ~1/64 of float32: every float64 instruction of the 256 threads
+  // costs, so the step tau/k is formed once per term and the maxima of the non-negative
+  // |dP_ij|^2 are taken on their bit patterns (integer order = float order; NaN above inf)
+  const unsigned long long thr2 = (unsigned long long)__double_as_longlong(a.thrs * a.thrs);
+  const unsigned long long big = (unsigned long long)__double_as_longlong(1e300);
+  int k = 0;
+  int status = 0;
+  while (true) {
+    ++k;
+    if (tid == 0) c_sh = a.tau / (double)k;
+    // T1 = Hbar A_{k-1}, T2 = Hbar S_{k-1} on the owned rows
+    for (int o = tid; o < 2 * nr * N; o += nt) {
+      const int q = o / (nr * N), e = o - q * nr * N;
+      const int ii = e / N, j = e - ii * N;
+      const double* X = q ? Sf : Af;
+      const double* h = Hr + ii * N;
+      double s = 0.0;
+      for (int m = 0; m < N; ++m) s = fma(h[m], X[m * N + j], s);
+      (q ? T2 : T1)[e] = s;
+    }
+    cluster.sync();
+    // new terms on the owned rows; broadcast into every CTA's copy
+    const double c = c_sh;
+    unsigned long long emax = 0;
+    for (int e = tid; e < nr * N; e += nt) {
+      const int ii = e / N, j = e - ii * N;
+      const int i = r0 + ii;
+      const int oj = j / rows;
+      const int jj = j - oj * rows;
+      const double* T1o = cluster.map_shared_rank(T1, oj);
+      const double* T2o = cluster.map_shared_rank(T2, oj);
+      const double t1ji = T1o[jj * N + i];
+      const double t2ji = T2o[jj * N + i];
+      const double ns = c * (T1[e] + t1ji);
+      const double na = -c * (T2[e] - t2ji);
+      S1r[e] += ns;
+      A1r[e] += na;
+      const double d2 = ns * ns + na * na;   // |dP_ij|^2
+      emax = max(emax, (unsigned long long)__double_as_longlong(d2));
+      const long off = (long)i * N + j;
+      for (int d = 0; d < C; ++d) {
+        cluster.map_shared_rank(Sf, d)[off] = ns;
+        cluster.map_shared_rank(Af, d)[off] = na;
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+    if ((tid & 31) == 0) shm[tid >> 5] = emax;
+    __syncthreads();
+    if (tid == 0) {
+      for (int w = 1; w < (nt >> 5); ++w) emax = max(emax, shm[w]);
+      for (int d = 0; d < C; ++d) cluster.map_shared_rank(mx, d)[rank] = emax;
+    }
+    cluster.sync();
+    unsigned long long err = 0;
+    for (int d = 0; d < C; ++d) err = max(err, mx[d]);
+    bool finished = false;
+    if (err > big) {                   // inf or NaN (or beyond 1e300)
+      status = RMGTD_EDIVERGED;
+      finished = true;
+    } else if (err <= thr2) {
+      finished = true;
+    } else if (k >= a.max_terms) {
+      status = RMGTD_ENOTCONVERGED;
+      finished = true;
+    }
+    if (finished) break;
+  }
+  for (int e = tid; e < nr * N; e += nt) {
+    const long o = rep * NN + (long)r0 * N + e;
+    a.S1[o] = S1r[e];
+    a.A1[o] = A1r[e];
+  }
+  if (rank == 0 && tid == 0) {
+    if (status) atomicCAS(a.status, 0, status);
+    if (a.ctl_out) {
+      RepCtl& cr = a.ctl_out[a.rep0 + rep];
+      if (status) cr.status = status;
+      cr.terms_last = k;
+      cr.terms_sum += k;
+      cr.terms_max = max(cr.terms_max, k);
+    }
+  }
+}
+
+template <int C>
+static int launch_eldyn_cluster(rmgtd_ctx* ctx, EldynArgs& a, size_t smem) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(C, a.nrep);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = ctx->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  void* args[] = {&a};
+  RMGTD_CUDA(ctx, cudaLaunchKernelExC(&cfg, (const void*)k_eldyn_cluster<C>, args));
+  ++ctx->launches;
+  return RMGTD_OK;
+}
+
+static size_t eldyn_cluster_smem(int N, int C) {
+  const int rows = (N + C - 1) / C;
+  return sizeof(double) * (2 * (size_t)N * N + 5 * (size_t)rows * N) +
+         sizeof(unsigned long long) * C;
+}
+
+// Cluster size for the series: 16 CTAs where the device runs such clusters (non-portable
+// size), else 8, else 0 (the cooperative kernel runs).
+static int eldyn_cluster_size(rmgtd_ctx* ctx) {
+  if (ctx->eldyn_cluster >= 0) return ctx->eldyn_cluster;
+  ctx->eldyn_cluster = 0;
+  for (int C : {16, 8}) {
+    const size_t smem = eldyn_cluster_smem(ctx->N, C);
+    const void* fn = C == 16 ? (const void*)k_eldyn_cluster<16> : (const void*)k_eldyn_cluster<8>;
+    if (C == 16 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+                       cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    if ((size_t)fa.maxDynamicSharedSizeBytes < smem &&
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C, 1);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, fn, &cfg) == cudaSuccess && nclusters > 0) {
+      ctx->eldyn_cluster = C;
+      break;
+    }
+    cudaGetLastError();
+  }
+  return ctx->eldyn_cluster;
+}
+
 int eldyn(rmgtd_ctx* ctx, const double* Ha, const double* Hb, long hstride, double tau,
           const double* S0, const double* A0, double* S1, double* A1, const RepCtl* ctl_in,
           RepCtl* ctl_out, int rep0, int nreps) {
@@ -876,7 +1104,13 @@ int eldyn(rmgtd_ctx* ctx, const double* Ha, const double* Hb, long hstride, doub
   a.thrs = ctx->opt.dP_thrs;
   a.bar = ctx->bar;
   a.status = ctx->status;
-  // small tiles for small N: the float64 work of a term spreads over more SMs
+  // N <= 64: one cluster per replica (no grid barrier); else the cooperative kernel, with
+  // small tiles for small N so the float64 work of a term spreads over more SMs
+  if (ctx->N <= 64) {
+    const int C = eldyn_cluster_size(ctx);
+    if (C == 16) return launch_eldyn_cluster<16>(ctx, a, eldyn_cluster_smem(ctx->N, 16));
+    if (C == 8) return launch_eldyn_cluster<8>(ctx, a, eldyn_cluster_smem(ctx->N, 8));
+  }
   if (ctx->N <= 32) return launch_eldyn_ts<4, 64>(ctx, a);
   if (ctx->N <= 64) return launch_eldyn_ts<8, 256>(ctx, a);
   if (ctx->N <= 512) return launch_eldyn_ts<16, 256>(ctx, a);

@@ -17,8 +17,10 @@
 // Shat operand once, and loops over 128-point tiles: stage the orbital tile (transposed
 // to point-major), one thread issues 4 K-steps x 3 products, commits to an mbarrier, all
 // threads wait (bounded), each warp reads its 32 TMEM lanes and forms drho for its points.
+#include <cuda.h>   // CUtensorMap and its enums (the encoder comes from the runtime)
 #include <cuda_bf16.h>
 #include <stdint.h>
+#include <string.h>
 
 #include <algorithm>
 
@@ -119,7 +121,7 @@ __device__ __forceinline__ void fence_async_smem() {
 
 // dynamic shared memory: a_hi, a_lo (128 x 32 floats each), b_hi, b_lo (nr * 32 rows x kK)
 __global__ void __launch_bounds__(kThreadsTc)
-k_rho_tc(int N, int Np, int Ng, int nr, const float* __restrict__ phi,
+k_rho_tc(int N, int Np, int Ng, int nr, const float* __restrict__ phit,
          const float* __restrict__ shat, const double* __restrict__ rho_ref,
          double* __restrict__ rho, float* __restrict__ drho, const RepCtl* __restrict__ ctl,
          int* status) {
@@ -168,10 +170,12 @@ k_rho_tc(int N, int Np, int Ng, int nr, const float* __restrict__ phi,
   // this thread's point of the next tile, prefetched into registers while the MMAs and the
   // epilogue of the current tile run
   float pf[kK];
+  // tiled orbitals: the 32 loads of a warp read one contiguous 4 KB block (zero past N)
   auto load_tile = [&](int t) {
     const int g = t * kM + tid;
+    const float* src = phit + ((long)(g >> 5) * kK) * 32 + (g & 31);
 #pragma unroll
-    for (int k = 0; k < kK; ++k) pf[k] = (k < N && g < Ng) ? phi[(long)k * Ng + g] : 0.0f;
+    for (int k = 0; k < kK; ++k) pf[k] = g < Ng ? src[k * 32] : 0.0f;
   };
   if ((int)blockIdx.x < ntiles) load_tile(blockIdx.x);
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -232,7 +236,7 @@ k_rho_tc(int N, int Np, int Ng, int nr, const float* __restrict__ phi,
 #pragma unroll
       for (int j = 0; j < 32; ++j) acc = fmaf(ph[j], y[j], acc);
       if (g < Ng && (!ctl || ctl[r].active)) {
-        rho[(long)r * Ng + g] = rho_ref[g] + (double)acc;
+        if (rho) rho[(long)r * Ng + g] = rho_ref[g] + (double)acc;
         drho[(long)r * Ng + g] = acc;
       }
     }
@@ -263,7 +267,7 @@ int rho_tc(rmgtd_ctx* ctx, double* rho, float* drho, const RepCtl* ctl, int nrep
   }
   const int ntiles = (int)((ctx->Ng + kM - 1) / kM);
   const int grid = std::min(ntiles, std::max(1, ctx->tune_rho_blocks) * ctx->num_sms);
-  k_rho_tc<<<grid, kThreadsTc, smem, ctx->stream>>>(N, Np, (int)ctx->Ng, nrep, ctx->phi32,
+  k_rho_tc<<<grid, kThreadsTc, smem, ctx->stream>>>(N, Np, (int)ctx->Ng, nrep, ctx->phi32t,
                                                      ctx->shat32, ctx->rho_ref, rho, drho, ctl,
                                                      ctx->status);
   ++ctx->launches;
@@ -271,35 +275,73 @@ int rho_tc(rmgtd_ctx* ctx, double* rho, float* drho, const RepCtl* ctl, int nrep
   return RMGTD_OK;
 }
 
-// ---- Hamiltonian update of the mixed path on the tensor cores ------------------------------
-// C_r[i][j] = sum_g phi_i(g) w_r(g) phi_j(g) for the 32 x 32 tile pair (It, Jt), It <= Jt,
-// of up to four replicas r (Section 3.1's H = H_ref + h^3 Phi^T diag(dV) Phi):
-//   D[(r, i)][j] += sum_k A[(r, i)][k] B[j][k],  A = phi_i w_r (M = 32 nr <= 128 rows),
-//   B = phi_j (N = 32), K = grid points in slabs of 32.
-// Each CTA (256 threads, 40 KB of shared memory, so several CTAs share an SM and hide each
-// other's load latency) reduces a contiguous range of grid points in tensor memory: stage a
-// slab (float32 split hi + lo as for the density), one thread issues 4 K-steps x 3 products
-// and commits, all wait for the MMAs before the slab buffer is restaged.  The float32
-// partial tile goes to part[split][rep][Np][Np] for the float64 reduction of the SIMT path.
 namespace tc {
 
-constexpr int kGKS = 32;                       // grid points per slab (K)
-constexpr int kGRows = 128;                    // A rows (TMEM lanes)
-constexpr int kGAfl = kGRows * kGKS;           // floats per A operand
-constexpr int kGBfl = 32 * kGKS;               // floats per B operand
-constexpr int kThreadsG = 256;
+// ---- float32 Gram partials on the tensor cores ---------------------------------------------
+// H update of the mixed path (Algorithm 1 line 26, Section 3.1's H = h^3 Phi^T (V Phi)):
+//   G_r[i][j] = sum_g (w_r(g) phi_i(g)) phi_j(g)     for the orbital tile pair (It, Jt)
+// as D = A B^T with M = 128 rows (4 replicas x 32 orbitals of tile It, w-weighted), N = 32
+// (orbitals of tile Jt), K = grid points, accumulated in tensor memory over the CTA's chunk
+// of the grid (split-K; k_gram32_reduce adds the chunks in a fixed order).  3xTF32 as in
+// k_rho_tc.  Warp-specialised pipeline over 32-point stages: an issuer warp (one elected
+// thread) keeps a ring of S stages of tiled TMA loads in flight (cp.async.bulk.tensor.2d,
+// completion on an mbarrier per slot) -- the 32 x 32 orbital box of tile It (and Jt) and the
+// 4 x 32 weight box -- and issues the 12 MMAs of each converted stage, committing to that
+// operand buffer's mbarrier; eight converter warps turn each stage into one of nb operand
+// buffers (weight product, hi/lo split, K-major core-matrix layout) and arrive on its
+// mbarrier.  No block-wide barrier inside the loop: the roles wait on each other's
+// mbarriers only (bounded; a time-out aborts every role and drains the loads).  The boxes use
+// the 128-byte swizzle (16-byte chunk c of row r stored at chunk c ^ (r mod 8)), so the
+// conversion's 16-byte shared loads of 8 rows are conflict-free; its stores write whole
+// 128-byte core-matrix rows per quarter warp.  Rows past N, points past Ng and replicas past
+// nrep arrive as zeros (the tensor maps' out-of-bounds fill).
+constexpr int kGKS = 32;                        // grid points per stage (K)
+constexpr int kGAfl = 128 * kGKS;               // floats per A operand (hi or lo)
+constexpr int kGBfl = 32 * kGKS;                // floats per B operand (hi or lo)
+constexpr int kGOpF = 2 * kGAfl + 2 * kGBfl;    // one operand buffer (40 KB)
+constexpr int kThreadsConv = 256;             // converter warps
+constexpr int kThreadsG = kThreadsConv + 32;    // + one TMA / MMA issuer warp
+constexpr int kGMaxStages = 16;
+constexpr int kGMaxOpBufs = 3;
 
-__global__ void __launch_bounds__(kThreadsG)
-k_gram_tc(int N, int Np, int Ng, const float* __restrict__ phi, const float* __restrict__ w,
-          int nrep, int T, int chunk, float* __restrict__ part, const RepCtl* __restrict__ ctl,
-          int* status) {
+constexpr int kGBoxB = 32 * kGKS * 4;           // bytes of one 32 x 32 orbital box
+constexpr int kGWBoxB = 4 * kGKS * 4;           // bytes of the 4 x 32 weight box
+
+// raw slot: orbital box It [, box Jt], weight box; 1024-byte multiples (swizzle atoms)
+__host__ __device__ constexpr int gram_slot_bytes(bool two_tiles) {
+  return (two_tiles ? 2 : 1) * kGBoxB + 1024;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// 4 floats at row r, column 4 q of a 128-byte-swizzled box of 32-float rows
+__device__ __forceinline__ float4 swz_ld4(const float* box, int r, int q) {
+  return *reinterpret_cast<const float4*>(box + r * 32 + ((q ^ (r & 7)) << 2));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+__global__ void __launch_bounds__(kThreadsG, 1)
+k_gram_tc(const __grid_constant__ CUtensorMap tm_phi, const __grid_constant__ CUtensorMap tm_w,
+          int N, int Np, int Ng, int nrep, int T, int chunk, int S, int nb,
+          float* __restrict__ part, const RepCtl* __restrict__ ctl, int* status) {
   extern __shared__ __align__(128) float sm[];
-  __shared__ __align__(8) uint64_t bar;
+  __shared__ __align__(8) uint64_t full[kGMaxStages];   // TMA -> converters
+  __shared__ __align__(8) uint64_t conv[kGMaxOpBufs];   // converters -> issuer
+  __shared__ __align__(8) uint64_t mdone[kGMaxOpBufs];  // MMAs -> converters
   __shared__ uint32_t tmem_base;
-  float* ah = sm;
-  float* al = sm + kGAfl;
-  float* bh = sm + 2 * kGAfl;
-  float* bl = sm + 2 * kGAfl + kGBfl;
+  __shared__ int abort_flag;
+  __shared__ int issued_n;                              // stages whose loads were issued
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   int It, Jt;
   {
@@ -311,12 +353,21 @@ k_gram_tc(int N, int Np, int Ng, const float* __restrict__ phi, const float* __r
     It = i;
     Jt = i + rem;
   }
+  const bool diag = (It == Jt);
+  const bool two = T > 1;                       // slot layout of this launch
+  const int slotB = gram_slot_bytes(two);
+  const int wbox = (two ? 2 : 1) * kGBoxB;      // weight box within a slot (bytes)
   const int rep0 = blockIdx.z * 4;
   const int nr = min(4, nrep - rep0);
-  const int split = blockIdx.x;
-  const int g_beg = split * chunk;
+  const int g_beg = blockIdx.x * chunk;
   const int g_end = min(Ng, g_beg + chunk);
+  const int nst = g_end > g_beg ? (g_end - g_beg + kGKS - 1) / kGKS : 0;
+  float* op = sm;                               // nb operand buffers
+  // S raw slots from the first 1024-byte boundary after the operands (swizzle atoms)
+  const uint32_t raw_s = (saddr(sm + nb * kGOpF) + 1023u) & ~1023u;
+  const float* raw = sm + (raw_s - saddr(sm)) / 4;
   const uint32_t ncols = 32;
+  constexpr int kConvWarps = kThreadsConv / 32;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -326,92 +377,155 @@ k_gram_tc(int N, int Np, int Ng, const float* __restrict__ phi, const float* __r
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&bar)) : "memory");
+    abort_flag = 0;
+    issued_n = 0;
+    for (int s = 0; s < S; ++s)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&full[s])) : "memory");
+    for (int b = 0; b < nb; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(&conv[b])),
+                   "r"(kConvWarps)
+                   : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&mdone[b])) : "memory");
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  // rows of A beyond 32 nr stay zero
-  for (int e = tid; e < 2 * kGAfl + 2 * kGBfl; e += blockDim.x) sm[e] = 0.0f;
+  // operand rows of replicas >= nr stay zero
+  for (int e = tid; e < nb * kGOpF; e += blockDim.x) op[e] = 0.0f;
+  fence_async_smem();
   fence_before();
   __syncthreads();
   fence_after();
   const uint32_t tbase = tmem_base;
-  const uint32_t idesc = idesc_tf32(kGRows, 32);
-  const int nslab = (g_end > g_beg) ? (g_end - g_beg + kGKS - 1) / kGKS : 0;
-  uint32_t phase = 0;
-  bool ok = true;
-  // staging map: warp w stages orbital rows 4 w + (lane >> 3), lane & 7 picks 4 points
-  const int q = lane & 7;
-  const int i = 4 * warp + (lane >> 3);   // 0 .. 31
-  for (int s = 0; s < nslab; ++s) {
-    const int g = g_beg + s * kGKS + 4 * q;
-    float wv[4][4];
+  volatile int* abort_v = &abort_flag;
+  volatile int* issued_v = &issued_n;
+
+  if (warp == kConvWarps) {
+    // ---- issuer warp: TMA loads into the ring, MMAs of converted stages ------------------
+    // Each box arrives whole (out-of-bounds elements zero-filled), so the transaction count
+    // is fixed; x = g0 is a multiple of 32.
+    auto issue = [&](int t) {
+      const int slot = t % S;
+      const int g0 = g_beg + t * kGKS;
+      const uint32_t bar = saddr(&full[slot]);
+      const uint32_t base = raw_s + (uint32_t)(slot * slotB);
+      mbar_expect_tx(bar, (uint32_t)((diag ? 1 : 2) * kGBoxB + kGWBoxB));
+        // tiled orbitals: the 32 x 32 block (point tile g0/32, orbital tile) is contiguous
+      const int row0 = (g0 >> 5) * Np;
+      tma_load_2d(base, &tm_phi, 0, row0 + It * 32, bar);
+      if (!diag) tma_load_2d(base + kGBoxB, &tm_phi, 0, row0 + Jt * 32, bar);
+      tma_load_2d(base + wbox, &tm_w, g0, rep0, bar);
+      *issued_v = t + 1;
+    };
+    if (lane == 0) {
+      const uint32_t idesc = idesc_tf32(128, 32);
+      for (int u = 0; u < min(S, nst); ++u) issue(u);
+      for (int t = 0; t < nst; ++t) {
+        const int ob = t % nb;
+        if (!mbar_wait(&conv[ob], (uint32_t)(t / nb) & 1u) || *abort_v) {
+          *abort_v = 1;
+          break;
+        }
+        fence_after();
+        const float* o = op + ob * kGOpF;
+        const uint32_t sah = saddr(o), sal = saddr(o + kGAfl), sbh = saddr(o + 2 * kGAfl),
+                       sbl = saddr(o + 2 * kGAfl + kGBfl);
 #pragma unroll
-    for (int r = 0; r < 4; ++r)
-#pragma unroll
-      for (int c = 0; c < 4; ++c)
-        wv[r][c] = (r < nr && g + c < g_end) ? w[(long)(rep0 + r) * Ng + g + c] : 0.0f;
-    float va[4], vb[4];
-    {
-      const int ra = It * 32 + i, rb = Jt * 32 + i;
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const bool in = g + c < g_end;
-        va[c] = (ra < N && in) ? phi[(long)ra * Ng + g + c] : 0.0f;
-        vb[c] = (rb < N && in) ? phi[(long)rb * Ng + g + c] : 0.0f;
+        for (int k = 0; k < kGKS / 8; ++k) {
+          const uint32_t off = k * 2 * kLBO;
+          mma_tf32(tbase, sdesc(sah + off), sdesc(sbh + off), idesc, (t > 0 || k > 0) ? 1u : 0u);
+          mma_tf32(tbase, sdesc(sah + off), sdesc(sbl + off), idesc, 1u);
+          mma_tf32(tbase, sdesc(sal + off), sdesc(sbh + off), idesc, 1u);
+        }
+        mma_commit(&mdone[ob]);
+        // the converters are done with raw slot t % S: refill it with stage t + S
+        if (t + S < nst) issue(t + S);
       }
     }
-    if (s > 0) {   // the MMAs of slab s - 1 read the buffers
-      ok = mbar_wait(&bar, phase);
-      phase ^= 1u;
-      if (__syncthreads_or(!ok)) break;
-      fence_after();
-    }
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      if (r >= nr) break;
-      float4 h4, l4;
-      split_tf32(va[0] * wv[r][0], h4.x, l4.x);
-      split_tf32(va[1] * wv[r][1], h4.y, l4.y);
-      split_tf32(va[2] * wv[r][2], h4.z, l4.z);
-      split_tf32(va[3] * wv[r][3], h4.w, l4.w);
-      *reinterpret_cast<float4*>(&ah[kmaj(r * 32 + i, 4 * q)]) = h4;
-      *reinterpret_cast<float4*>(&al[kmaj(r * 32 + i, 4 * q)]) = l4;
-    }
-    {
-      float4 h4, l4;
-      split_tf32(vb[0], h4.x, l4.x);
-      split_tf32(vb[1], h4.y, l4.y);
-      split_tf32(vb[2], h4.z, l4.z);
-      split_tf32(vb[3], h4.w, l4.w);
-      *reinterpret_cast<float4*>(&bh[kmaj(i, 4 * q)]) = h4;
-      *reinterpret_cast<float4*>(&bl[kmaj(i, 4 * q)]) = l4;
-    }
-    fence_async_smem();
-    __syncthreads();
-    if (tid == 0) {
-      fence_after();
-      const uint32_t sah = saddr(ah), sal = saddr(al), sbh = saddr(bh), sbl = saddr(bl);
-#pragma unroll
-      for (int k = 0; k < kGKS / 8; ++k) {
-        const uint32_t off = k * 2 * kLBO;
-        mma_tf32(tbase, sdesc(sah + off), sdesc(sbh + off), idesc, (s > 0 || k > 0) ? 1u : 0u);
-        mma_tf32(tbase, sdesc(sah + off), sdesc(sbl + off), idesc, 1u);
-        mma_tf32(tbase, sdesc(sal + off), sdesc(sbh + off), idesc, 1u);
+    __syncwarp();
+  } else {
+    // ---- converter warps: raw boxes -> operand buffers ------------------------------------
+    // a quarter warp covers 8 consecutive rows at one 4-point column
+    const int i = 8 * (warp & 3) + (lane & 7);
+    const int q = (lane >> 3) + 4 * (warp >> 2);
+    for (int t = 0; t < nst; ++t) {
+      const int slot = t % S, ob = t % nb;
+      bool ok = mbar_wait(&full[slot], (uint32_t)(t / S) & 1u);
+      if (ok && t >= nb) ok = mbar_wait(&mdone[ob], (uint32_t)((t - nb) / nb) & 1u);
+      if (!ok || *abort_v) {
+        *abort_v = 1;
+        break;
       }
-      mma_commit(&bar);
+      fence_after();
+      const float* rs = raw + slot * (slotB / 4);
+      // points past the chunk end (inside the grid: the next CTA's) are masked here
+      const int nv = min(kGKS, g_end - (g_beg + t * kGKS));
+      const bool in = 4 * q < nv;
+      float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+      if (in) a = swz_ld4(rs, i, q);
+      if (diag)
+        b = a;
+      else if (in)
+        b = swz_ld4(rs + kGBoxB / 4, i, q);
+      float* o = op + ob * kGOpF;
+      float* ah = o;
+      float* al = o + kGAfl;
+      float* bh = o + 2 * kGAfl;
+      float* bl = o + 2 * kGAfl + kGBfl;
+      for (int r = 0; r < nr; ++r) {
+        float4 wv = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (in) wv = swz_ld4(rs + wbox / 4, r, q);
+        float4 h4, l4;
+        split_tf32(a.x * wv.x, h4.x, l4.x);
+        split_tf32(a.y * wv.y, h4.y, l4.y);
+        split_tf32(a.z * wv.z, h4.z, l4.z);
+        split_tf32(a.w * wv.w, h4.w, l4.w);
+        *reinterpret_cast<float4*>(&ah[kmaj(r * 32 + i, 4 * q)]) = h4;
+        *reinterpret_cast<float4*>(&al[kmaj(r * 32 + i, 4 * q)]) = l4;
+      }
+      {
+        float4 h4, l4;
+        split_tf32(b.x, h4.x, l4.x);
+        split_tf32(b.y, h4.y, l4.y);
+        split_tf32(b.z, h4.z, l4.z);
+        split_tf32(b.w, h4.w, l4.w);
+        *reinterpret_cast<float4*>(&bh[kmaj(i, 4 * q)]) = h4;
+        *reinterpret_cast<float4*>(&bl[kmaj(i, 4 * q)]) = l4;
+      }
+      // operands visible to the tensor cores, raw slot released: one arrival per warp
+      fence_async_smem();
+      __syncwarp();
+      if (lane == 0)
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(&conv[ob]))
+                     : "memory");
     }
   }
-  if (ok && nslab > 0) {   // the last slab's MMAs
-    ok = mbar_wait(&bar, phase);
-    phase ^= 1u;
-    ok = !__syncthreads_or(!ok);
+  __syncthreads();
+  // drain: the last MMAs (their commit covers all earlier ones) and, after an abort, the TMA
+  // loads still in flight into this CTA's shared memory (every issued stage completes)
+  bool ok = !*abort_v;
+  if (tid == 0) {
+    bool drained = true;
+    if (nst > 0 && ok)
+      drained = mbar_wait(&mdone[(nst - 1) % nb], (uint32_t)((nst - 1) / nb) & 1u);
+    if (!ok) {
+      // wait for the last issued stage of every slot (phases complete in order; a completed
+      // phase returns at once), so no load is still writing when the CTA exits
+      const int n_iss = *issued_v;
+      for (int u = max(0, n_iss - S); u < n_iss; ++u) mbar_wait(&full[u % S], (uint32_t)(u / S) & 1u);
+      drained = false;
+    }
+    if (!drained) {
+      atomicCAS(status, 0, (int)RMGTD_ETIMEOUT);
+      *abort_v = 1;
+    }
   }
-  if (!ok && tid == 0) atomicCAS(status, 0, (int)RMGTD_ETIMEOUT);
+  __syncthreads();
+  ok = !*abort_v;
   fence_after();
-  // epilogue: TMEM lane m = 32 warp + lane is A row (r = warp, i = lane)
+  // epilogue: TMEM lane m = 32 warp + lane is A row (replica rep0 + warp, orbital It*32+lane)
   if (ok && warp < nr) {
     float y[32];
-    if (nslab > 0) {
+    if (nst > 0) {
       tmem_ld32(tbase + ((uint32_t)(warp * 32) << 16), y);
     } else {
 #pragma unroll
@@ -420,7 +534,7 @@ k_gram_tc(int N, int Np, int Ng, const float* __restrict__ phi, const float* __r
     const int r = rep0 + warp;
     const bool on = !ctl || ctl[r].active;
     const long NpNp = (long)Np * Np;
-    float* out = part + ((long)split * nrep + r) * NpNp + (long)(It * 32 + lane) * Np + Jt * 32;
+    float* out = part + ((long)blockIdx.x * nrep + r) * NpNp + (long)(It * 32 + lane) * Np + Jt * 32;
 #pragma unroll
     for (int j = 0; j < 32; j += 4)
       *reinterpret_cast<float4*>(out + j) =
@@ -439,22 +553,95 @@ k_gram_tc(int N, int Np, int Ng, const float* __restrict__ phi, const float* __r
 
 // float32 Gram partials on the tensor cores; returns 1 when the shapes are outside its
 // range (the caller then runs the SIMT kernel), else the status.  Partials as k_gram32.
+namespace {
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link to libcuda)
+EncodeTiledFn tensor_map_encoder() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// rows x Ng float32 matrix with row stride Ng (a multiple of 4): boxes of 32 points x
+// box_rows rows, 128-byte swizzle, zero fill out of bounds
+bool encode_rows(void* map, const float* base, long Ng, int rows, int box_rows) {
+  const EncodeTiledFn f = tensor_map_encoder();
+  if (!f) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)Ng, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)Ng * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)tc::kGKS, (cuuint32_t)box_rows};
+  const cuuint32_t es[2] = {1, 1};
+  return f(reinterpret_cast<CUtensorMap*>(map), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+           const_cast<float*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+           CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+// float32 Gram partials on the tensor cores; returns 1 when the shapes are outside its
+// range or the tensor maps cannot be made (the caller then runs the SIMT kernel), else the
+// status.  Partials as k_gram32.
 int gram_tc(rmgtd_ctx* ctx, const float* w, int nw, float* part, int nsplit, int chunk,
             const RepCtl* ctl) {
   using namespace tc;
+  static_assert(sizeof(CUtensorMap) == sizeof(ctx->tm_phi), "tensor map size");
   const int N = ctx->N;
   const int T = ceil_div(N, 32);
   const int Np = T * 32;
-  if (ctx->Ng >= (1l << 31) || chunk % kGKS) return 1;
-  const size_t smem = (size_t)(2 * kGAfl + 2 * kGBfl) * sizeof(float);
-  if (!ctx->gram_tc_attr) {
-    RMGTD_CUDA(ctx, cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem));
-    ctx->gram_tc_attr = 1;
+  // tensor maps want 16-byte row strides; boxes start at multiples of 32 points
+  if (ctx->Ng >= (1l << 31) || ctx->Ng % 4 || chunk % kGKS ||
+      ceil_div(ctx->Ng, 32L) * Np >= (1l << 31))
+    return 1;
+  if (!ctx->tm_phi_ok) {
+    if (!encode_rows(ctx->tm_phi, ctx->phi32t, 32, (int)(ceil_div(ctx->Ng, 32L) * Np), 32))
+      return 1;
+    ctx->tm_phi_ok = 1;
   }
+  if (ctx->tm_w_key != (const void*)w || ctx->tm_w_rows != nw) {
+    if (!encode_rows(ctx->tm_w, w, ctx->Ng, nw, 4)) return 1;
+    ctx->tm_w_key = w;
+    ctx->tm_w_rows = nw;
+  }
+  const int per_sm = std::max(1, std::min(ctx->tune_gram_blocks, 2));
+  const size_t budget = (per_sm == 1 ? 220 : 110) * 1024;
+  const int nb = per_sm == 1 ? 3 : 2;                        // operand buffers
+  const size_t slot = gram_slot_bytes(T > 1);
+  const size_t fixed = sizeof(float) * nb * kGOpF + 1024;   // operands + swizzle alignment
+  const int S = (int)std::min<size_t>(kGMaxStages, (budget - fixed) / slot);
+  if (S < 2) return 1;
+  const size_t smem = fixed + S * slot;
+  // the attribute belongs to the function (process-wide): only ever raise it
+  if (ctx->gram_tc_attr < (int)smem) {
+    cudaFuncAttributes fa;
+    RMGTD_CUDA(ctx, cudaFuncGetAttributes(&fa, k_gram_tc));
+    if ((size_t)fa.maxDynamicSharedSizeBytes < smem)
+      RMGTD_CUDA(ctx, cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem));
+    ctx->gram_tc_attr = (int)smem;
+  }
+  CUtensorMap tm_phi, tm_w;
+  memcpy(&tm_phi, ctx->tm_phi, sizeof(tm_phi));
+  memcpy(&tm_w, ctx->tm_w, sizeof(tm_w));
   const dim3 grid(nsplit, T * (T + 1) / 2, ceil_div(nw, 4));
-  k_gram_tc<<<grid, kThreadsG, smem, ctx->stream>>>(N, Np, (int)ctx->Ng, ctx->phi32, w, nw, T,
-                                                      chunk, part, ctl, ctx->status);
+  k_gram_tc<<<grid, kThreadsG, smem, ctx->stream>>>(tm_phi, tm_w, N, Np, (int)ctx->Ng, nw, T,
+                                                      chunk, S, nb, part, ctl, ctx->status);
   ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_gram_tc");
   return RMGTD_OK;

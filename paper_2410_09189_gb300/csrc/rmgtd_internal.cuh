@@ -91,6 +91,9 @@ struct rmgtd_ctx {
   // orbitals and potentials
   double* phi = nullptr;       // [N][Ng]
   float* phi32 = nullptr;      // [N][Ng] (mixed precision)
+  // the same orbitals in 32-point tiles: [ceil(Ng/32)][Np][32] with Np = 32 ceil(N/32), zero
+  // beyond N and Ng, so that a 32-orbital x 32-point block is 4 contiguous KB (tensor cores)
+  float* phi32t = nullptr;
   double* vion = nullptr;      // [Ng] V_loc + V_ext
   double* f_dev = nullptr;     // [N]
 
@@ -121,6 +124,7 @@ struct rmgtd_ctx {
   // grid fields [nrep][Ng]
   double *rho = nullptr, *vh = nullptr, *vxc = nullptr, *exc = nullptr, *vhxc = nullptr;
   double* rho_ref = nullptr;   // [Ng] density of Sref (mixed)
+  float* rho_ref32 = nullptr;  // [Ng] rho_ref rounded to float32 (mixed xc increment)
   double* vref = nullptr;      // [Ng] reference V_Hxc (mixed)
   double* vh_ref = nullptr;    // [Ng] reference V_H (mixed)
   float* dv32 = nullptr;       // [nrep][Ng] V_Hxc - vref (mixed)
@@ -151,11 +155,18 @@ struct rmgtd_ctx {
   int rho_tc_attr = 0;               // tensor-core density kernel configured
   // launch choices (defaults, or measured by rmgtd_autotune)
   int tune_rho_blocks = 3;           // CTAs per SM of the tensor-core density kernel
-  int tune_gram_tc = 0;              // mixed Gram on the tensor cores (1) or SIMT (0)
+  int tune_gram_tc = 1;              // mixed Gram on the tensor cores (1) or SIMT (0)
   int tune_gram_blocks = 2;          // CTAs per SM over the Gram's (pair, replica-group) units
   int tune_coop_div = 1;             // persistent Hartree solve on (SMs / div) blocks
   void* tune_x = nullptr;            // Hartree unknown redirected while timing (autotune)
   int gram_tc_attr = 0;              // tensor-core Gram kernel configured
+  // tiled-TMA descriptors of the tensor-core Gram kernel (CUtensorMap, 128 bytes each): the
+  // float32 orbitals, and the weight rows of the last call (pointer, rows)
+  alignas(64) unsigned char tm_phi[128] = {};
+  alignas(64) unsigned char tm_w[128] = {};
+  int tm_phi_ok = 0;
+  const void* tm_w_key = nullptr;
+  int tm_w_rows = 0;
   double* red_part = nullptr;  // reduction partials
   int red_blocks = 0;                // blocks of the grid-stride reduction kernels
   int red_cap = 0;                   // capacity of one partial slot
@@ -190,6 +201,10 @@ struct rmgtd_ctx {
   cudaGraphExec_t step_exec = nullptr;
   cudaGraph_t step_graph = nullptr;
   int in_batch = 0;             // stepped through an rmgtd_batch (own step calls refused)
+  // mixed path: the float64 fields (rho unless a network reads it, V_H, V_xc, eps_xc, V_Hxc)
+  // lag the float32 increments of the last pass until mixed_fields64 rebuilds them
+  int fields_stale = 0;
+  int eldyn_cluster = -1;           // cluster size of the commutator kernel (-1: not probed)
 
   // learned seed of the SCF loop (attached network; buffers allocated at attach)
   rmgtd_net* net = nullptr;
@@ -336,6 +351,12 @@ int apply_h_dev(rmgtd_ctx* ctx, const void* x, void* hx, int ncols, int dtype,
 int launch_lda(rmgtd_ctx* ctx, const double* rho, double* vh, int vh_mode, double* vxc,
                double* exc, double* vhxc, float* dv32, long n, const RepCtl* ctl, int nrep,
                long stride, int with_xc);
+// Mixed pass: dv32 <- dvh32 + V_xc(rho_ref + drho32) - V_xc(rho_ref) in float32 arithmetic.
+int launch_xc_mixed(rmgtd_ctx* ctx, const RepCtl* ctl, int nrep);
+// dv[g] <- V_xc(rho0[g] + d[g]) - V_xc(rho0[g]) (the same float32 increment, stand-alone).
+int launch_xc_increment(rmgtd_ctx* ctx, const double* rho0, const float* d, float* dv, long n);
+// rho <- rho_ref + drho32 for every replica.
+int rho_from_increment(rmgtd_ctx* ctx);
 // k_subspace.cu
 // out[r] = base[r * bstride] + scale * A^T diag(w_r) B (bstride 0: one base for all replicas)
 int gram(rmgtd_ctx* ctx, const double* A, const double* B, const double* w, long wstride,
@@ -347,6 +368,8 @@ int gram_mixed(rmgtd_ctx* ctx, const float* w, long wstride, int nw, double scal
                const double* base, double* out, const RepCtl* ctl, unsigned long long* errbits,
                long bstride = 0);
 int to_float(rmgtd_ctx* ctx, const double* in, float* out, long n);
+// phi32t <- phi32 in 32-point tiles (layout above)
+int tile_orbitals(rmgtd_ctx* ctx);
 int eldyn(rmgtd_ctx* ctx, const double* Ha, const double* Hb, long hstride, double tau,
           const double* S0, const double* A0, double* S1, double* A1, const RepCtl* ctl_in,
           RepCtl* ctl_out, int rep0, int nreps);

@@ -94,6 +94,7 @@ def load_library(path: Optional[str] = None):
         "rmgtd_set_matrix": (i, [vp, i, i, _c_double_p]),
         "rmgtd_hartree": (i, [vp, vp, vp]),
         "rmgtd_xc": (i, [vp, vp, vp, vp, ctypes.c_size_t]),
+        "rmgtd_xc_increment": (i, [vp, vp, vp, vp, ctypes.c_size_t]),
         "rmgtd_save": (i, [vp, ctypes.c_char_p]),
         "rmgtd_load": (i, [vp, ctypes.c_char_p]),
         "rmgtd_time": (i, [vp, _c_double_p, ctypes.POINTER(ctypes.c_longlong)]),
@@ -118,6 +119,8 @@ def load_library(path: Optional[str] = None):
         "rmgtd_attach_net": (i, [vp, vp]),
         "rmgtd_get_field": (i, [vp, i, i, vp]),
         "rmgtd_autotune": (i, [vp, _c_int_p]),
+        "rmgtd_set_tuning": (i, [vp, _c_int_p]),
+        "rmgtd_get_tuning": (i, [vp, _c_int_p]),
         "rmgtd_batch_create": (i, [ctypes.POINTER(vp), i, ctypes.POINTER(vp)]),
         "rmgtd_batch_destroy": (None, [vp]),
         "rmgtd_batch_step": (i, [vp, i, ctypes.POINTER(ctypes.POINTER(CStats))]),
@@ -282,6 +285,17 @@ class Context:
         self._check(self._lib.rmgtd_autotune(self._ctx, _iptr(c)))
         return tuple(int(v) for v in c)
 
+    def set_tuning(self, choice):
+        """Set the launch configuration (same order as autotune's result)."""
+        c = np.ascontiguousarray(choice, dtype=np.int32)
+        assert c.shape == (4,)
+        self._check(self._lib.rmgtd_set_tuning(self._ctx, _iptr(c)))
+
+    def tuning(self):
+        c = np.zeros(4, dtype=np.int32)
+        self._check(self._lib.rmgtd_get_tuning(self._ctx, _iptr(c)))
+        return tuple(int(v) for v in c)
+
     def attach_net(self, net: Optional["Net"]):
         """Seed every step's SCF loop with the network's correction (None detaches)."""
         self._net = net
@@ -337,6 +351,13 @@ class Context:
         self._check(self._lib.rmgtd_xc(self._ctx, ctypes.c_void_p(rho.data_ptr()),
                                        ctypes.c_void_p(vxc.data_ptr()),
                                        ctypes.c_void_p(exc.data_ptr()), rho.numel()))
+
+    def xc_increment(self, rho0, drho, dvxc):
+        """dvxc <- V_xc(rho0 + drho) - V_xc(rho0) (float64 rho0, float32 drho and dvxc)."""
+        self._check(self._lib.rmgtd_xc_increment(self._ctx, ctypes.c_void_p(rho0.data_ptr()),
+                                                 ctypes.c_void_p(drho.data_ptr()),
+                                                 ctypes.c_void_p(dvxc.data_ptr()),
+                                                 rho0.numel()))
 
     def save(self, path: str):
         self._check(self._lib.rmgtd_save(self._ctx, path.encode()))

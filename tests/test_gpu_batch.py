@@ -1,6 +1,8 @@
 """Several systems of uneven grids stepped by one CUDA graph per time step (rmgtd_batch), and
 the launch autotuner: the batch reproduces the separately stepped contexts bit for bit, and
 the tuned launch configurations change results only at rounding level."""
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -96,3 +98,42 @@ def test_autotune_changes_results_only_at_rounding_level(lib):
     d0, d1 = out
     scale = np.max(np.abs(d0))
     assert np.max(np.abs(d1 - d0)) <= 1e-7 * scale
+
+
+def test_tensor_core_gram_matches_simt_gram(lib):
+    """The Hamiltonian update on the tensor cores (3xTF32) against the float32 SIMT kernel:
+    the same trajectory up to rounding level, also with two CTAs per SM (fewer stages in
+    the copy ring) and a ragged last chunk of the grid."""
+    # Ng = 41 * 36 * 44 = 64944: a multiple of 4 (bulk copies) but not of 32 (ragged stage)
+    s = dataclasses.replace(inputs.scaled(inputs.ring(), n=40, h=0.5, nvirt=15), n=(41, 36, 44))
+    raw = inputs.smooth_random_orbitals(s).reshape(s.N, s.Ng)
+    kw = dict(nrep=3, H_thrs=1e-9, dP_thrs=1e-12, precision=lib.PREC_MIXED, use_graph=True)
+    out = []
+    for tuning in ((3, 0, 2, 1), (3, 1, 1, 1), (3, 1, 2, 1)):
+        ctx = lib.Context(s, raw, **kw)
+        ctx.set_tuning(tuning)
+        for a in range(3):
+            ctx.kick(a, a, 1e-3)
+        ctx.step(6)
+        out.append((np.array([ctx.dipole(a) for a in range(3)]),
+                    np.array([ctx.get_matrix(lib.MAT_H0, r) for r in range(3)])))
+        ctx.close()
+    # 3xTF32 keeps ~2^-21 of each product of the update h^3 Phi^T diag(dV) Phi; the float32
+    # SIMT sum ~2^-24 per term: the converged H of the two differs by ~1e-8 of |H|
+    d0, h0 = out[0]
+    scale = np.max(np.abs(d0))
+    for d1, h1 in out[1:]:
+        assert np.max(np.abs(d1 - d0)) <= 1e-7 * scale
+        assert np.max(np.abs(h1 - h0)) <= 5e-8 * np.max(np.abs(h0))
+
+
+def test_set_tuning_rejects_bad_values(lib):
+    s = inputs.scaled(inputs.ring(), n=24, h=0.6, nvirt=4)
+    raw = inputs.smooth_random_orbitals(s).reshape(s.N, s.Ng)
+    ctx = lib.Context(s, raw, nrep=1, precision=lib.PREC_MIXED)
+    before = ctx.tuning()
+    for bad in ((0, 0, 1, 1), (3, 2, 1, 1), (3, 0, 3, 1), (3, 0, 1, 3)):
+        with pytest.raises(lib.RmgtdError):
+            ctx.set_tuning(bad)
+        assert ctx.tuning() == before
+    ctx.close()

@@ -127,6 +127,47 @@ def test_hartree_and_xc(torch_dev):
         assert _rel(vh.cpu().numpy(), ref.ravel()) < 1e-10
 
 
+def test_xc_increment_matches_oracle(torch_dev):
+    """The mixed path's float32 xc increment V_xc(rho0 + d) - V_xc(rho0) against the float64
+    oracle LDA: densities from 1e-16 (below the floor) to 30, around r_s = 1 (rho = 3/(4 pi))
+    and across it, increments from 1e-9 to 0.6 of rho0 of both signs, zero increments and
+    increments that take the density below the floor.  The bound is a few float32 units of
+    the increment itself, plus 2e-13 |V_xc| for the points that take two float64 evaluations
+    (near the floor, near r_s = 1): each of those is within 2^-43 relative (one Newton step
+    per root, as test_hartree_and_xc checks), the accuracy of the float64 LDA itself."""
+    torch = torch_dev
+    rmgtd = _rmgtd()
+    rng = np.random.default_rng(11)
+    n = 400_000
+    rs1 = 3.0 / (4.0 * np.pi)
+    rho0 = np.concatenate([10 ** rng.uniform(-16, 1.5, n // 2),
+                           rs1 * (1 + 10 ** rng.uniform(-9, -1, n // 4) *
+                                  np.sign(rng.standard_normal(n // 4))),
+                           10 ** rng.uniform(-15, -12, n // 4)])
+    rel = np.sign(rng.standard_normal(n)) * 10 ** rng.uniform(-9, np.log10(0.6), n)
+    rel[::97] = 0.0
+    rel[1::89] = -1.0 - 1e-3            # below the floor (negative density)
+    d32 = (rho0 * rel).astype(np.float32)
+    d = d32.astype(np.float64)
+    v1, _ = olda.lda(rho0 + d)
+    v0, _ = olda.lda(rho0)
+    ref = v1 - v0
+    s = _ring_small(n=(20, 20, 20), h=0.5)
+    raw = inputs.smooth_random_orbitals(s).reshape(s.N, s.Ng)
+    with rmgtd.Context(s, raw) as ctx:
+        r0 = torch.from_numpy(rho0).cuda()
+        dd = torch.from_numpy(d32).cuda()
+        out = torch.empty(n, dtype=torch.float32, device="cuda")
+        ctx.xc_increment(r0, dd, out)
+        got = out.cpu().numpy().astype(np.float64)
+    err = np.abs(got - ref)
+    bound = 2e-6 * np.abs(ref) + 2e-13 * np.abs(v0) + 1e-30
+    bad = err > bound
+    assert not bad.any(), (np.count_nonzero(bad), rho0[bad][:3], d[bad][:3], ref[bad][:3],
+                           got[bad][:3])
+    assert np.all(got[rel == 0.0] == 0.0)
+
+
 def test_kick_matches_oracle(torch_dev):
     rmgtd = _rmgtd()
     s = _ring_small(n=(30, 30, 30), h=0.55, nvirt=20)
@@ -326,7 +367,10 @@ def test_mixed_trajectory_small_system(torch_dev, small_gs):
     assert abs(np.trace(P).real - s.n_electrons) < 1e-11
 
 
-def test_mixed_three_kicks_ragged(torch_dev):
+@pytest.mark.parametrize("tuning", [None, (3, 1, 1, 1), (2, 1, 2, 2)])
+def test_mixed_three_kicks_ragged(torch_dev, tuning):
+    """Three kicks on a ragged grid with two orbital tiles (N = 37): the default launch
+    configuration and the tensor-core Gram kernel (diagonal and off-diagonal tile pairs)."""
     rmgtd = _rmgtd()
     s = _ring_small(n=(30, 34, 38), h=0.5, nvirt=22)
     raw = inputs.smooth_random_orbitals(s).reshape(s.N, s.Ng)
@@ -336,6 +380,9 @@ def test_mixed_three_kicks_ragged(torch_dev):
     refs = [tddft.run(s, phi, o, nsteps=nsteps, axis=a, kappa=kap) for a in range(3)]
     with rmgtd.Context(s, raw, dt=dt, H_thrs=1e-9, dP_thrs=1e-12, nrep=3,
                        precision=rmgtd.PREC_MIXED) as ctx:
+        if tuning is not None:
+            ctx.set_tuning(tuning)
+            assert ctx.tuning() == tuning
         for a in range(3):
             ctx.kick(a, a, kap)
         d = [[ctx.dipole(a) for a in range(3)]]

@@ -186,7 +186,7 @@ def test_attach_rejects_mismatched_network(lib, small_ground_state):
 def test_trained_network_saves_scf_passes(lib, small_ground_state, tmp_path):
     """Train on the first 3/4 of a kicked trajectory (the library's kernels only), then
     continue the propagation with and without the learned seed from the same state: fewer
-    SCF passes with it, and the same converged dipole (the SCF loop is the judge)."""
+    SCF passes with it, and the same converged dipole (the SCF loop decides convergence)."""
     from paper_2410_09189_gb300 import surrogate
     s, gs = small_ground_state
     kw = dict(nrep=1, H_thrs=1e-7, dP_thrs=1e-10, precision=lib.PREC_FP64, use_graph=True)
@@ -216,7 +216,7 @@ def test_trained_network_saves_scf_passes(lib, small_ground_state, tmp_path):
           f"held-out seed RMS ratio {rep['heldout_ratio']:.3f}; dipole error vs tight SCF: "
           f"paper seed {e_plain:.2e}, learned seed {e_learned:.2e}")
     assert learned.mean() <= plain.mean() - 0.25
-    # the SCF loop stays the judge: the learned seed is no less accurate than the paper's
+    # the SCF loop still decides convergence: the learned seed is no less accurate than the paper's
     assert e_learned <= max(2.0 * e_plain, 1e-5 * np.max(np.abs(d_tight)))
     for c in (ctx, ctx2, ctx3):
         c.close()
