@@ -151,6 +151,74 @@ __device__ __forceinline__ float lap7f(const float* __restrict__ x, int ix, int 
   return 6.0f * c - s;  // h^2 * (-Lap_7 x)
 }
 
+// ---- quads: 4 consecutive x-points per thread (float32, nx a multiple of 4) -----------------
+// A thread loads whole 16-byte vectors of its row and of the neighbouring rows instead of
+// scalar neighbours, so one quad of a stencil needs 7 (7-point) or 29 (37-point) vector loads
+// instead of 28 or 148 scalar ones, with all of them in flight together.  Sums keep the
+// scalar kernels' order (+x, -x, +y, -y, +z, -z; absent neighbours add zero).
+__device__ __forceinline__ float4 ld4(const float* p) {
+  return *reinterpret_cast<const float4*>(p);
+}
+__device__ __forceinline__ float4 ld4_if(bool c, const float* p) {
+  return c ? ld4(p) : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+__device__ __forceinline__ float f4(const float4& v, int i) {
+  return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
+}
+
+// h^2 (-Lap_7 x) of the quad starting at g0 (x = ix0 .. ix0 + 3); c4 receives x there
+__device__ __forceinline__ float4 lap7_quad(const float* __restrict__ x, int g0, int ix0, int iy,
+                                            int iz, int nx, int ny, int nz, float4& c4) {
+  const int plane = nx * ny;
+  c4 = ld4(x + g0);
+  const float xl = ix0 > 0 ? x[g0 - 1] : 0.0f;
+  const float xr = ix0 + 4 < nx ? x[g0 + 4] : 0.0f;
+  const float4 yp = ld4_if(iy + 1 < ny, x + g0 + nx), ym = ld4_if(iy > 0, x + g0 - nx);
+  const float4 zp = ld4_if(iz + 1 < nz, x + g0 + plane), zm = ld4_if(iz > 0, x + g0 - plane);
+  float4 r;
+  r.x = 6.0f * c4.x - (((((c4.y + xl) + yp.x) + ym.x) + zp.x) + zm.x);
+  r.y = 6.0f * c4.y - (((((c4.z + c4.x) + yp.y) + ym.y) + zp.y) + zm.y);
+  r.z = 6.0f * c4.z - (((((c4.w + c4.y) + yp.z) + ym.z) + zp.z) + zm.z);
+  r.w = 6.0f * c4.w - (((((xr + c4.z) + yp.w) + ym.w) + zp.w) + zm.w);
+  return r;
+}
+
+// A12 x (the 37-point operator of apply_A12) on the quad; c4 receives x there
+__device__ __forceinline__ float4 A12_quad(const float* __restrict__ x, int g0, int ix0, int iy,
+                                           int iz, int nx, int ny, int nz, float ih2, float4& c4) {
+  const int plane = nx * ny;
+  float xl[20];   // x - 8 .. x + 11 of the row, zero outside it
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const int xo = ix0 - 8 + 4 * k;
+    const float4 v = ld4_if(xo >= 0 && xo < nx, x + g0 - 8 + 4 * k);
+    xl[4 * k] = v.x;
+    xl[4 * k + 1] = v.y;
+    xl[4 * k + 2] = v.z;
+    xl[4 * k + 3] = v.w;
+  }
+  c4 = make_float4(xl[8], xl[9], xl[10], xl[11]);
+  const float c0 = (float)(3.0 * fd_coef(0));
+  float sm[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) sm[q] = c0 * xl[8 + q];
+#pragma unroll
+  for (int m = 1; m <= kFdRadius; ++m) {
+    const float4 yp = ld4_if(iy + m < ny, x + g0 + m * nx);
+    const float4 ym = ld4_if(iy - m >= 0, x + g0 - m * nx);
+    const float4 zp = ld4_if(iz + m < nz, x + g0 + m * plane);
+    const float4 zm = ld4_if(iz - m >= 0, x + g0 - m * plane);
+    const float cm = (float)fd_coef(m);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float t = ((((xl[8 + q + m] + xl[8 + q - m]) + f4(yp, q)) + f4(ym, q)) + f4(zp, q)) +
+                      f4(zm, q);
+      sm[q] = fmaf(cm, t, sm[q]);
+    }
+  }
+  return make_float4(-sm[0] * ih2, -sm[1] * ih2, -sm[2] * ih2, -sm[3] * ih2);
+}
+
 __device__ __forceinline__ void tri_w(int f, int nc, int* c0, int* c1, float* w0, float* w1) {
   const int I = f >> 1;
   *c0 = I;
@@ -193,6 +261,37 @@ __device__ __forceinline__ float prolong_point(const float* __restrict__ xc, int
                 wy1 * (wx0 * at(x0, y1, z0) + wx1 * at(x1, y1, z0))) +
          wz1 * (wy0 * (wx0 * at(x0, y0, z1) + wx1 * at(x1, y0, z1)) +
                 wy1 * (wx0 * at(x0, y1, z1) + wx1 * at(x1, y1, z1)));
+}
+
+// Trilinear prolongation of the coarse correction onto the fine quad x0 .. x0 + 3 (x0 a
+// multiple of 4) of row (fy, fz): the quad reads coarse x I0 - 1 .. I0 + 2 (I0 = x0 / 2) of
+// its 2 x 2 coarse lines once; weights and sums as prolong_point.
+__device__ __forceinline__ float4 prolong_quad(const float* __restrict__ xc, int x0, int fy,
+                                               int fz, int cx, int cy, int cz) {
+  const int I0 = x0 >> 1;
+  int y0, y1, z0, z1;
+  float wy0, wy1, wz0, wz1;
+  tri_w(fy, cy, &y0, &y1, &wy0, &wy1);
+  tri_w(fz, cz, &z0, &z1, &wz0, &wz1);
+  const bool lok = I0 > 0, rok = I0 + 2 < cx;
+  const float wl = lok ? 0.25f : 0.0f, wr = rok ? 0.25f : 0.0f;
+  float h[4][4];   // [line][fine q]: x-interpolated coarse line (y0 z0, y1 z0, y0 z1, y1 z1)
+#pragma unroll
+  for (int ln = 0; ln < 4; ++ln) {
+    const int j = (ln & 1) ? y1 : y0, k = (ln & 2) ? z1 : z0;
+    const float* row = xc + (k * cy + j) * cx;
+    const float v0 = row[I0], v1 = row[I0 + 1];
+    const float vl = row[lok ? I0 - 1 : I0], vr = row[rok ? I0 + 2 : I0 + 1];
+    h[ln][0] = 0.75f * v0 + wl * vl;
+    h[ln][1] = 0.75f * v0 + 0.25f * v1;
+    h[ln][2] = 0.75f * v1 + 0.25f * v0;
+    h[ln][3] = 0.75f * v1 + wr * vr;
+  }
+  float r[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    r[q] = wz0 * (wy0 * h[0][q] + wy1 * h[1][q]) + wz1 * (wy0 * h[2][q] + wy1 * h[3][q]);
+  return make_float4(r[0], r[1], r[2], r[3]);
 }
 
 // ---- coarse tail of the V-cycle inside one block (levels with <= kTailMax points) ---------
@@ -254,12 +353,24 @@ __device__ void tail_vcycle(const Tail& L, const float* __restrict__ b_in,
     }
     const int nx = L.nx[l], ny = L.ny[l], nz = L.nz[l], n = L.n[l];
     const float h2 = L.h2[l], ih2 = 1.0f / h2, c = kJacobiW * h2 / 6.0f;
-    for (int g = threadIdx.x; g < n; g += blockDim.x) {   // x = c (2 b - c A b)
-      int ix, iy, iz;
-      xyz_of(g, nx, ny, L.dx[l], L.dy[l], ix, iy, iz);
-      float bc;
-      const float ab = lap7f(bs[l], ix, iy, iz, nx, ny, nz, &bc) * ih2;
-      xs[l][g] = c * (2.0f * bc - c * ab);
+    if ((nx & 3) == 0) {   // quads (the level's arrays start at multiples of 4 floats)
+      for (int g0 = 4 * threadIdx.x; g0 < n; g0 += 4 * blockDim.x) {
+        int ix, iy, iz;
+        xyz_of(g0, nx, ny, L.dx[l], L.dy[l], ix, iy, iz);
+        float4 bc;
+        const float4 ab = lap7_quad(bs[l], g0, ix, iy, iz, nx, ny, nz, bc);
+        *reinterpret_cast<float4*>(xs[l] + g0) = make_float4(
+            c * (2.0f * bc.x - c * (ab.x * ih2)), c * (2.0f * bc.y - c * (ab.y * ih2)),
+            c * (2.0f * bc.z - c * (ab.z * ih2)), c * (2.0f * bc.w - c * (ab.w * ih2)));
+      }
+    } else {
+      for (int g = threadIdx.x; g < n; g += blockDim.x) {   // x = c (2 b - c A b)
+        int ix, iy, iz;
+        xyz_of(g, nx, ny, L.dx[l], L.dy[l], ix, iy, iz);
+        float bc;
+        const float ab = lap7f(bs[l], ix, iy, iz, nx, ny, nz, &bc) * ih2;
+        xs[l][g] = c * (2.0f * bc - c * ab);
+      }
     }
     __syncthreads();
     const int cx = L.nx[l + 1], cy = L.ny[l + 1], nc = L.n[l + 1];
@@ -274,21 +385,49 @@ __device__ void tail_vcycle(const Tail& L, const float* __restrict__ b_in,
     const int nx = L.nx[l], ny = L.ny[l], nz = L.nz[l], n = L.n[l];
     const int cx = L.nx[l + 1], cy = L.ny[l + 1], cz = L.nz[l + 1];
     const float h2 = L.h2[l], ih2 = 1.0f / h2, c = kJacobiW * h2 / 6.0f;
-    for (int g = threadIdx.x; g < n; g += blockDim.x) {
-      int fx, fy, fz;
-      xyz_of(g, nx, ny, L.dx[l], L.dy[l], fx, fy, fz);
-      xs[l][g] += prolong_point(xs[l + 1], fx, fy, fz, cx, cy, cz);
+    const bool quad = (nx & 3) == 0;
+    if (quad) {
+      for (int g0 = 4 * threadIdx.x; g0 < n; g0 += 4 * blockDim.x) {
+        int fx, fy, fz;
+        xyz_of(g0, nx, ny, L.dx[l], L.dy[l], fx, fy, fz);
+        const float4 pq = prolong_quad(xs[l + 1], fx, fy, fz, cx, cy, cz);
+        float4 v = ld4(xs[l] + g0);
+        v.x += pq.x;
+        v.y += pq.y;
+        v.z += pq.z;
+        v.w += pq.w;
+        *reinterpret_cast<float4*>(xs[l] + g0) = v;
+      }
+    } else {
+      for (int g = threadIdx.x; g < n; g += blockDim.x) {
+        int fx, fy, fz;
+        xyz_of(g, nx, ny, L.dx[l], L.dy[l], fx, fy, fz);
+        xs[l][g] += prolong_point(xs[l + 1], fx, fy, fz, cx, cy, cz);
+      }
     }
     __syncthreads();
     for (int sw = 0; sw < kPost; ++sw) {
       const float* in = (sw & 1) ? ts[l] : xs[l];
       float* out = (sw & 1) ? xs[l] : ts[l];
-      for (int g = threadIdx.x; g < n; g += blockDim.x) {
-        int ix, iy, iz;
-        xyz_of(g, nx, ny, L.dx[l], L.dy[l], ix, iy, iz);
-        float cc;
-        const float ax = lap7f(in, ix, iy, iz, nx, ny, nz, &cc) * ih2;
-        out[g] = cc + c * (bs[l][g] - ax);
+      if (quad) {
+        for (int g0 = 4 * threadIdx.x; g0 < n; g0 += 4 * blockDim.x) {
+          int ix, iy, iz;
+          xyz_of(g0, nx, ny, L.dx[l], L.dy[l], ix, iy, iz);
+          float4 cc;
+          const float4 ax = lap7_quad(in, g0, ix, iy, iz, nx, ny, nz, cc);
+          const float4 bv = ld4(bs[l] + g0);
+          *reinterpret_cast<float4*>(out + g0) = make_float4(
+              cc.x + c * (bv.x - ax.x * ih2), cc.y + c * (bv.y - ax.y * ih2),
+              cc.z + c * (bv.z - ax.z * ih2), cc.w + c * (bv.w - ax.w * ih2));
+        }
+      } else {
+        for (int g = threadIdx.x; g < n; g += blockDim.x) {
+          int ix, iy, iz;
+          xyz_of(g, nx, ny, L.dx[l], L.dy[l], ix, iy, iz);
+          float cc;
+          const float ax = lap7f(in, ix, iy, iz, nx, ny, nz, &cc) * ih2;
+          out[g] = cc + c * (bs[l][g] - ax);
+        }
       }
       __syncthreads();
     }
@@ -477,6 +616,7 @@ struct Args {
   unsigned* bar;
   int* status;
   unsigned long long* counters;   // [0] solves, [1] CG iterations (summed over replicas)
+  int vec4;               // float path with nx % 4 == 0: level-0 phases on quads
 };
 
 __device__ __forceinline__ float wsum(float v) { return warp_sumf(v); }
@@ -549,6 +689,19 @@ __global__ void __launch_bounds__(kThreadsC, 1) k_hartree_coop(Args<V> a) {
     __syncthreads();
   };
 
+  // flattened quad loops (float path, vec4 with n0 % 128 == 0): the 32 quads of a warp are
+  // 128 consecutive points of one replica, so a warp-uniform replica index accumulates the
+  // warp's sums of each loop iteration into its own wpart slots
+  auto zero_parts = [&](int nd) {
+    if (lane == 0)
+      for (int d = 0; d < nd; ++d)
+        for (int rp = 0; rp < a.nrep; ++rp) wpart[d][rp][warp] = 0.0;
+  };
+  auto add_part = [&](int d, int rp, float v) {
+    v = warp_sumf(v);
+    if (lane == 0) wpart[d][rp][warp] += (double)v;
+  };
+
   {  // level table into shared memory
     const int* src = reinterpret_cast<const int*>(a.lt);
     int* dst = reinterpret_cast<int*>(&T);
@@ -567,6 +720,33 @@ __global__ void __launch_bounds__(kThreadsC, 1) k_hartree_coop(Args<V> a) {
   const V hv = (V)a.h;
 
   // ---- prologue: multipole moments of the density (change) ----------------------------
+  bool flat = false;
+  if constexpr (sizeof(V) == 4) flat = a.vec4 == 2;
+  if (flat) {
+    if constexpr (sizeof(V) == 4) {
+      zero_parts(4);
+      if (!a.zero_bc) {
+        const int N0 = n0 * nrep;
+        const float cx = 0.5f * (float)(nx - 1), cy = 0.5f * (float)(ny - 1);
+        const float cz = 0.5f * (float)(nz - 1);
+        for (int e0 = 4 * gtid; e0 < N0; e0 += 4 * gstride) {
+          const int rp = fdiv(e0, T.L[0].dn);
+          if (!act[rp]) continue;
+          int ix, iy, iz;
+          xyz_of(e0 - rp * n0, nx, ny, T.L[0].dx, T.L[0].dy, ix, iy, iz);
+          const float4 v = ld4(a.drho + e0);
+          const float s4 = ((v.x + v.y) + v.z) + v.w;
+          const float x0 = ((float)ix - cx) * hv;
+          const float sx = ((v.x * x0 + v.y * (x0 + hv)) + v.z * (x0 + 2.0f * hv)) +
+                           v.w * (x0 + 3.0f * hv);
+          add_part(0, rp, s4);
+          add_part(1, rp, sx);
+          add_part(2, rp, s4 * (((float)iy - cy) * hv));
+          add_part(3, rp, s4 * (((float)iz - cz) * hv));
+        }
+      }
+    }
+  } else
   for (int rp = 0; rp < nrep; ++rp) {
     V q0 = 0, q1 = 0, q2 = 0, q3 = 0;
     if (act[rp] && !a.zero_bc) {
@@ -590,7 +770,39 @@ __global__ void __launch_bounds__(kThreadsC, 1) k_hartree_coop(Args<V> a) {
   gsum(4, 4, 5, 6, 7);
 
   // ---- right-hand side b = 4 pi rho + ghost term, residual r = b - A x -----------------
-  {
+  if (flat) {
+    if constexpr (sizeof(V) == 4) {
+      zero_parts(2);
+      const double h3 = a.h * a.h * a.h;
+      const int N0 = n0 * nrep;
+      for (int e0 = 4 * gtid; e0 < N0; e0 += 4 * gstride) {
+        const int rp = fdiv(e0, T.L[0].dn);
+        if (!act[rp]) continue;
+        const int g0 = e0 - rp * n0;
+        int ix, iy, iz;
+        xyz_of(g0, nx, ny, T.L[0].dx, T.L[0].dy, ix, iy, iz);
+        const float4 dv = ld4(a.drho + e0);
+        const float fp = (float)(4.0 * kPi);
+        float4 bv = make_float4(fp * dv.x, fp * dv.y, fp * dv.z, fp * dv.w);
+        if (!a.zero_bc) {
+          const float Q = (float)(h3 * sc[4][rp]), px = (float)(h3 * sc[5][rp]);
+          const float py = (float)(h3 * sc[6][rp]), pz = (float)(h3 * sc[7][rp]);
+          const float4 g0v = ld4(a.gf32 + g0), g1v = ld4(a.gf32 + n0 + g0);
+          const float4 g2v = ld4(a.gf32 + 2 * n0 + g0), g3v = ld4(a.gf32 + 3 * n0 + g0);
+          bv.x += Q * g0v.x + px * g1v.x + py * g2v.x + pz * g3v.x;
+          bv.y += Q * g0v.y + px * g1v.y + py * g2v.y + pz * g3v.y;
+          bv.z += Q * g0v.z + px * g1v.z + py * g2v.z + pz * g3v.z;
+          bv.w += Q * g0v.w + px * g1v.w + py * g2v.w + pz * g3v.w;
+        }
+        float4 xc;
+        const float4 ax = A12_quad(a.x + rp * n0, g0, ix, iy, iz, nx, ny, nz, ih2, xc);
+        const float4 rv = make_float4(bv.x - ax.x, bv.y - ax.y, bv.z - ax.z, bv.w - ax.w);
+        *reinterpret_cast<float4*>(a.r + e0) = rv;
+        add_part(0, rp, ((bv.x * bv.x + bv.y * bv.y) + bv.z * bv.z) + bv.w * bv.w);
+        add_part(1, rp, ((rv.x * rv.x + rv.y * rv.y) + rv.z * rv.z) + rv.w * rv.w);
+      }
+    }
+  } else {
     const double h3 = a.h * a.h * a.h;
     for (int rp = 0; rp < nrep; ++rp) {
       V bb = 0, rr = 0;
@@ -605,7 +817,6 @@ __global__ void __launch_bounds__(kThreadsC, 1) k_hartree_coop(Args<V> a) {
           if (!a.zero_bc)
             bv += Q * ghost(a, 0, n0, g) + px * ghost(a, 1, n0, g) + py * ghost(a, 2, n0, g) +
                   pz * ghost(a, 3, n0, g);
-          a.b[base + g] = bv;
           const V rv = bv - apply_A12<V>(a.x + base, ix, iy, iz, nx, ny, nz, ih2);
           a.r[base + g] = rv;
           bb += bv * bv;
@@ -691,6 +902,26 @@ __global__ void __launch_bounds__(kThreadsC, 1) k_hartree_coop(Args<V> a) {
         continue;
       }
       // two pre-sweeps from zero in one pass: x = c (2 b - c A b); level 0 reads b from r
+      bool pre_done = false;
+      if constexpr (sizeof(V) == 4) {
+        if (l == 0 && a.vec4) {
+          for (int e0 = 4 * gtid; e0 < Nl; e0 += 4 * gstride) {
+            const int rep = fdiv(e0, L.dn);
+            if (!act[rep]) continue;
+            int ix, iy, iz;
+            xyz_of(e0 - rep * L.n, L.nx, L.ny, L.dx, L.dy, ix, iy, iz);
+            float4 bc;
+            const float4 ab = lap7_quad(a.r + rep * L.n, e0 - rep * L.n, ix, iy, iz, L.nx, L.ny,
+                                        L.nz, bc);
+            *reinterpret_cast<float4*>(L.b + e0) = bc;
+            *reinterpret_cast<float4*>(L.x + e0) =
+                make_float4(c * (2.0f * bc.x - c * ab.x * ih2f), c * (2.0f * bc.y - c * ab.y * ih2f),
+                            c * (2.0f * bc.z - c * ab.z * ih2f), c * (2.0f * bc.w - c * ab.w * ih2f));
+          }
+          pre_done = true;
+        }
+      }
+      if (!pre_done)
       for (int e = gtid; e < Nl; e += gstride) {
         const int rep = fdiv(e, L.dn);
         if (!act[rep]) continue;
@@ -776,25 +1007,85 @@ __global__ void __launch_bounds__(kThreadsC, 1) k_hartree_coop(Args<V> a) {
         }
         COOP_BAR();
       } else {
-        for (int e = gtid; e < Nl; e += gstride) {
-          const int rep = fdiv(e, L.dn);
-          if (!act[rep]) continue;
-          int ix, iy, iz;
-          xyz_of(e - rep * L.n, L.nx, L.ny, L.dx, L.dy, ix, iy, iz);
-          L.x[e] += prolong_point(C.x + rep * C.n, ix, iy, iz, C.nx, C.ny, C.nz);
+        bool pdone = false;
+        if constexpr (sizeof(V) == 4) {
+          if (a.vec4) {
+            for (int e0 = 4 * gtid; e0 < Nl; e0 += 4 * gstride) {
+              const int rep = fdiv(e0, L.dn);
+              if (!act[rep]) continue;
+              int ix, iy, iz;
+              xyz_of(e0 - rep * L.n, L.nx, L.ny, L.dx, L.dy, ix, iy, iz);
+              const float4 pq = prolong_quad(C.x + rep * C.n, ix, iy, iz, C.nx, C.ny, C.nz);
+              float4 v = ld4(L.x + e0);
+              v.x += pq.x;
+              v.y += pq.y;
+              v.z += pq.z;
+              v.w += pq.w;
+              *reinterpret_cast<float4*>(L.x + e0) = v;
+            }
+            pdone = true;
+          }
         }
+        if (!pdone)
+          for (int e = gtid; e < Nl; e += gstride) {
+            const int rep = fdiv(e, L.dn);
+            if (!act[rep]) continue;
+            int ix, iy, iz;
+            xyz_of(e - rep * L.n, L.nx, L.ny, L.dx, L.dy, ix, iy, iz);
+            L.x[e] += prolong_point(C.x + rep * C.n, ix, iy, iz, C.nx, C.ny, C.nz);
+          }
         COOP_BAR();
-        for (int e = gtid; e < Nl; e += gstride) {
-          const int rep = fdiv(e, L.dn);
-          if (!act[rep]) continue;
-          int ix, iy, iz;
-          xyz_of(e - rep * L.n, L.nx, L.ny, L.dx, L.dy, ix, iy, iz);
-          float cc;
-          const float ax = lap7f(L.x + rep * L.n, ix, iy, iz, L.nx, L.ny, L.nz, &cc) * ih2f;
-          L.t[e] = cc + c * (L.b[e] - ax);
+        bool done = false;
+        if constexpr (sizeof(V) == 4) {
+          if (a.vec4) {
+            for (int e0 = 4 * gtid; e0 < Nl; e0 += 4 * gstride) {
+              const int rep = fdiv(e0, L.dn);
+              if (!act[rep]) continue;
+              int ix, iy, iz;
+              xyz_of(e0 - rep * L.n, L.nx, L.ny, L.dx, L.dy, ix, iy, iz);
+              float4 cc;
+              const float4 ax = lap7_quad(L.x + rep * L.n, e0 - rep * L.n, ix, iy, iz, L.nx,
+                                          L.ny, L.nz, cc);
+              const float4 bv = ld4(L.b + e0);
+              *reinterpret_cast<float4*>(L.t + e0) = make_float4(
+                  cc.x + c * (bv.x - ax.x * ih2f), cc.y + c * (bv.y - ax.y * ih2f),
+                  cc.z + c * (bv.z - ax.z * ih2f), cc.w + c * (bv.w - ax.w * ih2f));
+            }
+            done = true;
+          }
         }
+        if (!done)
+          for (int e = gtid; e < Nl; e += gstride) {
+            const int rep = fdiv(e, L.dn);
+            if (!act[rep]) continue;
+            int ix, iy, iz;
+            xyz_of(e - rep * L.n, L.nx, L.ny, L.dx, L.dy, ix, iy, iz);
+            float cc;
+            const float ax = lap7f(L.x + rep * L.n, ix, iy, iz, L.nx, L.ny, L.nz, &cc) * ih2f;
+            L.t[e] = cc + c * (L.b[e] - ax);
+          }
         COOP_BAR();
       }
+      bool done_z = false;
+      if constexpr (sizeof(V) == 4) {
+        if (l == 0 && a.vec4) {
+          for (int e0 = 4 * gtid; e0 < Nl; e0 += 4 * gstride) {
+            const int rep = fdiv(e0, L.dn);
+            if (!act[rep]) continue;
+            int ix, iy, iz;
+            xyz_of(e0 - rep * L.n, L.nx, L.ny, L.dx, L.dy, ix, iy, iz);
+            float4 cc;
+            const float4 ax = lap7_quad(L.t + rep * L.n, e0 - rep * L.n, ix, iy, iz, L.nx, L.ny,
+                                        L.nz, cc);
+            const float4 bv = ld4(L.b + e0);
+            *reinterpret_cast<float4*>(a.z + e0) = make_float4(
+                cc.x + c * (bv.x - ax.x * ih2f), cc.y + c * (bv.y - ax.y * ih2f),
+                cc.z + c * (bv.z - ax.z * ih2f), cc.w + c * (bv.w - ax.w * ih2f));
+          }
+          done_z = true;
+        }
+      }
+      if (!done_z)
       for (int e = gtid; e < Nl; e += gstride) {
         const int rep = fdiv(e, L.dn);
         if (!act[rep]) continue;
@@ -819,9 +1110,67 @@ __global__ void __launch_bounds__(kThreadsC, 1) k_hartree_coop(Args<V> a) {
 
     // ---- A z and the dot products (r,z), (z,Az), (z,Ap_old), (p_old,Az) ------------------
     const bool first = (it == 0);
+    if (flat) {
+      if constexpr (sizeof(V) == 4) {
+        zero_parts(4);
+        const int N0 = n0 * nrep;
+        for (int e0 = 4 * gtid; e0 < N0; e0 += 4 * gstride) {
+          const int rp = fdiv(e0, T.L[0].dn);
+          if (!act[rp]) continue;
+          const int g0 = e0 - rp * n0;
+          int ix, iy, iz;
+          xyz_of(g0, nx, ny, T.L[0].dx, T.L[0].dy, ix, iy, iz);
+          float4 zc;
+          const float4 az = A12_quad(a.z + rp * n0, g0, ix, iy, iz, nx, ny, nz, ih2, zc);
+          *reinterpret_cast<float4*>(a.Az + e0) = az;
+          const float4 rv = ld4(a.r + e0);
+          add_part(0, rp, ((rv.x * zc.x + rv.y * zc.y) + rv.z * zc.z) + rv.w * zc.w);
+          add_part(1, rp, ((zc.x * az.x + zc.y * az.y) + zc.z * az.z) + zc.w * az.w);
+          if (!first) {
+            const float4 apv = ld4(a.Ap + e0), pv = ld4(a.p + e0);
+            add_part(2, rp, ((zc.x * apv.x + zc.y * apv.y) + zc.z * apv.z) + zc.w * apv.w);
+            add_part(3, rp, ((pv.x * az.x + pv.y * az.y) + pv.z * az.z) + pv.w * az.w);
+          }
+        }
+      }
+    } else
     for (int rp = 0; rp < nrep; ++rp) {
       V d0 = 0, d1 = 0, d2 = 0, d3 = 0;
-      if (act[rp]) {
+      bool quads = false;
+      if constexpr (sizeof(V) == 4) quads = a.vec4 != 0;
+      if (act[rp] && quads) {
+        if constexpr (sizeof(V) == 4) {
+          const int base = rp * n0;
+          const float* zr = a.z + base;
+          for (int g0 = 4 * gtid; g0 < n0; g0 += 4 * gstride) {
+            int ix, iy, iz;
+            xyz_of(g0, nx, ny, T.L[0].dx, T.L[0].dy, ix, iy, iz);
+            float4 zc;
+            const float4 az = A12_quad(zr, g0, ix, iy, iz, nx, ny, nz, ih2, zc);
+            *reinterpret_cast<float4*>(a.Az + base + g0) = az;
+            const float4 rv = ld4(a.r + base + g0);
+            d0 += rv.x * zc.x;
+            d0 += rv.y * zc.y;
+            d0 += rv.z * zc.z;
+            d0 += rv.w * zc.w;
+            d1 += zc.x * az.x;
+            d1 += zc.y * az.y;
+            d1 += zc.z * az.z;
+            d1 += zc.w * az.w;
+            if (!first) {
+              const float4 apv = ld4(a.Ap + base + g0), pv = ld4(a.p + base + g0);
+              d2 += zc.x * apv.x;
+              d2 += zc.y * apv.y;
+              d2 += zc.z * apv.z;
+              d2 += zc.w * apv.w;
+              d3 += pv.x * az.x;
+              d3 += pv.y * az.y;
+              d3 += pv.z * az.z;
+              d3 += pv.w * az.w;
+            }
+          }
+        }
+      } else if (act[rp]) {
         const int base = rp * n0;
         const V* zr = a.z + base;
         for (int g = gtid; g < n0; g += gstride) {
@@ -863,9 +1212,76 @@ __global__ void __launch_bounds__(kThreadsC, 1) k_hartree_coop(Args<V> a) {
     __syncthreads();
 
     // ---- p, Ap, x, r updates; partials of (r,r) and (r_new, z_old) ----------------------
+    if (flat) {
+      if constexpr (sizeof(V) == 4) {
+        zero_parts(2);
+        const int N0 = n0 * nrep;
+        for (int e = 4 * gtid; e < N0; e += 4 * gstride) {
+          const int rp = fdiv(e, T.L[0].dn);
+          if (!act[rp]) continue;
+          const float al = (float)alpha[rp], bt = (float)beta[rp];
+          const float4 zc = ld4(a.z + e), az = ld4(a.Az + e), xv = ld4(a.x + e),
+                       rv = ld4(a.r + e);
+          float4 pv = zc, apv = az;
+          if (!first) {
+            const float4 po = ld4(a.p + e), apo = ld4(a.Ap + e);
+            pv = make_float4(fmaf(bt, po.x, zc.x), fmaf(bt, po.y, zc.y), fmaf(bt, po.z, zc.z),
+                             fmaf(bt, po.w, zc.w));
+            apv = make_float4(fmaf(bt, apo.x, az.x), fmaf(bt, apo.y, az.y),
+                              fmaf(bt, apo.z, az.z), fmaf(bt, apo.w, az.w));
+          }
+          const float4 rn = make_float4(fmaf(-al, apv.x, rv.x), fmaf(-al, apv.y, rv.y),
+                                        fmaf(-al, apv.z, rv.z), fmaf(-al, apv.w, rv.w));
+          *reinterpret_cast<float4*>(a.p + e) = pv;
+          *reinterpret_cast<float4*>(a.Ap + e) = apv;
+          *reinterpret_cast<float4*>(a.x + e) =
+              make_float4(fmaf(al, pv.x, xv.x), fmaf(al, pv.y, xv.y), fmaf(al, pv.z, xv.z),
+                          fmaf(al, pv.w, xv.w));
+          *reinterpret_cast<float4*>(a.r + e) = rn;
+          add_part(0, rp, ((rn.x * rn.x + rn.y * rn.y) + rn.z * rn.z) + rn.w * rn.w);
+          add_part(1, rp, ((rn.x * zc.x + rn.y * zc.y) + rn.z * zc.z) + rn.w * zc.w);
+        }
+      }
+    } else
     for (int rp = 0; rp < nrep; ++rp) {
       V d0 = 0, d1 = 0;
-      if (act[rp]) {
+      bool quads = false;
+      if constexpr (sizeof(V) == 4) quads = a.vec4 != 0;
+      if (act[rp] && quads) {
+        if constexpr (sizeof(V) == 4) {
+          const int base = rp * n0;
+          const float al = (float)alpha[rp], bt = (float)beta[rp];
+          for (int g0 = 4 * gtid; g0 < n0; g0 += 4 * gstride) {
+            const int e = base + g0;
+            const float4 zc = ld4(a.z + e), az = ld4(a.Az + e), xv = ld4(a.x + e),
+                         rv = ld4(a.r + e);
+            float4 pv = zc, apv = az;
+            if (!first) {
+              const float4 po = ld4(a.p + e), apo = ld4(a.Ap + e);
+              pv = make_float4(fmaf(bt, po.x, zc.x), fmaf(bt, po.y, zc.y), fmaf(bt, po.z, zc.z),
+                               fmaf(bt, po.w, zc.w));
+              apv = make_float4(fmaf(bt, apo.x, az.x), fmaf(bt, apo.y, az.y),
+                                fmaf(bt, apo.z, az.z), fmaf(bt, apo.w, az.w));
+            }
+            const float4 xn = make_float4(fmaf(al, pv.x, xv.x), fmaf(al, pv.y, xv.y),
+                                          fmaf(al, pv.z, xv.z), fmaf(al, pv.w, xv.w));
+            const float4 rn = make_float4(fmaf(-al, apv.x, rv.x), fmaf(-al, apv.y, rv.y),
+                                          fmaf(-al, apv.z, rv.z), fmaf(-al, apv.w, rv.w));
+            *reinterpret_cast<float4*>(a.p + e) = pv;
+            *reinterpret_cast<float4*>(a.Ap + e) = apv;
+            *reinterpret_cast<float4*>(a.x + e) = xn;
+            *reinterpret_cast<float4*>(a.r + e) = rn;
+            d0 += rn.x * rn.x;
+            d0 += rn.y * rn.y;
+            d0 += rn.z * rn.z;
+            d0 += rn.w * rn.w;
+            d1 += rn.x * zc.x;
+            d1 += rn.y * zc.y;
+            d1 += rn.z * zc.z;
+            d1 += rn.w * zc.w;
+          }
+        }
+      } else if (act[rp]) {
         const int base = rp * n0;
         const V al = (V)alpha[rp], bt = (V)beta[rp];
         for (int g = gtid; g < n0; g += gstride) {
@@ -946,6 +1362,8 @@ int hartree_coop(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* ct
     a.bar = ctx->bar2;
     a.status = ctx->status;
     a.counters = ctx->tune_x ? nullptr : ctx->kexec + 2;
+    // quads of the float path (16-byte aligned rows); 2: also warp-uniform replicas
+    a.vec4 = (ctx->nx % 4 == 0) ? (((long)ctx->Ng % 128 == 0) ? 2 : 1) : 0;
   };
   const void* fn;
   void* args[1];

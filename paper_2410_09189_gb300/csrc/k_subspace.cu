@@ -501,9 +501,12 @@ k_gram32_reduce(int N, int Np, int nsplit, int nrep, const float* __restrict__ p
   const long NpNp = (long)Np * Np;
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   const long e = (long)blockIdx.x * 32 + lane;
-  double s = 0.0;
+  // Eight independent loads in flight per step, summed in split order as an unevaluated
+  // float pair (hi + lo, Knuth's two-sum: the rounding error of every addition is kept), so
+  // the sum carries ~2^-44 relative error with float32 instructions only -- GB300's float64
+  // rate (~1/64) made the former float64 accumulation the kernel's bound.
+  float shi = 0.0f, slo = 0.0f;
   if (e < NpNp) {
-    // eight independent loads in flight per step, summed in split order
     for (int k0 = wp; k0 < nsplit; k0 += 64) {
       float v[8];
 #pragma unroll
@@ -512,9 +515,15 @@ k_gram32_reduce(int N, int Np, int nsplit, int nrep, const float* __restrict__ p
         v[u] = k < nsplit ? part[((long)k * nrep + rep) * NpNp + e] : 0.0f;
       }
 #pragma unroll
-      for (int u = 0; u < 8; ++u) s += (double)v[u];
+      for (int u = 0; u < 8; ++u) {
+        const float t = shi + v[u];
+        const float bp = t - shi;
+        slo += (shi - (t - bp)) + (v[u] - bp);
+        shi = t;
+      }
     }
   }
+  const double s = (double)shi + (double)slo;
   sh[wp][lane] = s;
   __syncthreads();
   double emax = 0.0;
