@@ -488,16 +488,17 @@ k_gram32(int N, int Np, int Ng, const float* __restrict__ phi, const float* __re
   }
 }
 
-// out[rep] = base + scale * sum_split part (float64, fixed order), mirrored to i > j;
-// max_ij |out - prev| folded into errbits.  Block = 8 warps x 32 consecutive elements of
-// one replica; warp w sums the splits s = w, w + 8, ...
-__global__ void __launch_bounds__(256)
+// out[rep] = base + scale * sum_split part (fixed order), mirrored to i > j;
+// max_ij |out - prev| folded into errbits.  Block = 32 warps x 32 consecutive elements of
+// one replica; warp w sums the splits s = w, w + 32, ... (8 loads in flight per lane), so a
+// few hundred splits take one or two rounds of L2 latency.
+__global__ void __launch_bounds__(1024)
 k_gram32_reduce(int N, int Np, int nsplit, int nrep, const float* __restrict__ part,
                 double scale, const double* __restrict__ base, long bstride, double* out,
                 const double* prev, unsigned long long* errbits, const RepCtl* __restrict__ ctl) {
   const int rep = blockIdx.y;
   if (ctl && !ctl[rep].active) return;
-  __shared__ double sh[8][33];
+  __shared__ double sh[32][33];
   const long NpNp = (long)Np * Np;
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   const long e = (long)blockIdx.x * 32 + lane;
@@ -507,11 +508,11 @@ k_gram32_reduce(int N, int Np, int nsplit, int nrep, const float* __restrict__ p
   // rate (~1/64) made the former float64 accumulation the kernel's bound.
   float shi = 0.0f, slo = 0.0f;
   if (e < NpNp) {
-    for (int k0 = wp; k0 < nsplit; k0 += 64) {
+    for (int k0 = wp; k0 < nsplit; k0 += 256) {
       float v[8];
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
-        const int k = k0 + 8 * u;
+        const int k = k0 + 32 * u;
         v[u] = k < nsplit ? part[((long)k * nrep + rep) * NpNp + e] : 0.0f;
       }
 #pragma unroll
@@ -529,7 +530,7 @@ k_gram32_reduce(int N, int Np, int nsplit, int nrep, const float* __restrict__ p
   double emax = 0.0;
   if (wp == 0 && e < NpNp) {
     double t = 0.0;
-    for (int k = 0; k < 8; ++k) t += sh[k][lane];
+    for (int k = 0; k < 32; ++k) t += sh[k][lane];
     const int i = (int)(e / Np), j = (int)(e % Np);
     if (i < N && j < N && i <= j) {
       const long NN = (long)N * N;
@@ -580,7 +581,7 @@ int gram_mixed(rmgtd_ctx* ctx, const float* w, long wstride, int nw, double scal
     ++ctx->launches;
     RMGTD_LAUNCH(ctx, "k_gram32");
   }
-  k_gram32_reduce<<<dim3(ceil_div((long)Np * Np, 32L), nw), 256, 0, ctx->stream>>>(
+  k_gram32_reduce<<<dim3(ceil_div((long)Np * Np, 32L), nw), 1024, 0, ctx->stream>>>(
       N, Np, nsplit, nw, part, scale, base, bstride, out, out, errbits, ctl);
   ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_gram32_reduce");
