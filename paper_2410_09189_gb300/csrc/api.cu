@@ -209,13 +209,14 @@ int dft_eval(rmgtd_ctx* ctx, const double* S, const RepCtl* ctl, unsigned long l
   if (rc) return rc;
   if (ctx->hartree_xc) {
     ph_begin(ctx, PH_HARTREE);
-    rc = hartree_coop(ctx, ctx->rho, ctx->vh, ctl, 0, nrep, mixed);
+    // mixed: the solve's closing phase also forms dV = dV_H + dV_xc (no separate xc pass)
+    rc = hartree_coop(ctx, ctx->rho, ctx->vh, ctl, 0, nrep, mixed, mixed);
     ph_end(ctx);
     if (rc) return rc;
   }
   ph_begin(ctx, PH_XC);
   if (mixed) {
-    rc = launch_xc_mixed(ctx, ctl, nrep);
+    if (!ctx->hartree_xc) rc = launch_xc_mixed(ctx, ctl, nrep);
     ctx->fields_stale = 1;
   } else {
     rc = launch_lda(ctx, ctx->rho, ctx->hartree_xc ? ctx->vh : nullptr, 0, ctx->vxc, ctx->exc,
@@ -553,6 +554,8 @@ static int create_impl(const rmgtd_system* sys, const rmgtd_options* opt, rmgtd_
     {
       const long Np = ((N + 31) / 32) * 32;
       ctx->shat32 = (float*)A(sizeof(float) * Np * Np * nrep);
+      if (ctx->shat32)
+        RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->shat32, 0, sizeof(float) * Np * Np * nrep, ctx->stream));
     }
     ctx->pcg32_b = (float*)A(fsz * nrep);
     ctx->pcg32_r = (float*)A(fsz * nrep);
@@ -661,7 +664,7 @@ static int enqueue_pass(rmgtd_ctx* ctx, cudaGraphConditionalHandle cond, int use
   const long NN = (long)ctx->N * ctx->N;
   ph_begin(ctx, PH_ELDYN);
   int rc = eldyn(ctx, ctx->H0, ctx->H1, NN, ctx->opt.dt, ctx->S0, ctx->A0, ctx->S1, ctx->A1,
-                 ctx->ctl, ctx->ctl, 0, ctx->nrep);
+                 ctx->ctl, ctx->ctl, 0, ctx->nrep, ctx->mixed ? ctx->shat32 : nullptr);
   ph_end(ctx);
   if (rc) return rc;
   rc = dft_eval(ctx, ctx->S1, ctx->ctl, ctx->errbits);

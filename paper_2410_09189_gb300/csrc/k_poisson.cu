@@ -27,6 +27,7 @@
 #include <math.h>
 
 #include "fastdiv.h"
+#include "lda.cuh"
 #include "rmgtd_internal.cuh"
 
 namespace rmgtd {
@@ -617,6 +618,11 @@ struct Args {
   int* status;
   unsigned long long* counters;   // [0] solves, [1] CG iterations (summed over replicas)
   int vec4;               // float path with nx % 4 == 0: level-0 phases on quads
+  // float path: closing phase dv_out = x + V_xc(rho0 + drho) - V_xc(rho0) (the mixed pass's
+  // potential change; rho0f = rho0 rounded to float32), when dv_out is set
+  const double* rho0;
+  const float* rho0f;
+  float* dv_out;
 };
 
 __device__ __forceinline__ float wsum(float v) { return warp_sumf(v); }
@@ -1333,6 +1339,19 @@ __global__ void __launch_bounds__(kThreadsC, 1) k_hartree_coop(Args<V> a) {
     atomicAdd(&a.counters[0], 1ull);
     atomicAdd(&a.counters[1], (unsigned long long)a.st[threadIdx.x].it);
   }
+  // closing phase of the mixed pass: the potential change dV = dV_H + dV_xc of every replica
+  // solved here (the last barrier published x), in the same arithmetic as k_xc_mixed
+  if constexpr (sizeof(V) == 4) {
+    if (a.dv_out) {
+      const int N0 = n0 * nrep;
+      for (int e = gtid; e < N0; e += gstride) {
+        const int rp = fdiv(e, T.L[0].dn);
+        if (!act0[rp]) continue;
+        const int g = e - rp * n0;
+        a.dv_out[e] = dvxc_increment(a.rho0 + g, a.rho0f[g], a.drho[e]) + a.x[e];
+      }
+    }
+  }
 #undef COOP_BAR
 }
 
@@ -1340,7 +1359,7 @@ __global__ void __launch_bounds__(kThreadsC, 1) k_hartree_coop(Args<V> a) {
 
 // host launcher of the persistent solve; f32 selects the mixed-path correction solve
 int hartree_coop(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* ctl, int zero_bc,
-                 int nrep, int f32) {
+                 int nrep, int f32, int xc_fuse) {
   if (nrep > coop::kMaxRep) return set_error(ctx, RMGTD_EINVAL, "too many replicas");
   if (f32 && (!ctx->drho32 || !ctx->ghost32))
     return set_error(ctx, RMGTD_ESTATE, "mixed Hartree solve without float32 buffers");
@@ -1364,6 +1383,9 @@ int hartree_coop(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* ct
     a.counters = ctx->tune_x ? nullptr : ctx->kexec + 2;
     // quads of the float path (16-byte aligned rows); 2: also warp-uniform replicas
     a.vec4 = (ctx->nx % 4 == 0) ? (((long)ctx->Ng % 128 == 0) ? 2 : 1) : 0;
+    a.rho0 = ctx->rho_ref;
+    a.rho0f = ctx->rho_ref32;
+    a.dv_out = nullptr;
   };
   const void* fn;
   void* args[1];
@@ -1379,6 +1401,7 @@ int hartree_coop(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* ct
     af.Ap = ctx->pcg32_Ap;
     af.Az = ctx->pcg32_Az;
     af.tol = std::max(ctx->opt.poisson_tol, kMixedPoissonTol);
+    if (xc_fuse && !ctx->tune_x && ctx->rho_ref32) af.dv_out = ctx->dv32;
     fn = (const void*)coop::k_hartree_coop<float>;
     args[0] = &af;
   } else {

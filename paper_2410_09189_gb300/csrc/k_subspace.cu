@@ -335,10 +335,13 @@ k_rho32(int N, int Np, long Ng, const float* __restrict__ phi, const float* __re
 int rho_dev_mixed(rmgtd_ctx* ctx, const double* S, double* rho, const RepCtl* ctl, int nrep) {
   const int N = ctx->N, Np = ((N + 31) / 32) * 32;
   const long NpNp = (long)Np * Np;
-  k_shat32<<<dim3(std::max(1, (int)std::min<long>(ceil_div(NpNp, 256), 1024)), nrep), 256, 0,
-             ctx->stream>>>(N, Np, S, ctx->Sref, (long)N * N, ctx->shat32, ctl);
-  ++ctx->launches;
-  RMGTD_LAUNCH(ctx, "k_shat32");
+  if (!ctx->shat_fresh || S != ctx->S1) {
+    k_shat32<<<dim3(std::max(1, (int)std::min<long>(ceil_div(NpNp, 256), 1024)), nrep), 256, 0,
+               ctx->stream>>>(N, Np, S, ctx->Sref, (long)N * N, ctx->shat32, ctl);
+    ++ctx->launches;
+    RMGTD_LAUNCH(ctx, "k_shat32");
+  }
+  ctx->shat_fresh = 0;
   const int rc = rho_tc(ctx, rho, ctx->drho32, ctl, nrep);   // tensor cores when N <= 32
   if (rc <= 0) return rc;
   dim3 grid(ceil_div(ctx->Ng, kRhoThreads * kRho32Pts), nrep);
@@ -653,6 +656,11 @@ struct EldynArgs {
   double thrs;
   unsigned* bar;
   int* status;
+  // optional (cluster kernel): float32 Shat of the new P_1 for the mixed density, rows
+  // padded to Np: Shat_kj = 2 (S - Sref)_kj (k < j), (S - Sref)_kk, 0 below the diagonal
+  float* shat;
+  const double* Sref;
+  int Np;
 };
 
 template <int TS, int NT>
@@ -890,8 +898,7 @@ static int launch_eldyn_ts(rmgtd_ctx* ctx, EldynArgs& a) {
 // T2[j][i] from the owning CTA's shared memory (distributed shared memory), forms its rows of
 // S_k, A_k, adds them to P_1 and writes them into every CTA's copy.  Two cluster barriers per
 // term and no global-memory round trip: the series of every replica runs on its own cluster
-// and the replicas' clusters never wait on one another.  Sums run over m = 0..N-1 in order,
-// as in k_eldyn, so both kernels give the same bits.
+// and the replicas' clusters never wait on one another.
 namespace cg = cooperative_groups;
 
 template <int C>
@@ -945,15 +952,29 @@ __global__ void __launch_bounds__(256, 1) k_eldyn_cluster(EldynArgs a) {
   while (true) {
     ++k;
     if (tid == 0) c_sh = a.tau / (double)k;
-    // T1 = Hbar A_{k-1}, T2 = Hbar S_{k-1} on the owned rows
-    for (int o = tid; o < 2 * nr * N; o += nt) {
-      const int q = o / (nr * N), e = o - q * nr * N;
-      const int ii = e / N, j = e - ii * N;
-      const double* X = q ? Sf : Af;
-      const double* h = Hr + ii * N;
-      double s = 0.0;
-      for (int m = 0; m < N; ++m) s = fma(h[m], X[m * N + j], s);
-      (q ? T2 : T1)[e] = s;
+    // T1 = Hbar A_{k-1}, T2 = Hbar S_{k-1} on the owned rows.  Two adjacent lanes share an
+    // output, each summing half of the m range (two float64 FMA chains of N/2 in flight
+    // instead of one of N: the kernel is bound by their latency); the halves are added by a
+    // lane exchange.  Uniform trip count, so every lane reaches the exchange.
+    {
+      const int nout = 2 * nr * N, half = (N + 1) / 2;
+      for (int base = 0; base < 2 * nout; base += nt) {
+        const int o2 = base + tid;
+        const int o = o2 >> 1, hf = o2 & 1;
+        double sp = 0.0;
+        int q = 0, e = 0;
+        if (o < nout) {
+          q = o / (nr * N);
+          e = o - q * nr * N;
+          const int ii = e / N, j = e - ii * N;
+          const double* X = q ? Sf : Af;
+          const double* h = Hr + ii * N;
+          const int m0 = hf ? half : 0, m1 = hf ? N : half;
+          for (int m = m0; m < m1; ++m) sp = fma(h[m], X[m * N + j], sp);
+        }
+        sp += __shfl_xor_sync(0xffffffffu, sp, 1);
+        if (o < nout && hf == 0) (q ? T2 : T1)[e] = sp;
+      }
     }
     cluster.sync();
     // new terms on the owned rows; broadcast into every CTA's copy
@@ -1006,6 +1027,19 @@ __global__ void __launch_bounds__(256, 1) k_eldyn_cluster(EldynArgs a) {
     const long o = rep * NN + (long)r0 * N + e;
     a.S1[o] = S1r[e];
     a.A1[o] = A1r[e];
+  }
+  if (a.shat) {   // this CTA's rows of Shat (the rows past N stay zero)
+    const int Np = a.Np;
+    float* shr = a.shat + (long)(a.rep0 + rep) * Np * Np;
+    for (int e = tid; e < nr * Np; e += nt) {
+      const int ii = e / Np, j = e - ii * Np, k = r0 + ii;
+      double v = 0.0;
+      if (j < N && k <= j) {
+        const double d = S1r[ii * N + j] - a.Sref[(long)k * N + j];
+        v = (k < j) ? 2.0 * d : d;
+      }
+      shr[(long)k * Np + j] = (float)v;
+    }
   }
   if (rank == 0 && tid == 0) {
     if (status) atomicCAS(a.status, 0, status);
@@ -1092,7 +1126,7 @@ static int eldyn_cluster_size(rmgtd_ctx* ctx) {
 
 int eldyn(rmgtd_ctx* ctx, const double* Ha, const double* Hb, long hstride, double tau,
           const double* S0, const double* A0, double* S1, double* A1, const RepCtl* ctl_in,
-          RepCtl* ctl_out, int rep0, int nreps) {
+          RepCtl* ctl_out, int rep0, int nreps, float* shat_out) {
   if (nreps > 32) return set_error(ctx, RMGTD_EINVAL, "at most 32 replicas per expansion");
   EldynArgs a;
   a.N = ctx->N;
@@ -1116,10 +1150,19 @@ int eldyn(rmgtd_ctx* ctx, const double* Ha, const double* Hb, long hstride, doub
   a.status = ctx->status;
   // N <= 64: one cluster per replica (no grid barrier); else the cooperative kernel, with
   // small tiles for small N so the float64 work of a term spreads over more SMs
+  a.shat = nullptr;
+  a.Sref = ctx->Sref;
+  a.Np = ((ctx->N + 31) / 32) * 32;
+  ctx->shat_fresh = 0;
   if (ctx->N <= 64) {
     const int C = eldyn_cluster_size(ctx);
+    if ((C == 16 || C == 8) && shat_out && ctx->Sref) {
+      a.shat = shat_out;
+      ctx->shat_fresh = 1;   // the density pass that follows skips k_shat32
+    }
     if (C == 16) return launch_eldyn_cluster<16>(ctx, a, eldyn_cluster_smem(ctx->N, 16));
     if (C == 8) return launch_eldyn_cluster<8>(ctx, a, eldyn_cluster_smem(ctx->N, 8));
+    ctx->shat_fresh = 0;
   }
   if (ctx->N <= 32) return launch_eldyn_ts<4, 64>(ctx, a);
   if (ctx->N <= 64) return launch_eldyn_ts<8, 256>(ctx, a);

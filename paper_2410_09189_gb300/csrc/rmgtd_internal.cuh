@@ -205,6 +205,7 @@ struct rmgtd_ctx {
   // lag the float32 increments of the last pass until mixed_fields64 rebuilds them
   int fields_stale = 0;
   int eldyn_cluster = -1;           // cluster size of the commutator kernel (-1: not probed)
+  int shat_fresh = 0;               // the last commutator launch also wrote shat32 for S1
 
   // learned seed of the SCF loop (attached network; buffers allocated at attach)
   rmgtd_net* net = nullptr;
@@ -372,7 +373,8 @@ int to_float(rmgtd_ctx* ctx, const double* in, float* out, long n);
 int tile_orbitals(rmgtd_ctx* ctx);
 int eldyn(rmgtd_ctx* ctx, const double* Ha, const double* Hb, long hstride, double tau,
           const double* S0, const double* A0, double* S1, double* A1, const RepCtl* ctl_in,
-          RepCtl* ctl_out, int rep0, int nreps);
+          RepCtl* ctl_out, int rep0, int nreps,
+          float* shat_out = nullptr);
 int step_begin(rmgtd_ctx* ctx);
 int scf_control(rmgtd_ctx* ctx, const unsigned long long* errbits,
                 cudaGraphConditionalHandle cond, int use_cond);
@@ -387,8 +389,9 @@ int poisson_red_cap(int num_sms, int red_blocks);
 int hartree_extrapolate(rmgtd_ctx* ctx);
 // Hartree solve of every active replica in one cooperative launch; f32 = 1: float32
 // correction solve of the mixed path (reads drho32, writes dvh32)
+// xc_fuse (float32 path): the kernel's closing phase also writes dv32 = dV_H + dV_xc
 int hartree_coop(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* ctl, int zero_bc,
-                 int nrep, int f32);
+                 int nrep, int f32, int xc_fuse = 0);
 int hartree_reset_history(rmgtd_ctx* ctx);
 // k_tc.cu
 int rho_tc(rmgtd_ctx* ctx, double* rho, float* drho, const RepCtl* ctl, int nrep);
