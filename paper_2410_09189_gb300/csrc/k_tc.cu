@@ -148,9 +148,10 @@ k_rho_tc(int N, int Np, int Ng, int nr, const float* __restrict__ phit,
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&bar)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  // B operand: row n = r * 32 + j, column k: Shat_r[k][j] (zero beyond N)
+  // B operand: row n = r * 32 + j, column k: Shat_r[k][j] (zero beyond N); n fastest, so
+  // the global reads are coalesced rows of Shat and the K-major stores 4-way conflicted
   for (int e = tid; e < ncols_used * kK; e += blockDim.x) {
-    const int n = e / kK, k = e % kK;
+    const int k = e / ncols_used, n = e - k * ncols_used;
     const int r = n >> 5, j = n & 31;
     float v = 0.0f;
     if (j < N && k < N) v = shat[((long)r * Np + k) * Np + j];
