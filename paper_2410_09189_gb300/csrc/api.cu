@@ -541,7 +541,10 @@ static int create_impl(const rmgtd_system* sys, const rmgtd_options* opt, rmgtd_
     // reference state of the mixed path: the float64 set-up state (all replicas start in it)
     const size_t fsz = sizeof(float) * Ng;
     ctx->phi32 = (float*)A(fsz * N);
-    ctx->phi32t = (float*)A(sizeof(float) * 32 * ((N + 31) / 32) * 32 * ((Ng + 31) / 32));
+    // tiled copy, padded to whole 128-point tiles (the density kernel loads 16 KB per tile)
+    const size_t phit_bytes = sizeof(float) * 32 * ((N + 31) / 32) * 128 * ((Ng + 127) / 128);
+    ctx->phi32t = (float*)A(phit_bytes);
+    if (ctx->phi32t) RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->phi32t, 0, phit_bytes, ctx->stream));
     ctx->Sref = (double*)A(msz);
     ctx->Href = (double*)A(msz);
     ctx->rho_ref = (double*)A(gsz);

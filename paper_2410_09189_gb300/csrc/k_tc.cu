@@ -12,11 +12,11 @@
 //
 // Shared-memory operands use the canonical K-major layout without swizzle: core matrices
 // of 8 rows x 16 bytes (4 floats), the K-adjacent core matrix at +128 bytes (leading byte
-// offset), the next group of 8 rows at +K/4 * 128 bytes (stride byte offset).  One CTA
-// (128 threads) allocates nrep*32 (rounded up to a power of two) TMEM columns, stages the
-// Shat operand once, and loops over 128-point tiles: stage the orbital tile (transposed
-// to point-major), one thread issues 4 K-steps x 3 products, commits to an mbarrier, all
-// threads wait (bounded), each warp reads its 32 TMEM lanes and forms drho for its points.
+// offset), the next group of 8 rows at +K/4 * 128 bytes (stride byte offset).  The density
+// kernel (k_rho_ws) is persistent and warp-specialised: per 128-point tile one bulk copy of
+// the tiled orbitals, four converter warps building the operands, one issuer warp issuing the
+// MMAs into one of two tensor-memory accumulators, and the converters forming drho of the
+// previous tile while the tensor cores work on the current one.
 #include <cuda.h>   // CUtensorMap and its enums (the encoder comes from the runtime)
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -31,7 +31,6 @@ namespace tc {
 
 constexpr int kM = 128;          // grid points per tile = TMEM lanes
 constexpr int kK = 32;           // orbitals per tile (N <= 32)
-constexpr int kThreadsTc = 128;
 constexpr int kMaxRepTc = 8;     // N = 32 * nrep <= 256
 constexpr uint32_t kSBO = (kK / 4) * 128;             // 1024 B between 8-row groups
 constexpr uint32_t kLBO = 128;                        // K-adjacent core matrices
@@ -119,23 +118,65 @@ __device__ __forceinline__ void fence_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-// dynamic shared memory: a_hi, a_lo (128 x 32 floats each), b_hi, b_lo (nr * 32 rows x kK)
-__global__ void __launch_bounds__(kThreadsTc)
-k_rho_tc(int N, int Np, int Ng, int nr, const float* __restrict__ phit,
+// Density, warp-specialised and persistent (one CTA per SM, 128-point tiles t = blockIdx.x,
+// blockIdx.x + gridDim.x, ...): an issuer warp keeps kRhoStages tiles of the 32-point-tiled
+// orbitals in flight (one 16 KB cp.async.bulk per tile: 4 contiguous 4 KB blocks) and issues
+// each tile's 12 MMAs; nt teams of four warps (thread <-> point) take the tiles in turn
+// (tile i -> team i % nt, with its own K-major operand buffer and tensor-memory accumulator):
+// a team converts its tile (hi/lo split) and then, while the tensor cores work on it, forms
+// drho of its previous tile from its accumulator.  mbarriers between the roles: full[s]
+// (loads -> teams), afull[b] (operands written, load slot free -> issuer), mdone[b] (MMAs
+// done -> team), tfree[b] (accumulator read -> issuer).  All waits bounded; a time-out
+// aborts every role and drains the loads.
+constexpr int kRhoStages = 4;
+constexpr int kRhoMaxTeams = 3;
+constexpr int kRhoTileB = kM * kK * 4;        // 16 KB of tiled orbitals per tile
+
+__device__ __forceinline__ void bulk_g2s_1d(uint32_t dst, const void* src, uint32_t bytes,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(bar)) : "memory");
+}
+
+// dynamic shared memory: raw[kRhoStages][128 x 32], A[nt] (hi, lo: 128 x 32 each), B (hi, lo:
+// nr * 32 x 32 each); blockDim = 32 (4 nt + 1)
+__global__ void __launch_bounds__(32 * (4 * kRhoMaxTeams + 1), 1)
+k_rho_ws(int N, int Np, int Ng, int nr, int nt, const float* __restrict__ phit,
          const float* __restrict__ shat, const double* __restrict__ rho_ref,
          double* __restrict__ rho, float* __restrict__ drho, const RepCtl* __restrict__ ctl,
          int* status) {
   extern __shared__ __align__(128) float sm[];
-  __shared__ __align__(8) uint64_t bar;
+  __shared__ __align__(8) uint64_t full[kRhoStages];
+  __shared__ __align__(8) uint64_t afull[kRhoMaxTeams], mdone[kRhoMaxTeams], tfree[kRhoMaxTeams];
   __shared__ uint32_t tmem_base;
-  float* a_hi = sm;
-  float* a_lo = sm + kM * kK;
-  float* b_hi = sm + 2 * kM * kK;
+  __shared__ int abort_flag;
+  __shared__ int committed;                         // tiles whose MMAs were committed
+  float* raw = sm;                                  // kRhoStages x 4096 floats
+  float* abuf = sm + kRhoStages * kM * kK;          // nt x (hi, lo)
+  float* b_hi = abuf + nt * 2 * kM * kK;
   float* b_lo = b_hi + nr * 32 * kK;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int ncols_used = nr * 32;
+  uint32_t acc_cols = 32;
+  while (acc_cols < (uint32_t)ncols_used) acc_cols <<= 1;
   uint32_t ncols = 32;
-  while (ncols < (uint32_t)ncols_used) ncols <<= 1;
+  while (ncols < (uint32_t)nt * acc_cols) ncols <<= 1;   // nt accumulators
+  const int ntiles = (Ng + kM - 1) / kM;
+  const int ntl = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  volatile int* abort_v = &abort_flag;
+  const int issuer_warp = 4 * nt;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -145,11 +186,18 @@ k_rho_tc(int N, int Np, int Ng, int nr, const float* __restrict__ phit,
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&bar)) : "memory");
+    abort_flag = 0;
+    committed = 0;
+    for (int s = 0; s < kRhoStages; ++s)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&full[s])) : "memory");
+    for (int b = 0; b < nt; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(saddr(&afull[b])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&mdone[b])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(saddr(&tfree[b])) : "memory");
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  // B operand: row n = r * 32 + j, column k: Shat_r[k][j] (zero beyond N); n fastest, so
-  // the global reads are coalesced rows of Shat and the K-major stores 4-way conflicted
+  // B operand once: row n = r * 32 + j, column k: Shat_r[k][j] (zero beyond N)
   for (int e = tid; e < ncols_used * kK; e += blockDim.x) {
     const int k = e / ncols_used, n = e - k * ncols_used;
     const int r = n >> 5, j = n & 31;
@@ -165,85 +213,131 @@ k_rho_tc(int N, int Np, int Ng, int nr, const float* __restrict__ phit,
   __syncthreads();
   fence_after();
   const uint32_t tbase = tmem_base;
-  const uint32_t idesc = idesc_tf32(kM, ncols_used);
-  const int ntiles = (Ng + kM - 1) / kM;
-  uint32_t phase = 0;
-  // this thread's point of the next tile, prefetched into registers while the MMAs and the
-  // epilogue of the current tile run
-  float pf[kK];
-  // tiled orbitals: the 32 loads of a warp read one contiguous 4 KB block (zero past N)
-  auto load_tile = [&](int t) {
-    const int g = t * kM + tid;
-    const float* src = phit + ((long)(g >> 5) * kK) * 32 + (g & 31);
+
+  if (warp == issuer_warp) {
+    // ---- issuer warp -------------------------------------------------------------------
+    if (lane == 0) {
+      const uint32_t idesc = idesc_tf32(kM, ncols_used);
+      auto issue = [&](int i) {
+        const int t = blockIdx.x + i * gridDim.x;
+        const int s = i % kRhoStages;
+        const uint32_t bar = saddr(&full[s]);
+        mbar_expect_tx(bar, (uint32_t)kRhoTileB);
+        bulk_g2s_1d(saddr(raw + s * kM * kK), phit + (long)t * kM * kK, (uint32_t)kRhoTileB, bar);
+      };
+      int issued = 0;
+      for (; issued < min(kRhoStages, ntl); ++issued) issue(issued);
+      for (int i = 0; i < ntl; ++i) {
+        const int b = i % nt;
+        bool ok = mbar_wait(&afull[b], (uint32_t)(i / nt) & 1u);
+        if (ok && i + kRhoStages < ntl) {   // the team is done with slot i % kRhoStages
+          issue(i + kRhoStages);
+          issued = i + kRhoStages + 1;
+        }
+        if (ok && i >= nt) ok = mbar_wait(&tfree[b], (uint32_t)((i - nt) / nt) & 1u);
+        if (!ok || *abort_v) {
+          *abort_v = 1;
+          break;
+        }
+        fence_after();
+        const float* a = abuf + b * 2 * kM * kK;
+        const uint32_t ah = saddr(a), al = saddr(a + kM * kK), bh = saddr(b_hi), bl = saddr(b_lo);
+        const uint32_t d = tbase + (uint32_t)(b * acc_cols);
 #pragma unroll
-    for (int k = 0; k < kK; ++k) pf[k] = g < Ng ? src[k * 32] : 0.0f;
-  };
-  if ((int)blockIdx.x < ntiles) load_tile(blockIdx.x);
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int g0 = t * kM;
-    // stage the orbital tile: thread <-> point, rows of 4 orbitals as 16-byte stores
-    {
-      const int p = tid;
+        for (int s = 0; s < kK / 8; ++s) {
+          const uint32_t off = s * 2 * kLBO;
+          mma_tf32(d, sdesc(ah + off), sdesc(bh + off), idesc, s > 0 ? 1u : 0u);
+          mma_tf32(d, sdesc(ah + off), sdesc(bl + off), idesc, 1u);
+          mma_tf32(d, sdesc(al + off), sdesc(bh + off), idesc, 1u);
+        }
+        mma_commit(&mdone[b]);
+        *reinterpret_cast<volatile int*>(&committed) = i + 1;
+      }
+      // loads still in flight after an abort: wait for every issued stage (bounded)
+      if (*abort_v)
+        for (int u = max(0, issued - kRhoStages); u < issued; ++u)
+          mbar_wait(&full[u % kRhoStages], (uint32_t)(u / kRhoStages) & 1u);
+    }
+    __syncwarp();
+  } else if (warp < issuer_warp) {
+    // ---- team warps: team = warp / 4, thread <-> point p = tid % 128 of the tile ------------
+    const int team = warp >> 2;
+    const int p = tid & (kM - 1);
+    const int wq = warp & 3;                        // TMEM lane quadrant of this warp
+    float ph[kK], pv[kK];   // this tile's and the team's previous tile's values at p
+    unsigned on_mask = 0;   // replicas to write (active ones)
+    for (int r = 0; r < nr; ++r)
+      if (!ctl || ctl[r].active) on_mask |= 1u << r;
+    auto epilogue = [&](int i) {   // drho of tile i from accumulator i % nt
+      const int b = i % nt;
+      if (!mbar_wait(&mdone[b], (uint32_t)(i / nt) & 1u)) {
+        *abort_v = 1;
+        return false;
+      }
+      fence_after();
+      const int g = (blockIdx.x + i * gridDim.x) * kM + p;
+      for (int r = 0; r < nr; ++r) {
+        float y[32];
+        tmem_ld32(tbase + ((uint32_t)(wq * 32) << 16) + (uint32_t)(b * acc_cols + r * 32), y);
+        float acc = 0.0f;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) acc = fmaf(pv[j], y[j], acc);
+        if (g < Ng && ((on_mask >> r) & 1u)) {
+          if (rho) rho[(long)r * Ng + g] = rho_ref[g] + (double)acc;
+          drho[(long)r * Ng + g] = acc;
+        }
+      }
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tfree[b]);
+      return true;
+    };
+    int prev = -1;
+    for (int i = team; i < ntl; i += nt) {
+      const int s = i % kRhoStages, b = i % nt;
+      bool ok = mbar_wait(&full[s], (uint32_t)(i / kRhoStages) & 1u);
+      if (ok && i >= nt) ok = mbar_wait(&mdone[b], (uint32_t)((i - nt) / nt) & 1u);  // A[b] free
+      if (!ok || *abort_v) {
+        *abort_v = 1;
+        break;
+      }
+      // this point's 32 orbital values: 32-point block p / 32, row k, column p % 32
+      const float* rs = raw + s * kM * kK + (p >> 5) * (kK * 32) + (p & 31);
+#pragma unroll
+      for (int k = 0; k < kK; ++k) ph[k] = rs[k * 32];
+      float* a_hi = abuf + b * 2 * kM * kK;
+      float* a_lo = a_hi + kM * kK;
 #pragma unroll
       for (int kc = 0; kc < kK; kc += 4) {
         float4 h4, l4;
-        split_tf32(pf[kc], h4.x, l4.x);
-        split_tf32(pf[kc + 1], h4.y, l4.y);
-        split_tf32(pf[kc + 2], h4.z, l4.z);
-        split_tf32(pf[kc + 3], h4.w, l4.w);
+        split_tf32(ph[kc], h4.x, l4.x);
+        split_tf32(ph[kc + 1], h4.y, l4.y);
+        split_tf32(ph[kc + 2], h4.z, l4.z);
+        split_tf32(ph[kc + 3], h4.w, l4.w);
         *reinterpret_cast<float4*>(&a_hi[kmaj(p, kc)]) = h4;
         *reinterpret_cast<float4*>(&a_lo[kmaj(p, kc)]) = l4;
       }
-    }
-    fence_async_smem();
-    __syncthreads();
-    if (tid == 0) {
-      fence_after();
-      const uint32_t ah = saddr(a_hi), al = saddr(a_lo), bh = saddr(b_hi), bl = saddr(b_lo);
+      fence_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&afull[b]);
+      // while the tensor cores work on tile i: drho of this team's previous tile
+      if (prev >= 0 && !epilogue(prev)) break;
 #pragma unroll
-      for (int s = 0; s < kK / 8; ++s) {
-        const uint32_t off = s * 2 * kLBO;   // two core matrices (8 tf32) per K-step
-        mma_tf32(tbase, sdesc(ah + off), sdesc(bh + off), idesc, s > 0 ? 1u : 0u);
-        mma_tf32(tbase, sdesc(ah + off), sdesc(bl + off), idesc, 1u);
-        mma_tf32(tbase, sdesc(al + off), sdesc(bh + off), idesc, 1u);
-      }
-      mma_commit(&bar);
+      for (int k = 0; k < kK; ++k) pv[k] = ph[k];
+      prev = i;
     }
-    if (t + (int)gridDim.x < ntiles) load_tile(t + gridDim.x);
-    const bool ok = mbar_wait(&bar, phase);
-    phase ^= 1u;
-    if (__syncthreads_or(!ok)) {
-      if (tid == 0) atomicCAS(status, 0, (int)RMGTD_ETIMEOUT);
-      break;
-    }
-    fence_after();
-    // epilogue: warp w owns TMEM lanes 32w .. 32w + 31 = points g0 + 32w + lane
-    const int p = warp * 32 + lane;
-    const int g = g0 + p;
-    float ph[32];
-#pragma unroll
-    for (int kc = 0; kc < kK; kc += 4) {
-      const float4 h4 = *reinterpret_cast<const float4*>(&a_hi[kmaj(p, kc)]);
-      const float4 l4 = *reinterpret_cast<const float4*>(&a_lo[kmaj(p, kc)]);
-      ph[kc] = h4.x + l4.x;
-      ph[kc + 1] = h4.y + l4.y;
-      ph[kc + 2] = h4.z + l4.z;
-      ph[kc + 3] = h4.w + l4.w;
-    }
-    for (int r = 0; r < nr; ++r) {
-      float y[32];
-      tmem_ld32(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)(r * 32), y);
-      float acc = 0.0f;
-#pragma unroll
-      for (int j = 0; j < 32; ++j) acc = fmaf(ph[j], y[j], acc);
-      if (g < Ng && (!ctl || ctl[r].active)) {
-        if (rho) rho[(long)r * Ng + g] = rho_ref[g] + (double)acc;
-        drho[(long)r * Ng + g] = acc;
-      }
-    }
-    fence_before();
-    __syncthreads();
+    if (!*abort_v && prev >= 0) epilogue(prev);
   }
+  __syncthreads();
+  if (*abort_v && tid == 0) atomicCAS(status, 0, (int)RMGTD_ETIMEOUT);
+  // every committed MMA has completed before the accumulators are freed: each team waited on
+  // its tiles' mdone; after an abort wait for the last committed one (its commit covers the
+  // earlier ones; bounded)
+  if (*abort_v && tid == 0) {
+    const int c = *reinterpret_cast<volatile int*>(&committed);
+    if (c > 0) mbar_wait(&mdone[(c - 1) % nt], (uint32_t)((c - 1) / nt) & 1u);
+  }
+  fence_before();
   __syncthreads();
   if (warp == 0) {
     fence_after();
@@ -260,19 +354,24 @@ int rho_tc(rmgtd_ctx* ctx, double* rho, float* drho, const RepCtl* ctl, int nrep
   using namespace tc;
   const int N = ctx->N, Np = ((N + 31) / 32) * 32;
   if (Np != kK || nrep > kMaxRepTc || ctx->Ng >= (1l << 31)) return 1;
-  const size_t smem = (size_t)(2 * kM * kK + 2 * nrep * 32 * kK) * sizeof(float);
-  if (!ctx->rho_tc_attr) {
-    RMGTD_CUDA(ctx, cudaFuncSetAttribute(k_rho_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(2 * kM * kK + 2 * kMaxRepTc * 32 * kK) * 4));
+  // teams: three while three accumulators fit the 512 tensor-memory columns, else two
+  const int acc = nrep <= 1 ? 32 : nrep <= 2 ? 64 : nrep <= 4 ? 128 : 256;
+  const int nt = (3 * acc <= 512) ? 3 : 2;
+  const size_t smem =
+      (size_t)(kRhoStages * kM * kK + nt * 2 * kM * kK + 2 * nrep * 32 * kK) * sizeof(float);
+  if (!ctx->rho_tc_attr) {   // the largest layout (3 teams, kMaxRepTc replicas), set once
+    RMGTD_CUDA(ctx, cudaFuncSetAttribute(
+                        k_rho_ws, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                        (int)((kRhoStages * kM * kK + 3 * 2 * kM * kK + 2 * kMaxRepTc * 32 * kK) * 4)));
     ctx->rho_tc_attr = 1;
   }
   const int ntiles = (int)((ctx->Ng + kM - 1) / kM);
-  const int grid = std::min(ntiles, std::max(1, ctx->tune_rho_blocks) * ctx->num_sms);
-  k_rho_tc<<<grid, kThreadsTc, smem, ctx->stream>>>(N, Np, (int)ctx->Ng, nrep, ctx->phi32t,
-                                                     ctx->shat32, ctx->rho_ref, rho, drho, ctl,
-                                                     ctx->status);
+  const int grid = std::min(ntiles, ctx->num_sms);
+  k_rho_ws<<<grid, 32 * (4 * nt + 1), smem, ctx->stream>>>(
+      N, Np, (int)ctx->Ng, nrep, nt, ctx->phi32t, ctx->shat32, ctx->rho_ref, rho, drho, ctl,
+      ctx->status);
   ++ctx->launches;
-  RMGTD_LAUNCH(ctx, "k_rho_tc");
+  RMGTD_LAUNCH(ctx, "k_rho_ws");
   return RMGTD_OK;
 }
 
@@ -284,7 +383,7 @@ namespace tc {
 // as D = A B^T with M = 128 rows (4 replicas x 32 orbitals of tile It, w-weighted), N = 32
 // (orbitals of tile Jt), K = grid points, accumulated in tensor memory over the CTA's chunk
 // of the grid (split-K; k_gram32_reduce adds the chunks in a fixed order).  3xTF32 as in
-// k_rho_tc.  Warp-specialised pipeline over 32-point stages: an issuer warp (one elected
+// k_rho_ws.  Warp-specialised pipeline over 32-point stages: an issuer warp (one elected
 // thread) keeps a ring of S stages of tiled TMA loads in flight (cp.async.bulk.tensor.2d,
 // completion on an mbarrier per slot) -- the 32 x 32 orbital box of tile It (and Jt) and the
 // 4 x 32 weight box -- and issues the 12 MMAs of each converted stage, committing to that
@@ -327,10 +426,6 @@ __device__ __forceinline__ float4 swz_ld4(const float* box, int r, int q) {
   return *reinterpret_cast<const float4*>(box + r * 32 + ((q ^ (r & 7)) << 2));
 }
 
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-               : "memory");
-}
 
 __global__ void __launch_bounds__(kThreadsG, 1)
 k_gram_tc(const __grid_constant__ CUtensorMap tm_phi, const __grid_constant__ CUtensorMap tm_w,

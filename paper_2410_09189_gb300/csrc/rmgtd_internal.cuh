@@ -92,7 +92,8 @@ struct rmgtd_ctx {
   double* phi = nullptr;       // [N][Ng]
   float* phi32 = nullptr;      // [N][Ng] (mixed precision)
   // the same orbitals in 32-point tiles: [ceil(Ng/32)][Np][32] with Np = 32 ceil(N/32), zero
-  // beyond N and Ng, so that a 32-orbital x 32-point block is 4 contiguous KB (tensor cores)
+  // beyond N and Ng (allocated up to whole 128-point tiles), so that a 32-orbital x 32-point
+  // block is 4 contiguous KB and a 128-point tile 16 (tensor cores)
   float* phi32t = nullptr;
   double* vion = nullptr;      // [Ng] V_loc + V_ext
   double* f_dev = nullptr;     // [N]
