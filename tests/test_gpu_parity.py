@@ -242,6 +242,36 @@ def test_trajectory_three_kicks_ragged(torch_dev):
         assert np.max(np.abs(d[:, a, :] - ref)) / scale < 1e-6
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_large_orbital_block(torch_dev, precision):
+    """N = 70 (> 64): the commutator series on the cooperative kernel (tile pairs, one grid
+    barrier per term) instead of the cluster kernel, and the density and Gram kernels with
+    three orbital tiles; two replicas on a small ragged grid against the oracle."""
+    rmgtd = _rmgtd()
+    s = _ring_small(n=(20, 22, 24), h=0.6, nvirt=55)
+    assert s.N > 64
+    raw = inputs.smooth_random_orbitals(s).reshape(s.N, s.Ng)
+    phi = oham.orthonormalize(s, raw)
+    nsteps, dt, kap = 3, 0.02, 1e-2
+    o = tddft.Options(dt=dt, H_thrs=1e-10, dP_thrs=1e-13, poisson_tol=1e-13)
+    refs = [tddft.run(s, phi, o, nsteps=nsteps, axis=a, kappa=kap) for a in range(2)]
+    prec = rmgtd.PREC_FP64 if precision == "fp64" else rmgtd.PREC_MIXED
+    with rmgtd.Context(s, raw, dt=dt, H_thrs=1e-10, dP_thrs=1e-13, poisson_tol=1e-13,
+                       nrep=2, precision=prec) as ctx:
+        for a in range(2):
+            ctx.kick(a, a, kap)
+        d = [[ctx.dipole(a) for a in range(2)]]
+        for _ in range(nsteps):
+            ctx.step(1)
+            d.append([ctx.dipole(a) for a in range(2)])
+    d = np.array(d)
+    tol = 1e-6 if precision == "fp64" else 1e-4
+    for a in range(2):
+        ref = refs[a]["dipole"]
+        scale = np.max(np.abs(ref - ref[0]))
+        assert np.max(np.abs(d[:, a, :] - ref)) / scale < tol
+
+
 def test_checkpoint_resume_is_bitwise(torch_dev, small_gs):
     rmgtd = _rmgtd()
     s, gs = small_gs
