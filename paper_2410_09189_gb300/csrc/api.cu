@@ -209,8 +209,10 @@ int dft_eval(rmgtd_ctx* ctx, const double* S, const RepCtl* ctl, unsigned long l
   if (rc) return rc;
   if (ctx->hartree_xc) {
     ph_begin(ctx, PH_HARTREE);
-    // mixed: the solve's closing phase also forms dV = dV_H + dV_xc (no separate xc pass)
+    // mixed: the solve's closing phase also forms dV = dV_H + dV_xc (no separate xc pass),
+    // and it takes the multipole moments from the density kernel when that formed them
     rc = hartree_coop(ctx, ctx->rho, ctx->vh, ctl, 0, nrep, mixed, mixed);
+    ctx->rho_mom_blocks = 0;
     ph_end(ctx);
     if (rc) return rc;
   }
@@ -568,6 +570,8 @@ static int create_impl(const rmgtd_system* sys, const rmgtd_options* opt, rmgtd_
     ctx->pcg32_Az = (float*)A(fsz * nrep);
     ctx->drho32 = (float*)A(fsz * nrep);
     ctx->rho_ref32 = (float*)A(fsz);
+    ctx->rho_mom_cap = 4L * nrep * std::max(1, ctx->num_sms);
+    ctx->rho_mom = (double*)A(sizeof(double) * ctx->rho_mom_cap);
     ctx->ghost32 = (float*)A(fsz * 4);
     if (!ctx->phi32 || !ctx->phi32t || !ctx->pcg32_Az || !ctx->dvh32 || !ctx->Href || !ctx->vh_ref ||
         !ctx->drho32 || !ctx->ghost32 || !ctx->rho_ref32)

@@ -623,6 +623,10 @@ struct Args {
   const double* rho0;
   const float* rho0f;
   float* dv_out;
+  // moments of the density change already formed by the density kernel: [rep][4][nmom]
+  // per-CTA partials (NULL: the prologue forms them)
+  const double* mom;
+  int nmom;
 };
 
 __device__ __forceinline__ float wsum(float v) { return warp_sumf(v); }
@@ -728,6 +732,18 @@ __global__ void __launch_bounds__(kThreadsC, 1) k_hartree_coop(Args<V> a) {
   // ---- prologue: multipole moments of the density (change) ----------------------------
   bool flat = false;
   if constexpr (sizeof(V) == 4) flat = a.vec4 == 2;
+  if (a.mom) {
+    // formed by the density kernel: every block sums its per-CTA partials in the same order
+    for (int q = warp; q < 4 * nrep; q += kWarps) {
+      const int rp = q >> 2, k = q & 3;
+      const double* src = a.mom + (long)q * a.nmom;
+      double acc = 0.0;
+      for (int b = lane; b < a.nmom; b += 32) acc += src[b];
+      acc = warp_sum(acc);
+      if (lane == 0) sc[4 + k][rp] = acc;
+    }
+    __syncthreads();
+  } else {
   if (flat) {
     if constexpr (sizeof(V) == 4) {
       zero_parts(4);
@@ -774,6 +790,7 @@ __global__ void __launch_bounds__(kThreadsC, 1) k_hartree_coop(Args<V> a) {
   flush(4, 4, 5, 6, 7);
   COOP_BAR();
   gsum(4, 4, 5, 6, 7);
+  }
 
   // ---- right-hand side b = 4 pi rho + ghost term, residual r = b - A x -----------------
   if (flat) {
@@ -1386,6 +1403,8 @@ int hartree_coop(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* ct
     a.rho0 = ctx->rho_ref;
     a.rho0f = ctx->rho_ref32;
     a.dv_out = nullptr;
+    a.mom = nullptr;
+    a.nmom = 0;
   };
   const void* fn;
   void* args[1];
@@ -1402,6 +1421,11 @@ int hartree_coop(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* ct
     af.Az = ctx->pcg32_Az;
     af.tol = std::max(ctx->opt.poisson_tol, kMixedPoissonTol);
     if (xc_fuse && !ctx->tune_x && ctx->rho_ref32) af.dv_out = ctx->dv32;
+    // the mixed pass: moments from the density kernel that just ran
+    if (xc_fuse && !ctx->tune_x && ctx->rho_mom_blocks > 0 && rho == ctx->rho) {
+      af.mom = ctx->rho_mom;
+      af.nmom = ctx->rho_mom_blocks;
+    }
     fn = (const void*)coop::k_hartree_coop<float>;
     args[0] = &af;
   } else {

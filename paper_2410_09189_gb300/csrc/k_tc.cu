@@ -131,6 +131,7 @@ __device__ __forceinline__ void fence_async_smem() {
 constexpr int kRhoStages = 4;
 constexpr int kRhoMaxTeams = 3;
 constexpr int kRhoTileB = kM * kK * 4;        // 16 KB of tiled orbitals per tile
+constexpr int kMomRep = 4;                    // replicas whose moments the kernel forms
 
 __device__ __forceinline__ void bulk_g2s_1d(uint32_t dst, const void* src, uint32_t bytes,
                                             uint32_t bar) {
@@ -156,13 +157,14 @@ __global__ void __launch_bounds__(32 * (4 * kRhoMaxTeams + 1), 1)
 k_rho_ws(int N, int Np, int Ng, int nr, int nt, const float* __restrict__ phit,
          const float* __restrict__ shat, const double* __restrict__ rho_ref,
          double* __restrict__ rho, float* __restrict__ drho, const RepCtl* __restrict__ ctl,
-         int* status) {
+         int* status, double* __restrict__ mom, int nx, int ny, int nz, float hgrid) {
   extern __shared__ __align__(128) float sm[];
   __shared__ __align__(8) uint64_t full[kRhoStages];
   __shared__ __align__(8) uint64_t afull[kRhoMaxTeams], mdone[kRhoMaxTeams], tfree[kRhoMaxTeams];
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
   __shared__ int committed;                         // tiles whose MMAs were committed
+  __shared__ float momw[4 * kRhoMaxTeams][4 * kMomRep];     // per-warp moment sums
   float* raw = sm;                                  // kRhoStages x 4096 floats
   float* abuf = sm + kRhoStages * kM * kK;          // nt x (hi, lo)
   float* b_hi = abuf + nt * 2 * kM * kK;
@@ -268,6 +270,12 @@ k_rho_ws(int N, int Np, int Ng, int nr, int nt, const float* __restrict__ phit,
     unsigned on_mask = 0;   // replicas to write (active ones)
     for (int r = 0; r < nr; ++r)
       if (!ctl || ctl[r].active) on_mask |= 1u << r;
+    // multipole moments of drho (charge, dipole about the box centre) for the Hartree
+    // solve's boundary values, summed per thread over its points
+    float mq[kMomRep][4];
+#pragma unroll
+    for (int r = 0; r < kMomRep; ++r) mq[r][0] = mq[r][1] = mq[r][2] = mq[r][3] = 0.0f;
+    const float cx = 0.5f * (float)(nx - 1), cy = 0.5f * (float)(ny - 1), cz = 0.5f * (float)(nz - 1);
     auto epilogue = [&](int i) {   // drho of tile i from accumulator i % nt
       const int b = i % nt;
       if (!mbar_wait(&mdone[b], (uint32_t)(i / nt) & 1u)) {
@@ -276,6 +284,13 @@ k_rho_ws(int N, int Np, int Ng, int nr, int nt, const float* __restrict__ phit,
       }
       fence_after();
       const int g = (blockIdx.x + i * gridDim.x) * kM + p;
+      float xq = 0.0f, yq = 0.0f, zq = 0.0f;
+      if (mom && g < Ng) {
+        const int ix = g % nx, rest = g / nx;
+        xq = ((float)ix - cx) * hgrid;
+        yq = ((float)(rest % ny) - cy) * hgrid;
+        zq = ((float)(rest / ny) - cz) * hgrid;
+      }
       for (int r = 0; r < nr; ++r) {
         float y[32];
         tmem_ld32(tbase + ((uint32_t)(wq * 32) << 16) + (uint32_t)(b * acc_cols + r * 32), y);
@@ -285,6 +300,14 @@ k_rho_ws(int N, int Np, int Ng, int nr, int nt, const float* __restrict__ phit,
         if (g < Ng && ((on_mask >> r) & 1u)) {
           if (rho) rho[(long)r * Ng + g] = rho_ref[g] + (double)acc;
           drho[(long)r * Ng + g] = acc;
+#pragma unroll
+          for (int rr = 0; rr < kMomRep; ++rr)   // register-indexed (r is not a constant)
+            if (rr == r) {
+              mq[rr][0] += acc;
+              mq[rr][1] += acc * xq;
+              mq[rr][2] += acc * yq;
+              mq[rr][3] += acc * zq;
+            }
         }
       }
       fence_before();
@@ -327,8 +350,23 @@ k_rho_ws(int N, int Np, int Ng, int nr, int nt, const float* __restrict__ phit,
       prev = i;
     }
     if (!*abort_v && prev >= 0) epilogue(prev);
+    if (mom) {   // warp sums of the moments, one row of momw per team warp
+#pragma unroll
+      for (int r = 0; r < kMomRep; ++r)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float v = warp_sumf(mq[r][q]);
+          if (lane == 0 && r < nr) momw[warp][r * 4 + q] = v;
+        }
+    }
   }
   __syncthreads();
+  // block moments: fixed order over the team warps, float64, one partial per CTA
+  if (mom && tid < 4 * nr) {
+    double sacc = 0.0;
+    for (int w = 0; w < 4 * nt; ++w) sacc += (double)momw[w][tid];
+    mom[(long)tid * gridDim.x + blockIdx.x] = sacc;
+  }
   if (*abort_v && tid == 0) atomicCAS(status, 0, (int)RMGTD_ETIMEOUT);
   // every committed MMA has completed before the accumulators are freed: each team waited on
   // its tiles' mdone; after an abort wait for the last committed one (its commit covers the
@@ -367,9 +405,14 @@ int rho_tc(rmgtd_ctx* ctx, double* rho, float* drho, const RepCtl* ctl, int nrep
   }
   const int ntiles = (int)((ctx->Ng + kM - 1) / kM);
   const int grid = std::min(ntiles, ctx->num_sms);
+  // multipole moments of drho for the Hartree solve that follows (partials per CTA)
+  double* mom = nullptr;
+  if (ctx->rho_mom && nrep <= kMomRep && (long)4 * nrep * grid <= ctx->rho_mom_cap)
+    mom = ctx->rho_mom;
   k_rho_ws<<<grid, 32 * (4 * nt + 1), smem, ctx->stream>>>(
       N, Np, (int)ctx->Ng, nrep, nt, ctx->phi32t, ctx->shat32, ctx->rho_ref, rho, drho, ctl,
-      ctx->status);
+      ctx->status, mom, ctx->nx, ctx->ny, ctx->nz, (float)ctx->h);
+  ctx->rho_mom_blocks = mom ? grid : 0;
   ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_rho_ws");
   return RMGTD_OK;

@@ -207,6 +207,11 @@ struct rmgtd_ctx {
   int fields_stale = 0;
   int eldyn_cluster = -1;           // cluster size of the commutator kernel (-1: not probed)
   int shat_fresh = 0;               // the last commutator launch also wrote shat32 for S1
+  // multipole moments of drho from the tensor-core density kernel: [rep][4][blocks] per-CTA
+  // partials (rho_mom_blocks = 0: not formed by the last density launch)
+  double* rho_mom = nullptr;
+  long rho_mom_cap = 0;
+  int rho_mom_blocks = 0;
 
   // learned seed of the SCF loop (attached network; buffers allocated at attach)
   rmgtd_net* net = nullptr;
