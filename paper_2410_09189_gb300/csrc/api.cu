@@ -694,9 +694,10 @@ static int capture_step(rmgtd_ctx* ctx, cudaStream_t main) {
   ctx->stream = main;
   ctx->capturing = 1;
   const long long saved_launches = ctx->launches;
-  int rc = step_begin(ctx);
+  // H_1 extrapolation, control reset and the Hartree guess in one launch; the learned seed
+  // (which changes H_1 only) after it
+  int rc = step_begin_extrapolate(ctx);
   if (!rc && ctx->net) rc = net_predict(ctx);
-  if (!rc) rc = hartree_extrapolate(ctx);
   cudaGraphConditionalHandle hs = 0;
   cudaGraph_t body = nullptr;
   if (!rc) rc = new_handle(ctx, &hs, true);
@@ -746,9 +747,10 @@ static int build_step_graph(rmgtd_ctx* ctx) {
 
 // Eager step: the host reads the control blocks after every pass.
 static int eager_step(rmgtd_ctx* ctx) {
-  int rc = step_begin(ctx);
+  // H_1 extrapolation, control reset and the Hartree guess in one launch; the learned seed
+  // (which changes H_1 only) after it
+  int rc = step_begin_extrapolate(ctx);
   if (!rc && ctx->net) rc = net_predict(ctx);
-  if (!rc) rc = hartree_extrapolate(ctx);
   if (rc) return rc;
   for (int pass = 0; pass < ctx->opt.max_scf; ++pass) {
     rc = enqueue_pass(ctx, 0, 0);

@@ -936,7 +936,7 @@ __global__ void __launch_bounds__(kThreadsC, 1) k_hartree_coop(Args<V> a) {
             float4 bc;
             const float4 ab = lap7_quad(a.r + rep * L.n, e0 - rep * L.n, ix, iy, iz, L.nx, L.ny,
                                         L.nz, bc);
-            *reinterpret_cast<float4*>(L.b + e0) = bc;
+            // (no float copy of b = r: the float path's later level-0 passes read r itself)
             *reinterpret_cast<float4*>(L.x + e0) =
                 make_float4(c * (2.0f * bc.x - c * ab.x * ih2f), c * (2.0f * bc.y - c * ab.y * ih2f),
                             c * (2.0f * bc.z - c * ab.z * ih2f), c * (2.0f * bc.w - c * ab.w * ih2f));
@@ -985,8 +985,10 @@ __global__ void __launch_bounds__(kThreadsC, 1) k_hartree_coop(Args<V> a) {
           if (!act[rep]) continue;
           int I, J, K;
           xyz_of(e - rep * C.n, C.nx, C.ny, C.dx, C.dy, I, J, K);
-          C.b[e] = restrict_residual(L.x + rep * L.n, L.b + rep * L.n, I, J, K, L.nx, L.ny,
-                                     L.nz, ih2f);
+          const float* lb = L.b + rep * L.n;
+          if constexpr (sizeof(V) == 4)
+            if (l == 0 && a.vec4) lb = a.r + rep * L.n;   // b of level 0 is r
+          C.b[e] = restrict_residual(L.x + rep * L.n, lb, I, J, K, L.nx, L.ny, L.nz, ih2f);
         }
       }
       COOP_BAR();
@@ -1069,7 +1071,7 @@ __global__ void __launch_bounds__(kThreadsC, 1) k_hartree_coop(Args<V> a) {
               float4 cc;
               const float4 ax = lap7_quad(L.x + rep * L.n, e0 - rep * L.n, ix, iy, iz, L.nx,
                                           L.ny, L.nz, cc);
-              const float4 bv = ld4(L.b + e0);
+              const float4 bv = ld4(a.r + e0);   // b of level 0 is r
               *reinterpret_cast<float4*>(L.t + e0) = make_float4(
                   cc.x + c * (bv.x - ax.x * ih2f), cc.y + c * (bv.y - ax.y * ih2f),
                   cc.z + c * (bv.z - ax.z * ih2f), cc.w + c * (bv.w - ax.w * ih2f));
@@ -1100,7 +1102,7 @@ __global__ void __launch_bounds__(kThreadsC, 1) k_hartree_coop(Args<V> a) {
             float4 cc;
             const float4 ax = lap7_quad(L.t + rep * L.n, e0 - rep * L.n, ix, iy, iz, L.nx, L.ny,
                                         L.nz, cc);
-            const float4 bv = ld4(L.b + e0);
+            const float4 bv = ld4(a.r + e0);   // b of level 0 is r
             *reinterpret_cast<float4*>(a.z + e0) = make_float4(
                 cc.x + c * (bv.x - ax.x * ih2f), cc.y + c * (bv.y - ax.y * ih2f),
                 cc.z + c * (bv.z - ax.z * ih2f), cc.w + c * (bv.w - ax.w * ih2f));
@@ -1490,6 +1492,55 @@ __global__ void k_extrap(long n, T* __restrict__ x, T* __restrict__ p1, T* __res
     p2[e] = a;
     p1[e] = t;
   }
+}
+
+// Start of a step in one launch: H_1 <- 2 H_0 - H_-1 and the control blocks reset (as
+// k_step_begin) together with the extrapolation of the Hartree guess (as k_extrap).
+template <typename T>
+__global__ void k_begin_extrap(long n, const double* __restrict__ H0,
+                               const double* __restrict__ Hm1, double* __restrict__ H1,
+                               RepCtl* ctl, int nrep, const int* __restrict__ failed,
+                               int* status, long n2, T* __restrict__ x, T* __restrict__ p1,
+                               T* __restrict__ p2) {
+  const int f = *failed;
+  if (!f) {
+    const long stride = (long)gridDim.x * blockDim.x;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += stride)
+      H1[e] = 2.0 * H0[e] - Hm1[e];
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n2; e += stride) {
+      const T t = x[e], q = p1[e];
+      x[e] = (T)3 * (t - q) + p2[e];
+      p2[e] = q;
+      p1[e] = t;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x < nrep) {
+    RepCtl& c = ctl[threadIdx.x];
+    c.active = f ? 0 : 1;
+    c.passes = 0;
+    c.terms_last = c.terms_max = c.terms_sum = 0;
+    c.status = 0;
+    c.H_err = 0.0;
+  }
+  if (!f && blockIdx.x == 0 && threadIdx.x == 0) *status = 0;
+}
+
+int step_begin_extrapolate(rmgtd_ctx* ctx) {
+  if (!ctx->hartree_xc) return step_begin(ctx);
+  const long n = (long)ctx->nrep * ctx->N * ctx->N;
+  const long n2 = (long)ctx->nrep * ctx->Ng;
+  const int bl = (int)std::max<long>(1, std::min<long>(ceil_div(n2, kThreads), 65535L));
+  if (ctx->mixed)
+    k_begin_extrap<float><<<bl, kThreads, 0, ctx->stream>>>(
+        n, ctx->H0, ctx->Hm1, ctx->H1, ctx->ctl, ctx->nrep, ctx->failed, ctx->status, n2,
+        ctx->dvh32, ctx->dvh_prev32, ctx->dvh_prev2_32);
+  else
+    k_begin_extrap<double><<<bl, kThreads, 0, ctx->stream>>>(
+        n, ctx->H0, ctx->Hm1, ctx->H1, ctx->ctl, ctx->nrep, ctx->failed, ctx->status, n2,
+        ctx->vh, ctx->vh_prev, ctx->vh_prev2);
+  ++ctx->launches;
+  RMGTD_LAUNCH(ctx, "k_begin_extrap");
+  return RMGTD_OK;
 }
 
 int hartree_extrapolate(rmgtd_ctx* ctx) {

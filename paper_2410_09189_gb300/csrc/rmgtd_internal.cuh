@@ -382,6 +382,8 @@ int eldyn(rmgtd_ctx* ctx, const double* Ha, const double* Hb, long hstride, doub
           RepCtl* ctl_out, int rep0, int nreps,
           float* shat_out = nullptr);
 int step_begin(rmgtd_ctx* ctx);
+// step_begin and hartree_extrapolate in one launch
+int step_begin_extrapolate(rmgtd_ctx* ctx);
 int scf_control(rmgtd_ctx* ctx, const unsigned long long* errbits,
                 cudaGraphConditionalHandle cond, int use_cond);
 // launches counted while the SCF body was captured, minus the Hartree-iteration body
