@@ -397,7 +397,6 @@ static int create_impl(const rmgtd_system* sys, const rmgtd_options* opt, rmgtd_
   ctx->vxc = (double*)A(gsz * nrep);
   ctx->exc = (double*)A(gsz * nrep);
   ctx->vhxc = (double*)A(gsz * nrep);
-  ctx->pcg_b = (double*)A(gsz * nrep);
   ctx->pcg_r = (double*)A(gsz * nrep);
   ctx->pcg_z = (double*)A(gsz * nrep);
   ctx->pcg_p = (double*)A(gsz * nrep);
@@ -562,7 +561,6 @@ static int create_impl(const rmgtd_system* sys, const rmgtd_options* opt, rmgtd_
       if (ctx->shat32)
         RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->shat32, 0, sizeof(float) * Np * Np * nrep, ctx->stream));
     }
-    ctx->pcg32_b = (float*)A(fsz * nrep);
     ctx->pcg32_r = (float*)A(fsz * nrep);
     ctx->pcg32_z = (float*)A(fsz * nrep);
     ctx->pcg32_p = (float*)A(fsz * nrep);

@@ -608,7 +608,7 @@ struct Args {
   const float* cinv;
   int zero_bc;
   V* x;                   // unknown (initial guess in, solution out) [rep][n0]
-  V *b, *r, *z, *p, *Ap, *Az;
+  V *r, *z, *p, *Ap, *Az;
   double* part;           // [rep][kSlots][gridDim.x] per-block partial sums
   PcgState* st;
   const RepCtl* ctl;
@@ -1415,7 +1415,6 @@ int hartree_coop(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* ct
   if (f32) {
     fill(af);
     af.x = ctx->tune_x ? (float*)ctx->tune_x : ctx->dvh32;
-    af.b = ctx->pcg32_b;
     af.r = ctx->pcg32_r;
     af.z = ctx->pcg32_z;
     af.p = ctx->pcg32_p;
@@ -1433,7 +1432,6 @@ int hartree_coop(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* ct
   } else {
     fill(ad);
     ad.x = ctx->tune_x ? (double*)ctx->tune_x : vh;
-    ad.b = ctx->pcg_b;
     ad.r = ctx->pcg_r;
     ad.z = ctx->pcg_z;
     ad.p = ctx->pcg_p;
@@ -1477,25 +1475,12 @@ int hartree_coop(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* ct
   return RMGTD_OK;
 }
 
-// Initial guess of the first Hartree solve of a step: quadratic extrapolation in time of
-// the last three solutions, x <- 3 x(t) - 3 x(t - dt) + x(t - 2 dt) (error O(dt^3) against
-// O(dt^2) for the linear 2 x(t) - x(t - dt)); p2 <- p1, p1 <- x(t).  Only the CG starting
-// point changes, not the solution it converges to.
-template <typename T>
-__global__ void k_extrap(long n, T* __restrict__ x, T* __restrict__ p1, T* __restrict__ p2,
-                         const int* __restrict__ failed) {
-  if (*failed) return;
-  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n;
-       e += (long)gridDim.x * blockDim.x) {
-    const T t = x[e], a = p1[e];
-    x[e] = (T)3 * (t - a) + p2[e];
-    p2[e] = a;
-    p1[e] = t;
-  }
-}
-
 // Start of a step in one launch: H_1 <- 2 H_0 - H_-1 and the control blocks reset (as
-// k_step_begin) together with the extrapolation of the Hartree guess (as k_extrap).
+// k_step_begin) together with the initial guess of the step's first Hartree solve, the
+// quadratic extrapolation in time of the last three solutions,
+//   x <- 3 x(t) - 3 x(t - dt) + x(t - 2 dt)
+// (error O(dt^3) against O(dt^2) for the linear 2 x(t) - x(t - dt)); p2 <- p1, p1 <- x(t).
+// Only the CG starting point changes, not the solution it converges to.
 template <typename T>
 __global__ void k_begin_extrap(long n, const double* __restrict__ H0,
                                const double* __restrict__ Hm1, double* __restrict__ H1,
@@ -1543,20 +1528,6 @@ int step_begin_extrapolate(rmgtd_ctx* ctx) {
   return RMGTD_OK;
 }
 
-int hartree_extrapolate(rmgtd_ctx* ctx) {
-  if (!ctx->hartree_xc) return RMGTD_OK;
-  const long n = (long)ctx->nrep * ctx->Ng;
-  const int bl = (int)std::max<long>(1, std::min<long>(ceil_div(n, kThreads), 65535L));
-  if (ctx->mixed)
-    k_extrap<float><<<bl, kThreads, 0, ctx->stream>>>(n, ctx->dvh32, ctx->dvh_prev32,
-                                                      ctx->dvh_prev2_32, ctx->failed);
-  else
-    k_extrap<double><<<bl, kThreads, 0, ctx->stream>>>(n, ctx->vh, ctx->vh_prev, ctx->vh_prev2,
-                                                       ctx->failed);
-  ++ctx->launches;
-  RMGTD_LAUNCH(ctx, "k_extrap");
-  return RMGTD_OK;
-}
 
 // no history yet: p1 = p2 = current, so the first extrapolations reproduce the current guess
 int hartree_reset_history(rmgtd_ctx* ctx) {

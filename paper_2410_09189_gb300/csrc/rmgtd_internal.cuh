@@ -135,7 +135,7 @@ struct rmgtd_ctx {
   float* shat32 = nullptr;     // [nrep][Np][Np] float32 density-change matrix (mixed)
   double* vh_prev = nullptr;   // [nrep][Ng] V_H one step earlier (initial-guess history)
   double* vh_prev2 = nullptr;  // [nrep][Ng] V_H two steps earlier
-  float *pcg32_b = nullptr, *pcg32_r = nullptr, *pcg32_z = nullptr, *pcg32_p = nullptr,
+  float *pcg32_r = nullptr, *pcg32_z = nullptr, *pcg32_p = nullptr,
         *pcg32_Ap = nullptr, *pcg32_Az = nullptr;   // [nrep][Ng] float32 CG vectors (mixed)
   float* drho32 = nullptr;     // [nrep][Ng] rho - rho_ref in float32 (mixed)
   float* ghost32 = nullptr;    // [4][Ng] float32 copy of the ghost response fields (mixed)
@@ -148,7 +148,7 @@ struct rmgtd_ctx {
   size_t gram_part_elems = 0;
 
   // Hartree solve
-  double *pcg_b = nullptr, *pcg_r = nullptr, *pcg_z = nullptr, *pcg_p = nullptr,
+  double *pcg_r = nullptr, *pcg_z = nullptr, *pcg_p = nullptr,
          *pcg_Ap = nullptr, *pcg_Az = nullptr;    // [nrep][Ng]
   unsigned* bar2 = nullptr;          // grid-barrier counter of the persistent Hartree solve
   int coop_attr_set[2] = {0, 0};     // persistent Hartree kernel configured (float64, float32)
@@ -382,7 +382,7 @@ int eldyn(rmgtd_ctx* ctx, const double* Ha, const double* Hb, long hstride, doub
           RepCtl* ctl_out, int rep0, int nreps,
           float* shat_out = nullptr);
 int step_begin(rmgtd_ctx* ctx);
-// step_begin and hartree_extrapolate in one launch
+// step_begin and the quadratic extrapolation of the Hartree guess in one launch
 int step_begin_extrapolate(rmgtd_ctx* ctx);
 int scf_control(rmgtd_ctx* ctx, const unsigned long long* errbits,
                 cudaGraphConditionalHandle cond, int use_cond);
@@ -394,7 +394,6 @@ int orthonormalize(rmgtd_ctx* ctx);
 // k_poisson.cu
 int setup_multigrid(rmgtd_ctx* ctx);
 int poisson_red_cap(int num_sms, int red_blocks);
-int hartree_extrapolate(rmgtd_ctx* ctx);
 // Hartree solve of every active replica in one cooperative launch; f32 = 1: float32
 // correction solve of the mixed path (reads drho32, writes dvh32)
 // xc_fuse (float32 path): the kernel's closing phase also writes dv32 = dV_H + dV_xc
