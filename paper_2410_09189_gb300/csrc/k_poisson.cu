@@ -23,7 +23,10 @@
 // beta A p_old is carried as a vector, so the 37-point operator is applied once per
 // iteration to z, and (p, A p) follows from four dot products taken with A z.  Every block
 // sums the per-block partials of a reduction in the same order, so all blocks take the
-// same decisions and the result does not depend on timing.
+// same decisions and the result does not depend on timing.  Float32 level-0 passes work on
+// quads (4 consecutive x-points per thread, 16-byte loads).  In the mixed pass the prologue
+// takes the multipole moments of the density change from the density kernel, and a closing
+// phase forms the pass's potential change dV_H + dV_xc (the float32 xc increment).
 #include <math.h>
 
 #include "fastdiv.h"

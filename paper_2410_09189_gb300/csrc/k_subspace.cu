@@ -510,7 +510,8 @@ k_gram32_reduce(int N, int Np, int nsplit, int nrep, const float* __restrict__ p
   // the sum carries ~2^-44 relative error with float32 instructions only -- GB300's float64
   // rate (~1/64) made the former float64 accumulation the kernel's bound.
   float shi = 0.0f, slo = 0.0f;
-  if (e < NpNp) {
+  // only the upper triangle i <= j is used (mirrored below)
+  if (e < NpNp && (int)(e % Np) >= (int)(e / Np)) {
     for (int k0 = wp; k0 < nsplit; k0 += 256) {
       float v[8];
 #pragma unroll

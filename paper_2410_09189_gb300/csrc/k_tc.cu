@@ -674,10 +674,14 @@ k_gram_tc(const __grid_constant__ CUtensorMap tm_phi, const __grid_constant__ CU
     const bool on = !ctl || ctl[r].active;
     const long NpNp = (long)Np * Np;
     float* out = part + ((long)blockIdx.x * nrep + r) * NpNp + (long)(It * 32 + lane) * Np + Jt * 32;
+    // diagonal tile pairs: only j >= i is read by the reduction (4-column groups from the
+    // one holding the diagonal)
+    const int j0 = diag ? (lane & ~3) : 0;
 #pragma unroll
     for (int j = 0; j < 32; j += 4)
-      *reinterpret_cast<float4*>(out + j) =
-          on ? make_float4(y[j], y[j + 1], y[j + 2], y[j + 3]) : make_float4(0.f, 0.f, 0.f, 0.f);
+      if (j >= j0)
+        *reinterpret_cast<float4*>(out + j) =
+            on ? make_float4(y[j], y[j + 1], y[j + 2], y[j + 3]) : make_float4(0.f, 0.f, 0.f, 0.f);
   }
   fence_before();
   __syncthreads();
