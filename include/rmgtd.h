@@ -259,6 +259,18 @@ int rmgtd_autotune(rmgtd_ctx* ctx, int choice[4]);
 int rmgtd_set_tuning(rmgtd_ctx* ctx, const int choice[4]);
 int rmgtd_get_tuning(const rmgtd_ctx* ctx, int choice[4]);
 
+/* Preconditioner of the Hartree conjugate-gradient solve (Section 2.2's Poisson problem with
+ * the 12th-order operator of Eq. 2; both precisions).  The operator and the stopping test are
+ * the same for both; only the iteration count and rounding differ.
+ *   RMGTD_PRECOND_DST (default): the 3-D sine transform (DST-I) diagonalising the Toeplitz
+ *     part of the 12th-order operator, applied in float32 -- used when its matrices and tiles
+ *     fit in shared memory (lines up to ~100 points), else the multigrid V-cycle runs;
+ *   RMGTD_PRECOND_MG: the float32 multigrid V-cycle of 7-point operators.
+ * Other values: RMGTD_EINVAL, nothing changed; a context in a batch: RMGTD_ESTATE. */
+#define RMGTD_PRECOND_DST 0
+#define RMGTD_PRECOND_MG 1
+int rmgtd_set_hartree_preconditioner(rmgtd_ctx* ctx, int kind);
+
 /* Several contexts (different systems, each with its replicas) stepped by one CUDA graph per
  * time step: their steps are captured back to back into a single graph, launched once per
  * step on the contexts' common stream.  All contexts must use the same stream; attach the

@@ -984,6 +984,22 @@ int rmgtd_set_tuning(rmgtd_ctx* ctx, const int choice[4]) {
   return RMGTD_OK;
 }
 
+int rmgtd_set_hartree_preconditioner(rmgtd_ctx* ctx, int kind) {
+  if (!ctx) return set_error(nullptr, RMGTD_EINVAL, "ctx is NULL");
+  if (kind != RMGTD_PRECOND_DST && kind != RMGTD_PRECOND_MG)
+    return set_error(ctx, RMGTD_EINVAL, "set_hartree_preconditioner: unknown kind");
+  if (ctx->in_batch)
+    return set_error(ctx, RMGTD_ESTATE, "set_hartree_preconditioner: context belongs to a batch");
+  RMGTD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  ctx->hartree_precond = kind;
+  // the solve's arguments are baked into the step graph: rebuild it
+  if (ctx->step_exec) cudaGraphExecDestroy(ctx->step_exec);
+  if (ctx->step_graph) cudaGraphDestroy(ctx->step_graph);
+  ctx->step_exec = nullptr;
+  ctx->step_graph = nullptr;
+  return RMGTD_OK;
+}
+
 int rmgtd_get_tuning(const rmgtd_ctx* ctx, int choice[4]) {
   if (!ctx) return set_error(nullptr, RMGTD_EINVAL, "ctx is NULL");
   if (!choice) return RMGTD_EINVAL;

@@ -38,6 +38,10 @@ namespace rmgtd {
 constexpr double kPi = 3.14159265358979323846;
 constexpr float kJacobiW = 6.0f / 7.0f;
 constexpr int kTailMax = 4096;
+constexpr size_t kDstSmemMax = 160 * 1024;   // sine-transform preconditioner: larger grids
+                                              // fall back to the multigrid V-cycle
+constexpr int kCoarseDirect = 64;   // a level below the finest with at most this many points is
+                                    // the coarsest (solved exactly with its precomputed inverse)
 constexpr int kPre = 2, kPost = 2, kCoarseSweeps = 40;
 static_assert(kPre == 2, "the pre-smoothing pass fuses exactly two sweeps from zero");
 // relative residual of the float32 correction solve of the mixed path: the unknown is the
@@ -320,8 +324,9 @@ __device__ void tail_jacobi(const Tail& L, int l, float* x, float* t, const floa
 }
 
 // V-cycle of the tail levels for one replica inside one block (all threads of the block):
-// b_in / x_out are that replica's arrays of the first tail level, sm the dynamic shared
-// memory.  Down: both pre-sweeps from zero in one pass, residual, restriction; up:
+// b_in / x_out are that replica's arrays of the first tail level (x_out NULL: the result
+// stays in shared memory, at sm), sm the dynamic shared memory, cinv the transposed inverse
+// of the coarsest level's operator in shared memory (NULL: Jacobi sweeps there).  Down: both pre-sweeps from zero in one pass, residual, restriction; up:
 // prolongation, two post-sweeps ping-ponging between x and t.
 __device__ void tail_vcycle(const Tail& L, const float* __restrict__ b_in,
                             float* __restrict__ x_out, const float* __restrict__ cinv, float* sm) {
@@ -341,11 +346,12 @@ __device__ void tail_vcycle(const Tail& L, const float* __restrict__ b_in,
   for (int l = 0; l < L.nl; ++l) {
     const bool coarsest = (l == L.nl - 1);
     if (coarsest && cinv) {
-      // exact solve with the precomputed inverse of the coarsest operator
+      // exact solve with the precomputed inverse of the coarsest operator (cinv: its
+      // transpose in shared memory, so a warp reads 32 consecutive words per j)
       const int nc = L.n[l];
       for (int i = threadIdx.x; i < nc; i += blockDim.x) {
         float a = 0.0f;
-        for (int j = 0; j < nc; ++j) a = fmaf(cinv[i * nc + j], bs[l][j], a);
+        for (int j = 0; j < nc; ++j) a = fmaf(cinv[j * nc + i], bs[l][j], a);
         xs[l][i] = a;
       }
       __syncthreads();
@@ -439,7 +445,8 @@ __device__ void tail_vcycle(const Tail& L, const float* __restrict__ b_in,
       for (int g = threadIdx.x; g < n; g += blockDim.x) xs[l][g] = ts[l][g];
     __syncthreads();
   }
-  for (int g = threadIdx.x; g < n0; g += blockDim.x) x_out[g] = xs[0][g];
+  if (x_out)
+    for (int g = threadIdx.x; g < n0; g += blockDim.x) x_out[g] = xs[0][g];
   __syncthreads();
 }
 
@@ -477,7 +484,9 @@ __global__ void k_coarse_inverse(int nx, int ny, int nz, double h, double* __res
       if (i != k) M[(long)i * n + k] = 0.0;
     __syncthreads();
   }
-  for (long e = threadIdx.x; e < (long)n * n; e += blockDim.x) out[e] = (float)Minv[e];
+  // transposed: out[j n + i] = Minv[i][j] (the tail's threads i read consecutive words)
+  for (long e = threadIdx.x; e < (long)n * n; e += blockDim.x)
+    out[(e % n) * n + e / n] = (float)Minv[e];
 }
 
 // ---- host set-up ---------------------------------------------------------------------------
@@ -496,6 +505,7 @@ int setup_multigrid(rmgtd_ctx* ctx) {
     ctx->mg.push_back(L);
     if ((int)ctx->mg.size() >= kMaxLevels) break;
     if ((nx & 1) || (ny & 1) || (nz & 1) || nx < 4 || ny < 4 || nz < 4) break;
+    if (ctx->mg.size() >= 2 && L.n <= kCoarseDirect) break;
     nx /= 2;
     ny /= 2;
     nz /= 2;
@@ -511,6 +521,12 @@ int setup_multigrid(rmgtd_ctx* ctx) {
   size_t smem = 0;
   if (ctx->mg_tail_level >= 0)
     for (int l = ctx->mg_tail_level; l < nl; ++l) smem += 3 * sizeof(float) * ctx->mg[l].n;
+  // the coarsest level's inverse joins them when it is small (read from global otherwise)
+  ctx->mg_cinv_smem = 0;
+  if (ctx->mg_tail_level >= 0 && ctx->mg[nl - 1].n <= kCoarseDirect) {
+    smem += sizeof(float) * ctx->mg[nl - 1].n * ctx->mg[nl - 1].n;
+    ctx->mg_cinv_smem = 1;
+  }
   ctx->mg_tail_smem = smem;
   for (int l = 0; l < nl; ++l) {
     MgLevel& L = ctx->mg[l];
@@ -575,6 +591,34 @@ int setup_multigrid(rmgtd_ctx* ctx) {
   if (!ctx->mg_table) return set_error(ctx, RMGTD_ENOMEM, "level table");
   RMGTD_CUDA(ctx, cudaMemcpy(ctx->mg_table, &lt, sizeof(LevelTable), cudaMemcpyHostToDevice));
 
+  // sine-transform preconditioner tables: S_x, S_y, S_z (float32, row stride n rounded up to
+  // 4, zero padding) and the 1-D eigenvalues lx, ly, lz of the 12th-order operator's Toeplitz
+  // part, l[k] = -(a_0 + 2 sum_m a_m cos(m theta_k)) / h^2, theta_k = pi (k+1) / (n+1)
+  {
+    const int dims[3] = {ctx->nx, ctx->ny, ctx->nz};
+    size_t nS = 0;
+    for (int ax = 0; ax < 3; ++ax) nS += (size_t)dims[ax] * ((dims[ax] + 3) & ~3);
+    std::vector<float> tab(nS + dims[0] + dims[1] + dims[2], 0.0f);
+    size_t o = 0, ol = nS;
+    for (int ax = 0; ax < 3; ++ax) {
+      const int n = dims[ax], np = (n + 3) & ~3;
+      for (int k = 0; k < n; ++k) {
+        for (int j = 0; j < n; ++j)
+          tab[o + (size_t)k * np + j] = (float)std::sin(kPi * (double)(j + 1) * (k + 1) / (n + 1));
+        const double th = kPi * (k + 1) / (n + 1);
+        double sym = fd_coef(0);
+        for (int m = 1; m <= kFdRadius; ++m) sym += 2.0 * fd_coef(m) * std::cos(m * th);
+        tab[ol + k] = (float)(-sym / (ctx->h * ctx->h));
+      }
+      o += (size_t)n * np;
+      ol += n;
+    }
+    ctx->dst_tab = (float*)dev_alloc(ctx, sizeof(float) * tab.size());
+    if (!ctx->dst_tab) return set_error(ctx, RMGTD_ENOMEM, "sine-transform tables");
+    RMGTD_CUDA(ctx, cudaMemcpy(ctx->dst_tab, tab.data(), sizeof(float) * tab.size(),
+                               cudaMemcpyHostToDevice));
+  }
+
   ctx->ghost = (double*)dev_alloc(ctx, sizeof(double) * 4 * (size_t)ctx->Ng);
   if (!ctx->ghost) return set_error(ctx, RMGTD_ENOMEM, "ghost fields");
   const Grid3 G{ctx->nx, ctx->ny, ctx->nz, ctx->h};
@@ -609,6 +653,11 @@ struct Args {
   const double* gf;       // float64 ghost response fields [4][n0]
   const float* gf32;      // float32 copy (mixed path)
   const float* cinv;
+  int cinv_smem;          // copy cinv next to the tail levels in shared memory
+  // sine-transform preconditioner instead of the V-cycle (dst != 0): S_x, S_y, S_z (row
+  // strides rounded up to 4) then lx, ly, lz, in global memory; copied to shared memory
+  int dst;
+  const float* dst_tab;
   int zero_bc;
   V* x;                   // unknown (initial guess in, solution out) [rep][n0]
   V *r, *z, *p, *Ap, *Az;
@@ -631,6 +680,126 @@ struct Args {
   const double* mom;
   int nmom;
 };
+
+// ---- sine-transform preconditioner (float32) ------------------------------------------------
+// z = M r with M = S (Lambda^-1 (S r)) scaled by 8 / ((nx+1)(ny+1)(nz+1)): S is the 3-D DST-I
+// (per axis S_n[j][k] = sin(pi (j+1)(k+1) / (n+1)), symmetric, S_n S_n = (n+1)/2 I) and
+// Lambda(kx, ky, kz) = lx[kx] + ly[ky] + lz[kz] the eigenvalues of the Toeplitz part of the
+// 12th-order operator, l[k] = -(a_0 + 2 sum_m a_m cos(m theta_k)) / h^2, theta_k =
+// pi (k+1) / (n+1).  The operator with zero ghosts differs from that Toeplitz part only in the
+// rows within the stencil radius of a face, so M A has its spectrum close to 1 (the CG
+// residual falls by ~0.03-0.07 per iteration, against ~0.25 with the 7-point V-cycle).
+// One application is five passes of 1-D transforms (x, y, z with the scaling and the inverse
+// z, y, x), each over every line of the grid along its axis, split evenly over the blocks.
+struct DstGeom {
+  int n[3];      // line length per axis (nx, ny, nz)
+  int npad[3];   // row stride of S_n in shared memory (n rounded up to 4)
+};
+
+// One pass along axis ax over this block's share of the lines (all threads of the block):
+// out(line, j) = sum_k S[j][k] in(line, k); with scale (z axis): forward, times
+// norm / Lambda, inverse.  S: this axis's matrix in shared memory (row stride npad); tA, tB:
+// shared tiles of n x Wp floats (Wp = the block's line count rounded up to even); lbase,
+// lxy: shared scratch of one int / float per line.  Flat indices are split into (row,
+// column) incrementally (no division per element); int offsets (nrep n0 < 2^31).
+template <typename VI, typename VO>
+__device__ void dst_pass(int ax, const VI* __restrict__ in, VO* __restrict__ out, int nrep,
+                         int nx, int ny, int nz, const float* S, int npad, float* tA, float* tB,
+                         int* lbase, float* lxy, bool scale, const float* __restrict__ lam,
+                         float norm) {
+  const int n = ax == 0 ? nx : (ax == 1 ? ny : nz);
+  const int n0 = nx * ny * nz, plane = nx * ny;
+  const int nlines = nrep * (n0 / n);
+  const int l0 = (int)((long)blockIdx.x * nlines / gridDim.x);
+  const int l1 = (int)((long)(blockIdx.x + 1) * nlines / gridDim.x);
+  const int W = l1 - l0, Wp = W + (W & 1);
+  if (W == 0) return;   // (uniform over the block)
+  const int stride = ax == 0 ? 1 : (ax == 1 ? nx : plane);
+  const int tot = W * n;
+  // first element of each of this block's lines (and, for the scaling, lx[kx] + ly[ky])
+  for (int w = threadIdx.x; w < W; w += blockDim.x) {
+    const int l = l0 + w;
+    int b;
+    if (ax == 0) {
+      b = l * nx;
+    } else if (ax == 1) {
+      const int q = l / nx;
+      b = q * plane + (l - q * nx);
+    } else {
+      const int q = l / plane;
+      b = q * n0 + (l - q * plane);
+    }
+    lbase[w] = b;
+    if (scale) {
+      const int yx = l - (l / plane) * plane;
+      const int ky = yx / nx, kx = yx - ky * nx;
+      lxy[w] = lam[kx] + lam[nx + ky];
+    }
+  }
+  __syncthreads();
+  // e = q D + r over this block's elements, stepping by the block size
+  auto walk = [&](int D, auto&& body) {
+    int q = threadIdx.x / D, r = threadIdx.x - q * D;
+    const int dq = blockDim.x / D, dr = blockDim.x - dq * D;
+    for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+      body(e, q, r);
+      q += dq;
+      r += dr;
+      if (r >= D) {
+        r -= D;
+        ++q;
+      }
+    }
+  };
+  if (ax == 0)   // lines are rows: the block's rows are one contiguous range (w = q, k = r)
+    walk(n, [&](int e, int w, int k) { tA[k * Wp + w] = (float)in[l0 * nx + e]; });
+  else           // element k of consecutive lines: consecutive x (k = q, w = r)
+    walk(W, [&](int, int k, int w) { tA[k * Wp + w] = (float)in[lbase[w] + k * stride]; });
+  if (W & 1)
+    for (int k = threadIdx.x; k < n; k += blockDim.x) tA[k * Wp + W] = 0.0f;
+  __syncthreads();
+  // src -> dst: each thread 4 outputs j (one float4 of S row k, S symmetric) x 2 lines
+  const int njg = npad >> 2, nwp = Wp >> 1;
+  auto transform = [&](const float* src, float* dst) {
+    for (int t = threadIdx.x; t < njg * nwp; t += blockDim.x) {
+      const int jg = t / nwp, wp = t - jg * nwp;
+      float c0x = 0.f, c0y = 0.f, c1x = 0.f, c1y = 0.f, c2x = 0.f, c2y = 0.f, c3x = 0.f,
+            c3y = 0.f;
+#pragma unroll 4
+      for (int k = 0; k < n; ++k) {
+        const float4 sv = *reinterpret_cast<const float4*>(S + k * npad + 4 * jg);
+        const float2 v = *reinterpret_cast<const float2*>(src + k * Wp + 2 * wp);
+        c0x = fmaf(sv.x, v.x, c0x);
+        c0y = fmaf(sv.x, v.y, c0y);
+        c1x = fmaf(sv.y, v.x, c1x);
+        c1y = fmaf(sv.y, v.y, c1y);
+        c2x = fmaf(sv.z, v.x, c2x);
+        c2y = fmaf(sv.z, v.y, c2y);
+        c3x = fmaf(sv.w, v.x, c3x);
+        c3y = fmaf(sv.w, v.y, c3y);
+      }
+      const int j = 4 * jg;
+      if (j < n) *reinterpret_cast<float2*>(dst + j * Wp + 2 * wp) = make_float2(c0x, c0y);
+      if (j + 1 < n) *reinterpret_cast<float2*>(dst + (j + 1) * Wp + 2 * wp) = make_float2(c1x, c1y);
+      if (j + 2 < n) *reinterpret_cast<float2*>(dst + (j + 2) * Wp + 2 * wp) = make_float2(c2x, c2y);
+      if (j + 3 < n) *reinterpret_cast<float2*>(dst + (j + 3) * Wp + 2 * wp) = make_float2(c3x, c3y);
+    }
+    __syncthreads();
+  };
+  transform(tA, tB);
+  const float* res = tB;
+  if (scale) {
+    const float* lz = lam + nx + ny;
+    walk(W, [&](int, int k, int w) { tB[k * Wp + w] *= norm / (lxy[w] + lz[k]); });
+    __syncthreads();
+    transform(tB, tA);
+    res = tA;
+  }
+  if (ax == 0)
+    walk(n, [&](int e, int w, int k) { out[l0 * nx + e] = (VO)res[k * Wp + w]; });
+  else
+    walk(W, [&](int, int k, int w) { out[lbase[w] + k * stride] = (VO)res[k * Wp + w]; });
+}
 
 __device__ __forceinline__ float wsum(float v) { return warp_sumf(v); }
 __device__ __forceinline__ double wsum(double v) { return warp_sum(v); }
@@ -662,6 +831,7 @@ __global__ void __launch_bounds__(kThreadsC, 1) k_hartree_coop(Args<V> a) {
   __shared__ int act[kMaxRep];   // replica still iterating
   __shared__ int act0[kMaxRep];  // replica solved by this launch
   __shared__ int any_act;
+  __shared__ int s_tail_local, s_tail_rep;   // block-local tail (see below)
   const int G = gridDim.x;
   const int gstride = G * blockDim.x;
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -853,6 +1023,25 @@ __global__ void __launch_bounds__(kThreadsC, 1) k_hartree_coop(Args<V> a) {
       put(1, rp, rr);
     }
   }
+  // the coarsest tail level's (transposed) inverse, when small: a shared-memory copy after
+  // the tail levels (its load latency overlaps the barrier below; flush syncs the block)
+  const float* cinv = a.cinv;
+  if (a.dst) {
+    // the sine-transform matrices into shared memory (the tiles follow them)
+    int off = 0;
+    for (int ax = 0; ax < 3; ++ax) {
+      const int na = ax == 0 ? nx : (ax == 1 ? ny : nz);
+      off += na * ((na + 3) & ~3);
+    }
+    for (int e = threadIdx.x; e < off; e += blockDim.x) smem_tail[e] = a.dst_tab[e];
+  } else if (a.cinv && a.cinv_smem && nmulti < nl) {
+    int off = 0;
+    for (int l = 0; l < T.T.nl; ++l) off += 3 * T.T.n[l];
+    const int nc = T.T.n[T.T.nl - 1];
+    float* cs = smem_tail + off;
+    for (int e = threadIdx.x; e < nc * nc; e += blockDim.x) cs[e] = a.cinv[e];
+    cinv = cs;
+  }
   flush(2, 0, 1, 0, 0);
   COOP_BAR();
   gsum(2, 0, 1, 0, 0);
@@ -877,6 +1066,25 @@ __global__ void __launch_bounds__(kThreadsC, 1) k_hartree_coop(Args<V> a) {
   }
   __syncthreads();
 
+  // Blocks whose points of the level above the tail all belong to one replica (that level
+  // has at most one point per thread and a multiple of the block size per replica) run the
+  // tail of that replica themselves, redundantly, and read its result from shared memory in
+  // the first post-sweep above it: no grid barrier and no global round trip in between.
+  // (kept in shared memory: s_tail_local, s_tail_rep = -1 for a block without such points)
+  if (threadIdx.x == 0) {
+    s_tail_local = 0;
+    s_tail_rep = -1;
+    if (nmulti >= 2 && nmulti < nl) {
+      const long na = T.L[nmulti - 1].n;
+      if (na % blockDim.x == 0 && na * nrep <= (long)gstride) {
+        s_tail_local = 1;
+        const long e0 = (long)blockIdx.x * blockDim.x;
+        if (e0 < na * nrep) s_tail_rep = (int)(e0 / na);
+      }
+    }
+  }
+  __syncthreads();
+
   int it = 0;
   while (true) {
     if (threadIdx.x == 0) {
@@ -887,6 +1095,46 @@ __global__ void __launch_bounds__(kThreadsC, 1) k_hartree_coop(Args<V> a) {
     __syncthreads();
     if (!any_act) break;
 
+    // ---- sine-transform preconditioner z = M r: five passes, one grid barrier each -------
+    if (a.dst) {
+      int npd[3], off = 0;
+      long tile = 0;
+      for (int ax = 0; ax < 3; ++ax) {
+        const int na = ax == 0 ? nx : (ax == 1 ? ny : nz);
+        npd[ax] = (na + 3) & ~3;
+        const long nlines = (long)nrep * n0 / na;
+        const long wmax = (nlines + G - 1) / G + 1;
+        if ((long)na * wmax > tile) tile = (long)na * wmax;
+      }
+      const float* Sx = smem_tail;
+      const float* Sy = Sx + nx * npd[0];
+      const float* Sz = Sy + ny * npd[1];
+      off = nx * npd[0] + ny * npd[1] + nz * npd[2];
+      float* tA = smem_tail + off;
+      float* tB = tA + ((tile + 3) & ~3L);
+      long wmx = 0;
+      for (int ax = 0; ax < 3; ++ax) {
+        const int na = ax == 0 ? nx : (ax == 1 ? ny : nz);
+        const long wm = ((long)nrep * n0 / na + G - 1) / G + 1;
+        if (wm > wmx) wmx = wm;
+      }
+      int* lbase = reinterpret_cast<int*>(tB + ((tile + 3) & ~3L));
+      float* lxy = reinterpret_cast<float*>(lbase + ((wmx + 3) & ~3L));
+      const float* lam = a.dst_tab + off;
+      const float norm = (float)(8.0 / ((double)(nx + 1) * (ny + 1) * (nz + 1)));
+      float* W1 = T.L[0].x;
+      float* W2 = T.L[0].t;
+      dst_pass<V, float>(0, a.r, W1, nrep, nx, ny, nz, Sx, npd[0], tA, tB, lbase, lxy, false, lam, norm);
+      COOP_BAR();
+      dst_pass<float, float>(1, W1, W2, nrep, nx, ny, nz, Sy, npd[1], tA, tB, lbase, lxy, false, lam, norm);
+      COOP_BAR();
+      dst_pass<float, float>(2, W2, W1, nrep, nx, ny, nz, Sz, npd[2], tA, tB, lbase, lxy, true, lam, norm);
+      COOP_BAR();
+      dst_pass<float, float>(1, W1, W2, nrep, nx, ny, nz, Sy, npd[1], tA, tB, lbase, lxy, false, lam, norm);
+      COOP_BAR();
+      dst_pass<float, V>(0, W2, a.z, nrep, nx, ny, nz, Sx, npd[0], tA, tB, lbase, lxy, false, lam, norm);
+      COOP_BAR();
+    } else {
     // ---- V-cycle z = M r: down leg over the multi-block levels --------------------------
     for (int l = 0; l < nmulti; ++l) {
       const Level& L = T.L[l];
@@ -996,12 +1244,16 @@ __global__ void __launch_bounds__(kThreadsC, 1) k_hartree_coop(Args<V> a) {
       }
       COOP_BAR();
     }
-    // ---- tail levels: one block per replica ---------------------------------------------
+    // ---- tail levels: one block per replica, or every block its own replica's -----------
     if (nmulti < nl) {
       const Level& Lt = T.L[nmulti];
-      for (int rp = blockIdx.x; rp < nrep; rp += G)
-        if (act[rp]) tail_vcycle(T.T, Lt.b + rp * Lt.n, Lt.x + rp * Lt.n, a.cinv, smem_tail);
-      COOP_BAR();
+      const bool loc = s_tail_local;
+      const int r0 = loc ? (s_tail_rep >= 0 ? s_tail_rep : nrep) : blockIdx.x;
+      const int r1 = loc ? r0 + 1 : nrep;
+      for (int rp = r0; rp < r1; rp += G)
+        if (act[rp])
+          tail_vcycle(T.T, Lt.b + rp * Lt.n, loc ? nullptr : Lt.x + rp * Lt.n, cinv, smem_tail);
+      if (!loc) COOP_BAR();
     }
     // ---- up leg: x += P x_coarse, two post-sweeps (the last one writes z) ---------------
     for (int l = min(nmulti, nl - 1) - 1; l >= 0; --l) {
@@ -1018,7 +1270,8 @@ __global__ void __launch_bounds__(kThreadsC, 1) k_hartree_coop(Args<V> a) {
           int ix, iy, iz;
           xyz_of(e - rep * L.n, L.nx, L.ny, L.dx, L.dy, ix, iy, iz);
           const float* xr = L.x + rep * L.n;
-          const float* xc = C.x + rep * C.n;
+          // (a block-local tail holds this point's replica: rep == s_tail_rep)
+          const float* xc = (s_tail_local && l == nmulti - 1) ? smem_tail : C.x + rep * C.n;
           const int g = e - rep * L.n, plane = L.nx * L.ny;
           auto corr = [&](int qx, int qy, int qz, int q) {
             return xr[q] + prolong_point(xc, qx, qy, qz, C.nx, C.ny, C.nz);
@@ -1135,6 +1388,7 @@ __global__ void __launch_bounds__(kThreadsC, 1) k_hartree_coop(Args<V> a) {
         if (act[fdiv(e, T.L[0].dn)]) a.z[e] = (V)T.L[0].x[e];
       COOP_BAR();
     }
+    }   // V-cycle
 
     // ---- A z and the dot products (r,z), (z,Az), (z,Ap_old), (p_old,Az) ------------------
     const bool first = (it == 0);
@@ -1379,13 +1633,38 @@ __global__ void __launch_bounds__(kThreadsC, 1) k_hartree_coop(Args<V> a) {
 
 }  // namespace coop
 
+// shared memory of the sine-transform preconditioner for a launch of `grid` blocks: the three
+// matrices and two tiles of (n x the largest line count of a block, rounded up to even)
+static size_t dst_smem_bytes(const rmgtd_ctx* ctx, int nrep, int grid) {
+  const int dims[3] = {ctx->nx, ctx->ny, ctx->nz};
+  size_t fl = 0, tile = 0, wmx = 0;
+  for (int ax = 0; ax < 3; ++ax) {
+    const size_t n = dims[ax];
+    fl += n * ((n + 3) & ~(size_t)3);
+    const size_t nlines = (size_t)nrep * ctx->Ng / n;
+    const size_t wmax = (nlines + grid - 1) / grid + 1;
+    tile = std::max(tile, n * wmax);
+    wmx = std::max(wmx, wmax);
+  }
+  // + per-line scratch (one int and one float per line)
+  return sizeof(float) * (fl + 2 * ((tile + 3) & ~(size_t)3) + 2 * ((wmx + 3) & ~(size_t)3));
+}
+
 // host launcher of the persistent solve; f32 selects the mixed-path correction solve
 int hartree_coop(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* ctl, int zero_bc,
                  int nrep, int f32, int xc_fuse) {
   if (nrep > coop::kMaxRep) return set_error(ctx, RMGTD_EINVAL, "too many replicas");
   if (f32 && (!ctx->drho32 || !ctx->ghost32))
     return set_error(ctx, RMGTD_ESTATE, "mixed Hartree solve without float32 buffers");
-  const size_t smem = ctx->mg_tail_smem;
+  const int kk = f32 ? 1 : 0;
+  const int grid = std::max(1, (ctx->coop_attr_set[kk] ? ctx->coop_grid[kk]
+                                                       : std::min(ctx->num_sms, ctx->red_cap)) /
+                                   std::max(1, ctx->tune_coop_div));
+  size_t smem = ctx->mg_tail_smem;
+  const size_t dsm = dst_smem_bytes(ctx, nrep, grid);
+  const int use_dst = ctx->dst_tab && ctx->hartree_precond == RMGTD_PRECOND_DST &&
+                      dsm <= kDstSmemMax && (long)nrep * ctx->Ng < (1L << 31);
+  if (use_dst) smem = std::max(smem, dsm);
   auto fill = [&](auto& a) {
     a.lt = (const LevelTable*)ctx->mg_table;
     a.nrep = nrep;
@@ -1395,6 +1674,9 @@ int hartree_coop(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* ct
     a.gf = ctx->ghost;
     a.gf32 = ctx->ghost32;
     a.cinv = ctx->mg_cinv;
+    a.cinv_smem = ctx->mg_cinv_smem;
+    a.dst = use_dst;
+    a.dst_tab = ctx->dst_tab;
     a.zero_bc = zero_bc;
     a.part = ctx->red_part;
     a.st = ctx->pcg;
@@ -1461,9 +1743,12 @@ int hartree_coop(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* ct
     ctx->coop_grid[k] = std::min(per_sm * ctx->num_sms, ctx->red_cap);
     ctx->coop_attr_set[k] = 1;
   }
+  // the tiles of the sine-transform passes were sized for this grid
+  if (std::max(1, ctx->coop_grid[k] / std::max(1, ctx->tune_coop_div)) != grid)
+    return set_error(ctx, RMGTD_ECUDA, "persistent Hartree grid differs from the planned one");
   RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->bar2, 0, sizeof(unsigned), ctx->stream));
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(std::max(1, ctx->coop_grid[k] / std::max(1, ctx->tune_coop_div)));
+  cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(coop::kThreadsC);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = ctx->stream;

@@ -176,7 +176,10 @@ struct rmgtd_ctx {
   std::vector<rmgtd::MgLevel> mg;   // multi-CTA levels (level 0 = fine grid)
   int mg_tail_level = -1;           // first level solved inside one CTA
   size_t mg_tail_smem = 0;
-  float* mg_cinv = nullptr;         // inverse of the coarsest operator (tail), or NULL
+  float* mg_cinv = nullptr;         // inverse of the coarsest operator (tail, transposed), or NULL
+  int mg_cinv_smem = 0;             // the persistent solve keeps mg_cinv in shared memory
+  float* dst_tab = nullptr;         // sine-transform preconditioner: S_x, S_y, S_z, lx, ly, lz
+  int hartree_precond = RMGTD_PRECOND_DST;
   void* mg_table = nullptr;         // device level table of the persistent solve
 
   // control

@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "librmgtd.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ENOTCONVERGED, EDIVERGED, ETIMEOUT, ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
 PREC_FP64, PREC_MIXED = 0, 1
+PRECOND_DST, PRECOND_MG = 0, 1      # Hartree CG preconditioner (rmgtd_set_hartree_preconditioner)
 F64, F32, C128, C64 = 0, 1, 2, 3
 MAT_P_RE, MAT_P_IM, MAT_H0, MAT_HM1, MAT_HCORE, MAT_MX, MAT_MY, MAT_MZ, MAT_S = range(9)
 NPHASES = 6
@@ -121,6 +122,7 @@ def load_library(path: Optional[str] = None):
         "rmgtd_autotune": (i, [vp, _c_int_p]),
         "rmgtd_set_tuning": (i, [vp, _c_int_p]),
         "rmgtd_get_tuning": (i, [vp, _c_int_p]),
+        "rmgtd_set_hartree_preconditioner": (i, [vp, i]),
         "rmgtd_batch_create": (i, [ctypes.POINTER(vp), i, ctypes.POINTER(vp)]),
         "rmgtd_batch_destroy": (None, [vp]),
         "rmgtd_batch_step": (i, [vp, i, ctypes.POINTER(ctypes.POINTER(CStats))]),
@@ -290,6 +292,10 @@ class Context:
         c = np.ascontiguousarray(choice, dtype=np.int32)
         assert c.shape == (4,)
         self._check(self._lib.rmgtd_set_tuning(self._ctx, _iptr(c)))
+
+    def set_hartree_preconditioner(self, kind: int):
+        """PRECOND_DST (sine transform, the default where it fits) or PRECOND_MG (V-cycle)."""
+        self._check(self._lib.rmgtd_set_hartree_preconditioner(self._ctx, int(kind)))
 
     def tuning(self):
         c = np.zeros(4, dtype=np.int32)

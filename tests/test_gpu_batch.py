@@ -136,4 +136,7 @@ def test_set_tuning_rejects_bad_values(lib):
         with pytest.raises(lib.RmgtdError):
             ctx.set_tuning(bad)
         assert ctx.tuning() == before
+    for bad in (-1, 2):
+        with pytest.raises(lib.RmgtdError):
+            ctx.set_hartree_preconditioner(bad)
     ctx.close()

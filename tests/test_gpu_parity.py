@@ -101,7 +101,10 @@ def test_setup_matrices(torch_dev):
         assert abs(ctx.energy(0) - pr.energy(st["P0"], st["aux"])) < 1e-9
 
 
-def test_hartree_and_xc(torch_dev):
+@pytest.mark.parametrize("precond", ["dst", "mg"])
+def test_hartree_and_xc(torch_dev, precond):
+    """Hartree solve with either preconditioner (the operator and stopping test are the same)
+    against the oracle's; the sine-transform preconditioner needs fewer CG iterations."""
     torch = torch_dev
     rmgtd = _rmgtd()
     s = _ring_small(n=(40, 36, 44), h=0.4)
@@ -112,10 +115,19 @@ def test_hartree_and_xc(torch_dev):
     ref = opoisson.hartree(s, rho, tol=1e-13)
     vref, eref = olda.lda(rho.ravel())
     with rmgtd.Context(s, raw, poisson_tol=1e-13) as ctx:
+        iters = {}
         rd = torch.from_numpy(rho.ravel()).cuda()
-        vh = torch.zeros_like(rd)
-        ctx.hartree(rd, vh)
-        assert _rel(vh.cpu().numpy(), ref.ravel()) < 1e-10
+        for kind in (["mg", "dst"] if precond == "dst" else ["mg"]):
+            ctx.set_hartree_preconditioner(rmgtd.PRECOND_DST if kind == "dst" else rmgtd.PRECOND_MG)
+            vh = torch.zeros_like(rd)
+            n0, i0 = ctx.profile_counters()
+            ctx.hartree(rd, vh)
+            n1, i1 = ctx.profile_counters()
+            assert n1 - n0 == 1
+            iters[kind] = i1 - i0
+            assert _rel(vh.cpu().numpy(), ref.ravel()) < 1e-10
+        if precond == "dst":
+            assert iters["dst"] < iters["mg"], iters
         vxc = torch.empty_like(rd)
         exc = torch.empty_like(rd)
         ctx.xc(rd, vxc, exc)
@@ -397,10 +409,11 @@ def test_mixed_trajectory_small_system(torch_dev, small_gs):
     assert abs(np.trace(P).real - s.n_electrons) < 1e-11
 
 
-@pytest.mark.parametrize("tuning", [None, (3, 1, 1, 1), (2, 1, 2, 2)])
+@pytest.mark.parametrize("tuning", [None, (3, 1, 1, 1), (2, 1, 2, 2), "multigrid"])
 def test_mixed_three_kicks_ragged(torch_dev, tuning):
     """Three kicks on a ragged grid with two orbital tiles (N = 37): the default launch
-    configuration and the tensor-core Gram kernel (diagonal and off-diagonal tile pairs)."""
+    configuration, the tensor-core Gram kernel (diagonal and off-diagonal tile pairs) and the
+    multigrid preconditioner of the Hartree solve."""
     rmgtd = _rmgtd()
     s = _ring_small(n=(30, 34, 38), h=0.5, nvirt=22)
     raw = inputs.smooth_random_orbitals(s).reshape(s.N, s.Ng)
@@ -410,7 +423,9 @@ def test_mixed_three_kicks_ragged(torch_dev, tuning):
     refs = [tddft.run(s, phi, o, nsteps=nsteps, axis=a, kappa=kap) for a in range(3)]
     with rmgtd.Context(s, raw, dt=dt, H_thrs=1e-9, dP_thrs=1e-12, nrep=3,
                        precision=rmgtd.PREC_MIXED) as ctx:
-        if tuning is not None:
+        if tuning == "multigrid":
+            ctx.set_hartree_preconditioner(rmgtd.PRECOND_MG)
+        elif tuning is not None:
             ctx.set_tuning(tuning)
             assert ctx.tuning() == tuning
         for a in range(3):
