@@ -42,6 +42,13 @@ constexpr size_t kDstSmemMax = 160 * 1024;   // sine-transform preconditioner: l
                                               // fall back to the multigrid V-cycle
 constexpr int kCoarseDirect = 64;   // a level below the finest with at most this many points is
                                     // the coarsest (solved exactly with its precomputed inverse)
+// row stride (rounded up to 4) and size in floats of the sine-transform preconditioner's
+// folded matrices for lines of n points (ceil(n/2)^2 and floor(n/2)^2 entries, padded)
+__host__ __device__ inline int dst_pad4(int v) { return (v + 3) & ~3; }
+__host__ __device__ inline int dst_mat_floats(int n) {
+  const int hp = (n + 1) >> 1, h = n >> 1;
+  return hp * dst_pad4(hp) + h * dst_pad4(h);
+}
 constexpr int kPre = 2, kPost = 2, kCoarseSweeps = 40;
 static_assert(kPre == 2, "the pre-smoothing pass fuses exactly two sweeps from zero");
 // relative residual of the float32 correction solve of the mixed path: the unknown is the
@@ -164,6 +171,9 @@ __device__ __forceinline__ float lap7f(const float* __restrict__ x, int ix, int 
 // scalar neighbours, so one quad of a stencil needs 7 (7-point) or 29 (37-point) vector loads
 // instead of 28 or 148 scalar ones, with all of them in flight together.  Sums keep the
 // scalar kernels' order (+x, -x, +y, -y, +z, -z; absent neighbours add zero).
+__device__ __forceinline__ uint32_t saddr_f(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
 __device__ __forceinline__ float4 ld4(const float* p) {
   return *reinterpret_cast<const float4*>(p);
 }
@@ -597,20 +607,24 @@ int setup_multigrid(rmgtd_ctx* ctx) {
   {
     const int dims[3] = {ctx->nx, ctx->ny, ctx->nz};
     size_t nS = 0;
-    for (int ax = 0; ax < 3; ++ax) nS += (size_t)dims[ax] * ((dims[ax] + 3) & ~3);
+    for (int ax = 0; ax < 3; ++ax) nS += (size_t)dst_mat_floats(dims[ax]);
     std::vector<float> tab(nS + dims[0] + dims[1] + dims[2], 0.0f);
     size_t o = 0, ol = nS;
     for (int ax = 0; ax < 3; ++ax) {
-      const int n = dims[ax], np = (n + 3) & ~3;
+      const int n = dims[ax], hp = (n + 1) / 2, h = n / 2;
+      const int pe = dst_pad4(hp), po = dst_pad4(h);
+      auto S = [&](int j, int k) { return (float)std::sin(kPi * (double)(j + 1) * (k + 1) / (n + 1)); };
+      for (int k = 0; k < hp; ++k)
+        for (int i = 0; i < hp; ++i) tab[o + (size_t)k * pe + i] = S(2 * i, k);
+      for (int k = 0; k < h; ++k)
+        for (int i = 0; i < h; ++i) tab[o + (size_t)hp * pe + (size_t)k * po + i] = S(2 * i + 1, k);
       for (int k = 0; k < n; ++k) {
-        for (int j = 0; j < n; ++j)
-          tab[o + (size_t)k * np + j] = (float)std::sin(kPi * (double)(j + 1) * (k + 1) / (n + 1));
         const double th = kPi * (k + 1) / (n + 1);
         double sym = fd_coef(0);
         for (int m = 1; m <= kFdRadius; ++m) sym += 2.0 * fd_coef(m) * std::cos(m * th);
         tab[ol + k] = (float)(-sym / (ctx->h * ctx->h));
       }
-      o += (size_t)n * np;
+      o += (size_t)dst_mat_floats(n);
       ol += n;
     }
     ctx->dst_tab = (float*)dev_alloc(ctx, sizeof(float) * tab.size());
@@ -691,20 +705,23 @@ struct Args {
 // residual falls by ~0.03-0.07 per iteration, against ~0.25 with the 7-point V-cycle).
 // One application is five passes of 1-D transforms (x, y, z with the scaling and the inverse
 // z, y, x), each over every line of the grid along its axis, split evenly over the blocks.
-struct DstGeom {
-  int n[3];      // line length per axis (nx, ny, nz)
-  int npad[3];   // row stride of S_n in shared memory (n rounded up to 4)
-};
+// The matrices are stored folded: S[j][n-1-k] = (-1)^j S[j][k], so with the line's sums
+// P_k = x_k + x_{n-1-k} (k < n/2; P of the middle point of an odd line is that point) and
+// differences M_k = x_k - x_{n-1-k}, the even outputs are Se P and the odd ones So M, with
+// Se[k][i] = S[2i][k] (ceil(n/2) x ceil(n/2)) and So[k][i] = S[2i+1][k] (floor(n/2) squared),
+// row strides rounded up to 4: half the multiply-adds and half the table of a plain product.
+// (dst_pad4 and dst_mat_floats, the folded tables' row stride and size, are defined at the
+// top of this file)
 
 // One pass along axis ax over this block's share of the lines (all threads of the block):
 // out(line, j) = sum_k S[j][k] in(line, k); with scale (z axis): forward, times
-// norm / Lambda, inverse.  S: this axis's matrix in shared memory (row stride npad); tA, tB:
+// norm / Lambda, inverse.  S: this axis's folded matrices Se, So in shared memory; tA, tB:
 // shared tiles of n x Wp floats (Wp = the block's line count rounded up to even); lbase,
 // lxy: shared scratch of one int / float per line.  Flat indices are split into (row,
 // column) incrementally (no division per element); int offsets (nrep n0 < 2^31).
 template <typename VI, typename VO>
 __device__ void dst_pass(int ax, const VI* __restrict__ in, VO* __restrict__ out, int nrep,
-                         int nx, int ny, int nz, const float* S, int npad, float* tA, float* tB,
+                         int nx, int ny, int nz, const float* S, float* tA, float* tB,
                          int* lbase, float* lxy, bool scale, const float* __restrict__ lam,
                          float norm) {
   const int n = ax == 0 ? nx : (ax == 1 ? ny : nz);
@@ -737,11 +754,11 @@ __device__ void dst_pass(int ax, const VI* __restrict__ in, VO* __restrict__ out
     }
   }
   __syncthreads();
-  // e = q D + r over this block's elements, stepping by the block size
-  auto walk = [&](int D, auto&& body) {
+  // e = q D + r over [0, total), stepping by the block size
+  auto walk_n = [&](int total, int D, auto&& body) {
     int q = threadIdx.x / D, r = threadIdx.x - q * D;
     const int dq = blockDim.x / D, dr = blockDim.x - dq * D;
-    for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
       body(e, q, r);
       q += dq;
       r += dr;
@@ -751,24 +768,53 @@ __device__ void dst_pass(int ax, const VI* __restrict__ in, VO* __restrict__ out
       }
     }
   };
+  auto walk = [&](int D, auto&& body) { walk_n(tot, D, body); };
+  // float input: asynchronous 4-byte copies into the tile (all of a thread's loads in flight
+  // at once, one wait); float64 input: loads converted to float32
+  auto put = [&](float* dst, const VI* src) {
+    if constexpr (sizeof(VI) == 4)
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(saddr_f(dst)), "l"(src)
+                   : "memory");
+    else
+      *dst = (float)*src;
+  };
   if (ax == 0)   // lines are rows: the block's rows are one contiguous range (w = q, k = r)
-    walk(n, [&](int e, int w, int k) { tA[k * Wp + w] = (float)in[l0 * nx + e]; });
+    walk(n, [&](int e, int w, int k) { put(tA + k * Wp + w, in + l0 * nx + e); });
   else           // element k of consecutive lines: consecutive x (k = q, w = r)
-    walk(W, [&](int, int k, int w) { tA[k * Wp + w] = (float)in[lbase[w] + k * stride]; });
+    walk(W, [&](int, int k, int w) { put(tA + k * Wp + w, in + lbase[w] + k * stride); });
   if (W & 1)
     for (int k = threadIdx.x; k < n; k += blockDim.x) tA[k * Wp + W] = 0.0f;
+  if constexpr (sizeof(VI) == 4) asm volatile("cp.async.wait_all;" ::: "memory");
   __syncthreads();
-  // src -> dst: each thread 4 outputs j (one float4 of S row k, S symmetric) x 2 lines
-  const int njg = npad >> 2, nwp = Wp >> 1;
-  auto transform = [&](const float* src, float* dst) {
-    for (int t = threadIdx.x; t < njg * nwp; t += blockDim.x) {
-      const int jg = t / nwp, wp = t - jg * nwp;
+  // src -> dst: fold src's rows k, n-1-k into P (row k) and M (row n-1-k), then each thread
+  // forms 4 outputs j of one parity (one float4 of Se or So row k) x 2 lines
+  const int hp = (n + 1) >> 1, h = n >> 1;
+  const int nge = (hp + 3) >> 2, ngo = (h + 3) >> 2;
+  const float* Se = S;
+  const float* So = S + hp * dst_pad4(hp);
+  const int nwp = Wp >> 1;
+  auto transform = [&](float* src, float* dst) {
+    walk_n(h * Wp, Wp, [&](int, int k, int w) {
+      const float a = src[k * Wp + w], b = src[(n - 1 - k) * Wp + w];
+      src[k * Wp + w] = a + b;
+      src[(n - 1 - k) * Wp + w] = a - b;
+    });
+    __syncthreads();
+    for (int t = threadIdx.x; t < (nge + ngo) * nwp; t += blockDim.x) {
+      const int g = t / nwp, wp = t - g * nwp;
+      const int odd = g >= nge;
+      const int jg = odd ? g - nge : g;
+      const float* Sm = odd ? So : Se;
+      const int ps = odd ? 4 * ngo : 4 * nge, kn = odd ? h : hp;
+      // row of P_k (k) or M_k (n-1-k)
+      const float* sp = src + (odd ? (n - 1) * Wp : 0) + 2 * wp;
+      const int sstep = odd ? -Wp : Wp;
       float c0x = 0.f, c0y = 0.f, c1x = 0.f, c1y = 0.f, c2x = 0.f, c2y = 0.f, c3x = 0.f,
             c3y = 0.f;
 #pragma unroll 4
-      for (int k = 0; k < n; ++k) {
-        const float4 sv = *reinterpret_cast<const float4*>(S + k * npad + 4 * jg);
-        const float2 v = *reinterpret_cast<const float2*>(src + k * Wp + 2 * wp);
+      for (int k = 0; k < kn; ++k) {
+        const float4 sv = *reinterpret_cast<const float4*>(Sm + k * ps + 4 * jg);
+        const float2 v = *reinterpret_cast<const float2*>(sp + k * sstep);
         c0x = fmaf(sv.x, v.x, c0x);
         c0y = fmaf(sv.x, v.y, c0y);
         c1x = fmaf(sv.y, v.x, c1x);
@@ -778,11 +824,11 @@ __device__ void dst_pass(int ax, const VI* __restrict__ in, VO* __restrict__ out
         c3x = fmaf(sv.w, v.x, c3x);
         c3y = fmaf(sv.w, v.y, c3y);
       }
-      const int j = 4 * jg;
+      const int j = 8 * jg + odd;   // outputs j, j + 2, j + 4, j + 6
       if (j < n) *reinterpret_cast<float2*>(dst + j * Wp + 2 * wp) = make_float2(c0x, c0y);
-      if (j + 1 < n) *reinterpret_cast<float2*>(dst + (j + 1) * Wp + 2 * wp) = make_float2(c1x, c1y);
-      if (j + 2 < n) *reinterpret_cast<float2*>(dst + (j + 2) * Wp + 2 * wp) = make_float2(c2x, c2y);
-      if (j + 3 < n) *reinterpret_cast<float2*>(dst + (j + 3) * Wp + 2 * wp) = make_float2(c3x, c3y);
+      if (j + 2 < n) *reinterpret_cast<float2*>(dst + (j + 2) * Wp + 2 * wp) = make_float2(c1x, c1y);
+      if (j + 4 < n) *reinterpret_cast<float2*>(dst + (j + 4) * Wp + 2 * wp) = make_float2(c2x, c2y);
+      if (j + 6 < n) *reinterpret_cast<float2*>(dst + (j + 6) * Wp + 2 * wp) = make_float2(c3x, c3y);
     }
     __syncthreads();
   };
@@ -1028,11 +1074,7 @@ __global__ void __launch_bounds__(kThreadsC, 1) k_hartree_coop(Args<V> a) {
   const float* cinv = a.cinv;
   if (a.dst) {
     // the sine-transform matrices into shared memory (the tiles follow them)
-    int off = 0;
-    for (int ax = 0; ax < 3; ++ax) {
-      const int na = ax == 0 ? nx : (ax == 1 ? ny : nz);
-      off += na * ((na + 3) & ~3);
-    }
+    const int off = dst_mat_floats(nx) + dst_mat_floats(ny) + dst_mat_floats(nz);
     for (int e = threadIdx.x; e < off; e += blockDim.x) smem_tail[e] = a.dst_tab[e];
   } else if (a.cinv && a.cinv_smem && nmulti < nl) {
     int off = 0;
@@ -1097,19 +1139,17 @@ __global__ void __launch_bounds__(kThreadsC, 1) k_hartree_coop(Args<V> a) {
 
     // ---- sine-transform preconditioner z = M r: five passes, one grid barrier each -------
     if (a.dst) {
-      int npd[3], off = 0;
       long tile = 0;
       for (int ax = 0; ax < 3; ++ax) {
         const int na = ax == 0 ? nx : (ax == 1 ? ny : nz);
-        npd[ax] = (na + 3) & ~3;
         const long nlines = (long)nrep * n0 / na;
         const long wmax = (nlines + G - 1) / G + 1;
         if ((long)na * wmax > tile) tile = (long)na * wmax;
       }
       const float* Sx = smem_tail;
-      const float* Sy = Sx + nx * npd[0];
-      const float* Sz = Sy + ny * npd[1];
-      off = nx * npd[0] + ny * npd[1] + nz * npd[2];
+      const float* Sy = Sx + dst_mat_floats(nx);
+      const float* Sz = Sy + dst_mat_floats(ny);
+      const int off = dst_mat_floats(nx) + dst_mat_floats(ny) + dst_mat_floats(nz);
       float* tA = smem_tail + off;
       float* tB = tA + ((tile + 3) & ~3L);
       long wmx = 0;
@@ -1124,15 +1164,15 @@ __global__ void __launch_bounds__(kThreadsC, 1) k_hartree_coop(Args<V> a) {
       const float norm = (float)(8.0 / ((double)(nx + 1) * (ny + 1) * (nz + 1)));
       float* W1 = T.L[0].x;
       float* W2 = T.L[0].t;
-      dst_pass<V, float>(0, a.r, W1, nrep, nx, ny, nz, Sx, npd[0], tA, tB, lbase, lxy, false, lam, norm);
+      dst_pass<V, float>(0, a.r, W1, nrep, nx, ny, nz, Sx, tA, tB, lbase, lxy, false, lam, norm);
       COOP_BAR();
-      dst_pass<float, float>(1, W1, W2, nrep, nx, ny, nz, Sy, npd[1], tA, tB, lbase, lxy, false, lam, norm);
+      dst_pass<float, float>(1, W1, W2, nrep, nx, ny, nz, Sy, tA, tB, lbase, lxy, false, lam, norm);
       COOP_BAR();
-      dst_pass<float, float>(2, W2, W1, nrep, nx, ny, nz, Sz, npd[2], tA, tB, lbase, lxy, true, lam, norm);
+      dst_pass<float, float>(2, W2, W1, nrep, nx, ny, nz, Sz, tA, tB, lbase, lxy, true, lam, norm);
       COOP_BAR();
-      dst_pass<float, float>(1, W1, W2, nrep, nx, ny, nz, Sy, npd[1], tA, tB, lbase, lxy, false, lam, norm);
+      dst_pass<float, float>(1, W1, W2, nrep, nx, ny, nz, Sy, tA, tB, lbase, lxy, false, lam, norm);
       COOP_BAR();
-      dst_pass<float, V>(0, W2, a.z, nrep, nx, ny, nz, Sx, npd[0], tA, tB, lbase, lxy, false, lam, norm);
+      dst_pass<float, V>(0, W2, a.z, nrep, nx, ny, nz, Sx, tA, tB, lbase, lxy, false, lam, norm);
       COOP_BAR();
     } else {
     // ---- V-cycle z = M r: down leg over the multi-block levels --------------------------
@@ -1640,7 +1680,7 @@ static size_t dst_smem_bytes(const rmgtd_ctx* ctx, int nrep, int grid) {
   size_t fl = 0, tile = 0, wmx = 0;
   for (int ax = 0; ax < 3; ++ax) {
     const size_t n = dims[ax];
-    fl += n * ((n + 3) & ~(size_t)3);
+    fl += (size_t)dst_mat_floats(dims[ax]);
     const size_t nlines = (size_t)nrep * ctx->Ng / n;
     const size_t wmax = (nlines + grid - 1) / grid + 1;
     tile = std::max(tile, n * wmax);
