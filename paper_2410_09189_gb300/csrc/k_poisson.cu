@@ -42,12 +42,21 @@ constexpr size_t kDstSmemMax = 160 * 1024;   // sine-transform preconditioner: l
                                               // fall back to the multigrid V-cycle
 constexpr int kCoarseDirect = 64;   // a level below the finest with at most this many points is
                                     // the coarsest (solved exactly with its precomputed inverse)
-// row stride (rounded up to 4) and size in floats of the sine-transform preconditioner's
-// folded matrices for lines of n points (ceil(n/2)^2 and floor(n/2)^2 entries, padded)
-__host__ __device__ inline int dst_pad4(int v) { return (v + 3) & ~3; }
+// The sine-transform preconditioner's folded matrices for lines of n points, as tensor-core
+// A operands: kn x kn (kn = ceil(n/2) for the even outputs, floor(n/2) for the odd ones),
+// output-major with rows padded to 16 and a row stride of 4 mod 32 words covering kn rounded
+// up to 8 (zero padding), so the m16n8k8 fragment loads hit 32 distinct banks.
+__host__ __device__ inline int dst_astride(int kn) { return 32 * ((((kn + 7) & ~7) + 27) / 32) + 4; }
+__host__ __device__ inline int dst_arows(int kn) { return (kn + 15) & ~15; }
 __host__ __device__ inline int dst_mat_floats(int n) {
   const int hp = (n + 1) >> 1, h = n >> 1;
-  return hp * dst_pad4(hp) + h * dst_pad4(h);
+  return dst_arows(hp) * dst_astride(hp) + dst_arows(h) * dst_astride(h);
+}
+// tile columns for W lines: W rounded up to 8, and to 8 or 24 mod 32 (conflict-free B loads)
+__host__ __device__ inline int dst_wpad(int W) {
+  int Wp = (W + 7) & ~7;
+  if ((Wp & 31) == 0 || (Wp & 31) == 16) Wp += 8;
+  return Wp;
 }
 constexpr int kPre = 2, kPost = 2, kCoarseSweeps = 40;
 static_assert(kPre == 2, "the pre-smoothing pass fuses exactly two sweeps from zero");
@@ -612,12 +621,23 @@ int setup_multigrid(rmgtd_ctx* ctx) {
     size_t o = 0, ol = nS;
     for (int ax = 0; ax < 3; ++ax) {
       const int n = dims[ax], hp = (n + 1) / 2, h = n / 2;
-      const int pe = dst_pad4(hp), po = dst_pad4(h);
-      auto S = [&](int j, int k) { return (float)std::sin(kPi * (double)(j + 1) * (k + 1) / (n + 1)); };
-      for (int k = 0; k < hp; ++k)
-        for (int i = 0; i < hp; ++i) tab[o + (size_t)k * pe + i] = S(2 * i, k);
-      for (int k = 0; k < h; ++k)
-        for (int i = 0; i < h; ++i) tab[o + (size_t)hp * pe + (size_t)k * po + i] = S(2 * i + 1, k);
+      const int ase = dst_astride(hp), aso = dst_astride(h);
+      // S[j][k] rounded to TF32 (nearest, ties to even: 10 explicit mantissa bits)
+      auto S = [&](int j, int k) {
+        const float v = (float)std::sin(kPi * (double)(j + 1) * (k + 1) / (n + 1));
+        uint32_t u;
+        memcpy(&u, &v, 4);
+        u += 0xFFFu + ((u >> 13) & 1u);
+        u &= 0xFFFFE000u;
+        float r;
+        memcpy(&r, &u, 4);
+        return r;
+      };
+      for (int i = 0; i < hp; ++i)
+        for (int k = 0; k < hp; ++k) tab[o + (size_t)i * ase + k] = S(2 * i, k);
+      const size_t oo = o + (size_t)dst_arows(hp) * ase;
+      for (int i = 0; i < h; ++i)
+        for (int k = 0; k < h; ++k) tab[oo + (size_t)i * aso + k] = S(2 * i + 1, k);
       for (int k = 0; k < n; ++k) {
         const double th = kPi * (k + 1) / (n + 1);
         double sym = fd_coef(0);
@@ -708,10 +728,13 @@ struct Args {
 // The matrices are stored folded: S[j][n-1-k] = (-1)^j S[j][k], so with the line's sums
 // P_k = x_k + x_{n-1-k} (k < n/2; P of the middle point of an odd line is that point) and
 // differences M_k = x_k - x_{n-1-k}, the even outputs are Se P and the odd ones So M, with
-// Se[k][i] = S[2i][k] (ceil(n/2) x ceil(n/2)) and So[k][i] = S[2i+1][k] (floor(n/2) squared),
-// row strides rounded up to 4: half the multiply-adds and half the table of a plain product.
-// (dst_pad4 and dst_mat_floats, the folded tables' row stride and size, are defined at the
-// top of this file)
+// Se[i][k] = S[2i][k] (ceil(n/2) x ceil(n/2)) and So[i][k] = S[2i+1][k] (floor(n/2) squared):
+// half the multiply-adds and half the table of a plain product.  The products run on the
+// tensor cores as warp-level m16n8k8 TF32 MMAs (float32 accumulation; the tables are stored
+// already rounded to TF32): they are 16 x 88 x 32 tiles inside the persistent solve, where a
+// warp's MMA and its fragment loads cost less than any staging for larger tiles would.
+// (dst_astride, dst_arows, dst_mat_floats and dst_wpad, the tables' and tiles' layout, are
+// defined at the top of this file)
 
 // One pass along axis ax over this block's share of the lines (all threads of the block):
 // out(line, j) = sum_k S[j][k] in(line, k); with scale (z axis): forward, times
@@ -729,7 +752,7 @@ __device__ void dst_pass(int ax, const VI* __restrict__ in, VO* __restrict__ out
   const int nlines = nrep * (n0 / n);
   const int l0 = (int)((long)blockIdx.x * nlines / gridDim.x);
   const int l1 = (int)((long)(blockIdx.x + 1) * nlines / gridDim.x);
-  const int W = l1 - l0, Wp = W + (W & 1);
+  const int W = l1 - l0, Wp = dst_wpad(W);
   if (W == 0) return;   // (uniform over the block)
   const int stride = ax == 0 ? 1 : (ax == 1 ? nx : plane);
   const int tot = W * n;
@@ -782,17 +805,19 @@ __device__ void dst_pass(int ax, const VI* __restrict__ in, VO* __restrict__ out
     walk(n, [&](int e, int w, int k) { put(tA + k * Wp + w, in + l0 * nx + e); });
   else           // element k of consecutive lines: consecutive x (k = q, w = r)
     walk(W, [&](int, int k, int w) { put(tA + k * Wp + w, in + lbase[w] + k * stride); });
-  if (W & 1)
-    for (int k = threadIdx.x; k < n; k += blockDim.x) tA[k * Wp + W] = 0.0f;
+  if (Wp > W)   // zero columns past the block's lines
+    walk_n(n * (Wp - W), Wp - W, [&](int, int k, int w) { tA[k * Wp + W + w] = 0.0f; });
   if constexpr (sizeof(VI) == 4) asm volatile("cp.async.wait_all;" ::: "memory");
   __syncthreads();
-  // src -> dst: fold src's rows k, n-1-k into P (row k) and M (row n-1-k), then each thread
-  // forms 4 outputs j of one parity (one float4 of Se or So row k) x 2 lines
+  // src -> dst: fold src's rows k, n-1-k into P (row k) and M (row n-1-k), then each warp
+  // forms 16 outputs of one parity x 8 lines per task with m16n8k8 TF32 MMAs:
+  // D[i][w] = sum_k A[i][k] B[k][w], A = Se or So (shared, TF32 already), B[k][w] = P_k or M_k
   const int hp = (n + 1) >> 1, h = n >> 1;
-  const int nge = (hp + 3) >> 2, ngo = (h + 3) >> 2;
   const float* Se = S;
-  const float* So = S + hp * dst_pad4(hp);
-  const int nwp = Wp >> 1;
+  const float* So = S + dst_arows(hp) * dst_astride(hp);
+  const int ase = dst_astride(hp), aso = dst_astride(h);
+  const int nmte = (hp + 15) >> 4, nmto = (h + 15) >> 4, nnt = Wp >> 3;
+  const int lane = threadIdx.x & 31, gq = lane >> 2, tq = lane & 3;
   auto transform = [&](float* src, float* dst) {
     walk_n(h * Wp, Wp, [&](int, int k, int w) {
       const float a = src[k * Wp + w], b = src[(n - 1 - k) * Wp + w];
@@ -800,35 +825,39 @@ __device__ void dst_pass(int ax, const VI* __restrict__ in, VO* __restrict__ out
       src[(n - 1 - k) * Wp + w] = a - b;
     });
     __syncthreads();
-    for (int t = threadIdx.x; t < (nge + ngo) * nwp; t += blockDim.x) {
-      const int g = t / nwp, wp = t - g * nwp;
-      const int odd = g >= nge;
-      const int jg = odd ? g - nge : g;
-      const float* Sm = odd ? So : Se;
-      const int ps = odd ? 4 * ngo : 4 * nge, kn = odd ? h : hp;
-      // row of P_k (k) or M_k (n-1-k)
-      const float* sp = src + (odd ? (n - 1) * Wp : 0) + 2 * wp;
-      const int sstep = odd ? -Wp : Wp;
-      float c0x = 0.f, c0y = 0.f, c1x = 0.f, c1y = 0.f, c2x = 0.f, c2y = 0.f, c3x = 0.f,
-            c3y = 0.f;
-#pragma unroll 4
-      for (int k = 0; k < kn; ++k) {
-        const float4 sv = *reinterpret_cast<const float4*>(Sm + k * ps + 4 * jg);
-        const float2 v = *reinterpret_cast<const float2*>(sp + k * sstep);
-        c0x = fmaf(sv.x, v.x, c0x);
-        c0y = fmaf(sv.x, v.y, c0y);
-        c1x = fmaf(sv.y, v.x, c1x);
-        c1y = fmaf(sv.y, v.y, c1y);
-        c2x = fmaf(sv.z, v.x, c2x);
-        c2y = fmaf(sv.z, v.y, c2y);
-        c3x = fmaf(sv.w, v.x, c3x);
-        c3y = fmaf(sv.w, v.y, c3y);
+    for (int task = threadIdx.x >> 5; task < (nmte + nmto) * nnt; task += blockDim.x >> 5) {
+      const int mt = task / nnt, nt = task - mt * nnt;
+      const int odd = mt >= nmte;
+      const int m0 = (odd ? mt - nmte : mt) * 16;
+      const float* A = odd ? So : Se;
+      const int as = odd ? aso : ase, kn = odd ? h : hp;
+      const float* Ar = A + (m0 + gq) * as + tq;
+      const int col = nt * 8 + gq;
+      float d0 = 0.f, d1 = 0.f, d2 = 0.f, d3 = 0.f;
+      for (int k0 = 0; k0 < kn; k0 += 8) {
+        const uint32_t a0 = __float_as_uint(Ar[k0]), a1 = __float_as_uint(Ar[8 * as + k0]);
+        const uint32_t a2 = __float_as_uint(Ar[k0 + 4]), a3 = __float_as_uint(Ar[8 * as + k0 + 4]);
+        // rows of P_k (k) or M_k (n-1-k); past kn the A columns are zero: clamp into the tile
+        int r0 = k0 + tq, r1 = k0 + tq + 4;
+        if (odd) {
+          r0 = n - 1 - r0;
+          r1 = n - 1 - r1;
+        }
+        r0 = min(max(r0, 0), n - 1);
+        r1 = min(max(r1, 0), n - 1);
+        uint32_t b0, b1;
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(b0) : "f"(src[r0 * Wp + col]));
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(b1) : "f"(src[r1 * Wp + col]));
+        asm volatile(
+            "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+            "{%8,%9}, {%0,%1,%2,%3};"
+            : "+f"(d0), "+f"(d1), "+f"(d2), "+f"(d3)
+            : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
       }
-      const int j = 8 * jg + odd;   // outputs j, j + 2, j + 4, j + 6
-      if (j < n) *reinterpret_cast<float2*>(dst + j * Wp + 2 * wp) = make_float2(c0x, c0y);
-      if (j + 2 < n) *reinterpret_cast<float2*>(dst + (j + 2) * Wp + 2 * wp) = make_float2(c1x, c1y);
-      if (j + 4 < n) *reinterpret_cast<float2*>(dst + (j + 4) * Wp + 2 * wp) = make_float2(c2x, c2y);
-      if (j + 6 < n) *reinterpret_cast<float2*>(dst + (j + 6) * Wp + 2 * wp) = make_float2(c3x, c3y);
+      // D rows m0 + gq (d0, d1) and m0 + gq + 8 (d2, d3), columns nt*8 + 2 tq, + 1
+      const int j0 = 2 * (m0 + gq) + odd, j1 = j0 + 16;
+      if (j0 < n) *reinterpret_cast<float2*>(dst + j0 * Wp + nt * 8 + 2 * tq) = make_float2(d0, d1);
+      if (j1 < n) *reinterpret_cast<float2*>(dst + j1 * Wp + nt * 8 + 2 * tq) = make_float2(d2, d3);
     }
     __syncthreads();
   };
@@ -1143,7 +1172,7 @@ __global__ void __launch_bounds__(kThreadsC, 1) k_hartree_coop(Args<V> a) {
       for (int ax = 0; ax < 3; ++ax) {
         const int na = ax == 0 ? nx : (ax == 1 ? ny : nz);
         const long nlines = (long)nrep * n0 / na;
-        const long wmax = (nlines + G - 1) / G + 1;
+        const long wmax = (nlines + G - 1) / G + 15;
         if ((long)na * wmax > tile) tile = (long)na * wmax;
       }
       const float* Sx = smem_tail;
@@ -1155,7 +1184,7 @@ __global__ void __launch_bounds__(kThreadsC, 1) k_hartree_coop(Args<V> a) {
       long wmx = 0;
       for (int ax = 0; ax < 3; ++ax) {
         const int na = ax == 0 ? nx : (ax == 1 ? ny : nz);
-        const long wm = ((long)nrep * n0 / na + G - 1) / G + 1;
+        const long wm = ((long)nrep * n0 / na + G - 1) / G + 15;
         if (wm > wmx) wmx = wm;
       }
       int* lbase = reinterpret_cast<int*>(tB + ((tile + 3) & ~3L));
@@ -1682,7 +1711,7 @@ static size_t dst_smem_bytes(const rmgtd_ctx* ctx, int nrep, int grid) {
     const size_t n = dims[ax];
     fl += (size_t)dst_mat_floats(dims[ax]);
     const size_t nlines = (size_t)nrep * ctx->Ng / n;
-    const size_t wmax = (nlines + grid - 1) / grid + 1;
+    const size_t wmax = (nlines + grid - 1) / grid + 15;   // >= dst_wpad(lines of a block)
     tile = std::max(tile, n * wmax);
     wmx = std::max(wmx, wmax);
   }
