@@ -203,34 +203,42 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # 152 SMs x 128 FP32 lanes x 
 
 def _mg_levels(n):
     """Level sizes of the Hartree multigrid (same coarsening rule as the library): halve while
-    every dimension is even and >= 4; the first level >= 1 with <= 4096 points starts the
-    single-block tail."""
+    every dimension is even and >= 4, stopping at a level below the finest with <= 64 points;
+    the first level >= 1 with <= 4096 points starts the single-block tail."""
     nx, ny, nz = n
     lv = []
     while True:
         lv.append(nx * ny * nz)
         if len(lv) >= 12 or nx % 2 or ny % 2 or nz % 2 or min(nx, ny, nz) < 4:
             break
+        if len(lv) >= 2 and lv[-1] <= 64:
+            break
         nx, ny, nz = nx // 2, ny // 2, nz // 2
     tail = next((l for l in range(1, len(lv)) if lv[l] <= 4096), None)
     return lv, tail
 
 
-def hartree_bytes(n, solves, iters, mixed):
+def hartree_bytes(n, solves, iters, mixed, precond="dst"):
     """Algorithmic bytes of the persistent Hartree solve: each array every phase reads or
-    writes, counted once (no stencil re-reads).  Per fine point and CG iteration: level 0 of
-    the V-cycle 45 + 2 s_V bytes (pre-sweeps 8 + s_V, residual with the box restriction
-    8.5, prolongation 8.5, post-sweeps 12 + 8 + s_V), each coarser multi-block level 49 bytes
-    per own point, the tail 8 bytes per tail point, A z with its dots 5 s_V and the vector
-    update 10 s_V (s_V = 4 float32 / 8 float64; the first iteration of a solve reads no p,
-    A p: -4 s_V).  Per solve: moments and right-hand side 2 s_rho + 4 s_ghost + 3 s_V."""
+    writes, counted once (no stencil re-reads).  Per fine point and CG iteration: A z with its
+    dots 5 s_V and the vector update 10 s_V (s_V = 4 float32 / 8 float64; the first iteration
+    of a solve reads no p, A p: -4 s_V), plus the preconditioner -- the sine-transform one
+    (the default on this workload) 32 + 2 s_V (five line passes, each reading and writing the
+    grid once: r in s_V, three float32 intermediates, z out in s_V); the multigrid V-cycle at
+    level 0 45 + 2 s_V (pre-sweeps 8 + s_V, residual with the box restriction 8.5,
+    prolongation 8.5, post-sweeps 12 + 8 + s_V), each coarser multi-block level 49 bytes per
+    own point, the tail 8 bytes per tail point.  Per solve: moments and right-hand side
+    2 s_rho + 4 s_ghost + 3 s_V."""
     sv = 4 if mixed else 8
     lv, tail = _mg_levels(n)
-    nmulti = tail if tail is not None else len(lv)
-    per_it = lv[0] * (45 + 2 * sv + 15 * sv)
-    per_it += sum(49 * lv[l] for l in range(1, nmulti))
-    if tail is not None:
-        per_it += 8 * lv[tail]
+    if precond == "dst":
+        per_it = lv[0] * (32 + 2 * sv + 15 * sv)
+    else:
+        nmulti = tail if tail is not None else len(lv)
+        per_it = lv[0] * (45 + 2 * sv + 15 * sv)
+        per_it += sum(49 * lv[l] for l in range(1, nmulti))
+        if tail is not None:
+            per_it += 8 * lv[tail]
     prologue = lv[0] * (2 * sv + 4 * sv + 3 * sv)
     return float(iters) * per_it + float(solves) * (prologue - 4 * sv * lv[0])
 
