@@ -423,7 +423,7 @@ def run_ours(args):
             "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
             "traffic": _traffic(kname, "ring64") if mixed else None,
             "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, mean of the "
-                              "first two launches of the host-driven region (5 CG iterations "
+                              "first two launches of the host-driven region (2 CG iterations "
                               "each; profiles/traffic_k_hartree_coop_ring64.txt)",
             "algorithmic_bytes_per_launch": h_bytes, "launch_ms": h_s * 1e3,
             "cg_iterations_per_solve": h_iters / max(h_solves, 1),
