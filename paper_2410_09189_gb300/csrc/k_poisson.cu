@@ -809,55 +809,61 @@ __device__ void dst_pass(int ax, const VI* __restrict__ in, VO* __restrict__ out
     walk_n(n * (Wp - W), Wp - W, [&](int, int k, int w) { tA[k * Wp + W + w] = 0.0f; });
   if constexpr (sizeof(VI) == 4) asm volatile("cp.async.wait_all;" ::: "memory");
   __syncthreads();
-  // src -> dst: fold src's rows k, n-1-k into P (row k) and M (row n-1-k), then each warp
-  // forms 16 outputs of one parity x 8 lines per task with m16n8k8 TF32 MMAs:
-  // D[i][w] = sum_k A[i][k] B[k][w], A = Se or So (shared, TF32 already), B[k][w] = P_k or M_k
+  // src -> dst with m16n8k8 TF32 MMAs: D[i][w] = sum_k A[i][k] B[k][w], A = Se or So
+  // (shared, TF32 already), B[k][w] = P_k = x_k + x_{n-1-k} (the middle point of an odd line
+  // alone) or M_k = x_k - x_{n-1-k}, formed while the B fragments are loaded.  Each warp takes
+  // one 8-line column tile and one parity and forms both of its 16-row output tiles (two
+  // independent accumulator chains sharing the B fragments).
   const int hp = (n + 1) >> 1, h = n >> 1;
   const float* Se = S;
   const float* So = S + dst_arows(hp) * dst_astride(hp);
   const int ase = dst_astride(hp), aso = dst_astride(h);
   const int nmte = (hp + 15) >> 4, nmto = (h + 15) >> 4, nnt = Wp >> 3;
   const int lane = threadIdx.x & 31, gq = lane >> 2, tq = lane & 3;
-  auto transform = [&](float* src, float* dst) {
-    walk_n(h * Wp, Wp, [&](int, int k, int w) {
-      const float a = src[k * Wp + w], b = src[(n - 1 - k) * Wp + w];
-      src[k * Wp + w] = a + b;
-      src[(n - 1 - k) * Wp + w] = a - b;
-    });
-    __syncthreads();
-    for (int task = threadIdx.x >> 5; task < (nmte + nmto) * nnt; task += blockDim.x >> 5) {
-      const int mt = task / nnt, nt = task - mt * nnt;
-      const int odd = mt >= nmte;
-      const int m0 = (odd ? mt - nmte : mt) * 16;
+  auto transform = [&](const float* src, float* dst) {
+    for (int task = threadIdx.x >> 5; task < 2 * nnt; task += blockDim.x >> 5) {
+      const int odd = task >= nnt;
+      const int nt = odd ? task - nnt : task;
       const float* A = odd ? So : Se;
-      const int as = odd ? aso : ase, kn = odd ? h : hp;
-      const float* Ar = A + (m0 + gq) * as + tq;
+      const int as = odd ? aso : ase, kn = odd ? h : hp, nmt = odd ? nmto : nmte;
       const int col = nt * 8 + gq;
-      float d0 = 0.f, d1 = 0.f, d2 = 0.f, d3 = 0.f;
+      for (int mp = 0; mp < nmt; mp += 2) {   // output tiles mp, mp + 1 (one pass for n <= 64)
+      float d[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
       for (int k0 = 0; k0 < kn; k0 += 8) {
-        const uint32_t a0 = __float_as_uint(Ar[k0]), a1 = __float_as_uint(Ar[8 * as + k0]);
-        const uint32_t a2 = __float_as_uint(Ar[k0 + 4]), a3 = __float_as_uint(Ar[8 * as + k0 + 4]);
-        // rows of P_k (k) or M_k (n-1-k); past kn the A columns are zero: clamp into the tile
-        int r0 = k0 + tq, r1 = k0 + tq + 4;
-        if (odd) {
-          r0 = n - 1 - r0;
-          r1 = n - 1 - r1;
+        uint32_t b[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          // past kn the A columns are zero: any row in the tile will do
+          const int k = k0 + tq + 4 * u;
+          const int ka = min(k, n - 1), kb = max(n - 1 - k, 0);
+          const float xa = src[ka * Wp + col], xb = src[kb * Wp + col];
+          const float v = (ka == kb) ? xa : (odd ? xa - xb : xa + xb);
+          asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(b[u]) : "f"(v));
         }
-        r0 = min(max(r0, 0), n - 1);
-        r1 = min(max(r1, 0), n - 1);
-        uint32_t b0, b1;
-        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(b0) : "f"(src[r0 * Wp + col]));
-        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(b1) : "f"(src[r1 * Wp + col]));
-        asm volatile(
-            "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-            "{%8,%9}, {%0,%1,%2,%3};"
-            : "+f"(d0), "+f"(d1), "+f"(d2), "+f"(d3)
-            : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+#pragma unroll
+        for (int mi = 0; mi < 2; ++mi) {
+          if (mp + mi < nmt) {
+            const float* Ar = A + (16 * (mp + mi) + gq) * as + tq + k0;
+            const uint32_t a0 = __float_as_uint(Ar[0]), a1 = __float_as_uint(Ar[8 * as]);
+            const uint32_t a2 = __float_as_uint(Ar[4]), a3 = __float_as_uint(Ar[8 * as + 4]);
+            asm volatile(
+                "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, "
+                "{%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+                : "+f"(d[mi][0]), "+f"(d[mi][1]), "+f"(d[mi][2]), "+f"(d[mi][3])
+                : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b[0]), "r"(b[1]));
+          }
+        }
       }
-      // D rows m0 + gq (d0, d1) and m0 + gq + 8 (d2, d3), columns nt*8 + 2 tq, + 1
-      const int j0 = 2 * (m0 + gq) + odd, j1 = j0 + 16;
-      if (j0 < n) *reinterpret_cast<float2*>(dst + j0 * Wp + nt * 8 + 2 * tq) = make_float2(d0, d1);
-      if (j1 < n) *reinterpret_cast<float2*>(dst + j1 * Wp + nt * 8 + 2 * tq) = make_float2(d2, d3);
+      // D rows 16 m + gq (d0, d1) and 16 m + gq + 8 (d2, d3), columns nt*8 + 2 tq, + 1
+#pragma unroll
+      for (int mi = 0; mi < 2; ++mi) {
+        const int j0 = 2 * (16 * (mp + mi) + gq) + odd, j1 = j0 + 16;
+        if (mp + mi < nmt && j0 < n)
+          *reinterpret_cast<float2*>(dst + j0 * Wp + nt * 8 + 2 * tq) = make_float2(d[mi][0], d[mi][1]);
+        if (mp + mi < nmt && j1 < n)
+          *reinterpret_cast<float2*>(dst + j1 * Wp + nt * 8 + 2 * tq) = make_float2(d[mi][2], d[mi][3]);
+      }
+      }
     }
     __syncthreads();
   };
