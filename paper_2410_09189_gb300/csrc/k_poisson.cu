@@ -6,20 +6,26 @@
 // The ghost term is linear in (Q, p): L_ghost(V_b) = Q G0 + px Gx + py Gy + pz Gz with four
 // grid fields G fixed by the grid, formed once at set-up.
 //
-// Solver: flexible (Polak-Ribiere) conjugate gradients, preconditioned by one
-// multigrid V-cycle in float32 (the paper's multigrid, Section 2.1): cell-centred coarsening
-// by 2, 7-point operators at spacing 2^l h, damped Jacobi smoothing (2 pre, 2 post),
-// trilinear prolongation and the box restriction (mean over the 8 children, formed in the
-// same pass as the residual; the V-cycle is then not symmetric, which flexible CG
-// tolerates); the levels with <= 4096 points run inside one block, whose coarsest level
-// is solved exactly.  The float64 path iterates
+// Solver: flexible (Polak-Ribiere) conjugate gradients.  Default preconditioner: the 3-D
+// sine transform (DST-I) that diagonalises the Toeplitz part of the 12th-order operator,
+// applied in float32 as five passes of 1-D transforms on the tensor cores (TF32 MMAs); the
+// operator with zero ghosts differs from that part only next to the faces, so CG needs a
+// few iterations (1.6-1.7 per solve on the 64^3 ring against 2.9 with the V-cycle).  Where
+// its tables do not fit in shared memory, or on request, one multigrid V-cycle in float32
+// (the paper's multigrid, Section 2.1): cell-centred coarsening by 2 down to <= 64 points,
+// 7-point operators at spacing 2^l h, damped Jacobi smoothing (2 pre, 2 post), trilinear
+// prolongation and the box restriction (mean over the 8 children, formed in the same pass
+// as the residual; the V-cycle is then not symmetric, which flexible CG tolerates); the
+// levels with <= 4096 points run inside single blocks, whose coarsest level is solved
+// exactly.  The float64 path iterates
 // on V itself; the mixed path iterates in float32 on the change of V relative to the
 // reference potential, with float32 right-hand side and dot products summed per warp in
 // float32 and across warps and blocks in float64 (float64 runs at a small fraction of the
 // float32 rate on this GPU, so no per-point float64 work remains in that solve).
 //
 // One cooperative launch runs the whole solve: prologue, every CG iteration and every
-// V-cycle phase, separated by grid barriers (12 per iteration at 64^3).  A p = A z +
+// preconditioner phase, separated by grid barriers (7 per iteration with the sine
+// transform, 11 with the V-cycle at 64^3).  A p = A z +
 // beta A p_old is carried as a vector, so the 37-point operator is applied once per
 // iteration to z, and (p, A p) follows from four dot products taken with A z.  Every block
 // sums the per-block partials of a reduction in the same order, so all blocks take the
