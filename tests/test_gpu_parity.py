@@ -139,6 +139,28 @@ def test_hartree_and_xc(torch_dev, precond):
         assert _rel(vh.cpu().numpy(), ref.ravel()) < 1e-10
 
 
+def test_hartree_long_lines(torch_dev):
+    """A 72-point axis: lines longer than 64 points take more than two 16-output tiles per
+    parity in the sine-transform passes (and larger shared-memory tables)."""
+    torch = torch_dev
+    rmgtd = _rmgtd()
+    s = _ring_small(n=(72, 36, 40), h=0.4)
+    raw = inputs.smooth_random_orbitals(s).reshape(s.N, s.Ng)
+    x, y, z = oham.full_coords(s)
+    rho = (np.exp(-((x - 2.1) ** 2 + (y + 0.4) ** 2 + z ** 2) / 2.0)
+           + 0.5 * np.exp(-((x + 4.0) ** 2 + (y - 1.0) ** 2 + (z - 0.7) ** 2) / 1.5))
+    ref = opoisson.hartree(s, rho, tol=1e-13)
+    with rmgtd.Context(s, raw, poisson_tol=1e-13) as ctx:
+        rd = torch.from_numpy(rho.ravel()).cuda()
+        vh = torch.zeros_like(rd)
+        n0, i0 = ctx.profile_counters()
+        ctx.hartree(rd, vh)
+        n1, i1 = ctx.profile_counters()
+        assert _rel(vh.cpu().numpy(), ref.ravel()) < 1e-10
+        # the transform preconditioner (not the multigrid fallback) ran: few iterations
+        assert n1 - n0 == 1 and i1 - i0 <= 14, (n1 - n0, i1 - i0)
+
+
 def test_xc_increment_matches_oracle(torch_dev):
     """The mixed path's float32 xc increment V_xc(rho0 + d) - V_xc(rho0) against the float64
     oracle LDA: densities from 1e-16 (below the floor) to 30, around r_s = 1 (rho = 3/(4 pi))
