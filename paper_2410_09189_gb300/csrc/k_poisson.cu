@@ -733,7 +733,8 @@ struct Args {
 // z, y, x), each over every line of the grid along its axis, split evenly over the blocks.
 // The matrices are stored folded: S[j][n-1-k] = (-1)^j S[j][k], so with the line's sums
 // P_k = x_k + x_{n-1-k} (k < n/2; P of the middle point of an odd line is that point) and
-// differences M_k = x_k - x_{n-1-k}, the even outputs are Se P and the odd ones So M, with
+// differences M_k = x_k - x_{n-1-k} (both formed while the MMA operands are loaded), the even
+// outputs are Se P and the odd ones So M, with
 // Se[i][k] = S[2i][k] (ceil(n/2) x ceil(n/2)) and So[i][k] = S[2i+1][k] (floor(n/2) squared):
 // half the multiply-adds and half the table of a plain product.  The products run on the
 // tensor cores as warp-level m16n8k8 TF32 MMAs (float32 accumulation; the tables are stored
@@ -745,7 +746,7 @@ struct Args {
 // One pass along axis ax over this block's share of the lines (all threads of the block):
 // out(line, j) = sum_k S[j][k] in(line, k); with scale (z axis): forward, times
 // norm / Lambda, inverse.  S: this axis's folded matrices Se, So in shared memory; tA, tB:
-// shared tiles of n x Wp floats (Wp = the block's line count rounded up to even); lbase,
+// shared tiles of n x Wp floats (Wp = dst_wpad(the block's line count)); lbase,
 // lxy: shared scratch of one int / float per line.  Flat indices are split into (row,
 // column) incrementally (no division per element); int offsets (nrep n0 < 2^31).
 template <typename VI, typename VO>
