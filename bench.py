@@ -63,10 +63,21 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                 "-i", str(self.device), "-lms", "200"],
+                 "-i", str(self.device), "-lms", "20"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        # the timed region is short (~0.4 ms per step): let sampling start first (first line
+        # written, at most 1.5 s), so the samples cover the region itself
+        t0 = time.time()
+        while time.time() - t0 < 1.5 and self.proc.poll() is None:
+            try:
+                if os.path.getsize(self.path) > 0:
+                    break
+            except OSError:
+                break
+            time.sleep(0.01)
 
     def stop(self):
         if self.proc is None:
