@@ -542,10 +542,17 @@ static int create_impl(const rmgtd_system* sys, const rmgtd_options* opt, rmgtd_
     // reference state of the mixed path: the float64 set-up state (all replicas start in it)
     const size_t fsz = sizeof(float) * Ng;
     ctx->phi32 = (float*)A(fsz * N);
-    // tiled copy, padded to whole 128-point tiles (the density kernel loads 16 KB per tile)
-    const size_t phit_bytes = sizeof(float) * 32 * ((N + 31) / 32) * 128 * ((Ng + 127) / 128);
-    ctx->phi32t = (float*)A(phit_bytes);
-    if (ctx->phi32t) RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->phi32t, 0, phit_bytes, ctx->stream));
+    // bfloat16 planes for the orbital-tiled tensor-core contractions (32 < N <= 256)
+    rc = planes_setup(ctx);
+    if (rc) return rc;
+    // else the 32-point tiled copy, padded to whole 128-point tiles (the N <= 32 density kernel
+    // loads 16 KB per tile; the tiled Gram kernel reads 32 x 32 boxes)
+    if (!ctx->phi_pl) {
+      const size_t phit_bytes = sizeof(float) * 32 * ((N + 31) / 32) * 128 * ((Ng + 127) / 128);
+      ctx->phi32t = (float*)A(phit_bytes);
+      if (!ctx->phi32t) return set_error(ctx, RMGTD_ENOMEM, "tiled orbitals");
+      RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->phi32t, 0, phit_bytes, ctx->stream));
+    }
     ctx->Sref = (double*)A(msz);
     ctx->Href = (double*)A(msz);
     ctx->rho_ref = (double*)A(gsz);
@@ -571,13 +578,15 @@ static int create_impl(const rmgtd_system* sys, const rmgtd_options* opt, rmgtd_
     ctx->rho_mom_cap = 4L * nrep * std::max(1, ctx->num_sms);
     ctx->rho_mom = (double*)A(sizeof(double) * ctx->rho_mom_cap);
     ctx->ghost32 = (float*)A(fsz * 4);
-    if (!ctx->phi32 || !ctx->phi32t || !ctx->pcg32_Az || !ctx->dvh32 || !ctx->Href || !ctx->vh_ref ||
+    if (!ctx->phi32 || !ctx->pcg32_Az || !ctx->dvh32 || !ctx->Href || !ctx->vh_ref ||
         !ctx->drho32 || !ctx->ghost32 || !ctx->rho_ref32)
       return set_error(ctx, RMGTD_ENOMEM, "mixed-precision buffers");
     rc = to_float(ctx, ctx->phi, ctx->phi32, (long)N * Ng);
     if (rc) return rc;
-    rc = tile_orbitals(ctx);
-    if (rc) return rc;
+    if (ctx->phi32t) {
+      rc = tile_orbitals(ctx);
+      if (rc) return rc;
+    }
     rc = to_float(ctx, ctx->ghost, ctx->ghost32, 4L * Ng);
     if (rc) return rc;
     RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->Sref, ctx->S0, msz, cudaMemcpyDeviceToDevice, ctx->stream));

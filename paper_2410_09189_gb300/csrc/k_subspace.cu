@@ -335,6 +335,10 @@ k_rho32(int N, int Np, long Ng, const float* __restrict__ phi, const float* __re
 int rho_dev_mixed(rmgtd_ctx* ctx, const double* S, double* rho, const RepCtl* ctl, int nrep) {
   const int N = ctx->N, Np = ((N + 31) / 32) * 32;
   const long NpNp = (long)Np * Np;
+  if (ctx->phi_pl) {   // orbital planes on the tensor cores (32 < N <= 256)
+    ctx->shat_fresh = 0;
+    return rho_planes(ctx, S, rho, ctx->drho32, ctl, nrep);
+  }
   if (!ctx->shat_fresh || S != ctx->S1) {
     k_shat32<<<dim3(std::max(1, (int)std::min<long>(ceil_div(NpNp, 256), 1024)), nrep), 256, 0,
                ctx->stream>>>(N, Np, S, ctx->Sref, (long)N * N, ctx->shat32, ctl);
@@ -577,7 +581,20 @@ int gram_mixed(rmgtd_ctx* ctx, const float* w, long wstride, int nw, double scal
   int chunk = (int)(ceil_div(ceil_div(ctx->Ng, (long)nsplit), (long)kG32Slab) * kG32Slab);
   nsplit = (int)ceil_div(ctx->Ng, (long)chunk);   // no empty splits
   float* part = reinterpret_cast<float*>(ctx->gram_part);
-  const int rc = tc ? gram_tc(ctx, w, nw, part, nsplit, chunk, ctl) : 1;
+  int rc = 1;
+  if (tc && ctx->phi_pl) {
+    // orbital planes: one CTA per SM over (split, replica), chunks of whole 64-point stages
+    int ps = std::max(1, ctx->num_sms / nw);
+    ps = (int)std::min<long>(ps, (long)(2 * ctx->gram_part_elems) / std::max<long>(per, 1));
+    const int pchunk = (int)(ceil_div(ceil_div(ctx->Ng, (long)ps), 64L) * 64);
+    const int pns = (int)ceil_div(ctx->Ng, (long)pchunk);
+    rc = gram_planes(ctx, w, nw, part, pns, pchunk, ctl);
+    if (rc == 0) {
+      nsplit = pns;
+      chunk = pchunk;
+    }
+  }
+  if (rc > 0 && tc) rc = gram_tc(ctx, w, nw, part, nsplit, chunk, ctl);
   if (rc < 0) return rc;
   if (rc > 0) {
     k_gram32<<<dim3(nsplit, npairs, ngroups), kG32Threads, 0, ctx->stream>>>(

@@ -95,6 +95,17 @@ struct rmgtd_ctx {
   // beyond N and Ng (allocated up to whole 128-point tiles), so that a 32-orbital x 32-point
   // block is 4 contiguous KB and a 128-point tile 16 (tensor cores)
   float* phi32t = nullptr;
+  // the same orbitals as two bfloat16 planes (hi, lo) [2][Np_pl][Ngp_pl] (Np_pl = N rounded up
+  // to 32, Ngp_pl = Ng rounded up to 64, zero beyond) for the orbital-tiled tensor-core
+  // contractions (32 < N <= 256); NULL when those are not used
+  __nv_bfloat16* phi_pl = nullptr;
+  __nv_bfloat16* bt_pl = nullptr;  // [nrep][2][Np_pl][Np_pl] density-change matrix (transposed)
+  int Np_pl = 0;
+  long Ngp_pl = 0;
+  alignas(64) unsigned char tm_pa[128] = {};   // planes, 64 x 64 boxes (density operand A)
+  alignas(64) unsigned char tm_pb[128] = {};   // planes, 64 x Np_pl boxes (Gram operand B)
+  alignas(64) unsigned char tm_bt[128] = {};   // density-change planes, 64 x 32 boxes
+  int rho_pl_attr = 0, gram_pl_attr = 0;       // dynamic shared memory set for the kernels
   double* vion = nullptr;      // [Ng] V_loc + V_ext
   double* f_dev = nullptr;     // [N]
 
@@ -407,6 +418,13 @@ int hartree_reset_history(rmgtd_ctx* ctx);
 int rho_tc(rmgtd_ctx* ctx, double* rho, float* drho, const RepCtl* ctl, int nrep);
 int gram_tc(rmgtd_ctx* ctx, const float* w, int nw, float* part, int nsplit, int chunk,
             const RepCtl* ctl);
+// k_contract.cu (orbital planes, 32 < N <= 256): set-up, and the two contractions; the latter
+// return 1 when the planes are not set up (the caller then uses the other kernels)
+int planes_setup(rmgtd_ctx* ctx);
+int rho_planes(rmgtd_ctx* ctx, const double* S, double* rho, float* drho, const RepCtl* ctl,
+               int nrep);
+int gram_planes(rmgtd_ctx* ctx, const float* w, int nw, float* part, int nsplit, int chunk,
+                const RepCtl* ctl);
 int conv16_tc(int nx, int ny, int nz, int B, const float* x, const __nv_bfloat16* W,
               const float* bias, float* y, int silu, int* status, int num_sms, cudaStream_t s);
 // k_surrogate.cu
