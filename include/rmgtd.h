@@ -121,6 +121,8 @@ typedef struct {
                               0: P_0 = diag(f) (the orbitals are taken as the ground state) */
   double subspace_mix;     /* linear mixing of P in those iterations (default 0.3) */
   double subspace_tol;     /* stop when max|P_new - P| <= subspace_tol (default 1e-10) */
+  double mixed_poisson_tol;  /* mixed path: relative residual of the float32 Hartree correction
+                                solve (0 = default 3e-6; values below 1e-8 are raised to 1e-8) */
 } rmgtd_options;
 
 /* Per-step, per-replica statistics written by rmgtd_step. */
@@ -193,8 +195,10 @@ int rmgtd_get_matrix(rmgtd_ctx* ctx, int which, int rep, double* host_out);
 int rmgtd_set_matrix(rmgtd_ctx* ctx, int which, int rep, const double* host_in);
 
 /* Hartree potential of a device density (Ng doubles) with the context's grid: solves
- * Lap_12 V = -4 pi rho with monopole + dipole ghost values by multigrid-preconditioned
- * CG to poisson_tol.  vh_dev is used as the initial guess.  Errors: RMGTD_ENOTCONVERGED. */
+ * Lap_12 V = -4 pi rho with monopole + dipole ghost values by conjugate gradients to
+ * poisson_tol, preconditioned as chosen by rmgtd_set_hartree_preconditioner (default: the
+ * sine transform; the multigrid V-cycle where its tables do not fit).  vh_dev is used as
+ * the initial guess.  Errors: RMGTD_ENOTCONVERGED. */
 int rmgtd_hartree(rmgtd_ctx* ctx, const double* rho_dev, double* vh_dev);
 
 /* LDA (Slater + PZ81) on n device points: vxc_dev, exc_dev receive V_xc and eps_xc. */
@@ -270,6 +274,9 @@ int rmgtd_get_tuning(const rmgtd_ctx* ctx, int choice[4]);
 #define RMGTD_PRECOND_DST 0
 #define RMGTD_PRECOND_MG 1
 int rmgtd_set_hartree_preconditioner(rmgtd_ctx* ctx, int kind);
+/* The preconditioner the context's Hartree solves use now (*kind: RMGTD_PRECOND_DST when it
+ * was chosen and its tables fit, else RMGTD_PRECOND_MG).  Errors: RMGTD_EINVAL (NULL). */
+int rmgtd_get_hartree_preconditioner(rmgtd_ctx* ctx, int* kind);
 
 /* Several contexts (different systems, each with its replicas) stepped by one CUDA graph per
  * time step: their steps are captured back to back into a single graph, launched once per
@@ -355,12 +362,24 @@ int rmgtd_get_field(rmgtd_ctx* ctx, int which, int rep, double* dev_out);
  * 8 MiB array of float64 inside the library (held on every GPU that loads the library until
  * the process exits), so n_orb must satisfy n_orb^2 <= 1048576 (n_orb <= 1024); larger sizes
  * return RMGTD_EINVAL.  The first call on a device looks up the array's address on that
- * device (make that first call before any stream capture).  All calls share the array:
+ * device (make that first call before any stream capture); the address is looked up again
+ * when the device's current CUDA context has changed since (after cudaDeviceReset or a
+ * rebuilt primary context), so such a call, too, should come before any capture.  All calls
+ * share the array:
  * calls whose work overlaps on the device race; serialise them on one stream.  Work is
  * enqueued on `stream` (cudaStream_t, NULL = default stream) and the call does not wait.
  * Errors (message through rmgtd_last_error(NULL)): RMGTD_EINVAL, RMGTD_ECUDA. */
 int rmgtd_gram_noalloc(const double* a_dev, const double* b_dev, const double* w_dev,
                        int n_orb, long long n_grid, double scale, double* c_dev, void* stream);
+
+/* Failure-detection diagnostic (no counterpart in the paper): launches one block per SM
+ * that wait at a grid barrier on a counter of their own which block 0 never reaches, with
+ * the wait limited to `polls` polls (1 .. 20000000) instead of the library's default limit,
+ * and returns the status the waiting blocks recorded -- RMGTD_ETIMEOUT when the bounded wait
+ * gave up, as every device-side wait of the library does -- in *status_out.  The context's
+ * propagation state, its status word and its barrier counters are not touched.
+ * Synchronises the stream.  Errors: RMGTD_EINVAL (polls out of range, NULL), RMGTD_ECUDA. */
+int rmgtd_selftest_barrier_timeout(rmgtd_ctx* ctx, unsigned polls, int* status_out);
 
 /* Message of the last error on `ctx` (thread-local message when ctx is NULL). */
 const char* rmgtd_last_error(const rmgtd_ctx* ctx);

@@ -229,7 +229,10 @@ int dft_eval(rmgtd_ctx* ctx, const double* S, const RepCtl* ctl, unsigned long l
   if (errbits)
     RMGTD_CUDA(ctx, cudaMemsetAsync(errbits, 0, sizeof(unsigned long long) * nrep, ctx->stream));
   ph_begin(ctx, PH_HUPDATE);
-  if (mixed)
+  if (mixed && ctx->Ha)   // orbital planes: H = Ha + h^3 Phi^T diag(dV - dVa) Phi per replica
+    rc = gram_mixed(ctx, ctx->dv32, ctx->Ng, nrep, ctx->h3, ctx->Ha, ctx->H1, ctl, errbits,
+                    (long)ctx->N * ctx->N, ctx->dv_a32);
+  else if (mixed)
     rc = gram_mixed(ctx, ctx->dv32, ctx->Ng, nrep, ctx->h3, ctx->Href, ctx->H1, ctl, errbits);
   else
     rc = gram(ctx, ctx->phi, ctx->phi, ctx->vhxc, ctx->Ng, nrep, ctx->h3, ctx->Hcore, ctx->H1,
@@ -287,6 +290,13 @@ static int check_status(rmgtd_ctx* ctx, const char* where) {
     return set_error(ctx, st, buf);
   }
   return RMGTD_OK;
+}
+
+// Diagnostic of the bounded waits: every block but block 0 waits at one grid barrier that
+// block 0 never reaches, giving up after `limit` polls (status[0] <- RMGTD_ETIMEOUT).
+__global__ void k_barrier_timeout_probe(unsigned* count, int* status, unsigned limit) {
+  if (blockIdx.x == 0) return;
+  grid_barrier(count, gridDim.x, status, limit);
 }
 
 }  // namespace rmgtd
@@ -598,6 +608,8 @@ static int create_impl(const rmgtd_system* sys, const rmgtd_options* opt, rmgtd_
     RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->vref, ctx->vhxc, gsz, cudaMemcpyDeviceToDevice, ctx->stream));
     RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->dvh32, 0, fsz * nrep, ctx->stream));
     RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->dv32, 0, fsz * nrep, ctx->stream));
+    rc = planes_anchor_reset(ctx);
+    if (rc) return rc;
     ctx->mixed = 1;
   }
   rc = hartree_reset_history(ctx);
@@ -778,6 +790,20 @@ static int eager_step(rmgtd_ctx* ctx) {
 
 // After a chunk of `chunk` launched steps: copy the per-step statistics out (to
 // stats[done_total ..] when given), advance time and step count, report a failed step.
+// After a failed step the kept state (P_0, H_0, H_-1 of the last completed step) is intact,
+// but the grid fields and the Hartree guess history hold the failed step's values (non-finite
+// after a divergence): rebuild them from P_0, the Hartree solve starting from zero.  The
+// failed step's error message is kept.
+static void recover_after_failed_step(rmgtd_ctx* ctx) {
+  const std::string msg = ctx->err;
+  if (cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream) == cudaSuccess &&
+      cudaMemsetAsync(ctx->vh, 0, sizeof(double) * ctx->Ng * ctx->nrep, ctx->stream) ==
+          cudaSuccess &&
+      refresh_fields(ctx) == RMGTD_OK)
+    cudaStreamSynchronize(ctx->stream);
+  ctx->err = msg;
+}
+
 static int finish_chunk(rmgtd_ctx* ctx, int chunk, int done_total, rmgtd_stats* stats, int* done_out) {
   const int nrep = ctx->nrep;
   int* hdr = (int*)&ctx->ctl_host[nrep];  // scratch: done, failed, status
@@ -812,7 +838,9 @@ static int finish_chunk(rmgtd_ctx* ctx, int chunk, int done_total, rmgtd_stats* 
     char buf[128];
     snprintf(buf, sizeof(buf), "step %lld failed with status %d", ctx->steps + 1, worst);
     ph_flush(ctx);
-    return set_error(ctx, worst, buf);
+    const int rc = set_error(ctx, worst, buf);
+    recover_after_failed_step(ctx);
+    return rc;
   }
   return RMGTD_OK;
 }
@@ -1345,6 +1373,36 @@ int rmgtd_xc_increment(rmgtd_ctx* ctx, const double* rho0_dev, const float* drho
   return RMGTD_OK;
 }
 
+int rmgtd_get_hartree_preconditioner(rmgtd_ctx* ctx, int* kind) {
+  if (!ctx || !kind) return set_error(ctx, RMGTD_EINVAL, "get_hartree_preconditioner: NULL");
+  *kind = hartree_precond_in_use(ctx);
+  return RMGTD_OK;
+}
+
+int rmgtd_selftest_barrier_timeout(rmgtd_ctx* ctx, unsigned polls, int* status_out) {
+  if (!ctx || !status_out) return set_error(ctx, RMGTD_EINVAL, "selftest: NULL argument");
+  if (polls < 1 || polls > kSpinLimit)
+    return set_error(ctx, RMGTD_EINVAL, "selftest: polls must be in 1 .. 20000000");
+  unsigned* buf = (unsigned*)dev_alloc(ctx, 2 * sizeof(unsigned));
+  if (!buf) return set_error(ctx, RMGTD_ENOMEM, "selftest buffer");
+  int rc = RMGTD_OK;
+  int st = 0;
+  cudaError_t e = cudaMemsetAsync(buf, 0, 2 * sizeof(unsigned), ctx->stream);
+  if (e == cudaSuccess) {
+    k_barrier_timeout_probe<<<std::max(2, ctx->num_sms), 32, 0, ctx->stream>>>(
+        buf, reinterpret_cast<int*>(buf + 1), polls);
+    ++ctx->launches;
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&st, buf + 1, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) rc = cuda_check(ctx, e, "selftest barrier time-out");
+  dev_free(ctx, buf);
+  if (rc == RMGTD_OK) *status_out = st;
+  return rc;
+}
+
 int rmgtd_time(rmgtd_ctx* ctx, double* t, long long* steps) {
   if (!ctx) return set_error(nullptr, RMGTD_EINVAL, "ctx is NULL");
   if (t) *t = ctx->t;
@@ -1391,6 +1449,18 @@ int rmgtd_save(rmgtd_ctx* ctx, const char* path) {
                                cudaMemcpyDeviceToHost));
     ok = fwrite(d32.data(), sizeof(float), 3 * gcount, fp) == 3 * gcount;
   }
+  if (ok && ctx->mixed && ctx->Sa) {   // anchors of the orbital-plane contractions
+    std::vector<double> m(2 * mcount);
+    std::vector<float> f(2 * gcount);
+    RMGTD_CUDA(ctx, cudaMemcpy(m.data(), ctx->Sa, sizeof(double) * mcount, cudaMemcpyDeviceToHost));
+    RMGTD_CUDA(ctx, cudaMemcpy(m.data() + mcount, ctx->Ha, sizeof(double) * mcount,
+                               cudaMemcpyDeviceToHost));
+    RMGTD_CUDA(ctx, cudaMemcpy(f.data(), ctx->rho_a32, sizeof(float) * gcount, cudaMemcpyDeviceToHost));
+    RMGTD_CUDA(ctx, cudaMemcpy(f.data() + gcount, ctx->dv_a32, sizeof(float) * gcount,
+                               cudaMemcpyDeviceToHost));
+    ok = fwrite(m.data(), sizeof(double), 2 * mcount, fp) == 2 * mcount &&
+         fwrite(f.data(), sizeof(float), 2 * gcount, fp) == 2 * gcount;
+  }
   fclose(fp);
   if (!ok) return set_error(ctx, RMGTD_EINVAL, "save: write failed");
   return RMGTD_OK;
@@ -1422,6 +1492,14 @@ int rmgtd_load(rmgtd_ctx* ctx, const char* path) {
     d32.resize(3 * gcount);
     ok = fread(d32.data(), sizeof(float), 3 * gcount, fp) == 3 * gcount;
   }
+  std::vector<double> am;
+  std::vector<float> af;
+  if (ok && ctx->mixed && ctx->Sa) {
+    am.resize(2 * mcount);
+    af.resize(2 * gcount);
+    ok = fread(am.data(), sizeof(double), 2 * mcount, fp) == 2 * mcount &&
+         fread(af.data(), sizeof(float), 2 * gcount, fp) == 2 * gcount;
+  }
   fclose(fp);
   if (!ok) return set_error(ctx, RMGTD_EINVAL, "load: truncated checkpoint");
   RMGTD_CUDA(ctx, cudaMemcpy(ctx->vh_prev, vp.data(), sizeof(double) * gcount, cudaMemcpyHostToDevice));
@@ -1432,6 +1510,14 @@ int rmgtd_load(rmgtd_ctx* ctx, const char* path) {
     RMGTD_CUDA(ctx, cudaMemcpy(ctx->dvh_prev32, d32.data() + gcount, sizeof(float) * gcount,
                                cudaMemcpyHostToDevice));
     RMGTD_CUDA(ctx, cudaMemcpy(ctx->dvh_prev2_32, d32.data() + 2 * gcount, sizeof(float) * gcount,
+                               cudaMemcpyHostToDevice));
+  }
+  if (!am.empty()) {
+    RMGTD_CUDA(ctx, cudaMemcpy(ctx->Sa, am.data(), sizeof(double) * mcount, cudaMemcpyHostToDevice));
+    RMGTD_CUDA(ctx, cudaMemcpy(ctx->Ha, am.data() + mcount, sizeof(double) * mcount,
+                               cudaMemcpyHostToDevice));
+    RMGTD_CUDA(ctx, cudaMemcpy(ctx->rho_a32, af.data(), sizeof(float) * gcount, cudaMemcpyHostToDevice));
+    RMGTD_CUDA(ctx, cudaMemcpy(ctx->dv_a32, af.data() + gcount, sizeof(float) * gcount,
                                cudaMemcpyHostToDevice));
   }
   double* parts[4] = {ctx->S0, ctx->A0, ctx->H0, ctx->Hm1};

@@ -10,10 +10,17 @@
 // per product, with the same four bytes per orbital value as a float32 copy.  All operand
 // tiles arrive by TMA with the 128-byte swizzle; no per-replica padding.
 //
+// Anchors: both contractions work on the change since the replica's anchor, a consistent
+// pair of states moved to the new state after every completed step (rho(Sa) with Sa, and
+// Ha = H(Va) with Va): drho = drho_a + sum (S - Sa)_ij phi_i phi_j and
+// H = Ha + h^3 Phi^T diag(V - Va) Phi.  The split's rounding then scales with one step's
+// change, so the SCF loop converges as on the float64 path; the float64 reference state of
+// the set-up (rho_ref, V_ref) stays the origin of drho and dV.
+//
 // Density change (k_rho_planes), per replica r and 128-point tile:
 //   D[g][j] = sum_{k <= j} phi_k(g) Shat_r[k][j]    (M = 128 points, N = Np - 64 c, K = orbitals)
 //   drho_r(g) = sum_j phi_j(g) D[g][j]
-// Shat_r is upper triangular (2 dS_kj for k < j, dS_jj on the diagonal, dS = Re P - P_ref), so
+// Shat_r is upper triangular (2 dS_kj for k < j, dS_jj on the diagonal, dS = Re P - Sa_r), so
 // the K loop runs over 64-orbital chunks c and chunk c only adds to columns j >= 64 c: after
 // chunk c's MMAs, columns [64 c, 64 c + 64) are final, and the epilogue forms their part of
 // drho from the same shared-memory chunk (the orbitals are read from HBM once) while the
@@ -74,13 +81,15 @@ __global__ void k_split_planes(int N, int Np, long Ng, long Ngp, const double* _
 }
 
 // Bt_r[plane][j][k] = Shat_r[k][j] split into bfloat16 hi / lo: 2 dS_kj (k < j), dS_jj (k = j),
-// 0 otherwise or past N; dS = S_r - S_ref (float64 in, rounded once per plane)
+// 0 otherwise or past N; dS = S_r - Sa_r (the replica's anchor; float64 in, rounded once per
+// plane)
 __global__ void k_shat_planes(int N, int Np, const double* __restrict__ S,
-                              const double* __restrict__ Sref, long sstride,
+                              const double* __restrict__ Sa, long sstride,
                               __nv_bfloat16* __restrict__ bt, const RepCtl* __restrict__ ctl) {
   const int rep = blockIdx.y;
   if (ctl && !ctl[rep].active) return;
   const double* Sr = S + rep * sstride;
+  const double* Sref = Sa + rep * sstride;
   const long NpNp = (long)Np * Np;
   __nv_bfloat16* hi = bt + 2 * rep * NpNp;
   __nv_bfloat16* lo = hi + NpNp;
@@ -110,7 +119,8 @@ __global__ void k_shat_planes(int N, int Np, const double* __restrict__ S,
 __global__ void __launch_bounds__(kRdThreads, 1)
 k_rho_planes(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__ CUtensorMap tm_bt,
              int N, int Np, int Ng, int nrep, int slots, const double* __restrict__ rho_ref,
-             double* __restrict__ rho, float* __restrict__ drho, const RepCtl* __restrict__ ctl,
+             const float* __restrict__ drho_a, double* __restrict__ rho,
+             float* __restrict__ drho, const RepCtl* __restrict__ ctl,
              int* status, double* __restrict__ mom, int nx, int ny, int nz, float hgrid) {
   extern __shared__ unsigned char smraw[];
   __shared__ __align__(8) uint64_t bfull, full[kRdMaxSlots], empty[kRdMaxSlots];
@@ -282,6 +292,7 @@ k_rho_planes(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__ C
       if (lane == 0) mbar_arrive(&tfree[b]);
       const int g = (cta + i * ncta) * kPM + p;
       if (g < Ng) {
+        acc += drho_a[(long)rep * Ng + g];   // rho(Sa) - rho_ref
         drho[(long)rep * Ng + g] = acc;
         if (rho) rho[(long)rep * Ng + g] = rho_ref[g] + (double)acc;
         if (mom) {
@@ -344,7 +355,8 @@ k_rho_planes(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__ C
 // mbarriers: full[s] (copy landed), conv[s] (A operands of slot s written, 8 warp arrivals),
 // empty[s] (the MMAs of slot s completed), accf (all MMAs completed).
 __global__ void __launch_bounds__(kGpThreads, 1)
-k_gram_planes(const __grid_constant__ CUtensorMap tm_b, const float* __restrict__ w, int N,
+k_gram_planes(const __grid_constant__ CUtensorMap tm_b, const float* __restrict__ w,
+              const float* __restrict__ w_anchor, int N,
               int Np, int Ng, int nrep, int chunk, int stages, float* __restrict__ part,
               const RepCtl* __restrict__ ctl, int* status) {
   extern __shared__ unsigned char smraw[];
@@ -452,6 +464,7 @@ k_gram_planes(const __grid_constant__ CUtensorMap tm_b, const float* __restrict_
     const int ct = tid - 64;                 // 0 .. 255
     const int c = ct & 7;                    // logical 16-byte chunk: points 8 c .. 8 c + 7
     const float* wr = w + (long)rep * Ng;
+    const float* war = w_anchor ? w_anchor + (long)rep * Ng : nullptr;
     for (int t = 0; t < nst; ++t) {
       const int s = t % stages;
       if (!mbar_wait(&full[s], (uint32_t)(t / stages) & 1u) || *abort_v) {
@@ -461,7 +474,8 @@ k_gram_planes(const __grid_constant__ CUtensorMap tm_b, const float* __restrict_
       const int g0 = g_beg + kPK * t + 8 * c;
       float wv[8];
 #pragma unroll
-      for (int e = 0; e < 8; ++e) wv[e] = (g0 + e < g_end) ? __ldg(wr + g0 + e) : 0.0f;
+      for (int e = 0; e < 8; ++e)
+        wv[e] = (g0 + e < g_end) ? __ldg(wr + g0 + e) - (war ? __ldg(war + g0 + e) : 0.0f) : 0.0f;
       unsigned char* sb = gbase + (size_t)s * slotB;
       for (int I = 0; I < TI; ++I) {
         const int rows = min(kPM, Np - kPM * I);
@@ -602,8 +616,72 @@ int planes_setup(rmgtd_ctx* ctx) {
     ctx->bt_pl = nullptr;
     return RMGTD_OK;
   }
+  const size_t msz = sizeof(double) * (size_t)N * N * ctx->nrep;
+  const size_t fsz = sizeof(float) * (size_t)ctx->Ng * ctx->nrep;
+  ctx->Sa = (double*)dev_alloc(ctx, msz);
+  ctx->Ha = (double*)dev_alloc(ctx, msz);
+  ctx->rho_a32 = (float*)dev_alloc(ctx, fsz);
+  ctx->dv_a32 = (float*)dev_alloc(ctx, fsz);
+  if (!ctx->Sa || !ctx->Ha || !ctx->rho_a32 || !ctx->dv_a32)
+    return set_error(ctx, RMGTD_ENOMEM, "orbital-plane anchors");
   ctx->Np_pl = Np;
   ctx->Ngp_pl = Ngp;
+  return RMGTD_OK;
+}
+
+int planes_anchor_reset(rmgtd_ctx* ctx) {
+  if (!ctx->phi_pl) return RMGTD_OK;
+  const size_t NN = (size_t)ctx->N * ctx->N;
+  for (int r = 0; r < ctx->nrep; ++r) {
+    RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->Sa + r * NN, ctx->Sref, sizeof(double) * NN,
+                                    cudaMemcpyDeviceToDevice, ctx->stream));
+    RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->Ha + r * NN, ctx->Href, sizeof(double) * NN,
+                                    cudaMemcpyDeviceToDevice, ctx->stream));
+  }
+  const size_t fsz = sizeof(float) * (size_t)ctx->Ng * ctx->nrep;
+  RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->rho_a32, 0, fsz, ctx->stream));
+  RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->dv_a32, 0, fsz, ctx->stream));
+  return RMGTD_OK;
+}
+
+namespace tc {
+
+// After a step: when it completed for every replica (k_step_end's condition: no earlier
+// failure in this call, device status clear, every replica's status clear) the anchors move
+// to the new state: Sa <- S0 (= the final P_1), Ha <- H0 (= H of the final pass),
+// rho_a <- drho and Va <- dV of that pass.
+__global__ void k_anchor_update(long nm, long ng, const double* __restrict__ S0,
+                                const double* __restrict__ H0, const float* __restrict__ drho,
+                                const float* __restrict__ dv, double* __restrict__ Sa,
+                                double* __restrict__ Ha, float* __restrict__ rho_a,
+                                float* __restrict__ dv_a, const RepCtl* __restrict__ ctl,
+                                int nrep, const int* failed, const int* status) {
+  if (*failed || *status != 0) return;
+  for (int r = 0; r < nrep; ++r)
+    if (ctl[r].status != 0) return;
+  const long stride = (long)gridDim.x * blockDim.x;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < nm; e += stride) {
+    Sa[e] = S0[e];
+    Ha[e] = H0[e];
+  }
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < ng; e += stride) {
+    rho_a[e] = drho[e];
+    dv_a[e] = dv[e];
+  }
+}
+
+}  // namespace tc
+
+int planes_anchor_update(rmgtd_ctx* ctx) {
+  if (!ctx->phi_pl || !ctx->mixed) return RMGTD_OK;
+  const long nm = (long)ctx->nrep * ctx->N * ctx->N, ng = (long)ctx->nrep * ctx->Ng;
+  const int blocks = (int)std::max<long>(1, std::min<long>(ceil_div(ng, 256), 4L * ctx->num_sms));
+  tc::k_anchor_update<<<blocks, 256, 0, ctx->stream>>>(nm, ng, ctx->S0, ctx->H0, ctx->drho32,
+                                                       ctx->dv32, ctx->Sa, ctx->Ha, ctx->rho_a32,
+                                                       ctx->dv_a32, ctx->ctl, ctx->nrep,
+                                                       ctx->failed, ctx->status);
+  ++ctx->launches;
+  RMGTD_LAUNCH(ctx, "k_anchor_update");
   return RMGTD_OK;
 }
 
@@ -616,7 +694,7 @@ int rho_planes(rmgtd_ctx* ctx, const double* S, double* rho, float* drho, const 
   const int N = ctx->N, Np = ctx->Np_pl;
   const long NpNp = (long)Np * Np;
   k_shat_planes<<<dim3(std::max(1, (int)std::min<long>(ceil_div(NpNp, 256), 256)), nrep), 256, 0,
-                  ctx->stream>>>(N, Np, S, ctx->Sref, (long)N * N, ctx->bt_pl, ctl);
+                  ctx->stream>>>(N, Np, S, ctx->Sa, (long)N * N, ctx->bt_pl, ctl);
   ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_shat_planes");
   int slots = kRdMaxSlots;
@@ -635,7 +713,8 @@ int rho_planes(rmgtd_ctx* ctx, const double* S, double* rho, float* drho, const 
   memcpy(&ta, ctx->tm_pa, sizeof(ta));
   memcpy(&tb, ctx->tm_bt, sizeof(tb));
   k_rho_planes<<<grid, kRdThreads, smem, ctx->stream>>>(
-      ta, tb, N, Np, (int)ctx->Ng, nrep, slots, ctx->rho_ref, rho, drho, ctl, ctx->status, mom,
+      ta, tb, N, Np, (int)ctx->Ng, nrep, slots, ctx->rho_ref, ctx->rho_a32, rho, drho, ctl,
+      ctx->status, mom,
       ctx->nx, ctx->ny, ctx->nz, (float)ctx->h);
   ctx->rho_mom_blocks = mom ? ncta : 0;
   ++ctx->launches;
@@ -645,8 +724,8 @@ int rho_planes(rmgtd_ctx* ctx, const double* S, double* rho, float* drho, const 
 
 // Gram partials of the mixed path through the orbital planes (layout of k_gram32's); returns
 // 1 when the planes are not set up, else the status.  chunk must be a multiple of 64.
-int gram_planes(rmgtd_ctx* ctx, const float* w, int nw, float* part, int nsplit, int chunk,
-                const RepCtl* ctl) {
+int gram_planes(rmgtd_ctx* ctx, const float* w, const float* w_anchor, int nw, float* part,
+                int nsplit, int chunk, const RepCtl* ctl) {
   using namespace tc;
   if (!ctx->phi_pl || chunk % kPK) return 1;
   const int Np = ctx->Np_pl;
@@ -661,7 +740,7 @@ int gram_planes(rmgtd_ctx* ctx, const float* w, int nw, float* part, int nsplit,
   CUtensorMap tb;
   memcpy(&tb, ctx->tm_pb, sizeof(tb));
   k_gram_planes<<<dim3(nsplit, nw), kGpThreads, smem, ctx->stream>>>(
-      tb, w, ctx->N, Np, (int)ctx->Ng, nw, chunk, stages, part, ctl, ctx->status);
+      tb, w, w_anchor, ctx->N, Np, (int)ctx->Ng, nw, chunk, stages, part, ctl, ctx->status);
   ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_gram_planes");
   return RMGTD_OK;

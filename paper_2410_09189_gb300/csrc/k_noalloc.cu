@@ -12,6 +12,8 @@
 // The scratch array is shared by every call in the process on a given GPU and keeps the
 // last call's contents: calls whose work overlaps on the device race on it.  Each call
 // overwrites every scratch element it later reads, so nothing needs clearing.
+#include <cuda.h>   // CUcontext (the driver entry point comes from the runtime)
+
 #include <mutex>
 
 #include "rmgtd_internal.cuh"
@@ -25,9 +27,33 @@ constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) double g_gram_scratch[kScratchDoubles];
 
-// device address of g_gram_scratch per device ordinal (looked up once per device)
+// device address of g_gram_scratch per device ordinal, with the CUDA context it was looked
+// up in: a different current context on that device (after cudaDeviceReset, or a primary
+// context torn down and rebuilt) makes the next call look the address up again
 double* g_scratch_addr[kMaxDevices] = {nullptr};
+CUcontext g_scratch_ctx[kMaxDevices] = {nullptr};
 std::mutex g_scratch_mu;
+
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+
+// cuCtxGetCurrent through the runtime's driver entry point (no link to libcuda); NULL when
+// unavailable, in which case the address is looked up on every call
+CtxGetCurrentFn ctx_get_current() {
+  static CtxGetCurrentFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<CtxGetCurrentFn>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
 
 // partial[split][i*N + j] = sum over the split's grid range of A[i][g] w[g] B[j][g]
 __global__ void __launch_bounds__(256)
@@ -112,13 +138,17 @@ extern "C" int rmgtd_gram_noalloc(const double* a_dev, const double* b_dev, cons
   double* scratch = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
+    CUcontext cur = nullptr;
+    const CtxGetCurrentFn get = ctx_get_current();
+    const bool known = get && get(&cur) == CUDA_SUCCESS && cur;
+    if (!g_scratch_addr[dev] || !known || g_scratch_ctx[dev] != cur) {
       void* p = nullptr;
       e = cudaGetSymbolAddress(&p, g_gram_scratch);
       if (e != cudaSuccess)
         return set_error(nullptr, RMGTD_ECUDA,
                          std::string("gram_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
       g_scratch_addr[dev] = (double*)p;
+      g_scratch_ctx[dev] = known ? cur : nullptr;
     }
     scratch = g_scratch_addr[dev];
   }

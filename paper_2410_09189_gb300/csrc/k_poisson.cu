@@ -1732,6 +1732,19 @@ static size_t dst_smem_bytes(const rmgtd_ctx* ctx, int nrep, int grid) {
   return sizeof(float) * (fl + 2 * ((tile + 3) & ~(size_t)3) + 2 * ((wmx + 3) & ~(size_t)3));
 }
 
+// the preconditioner a solve of all replicas uses (RMGTD_PRECOND_DST when requested and its
+// tables and tiles fit in shared memory, else RMGTD_PRECOND_MG)
+int hartree_precond_in_use(rmgtd_ctx* ctx) {
+  const int kk = ctx->mixed ? 1 : 0;
+  const int grid = std::max(1, (ctx->coop_attr_set[kk] ? ctx->coop_grid[kk]
+                                                       : std::min(ctx->num_sms, ctx->red_cap)) /
+                                   std::max(1, ctx->tune_coop_div));
+  const int use_dst = ctx->dst_tab && ctx->hartree_precond == RMGTD_PRECOND_DST &&
+                      dst_smem_bytes(ctx, ctx->nrep, grid) <= kDstSmemMax &&
+                      (long)ctx->nrep * ctx->Ng < (1L << 31);
+  return use_dst ? RMGTD_PRECOND_DST : RMGTD_PRECOND_MG;
+}
+
 // host launcher of the persistent solve; f32 selects the mixed-path correction solve
 int hartree_coop(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* ctl, int zero_bc,
                  int nrep, int f32, int xc_fuse) {
@@ -1787,7 +1800,8 @@ int hartree_coop(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* ct
     af.p = ctx->pcg32_p;
     af.Ap = ctx->pcg32_Ap;
     af.Az = ctx->pcg32_Az;
-    af.tol = std::max(ctx->opt.poisson_tol, kMixedPoissonTol);
+    af.tol = ctx->opt.mixed_poisson_tol > 0.0 ? std::max(ctx->opt.mixed_poisson_tol, 1e-8)
+                                              : std::max(ctx->opt.poisson_tol, kMixedPoissonTol);
     if (xc_fuse && !ctx->tune_x && ctx->rho_ref32) af.dv_out = ctx->dv32;
     // the mixed pass: moments from the density kernel that just ran
     if (xc_fuse && !ctx->tune_x && ctx->rho_mom_blocks > 0 && rho == ctx->rho) {

@@ -561,7 +561,7 @@ k_gram32_reduce(int N, int Np, int nsplit, int nrep, const float* __restrict__ p
 
 int gram_mixed(rmgtd_ctx* ctx, const float* w, long wstride, int nw, double scale,
                const double* base, double* out, const RepCtl* ctl, unsigned long long* errbits,
-               long bstride) {
+               long bstride, const float* w_anchor) {
   const int N = ctx->N;
   const int T = ceil_div(N, kGT);
   const int Np = T * kGT;
@@ -588,12 +588,14 @@ int gram_mixed(rmgtd_ctx* ctx, const float* w, long wstride, int nw, double scal
     ps = (int)std::min<long>(ps, (long)(2 * ctx->gram_part_elems) / std::max<long>(per, 1));
     const int pchunk = (int)(ceil_div(ceil_div(ctx->Ng, (long)ps), 64L) * 64);
     const int pns = (int)ceil_div(ctx->Ng, (long)pchunk);
-    rc = gram_planes(ctx, w, nw, part, pns, pchunk, ctl);
+    rc = gram_planes(ctx, w, w_anchor, nw, part, pns, pchunk, ctl);
     if (rc == 0) {
       nsplit = pns;
       chunk = pchunk;
     }
   }
+  if (w_anchor && rc != 0)
+    return set_error(ctx, RMGTD_ESTATE, "gram_mixed: anchored weights need the orbital planes");
   if (rc > 0 && tc) rc = gram_tc(ctx, w, nw, part, nsplit, chunk, ctl);
   if (rc < 0) return rc;
   if (rc > 0) {
@@ -1311,7 +1313,7 @@ int step_end(rmgtd_ctx* ctx) {
       ctx->failed, ctx->done_steps, ctx->stats_dev, ctx->stats_cap, ctx->status);
   ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_step_end");
-  return RMGTD_OK;
+  return planes_anchor_update(ctx);
 }
 
 // ---------------------------------------------------------------------------------------

@@ -106,6 +106,14 @@ struct rmgtd_ctx {
   alignas(64) unsigned char tm_pb[128] = {};   // planes, 64 x Np_pl boxes (Gram operand B)
   alignas(64) unsigned char tm_bt[128] = {};   // density-change planes, 64 x 32 boxes
   int rho_pl_attr = 0, gram_pl_attr = 0;       // dynamic shared memory set for the kernels
+  // anchors of the orbital-plane contractions (per replica, consistent pairs): the density is
+  // formed as rho(Sa) + sum (S - Sa)_ij phi_i phi_j and the Hamiltonian as
+  // Ha + h^3 Phi^T diag(V - Va) Phi, so the split products' rounding scales with the change
+  // since the last completed step, not with the distance from the set-up state
+  double* Sa = nullptr;       // [nrep][N*N] Re P of the anchor
+  double* Ha = nullptr;       // [nrep][N*N] H of the anchor potential
+  float* rho_a32 = nullptr;   // [nrep][Ng] rho(Sa) - rho_ref
+  float* dv_a32 = nullptr;    // [nrep][Ng] V_Hxc of the anchor - vref
   double* vion = nullptr;      // [Ng] V_loc + V_ext
   double* f_dev = nullptr;     // [N]
 
@@ -331,9 +339,11 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
 // only grows; `target` = gridDim.x * (number of this barrier, counting from 1).  Thread 0
 // of each block arrives with a release reduction (the block barrier before it orders the
 // block's writes ahead of it) and polls with acquire loads (the block barrier after it
-// orders the block's later reads behind it).  The wait gives up after kSpinLimit polls and
-// records RMGTD_ETIMEOUT in *status; returns false then.
-__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned target, int* status) {
+// orders the block's later reads behind it).  The wait gives up after `limit` polls
+// (kSpinLimit unless a diagnostic passes a smaller one) and records RMGTD_ETIMEOUT in
+// *status; returns false then.
+__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned target, int* status,
+                                             unsigned limit = kSpinLimit) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -341,7 +351,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned target, i
     asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(count) : "memory");
     unsigned spins = 0;
     while (ld_acquire_u32(count) < target) {
-      if (++spins > kSpinLimit) {
+      if (++spins > limit) {
         atomicCAS(status, 0, (int)RMGTD_ETIMEOUT);
         ok = 0;
         break;
@@ -385,9 +395,10 @@ int gram(rmgtd_ctx* ctx, const double* A, const double* B, const double* w, long
          const RepCtl* ctl, int sym, unsigned long long* errbits, long bstride = 0);
 int rho_dev(rmgtd_ctx* ctx, const double* S, double* rho, const RepCtl* ctl, int nrep);
 int rho_dev_mixed(rmgtd_ctx* ctx, const double* S, double* rho, const RepCtl* ctl, int nrep);
+// w_anchor (may be NULL, orbital-plane path only): the weight is w - w_anchor
 int gram_mixed(rmgtd_ctx* ctx, const float* w, long wstride, int nw, double scale,
                const double* base, double* out, const RepCtl* ctl, unsigned long long* errbits,
-               long bstride = 0);
+               long bstride = 0, const float* w_anchor = nullptr);
 int to_float(rmgtd_ctx* ctx, const double* in, float* out, long n);
 // phi32t <- phi32 in 32-point tiles (layout above)
 int tile_orbitals(rmgtd_ctx* ctx);
@@ -414,6 +425,7 @@ int poisson_red_cap(int num_sms, int red_blocks);
 int hartree_coop(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* ctl, int zero_bc,
                  int nrep, int f32, int xc_fuse = 0);
 int hartree_reset_history(rmgtd_ctx* ctx);
+int hartree_precond_in_use(rmgtd_ctx* ctx);
 // k_tc.cu
 int rho_tc(rmgtd_ctx* ctx, double* rho, float* drho, const RepCtl* ctl, int nrep);
 int gram_tc(rmgtd_ctx* ctx, const float* w, int nw, float* part, int nsplit, int chunk,
@@ -421,10 +433,16 @@ int gram_tc(rmgtd_ctx* ctx, const float* w, int nw, float* part, int nsplit, int
 // k_contract.cu (orbital planes, 32 < N <= 256): set-up, and the two contractions; the latter
 // return 1 when the planes are not set up (the caller then uses the other kernels)
 int planes_setup(rmgtd_ctx* ctx);
+// anchors <- the set-up reference state (all replicas)
+int planes_anchor_reset(rmgtd_ctx* ctx);
+// after a completed step (same condition as k_step_end): Sa <- S0, Ha <- H0, rho_a <- drho,
+// Va <- dV of every replica
+int planes_anchor_update(rmgtd_ctx* ctx);
 int rho_planes(rmgtd_ctx* ctx, const double* S, double* rho, float* drho, const RepCtl* ctl,
                int nrep);
-int gram_planes(rmgtd_ctx* ctx, const float* w, int nw, float* part, int nsplit, int chunk,
-                const RepCtl* ctl);
+// w_anchor (may be NULL): the weight is w - w_anchor
+int gram_planes(rmgtd_ctx* ctx, const float* w, const float* w_anchor, int nw, float* part,
+                int nsplit, int chunk, const RepCtl* ctl);
 int conv16_tc(int nx, int ny, int nz, int B, const float* x, const __nv_bfloat16* W,
               const float* bias, float* y, int silu, int* status, int num_sms, cudaStream_t s);
 // k_surrogate.cu

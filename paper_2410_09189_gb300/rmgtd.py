@@ -59,7 +59,7 @@ class COptions(ctypes.Structure):
         ("use_graph", ctypes.c_int), ("stream", ctypes.c_void_p),
         ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", ctypes.c_void_p),
         ("subspace_scf", ctypes.c_int), ("subspace_mix", ctypes.c_double),
-        ("subspace_tol", ctypes.c_double),
+        ("subspace_tol", ctypes.c_double), ("mixed_poisson_tol", ctypes.c_double),
     ]
 
 
@@ -128,6 +128,8 @@ def load_library(path: Optional[str] = None):
         "rmgtd_batch_step": (i, [vp, i, ctypes.POINTER(ctypes.POINTER(CStats))]),
         "rmgtd_profile_read": (i, [vp, _c_double_p, ctypes.POINTER(ctypes.c_longlong),
                                    ctypes.POINTER(ctypes.c_longlong)]),
+        "rmgtd_selftest_barrier_timeout": (i, [vp, ctypes.c_uint, _c_int_p]),
+        "rmgtd_get_hartree_preconditioner": (i, [vp, _c_int_p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -154,7 +156,8 @@ class Context:
                  orthonormalize: bool = True, poisson_tol: float = 1e-12,
                  poisson_max_iter: int = 200, use_graph: bool = True,
                  stream: Optional[int] = None, torch_alloc: bool = True,
-                 subspace_scf: int = 0, subspace_mix: float = 0.3, subspace_tol: float = 1e-10):
+                 subspace_scf: int = 0, subspace_mix: float = 0.3, subspace_tol: float = 1e-10,
+                 mixed_poisson_tol: float = 0.0):
         import torch
 
         lib = load_library()
@@ -203,6 +206,7 @@ class Context:
         opt.use_graph = 1 if use_graph else 0
         opt.subspace_scf, opt.subspace_mix = int(subspace_scf), float(subspace_mix)
         opt.subspace_tol = float(subspace_tol)
+        opt.mixed_poisson_tol = float(mixed_poisson_tol)
         if stream is None:
             stream = torch.cuda.current_stream().cuda_stream
         self.stream = int(stream)
@@ -382,6 +386,19 @@ class Context:
         n = ctypes.c_longlong()
         self._check(self._lib.rmgtd_profile_read(self._ctx, _dptr(ms), calls, ctypes.byref(n)))
         return (dict(zip(PHASES, ms.tolist())), dict(zip(PHASES, list(calls))), int(n.value))
+
+    def hartree_preconditioner(self) -> int:
+        """PRECOND_DST or PRECOND_MG: the preconditioner the Hartree solves use now."""
+        k = ctypes.c_int(-1)
+        self._check(self._lib.rmgtd_get_hartree_preconditioner(self._ctx, ctypes.byref(k)))
+        return int(k.value)
+
+    def selftest_barrier_timeout(self, polls: int) -> int:
+        """Status recorded by blocks whose grid-barrier wait (limited to `polls` polls) had
+        to give up (rmgtd_selftest_barrier_timeout)."""
+        st = ctypes.c_int(0)
+        self._check(self._lib.rmgtd_selftest_barrier_timeout(self._ctx, int(polls), ctypes.byref(st)))
+        return int(st.value)
 
     def profile_counters(self):
         """(Hartree replica solves, CG iterations summed over them) since profile()."""

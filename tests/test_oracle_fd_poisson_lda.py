@@ -147,3 +147,65 @@ def test_p_projectors_odd():
     for m, (idx, val) in enumerate(projs[:3]):
         q = (x, y, z)[m][idx] - s.pos[s.proj_atom[m], m]
         assert np.all(val * q >= 0)
+
+
+def _one_ion(n, h, Z, rc, pos):
+    s = inputs.small(n=n, h=h)
+    s.pos = np.array([pos], dtype=float)
+    s.Z = np.array([Z], dtype=float)
+    s.rc_loc = np.array([rc], dtype=float)
+    return s
+
+
+def test_local_well_is_the_potential_of_a_gaussian_ion():
+    """-v_local / Z of one ion is the Hartree potential of a unit Gaussian charge of width
+    sigma = r_c / sqrt(2) (Section 2.1's local pseudopotential read as the field of a Gaussian
+    ion): compared with the oracle's own Poisson solve of that density (pinned separately by
+    the closed form above), on an odd grid whose centre point sits on the ion, so the r = 0
+    value -2 Z / (r_c sqrt(pi)) is part of the comparison."""
+    Z, rc = 1.5, math.sqrt(2.0) * 1.0          # sigma = 1.0 bohr, as in the Poisson pin
+    s = _one_ion(65, 0.3, Z, rc, (0.0, 0.0, 0.0))
+    x, y, z = ham.full_coords(s)
+    r2 = x * x + y * y + z * z
+    sigma = rc / math.sqrt(2.0)
+    rho = (2 * math.pi * sigma ** 2) ** -1.5 * np.exp(-r2 / (2 * sigma ** 2))
+    V = poisson.hartree(s, rho, tol=1e-13)
+    v = ham.v_local(s)
+    assert np.max(np.abs(-v / Z - V)) < 1e-7
+    c = (s.n[0] - 1) // 2
+    assert r2[c, c, c] == 0.0
+    assert v[c, c, c] == pytest.approx(-2.0 * Z / (rc * math.sqrt(math.pi)), rel=1e-15)
+    # the sign and radius convention a plausible slip would break: erf(r/(2 rc)) or +Z
+    assert np.max(np.abs(-v / Z - V)) < 1e-3 * np.max(np.abs(V))
+
+
+def test_local_wells_superpose():
+    """Several ions: the local potential is the sum of the single-ion wells."""
+    s2 = inputs.small(n=24, h=0.4)
+    s2.Z = np.array([1.0, 2.5])
+    s2.rc_loc = np.array([0.5, 0.9])
+    s2.pos = np.array([[0.3, -0.2, 0.7], [-1.1, 0.4, -0.5]])
+    total = ham.v_local(s2)
+    parts = sum(ham.v_local(_one_ion(24, 0.4, s2.Z[a], s2.rc_loc[a], s2.pos[a])) for a in range(2))
+    assert np.max(np.abs(total - parts)) < 1e-13
+
+
+def test_ion_energy_is_the_gaussian_ion_interaction():
+    """E_ion = sum_{a<b} Z_a Z_b erf(R_ab / sqrt(rc_a^2 + rc_b^2)) / R_ab is the electrostatic
+    interaction of Gaussian ion charges: compared with the grid integral
+    h^3 sum_r rho_a(r) (-v_local_b(r)) of each pair (rho_a the Gaussian charge Z_a of width
+    rc_a / sqrt(2), v_local_b the oracle's well of ion b, pinned above), on a fine grid."""
+    s = inputs.small(n=80, h=0.16)
+    s.Z = np.array([1.5, 2.0, 0.75])
+    s.rc_loc = np.array([0.9, 1.1, 1.0])
+    s.pos = np.array([[0.8, -0.3, 0.9], [-0.9, 0.6, -0.4], [0.2, 0.9, -1.0]])
+    x, y, z = ham.full_coords(s)
+    h3 = s.h ** 3
+    expect = 0.0
+    for a in range(3):
+        r2 = (x - s.pos[a, 0]) ** 2 + (y - s.pos[a, 1]) ** 2 + (z - s.pos[a, 2]) ** 2
+        rho_a = s.Z[a] * (math.pi * s.rc_loc[a] ** 2) ** -1.5 * np.exp(-r2 / s.rc_loc[a] ** 2)
+        for b in range(a):
+            vb = ham.v_local(_one_ion(80, 0.16, s.Z[b], s.rc_loc[b], s.pos[b]))
+            expect += h3 * float(np.sum(rho_a * (-vb)))
+    assert ham.ion_energy(s) == pytest.approx(expect, rel=1e-9, abs=1e-12)
