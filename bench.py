@@ -1,21 +1,27 @@
 #!/usr/bin/env python
 """Benchmark of the RT-TDDFT time step (Algorithm 1) on GB300.
 
-Workload: the benzene-like ring (12 pseudo-atoms, s-type KB on the 6 heavy atoms), 64^3 grid
-at h = 0.35 bohr, N = 15 occupied + 15 virtual orbitals, three replicas kicked along x, y, z
-(kappa = 1e-3) propagated together, dt = 0.05 a.u., H_thrs = 1e-7, dP_thrs = 1e-10.  One
-"step" advances all three replicas by one time step, SCF passes included.  Orbitals are
-seeded smooth random fields orthonormalised on the device (synthetic data).
+Headline workload (default): the 147-atom Mackay icosahedron (Z = 1 Gaussian-erf wells with an
+s-type Kleinman-Bylander projector on every atom), 128^3 grid at h = 0.4 bohr, N = 74 doubly
+occupied + 74 virtual orbitals, one replica kicked along z (kappa = 1e-3), dt = 0.05 a.u.,
+H_thrs = 1e-7, dP_thrs = 1e-10, started from P_0 = diag(f) of seeded smooth random orbitals
+orthonormalised on the device (synthetic data; no molecular inputs exist here).  One "step" is
+one time step of the replica, SCF passes included.  `value` is the mixed path (tensor-core
+bfloat16 split products around a float64 reference state); the float64 path is timed on the
+same workload.  The accuracy of both paths is stated against the stored FP64 oracle run of the
+same workload (tests/golden/icosa128_window.json).  The 12-atom ring (64^3, N = 30, three
+kicks) is measured as a secondary line.
 
 Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle on the same
-workload instead (a bounded sample per step).  Under torchrun every rank propagates its own
-replica set (independent problems, no data-path collective): weak scaling.
+workload.  Under torchrun every rank propagates its own replica (independent problems, no
+data-path collective): weak scaling.
 """
 from __future__ import annotations
 
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -30,10 +36,23 @@ if ROOT not in sys.path:
 
 METRIC = "RT-TDDFT time-steps/sec and grid-point·orbital updates/sec, mixed vs FP64 GPU"
 UNIT = "time-steps/s"
-SUBSPACE_SCF = 200          # set-up SCF iterations inside the orbital block (stationary start)
-SUR_STEPS = 300             # trajectory steps recorded to train the learned SCF seed
+SUR_STEPS = 300             # trajectory steps recorded to train the learned SCF seed (ring)
 SUR_ITERS = 2000            # Adam iterations of that training
-FP64_PEAK_GFLOPS = 1250.0   # GB300 float64 rate (nominal 1.25 TFLOP/s)
+FP64_PEAK_TFLOPS = 1.25     # GB300 float64 rate (nominal)
+REF_BUDGET_S = 150.0        # wall-clock budget of the oracle's timed steps (reference arm)
+CPU_BASELINE_BUDGET_S = 30.0
+
+# the workloads: constructor, replicas and kick axes, start, stored oracle run
+WORKLOADS = {
+    "icosa": dict(label="icosahedron-147-atoms-128^3-N148-kick-z", nrep=1, axes=(2,),
+                  subspace_scf=0, golden="icosa128_window.json", trajectory_steps=1000,
+                  start="P_0 = diag(f) of the orthonormalised seeded orbitals, kick along z"),
+    "ring": dict(label="ring-12-atoms-64^3-N30-kicks-xyz", nrep=3, axes=(0, 1, 2),
+                 subspace_scf=200, golden="ring64_three_kicks.json", trajectory_steps=2000,
+                 start="ground state inside the orbital block (<= 200 SCF iterations at set-up), "
+                       "then kicks along x, y, z"),
+}
+BENCH_THRESHOLDS = dict(H_thrs=1e-7, dP_thrs=1e-10, poisson_tol=1e-10)
 
 
 def _peaks():
@@ -104,21 +123,202 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
-def _workload():
+def _system(name):
     from paper_2410_09189_gb300 import inputs
-    s = inputs.ring()
+    s = inputs.icosa() if name == "icosa" else inputs.ring()
     raw = inputs.smooth_random_orbitals(s).reshape(s.N, s.Ng)
     return s, raw
 
 
-def _config(s, precision):
-    return {"workload": "ring-12-atoms-64^3-N30-kicks-xyz", "grid": list(s.n), "h": s.h,
-            "N": s.N, "nocc": s.nocc, "replicas": 3, "dt": s.dt, "kappa": s.kappa,
-            "H_thrs": 1e-7, "dP_thrs": 1e-10, "precision": precision,
+def _config(name, s, precision):
+    w = WORKLOADS[name]
+    return {"workload": w["label"], "grid": list(s.n), "h": s.h, "N": s.N, "nocc": s.nocc,
+            "natoms": int(len(s.Z)), "kb_projectors": s.nproj, "replicas": w["nrep"],
+            "dt": s.dt, "kappa": s.kappa, **BENCH_THRESHOLDS, "precision": precision,
             "orbitals": "seeded smooth random fields, orthonormalised on the device",
-            "initial_state": f"ground state inside the orbital block (<= {SUBSPACE_SCF} SCF "
-                             "iterations at set-up), then kicks along x, y, z",
-            "l2": "flushed (256 MiB write) between timed steps"}
+            "initial_state": w["start"],
+            "l2": "flushed (256 MiB write) between timed steps; orbital planes exceed L2"}
+
+
+def _golden(name):
+    with open(os.path.join(ROOT, "tests", "golden", WORKLOADS[name]["golden"])) as f:
+        return json.load(f)
+
+
+def accuracy_against_oracle(d, e, t, golden, steps_done):
+    """Errors of one GPU trajectory against the stored oracle run, over the stored steps the
+    trajectory covers: dipole max_t |d - d_ref| / max_t |d_ref(t) - d_ref(0)| (per replica,
+    worst replica reported), energy max_t |E - E_ref|, trace max_t |Tr P - Tr P_ref|.
+    d[k][a], e[k][a], t[k][a]: observables after step k (k = 0: after the kicks)."""
+    out = {"dipole_rel_err": 0.0, "energy_err": 0.0, "trace_err": 0.0}
+    nst = 0
+    for a, tr in enumerate(golden["replicas"]):
+        steps = tr.get("step", list(range(len(tr["dipole"]))))
+        use = [i for i, k in enumerate(steps) if k <= steps_done]
+        ref = np.array(tr["dipole"])[use]
+        got = np.array([d[steps[i]][a] for i in use])
+        scale = np.max(np.abs(np.array(tr["dipole"]) - np.array(tr["dipole"])[0]))
+        out["dipole_rel_err"] = max(out["dipole_rel_err"], float(np.max(np.abs(got - ref)) / scale))
+        out["energy_err"] = max(out["energy_err"], float(np.max(np.abs(
+            np.array([e[steps[i]][a] for i in use]) - np.array(tr["energy"])[use]))))
+        out["trace_err"] = max(out["trace_err"], float(np.max(np.abs(
+            np.array([t[steps[i]][a] for i in use]) - np.array(tr["trace"])[use]))))
+        nst = steps[use[-1]]
+    out["window"] = f"steps 0..{nst} after the kick(s), compared at the oracle's stored steps"
+    out["oracle_thresholds"] = {k: golden["options"][k] for k in ("H_thrs", "dP_thrs")}
+    return out
+
+
+def trajectory_observables(ctx, nrep, nsteps, every=1):
+    """dipole, energy and Tr P of every replica after each `every`-th step (k = 0: now)."""
+    from paper_2410_09189_gb300 import rmgtd
+    d, e, t = {}, {}, {}
+
+    def rec(k):
+        d[k] = [ctx.dipole(a) for a in range(nrep)]
+        e[k] = [ctx.energy(a) for a in range(nrep)]
+        t[k] = [float(np.trace(ctx.get_matrix(rmgtd.MAT_P_RE, a))) for a in range(nrep)]
+
+    rec(0)
+    k = 0
+    while k < nsteps:
+        n = min(every, nsteps - k)
+        ctx.step(n)
+        k += n
+        rec(k)
+    return d, e, t
+
+
+# ---------------------------------------------------------------------------------------
+def _host_info():
+    model = platform.processor() or platform.machine()
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part", "hardware")):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    return {"cpu": model, "machine": platform.machine(), "logical_cores": os.cpu_count()}
+
+
+def _blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        return max([d.get("num_threads", 1) for d in threadpool_info()] or [os.cpu_count()])
+    except Exception:
+        return os.cpu_count()
+
+
+class OracleRun:
+    """The FP64 oracle on a workload, from the same start as the GPU arm: the propagator of
+    Algorithm 1 (H update in the Delta-V form H_core + h^3 Phi^T diag(V) Phi -- the form the
+    GPU path computes; the oracle's full grid apply gives the same H up to rounding), the
+    kicked replicas, and timers for whole time steps and single SCF passes."""
+
+    def __init__(self, name):
+        from oracle import hamiltonian as oham, tddft
+        self.tddft = tddft
+        s, raw = _system(name)
+        w = WORKLOADS[name]
+        self.s = s
+        t0 = time.perf_counter()
+        phi = oham.orthonormalize(s, raw)
+        del raw
+        self.pr = tddft.Propagator(s, phi, tddft.Options(
+            dt=s.dt, H_thrs=BENCH_THRESHOLDS["H_thrs"], dP_thrs=BENCH_THRESHOLDS["dP_thrs"],
+            poisson_tol=BENCH_THRESHOLDS["poisson_tol"], full_apply=False))
+        st0 = self.pr.initial_state(w["subspace_scf"])
+        self.states = []
+        for a in w["axes"]:
+            st = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in st0.items()}
+            st["P0"] = self.pr.kick(st["P0"], a, s.kappa)
+            self.states.append(st)
+        self.setup_s = time.perf_counter() - t0
+        self.passes = []
+
+    def steps(self, budget_s, max_steps):
+        """Whole time steps (every replica advanced once), timed one by one until max_steps
+        or the budget is used (at least one)."""
+        times = []
+        t_start = time.perf_counter()
+        while len(times) < max_steps:
+            t1 = time.perf_counter()
+            for st in self.states:
+                self.passes.append(self.pr.step(st)["passes"])
+            times.append(time.perf_counter() - t1)
+            if time.perf_counter() - t_start > budget_s:
+                break
+        return times
+
+    def one_pass(self):
+        """Seconds of one SCF pass of replica 0 (commutator series + DFT evaluation)."""
+        st = self.states[0]
+        Hbar = 0.5 * (st["H0"] + (2.0 * st["H0"] - st["Hm1"]))
+        t1 = time.perf_counter()
+        P1, _ = self.pr.expand(st["P0"], Hbar, self.s.dt)
+        self.pr.dft(P1)
+        return time.perf_counter() - t1
+
+
+def run_reference(args):
+    """The reference arm: the FP64 CPU oracle on the headline workload and from the same
+    initial state, on the host cores.  Each timed step is one whole time step (every replica,
+    SCF passes included); steps are timed until --steps or a wall-clock budget is reached, and
+    the line reports the measured mean."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    name = args.workload
+    orc = OracleRun(name)
+    s = orc.s
+    w_times = orc.steps(REF_BUDGET_S, args.warmup + args.steps)
+    nw = min(args.warmup, len(w_times) - 1)
+    timed = w_times[nw:]
+    mean = statistics.mean(timed)
+    value = 1.0 / mean
+    cores = _blas_threads()
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+           "n_gpus": args.gpus, "steps": len(timed), "warmup": nw,
+           "ms_per_step": mean * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": _config(name, s, "fp64-cpu-oracle"),
+           "grid_point_orbital_updates_per_s": value * s.Ng * s.N * WORKLOADS[name]["nrep"],
+           "same_config": True,
+           "scf_passes_per_replica_step": float(np.mean(orc.passes)) if orc.passes else None,
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "host": _host_info(), "setup_s": orc.setup_s,
+                            "sample": f"{len(timed)} whole time step(s) of the workload timed "
+                                      f"(requested {args.steps} after {args.warmup} warm-up; "
+                                      f"wall-clock budget {REF_BUDGET_S:.0f} s)"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def cpu_baseline_sample(name):
+    """The oracle timed on the host cores on a bounded sample of the headline workload:
+    whole time steps with all BLAS threads (about 30 s), and one SCF pass with one thread,
+    scaled by the passes per step of the first measurement."""
+    orc = OracleRun(name)
+    times = orc.steps(CPU_BASELINE_BUDGET_S, 3)
+    out = {"value": 1.0 / statistics.mean(times), "unit": UNIT, "cores": _blas_threads(),
+           "kind": "oracle", "host": _host_info(), "setup_s": orc.setup_s,
+           "sample": f"{len(times)} whole time step(s) of the workload from the GPU arm's start "
+                     f"(budget {CPU_BASELINE_BUDGET_S:.0f} s)"}
+    passes = float(np.mean(orc.passes)) * len(orc.states)
+    try:
+        from threadpoolctl import threadpool_limits
+        with threadpool_limits(limits=1):
+            t1 = orc.one_pass()
+        out["one_thread"] = {"value": 1.0 / (t1 * passes), "cores": 1,
+                             "sample": f"one SCF pass with BLAS on 1 thread, x {passes:.2f} "
+                                       "passes per time step (all replicas) of the first "
+                                       "measurement"}
+    except Exception as e:  # threadpoolctl missing on the host
+        out["one_thread"] = {"unavailable": str(e)}
+    return out
 
 
 # ---------------------------------------------------------------------------------------
@@ -138,78 +338,6 @@ def job_throughput(steps: int, world: int, max_ms: float) -> float:
     """Whole-job time-steps/s: every rank advances its own replica set `steps` steps (weak
     scaling), and the job takes as long as the slowest rank."""
     return world * steps / (max_ms * 1e-3)
-
-
-def run_reference(args):
-    """The FP64 CPU oracle on the same workload: each step is one time step of ONE replica
-    (a bounded sample), reported in the 3-replica unit."""
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
-        return 0
-    from oracle import hamiltonian as oham, tddft
-    s, raw = _workload()
-    phi = oham.orthonormalize(s, raw)
-    pr = tddft.Propagator(s, phi, tddft.Options(dt=s.dt))
-    st = pr.initial_state()
-    st["P0"] = pr.kick(st["P0"], 2, s.kappa)
-    times = []
-    for i in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        pr.step(st)
-        dt = time.perf_counter() - t0
-        if i >= args.warmup:
-            times.append(dt)
-    per_rep = statistics.mean(times)
-    value = 1.0 / (3.0 * per_rep)
-    cores = os.cpu_count()
-    try:
-        from threadpoolctl import threadpool_info
-        cores = max([d.get("num_threads", 1) for d in threadpool_info()] or [cores])
-    except Exception:
-        pass
-    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
-           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-           "ms_per_step": 3.0 * per_rep * 1e3, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": _config(s, "fp64-cpu-oracle"),
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                            "sample": "one time step of one of the three replicas per timed "
-                                      "step, scaled x3"},
-           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
-                   "d2h_bytes_per_step": 0}}
-    print(json.dumps(out), flush=True)
-    return 0
-
-
-def cpu_baseline_sample(budget_s: float = 20.0):
-    """Time the oracle as it stands on a bounded sample of the workload (host cores)."""
-    from oracle import hamiltonian as oham, tddft
-    s, raw = _workload()
-    phi = oham.orthonormalize(s, raw)
-    pr = tddft.Propagator(s, phi, tddft.Options(dt=s.dt))
-    st = pr.initial_state()
-    st["P0"] = pr.kick(st["P0"], 2, s.kappa)
-    times = []
-    t_start = time.perf_counter()
-    while True:
-        t0 = time.perf_counter()
-        pr.step(st)
-        times.append(time.perf_counter() - t0)
-        if time.perf_counter() - t_start > budget_s or len(times) >= 4:
-            break
-    per_rep = statistics.mean(times)
-    cores = os.cpu_count()
-    try:
-        from threadpoolctl import threadpool_info
-        cores = max([d.get("num_threads", 1) for d in threadpool_info()] or [cores])
-    except Exception:
-        pass
-    return {"value": 1.0 / (3.0 * per_rep), "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{len(times)} time step(s) of one replica (x3 for the 3-replica unit)"}
-
-
-# ---------------------------------------------------------------------------------------
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
 
 
 def _mg_levels(n):
@@ -278,16 +406,67 @@ def _traffic(kernel, workload):
         return None
 
 
-def _flops_per_phase(N, Ng, rep_passes, terms_total):
-    """Algorithmic work of the float64 phases (per whole timed region)."""
+
+def _phase_work(s, mixed, rep_passes, terms_total, h_solves, h_iters, precond):
+    """Algorithmic work of each phase over the profiled region: flops, bytes and the peak
+    that bounds it (the roofline's numerators)."""
+    N, Ng = s.N, s.Ng
+    sv = 4 if mixed else 8
+    # the two contractions read the orbitals once (bfloat16 hi + lo planes, 4 B per value on
+    # the mixed path; float64 on the other) and a grid array (drho written / dV read)
+    orb_b = (4 if mixed else 8) * N * Ng + sv * Ng
     return {
         # rho = sum_ij S_ij phi_i phi_j with S symmetric: N(N+1)/2 multiply-adds per point
-        "rho": float(rep_passes) * Ng * N * (N + 1),
+        "rho": {"flops": float(rep_passes) * Ng * N * (N + 1), "bytes": float(rep_passes) * orb_b},
         # H_ij = h^3 sum_g phi_i V phi_j, j >= i: N(N+1)/2 multiply-adds per point (+ V)
-        "hupdate": float(rep_passes) * Ng * (N * (N + 1) + N),
-        # two N x N x N products per commutator term
-        "eldyn": float(terms_total) * 4.0 * N ** 3,
+        "hupdate": {"flops": float(rep_passes) * Ng * (N * (N + 1) + N),
+                    "bytes": float(rep_passes) * orb_b},
+        # two N x N x N products per commutator term (float64)
+        "eldyn": {"flops": float(terms_total) * 4.0 * N ** 3, "bytes": 0.0},
+        "hartree": {"flops": 0.0, "bytes": hartree_bytes(s.n, h_solves, h_iters, mixed,
+                                                         precond)},
     }
+
+
+def _roofline_entry(phase, work, ms, calls, mixed, peaks, peak_kind):
+    """Fraction of the phase's roofline: the larger of its HBM time (algorithmic bytes at the
+    measured copy bandwidth) and its arithmetic time (tensor pipe for the mixed contractions,
+    float64 ALU otherwise), over the measured time."""
+    t = ms * 1e-3
+    hbm = work["bytes"] / t / 1e9
+    hbm_frac = hbm / peaks["hbm_gbs"]
+    e = {"phase": phase, "ms_per_call": ms / max(calls, 1), "calls": calls,
+         "hbm_gbs": hbm, "hbm_frac": hbm_frac,
+         "algorithmic_bytes_per_call": work["bytes"] / max(calls, 1)}
+    if phase in ("rho", "hupdate") and mixed:
+        useful = work["flops"] / t / 1e12
+        pipe = 3.0 * useful      # hi*hi + hi*lo + lo*hi: three bfloat16 products per product
+        peak = peaks["bf16_tflops_sustained"]
+        e.update({"tensor_tflops_useful": useful, "tensor_tflops_pipe": pipe,
+                  "tensor_peak": peak, "tensor_frac": pipe / peak,
+                  "tensor_peak_source": f"{peak_kind} bf16_tflops_sustained (the kernels run "
+                                        "inside a long step); 3 split products per product"})
+        if pipe / peak > hbm_frac:
+            e.update({"bound": "tensor", "achieved": pipe, "peak": peak, "unit": "TFLOP/s",
+                      "frac": pipe / peak})
+        else:
+            e.update({"bound": "hbm", "achieved": hbm, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                      "frac": hbm_frac})
+    elif phase in ("rho", "hupdate", "eldyn"):
+        alu = work["flops"] / t / 1e12
+        e.update({"bound": "alu", "achieved": alu, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                  "frac": alu / FP64_PEAK_TFLOPS,
+                  "peak_source": "GB300 float64 rate, nominal 1.25 TFLOP/s"})
+    else:
+        e.update({"bound": "hbm", "achieved": hbm, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                  "frac": hbm_frac})
+    return e
+
+
+KERNELS = {("rho", True): "k_rho_planes", ("hupdate", True): "k_gram_planes",
+           ("hartree", True): "k_hartree_coop", ("eldyn", True): "k_eldyn",
+           ("rho", False): "k_rho", ("hupdate", False): "k_gram_partial",
+           ("hartree", False): "k_hartree_coop", ("eldyn", False): "k_eldyn"}
 
 
 def run_ours(args):
@@ -308,195 +487,229 @@ def run_ours(args):
     __graft_entry__.build()
     from paper_2410_09189_gb300 import rmgtd
 
-    prec = rmgtd.PREC_MIXED if args.precision == "mixed" else rmgtd.PREC_FP64
-    s, raw = _workload()
-    kw = dict(nrep=3, H_thrs=1e-7, dP_thrs=1e-10, poisson_tol=1e-10,
-              subspace_scf=SUBSPACE_SCF)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB
     stream = torch.cuda.current_stream()
-
-    def timed_steps(ctx, nsteps, profile, nvtx_name="rmgtd_other"):
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(nsteps)]
-        if profile:
-            ctx.profile(True)
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
-        w0 = time.perf_counter()
-        st = []
-        torch.cuda.nvtx.range_push(nvtx_name)
-        for i in range(nsteps):
-            flush.zero_()
-            ev[i][0].record(stream)
-            st.append(ctx.step(1))
-            ev[i][1].record(stream)
-        torch.cuda.nvtx.range_pop()
-        torch.cuda.synchronize()
-        if world > 1:
-            dist.barrier()
-        wall = time.perf_counter() - w0
-        prof = ctx.profile_read() if profile else None
-        return [a.elapsed_time(b) for a, b in ev], np.concatenate(st), wall, prof
-
-    def run_path(p, nsteps, with_clocks, state=None, net=None):
-        c = rmgtd.Context(s, raw, use_graph=True, precision=p, **kw)
-        if state is None:
-            for a in range(3):
-                c.kick(a, a, s.kappa)
-        else:
-            c.load(state)
-        if net is not None:
-            c.attach_net(net)
-        for _ in range(args.warmup):
-            c.step(1)
-        smp = ClockSampler(local)
-        if with_clocks:
-            smp.start()
-        ms, stt, wl, prof = timed_steps(c, nsteps, profile=True,
-                                        nvtx_name="rmgtd_timed" if with_clocks else "rmgtd_other")
-        clk = smp.stop() if with_clocks else None
-        c.close()
-        tot = max_over_ranks(float(sum(ms)), world)
-        return tot, stt, wl, prof[2], clk
-
-    # timed region: every step is one CUDA graph (device-side SCF and Hartree loops)
-    total_ms, st, wall, launches, clocks = run_path(prec, args.steps, True)
-    rep_passes = int(st["passes"].sum())
-    terms_total = int(st["terms_sum"].sum())
-    value = job_throughput(args.steps, world, total_ms)
-    ms_per_step = total_ms / args.steps
+    prec = rmgtd.PREC_MIXED if args.precision == "mixed" else rmgtd.PREC_FP64
     other = rmgtd.PREC_FP64 if prec == rmgtd.PREC_MIXED else rmgtd.PREC_MIXED
-    o_ms, o_st, _, _, _ = run_path(other, args.steps, False)
-    other_path = {"precision": "fp64" if other == rmgtd.PREC_FP64 else "mixed",
-                  "value": world * args.steps / (o_ms * 1e-3), "unit": UNIT,
-                  "ms_per_step": o_ms / args.steps,
-                  "scf_passes_per_replica_step": float(o_st["passes"].sum()) / (3.0 * args.steps)}
+    pname = {rmgtd.PREC_MIXED: "mixed", rmgtd.PREC_FP64: "fp64"}
 
-    # the mixed path with the learned seed: a network trained (library kernels only) on the
-    # first SUR_STEPS steps of this workload's own trajectory, then the continuation timed
-    # with and without it from the same state (a window the network has not seen)
-    surrogate_path = None
-    if prec == rmgtd.PREC_MIXED and not args.no_surrogate:
-        from paper_2410_09189_gb300 import surrogate
-        tctx = rmgtd.Context(s, raw, use_graph=True, precision=prec, **kw)
-        for a in range(3):
-            tctx.kick(a, a, s.kappa)
-        t0 = time.perf_counter()
-        net, rep = surrogate.train_on_trajectory(tctx, nsteps=SUR_STEPS, iters=SUR_ITERS,
-                                                 batch=8, lr=5e-4)
-        train_s = time.perf_counter() - t0
-        state = os.path.join(tempfile.mkdtemp(), "state.bin")
-        tctx.save(state)
-        tctx.close()
-        p_ms, p_st, _, _, _ = run_path(prec, args.steps, False, state=state)
-        n_ms, n_st, _, _, _ = run_path(prec, args.steps, False, state=state, net=net)
-        surrogate_path = {
-            "value": world * args.steps / (n_ms * 1e-3), "unit": UNIT,
-            "ms_per_step": n_ms / args.steps,
-            "scf_passes_per_replica_step": float(n_st["passes"].sum()) / (3.0 * args.steps),
-            "same_window_without_seed": {
-                "value": world * args.steps / (p_ms * 1e-3), "ms_per_step": p_ms / args.steps,
-                "scf_passes_per_replica_step": float(p_st["passes"].sum()) / (3.0 * args.steps)},
-            "window": f"steps {SUR_STEPS + args.warmup + 1}..{SUR_STEPS + args.warmup + args.steps}"
-                      " after the kicks",
-            "training": {"trajectory_steps": SUR_STEPS, "adam_iterations": SUR_ITERS, "batch": 8,
-                         "lr": 5e-4, "seconds_incl_recording": train_s,
-                         "heldout_seed_rms_ratio": rep["heldout_ratio"],
-                         "samples": rep["train_samples"]}}
+    def measure(name, nsteps, warmup, with_clocks, want_profile=True, want_accuracy=True,
+                want_other=True):
+        s, raw = _system(name)
+        w = WORKLOADS[name]
+        nrep = w["nrep"]
+        kw = dict(nrep=nrep, subspace_scf=w["subspace_scf"], **BENCH_THRESHOLDS)
 
-    # second timed region, host-driven steps with CUDA events around every phase on the
-    # library's stream: the per-kernel durations behind the roofline
-    pctx = rmgtd.Context(s, raw, use_graph=False, precision=prec, **kw)
-    for a in range(3):
-        pctx.kick(a, a, s.kappa)
-    for _ in range(args.warmup):
-        pctx.step(1)
-    p_ms, p_st, _, (phase_ms, phase_calls, _) = timed_steps(pctx, args.steps, profile=True,
-                                                            nvtx_name="rmgtd_host_driven")
-    h_solves, h_iters = pctx.profile_counters()
-    pctx.close()
-    p_rep_passes = int(p_st["passes"].sum())
-    p_terms = int(p_st["terms_sum"].sum())
+        def make(p, graph=True):
+            c = rmgtd.Context(s, raw, use_graph=graph, precision=p, **kw)
+            for r, a in enumerate(w["axes"]):
+                c.kick(r, a, s.kappa)
+            return c
 
-    peaks, peak_kind = _peaks()
+        def timed_steps(ctx, n, profile, tag):
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(n)]
+            if profile:
+                ctx.profile(True)
+            if world > 1:
+                dist.barrier()
+            torch.cuda.synchronize()
+            w0 = time.perf_counter()
+            st = []
+            torch.cuda.nvtx.range_push(tag)
+            for i in range(n):
+                flush.zero_()
+                ev[i][0].record(stream)
+                st.append(ctx.step(1))
+                ev[i][1].record(stream)
+            torch.cuda.nvtx.range_pop()
+            torch.cuda.synchronize()
+            if world > 1:
+                dist.barrier()
+            wall = time.perf_counter() - w0
+            prof = ctx.profile_read() if profile else None
+            return [a.elapsed_time(b) for a, b in ev], np.concatenate(st), wall, prof
+
+        def run_path(p, clocks, state=None, net=None):
+            c = make(p) if state is None else rmgtd.Context(s, raw, use_graph=True, precision=p,
+                                                             **kw)
+            if state is not None:
+                c.load(state)
+            if net is not None:
+                c.attach_net(net)
+            for _ in range(warmup):
+                c.step(1)
+            smp = ClockSampler(local)
+            if clocks:
+                smp.start()
+            ms, stt, wl, prof = timed_steps(c, nsteps, True,
+                                            "rmgtd_timed" if clocks else "rmgtd_other")
+            clk = smp.stop() if clocks else None
+            c.close()
+            tot = max_over_ranks(float(sum(ms)), world)
+            return tot, stt, wl, prof[2], clk
+
+        res = {"s": s, "raw": raw, "make": make, "run_path": run_path, "timed_steps": timed_steps}
+        total_ms, st, wall, launches, clocks = run_path(prec, with_clocks)
+        res.update(total_ms=total_ms, st=st, wall=wall, launches=launches, clocks=clocks,
+                   value=job_throughput(nsteps, world, total_ms),
+                   passes=float(st["passes"].sum()) / (nrep * nsteps),
+                   terms=float(st["terms_sum"].sum()) / max(float(st["passes"].sum()), 1.0))
+        if want_other:
+            o_ms, o_st, _, _, _ = run_path(other, False)
+            res["other_path"] = {"precision": pname[other],
+                                 "value": job_throughput(nsteps, world, o_ms), "unit": UNIT,
+                                 "ms_per_step": o_ms / nsteps,
+                                 "scf_passes_per_replica_step":
+                                     float(o_st["passes"].sum()) / (nrep * nsteps)}
+        if want_accuracy:
+            g = _golden(name)
+            last = g["replicas"][0].get("step", [len(g["replicas"][0]["dipole"]) - 1])[-1]
+            every = 1
+            st_list = g["replicas"][0].get("step")
+            if st_list and len(st_list) > 1:
+                every = st_list[1] - st_list[0]
+            acc = {}
+            for p in (prec, other):
+                c = make(p)
+                d, e, t = trajectory_observables(c, nrep, last, every)
+                c.close()
+                acc[pname[p]] = accuracy_against_oracle(d, e, t, g, last)
+            res["accuracy"] = acc
+        if want_profile:
+            pctx = make(prec, graph=False)
+            for _ in range(warmup):
+                pctx.step(1)
+            p_ms, p_st, _, (phase_ms, phase_calls, _) = timed_steps(pctx, nsteps, True,
+                                                                    "rmgtd_host_driven")
+            h_solves, h_iters = pctx.profile_counters()
+            precond = "dst" if pctx.hartree_preconditioner() == rmgtd.PRECOND_DST else "mg"
+            pctx.close()
+            res.update(phase_ms=phase_ms, phase_calls=phase_calls, p_ms=p_ms, p_st=p_st,
+                       h_solves=h_solves, h_iters=h_iters, precond=precond)
+        return res
+
+    name = args.workload
+    w = WORKLOADS[name]
+    K, W = args.steps, args.warmup
+    m = measure(name, K, W, True)
+    s = m["s"]
     mixed = prec == rmgtd.PREC_MIXED
-    flops = _flops_per_phase(s.N, s.Ng, p_rep_passes, p_terms)
-    dom = max(phase_ms, key=lambda k: phase_ms[k])
-    # the dominant kernel: the Hartree solve is one cooperative launch per DFT evaluation
-    kname = "k_hartree_coop"
-    h_calls = max(phase_calls["hartree"], 1)
-    h_bytes = hartree_bytes(s.n, h_solves, h_iters, mixed) / h_calls
-    h_s = phase_ms["hartree"] / h_calls * 1e-3
-    achieved = h_bytes / h_s / 1e9
-    roof = {"kernel": f"{kname}<{'float' if mixed else 'double'}>", "phase": "hartree",
-            "dominant_phase": dom, "bound": "hbm", "achieved": achieved,
-            "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
-            "traffic": _traffic(kname, "ring64") if mixed else None,
-            "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, mean of the "
-                              "first two launches of the host-driven region (2 CG iterations "
-                              "each; profiles/traffic_k_hartree_coop_ring64.txt)",
-            "algorithmic_bytes_per_launch": h_bytes, "launch_ms": h_s * 1e3,
-            "cg_iterations_per_solve": h_iters / max(h_solves, 1),
-            "peak_source": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
-            "timing": "CUDA events on the library stream around each Hartree launch, "
-                      "host-driven steps over the same workload (second timed region)"}
-    # the other phases: arithmetic against the ALU peak of their precision
-    alu_peak = FP32_PEAK_TFLOPS if mixed else FP64_PEAK_GFLOPS / 1e3
+    peaks, peak_kind = _peaks()
+    rep_passes = int(m["p_st"]["passes"].sum())
+    terms = int(m["p_st"]["terms_sum"].sum())
+    work = _phase_work(s, mixed, rep_passes, terms, m["h_solves"], m["h_iters"], m["precond"])
     phases = {}
-    for ph in ("rho", "hupdate", "eldyn"):
-        if phase_ms.get(ph, 0) > 0:
-            tf = flops[ph] / (phase_ms[ph] * 1e-3) / 1e12
-            pk = FP64_PEAK_GFLOPS / 1e3 if ph == "eldyn" else alu_peak
-            phases[ph] = {"bound": "alu", "achieved": tf, "peak": pk, "unit": "TFLOP/s",
-                          "frac": tf / pk, "ms_per_call": phase_ms[ph] / max(phase_calls[ph], 1)}
-    roof["other_phases"] = phases
-    roof["alu_peak_source"] = ("float32: 152 SMs x 128 lanes x 2 flop x 2.07 GHz = 80.5 TFLOP/s "
-                               "(nominal); float64: 1.25 TFLOP/s (nominal GB300)")
+    for ph in ("rho", "hupdate", "eldyn", "hartree"):
+        if m["phase_ms"].get(ph, 0) > 0:
+            phases[ph] = _roofline_entry(ph, work[ph], m["phase_ms"][ph], m["phase_calls"][ph],
+                                         mixed, peaks, peak_kind)
+            phases[ph]["kernel"] = KERNELS[(ph, mixed)]
+    dom = max(phases, key=lambda k: m["phase_ms"][k])
+    roof = dict(phases[dom])
+    roof["dominant_phase"] = dom
+    roof["traffic"] = _traffic(roof["kernel"], name) if mixed else None
+    roof["traffic_source"] = (f"ncu dram__bytes_read.sum + dram__bytes_write.sum per launch "
+                              f"(profiles/traffic_{roof['kernel']}_{name}.txt), null unless "
+                              "taken on the kernel's current source")
+    roof["timing"] = ("CUDA events on the library stream around each phase, host-driven steps "
+                      "of the same workload (second timed region); a phase includes its small "
+                      "helper launches")
+    if dom == "hartree":
+        roof["cg_iterations_per_solve"] = m["h_iters"] / max(m["h_solves"], 1)
+        roof["preconditioner"] = m["precond"]
+    roof["peak_source"] = f"{peak_kind} MEASURED_PEAKS.json"
+    roof["other_phases"] = {k: v for k, v in phases.items() if k != dom}
 
     result = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "metric": METRIC, "value": m["value"], "unit": UNIT, "n_gpus": world, "steps": K,
+        "warmup": W, "ms_per_step": m["total_ms"] / K, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if prec == rmgtd.PREC_FP64 else "f32+f64",
-        "data": "synthetic", "config": _config(s, args.precision),
-        "grid_point_orbital_updates_per_s": value * s.Ng * s.N * 3,
-        "scf_passes_per_replica_step": rep_passes / (3.0 * args.steps),
-        "commutator_terms_per_expansion": terms_total / max(rep_passes, 1),
-        "other_path": other_path,
-        "surrogate_path": surrogate_path,
-        "phase_ms_per_step_host_driven": {k: v / args.steps for k, v in phase_ms.items()},
-        "ms_per_step_host_driven": float(sum(p_ms)) / args.steps,
-        "gpu_launches": launches, "roofline": roof, "clocks": clocks,
-        "wall_s_timed_region": wall,
+        "dtype": "bf16x3+f32+f64" if mixed else "f64", "data": "synthetic",
+        "config": _config(name, s, args.precision),
+        "grid_point_orbital_updates_per_s": m["value"] * s.Ng * s.N * w["nrep"],
+        "scf_passes_per_replica_step": m["passes"],
+        "commutator_terms_per_expansion": m["terms"],
+        "accuracy": m["accuracy"],
+        "other_path": m["other_path"],
+        "phase_ms_per_step_host_driven": {k: v / K for k, v in m["phase_ms"].items()},
+        "ms_per_step_host_driven": float(sum(m["p_ms"])) / K,
+        "gpu_launches": m["launches"], "roofline": roof, "clocks": m["clocks"],
+        "wall_s_timed_region": m["wall"],
     }
 
-    # end to end through the public API: host orbitals in, dipoles out every step
+    # end to end through the public API: context from host orbitals, kicks, the workload's
+    # trajectory length with every replica's dipole read back after every step
     torch.cuda.synchronize()
+    nsteps_e2e = w["trajectory_steps"]
     t0 = time.perf_counter()
-    c2 = rmgtd.Context(s, raw, use_graph=True, precision=prec, **kw)
-    for a in range(3):
-        c2.kick(a, a, s.kappa)
-    for _ in range(args.steps):
-        c2.step(1)
-        for a in range(3):
-            c2.dipole(a)
+    c2 = m["make"](prec)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    for _ in range(nsteps_e2e):
+        c2.step(1, stats=False)
+        for r in range(w["nrep"]):
+            c2.dipole(r)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     c2.close()
-    h2d = raw.nbytes + s.pos.nbytes * 3
-    result["e2e"] = {"value": world * args.steps / e2e_s, "unit": UNIT,
-                     "h2d_bytes_per_step": h2d / args.steps,
-                     "d2h_bytes_per_step": 3 * 3 * 8 + 3 * 24,
-                     "includes": "context creation from host orbitals (upload, set-up, "
-                                 "initial SCF), 3 kicks, steps, dipole read-back per step"}
+    h2d = m["raw"].nbytes + s.pos.nbytes * 3
+    result["e2e"] = {"value": world * nsteps_e2e / e2e_s, "unit": UNIT,
+                     "h2d_bytes_per_step": h2d / nsteps_e2e,
+                     "d2h_bytes_per_step": 24 * w["nrep"],
+                     "steps": nsteps_e2e, "setup_s": t_setup,
+                     "steady_state_steps_per_s": nsteps_e2e / max(e2e_s - t_setup, 1e-9),
+                     "includes": "context creation from host orbitals (upload, set-up), the "
+                                 "kick(s), the workload's trajectory with the dipole of every "
+                                 "replica read back after every step"}
+
+    # secondary line: the ring workload, with the learned seed's comparison
+    if name == "icosa" and not args.no_ring:
+        r = measure("ring", max(K, 40), W, False, want_profile=False)
+        ring = {"workload": WORKLOADS["ring"]["label"], "value": r["value"], "unit": UNIT,
+                "ms_per_step": r["total_ms"] / max(K, 40), "steps": max(K, 40),
+                "scf_passes_per_replica_step": r["passes"], "other_path": r["other_path"],
+                "accuracy": r["accuracy"],
+                "grid_point_orbital_updates_per_s": r["value"] * r["s"].Ng * r["s"].N * 3}
+        if mixed and not args.no_surrogate:
+            ring["surrogate_path"] = _surrogate_path(rmgtd, r, max(K, 40), world)
+        result["ring_workload"] = ring
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        result["cpu_baseline"] = cpu_baseline_sample()
+        result["cpu_baseline"] = cpu_baseline_sample(name)
     if world > 1:
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(result), flush=True)
     return 0
+
+
+def _surrogate_path(rmgtd, r, nsteps, world):
+    """The mixed path with the learned SCF seed on the ring: a network trained (library
+    kernels only) on the first SUR_STEPS steps of the workload's own trajectory, then the
+    continuation timed with and without it from the same state (a window the network has
+    not seen)."""
+    from paper_2410_09189_gb300 import surrogate
+    tctx = r["make"](rmgtd.PREC_MIXED)
+    t0 = time.perf_counter()
+    net, rep = surrogate.train_on_trajectory(tctx, nsteps=SUR_STEPS, iters=SUR_ITERS, batch=8,
+                                             lr=5e-4)
+    train_s = time.perf_counter() - t0
+    state = os.path.join(tempfile.mkdtemp(), "state.bin")
+    tctx.save(state)
+    tctx.close()
+    p_ms, p_st, _, _, _ = r["run_path"](rmgtd.PREC_MIXED, False, state=state)
+    n_ms, n_st, _, _, _ = r["run_path"](rmgtd.PREC_MIXED, False, state=state, net=net)
+    return {
+        "value": world * nsteps / (n_ms * 1e-3), "unit": UNIT, "ms_per_step": n_ms / nsteps,
+        "scf_passes_per_replica_step": float(n_st["passes"].sum()) / (3.0 * nsteps),
+        "same_window_without_seed": {
+            "value": world * nsteps / (p_ms * 1e-3), "ms_per_step": p_ms / nsteps,
+            "scf_passes_per_replica_step": float(p_st["passes"].sum()) / (3.0 * nsteps)},
+        "window": f"{nsteps} steps after step {SUR_STEPS} (+ warm-up) of the kicked trajectory",
+        "training": {"trajectory_steps": SUR_STEPS, "adam_iterations": SUR_ITERS, "batch": 8,
+                     "lr": 5e-4, "seconds_incl_recording": train_s,
+                     "heldout_seed_rms_ratio": rep["heldout_ratio"],
+                     "samples": rep["train_samples"]}}
 
 
 def run_batch8(args):
@@ -582,11 +795,13 @@ def run_batch8(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="icosa", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ring", action="store_true", help="skip the secondary ring line")
     ap.add_argument("--no-surrogate", action="store_true",
                     help="skip training and timing the learned SCF seed")
     ap.add_argument("--batch8", action="store_true",

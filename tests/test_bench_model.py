@@ -38,3 +38,25 @@ def test_hartree_bytes_multigrid_model():
     per_it = lv[0] * (45 + 17 * 4) + 49 * lv[1] + 8 * lv[tail]
     got = b.hartree_bytes((64, 64, 64), solves=1, iters=2, mixed=True, precond="mg")
     assert got == 2 * per_it + lv[0] * (9 * 4 - 4 * 4)
+
+
+def test_accuracy_against_the_stored_oracle_run():
+    """The bench's per-run errors: dipole error relative to the stored run's own variation
+    (worst replica), energy and trace errors absolute, over the stored steps the GPU run
+    covers (every fifth step here)."""
+    import numpy as np
+    b = _bench()
+    steps = [0, 5, 10, 15]
+    ref_d = [[[0.0, 0.0, 1.0 + 0.1 * k] for k in range(4)], [[0.0, 2.0 * k, 0.0] for k in range(4)]]
+    g = {"options": {"H_thrs": 1e-10, "dP_thrs": 1e-12},
+         "replicas": [{"step": steps, "dipole": ref_d[a], "energy": [-1.0 - a] * 4,
+                       "trace": [2.0] * 4} for a in range(2)]}
+    d = {k: [np.array(ref_d[0][i]) + [0.0, 0.0, 3e-5 if k == 10 else 0.0],
+             np.array(ref_d[1][i])] for i, k in enumerate(steps)}
+    e = {k: [-1.0, -2.0 + (1e-9 if k == 5 else 0.0)] for k in steps}
+    t = {k: [2.0, 2.0 - 1e-12] for k in steps}
+    out = b.accuracy_against_oracle(d, e, t, g, steps_done=10)
+    assert abs(out["dipole_rel_err"] - 3e-5 / 0.3) < 1e-12     # replica 0: variation 0.3
+    assert abs(out["energy_err"] - 1e-9) < 1e-15
+    assert abs(out["trace_err"] - 1e-12) < 1e-15
+    assert out["window"].startswith("steps 0..10")

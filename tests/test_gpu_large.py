@@ -1,0 +1,295 @@
+"""Full-size parity of the CUDA path with the oracle, the orbital-tiled tensor-core
+contractions, the Hartree solve on odd and long axes, and the failure paths.
+
+* Full-size trajectories are compared with stored oracle runs (``tests/golden/*.json``,
+  written by ``tests/golden/make_trajectory_goldens.py`` from ``oracle/`` alone):
+  - the 147-atom icosahedron on its 128^3 grid (N = 148), 64-step window from P_0 = diag(f);
+  - the 12-atom ring on its 64^3 grid (N = 30), three kicks, 2,000 steps from the ground state
+    inside the orbital block.
+  Dipole tolerance (reading of "relative": max_t |d - d_ref| / max_t |d_ref(t) - d_ref(0)|):
+  1e-6 on the float64 path, 1e-4 on the mixed path, the targets the method states for each.
+* The bfloat16 hi/lo split of the orbital-plane contractions keeps each product to about
+  3 * 2^-18 (two operand roundings and the dropped lo * lo term): the density change is
+  bounded at 5e-5 of its own size (a few units of that, summed over orbitals with partial
+  cancellation), far above float32 rounding and far below the 1e-4 dipole target; the
+  Hamiltonian change at 1e-4 of its size, since the float32 Hartree correction (relative
+  residual 3e-6) and the float32 xc increment add their rounding to the split's.
+"""
+import dataclasses
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import hamiltonian as oham, poisson as opoisson, tddft
+from paper_2410_09189_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    from paper_2410_09189_gb300 import rmgtd
+    return rmgtd
+
+
+def _golden(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return json.load(f)
+
+
+def _ring_small(n, h, nvirt):
+    s = inputs.ring(n=32, h=h, nvirt=nvirt)
+    return dataclasses.replace(s, n=tuple(n))
+
+
+# ---- orbital-plane contractions against the oracle ---------------------------------------------
+@pytest.mark.parametrize("case", ["N37-ragged-3rep", "N70-2rep", "N148-3rep"])
+def test_orbital_plane_contractions_match_oracle(lib, case):
+    """rho and H of the mixed path (tensor-core density and Gram through the bfloat16 planes,
+    32 < N <= 256) against the oracle's density and DFT(rho) of the same P, after two kicked
+    steps; ragged grids (partial last tiles and stages), one to three replicas."""
+    import torch
+    rmgtd = lib
+    if case == "N37-ragged-3rep":
+        s, nrep = _ring_small((30, 34, 38), 0.5, 22), 3
+    elif case == "N70-2rep":
+        s, nrep = _ring_small((20, 22, 24), 0.6, 55), 2
+    else:
+        s, nrep = dataclasses.replace(inputs.icosa(), n=(41, 44, 46), h=0.95), 3
+    assert 32 < s.N <= 256
+    raw = inputs.smooth_random_orbitals(s).reshape(s.N, s.Ng)
+    phi = oham.orthonormalize(s, raw)
+    pr = tddft.Propagator(s, phi, tddft.Options(poisson_tol=1e-13))
+    P_ref = np.diag(s.occupations).astype(complex)
+    rho_ref = pr.density(P_ref)
+    H_ref, _ = pr.dft(P_ref)
+    with rmgtd.Context(s, raw, dt=0.02, H_thrs=1e-9, dP_thrs=1e-12, nrep=nrep,
+                       precision=rmgtd.PREC_MIXED) as ctx:
+        for a in range(nrep):
+            ctx.kick(a, a % 3, 1e-2)
+        ctx.step(2)
+        buf = torch.empty(s.Ng, dtype=torch.float64, device="cuda")
+        for a in range(nrep):
+            ctx.field_into(rmgtd.FIELD_RHO, a, buf.data_ptr())
+            rho = buf.cpu().numpy()
+            P = ctx.density_matrix(a)
+            ref = pr.density(P)
+            H, _ = pr.dft(P)
+            Hg = ctx.get_matrix(rmgtd.MAT_H0, a)
+            drho = np.max(np.abs(ref - rho_ref))
+            dH = np.max(np.abs(H - H_ref))
+            assert np.max(np.abs(rho - ref)) <= 5e-5 * drho, (a, np.max(np.abs(rho - ref)) / drho)
+            assert np.max(np.abs(Hg - H)) <= 1e-4 * dH, (a, np.max(np.abs(Hg - H)) / dH)
+
+
+# ---- full-size trajectories against the stored oracle runs -------------------------------------
+def _dipole_error(d, ref):
+    scale = np.max(np.abs(ref - ref[0]))
+    return float(np.max(np.abs(d - ref)) / scale)
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_icosahedron_128_window_matches_oracle(lib, precision):
+    """The 147-atom icosahedron at full size (128^3, N = 148, one z kick) over the stored
+    64-step oracle window: dipole within 1e-6 (float64) / 1e-4 (mixed) of its variation,
+    energy and Tr P."""
+    rmgtd = lib
+    g = _golden("icosa128_window.json")
+    s = inputs.icosa()
+    tr = g["replicas"][0]
+    steps = tr.get("step", list(range(len(tr["dipole"]))))
+    raw = inputs.smooth_random_orbitals(s).reshape(s.N, s.Ng)
+    prec = rmgtd.PREC_FP64 if precision == "fp64" else rmgtd.PREC_MIXED
+    o = g["options"]
+    # the mixed path's SCF floor here is ~1e-9 (float32 Hartree correction and xc increment,
+    # split products of one step's change): it runs at the benchmark threshold
+    H_thrs = o["H_thrs"] if precision == "fp64" else 1e-7
+    with rmgtd.Context(s, raw, dt=s.dt, H_thrs=H_thrs, dP_thrs=o["dP_thrs"],
+                       poisson_tol=o["poisson_tol"], precision=prec, nrep=1) as ctx:
+        ctx.kick(0, 2, s.kappa)
+        d, e, t = [ctx.dipole(0)], [ctx.energy(0)], [np.trace(ctx.get_matrix(rmgtd.MAT_P_RE, 0))]
+        for _ in range(steps[-1]):
+            ctx.step(1)
+            d.append(ctx.dipole(0))
+            e.append(ctx.energy(0))
+            t.append(np.trace(ctx.get_matrix(rmgtd.MAT_P_RE, 0)))
+    d, e, t = np.array(d)[steps], np.array(e)[steps], np.array(t)[steps]
+    ref = np.array(tr["dipole"])
+    err = _dipole_error(d, ref)
+    tol = 1e-6 if precision == "fp64" else 1e-4
+    assert err < tol, err
+    e_ref = np.array(tr["energy"])
+    # energy: float64 path at the SCF threshold; mixed path within 1e-4 of the energy change
+    etol = 1e-8 * np.max(np.abs(e_ref)) if precision == "fp64" else \
+        1e-4 * max(np.max(np.abs(e_ref - e_ref[0])), 1e-6)
+    assert np.max(np.abs(e - e_ref)) < etol, (np.max(np.abs(e - e_ref)), etol)
+    assert np.max(np.abs(t - np.array(tr["trace"]))) < 1e-9
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_ring_64_three_kicks_2000_steps_match_oracle(lib, precision):
+    """The ring workload at full size (64^3, N = 30), started from the ground state inside the
+    orbital block, three kicked replicas, 2,000 steps against the stored oracle run (every
+    fifth step): dipole within 1e-6 / 1e-4 of its variation per replica, energy, Tr P."""
+    rmgtd = lib
+    g = _golden("ring64_three_kicks.json")
+    s = inputs.ring()
+    raw = inputs.smooth_random_orbitals(s).reshape(s.N, s.Ng)
+    o = g["options"]
+    prec = rmgtd.PREC_FP64 if precision == "fp64" else rmgtd.PREC_MIXED
+    H_thrs = o["H_thrs"] if precision == "fp64" else 1e-9
+    steps = g["replicas"][0]["step"]
+    with rmgtd.Context(s, raw, dt=s.dt, H_thrs=H_thrs, dP_thrs=o["dP_thrs"],
+                       poisson_tol=o["poisson_tol"], precision=prec, nrep=3,
+                       subspace_scf=o["subspace_scf"], subspace_mix=o["subspace_mix"],
+                       subspace_tol=o["subspace_tol"]) as ctx:
+        for a in range(3):
+            ctx.kick(a, g["replicas"][a]["axis"], s.kappa)
+        rec = {0: ([ctx.dipole(a) for a in range(3)], [ctx.energy(a) for a in range(3)])}
+        done = 0
+        for k in steps[1:]:
+            ctx.step(k - done)
+            done = k
+            rec[k] = ([ctx.dipole(a) for a in range(3)], [ctx.energy(a) for a in range(3)])
+        tr = [np.trace(ctx.get_matrix(rmgtd.MAT_P_RE, a)) for a in range(3)]
+    tol = 1e-6 if precision == "fp64" else 1e-4
+    for a in range(3):
+        ref = np.array(g["replicas"][a]["dipole"])
+        d = np.array([rec[k][0][a] for k in steps])
+        err = _dipole_error(d, ref)
+        assert err < tol, (a, err)
+        e_ref = np.array(g["replicas"][a]["energy"])
+        e = np.array([rec[k][1][a] for k in steps])
+        etol = 1e-8 * np.max(np.abs(e_ref)) if precision == "fp64" else 1e-6 * np.max(np.abs(e_ref))
+        assert np.max(np.abs(e - e_ref)) < etol, (a, np.max(np.abs(e - e_ref)))
+        assert abs(tr[a] - g["replicas"][a]["trace"][-1]) < 1e-9
+
+
+# ---- Hartree solve on odd and long axes ----------------------------------------------------------
+def _two_gaussians(s, shift=(1.1, -0.4, 0.0)):
+    x, y, z = oham.full_coords(s)
+    return (np.exp(-((x - shift[0]) ** 2 + (y - shift[1]) ** 2 + (z - shift[2]) ** 2) / 2.0)
+            + 0.5 * np.exp(-((x + 2.0) ** 2 + (y - 1.0) ** 2 + (z - 0.7) ** 2) / 1.5))
+
+
+@pytest.mark.parametrize("precond", ["dst", "mg"])
+def test_hartree_odd_axes(lib, precond):
+    """Odd line lengths on every axis (41 x 37 x 43): the folded sine transform's unpaired
+    middle point and odd multigrid levels, against the oracle at 1e-10, with the transform
+    preconditioner's small iteration count."""
+    import torch
+    rmgtd = lib
+    s = _ring_small((41, 37, 43), 0.4, 15)
+    raw = inputs.smooth_random_orbitals(s).reshape(s.N, s.Ng)
+    rho = _two_gaussians(s)
+    ref = opoisson.hartree(s, rho, tol=1e-13)
+    with rmgtd.Context(s, raw, poisson_tol=1e-13) as ctx:
+        if precond == "mg":
+            ctx.set_hartree_preconditioner(rmgtd.PRECOND_MG)
+        rd = torch.from_numpy(rho.ravel()).cuda()
+        vh = torch.zeros_like(rd)
+        n0, i0 = ctx.profile_counters()
+        ctx.hartree(rd, vh)
+        n1, i1 = ctx.profile_counters()
+        err = np.max(np.abs(vh.cpu().numpy() - ref.ravel())) / np.max(np.abs(ref))
+        assert err < 1e-10, err
+        if precond == "dst":
+            assert n1 - n0 == 1 and i1 - i0 <= 14, (n1 - n0, i1 - i0)
+
+
+def test_hartree_multigrid_fallback_on_a_128_point_axis(lib):
+    """A 132-point axis: the sine-transform tables no longer fit in shared memory, so the
+    multigrid V-cycle preconditions the solve (the configuration of the 128^3 workload);
+    against the oracle at 1e-10."""
+    import torch
+    rmgtd = lib
+    s = _ring_small((132, 24, 28), 0.35, 15)
+    raw = inputs.smooth_random_orbitals(s).reshape(s.N, s.Ng)
+    rho = _two_gaussians(s, shift=(4.0, -0.4, 0.3))
+    ref = opoisson.hartree(s, rho, tol=1e-13)
+    with rmgtd.Context(s, raw, poisson_tol=1e-13) as ctx:
+        rd = torch.from_numpy(rho.ravel()).cuda()
+        vh = torch.zeros_like(rd)
+        ctx.hartree(rd, vh)
+        err = np.max(np.abs(vh.cpu().numpy() - ref.ravel())) / np.max(np.abs(ref))
+        assert err < 1e-10, err
+
+
+# ---- failure paths (host-made failures and bounded device waits) ---------------------------------
+def test_poisoned_hamiltonian_reports_divergence_and_keeps_state(lib, small_ground_state):
+    """A NaN written into H_0 from the host: the commutator series sees a non-finite term and
+    the step returns RMGTD_EDIVERGED with the last completed state in place; restoring H_0
+    lets the propagation continue."""
+    rmgtd = lib
+    s, gs = small_ground_state
+    for prec in (rmgtd.PREC_FP64, rmgtd.PREC_MIXED):
+        with rmgtd.Context(s, gs["phi"], orthonormalize=False, precision=prec) as ctx:
+            ctx.kick(0, 2, 1e-2)
+            ctx.step(2)
+            P_before = ctx.density_matrix(0)
+            H0 = ctx.get_matrix(rmgtd.MAT_H0, 0)
+            bad = H0.copy()
+            bad[3, 5] = bad[5, 3] = np.nan
+            ctx.set_matrix(rmgtd.MAT_H0, 0, bad)
+            with pytest.raises(rmgtd.RmgtdError) as ei:
+                ctx.step(1)
+            assert ei.value.code == rmgtd.EDIVERGED
+            assert np.array_equal(ctx.density_matrix(0), P_before)
+            assert ctx.time()[1] == 2
+            ctx.set_matrix(rmgtd.MAT_H0, 0, H0)
+            ctx.step(1)
+            assert ctx.time()[1] == 3
+            assert np.all(np.isfinite(ctx.dipole(0)))
+
+
+def test_unstable_time_step_fails_cleanly(lib, small_ground_state):
+    """dt = 5 a.u., where Section 4.1 reports the propagation unstable: every step either
+    completes with a finite state and Tr P conserved, or returns an error status (series or
+    SCF cap, divergence) with the state before the call kept -- never a silently broken
+    state."""
+    rmgtd = lib
+    s, gs = small_ground_state
+    with rmgtd.Context(s, gs["phi"], orthonormalize=False, dt=5.0, max_scf=50,
+                       max_terms=200) as ctx:
+        ctx.kick(0, 2, 1e-1)
+        ne = 2.0 * s.nocc
+        for _ in range(20):
+            P_before = ctx.density_matrix(0)
+            t_before = ctx.time()
+            try:
+                ctx.step(1)
+            except rmgtd.RmgtdError as e:
+                assert e.code in (rmgtd.ENOTCONVERGED, rmgtd.EDIVERGED), e.code
+                assert np.array_equal(ctx.density_matrix(0), P_before)
+                assert ctx.time() == t_before
+                break
+            P = ctx.density_matrix(0)
+            assert np.all(np.isfinite(P))
+            assert abs(np.trace(P).real - ne) < 1e-9
+
+
+def test_bounded_barrier_wait_times_out(lib, small_ground_state):
+    """A grid barrier that one block never reaches, with the wait limited to a few thousand
+    polls: the waiting blocks give up and report RMGTD_ETIMEOUT; the context is unchanged and
+    still steps."""
+    rmgtd = lib
+    s, gs = small_ground_state
+    with rmgtd.Context(s, gs["phi"], orthonormalize=False) as ctx:
+        ctx.kick(0, 2, 1e-2)
+        ctx.step(1)
+        P_before = ctx.density_matrix(0)
+        assert ctx.selftest_barrier_timeout(5000) == rmgtd.ETIMEOUT
+        assert np.array_equal(ctx.density_matrix(0), P_before)
+        with pytest.raises(rmgtd.RmgtdError):
+            ctx.selftest_barrier_timeout(0)
+        ctx.step(1)
+        assert ctx.time()[1] == 2
