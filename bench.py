@@ -569,12 +569,22 @@ def run_ours(args):
             st_list = g["replicas"][0].get("step")
             if st_list and len(st_list) > 1:
                 every = st_list[1] - st_list[0]
-            acc = {}
+            acc, dip = {}, {}
             for p in (prec, other):
                 c = make(p)
                 d, e, t = trajectory_observables(c, nrep, last, every)
                 c.close()
                 acc[pname[p]] = accuracy_against_oracle(d, e, t, g, last)
+                dip[p] = d
+            # the two GPU paths at the same thresholds: the precision's own share of the error
+            worst = 0.0
+            for a, tr in enumerate(g["replicas"]):
+                ref = np.array(tr["dipole"])
+                scale = np.max(np.abs(ref - ref[0]))
+                diff = max(float(np.max(np.abs(np.array(dip[prec][k][a]) - np.array(dip[other][k][a]))))
+                           for k in dip[prec])
+                worst = max(worst, diff / scale)
+            acc["mixed_vs_fp64_gpu_dipole_rel"] = worst
             res["accuracy"] = acc
         if want_profile:
             pctx = make(prec, graph=False)

@@ -4,8 +4,10 @@
 //
 // Operands: the orbitals are stored once, at set-up, as two bfloat16 planes Phi = hi + lo
 // (hi = Phi rounded to bfloat16, lo = the rest rounded again; |Phi - hi - lo| <= 2^-17 |Phi|),
-// orbital-major [2][Np][Ngp] (Np = N rounded up to 32, Ngp = Ng rounded up to 64, zeros
-// beyond).  Every product a*b is formed on the tensor cores as a_hi b_hi + a_hi b_lo + a_lo b_hi
+// in 64-point blocks [2][nblk][Np][64] (Np = N rounded up to 32, nblk = Ng / 64 rounded up,
+// zeros beyond): every operand box of a TMA copy -- 64 points of 64 orbitals for the density,
+// 64 points of all Np orbitals for the Gram -- is one contiguous run of memory, so the copies
+// read whole DRAM pages instead of 128-byte pieces of rows Ng values apart.  Every product a*b is formed on the tensor cores as a_hi b_hi + a_hi b_lo + a_lo b_hi
 // (kind::f16, bfloat16 inputs, float32 accumulation in tensor memory): about 2^-16 relative
 // per product, with the same four bytes per orbital value as a float32 copy.  All operand
 // tiles arrive by TMA with the 128-byte swizzle; no per-replica padding.
@@ -65,14 +67,15 @@ __device__ __forceinline__ void split2(float x0, float x1, uint32_t& h, uint32_t
 }
 
 // ---- set-up and per-pass operand preparation ------------------------------------------------
-// planes[0][k][g] = hi, planes[1][k][g] = lo of phi_k(g) (zero past N and Ng)
+// planes[0][b][k][q] = hi, planes[1][b][k][q] = lo of phi_k(64 b + q) (zero past N and Ng)
 __global__ void k_split_planes(int N, int Np, long Ng, long Ngp, const double* __restrict__ phi,
                                __nv_bfloat16* __restrict__ planes) {
   const long n = (long)Np * Ngp;
   for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n;
        e += (long)gridDim.x * blockDim.x) {
-    const int k = (int)(e / Ngp);
-    const long g = e - (long)k * Ngp;
+    const long b = e / ((long)Np * kPK);
+    const int k = (int)((e / kPK) % Np);
+    const long g = b * kPK + (e % kPK);
     const double x = (k < N && g < Ng) ? phi[(long)k * Ng + g] : 0.0;
     const __nv_bfloat16 h = __double2bfloat16(x);
     planes[e] = h;
@@ -193,11 +196,13 @@ k_rho_planes(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__ C
           }
           const uint32_t dst = ring + (uint32_t)s * kRdSlotB;
           const uint32_t bar = saddr(&full[s]);
+          const int b0 = x0 / kPK;                    // the tile's two 64-point blocks
           mbar_expect_tx(bar, (uint32_t)kRdSlotB);
-          tma_load_3d(dst, &tm_a, x0, kPK * c, 0, bar);
-          tma_load_3d(dst + kPlaneBox, &tm_a, x0 + kPK, kPK * c, 0, bar);
-          tma_load_3d(dst + 2 * kPlaneBox, &tm_a, x0, kPK * c, 1, bar);
-          tma_load_3d(dst + 3 * kPlaneBox, &tm_a, x0 + kPK, kPK * c, 1, bar);
+          tma_load_4d(dst, &tm_a, 0, kPK * c, b0, 0, bar);
+          tma_load_4d(dst + kPlaneBox, &tm_a, 0, kPK * c, b0 + 1, 0, bar);
+          tma_load_4d(dst + 2 * kPlaneBox, &tm_a, 0, kPK * c, b0, 1, bar);
+          tma_load_4d(dst + 3 * kPlaneBox, &tm_a, 0, kPK * c, b0 + 1, 1, bar);
+
           *reinterpret_cast<volatile int*>(&issued_n) = q + 1;
         }
       }
@@ -254,6 +259,9 @@ k_rho_planes(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__ C
     int q = 0;
     for (int i = 0; i < ntl; ++i) {
       const int b = i & 1;
+      const int g = (cta + i * ncta) * kPM + p;
+      // the anchor's density change at this point, loaded ahead of the chunk loop
+      const float anc = g < Ng ? __ldg(drho_a + (long)rep * Ng + g) : 0.0f;
       float acc = 0.0f;
       bool ok = true;
       for (int c = 0; c < C; ++c, ++q) {
@@ -290,9 +298,8 @@ k_rho_planes(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__ C
       fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&tfree[b]);
-      const int g = (cta + i * ncta) * kPM + p;
       if (g < Ng) {
-        acc += drho_a[(long)rep * Ng + g];   // rho(Sa) - rho_ref
+        acc += anc;   // rho(Sa) - rho_ref
         drho[(long)rep * Ng + g] = acc;
         if (rho) rho[(long)rep * Ng + g] = rho_ref[g] + (double)acc;
         if (mom) {
@@ -348,15 +355,16 @@ k_rho_planes(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__ C
 }
 
 // ---- Gram of the weighted orbitals on the tensor cores ---------------------------------------
-// Roles: warp 0 lane 0 issues one TMA copy per plane and stage (all Np orbital rows of 64
-// points), warp 1 lane 0 issues the MMAs (accumulator of row tile 0: Np columns at 0; of row
+// Roles: warp 0 lane 0 issues one TMA copy per plane and stage (all Np orbital rows of a
+// 64-point block, contiguous) and the bulk copies of the stage's weights, warp 1 lane 0
+// issues the MMAs (accumulator of row tile 0: Np columns at 0; of row
 // tile 1: Np - 128 columns at Np), warps 2..9 convert (thread: one logical 16-byte chunk c of
 // 8 points and rows r, r + 32, ...) and afterwards copy the accumulators to the partials.
 // mbarriers: full[s] (copy landed), conv[s] (A operands of slot s written, 8 warp arrivals),
 // empty[s] (the MMAs of slot s completed), accf (all MMAs completed).
 __global__ void __launch_bounds__(kGpThreads, 1)
 k_gram_planes(const __grid_constant__ CUtensorMap tm_b, const float* __restrict__ w,
-              const float* __restrict__ w_anchor, int N,
+              const float* __restrict__ w_anchor, int wbulk, int N,
               int Np, int Ng, int nrep, int chunk, int stages, float* __restrict__ part,
               const RepCtl* __restrict__ ctl, int* status) {
   extern __shared__ unsigned char smraw[];
@@ -372,7 +380,10 @@ k_gram_planes(const __grid_constant__ CUtensorMap tm_b, const float* __restrict_
   const int g_end = min(Ng, g_beg + chunk);
   const int nst = g_end > g_beg ? (g_end - g_beg + kPK - 1) / kPK : 0;
   const uint32_t bplane = (uint32_t)Np * 128u;         // one plane of a stage
-  const uint32_t slotB = 2u * bplane + (uint32_t)TI * 2u * 16384u;
+  // slot: B hi, B lo, A hi / lo of the row tiles, the stage's weights (64 floats, then the
+  // anchor's 64) in a 1024-byte area
+  const uint32_t wofs = 2u * bplane + (uint32_t)TI * 2u * 16384u;
+  const uint32_t slotB = wofs + 1024u;
   const uint32_t base = (saddr(smraw) + 1023u) & ~1023u;
   unsigned char* const gbase = smraw + (base - saddr(smraw));
   volatile int* abort_v = &abort_flag;
@@ -417,9 +428,18 @@ k_gram_planes(const __grid_constant__ CUtensorMap tm_b, const float* __restrict_
         }
         const uint32_t dst = base + (uint32_t)s * slotB;
         const uint32_t bar = saddr(&full[s]);
-        mbar_expect_tx(bar, 2u * bplane);
-        tma_load_3d(dst, &tm_b, g_beg + kPK * t, 0, 0, bar);
-        tma_load_3d(dst + bplane, &tm_b, g_beg + kPK * t, 0, 1, bar);
+        const int g0 = g_beg + kPK * t;
+        // the weights by bulk copy (rows 16-byte aligned: Ng a multiple of 4); points of the
+        // stage past Ng are not copied and are masked by the converters
+        const uint32_t wb = wbulk ? 4u * (uint32_t)min(kPK, Ng - g0) : 0u;
+        mbar_expect_tx(bar, 2u * bplane + (w_anchor ? 2u : 1u) * wb);
+        tma_load_4d(dst, &tm_b, 0, 0, g0 / kPK, 0, bar);
+        tma_load_4d(dst + bplane, &tm_b, 0, 0, g0 / kPK, 1, bar);
+
+        if (wb) {
+          bulk_g2s_1d(dst + wofs, w + (long)rep * Ng + g0, wb, bar);
+          if (w_anchor) bulk_g2s_1d(dst + wofs + 256u, w_anchor + (long)rep * Ng + g0, wb, bar);
+        }
         *reinterpret_cast<volatile int*>(&issued_n) = t + 1;
       }
     }
@@ -472,11 +492,20 @@ k_gram_planes(const __grid_constant__ CUtensorMap tm_b, const float* __restrict_
         break;
       }
       const int g0 = g_beg + kPK * t + 8 * c;
+      unsigned char* sb = gbase + (size_t)s * slotB;
+      const float* ws = reinterpret_cast<const float*>(sb + wofs) + 8 * c;
       float wv[8];
 #pragma unroll
-      for (int e = 0; e < 8; ++e)
-        wv[e] = (g0 + e < g_end) ? __ldg(wr + g0 + e) - (war ? __ldg(war + g0 + e) : 0.0f) : 0.0f;
-      unsigned char* sb = gbase + (size_t)s * slotB;
+      for (int e = 0; e < 8; ++e) {
+        float v = 0.0f;
+        if (g0 + e < g_end) {
+          if (wbulk)
+            v = war ? ws[e] - ws[64 + e] : ws[e];
+          else
+            v = war ? __ldg(wr + g0 + e) - __ldg(war + g0 + e) : __ldg(wr + g0 + e);
+        }
+        wv[e] = v;
+      }
       for (int I = 0; I < TI; ++I) {
         const int rows = min(kPM, Np - kPM * I);
         for (int r = ct >> 3; r < rows; r += 32) {
@@ -555,6 +584,22 @@ k_gram_planes(const __grid_constant__ CUtensorMap tm_b, const float* __restrict_
 
 namespace {
 
+// 4-D bfloat16 tensor map of the orbital planes [2][nblk][Np][64]: dims {64, Np, nblk, 2},
+// box {box_x, box_y, 1, 1}, the given swizzle, zero fill out of bounds (rows past Np too)
+bool encode_blocked_planes(void* map, const void* base, long Np, long nblk, int box_x,
+                           int box_y, CUtensorMapSwizzle swz) {
+  const EncodeTiledFn f = tensor_map_encoder();
+  if (!f) return false;
+  const cuuint64_t dims[4] = {(cuuint64_t)tc::kPK, (cuuint64_t)Np, (cuuint64_t)nblk, 2};
+  const cuuint64_t strides[3] = {(cuuint64_t)tc::kPK * 2, (cuuint64_t)Np * tc::kPK * 2,
+                                 (cuuint64_t)nblk * Np * tc::kPK * 2};
+  const cuuint32_t box[4] = {(cuuint32_t)box_x, (cuuint32_t)box_y, 1, 1};
+  const cuuint32_t es[4] = {1, 1, 1, 1};
+  return f(reinterpret_cast<CUtensorMap*>(map), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4,
+           const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
+           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // 3-D bfloat16 tensor map: dims {x, y, z} with row stride x_stride elements and plane stride
 // z_stride elements, box {64, box_y, 1}, 128-byte swizzle, zero fill out of bounds
 bool encode_planes(void* map, const void* base, long x, long y, long z, long x_stride,
@@ -578,7 +623,7 @@ size_t rho_planes_smem(int Np, int slots) {
 }
 
 size_t gram_planes_smem(int Np, int stages) {
-  const size_t slot = 2u * (size_t)Np * 128u + (size_t)(Np > tc::kPM ? 2 : 1) * 32768u;
+  const size_t slot = 2u * (size_t)Np * 128u + (size_t)(Np > tc::kPM ? 2 : 1) * 32768u + 1024u;
   return 1024 + (size_t)stages * slot;
 }
 
@@ -607,8 +652,10 @@ int planes_setup(rmgtd_ctx* ctx) {
   k_split_planes<<<blocks, 256, 0, ctx->stream>>>(N, Np, ctx->Ng, Ngp, ctx->phi, ctx->phi_pl);
   ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_split_planes");
-  if (!encode_planes(ctx->tm_pa, ctx->phi_pl, Ngp, Np, 2, Ngp, (long)Np * Ngp, kPK) ||
-      !encode_planes(ctx->tm_pb, ctx->phi_pl, Ngp, Np, 2, Ngp, (long)Np * Ngp, Np) ||
+  if (!encode_blocked_planes(ctx->tm_pa, ctx->phi_pl, Np, Ngp / kPK, kPK, kPK,
+                             CU_TENSOR_MAP_SWIZZLE_128B) ||
+      !encode_blocked_planes(ctx->tm_pb, ctx->phi_pl, Np, Ngp / kPK, kPK, Np,
+                             CU_TENSOR_MAP_SWIZZLE_128B) ||
       !encode_planes(ctx->tm_bt, ctx->bt_pl, Np, Np, 2L * ctx->nrep, Np, (long)Np * Np, 32)) {
     dev_free(ctx, ctx->phi_pl);
     dev_free(ctx, ctx->bt_pl);
@@ -740,7 +787,8 @@ int gram_planes(rmgtd_ctx* ctx, const float* w, const float* w_anchor, int nw, f
   CUtensorMap tb;
   memcpy(&tb, ctx->tm_pb, sizeof(tb));
   k_gram_planes<<<dim3(nsplit, nw), kGpThreads, smem, ctx->stream>>>(
-      tb, w, w_anchor, ctx->N, Np, (int)ctx->Ng, nw, chunk, stages, part, ctl, ctx->status);
+      tb, w, w_anchor, ctx->Ng % 4 == 0 ? 1 : 0, ctx->N, Np, (int)ctx->Ng, nw, chunk, stages,
+      part, ctl, ctx->status);
   ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_gram_planes");
   return RMGTD_OK;

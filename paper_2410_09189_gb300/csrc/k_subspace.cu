@@ -794,10 +794,15 @@ __global__ void __launch_bounds__(NT) k_eldyn(EldynArgs a) {
           const int ra = e / TS, cb = e % TS;
           const double* Hx = (q == 0 || q == 2) ? Hi : Hj;
           const double* Dx = (q == 0) ? Aj : (q == 1) ? Ai : (q == 2) ? Sj : Si;
-          double s = acc[u];
+          // two float64 FMA chains (even and odd kk): the chain latency, not the rate, would
+          // otherwise bound a thread with one output
+          double s0 = acc[u], s1 = 0.0;
 #pragma unroll 8
-          for (int kk = 0; kk < KC; ++kk) s = fma(Hx[ra * (KC + 1) + kk], Dx[kk * TSP + cb], s);
-          acc[u] = s;
+          for (int kk = 0; kk < KC; kk += 2) {
+            s0 = fma(Hx[ra * (KC + 1) + kk], Dx[kk * TSP + cb], s0);
+            s1 = fma(Hx[ra * (KC + 1) + kk + 1], Dx[(kk + 1) * TSP + cb], s1);
+          }
+          acc[u] = s0 + s1;
         }
         __syncthreads();
       }
@@ -1184,10 +1189,25 @@ int eldyn(rmgtd_ctx* ctx, const double* Ha, const double* Hb, long hstride, doub
     if (C == 8) return launch_eldyn_cluster<8>(ctx, a, eldyn_cluster_smem(ctx->N, 8));
     ctx->shat_fresh = 0;
   }
-  if (ctx->N <= 32) return launch_eldyn_ts<4, 64>(ctx, a);
-  if (ctx->N <= 64) return launch_eldyn_ts<8, 256>(ctx, a);
-  if (ctx->N <= 512) return launch_eldyn_ts<16, 256>(ctx, a);
-  return launch_eldyn_ts<32, 256>(ctx, a);
+  // GB300's float64 units (~2 FMA per clock and SM) bound the series: pick the tile size
+  // whose symmetric tile pairs spread the work of a term most evenly over the SMs (the most
+  // loaded SM's share of tile-pair work, items / SMs rounded up times TS^2), small tiles
+  // first on ties; 32-point tiles beyond 512 orbitals
+  if (ctx->N > 512) return launch_eldyn_ts<32, 256>(ctx, a);
+  int best_ts = 16;
+  long best = -1;
+  for (int ts : {4, 8, 16}) {
+    const long T = ceil_div(ctx->N, ts);
+    const long items = T * (T + 1) / 2 * nreps;
+    const long load = ceil_div(items, (long)ctx->num_sms) * ts * ts;
+    if (best < 0 || load < best) {
+      best = load;
+      best_ts = ts;
+    }
+  }
+  if (best_ts == 4) return launch_eldyn_ts<4, 64>(ctx, a);
+  if (best_ts == 8) return launch_eldyn_ts<8, 256>(ctx, a);
+  return launch_eldyn_ts<16, 256>(ctx, a);
 }
 
 // ---------------------------------------------------------------------------------------
