@@ -697,6 +697,7 @@ struct Args {
   // sine-transform preconditioner instead of the V-cycle (dst != 0): S_x, S_y, S_z (row
   // strides rounded up to 4) then lx, ly, lz, in global memory; copied to shared memory
   int dst;
+  int dst_wb;             // lines per batch of a transform pass
   const float* dst_tab;
   int zero_bc;
   V* x;                   // unknown (initial guess in, solution out) [rep][n0]
@@ -743,24 +744,26 @@ struct Args {
 // (dst_astride, dst_arows, dst_mat_floats and dst_wpad, the tables' and tiles' layout, are
 // defined at the top of this file)
 
-// One pass along axis ax over this block's share of the lines (all threads of the block):
-// out(line, j) = sum_k S[j][k] in(line, k); with scale (z axis): forward, times
-// norm / Lambda, inverse.  S: this axis's folded matrices Se, So in shared memory; tA, tB:
-// shared tiles of n x Wp floats (Wp = dst_wpad(the block's line count)); lbase,
-// lxy: shared scratch of one int / float per line.  Flat indices are split into (row,
+// One pass along axis ax over this block's share of the lines (all threads of the block),
+// in batches of at most wb lines: out(line, j) = sum_k S[j][k] in(line, k); with scale
+// (z axis): forward, times norm / Lambda, inverse.  S: this axis's folded matrices Se, So in
+// shared memory; tA, tB: shared tiles of n x Wp floats (Wp = dst_wpad(the batch's line
+// count)); lbase, lxy: shared scratch of one int / float per line of a batch.  Flat indices are split into (row,
 // column) incrementally (no division per element); int offsets (nrep n0 < 2^31).
 template <typename VI, typename VO>
 __device__ void dst_pass(int ax, const VI* __restrict__ in, VO* __restrict__ out, int nrep,
                          int nx, int ny, int nz, const float* S, float* tA, float* tB,
                          int* lbase, float* lxy, bool scale, const float* __restrict__ lam,
-                         float norm) {
+                         float norm, int wb) {
   const int n = ax == 0 ? nx : (ax == 1 ? ny : nz);
   const int n0 = nx * ny * nz, plane = nx * ny;
   const int nlines = nrep * (n0 / n);
-  const int l0 = (int)((long)blockIdx.x * nlines / gridDim.x);
-  const int l1 = (int)((long)(blockIdx.x + 1) * nlines / gridDim.x);
-  const int W = l1 - l0, Wp = dst_wpad(W);
-  if (W == 0) return;   // (uniform over the block)
+  const int lb = (int)((long)blockIdx.x * nlines / gridDim.x);
+  const int le = (int)((long)(blockIdx.x + 1) * nlines / gridDim.x);
+  // the block's lines in batches of at most wb (the tiles hold n x dst_wpad(wb) floats)
+  for (int l0 = lb; l0 < le; l0 += wb) {
+  if (l0 > lb) __syncthreads();   // the previous batch's store has read the tiles
+  const int W = min(wb, le - l0), Wp = dst_wpad(W);
   const int stride = ax == 0 ? 1 : (ax == 1 ? nx : plane);
   const int tot = W * n;
   // first element of each of this block's lines (and, for the scaling, lx[kx] + ly[ky])
@@ -887,6 +890,7 @@ __device__ void dst_pass(int ax, const VI* __restrict__ in, VO* __restrict__ out
     walk(n, [&](int e, int w, int k) { out[l0 * nx + e] = (VO)res[k * Wp + w]; });
   else
     walk(W, [&](int, int k, int w) { out[lbase[w] + k * stride] = (VO)res[k * Wp + w]; });
+  }
 }
 
 __device__ __forceinline__ float wsum(float v) { return warp_sumf(v); }
@@ -1181,40 +1185,30 @@ __global__ void __launch_bounds__(kThreadsC, 1) k_hartree_coop(Args<V> a) {
 
     // ---- sine-transform preconditioner z = M r: five passes, one grid barrier each -------
     if (a.dst) {
-      long tile = 0;
-      for (int ax = 0; ax < 3; ++ax) {
-        const int na = ax == 0 ? nx : (ax == 1 ? ny : nz);
-        const long nlines = (long)nrep * n0 / na;
-        const long wmax = (nlines + G - 1) / G + 15;
-        if ((long)na * wmax > tile) tile = (long)na * wmax;
-      }
+      const int wb = a.dst_wb;
+      const long tile = (long)max(nx, max(ny, nz)) * dst_wpad(wb);
       const float* Sx = smem_tail;
       const float* Sy = Sx + dst_mat_floats(nx);
       const float* Sz = Sy + dst_mat_floats(ny);
       const int off = dst_mat_floats(nx) + dst_mat_floats(ny) + dst_mat_floats(nz);
       float* tA = smem_tail + off;
       float* tB = tA + ((tile + 3) & ~3L);
-      long wmx = 0;
-      for (int ax = 0; ax < 3; ++ax) {
-        const int na = ax == 0 ? nx : (ax == 1 ? ny : nz);
-        const long wm = ((long)nrep * n0 / na + G - 1) / G + 15;
-        if (wm > wmx) wmx = wm;
-      }
+      const long wmx = wb;
       int* lbase = reinterpret_cast<int*>(tB + ((tile + 3) & ~3L));
       float* lxy = reinterpret_cast<float*>(lbase + ((wmx + 3) & ~3L));
       const float* lam = a.dst_tab + off;
       const float norm = (float)(8.0 / ((double)(nx + 1) * (ny + 1) * (nz + 1)));
       float* W1 = T.L[0].x;
       float* W2 = T.L[0].t;
-      dst_pass<V, float>(0, a.r, W1, nrep, nx, ny, nz, Sx, tA, tB, lbase, lxy, false, lam, norm);
+      dst_pass<V, float>(0, a.r, W1, nrep, nx, ny, nz, Sx, tA, tB, lbase, lxy, false, lam, norm, wb);
       COOP_BAR();
-      dst_pass<float, float>(1, W1, W2, nrep, nx, ny, nz, Sy, tA, tB, lbase, lxy, false, lam, norm);
+      dst_pass<float, float>(1, W1, W2, nrep, nx, ny, nz, Sy, tA, tB, lbase, lxy, false, lam, norm, wb);
       COOP_BAR();
-      dst_pass<float, float>(2, W2, W1, nrep, nx, ny, nz, Sz, tA, tB, lbase, lxy, true, lam, norm);
+      dst_pass<float, float>(2, W2, W1, nrep, nx, ny, nz, Sz, tA, tB, lbase, lxy, true, lam, norm, wb);
       COOP_BAR();
-      dst_pass<float, float>(1, W1, W2, nrep, nx, ny, nz, Sy, tA, tB, lbase, lxy, false, lam, norm);
+      dst_pass<float, float>(1, W1, W2, nrep, nx, ny, nz, Sy, tA, tB, lbase, lxy, false, lam, norm, wb);
       COOP_BAR();
-      dst_pass<float, V>(0, W2, a.z, nrep, nx, ny, nz, Sx, tA, tB, lbase, lxy, false, lam, norm);
+      dst_pass<float, V>(0, W2, a.z, nrep, nx, ny, nz, Sx, tA, tB, lbase, lxy, false, lam, norm, wb);
       COOP_BAR();
     } else {
     // ---- V-cycle z = M r: down leg over the multi-block levels --------------------------
@@ -1715,21 +1709,30 @@ __global__ void __launch_bounds__(kThreadsC, 1) k_hartree_coop(Args<V> a) {
 
 }  // namespace coop
 
-// shared memory of the sine-transform preconditioner for a launch of `grid` blocks: the three
-// matrices and two tiles of (n x the largest line count of a block, rounded up to even)
+// shared memory of the sine-transform preconditioner with batches of wb lines: the three
+// matrices, two tiles of n_max x dst_wpad(wb) floats and one int and one float per line
+static size_t dst_smem_batch(const rmgtd_ctx* ctx, int wb) {
+  const int nmax = std::max(ctx->nx, std::max(ctx->ny, ctx->nz));
+  const size_t fl = (size_t)dst_mat_floats(ctx->nx) + dst_mat_floats(ctx->ny) + dst_mat_floats(ctx->nz);
+  const size_t tile = (size_t)nmax * dst_wpad(wb);
+  return sizeof(float) * (fl + 2 * ((tile + 3) & ~(size_t)3) + 2 * (((size_t)wb + 3) & ~(size_t)3));
+}
+
+// lines per batch of a transform pass for a launch of `grid` blocks: every line of a block
+// at once when that fits in kDstSmemMax, else the largest batch (at least 8 lines) that does;
+// 0 when not even that fits
+static int dst_batch_lines(const rmgtd_ctx* ctx, int nrep, int grid) {
+  long wmax = 0;
+  for (int n : {ctx->nx, ctx->ny, ctx->nz})
+    wmax = std::max(wmax, ((long)nrep * ctx->Ng / n + grid - 1) / grid);
+  int wb = (int)std::max(1L, wmax);
+  while (wb > 8 && dst_smem_batch(ctx, wb) > kDstSmemMax) wb = std::max(8, wb * 3 / 4);
+  return dst_smem_batch(ctx, wb) <= kDstSmemMax ? wb : 0;
+}
+
 static size_t dst_smem_bytes(const rmgtd_ctx* ctx, int nrep, int grid) {
-  const int dims[3] = {ctx->nx, ctx->ny, ctx->nz};
-  size_t fl = 0, tile = 0, wmx = 0;
-  for (int ax = 0; ax < 3; ++ax) {
-    const size_t n = dims[ax];
-    fl += (size_t)dst_mat_floats(dims[ax]);
-    const size_t nlines = (size_t)nrep * ctx->Ng / n;
-    const size_t wmax = (nlines + grid - 1) / grid + 15;   // >= dst_wpad(lines of a block)
-    tile = std::max(tile, n * wmax);
-    wmx = std::max(wmx, wmax);
-  }
-  // + per-line scratch (one int and one float per line)
-  return sizeof(float) * (fl + 2 * ((tile + 3) & ~(size_t)3) + 2 * ((wmx + 3) & ~(size_t)3));
+  const int wb = dst_batch_lines(ctx, nrep, grid);
+  return wb > 0 ? dst_smem_batch(ctx, wb) : (size_t)-1;
 }
 
 // the preconditioner a solve of all replicas uses (RMGTD_PRECOND_DST when requested and its
@@ -1771,6 +1774,7 @@ int hartree_coop(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* ct
     a.cinv = ctx->mg_cinv;
     a.cinv_smem = ctx->mg_cinv_smem;
     a.dst = use_dst;
+    a.dst_wb = use_dst ? dst_batch_lines(ctx, nrep, grid) : 0;
     a.dst_tab = ctx->dst_tab;
     a.zero_bc = zero_bc;
     a.part = ctx->red_part;

@@ -207,10 +207,11 @@ def test_hartree_odd_axes(lib, precond):
             assert n1 - n0 == 1 and i1 - i0 <= 14, (n1 - n0, i1 - i0)
 
 
-def test_hartree_multigrid_fallback_on_a_128_point_axis(lib):
-    """A 132-point axis: the sine-transform tables no longer fit in shared memory, so the
-    multigrid V-cycle preconditions the solve (the configuration of the 128^3 workload);
-    against the oracle at 1e-10."""
+@pytest.mark.parametrize("precond", ["dst", "mg"])
+def test_hartree_on_a_132_point_axis(lib, precond):
+    """A 132-point axis (longer than the 128-point lines of the icosahedron workload): the
+    sine-transform passes take the block's lines in batches so the tables and tiles fit in
+    shared memory; the multigrid V-cycle on request.  Both against the oracle at 1e-10."""
     import torch
     rmgtd = lib
     s = _ring_small((132, 24, 28), 0.35, 15)
@@ -218,11 +219,39 @@ def test_hartree_multigrid_fallback_on_a_128_point_axis(lib):
     rho = _two_gaussians(s, shift=(4.0, -0.4, 0.3))
     ref = opoisson.hartree(s, rho, tol=1e-13)
     with rmgtd.Context(s, raw, poisson_tol=1e-13) as ctx:
+        if precond == "mg":
+            ctx.set_hartree_preconditioner(rmgtd.PRECOND_MG)
+        want = rmgtd.PRECOND_DST if precond == "dst" else rmgtd.PRECOND_MG
+        assert ctx.hartree_preconditioner() == want
         rd = torch.from_numpy(rho.ravel()).cuda()
         vh = torch.zeros_like(rd)
         ctx.hartree(rd, vh)
         err = np.max(np.abs(vh.cpu().numpy() - ref.ravel())) / np.max(np.abs(ref))
         assert err < 1e-10, err
+
+
+def test_hartree_transform_batches_on_the_128_cube(lib):
+    """The 128^3 grid with one replica: 108 lines per block at most, taken in batches by the
+    sine-transform passes; the solve (mixed context, float32 correction solve inside the
+    step; float64 here) against the oracle at 1e-10, with few CG iterations."""
+    import torch
+    rmgtd = lib
+    s = dataclasses.replace(inputs.icosa(), nocc=2, nvirt=2)
+    raw = inputs.smooth_random_orbitals(s).reshape(s.N, s.Ng)
+    x, y, z = oham.full_coords(s)
+    rho = (np.exp(-((x - 3.1) ** 2 + (y + 1.4) ** 2 + z ** 2) / 8.0)
+           + 0.5 * np.exp(-((x + 6.0) ** 2 + (y - 2.0) ** 2 + (z - 1.7) ** 2) / 5.0))
+    ref = opoisson.hartree(s, rho, tol=1e-13)
+    with rmgtd.Context(s, raw, poisson_tol=1e-13) as ctx:
+        assert ctx.hartree_preconditioner() == rmgtd.PRECOND_DST
+        rd = torch.from_numpy(rho.ravel()).cuda()
+        vh = torch.zeros_like(rd)
+        n0, i0 = ctx.profile_counters()
+        ctx.hartree(rd, vh)
+        n1, i1 = ctx.profile_counters()
+        err = np.max(np.abs(vh.cpu().numpy() - ref.ravel())) / np.max(np.abs(ref))
+        assert err < 1e-10, err
+        assert n1 - n0 == 1 and i1 - i0 <= 16, (n1 - n0, i1 - i0)
 
 
 # ---- failure paths (host-made failures and bounded device waits) ---------------------------------
