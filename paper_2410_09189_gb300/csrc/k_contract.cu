@@ -50,9 +50,35 @@ constexpr int kPlaneBox = kPK * kPK * 2; // one 64 x 64 bf16 box (8 KB)
 constexpr int kRdSlotB = 4 * kPlaneBox;  // density chunk: hi box0, hi box1, lo box0, lo box1
 constexpr int kRdMaxSlots = 4;
 constexpr int kRdThreads = 6 * 32;       // TMA producer, MMA issuer, 4 epilogue warps
-constexpr int kGpThreads = 10 * 32;      // TMA producer, MMA issuer, 8 converter/epilogue warps
-constexpr int kGpMaxStages = 4;
+constexpr int kGConvWarps = 16;          // converter / epilogue warps of the Gram
+constexpr int kGpThreads = (2 + kGConvWarps) * 32;   // + TMA producer and MMA issuer
+constexpr int kGpMaxStages = 6;   // raw slots of the Gram's copy ring
 constexpr int kSmemLimit = 226 * 1024;   // dynamic part (static barriers take the rest)
+
+__device__ __forceinline__ uint4 lds_u4(uint32_t a) {
+  uint4 v;
+  asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "r"(a));
+  return v;
+}
+__device__ __forceinline__ float4 lds_f4(uint32_t a) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "r"(a));
+  return v;
+}
+__device__ __forceinline__ float lds_f(uint32_t a) {
+  float v;
+  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ void sts_u4(uint32_t a, uint4 v) {
+  asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(v.x), "r"(v.y), "r"(v.z),
+               "r"(v.w)
+               : "memory");
+}
 
 __device__ __forceinline__ float bf_lo(uint32_t v) { return __uint_as_float(v << 16); }
 __device__ __forceinline__ float bf_hi(uint32_t v) { return __uint_as_float(v & 0xFFFF0000u); }
@@ -355,21 +381,36 @@ k_rho_planes(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__ C
 }
 
 // ---- Gram of the weighted orbitals on the tensor cores ---------------------------------------
-// Roles: warp 0 lane 0 issues one TMA copy per plane and stage (all Np orbital rows of a
-// 64-point block, contiguous) and the bulk copies of the stage's weights, warp 1 lane 0
-// issues the MMAs (accumulator of row tile 0: Np columns at 0; of row
-// tile 1: Np - 128 columns at Np), warps 2..9 convert (thread: one logical 16-byte chunk c of
-// 8 points and rows r, r + 32, ...) and afterwards copy the accumulators to the partials.
-// mbarriers: full[s] (copy landed), conv[s] (A operands of slot s written, 8 warp arrivals),
-// empty[s] (the MMAs of slot s completed), accf (all MMAs completed).
+// Per replica and grid chunk (split-K), 64-point stages:
+//   D_I[i][j] = sum_g (w(g) phi_i(g)) phi_j(g)    (row tile I = 0, 1 of 128 orbitals; j >= 128 I)
+// A = w * (hi + lo) of the tile's rows, rounded again into bfloat16 hi / lo by the converter
+// warps into one of two operand sets; B = the raw orbital rows 128 I .. Np of the stage (both
+// planes, straight from the TMA copy).  Row tile 1 holds Np - 128 rows: its MMAs read 128
+// rows from the start of its buffers, and the rows past Np-128 (whatever shared memory follows)
+// only reach accumulator rows that are never stored.
+// Roles: warp 0 lane 0 issues the copies into a ring of `slots` raw slots (both planes of a
+// 64-point block, contiguous, and the stage's weights by bulk copy), warp 1 lane 0 the MMAs
+// (accumulator of row tile 0: Np columns at 0; of row tile 1: Np - 128 at Np), the 16 warps
+// from 2 on convert (thread: one 16-byte chunk of 8 points in rows r, r + 64, ...) and
+// afterwards copy the accumulators to the partials.  mbarriers: full[s] (copies of raw slot s
+// landed), rfree[s] (the MMAs reading raw slot s completed), conv[a] (operand set a written,
+// one arrival per converter warp), afree[a] (the MMAs reading operand set a completed), accf (all MMAs completed).
+// A stage's raw slot is released as soon as its MMAs complete, so `slots` copies stay in flight
+// while the converters fill the other operand set.  Every wait is bounded; a time-out raises
+// the abort flag and the CTA drains its copies and MMAs before it frees tensor memory.
+__host__ __device__ constexpr uint32_t gram_aset_bytes(int Np) {
+  return 32768u + (Np > kPM ? 2u * (uint32_t)(Np - kPM) * 128u : 0u);
+}
+__host__ __device__ constexpr uint32_t gram_raw_bytes(int Np) { return 2u * (uint32_t)Np * 128u + 1024u; }
+
 __global__ void __launch_bounds__(kGpThreads, 1)
 k_gram_planes(const __grid_constant__ CUtensorMap tm_b, const float* __restrict__ w,
-              const float* __restrict__ w_anchor, int wbulk, int N,
-              int Np, int Ng, int nrep, int chunk, int stages, float* __restrict__ part,
-              const RepCtl* __restrict__ ctl, int* status) {
+              const float* __restrict__ w_anchor, int wbulk, int N, int Np, int Ng, int nrep,
+              int chunk, int slots, float* __restrict__ part, const RepCtl* __restrict__ ctl,
+              int* status) {
   extern __shared__ unsigned char smraw[];
-  __shared__ __align__(8) uint64_t full[kGpMaxStages], conv[kGpMaxStages], empty[kGpMaxStages];
-  __shared__ __align__(8) uint64_t accf;
+  __shared__ __align__(8) uint64_t full[kGpMaxStages], rfree[kGpMaxStages];
+  __shared__ __align__(8) uint64_t conv[2], afree[2], accf;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag, issued_n, committed_n;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -379,13 +420,15 @@ k_gram_planes(const __grid_constant__ CUtensorMap tm_b, const float* __restrict_
   const int g_beg = split * chunk;
   const int g_end = min(Ng, g_beg + chunk);
   const int nst = g_end > g_beg ? (g_end - g_beg + kPK - 1) / kPK : 0;
-  const uint32_t bplane = (uint32_t)Np * 128u;         // one plane of a stage
-  // slot: B hi, B lo, A hi / lo of the row tiles, the stage's weights (64 floats, then the
-  // anchor's 64) in a 1024-byte area
-  const uint32_t wofs = 2u * bplane + (uint32_t)TI * 2u * 16384u;
-  const uint32_t slotB = wofs + 1024u;
+  const uint32_t bplane = (uint32_t)Np * 128u;          // one raw plane of a stage
+  const uint32_t asetB = gram_aset_bytes(Np);
+  const uint32_t a1ofs = 32768u, a1pl = (uint32_t)max(0, Np - kPM) * 128u;
+  const uint32_t rawB = gram_raw_bytes(Np), wofs = 2u * bplane;
+  // shared memory: operand sets 0, 1, then the raw ring (row tile 1's 128-row reads past its
+  // buffers stay inside the allocation)
   const uint32_t base = (saddr(smraw) + 1023u) & ~1023u;
   unsigned char* const gbase = smraw + (base - saddr(smraw));
+  const uint32_t ring = base + 2u * asetB;
   volatile int* abort_v = &abort_flag;
 
   if (warp == 1) tmem_alloc(&tmem_base, 512);
@@ -393,26 +436,17 @@ k_gram_planes(const __grid_constant__ CUtensorMap tm_b, const float* __restrict_
     abort_flag = 0;
     issued_n = 0;
     committed_n = 0;
-    for (int s = 0; s < stages; ++s) {
+    for (int s = 0; s < slots; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&conv[s], 8);
-      mbar_init(&empty[s], 1);
+      mbar_init(&rfree[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&conv[a], kGConvWarps);
+      mbar_init(&afree[a], 1);
     }
     mbar_init(&accf, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  // rows of row tile 1 past Np stay zero in every slot's A operands
-  if (TI == 2 && Np < 2 * kPM) {
-    const int r0 = Np - kPM;
-    for (int s = 0; s < stages; ++s) {
-      uint4* a1 = reinterpret_cast<uint4*>(gbase + (size_t)s * slotB + 2 * bplane + 2 * 16384);
-      for (int e = tid; e < 2 * (kPM - r0) * 8; e += blockDim.x) {
-        const int pl = e / ((kPM - r0) * 8), rr = e % ((kPM - r0) * 8);
-        a1[pl * 1024 + r0 * 8 + rr] = make_uint4(0u, 0u, 0u, 0u);
-      }
-    }
-  }
-  fence_async_smem();
   fence_before();
   __syncthreads();
   fence_after();
@@ -421,12 +455,12 @@ k_gram_planes(const __grid_constant__ CUtensorMap tm_b, const float* __restrict_
   if (warp == 0) {
     if (lane == 0) {
       for (int t = 0; t < nst && !*abort_v; ++t) {
-        const int s = t % stages;
-        if (t >= stages && !mbar_wait(&empty[s], (uint32_t)(t / stages - 1) & 1u)) {
+        const int s = t % slots;
+        if (t >= slots && !mbar_wait(&rfree[s], (uint32_t)(t / slots - 1) & 1u)) {
           *abort_v = 1;
           break;
         }
-        const uint32_t dst = base + (uint32_t)s * slotB;
+        const uint32_t dst = ring + (uint32_t)s * rawB;
         const uint32_t bar = saddr(&full[s]);
         const int g0 = g_beg + kPK * t;
         // the weights by bulk copy (rows 16-byte aligned: Ng a multiple of 4); points of the
@@ -435,7 +469,6 @@ k_gram_planes(const __grid_constant__ CUtensorMap tm_b, const float* __restrict_
         mbar_expect_tx(bar, 2u * bplane + (w_anchor ? 2u : 1u) * wb);
         tma_load_4d(dst, &tm_b, 0, 0, g0 / kPK, 0, bar);
         tma_load_4d(dst + bplane, &tm_b, 0, 0, g0 / kPK, 1, bar);
-
         if (wb) {
           bulk_g2s_1d(dst + wofs, w + (long)rep * Ng + g0, wb, bar);
           if (w_anchor) bulk_g2s_1d(dst + wofs + 256u, w_anchor + (long)rep * Ng + g0, wb, bar);
@@ -448,20 +481,20 @@ k_gram_planes(const __grid_constant__ CUtensorMap tm_b, const float* __restrict_
     if (lane == 0) {
       bool ok = true;
       for (int t = 0; t < nst; ++t) {
-        const int s = t % stages;
-        if (!mbar_wait(&conv[s], (uint32_t)(t / stages) & 1u) || *abort_v) {
+        const int s = t % slots, a = t & 1;
+        if (!mbar_wait(&conv[a], (uint32_t)(t >> 1) & 1u) || *abort_v) {
           *abort_v = 1;
           ok = false;
           break;
         }
         fence_after();
-        const uint32_t sb = base + (uint32_t)s * slotB;
+        const uint32_t ab = base + (uint32_t)a * asetB, rb = ring + (uint32_t)s * rawB;
         for (int I = 0; I < TI; ++I) {
           const int nI = Np - kPM * I;
           const uint32_t idesc = idesc_bf16_major(kPM, nI, 0, 0);
           const uint32_t d = tbase + (uint32_t)(I ? Np : 0);
-          const uint32_t a_hi = sb + 2 * bplane + (uint32_t)I * 32768u, a_lo = a_hi + 16384u;
-          const uint32_t b_hi = sb + (uint32_t)(kPM * I) * 128u, b_lo = b_hi + bplane;
+          const uint32_t a_hi = ab + (I ? a1ofs : 0u), a_lo = a_hi + (I ? a1pl : 16384u);
+          const uint32_t b_hi = rb + (uint32_t)(kPM * I) * 128u, b_lo = b_hi + bplane;
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk) {
             const uint64_t ah = sdesc_sw128(a_hi + kk * 32, 16, 1024);
@@ -473,63 +506,85 @@ k_gram_planes(const __grid_constant__ CUtensorMap tm_b, const float* __restrict_
             mma_bf16(d, al, bh, idesc, 1u);
           }
         }
-        mma_commit(&empty[s]);
+        mma_commit(&rfree[s]);
+        mma_commit(&afree[a]);
         *reinterpret_cast<volatile int*>(&committed_n) = t + 1;
       }
       if (ok && nst > 0) mma_commit(&accf);
     }
     __syncwarp();
   } else {
-    // ---- converters: w * (hi + lo) -> A hi / lo of row tiles 0 and 1 -------------------------
-    const int ct = tid - 64;                 // 0 .. 255
-    const int c = ct & 7;                    // logical 16-byte chunk: points 8 c .. 8 c + 7
+    // ---- converters: A = w * (hi + lo) of rows 0 .. Np-1 into operand set t & 1 ---------------
+    // thread: logical 16-byte chunk c (points 8 c .. 8 c + 7) of rows r0, r0 + 64, ...; rows
+    // 64 apart share the swizzle phase, so every offset is a per-thread constant plus 8 KB steps
+    const int ct = tid - 64;                 // 0 .. 32 kGConvWarps - 1
+    const int c = ct & 7, r0 = ct >> 3;
+    constexpr int kRowStep = 4 * kGConvWarps;  // 64 rows per pass
+    static_assert(kRowStep % 8 == 0, "rows of a thread must share the swizzle phase");
+    const uint32_t sw = (uint32_t)((c ^ (r0 & 7)) << 4);
+    const int nrow = r0 < Np ? (Np - 1 - r0) / kRowStep + 1 : 0;   // <= 4 (Np <= 256)
     const float* wr = w + (long)rep * Ng;
     const float* war = w_anchor ? w_anchor + (long)rep * Ng : nullptr;
     for (int t = 0; t < nst; ++t) {
-      const int s = t % stages;
-      if (!mbar_wait(&full[s], (uint32_t)(t / stages) & 1u) || *abort_v) {
+      const int s = t % slots, a = t & 1;
+      bool ok = mbar_wait(&full[s], (uint32_t)(t / slots) & 1u);
+      if (ok && t >= 2) ok = mbar_wait(&afree[a], (uint32_t)((t >> 1) - 1) & 1u);
+      if (!ok || *abort_v) {
         *abort_v = 1;
         break;
       }
       const int g0 = g_beg + kPK * t + 8 * c;
-      unsigned char* sb = gbase + (size_t)s * slotB;
-      const float* ws = reinterpret_cast<const float*>(sb + wofs) + 8 * c;
+      const uint32_t rs = ring + (uint32_t)s * rawB;    // shared addresses
+      const uint32_t as = base + (uint32_t)a * asetB;
       float wv[8];
-#pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        float v = 0.0f;
-        if (g0 + e < g_end) {
-          if (wbulk)
-            v = war ? ws[e] - ws[64 + e] : ws[e];
-          else
-            v = war ? __ldg(wr + g0 + e) - __ldg(war + g0 + e) : __ldg(wr + g0 + e);
+      if (wbulk && g0 + 8 <= g_end) {
+        const float4 w0 = lds_f4(rs + wofs + 32u * c), w1 = lds_f4(rs + wofs + 32u * c + 16u);
+        wv[0] = w0.x; wv[1] = w0.y; wv[2] = w0.z; wv[3] = w0.w;
+        wv[4] = w1.x; wv[5] = w1.y; wv[6] = w1.z; wv[7] = w1.w;
+        if (war) {
+          const float4 v0 = lds_f4(rs + wofs + 256u + 32u * c), v1 = lds_f4(rs + wofs + 272u + 32u * c);
+          wv[0] -= v0.x; wv[1] -= v0.y; wv[2] -= v0.z; wv[3] -= v0.w;
+          wv[4] -= v1.x; wv[5] -= v1.y; wv[6] -= v1.z; wv[7] -= v1.w;
         }
-        wv[e] = v;
+      } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          float v = 0.0f;
+          if (g0 + e < g_end) {
+            if (wbulk)
+              v = war ? lds_f(rs + wofs + 4u * (8 * c + e)) - lds_f(rs + wofs + 256u + 4u * (8 * c + e))
+                      : lds_f(rs + wofs + 4u * (8 * c + e));
+            else
+              v = war ? __ldg(wr + g0 + e) - __ldg(war + g0 + e) : __ldg(wr + g0 + e);
+          }
+          wv[e] = v;
+        }
       }
-      for (int I = 0; I < TI; ++I) {
-        const int rows = min(kPM, Np - kPM * I);
-        for (int r = ct >> 3; r < rows; r += 32) {
-          const int R = kPM * I + r;
-          const int off = R * 128 + ((c ^ (R & 7)) << 4);
-          const uint4 h4 = *reinterpret_cast<const uint4*>(sb + off);
-          const uint4 l4 = *reinterpret_cast<const uint4*>(sb + bplane + off);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (k < nrow) {
+          const int R = r0 + kRowStep * k;
+          const uint32_t off = (uint32_t)R * 128u + sw;
+          const uint4 h4 = lds_u4(rs + off);
+          const uint4 l4 = lds_u4(rs + bplane + off);
           const uint32_t hv[4] = {h4.x, h4.y, h4.z, h4.w}, lv[4] = {l4.x, l4.y, l4.z, l4.w};
           uint32_t oh[4], ol[4];
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
-            const float x0 = (bf_lo(hv[u]) + bf_lo(lv[u])) * wv[2 * u];
-            const float x1 = (bf_hi(hv[u]) + bf_hi(lv[u])) * wv[2 * u + 1];
+            const float x0 = fmaf(bf_lo(hv[u]), wv[2 * u], bf_lo(lv[u]) * wv[2 * u]);
+            const float x1 = fmaf(bf_hi(hv[u]), wv[2 * u + 1], bf_hi(lv[u]) * wv[2 * u + 1]);
             split2(x0, x1, oh[u], ol[u]);
           }
-          const int aoff = r * 128 + ((c ^ (r & 7)) << 4);   // R = r (mod 8)
-          unsigned char* ab = sb + 2 * bplane + I * 32768;
-          *reinterpret_cast<uint4*>(ab + aoff) = make_uint4(oh[0], oh[1], oh[2], oh[3]);
-          *reinterpret_cast<uint4*>(ab + 16384 + aoff) = make_uint4(ol[0], ol[1], ol[2], ol[3]);
+          // row R of tile R / 128 at the same swizzled position (128 I is a multiple of 8)
+          const uint32_t ah = R < kPM ? as + off : as + a1ofs + off - (uint32_t)kPM * 128u;
+          const uint32_t al = ah + (R < kPM ? 16384u : a1pl);
+          sts_u4(ah, make_uint4(oh[0], oh[1], oh[2], oh[3]));
+          sts_u4(al, make_uint4(ol[0], ol[1], ol[2], ol[3]));
         }
       }
       fence_async_smem();
       __syncwarp();
-      if (lane == 0) mbar_arrive(&conv[s]);
+      if (lane == 0) mbar_arrive(&conv[a]);
     }
     // ---- epilogue: accumulators -> partials (rows of the upper block triangle) ---------------
     bool ok = !*abort_v;
@@ -537,13 +592,14 @@ k_gram_planes(const __grid_constant__ CUtensorMap tm_b, const float* __restrict_
     ok = __all_sync(0xffffffffu, ok);   // tcgen05.ld below is warp-collective
     if (!ok) *abort_v = 1;
     fence_after();
-    const int wq = warp & 3, half = (warp - 2) >> 2;
+    // warps sharing a TMEM lane quadrant (warp mod 4) split the 32-column groups
+    const int wq = warp & 3, grp = (warp - 2) >> 2;
     if (ok) {
       for (int I = 0; I < TI; ++I) {
         const int row = kPM * I + 32 * wq + lane;
         const int nI = Np - kPM * I;
         float* prow = part + ((long)(split * nrep + rep) * Np + row) * Np + kPM * I;
-        for (int m = half; m < nI / 32; m += 2) {
+        for (int m = grp; m < nI / 32; m += kGConvWarps / 4) {
           float y[32];
           if (nst > 0) {
             tmem_ld32(tbase + ((uint32_t)(wq * 32) << 16) + (uint32_t)((I ? Np : 0) + 32 * m), y);
@@ -565,11 +621,11 @@ k_gram_planes(const __grid_constant__ CUtensorMap tm_b, const float* __restrict_
   if (*abort_v && tid == 0) {
     atomicCAS(status, 0, (int)RMGTD_ETIMEOUT);
     const int ni = *reinterpret_cast<volatile int*>(&issued_n);
-    for (int u = max(0, ni - stages); u < ni; ++u)
-      mbar_wait(&full[u % stages], (uint32_t)(u / stages) & 1u);
+    for (int u = max(0, ni - slots); u < ni; ++u)
+      mbar_wait(&full[u % slots], (uint32_t)(u / slots) & 1u);
     // the last commit covers every MMA issued before it
     const int nc = *reinterpret_cast<volatile int*>(&committed_n);
-    if (nc > 0) mbar_wait(&empty[(nc - 1) % stages], (uint32_t)((nc - 1) / stages) & 1u);
+    if (nc > 0) mbar_wait(&rfree[(nc - 1) % slots], (uint32_t)((nc - 1) / slots) & 1u);
   }
   (void)N;
   fence_before();
@@ -622,9 +678,8 @@ size_t rho_planes_smem(int Np, int slots) {
   return 1024 + b + (size_t)slots * tc::kRdSlotB;
 }
 
-size_t gram_planes_smem(int Np, int stages) {
-  const size_t slot = 2u * (size_t)Np * 128u + (size_t)(Np > tc::kPM ? 2 : 1) * 32768u + 1024u;
-  return 1024 + (size_t)stages * slot;
+size_t gram_planes_smem(int Np, int slots) {
+  return 1024 + 2 * (size_t)tc::gram_aset_bytes(Np) + (size_t)slots * tc::gram_raw_bytes(Np);
 }
 
 }  // namespace
