@@ -98,6 +98,10 @@ typedef struct {
   const double* phi0;      /* [N][Ng] starting orbitals (orbital-major), required */
   double v_ext_omega;      /* > 0 adds the harmonic well 0.5 w^2 r^2 (test mode) */
   int hartree_xc;          /* 1: V_eff includes V_H + V_xc; 0: independent electrons */
+  const double* rho_core;  /* [Ng] frozen core density (may be NULL): added to rho in the
+                              exchange-correlation only (V_xc and eps_xc of rho + rho_core,
+                              E_xc = h^3 sum (rho + rho_core) eps_xc), not in the Hartree
+                              potential, the dipole or Tr P */
 } rmgtd_system;
 
 typedef struct {
@@ -169,6 +173,18 @@ void rmgtd_destroy(rmgtd_ctx* ctx);
  * (rmgtd_dtype), must not overlap.  Errors: RMGTD_EINVAL. */
 int rmgtd_apply_h(rmgtd_ctx* ctx, const void* x_dev, void* hx_dev, int ncols, int dtype,
                   int rep);
+
+/* Time-dependent external field E(t) of replica `rep` (Algorithm 1: the external potential
+ * enters Omega through V_{j-1} + V_j, its values at both ends of the step).  Samples
+ * E_xyz[j][q] = E_q(j dt), q = x, y, z (host, nsamp x 3 doubles, atomic units), with j
+ * counted in completed steps of the context (t = j dt); E = 0 past the last sample.  A step
+ * then propagates with Omega = -i dt (Hbar + sum_q ebar_q M_q), ebar = (E(t_j) + E(t_j + dt))/2:
+ * the sign of the kick, so a field kappa delta(t) along q is the kick along q.  nsamp = 0
+ * clears the replica's field.  rmgtd_energy reports the energy without the field's
+ * interaction term.  The samples are copied and are not part of a checkpoint.  Errors:
+ * RMGTD_EINVAL (replica, count, NULL or non-finite samples), RMGTD_ENOMEM, RMGTD_ESTATE (the
+ * context belongs to a batch). */
+int rmgtd_set_field(rmgtd_ctx* ctx, int rep, const double* E_xyz, int nsamp);
 
 /* Delta kick of replica `rep` along axis q (0 = x, 1 = y, 2 = z):
  * P <- exp(-i kappa M_q) P exp(i kappa M_q) by the commutator expansion (Eq. 34 with a

@@ -21,12 +21,20 @@ the overlap is the identity and the orthogonal commutator expansion applies (Sec
   Reading of the loop order: the paper computes H_err before the update and never defines
   H_1^old on the first pass; here H_err compares the Hamiltonian the propagation used with
   the one its density produces, and a pass is one DFT evaluation.
+* Time-dependent external field E(t) (optional): the external potential enters Omega through
+  V_{j-1} + V_j, its values at both ends of the step (Algorithm 1's Omega assignment), i.e.
+  Omega = -i dt ((H_0 + H_1)/2 + sum_q (E_q(t_j) + E_q(t_j + dt))/2 M_q); a field
+  kappa delta(t) along q is the kick along q.
 * rho(P)(r) = sum_ij Re(P)_ij phi_i(r) phi_j(r) (the density of P = sum f |psi><psi|; the
   imaginary part of a Hermitian P cancels).
 * DFT(rho): Hartree by ``poisson.hartree``, LDA by ``lda.lda``, then
   H = h^3 Phi (H[rho] Phi^T) with the *full* grid Hamiltonian applied to every orbital.
 * Observables: electronic dipole d_q = Tr(Re(P) M_q) (line 27 without mu_0), and
   E = Tr(Re(P) H_core) + 1/2 h^3 sum rho V_H + h^3 sum rho eps_xc + E_ion.
+* Frozen core density rho_core (optional, ``sys.rho_core``; Section 3.1's frozen semicore
+  electrons): a fixed density added to rho in the exchange-correlation only, V_xc and eps_xc
+  of rho + rho_core and E_xc = h^3 sum (rho + rho_core) eps_xc; the Hartree potential, the
+  dipole and Tr P see rho alone.
 
 Pinned by: the two-level closed form of the kicked harmonic oscillator, the spectral
 propagator W exp(omega) W^dagger (Section 2.2), Tr(P) conservation, energy conservation,
@@ -91,8 +99,9 @@ def spectral_propagate(P0: np.ndarray, Hbar: np.ndarray, tau: float) -> np.ndarr
 class Propagator:
     """Algorithm 1 in a fixed orthonormal basis ``phi`` of shape (N, Ng)."""
 
-    def __init__(self, sys, phi: np.ndarray, opts: Optional[Options] = None):
+    def __init__(self, sys, phi: np.ndarray, opts: Optional[Options] = None, field=None):
         self.sys = sys
+        self.field = field      # None or t -> (E_x, E_y, E_z)
         self.opts = opts or Options()
         self.phi = np.ascontiguousarray(phi, dtype=np.float64)
         self.h3 = sys.h ** 3
@@ -105,6 +114,8 @@ class Propagator:
                   for q in ham.full_coords(sys)]
         self.E_ion = ham.ion_energy(sys)
         self.vh = None
+        core = getattr(sys, "rho_core", None)
+        self.rho_core = np.zeros(sys.Ng) if core is None else np.asarray(core, float).ravel()
 
     @staticmethod
     def _sym(A):
@@ -122,7 +133,7 @@ class Propagator:
             vh = hartree(self.sys, rho.reshape(self.shape), tol=self.opts.poisson_tol,
                          x0=self.vh).ravel()
             self.vh = vh
-            vxc, exc = lda(rho)
+            vxc, exc = lda(rho + self.rho_core)   # the frozen core enters the xc only
         else:
             vh = np.zeros_like(rho)
             vxc = np.zeros_like(rho)
@@ -149,7 +160,7 @@ class Propagator:
     def energy(self, P, aux) -> float:
         e = float(np.trace(np.real(P) @ self.Hcore))
         e += 0.5 * self.h3 * float(np.dot(aux["rho"], aux["vh"]))
-        e += self.h3 * float(np.dot(aux["rho"], aux["exc"]))
+        e += self.h3 * float(np.dot(aux["rho"] + self.rho_core, aux["exc"]))
         return e + self.E_ion
 
     # --- driver ----------------------------------------------------------------------
@@ -184,13 +195,22 @@ class Propagator:
             H0, aux = self.dft(P0)
         return {"P0": P0, "H0": H0, "Hm1": H0.copy(), "aux": aux, "t": 0.0, "j": 0}
 
+    def field_term(self, t: float) -> np.ndarray:
+        """sum_q (E_q(t) + E_q(t + dt))/2 M_q for the step starting at t (zero without a field)."""
+        if self.field is None:
+            return np.zeros_like(self.Hcore)
+        e = 0.5 * (np.asarray(self.field(t), dtype=float)
+                   + np.asarray(self.field(t + self.opts.dt), dtype=float))
+        return sum(e[q] * self.M[q] for q in range(3))
+
     def step(self, st):
         o = self.opts
         P0, H0, Hm1 = st["P0"], st["H0"], st["Hm1"]
         H1 = 2.0 * H0 - Hm1
+        V = self.field_term(st["t"])
         terms = []
         for npass in range(1, o.max_scf + 1):
-            P1, k = self.expand(P0, 0.5 * (H0 + H1), o.dt)
+            P1, k = self.expand(P0, 0.5 * (H0 + H1) + V, o.dt)
             terms.append(k)
             Hnew, aux = self.dft(P1)
             err = float(np.max(np.abs(Hnew - H1)))
@@ -206,9 +226,11 @@ class Propagator:
 
 
 def run(sys, phi, opts: Optional[Options] = None, nsteps: int = 10, axis: int = 2,
-        kappa: Optional[float] = None, subspace_scf: int = 0, subspace_mix: float = 0.3):
-    """Kick along `axis` and propagate; returns per-step dipole, energy, trace, stats."""
-    pr = Propagator(sys, phi, opts)
+        kappa: Optional[float] = None, subspace_scf: int = 0, subspace_mix: float = 0.3,
+        field=None):
+    """Kick along `axis` and propagate (in the external field `field(t)` if given); returns
+    per-step dipole, energy, trace, stats."""
+    pr = Propagator(sys, phi, opts, field=field)
     st = pr.initial_state(subspace_scf, subspace_mix)
     kap = sys.kappa if kappa is None else kappa
     out = {"dipole_gs": pr.dipole(st["P0"]), "energy_gs": pr.energy(st["P0"], st["aux"])}

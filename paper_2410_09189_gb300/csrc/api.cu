@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <initializer_list>
 #include <string>
 
@@ -424,6 +425,10 @@ static int create_impl(const rmgtd_system* sys, const rmgtd_options* opt, rmgtd_
   ctx->failed = (int*)A(sizeof(int));
   ctx->kexec = (unsigned long long*)A(4 * sizeof(unsigned long long));
   ctx->done_steps = (int*)A(sizeof(int));
+  ctx->step_dev = (long long*)A(sizeof(long long));
+  ctx->fld_ebar = (double*)A(sizeof(double) * 3 * nrep);
+  ctx->fld_nsamp = (int*)A(sizeof(int) * nrep);
+  ctx->fld_host.assign(nrep, std::vector<double>());
   ctx->stats_cap = 256;
   ctx->stats_dev = (RepCtl*)A(sizeof(RepCtl) * ctx->stats_cap * nrep);
   {
@@ -441,6 +446,9 @@ static int create_impl(const rmgtd_system* sys, const rmgtd_options* opt, rmgtd_
   RMGTD_CUDA(ctx, cudaMallocHost((void**)&ctx->obs_host, sizeof(double) * 8 * nrep));
   RMGTD_CUDA(ctx, cudaMallocHost((void**)&ctx->stats_host, sizeof(RepCtl) * ctx->stats_cap * nrep));
   RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->failed, 0, sizeof(int), ctx->stream));
+  RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->step_dev, 0, sizeof(long long), ctx->stream));
+  RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->fld_ebar, 0, sizeof(double) * 3 * nrep, ctx->stream));
+  RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->fld_nsamp, 0, sizeof(int) * nrep, ctx->stream));
   RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->kexec, 0, 4 * sizeof(unsigned long long), ctx->stream));
   RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream));
   RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->vh, 0, gsz * nrep, ctx->stream));
@@ -460,6 +468,12 @@ static int create_impl(const rmgtd_system* sys, const rmgtd_options* opt, rmgtd_
     RMGTD_CUDA(ctx, cudaMemcpyAsync(pos_d, sys->pos, sizeof(double) * 3 * na, cudaMemcpyHostToDevice, ctx->stream));
     RMGTD_CUDA(ctx, cudaMemcpyAsync(Z_d, sys->Z, sizeof(double) * na, cudaMemcpyHostToDevice, ctx->stream));
     RMGTD_CUDA(ctx, cudaMemcpyAsync(rc_d, sys->rc_loc, sizeof(double) * na, cudaMemcpyHostToDevice, ctx->stream));
+  }
+  if (sys->rho_core) {   // frozen core density: xc only
+    ctx->rho_core = (double*)A(gsz);
+    if (!ctx->rho_core) return set_error(ctx, RMGTD_ENOMEM, "core density");
+    RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->rho_core, sys->rho_core, gsz, cudaMemcpyHostToDevice,
+                                    ctx->stream));
   }
   int rc = launch_vion(ctx, pos_d, Z_d, rc_d, na);
   if (rc) return rc;
@@ -602,7 +616,15 @@ static int create_impl(const rmgtd_system* sys, const rmgtd_options* opt, rmgtd_
     RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->Sref, ctx->S0, msz, cudaMemcpyDeviceToDevice, ctx->stream));
     RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->Href, ctx->H0, msz, cudaMemcpyDeviceToDevice, ctx->stream));
     RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->rho_ref, ctx->rho, gsz, cudaMemcpyDeviceToDevice, ctx->stream));
-    rc = to_float(ctx, ctx->rho, ctx->rho_ref32, Ng);
+    // base of the xc increment: rho_ref, plus the frozen core when there is one
+    ctx->rho_xc_ref = ctx->rho_ref;
+    if (ctx->rho_core) {
+      ctx->rho_xc_ref = (double*)A(gsz);
+      if (!ctx->rho_xc_ref) return set_error(ctx, RMGTD_ENOMEM, "xc reference density");
+      rc = add_fields(ctx, ctx->rho_ref, ctx->rho_core, ctx->rho_xc_ref, Ng);
+      if (rc) return rc;
+    }
+    rc = to_float(ctx, ctx->rho_xc_ref, ctx->rho_ref32, Ng);
     if (rc) return rc;
     RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->vh_ref, ctx->vh, gsz, cudaMemcpyDeviceToDevice, ctx->stream));
     RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->vref, ctx->vhxc, gsz, cudaMemcpyDeviceToDevice, ctx->stream));
@@ -690,7 +712,8 @@ static int enqueue_pass(rmgtd_ctx* ctx, cudaGraphConditionalHandle cond, int use
   const long NN = (long)ctx->N * ctx->N;
   ph_begin(ctx, PH_ELDYN);
   int rc = eldyn(ctx, ctx->H0, ctx->H1, NN, ctx->opt.dt, ctx->S0, ctx->A0, ctx->S1, ctx->A1,
-                 ctx->ctl, ctx->ctl, 0, ctx->nrep, ctx->mixed ? ctx->shat32 : nullptr);
+                 ctx->ctl, ctx->ctl, 0, ctx->nrep, ctx->mixed ? ctx->shat32 : nullptr,
+                 ctx->fld_on ? ctx->fld_ebar : nullptr);
   ph_end(ctx);
   if (rc) return rc;
   rc = dft_eval(ctx, ctx->S1, ctx->ctl, ctx->errbits);
@@ -716,6 +739,7 @@ static int capture_step(rmgtd_ctx* ctx, cudaStream_t main) {
   // H_1 extrapolation, control reset and the Hartree guess in one launch; the learned seed
   // (which changes H_1 only) after it
   int rc = step_begin_extrapolate(ctx);
+  if (!rc) rc = field_begin(ctx);
   if (!rc && ctx->net) rc = net_predict(ctx);
   cudaGraphConditionalHandle hs = 0;
   cudaGraph_t body = nullptr;
@@ -769,6 +793,7 @@ static int eager_step(rmgtd_ctx* ctx) {
   // H_1 extrapolation, control reset and the Hartree guess in one launch; the learned seed
   // (which changes H_1 only) after it
   int rc = step_begin_extrapolate(ctx);
+  if (!rc) rc = field_begin(ctx);
   if (!rc && ctx->net) rc = net_predict(ctx);
   if (rc) return rc;
   for (int pass = 0; pass < ctx->opt.max_scf; ++pass) {
@@ -1356,7 +1381,7 @@ int rmgtd_xc(rmgtd_ctx* ctx, const double* rho_dev, double* vxc_dev, double* exc
   if (!ctx) return set_error(nullptr, RMGTD_EINVAL, "ctx is NULL");
   if (!rho_dev || !vxc_dev || n == 0) return set_error(ctx, RMGTD_EINVAL, "xc: bad arguments");
   int rc = launch_lda(ctx, rho_dev, nullptr, 0, vxc_dev, exc_dev, nullptr, nullptr, (long)n, nullptr,
-                      1, (long)n, 1);
+                      1, (long)n, 1, false);
   if (rc) return rc;
   RMGTD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   return RMGTD_OK;
@@ -1370,6 +1395,55 @@ int rmgtd_xc_increment(rmgtd_ctx* ctx, const double* rho0_dev, const float* drho
   int rc = launch_xc_increment(ctx, rho0_dev, drho_dev, dvxc_dev, (long)n);
   if (rc) return rc;
   RMGTD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return RMGTD_OK;
+}
+
+int rmgtd_set_field(rmgtd_ctx* ctx, int rep, const double* E_xyz, int nsamp) {
+  if (!ctx) return set_error(nullptr, RMGTD_EINVAL, "ctx is NULL");
+  if (rep < 0 || rep >= ctx->nrep || nsamp < 0 || (nsamp > 0 && !E_xyz))
+    return set_error(ctx, RMGTD_EINVAL, "set_field: bad replica, count or NULL samples");
+  if (ctx->in_batch) return set_error(ctx, RMGTD_ESTATE, "set_field: context belongs to a batch");
+  for (int i = 0; i < 3 * nsamp; ++i)
+    if (!std::isfinite(E_xyz[i])) return set_error(ctx, RMGTD_EINVAL, "set_field: non-finite sample");
+  ctx->fld_host[rep].assign(E_xyz, E_xyz + 3 * (size_t)nsamp);
+  int cap = 0, on = 0;
+  for (const auto& v : ctx->fld_host) {
+    cap = std::max(cap, (int)(v.size() / 3));
+    on |= !v.empty();
+  }
+  RMGTD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  const bool regrow = cap > ctx->fld_cap;   // the captured kernels hold the old buffer and pitch
+  if (regrow) {
+    dev_free(ctx, ctx->fld_samples);
+    ctx->fld_samples = (double*)dev_alloc(ctx, sizeof(double) * 3 * (size_t)cap * ctx->nrep);
+    if (!ctx->fld_samples) {
+      ctx->fld_cap = 0;
+      ctx->fld_on = 0;
+      return set_error(ctx, RMGTD_ENOMEM, "set_field: samples");
+    }
+    ctx->fld_cap = cap;
+  }
+  std::vector<int> ns(ctx->nrep);
+  if (ctx->fld_cap > 0) {
+    std::vector<double> all(3 * (size_t)ctx->fld_cap * ctx->nrep, 0.0);
+    for (int r = 0; r < ctx->nrep; ++r) {
+      std::copy(ctx->fld_host[r].begin(), ctx->fld_host[r].end(),
+                all.begin() + 3 * (size_t)ctx->fld_cap * r);
+      ns[r] = (int)(ctx->fld_host[r].size() / 3);
+    }
+    RMGTD_CUDA(ctx, cudaMemcpy(ctx->fld_samples, all.data(), sizeof(double) * all.size(),
+                               cudaMemcpyHostToDevice));
+  }
+  RMGTD_CUDA(ctx, cudaMemcpy(ctx->fld_nsamp, ns.data(), sizeof(int) * ctx->nrep,
+                             cudaMemcpyHostToDevice));
+  if (on != ctx->fld_on || regrow) {   // the step graph holds the field's kernels or not,
+                                       // or their old buffer: rebuild it
+    if (ctx->step_exec) cudaGraphExecDestroy(ctx->step_exec);
+    if (ctx->step_graph) cudaGraphDestroy(ctx->step_graph);
+    ctx->step_exec = nullptr;
+    ctx->step_graph = nullptr;
+  }
+  ctx->fld_on = on;
   return RMGTD_OK;
 }
 
@@ -1529,6 +1603,10 @@ int rmgtd_load(rmgtd_ctx* ctx, const char* path) {
   RMGTD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   ctx->t = t;
   ctx->steps = hdr[5];
+  {
+    const long long sd = ctx->steps;
+    RMGTD_CUDA(ctx, cudaMemcpy(ctx->step_dev, &sd, sizeof(long long), cudaMemcpyHostToDevice));
+  }
   // observables need rho / eps_xc of the restored P; V_H is restored exactly (warm start)
   int rc = rho_dev(ctx, ctx->S0, ctx->rho, nullptr, ctx->nrep);
   if (rc) return rc;

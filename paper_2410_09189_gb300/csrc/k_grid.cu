@@ -381,7 +381,7 @@ int launch_xc_mixed(rmgtd_ctx* ctx, const RepCtl* ctl, int nrep) {
   const long n = ctx->Ng;
   const int blocks = (int)std::min<long>(ceil_div(n, kThreads), 4L * ctx->num_sms);
   k_xc_mixed<<<dim3(std::max(blocks, 1), nrep), kThreads, 0, ctx->stream>>>(
-      ctx->rho_ref, ctx->rho_ref32, ctx->drho32, ctx->dvh32, ctx->dv32, n, ctl, n,
+      ctx->rho_xc_ref, ctx->rho_ref32, ctx->drho32, ctx->dvh32, ctx->dv32, n, ctl, n,
       ctx->hartree_xc, ctx->hartree_xc);
   ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_xc_mixed");
@@ -423,14 +423,14 @@ __global__ void k_lda(const double* __restrict__ rho, double* __restrict__ vh, i
                       double* __restrict__ vxc, double* __restrict__ exc,
                       double* __restrict__ vhxc, const double* __restrict__ vref,
                       float* __restrict__ dv32, long n, const RepCtl* __restrict__ ctl,
-                      long stride, int with_xc) {
+                      long stride, int with_xc, const double* __restrict__ rho_core) {
   const int rep = blockIdx.y;
   if (ctl && !ctl[rep].active) return;
   const long o = rep * stride;
   for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < n;
        g += (long)gridDim.x * blockDim.x) {
     double v = 0.0, e = 0.0;
-    if (with_xc) lda_point(rho[o + g], v, e);
+    if (with_xc) lda_point(rho[o + g] + (rho_core ? rho_core[g] : 0.0), v, e);
     vxc[o + g] = v;
     if (exc) exc[o + g] = e;
     double vhv = 0.0;
@@ -450,11 +450,11 @@ __global__ void k_lda(const double* __restrict__ rho, double* __restrict__ vh, i
 
 int launch_lda(rmgtd_ctx* ctx, const double* rho, double* vh, int vh_mode, double* vxc,
                double* exc, double* vhxc, float* dv32, long n, const RepCtl* ctl, int nrep,
-               long stride, int with_xc) {
+               long stride, int with_xc, bool with_core) {
   const int blocks = (int)std::min<long>(ceil_div(n, kThreads), 4L * ctx->num_sms);
   k_lda<<<dim3(std::max(blocks, 1), nrep), kThreads, 0, ctx->stream>>>(
       rho, vh, vh_mode, ctx->vh_ref, ctx->dvh32, vxc, exc, vhxc, ctx->vref, dv32, n, ctl, stride,
-      with_xc);
+      with_xc, with_core ? ctx->rho_core : nullptr);
   ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_lda");
   return RMGTD_OK;

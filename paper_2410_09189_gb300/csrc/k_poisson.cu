@@ -1786,7 +1786,7 @@ int hartree_coop(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* ct
     a.counters = ctx->tune_x ? nullptr : ctx->kexec + 2;
     // quads of the float path (16-byte aligned rows); 2: also warp-uniform replicas
     a.vec4 = (ctx->nx % 4 == 0) ? (((long)ctx->Ng % 128 == 0) ? 2 : 1) : 0;
-    a.rho0 = ctx->rho_ref;
+    a.rho0 = ctx->rho_xc_ref;    // rho_ref (+ the frozen core): the xc increment's base
     a.rho0f = ctx->rho_ref32;
     a.dv_out = nullptr;
     a.mom = nullptr;

@@ -638,6 +638,21 @@ int tile_orbitals(rmgtd_ctx* ctx) {
   return RMGTD_OK;
 }
 
+__global__ void k_add_fields(long n, const double* __restrict__ a, const double* __restrict__ b,
+                             double* __restrict__ out) {
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n;
+       e += (long)gridDim.x * blockDim.x)
+    out[e] = a[e] + b[e];
+}
+
+int add_fields(rmgtd_ctx* ctx, const double* a, const double* b, double* out, long n) {
+  const int blocks = (int)std::max<long>(1, std::min<long>(ceil_div(n, 256), 8L * ctx->num_sms));
+  k_add_fields<<<blocks, 256, 0, ctx->stream>>>(n, a, b, out);
+  ++ctx->launches;
+  RMGTD_LAUNCH(ctx, "k_add_fields");
+  return RMGTD_OK;
+}
+
 int to_float(rmgtd_ctx* ctx, const double* in, float* out, long n) {
   const int blocks = (int)std::max<long>(1, std::min<long>(ceil_div(n, 256), 8L * ctx->num_sms));
   k_to_float<<<blocks, 256, 0, ctx->stream>>>(n, in, out);
@@ -681,7 +696,19 @@ struct EldynArgs {
   float* shat;
   const double* Sref;
   int Np;
+  // external field of the step (NULL: none): Hbar += sum_q ebar[rep][q] M_q, ebar the mean of
+  // E(t_j) and E(t_j + dt) (Algorithm 1's V_{j-1} + V_j in Omega)
+  const double* fM;       // [3][N*N] dipole matrices
+  const double* febar;    // [rep][3]
 };
+
+// the field's contribution to Hbar at element o of replica rep (0 without a field)
+__device__ __forceinline__ double field_term(const EldynArgs& a, int rep, long o) {
+  if (!a.febar) return 0.0;
+  const long NN = (long)a.N * a.N;
+  const double* e = a.febar + 3 * rep;
+  return e[0] * a.fM[o] + e[1] * a.fM[NN + o] + e[2] * a.fM[2 * NN + o];
+}
 
 template <int TS, int NT>
 __global__ void __launch_bounds__(NT) k_eldyn(EldynArgs a) {
@@ -760,8 +787,12 @@ __global__ void __launch_bounds__(NT) k_eldyn(EldynArgs a) {
           const int ri = I * TS + r, rj = J * TS + r;
           double hi = 0.0, hj = 0.0;
           if (kg < N) {
-            if (ri < N) hi = 0.5 * (Ha[(long)ri * N + kg] + Hb[(long)ri * N + kg]);
-            if (rj < N) hj = 0.5 * (Ha[(long)rj * N + kg] + Hb[(long)rj * N + kg]);
+            if (ri < N)
+              hi = 0.5 * (Ha[(long)ri * N + kg] + Hb[(long)ri * N + kg]) +
+                   field_term(a, a.rep0 + rep, (long)ri * N + kg);
+            if (rj < N)
+              hj = 0.5 * (Ha[(long)rj * N + kg] + Hb[(long)rj * N + kg]) +
+                   field_term(a, a.rep0 + rep, (long)rj * N + kg);
           }
           Hi[r * (KC + 1) + kk] = hi;
           Hj[r * (KC + 1) + kk] = hj;
@@ -961,7 +992,7 @@ __global__ void __launch_bounds__(256, 1) k_eldyn_cluster(EldynArgs a) {
   }
   for (int e = tid; e < nr * N; e += nt) {
     const long o = (long)r0 * N + e;
-    Hr[e] = 0.5 * (Ha[o] + Hb[o]);
+    Hr[e] = 0.5 * (Ha[o] + Hb[o]) + field_term(a, a.rep0 + rep, o);
     S1r[e] = S0[o];
     A1r[e] = A0[o];
   }
@@ -1151,9 +1182,11 @@ static int eldyn_cluster_size(rmgtd_ctx* ctx) {
 
 int eldyn(rmgtd_ctx* ctx, const double* Ha, const double* Hb, long hstride, double tau,
           const double* S0, const double* A0, double* S1, double* A1, const RepCtl* ctl_in,
-          RepCtl* ctl_out, int rep0, int nreps, float* shat_out) {
+          RepCtl* ctl_out, int rep0, int nreps, float* shat_out, const double* febar) {
   if (nreps > 32) return set_error(ctx, RMGTD_EINVAL, "at most 32 replicas per expansion");
   EldynArgs a;
+  a.fM = ctx->M;
+  a.febar = febar;
   a.N = ctx->N;
   a.nrep = nreps;
   a.rep0 = rep0;
@@ -1280,7 +1313,7 @@ __global__ void k_step_end(long n, double* __restrict__ Hm1, double* __restrict_
                            double* __restrict__ A0, const double* __restrict__ S1,
                            const double* __restrict__ A1, const RepCtl* __restrict__ ctl, int nrep,
                            int* failed, int* done_steps, RepCtl* stats, int stats_cap,
-                           const int* __restrict__ status) {
+                           const int* __restrict__ status, long long* step_dev) {
   if (*failed) return;
   int ok = (*status == 0);
   for (int r = 0; r < nrep; ++r) ok &= (ctl[r].status == 0);
@@ -1297,10 +1330,12 @@ __global__ void k_step_end(long n, double* __restrict__ Hm1, double* __restrict_
     const int k = *done_steps;
     if (k < stats_cap)
       for (int r = 0; r < nrep; ++r) stats[(long)k * nrep + r] = ctl[r];
-    if (ok)
+    if (ok) {
       *done_steps = k + 1;
-    else
+      ++*step_dev;   // completed steps of the context (the field's sample index)
+    } else {
       *failed = 1;
+    }
   }
 }
 
@@ -1325,12 +1360,36 @@ int scf_control(rmgtd_ctx* ctx, const unsigned long long* errbits,
   return RMGTD_OK;
 }
 
+// ebar[r] = (E_r(t_k) + E_r(t_k + dt)) / 2 for the step that starts after k completed steps
+// (samples E_r(j dt), j < nsamp[r]; zero past them)
+__global__ void k_field_ebar(int nrep, int cap, const double* __restrict__ samples,
+                             const int* __restrict__ nsamp, const long long* __restrict__ step_dev,
+                             double* __restrict__ ebar) {
+  const int t = threadIdx.x;
+  if (t >= 3 * nrep) return;
+  const int r = t / 3, q = t % 3;
+  const long long k = *step_dev;
+  const double* E = samples + (long)r * cap * 3;
+  const double e0 = k < nsamp[r] ? E[3 * k + q] : 0.0;
+  const double e1 = k + 1 < nsamp[r] ? E[3 * (k + 1) + q] : 0.0;
+  ebar[t] = 0.5 * (e0 + e1);
+}
+
+int field_begin(rmgtd_ctx* ctx) {
+  if (!ctx->fld_on) return RMGTD_OK;
+  k_field_ebar<<<1, 96, 0, ctx->stream>>>(ctx->nrep, ctx->fld_cap, ctx->fld_samples,
+                                           ctx->fld_nsamp, ctx->step_dev, ctx->fld_ebar);
+  ++ctx->launches;
+  RMGTD_LAUNCH(ctx, "k_field_ebar");
+  return RMGTD_OK;
+}
+
 int step_end(rmgtd_ctx* ctx) {
   const long n = (long)ctx->nrep * ctx->N * ctx->N;
   const int blocks = (int)std::min<long>(ceil_div(n, 256), 2L * ctx->num_sms);
   k_step_end<<<std::max(blocks, 1), 256, 0, ctx->stream>>>(
       n, ctx->Hm1, ctx->H0, ctx->H1, ctx->S0, ctx->A0, ctx->S1, ctx->A1, ctx->ctl, ctx->nrep,
-      ctx->failed, ctx->done_steps, ctx->stats_dev, ctx->stats_cap, ctx->status);
+      ctx->failed, ctx->done_steps, ctx->stats_dev, ctx->stats_cap, ctx->status, ctx->step_dev);
   ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_step_end");
   return planes_anchor_update(ctx);
@@ -1344,7 +1403,8 @@ constexpr int kObs = 7;
 __global__ void k_obs_partial(int N, long Ng, const double* __restrict__ S,
                               const double* __restrict__ M, const double* __restrict__ Hc,
                               const double* __restrict__ rho, const double* __restrict__ vh,
-                              const double* __restrict__ exc, double* __restrict__ part) {
+                              const double* __restrict__ exc, const double* __restrict__ rho_core,
+                              double* __restrict__ part) {
   const int rep = blockIdx.y;
   const long NN = (long)N * N;
   const double* Sr = S + rep * NN;
@@ -1365,7 +1425,7 @@ __global__ void k_obs_partial(int N, long Ng, const double* __restrict__ S,
   for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < Ng; g += stride) {
     const double r = rr[g];
     q[5] += r * vr[g];
-    q[6] += r * er[g];
+    q[6] += (rho_core ? r + rho_core[g] : r) * er[g];   // E_xc of rho + rho_core
   }
   __shared__ double sh[32];
   for (int t = 0; t < kObs; ++t) {
@@ -1402,7 +1462,8 @@ __global__ void k_obs_final(int nblk, const double* __restrict__ part, double h3
 int observables(rmgtd_ctx* ctx) {
   const int nblk = ctx->red_blocks;
   k_obs_partial<<<dim3(nblk, ctx->nrep), 256, 0, ctx->stream>>>(
-      ctx->N, ctx->Ng, ctx->S0, ctx->M, ctx->Hcore, ctx->rho, ctx->vh, ctx->exc, ctx->red_part);
+      ctx->N, ctx->Ng, ctx->S0, ctx->M, ctx->Hcore, ctx->rho, ctx->vh, ctx->exc, ctx->rho_core,
+      ctx->red_part);
   ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_obs_partial");
   k_obs_final<<<ctx->nrep, 256, 0, ctx->stream>>>(nblk, ctx->red_part, ctx->h3, ctx->E_ion,

@@ -115,6 +115,8 @@ struct rmgtd_ctx {
   float* rho_a32 = nullptr;   // [nrep][Ng] rho(Sa) - rho_ref
   float* dv_a32 = nullptr;    // [nrep][Ng] V_Hxc of the anchor - vref
   double* vion = nullptr;      // [Ng] V_loc + V_ext
+  double* rho_core = nullptr;  // [Ng] frozen core density (xc only), or NULL
+  double* rho_xc_ref = nullptr;  // [Ng] rho_ref + rho_core: base of the mixed xc increment
   double* f_dev = nullptr;     // [N]
 
   // Kleinman-Bylander projectors as dense boxes
@@ -234,6 +236,16 @@ struct rmgtd_ctx {
   double* rho_mom = nullptr;
   long rho_mom_cap = 0;
   int rho_mom_blocks = 0;
+
+  // external field E(t) (rmgtd_set_field): samples E_r(j dt) per replica [nrep][fld_cap][3],
+  // their counts, the step's mean [nrep][3]; step_dev counts completed steps on the device
+  int fld_on = 0;
+  int fld_cap = 0;
+  double* fld_samples = nullptr;
+  int* fld_nsamp = nullptr;
+  double* fld_ebar = nullptr;
+  std::vector<std::vector<double>> fld_host;
+  long long* step_dev = nullptr;
 
   // learned seed of the SCF loop (attached network; buffers allocated at attach)
   rmgtd_net* net = nullptr;
@@ -379,9 +391,11 @@ int apply_h_dev(rmgtd_ctx* ctx, const void* x, void* hx, int ncols, int dtype,
                 const double* vextra);
 // vh_mode: 0 = vh is an input; 1 = vh <- vh_ref + dvh32 (mixed step); 2 = vh is an input
 // and dvh32 <- vh - vh_ref (mixed refresh).  dv32 (if given) <- V_H + V_xc - vref.
+// with_core: the context's frozen core density (if any) is added to rho in the xc (grid
+// fields of the context; not for the stand-alone rmgtd_xc)
 int launch_lda(rmgtd_ctx* ctx, const double* rho, double* vh, int vh_mode, double* vxc,
                double* exc, double* vhxc, float* dv32, long n, const RepCtl* ctl, int nrep,
-               long stride, int with_xc);
+               long stride, int with_xc, bool with_core = true);
 // Mixed pass: dv32 <- dvh32 + V_xc(rho_ref + drho32) - V_xc(rho_ref) in float32 arithmetic.
 int launch_xc_mixed(rmgtd_ctx* ctx, const RepCtl* ctl, int nrep);
 // dv[g] <- V_xc(rho0[g] + d[g]) - V_xc(rho0[g]) (the same float32 increment, stand-alone).
@@ -400,12 +414,17 @@ int gram_mixed(rmgtd_ctx* ctx, const float* w, long wstride, int nw, double scal
                const double* base, double* out, const RepCtl* ctl, unsigned long long* errbits,
                long bstride = 0, const float* w_anchor = nullptr);
 int to_float(rmgtd_ctx* ctx, const double* in, float* out, long n);
+// out = a + b on n points
+int add_fields(rmgtd_ctx* ctx, const double* a, const double* b, double* out, long n);
 // phi32t <- phi32 in 32-point tiles (layout above)
 int tile_orbitals(rmgtd_ctx* ctx);
+// febar (may be NULL): [nrep][3] field of the step, Hbar += sum_q febar[r][q] M_q
 int eldyn(rmgtd_ctx* ctx, const double* Ha, const double* Hb, long hstride, double tau,
           const double* S0, const double* A0, double* S1, double* A1, const RepCtl* ctl_in,
           RepCtl* ctl_out, int rep0, int nreps,
-          float* shat_out = nullptr);
+          float* shat_out = nullptr, const double* febar = nullptr);
+// the step's mean field ebar from the samples (no-op without a field)
+int field_begin(rmgtd_ctx* ctx);
 int step_begin(rmgtd_ctx* ctx);
 // step_begin and the quadratic extrapolation of the Hartree guess in one launch
 int step_begin_extrapolate(rmgtd_ctx* ctx);

@@ -57,6 +57,7 @@ class System:
     hartree_xc: bool = True  # False: independent electrons in V_loc (+ v_ext)
     v_ext_omega: float = 0.0  # >0 adds a harmonic well 0.5*omega^2*r^2 (test mode)
     seed: int = SEED_BASE
+    rho_core: Optional[np.ndarray] = None  # frozen core density (nz, ny, nx), xc only
 
     @property
     def N(self) -> int:
@@ -253,6 +254,21 @@ def smooth_random_orbitals(sys: System, sub_index: int = 0, sigma_pts: float = 2
     for i in range(sys.N):
         w = rng.standard_normal(shape)
         out[i] = gaussian_filter(w, sigma_pts, mode="constant") * win
+    return out
+
+
+def gaussian_core_density(sys: System, charge: float = 0.5, width: float = 0.6) -> np.ndarray:
+    """A model frozen core density, shape (nz, ny, nx): a normalised Gaussian of `charge`
+    electrons and `width` bohr on every atom (an input field, like the orbitals)."""
+    x = (np.arange(sys.n[0]) - 0.5 * (sys.n[0] - 1)) * sys.h
+    y = (np.arange(sys.n[1]) - 0.5 * (sys.n[1] - 1)) * sys.h
+    z = (np.arange(sys.n[2]) - 0.5 * (sys.n[2] - 1)) * sys.h
+    out = np.zeros(grid_shape(sys))
+    norm = charge / (math.pi * width * width) ** 1.5
+    for p in sys.pos:
+        out += (norm * np.exp(-((z[:, None, None] - p[2]) ** 2) / width ** 2)
+                * np.exp(-((y[None, :, None] - p[1]) ** 2) / width ** 2)
+                * np.exp(-((x[None, None, :] - p[0]) ** 2) / width ** 2))
     return out
 
 

@@ -47,6 +47,7 @@ class CSystem(ctypes.Structure):
         ("proj_m", _c_int_p), ("proj_rc", _c_double_p), ("E_kb", _c_double_p),
         ("nocc", ctypes.c_int), ("nvirt", ctypes.c_int), ("f", _c_double_p),
         ("phi0", _c_double_p), ("v_ext_omega", ctypes.c_double), ("hartree_xc", ctypes.c_int),
+        ("rho_core", _c_double_p),
     ]
 
 
@@ -130,6 +131,7 @@ def load_library(path: Optional[str] = None):
                                    ctypes.POINTER(ctypes.c_longlong)]),
         "rmgtd_selftest_barrier_timeout": (i, [vp, ctypes.c_uint, _c_int_p]),
         "rmgtd_get_hartree_preconditioner": (i, [vp, _c_int_p]),
+        "rmgtd_set_field": (i, [vp, i, _c_double_p, i]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -195,6 +197,12 @@ class Context:
         cs.phi0 = _dptr(phi)
         cs.v_ext_omega = float(sys.v_ext_omega)
         cs.hartree_xc = 1 if sys.hartree_xc else 0
+        if getattr(sys, "rho_core", None) is not None:
+            core = np.ascontiguousarray(np.asarray(sys.rho_core, dtype=np.float64).reshape(-1))
+            if core.size != sys.Ng:
+                raise ValueError("rho_core must have one value per grid point")
+            arrs["core"] = core
+            cs.rho_core = _dptr(core)
         opt = COptions()
         lib.rmgtd_default_options(ctypes.byref(opt))
         opt.dt = float(sys.dt if dt is None else dt)
@@ -265,6 +273,13 @@ class Context:
         self.close()
 
     # --- ABI -----------------------------------------------------------------------------
+    def set_field(self, rep: int, E):
+        """Samples E[j] = (E_x, E_y, E_z)(j dt) of replica `rep`'s external field
+        (rmgtd_set_field); an empty array clears it."""
+        E = np.ascontiguousarray(np.asarray(E, dtype=np.float64).reshape(-1, 3))
+        self._keep.append(E)
+        self._check(self._lib.rmgtd_set_field(self._ctx, int(rep), _dptr(E), int(E.shape[0])))
+
     def kick(self, rep: int, axis: int, kappa: float):
         self._check(self._lib.rmgtd_kick(self._ctx, rep, axis, float(kappa)))
 

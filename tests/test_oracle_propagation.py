@@ -163,3 +163,64 @@ def test_subspace_ground_state_is_stationary_projector():
     P1, H1, _, _, _ = prh.subspace_ground_state(1, 1.0, 0.0)
     w, W = np.linalg.eigh(prh.Hcore)
     assert np.max(np.abs(P1 - 2.0 * np.outer(W[:, 0], W[:, 0]))) < 1e-12
+
+
+def test_harmonic_two_level_field_linear_response(ho):
+    """A weak field E_z(t) = E0 sin(W t) on the harmonic oscillator's two-level active space
+    (ground orbital and the z-excited one, coupled by M_z with element a = (2 w)^(-1/2)): the
+    dipole is the convolution of the kick response, d(t) = -4 a^2 E0 integral_0^t
+    sin(w (t - s)) sin(W s) ds = -4 a^2 E0 (W sin(w t) - w sin(W t)) / (W^2 - w^2), to the
+    O(E0^2) nonlinearity and the O(dt^2) time stepping (Algorithm 1's V_{j-1} + V_j in Omega).
+    A wrong sign or factor of the field term, or a field sampled at one end of the step only,
+    moves d(t) by far more than the bound."""
+    s, gs = ho
+    w = s.v_ext_omega
+    E0, W = 1e-4, 0.3
+    o = tddft.Options(dt=0.05, H_thrs=1e-12, dP_thrs=1e-15)
+    r = tddft.run(s, gs["phi"], o, nsteps=300, axis=2, kappa=0.0,
+                  field=lambda t: np.array([0.0, 0.0, E0 * math.sin(W * t)]))
+    a = 1.0 / math.sqrt(2 * w)
+    t = r["t"]
+    expect = -4.0 * a * a * E0 * (W * np.sin(w * t) - w * np.sin(W * t)) / (W * W - w * w)
+    d = r["dipole"][:, 2] - r["dipole"][0, 2]
+    amp = np.max(np.abs(expect))
+    assert np.max(np.abs(d - expect)) < 2e-3 * amp, np.max(np.abs(d - expect)) / amp
+    assert np.max(np.abs(r["dipole"][:, :2] - r["dipole"][0, :2])) < 1e-10
+
+
+def test_xc_energy_gradient_is_the_xc_hamiltonian_with_a_frozen_core(small_ground_state):
+    """The Kohn-Sham exchange-correlation matrix is the gradient of the xc energy with respect
+    to the density matrix, with a frozen core density added to rho inside the xc (Section 3.1's
+    frozen semicore): [E_xc(P + e D) - E_xc(P - e D)] / 2e = Tr(H_xc D) for a symmetric D, with
+    E_xc = E - Tr(P H_core) - 1/2 h^3 sum rho V_H - E_ion from the oracle's energy and
+    H_xc = h^3 Phi^T diag(V_xc) Phi from its H.  An energy that weights eps_xc by rho instead
+    of rho + rho_core, or a V_xc without the core, fails by orders of magnitude."""
+    import dataclasses
+    s, gs = small_ground_state
+    s = dataclasses.replace(s, rho_core=inputs.gaussian_core_density(s, charge=0.6, width=0.7))
+    pr = tddft.Propagator(s, gs["phi"], tddft.Options(poisson_tol=1e-13))
+    f = s.occupations
+    rng = np.random.default_rng(11)
+    D = rng.standard_normal((s.N, s.N))
+    D = 0.5 * (D + D.T) / np.linalg.norm(D, 2)
+    # P >= 0.1 I and |e D| << 0.1: rho >= 0 everywhere for P, P + e D and P - e D (a negative
+    # density would meet the LDA's floor and break the finite difference)
+    P = np.diag(f + 0.1).astype(complex)
+
+    def exc_energy(PP):
+        H, aux = pr.dft(PP)
+        e_nonxc = (float(np.trace(np.real(PP) @ pr.Hcore)) + 0.5 * pr.h3 * float(aux["rho"] @ aux["vh"])
+                   + pr.E_ion)
+        return pr.energy(PP, aux) - e_nonxc, aux
+
+    _, aux = exc_energy(P)
+    Hxc = pr.h3 * (pr.phi @ (aux["vxc"] * pr.phi).T)
+    eps = 1e-4
+    g = (exc_energy(P + eps * D)[0] - exc_energy(P - eps * D)[0]) / (2 * eps)
+    expect = float(np.trace(Hxc @ D))
+    assert abs(g - expect) < 1e-6 * abs(expect), (g, expect)
+    # the core changes the xc energy and matrix (it is not silently ignored)
+    pr0 = tddft.Propagator(dataclasses.replace(s, rho_core=None), gs["phi"],
+                           tddft.Options(poisson_tol=1e-13))
+    _, aux0 = pr0.dft(P)
+    assert np.max(np.abs(aux0["vxc"] - aux["vxc"])) > 1e-3
