@@ -25,6 +25,14 @@ the overlap is the identity and the orthogonal commutator expansion applies (Sec
   V_{j-1} + V_j, its values at both ends of the step (Algorithm 1's Omega assignment), i.e.
   Omega = -i dt ((H_0 + H_1)/2 + sum_q (E_q(t_j) + E_q(t_j + dt))/2 M_q); a field
   kappa delta(t) along q is the kick along q.
+* Second-order Magnus term (option ``magnus2``, Section 2.2): with H linear in time over the
+  step, Omega_2 = (dt^2/12)[H_0, H_1] (hbar = 1), each H with the field's value at its end,
+  is added to Omega; Omega stays anti-Hermitian and the same series applies.
+* Non-orthogonal basis (option ``nonorthogonal``, Section 2.2 and Appendix A.2): Phi is used
+  as given, S = h^3 Phi Phi^T, Omega = -i dt S^-1 (Hbar + V), so that the series is
+  dP_k = (1/k)(-i dt)(S^-1 Hbar dP_{k-1} - dP_{k-1} Hbar S^-1); the kick uses S^-1 M_q; the
+  start is P = L^-T diag(f) L^-1 (S = L L^T: the occupations on the Cholesky-orthonormalised
+  orbitals); the electron count is Tr(Re P S).
 * rho(P)(r) = sum_ij Re(P)_ij phi_i(r) phi_j(r) (the density of P = sum f |psi><psi|; the
   imaginary part of a Hermitian P cancels).
 * DFT(rho): Hartree by ``poisson.hartree``, LDA by ``lda.lda``, then
@@ -38,7 +46,9 @@ the overlap is the identity and the orthogonal commutator expansion applies (Sec
 
 Pinned by: the two-level closed form of the kicked harmonic oscillator, the spectral
 propagator W exp(omega) W^dagger (Section 2.2), Tr(P) conservation, energy conservation,
-and the time-domain Thomas-Reiche-Kuhn slope.
+the time-domain Thomas-Reiche-Kuhn slope, the linear response to a weak field, the global
+order (2 and 4) of the Magnus truncations against an independent ODE integration, and the
+non-orthogonal series against the orthonormalised basis (Appendix A.2).
 """
 from __future__ import annotations
 
@@ -66,12 +76,20 @@ class Options:
     max_terms: int = 200
     poisson_tol: float = 1e-13
     full_apply: bool = True
+    magnus2: bool = False        # add Omega_2 = (dt^2/12)[H_0, H_1] (Section 2.2)
+    nonorthogonal: bool = False  # propagate in the given basis with S^-1 H (Section 2.2)
 
 
 def commutator_series(P0: np.ndarray, Hbar: np.ndarray, tau: float, thrs: float,
                       max_terms: int = 200):
     """P = e^{-i tau Hbar} P0 e^{+i tau Hbar} by the series of Eq. 33; returns (P, terms)."""
-    Omega = -1j * tau * Hbar
+    return omega_series(P0, -1j * tau * Hbar, thrs, max_terms)
+
+
+def omega_series(P0: np.ndarray, Omega: np.ndarray, thrs: float, max_terms: int = 200):
+    """P = e^{Omega} P0 e^{Omega^dagger} as P0 + sum_k dP_k, dP_k = (Omega dP_{k-1} +
+    dP_{k-1} Omega^dagger)/k, dP_0 = P0 (Eq. 33; with Omega = -i dt S^-1 Hbar the series of the
+    non-orthogonal basis, Section 2.2); stops at max|dP_k| <= thrs.  Returns (P, terms)."""
     OmegaH = Omega.conj().T
     P = P0.astype(np.complex128).copy()
     dP = P.copy()
@@ -114,6 +132,9 @@ class Propagator:
                   for q in ham.full_coords(sys)]
         self.E_ion = ham.ion_energy(sys)
         self.vh = None
+        # overlap S = h^3 Phi Phi^T; the identity in an orthonormal basis
+        self.S = self._sym(self.h3 * (self.phi @ self.phi.T))
+        self.Sinv = np.linalg.inv(self.S) if self.opts.nonorthogonal else None
         core = getattr(sys, "rho_core", None)
         self.rho_core = np.zeros(sys.Ng) if core is None else np.asarray(core, float).ravel()
 
@@ -150,9 +171,18 @@ class Propagator:
         return commutator_series(P0, Hbar, tau, self.opts.dP_thrs, self.opts.max_terms)
 
     def kick(self, P, axis: int, kappa: float):
-        P1, _ = commutator_series(P, self.M[axis], kappa, self.opts.dP_thrs,
-                                  self.opts.max_terms)
+        Omega = -1j * kappa * self._metric(self.M[axis])
+        P1, _ = omega_series(P, Omega, self.opts.dP_thrs, self.opts.max_terms)
         return P1
+
+    def _metric(self, A):
+        """S^-1 A in the non-orthogonal basis, A otherwise."""
+        return self.Sinv @ A if self.opts.nonorthogonal else A
+
+    def trace(self, P) -> float:
+        """Number of electrons Tr(Re P S) (Tr P in an orthonormal basis)."""
+        return float(np.trace(np.real(P) @ self.S)) if self.opts.nonorthogonal else \
+            float(np.real(np.trace(P)))
 
     def dipole(self, P) -> np.ndarray:
         return np.array([np.trace(np.real(P) @ M) for M in self.M])
@@ -187,8 +217,16 @@ class Propagator:
 
     def initial_state(self, subspace_scf: int = 0, mix: float = 0.3, tol: float = 1e-10):
         if subspace_scf > 0:
+            if self.opts.nonorthogonal:
+                raise ValueError("the subspace ground state needs an orthonormal basis")
             P, H0, aux, _, _ = self.subspace_ground_state(subspace_scf, mix, tol)
             P0 = P.astype(np.complex128)
+        elif self.opts.nonorthogonal:
+            # occupations on the Cholesky-orthonormalised orbitals L^-1 Phi (S = L L^T):
+            # P = L^-T diag(f) L^-1, the back transformation R^-1 P_o L^-1 of Appendix A.2
+            X = np.linalg.inv(np.linalg.cholesky(self.S))
+            P0 = (X.T @ np.diag(self.sys.occupations) @ X).astype(np.complex128)
+            H0, aux = self.dft(P0)
         else:
             f = self.sys.occupations
             P0 = np.diag(f).astype(np.complex128)
@@ -199,18 +237,37 @@ class Propagator:
         """sum_q (E_q(t) + E_q(t + dt))/2 M_q for the step starting at t (zero without a field)."""
         if self.field is None:
             return np.zeros_like(self.Hcore)
-        e = 0.5 * (np.asarray(self.field(t), dtype=float)
-                   + np.asarray(self.field(t + self.opts.dt), dtype=float))
+        return 0.5 * (self.field_at(t) + self.field_at(t + self.opts.dt))
+
+    def field_at(self, t: float) -> np.ndarray:
+        """sum_q E_q(t) M_q (zero without a field)."""
+        if self.field is None:
+            return np.zeros_like(self.Hcore)
+        e = np.asarray(self.field(t), dtype=float)
         return sum(e[q] * self.M[q] for q in range(3))
+
+    def omega(self, H0, H1, t: float) -> np.ndarray:
+        """Omega of the step from t to t + dt with H changing linearly from H_0 to H_1 (the
+        field's values at both ends added): Omega_1 = -i dt (H_0 + H_1)/2 (S^-1 in front in
+        the non-orthogonal basis), plus Omega_2 = (dt^2/12)[H_0, H_1] with the magnus2
+        option (Section 2.2)."""
+        dt = self.opts.dt
+        Om = -1j * dt * self._metric(0.5 * (H0 + H1) + self.field_term(t))
+        if self.opts.magnus2:
+            if self.opts.nonorthogonal:
+                raise ValueError("Omega_2 is implemented for an orthonormal basis only")
+            A = H0 + self.field_at(t)
+            B = H1 + self.field_at(t + dt)
+            Om = Om + (dt * dt / 12.0) * (A @ B - B @ A)
+        return Om
 
     def step(self, st):
         o = self.opts
         P0, H0, Hm1 = st["P0"], st["H0"], st["Hm1"]
         H1 = 2.0 * H0 - Hm1
-        V = self.field_term(st["t"])
         terms = []
         for npass in range(1, o.max_scf + 1):
-            P1, k = self.expand(P0, 0.5 * (H0 + H1) + V, o.dt)
+            P1, k = omega_series(P0, self.omega(H0, H1, st["t"]), o.dP_thrs, o.max_terms)
             terms.append(k)
             Hnew, aux = self.dft(P1)
             err = float(np.max(np.abs(Hnew - H1)))
@@ -239,13 +296,13 @@ def run(sys, phi, opts: Optional[Options] = None, nsteps: int = 10, axis: int = 
     _, aux0 = pr.dft(st["P0"])          # observables at t = 0+ (state H_0 is unchanged)
     out.update({"t": [0.0], "dipole": [pr.dipole(st["P0"])],
                 "energy": [pr.energy(st["P0"], aux0)],
-                "trace": [float(np.real(np.trace(st["P0"])))], "passes": [], "terms": []})
+                "trace": [pr.trace(st["P0"])], "passes": [], "terms": []})
     for _ in range(nsteps):
         s = pr.step(st)
         out["t"].append(st["t"])
         out["dipole"].append(pr.dipole(st["P0"]))
         out["energy"].append(pr.energy(st["P0"], st["aux"]))
-        out["trace"].append(float(np.real(np.trace(st["P0"]))))
+        out["trace"].append(pr.trace(st["P0"]))
         out["passes"].append(s["passes"])
         out["terms"].append(s["terms"])
     for key in ("t", "dipole", "energy", "trace"):
