@@ -17,6 +17,8 @@ Plain, slow, obviously-correct NumPy/SciPy in float64, written from the paper:
                      (Algorithm 1, lines 1-3).
 * ``tddft``       -- Algorithm 1: commutator expansion (Eqs. 19, 32-33), Hamiltonian
                      self-consistency, linear extrapolation, kick (Eq. 34), dipole.
+* ``gridprop``    -- the occupied orbitals propagated on the grid, the complete-grid-basis
+                     limit of Algorithm 1 (Section 2.2).
 * ``spectrum``    -- absorption spectrum (dipole strength function) from the kicked dipole
                      series of the three kick directions (Section 4).
 * ``surrogate``   -- learned correction to the linear-extrapolation seed of the SCF loop
