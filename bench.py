@@ -202,12 +202,45 @@ def _host_info():
     return {"cpu": model, "machine": platform.machine(), "logical_cores": os.cpu_count()}
 
 
-def _blas_threads():
+_BLAS_SET = ("openblas_set_num_threads", "openblas_set_num_threads64_",
+             "scipy_openblas_set_num_threads", "scipy_openblas_set_num_threads64_")
+_BLAS_GET = ("openblas_get_num_threads", "openblas_get_num_threads64_",
+             "scipy_openblas_get_num_threads", "scipy_openblas_get_num_threads64_")
+
+
+def _blas_libs():
+    """(get, set) thread-count functions of every OpenBLAS loaded in this process (numpy's and
+    scipy's copies), found through /proc/self/maps -- threadpoolctl is not installed
+    everywhere."""
+    import ctypes
+    paths = set()
     try:
-        from threadpoolctl import threadpool_info
-        return max([d.get("num_threads", 1) for d in threadpool_info()] or [os.cpu_count()])
-    except Exception:
-        return os.cpu_count()
+        for line in open("/proc/self/maps"):
+            f = line.split()[-1]
+            if "blas" in os.path.basename(f).lower() and ".so" in f:
+                paths.add(f)
+    except OSError:
+        return []
+    out = []
+    for p in sorted(paths):
+        try:
+            lib = ctypes.CDLL(p)
+        except OSError:
+            continue
+        get = next((getattr(lib, n) for n in _BLAS_GET if hasattr(lib, n)), None)
+        set_ = next((getattr(lib, n) for n in _BLAS_SET if hasattr(lib, n)), None)
+        if get is not None and set_ is not None:
+            get.restype = ctypes.c_int
+            set_.argtypes = [ctypes.c_int]
+            out.append((get, set_))
+    return out
+
+
+def _blas_threads():
+    libs = _blas_libs()
+    if libs:
+        return max(int(g()) for g, _ in libs)
+    return os.cpu_count()
 
 
 class OracleRun:
@@ -308,16 +341,22 @@ def cpu_baseline_sample(name):
            "sample": f"{len(times)} whole time step(s) of the workload from the GPU arm's start "
                      f"(budget {CPU_BASELINE_BUDGET_S:.0f} s)"}
     passes = float(np.mean(orc.passes)) * len(orc.states)
+    libs = _blas_libs()
+    if not libs:
+        out["one_thread"] = {"unavailable": "no OpenBLAS thread control found in this process"}
+        return out
+    before = [int(g()) for g, _ in libs]
     try:
-        from threadpoolctl import threadpool_limits
-        with threadpool_limits(limits=1):
-            t1 = orc.one_pass()
-        out["one_thread"] = {"value": 1.0 / (t1 * passes), "cores": 1,
-                             "sample": f"one SCF pass with BLAS on 1 thread, x {passes:.2f} "
-                                       "passes per time step (all replicas) of the first "
-                                       "measurement"}
-    except Exception as e:  # threadpoolctl missing on the host
-        out["one_thread"] = {"unavailable": str(e)}
+        for _, set_ in libs:
+            set_(1)
+        t1 = orc.one_pass()
+    finally:
+        for (_, set_), n in zip(libs, before):
+            set_(n)
+    out["one_thread"] = {"value": 1.0 / (t1 * passes), "cores": 1,
+                         "sample": f"one SCF pass with BLAS on 1 thread, x {passes:.2f} "
+                                   "passes per time step (all replicas) of the first "
+                                   "measurement"}
     return out
 
 

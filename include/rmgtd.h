@@ -127,6 +127,28 @@ typedef struct {
   double subspace_tol;     /* stop when max|P_new - P| <= subspace_tol (default 1e-10) */
   double mixed_poisson_tol;  /* mixed path: relative residual of the float32 Hartree correction
                                 solve (0 = default 3e-6; values below 1e-8 are raised to 1e-8) */
+  int magnus_order;        /* 1 (or 0): Omega = Omega_1 = -i dt (H_0 + H_1)/2 (Eq. 15);
+                              2: plus Omega_2 = (dt^2/12)[H_0, H_1] (Section 2.2, H linear over
+                              the step; each H with the external field's value at its end) */
+  int nonorthogonal;       /* 1: propagate in the basis phi0 as given (Section 2.2, the series
+                              with S^-1 Hbar; Appendix A.2): S = h^3 Phi^T Phi, Omega =
+                              -i dt S^-1 (Hbar + V), kicks with S^-1 M_q, start P_0 =
+                              L^-T diag(f) L^-1 (S = L L^T), electron count Tr(Re P S).
+                              Requires orthonormalize = 0, subspace_scf = 0, magnus_order 1. */
+  int grid_basis;          /* 1: propagate the occupied orbitals on the grid, the complete-
+                              grid-basis limit of Algorithm 1 (Section 2.2: the scheme holds in
+                              any basis).  Per step V_1 = 2 V_0 - V_-1; per SCF pass the series
+                              psi^(k) = (-i dt/k) Hbar psi^(k-1), Hbar = T + V_ion + V_NL +
+                              (V_0 + V_1)/2 + Ebar.q, stopped at max|psi^(k)| <= dP_thrs; then
+                              V_new of rho = sum f |psi|^2 and H_err = max|V_new - V_1| (the grid
+                              basis's H_new - H_1 is diagonal); after the loop a float64
+                              Cholesky re-orthonormalisation.  The kick is the phase
+                              e^{-i kappa q}.  phi0 holds the occupied orbitals: nvirt = 0,
+                              precision FP64, magnus_order 1, nonorthogonal 0, subspace_scf 0.
+                              rmgtd_kick / set_field / step / dipole / energy / density act on
+                              the orbitals (stats: passes, terms of the orbital series,
+                              H_err = max|V_new - V_1|); the matrix, save / load, batch,
+                              autotune and network calls return RMGTD_ESTATE. */
 } rmgtd_options;
 
 /* Per-step, per-replica statistics written by rmgtd_step. */
@@ -152,7 +174,8 @@ typedef enum {
 } rmgtd_matrix;
 
 /* Fill `opt` with defaults: dt 0.05, H_thrs 1e-7, dP_thrs 1e-10, max_scf 50,
- * max_terms 200, FP64, nrep 1, orthonormalize 1, poisson_tol 1e-12, 200 PCG iterations,
+ * max_terms 200, FP64, nrep 1, orthonormalize 1, magnus_order 1, nonorthogonal 0,
+ * poisson_tol 1e-12, 200 PCG iterations,
  * use_graph 1 (each time step is one CUDA graph with device-side while loops for the SCF
  * passes and the Hartree iterations), default stream, cudaMalloc. */
 void rmgtd_default_options(rmgtd_options* opt);
@@ -195,6 +218,22 @@ int rmgtd_kick(rmgtd_ctx* ctx, int rep, int axis, double kappa);
  * NULL) receives nsteps * nrep entries, step-major.  Returns the first non-OK replica
  * status; on failure the state of the last completed step is kept. */
 int rmgtd_step(rmgtd_ctx* ctx, int nsteps, rmgtd_stats* stats);
+
+/* Dipole strength function of the kicked runs (Section 4: the spectrum is the sum of the
+ * Fourier transforms of mu_x(t), mu_y(t), mu_z(t) of the runs kicked along x, y and z).
+ * dipole: host [nq][nt] doubles, row q the dipole component along the kick of the run kicked
+ * along q (by kappa), sampled at t_n = n dt.  With the trapezoid rule over the samples and an
+ * exponential damping gamma >= 0 (Lorentzian lines):
+ *   S(omega_w) = -(2 omega_w / (pi kappa nq)) sum_q sum_n w_n dt (d_q(t_n) - d_q(0))
+ *                e^{-gamma t_n} sin(omega_w t_n),
+ * i.e. (2 omega / pi) Im alpha(omega), alpha = -(1/kappa) FT(d - d(0)), whose integral over
+ * omega > 0 is the electron count in a complete basis (sum rule).  omega: host [nw]; S: host
+ * [nw] output.  Runs on the current device in float64 (one warp per frequency), allocating
+ * and freeing its own device buffers; synchronous.  1 <= nq <= 64, 1 <= nw <= 2^24.
+ * Errors: RMGTD_EINVAL (NULL pointers, sizes, dt <= 0, kappa = 0, gamma < 0), RMGTD_ECUDA;
+ * the message is read with rmgtd_last_error(NULL). */
+int rmgtd_spectrum(const double* dipole, int nq, long nt, double dt, double kappa, double gamma,
+                   const double* omega, int nw, double* S);
 
 /* rho(r) of replica `rep` for the current P (host array of Ng doubles). */
 int rmgtd_density(rmgtd_ctx* ctx, int rep, double* rho_host);

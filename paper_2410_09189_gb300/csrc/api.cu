@@ -323,6 +323,9 @@ void rmgtd_default_options(rmgtd_options* o) {
   o->subspace_scf = 0;
   o->subspace_mix = 0.3;
   o->subspace_tol = 1e-10;
+  o->magnus_order = 1;
+  o->nonorthogonal = 0;
+  o->grid_basis = 0;
 }
 
 const char* rmgtd_last_error(const rmgtd_ctx* ctx) {
@@ -426,7 +429,16 @@ static int create_impl(const rmgtd_system* sys, const rmgtd_options* opt, rmgtd_
   ctx->kexec = (unsigned long long*)A(4 * sizeof(unsigned long long));
   ctx->done_steps = (int*)A(sizeof(int));
   ctx->step_dev = (long long*)A(sizeof(long long));
-  ctx->fld_ebar = (double*)A(sizeof(double) * 3 * nrep);
+  ctx->fld_ebar = (double*)A(sizeof(double) * 9 * nrep);
+  if (opt->nonorthogonal || opt->magnus_order == 2) {
+    ctx->Hx0 = (double*)A(msz * nrep);
+    ctx->Hx1 = (double*)A(msz * nrep);
+  }
+  if (opt->nonorthogonal) {
+    ctx->Sinv = (double*)A(msz);
+    ctx->Gm = (double*)A(msz * nrep);
+  }
+  if (opt->magnus_order == 2) ctx->Dm = (double*)A(msz * nrep);
   ctx->fld_nsamp = (int*)A(sizeof(int) * nrep);
   ctx->fld_host.assign(nrep, std::vector<double>());
   ctx->stats_cap = 256;
@@ -447,7 +459,7 @@ static int create_impl(const rmgtd_system* sys, const rmgtd_options* opt, rmgtd_
   RMGTD_CUDA(ctx, cudaMallocHost((void**)&ctx->stats_host, sizeof(RepCtl) * ctx->stats_cap * nrep));
   RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->failed, 0, sizeof(int), ctx->stream));
   RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->step_dev, 0, sizeof(long long), ctx->stream));
-  RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->fld_ebar, 0, sizeof(double) * 3 * nrep, ctx->stream));
+  RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->fld_ebar, 0, sizeof(double) * 9 * nrep, ctx->stream));
   RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->fld_nsamp, 0, sizeof(int) * nrep, ctx->stream));
   RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->kexec, 0, 4 * sizeof(unsigned long long), ctx->stream));
   RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream));
@@ -534,6 +546,10 @@ static int create_impl(const rmgtd_system* sys, const rmgtd_options* opt, rmgtd_
       N, nrep, ctx->f_dev, ctx->S0, ctx->A0);
   ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_diag_init");
+  if (opt->nonorthogonal) {   // S^-1 and P_0 = L^-T diag(f) L^-1 (replaces diag(f))
+    rc = nonorth_setup(ctx);
+    if (rc) return rc;
+  }
   k_set_active<<<1, 32, 0, ctx->stream>>>(ctx->ctl, nrep, 1);
   ++ctx->launches;
   rc = dft_eval(ctx, ctx->S0, ctx->ctl, nullptr);
@@ -562,6 +578,10 @@ static int create_impl(const rmgtd_system* sys, const rmgtd_options* opt, rmgtd_
   RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->A1, ctx->A0, msz * nrep, cudaMemcpyDeviceToDevice, ctx->stream));
   k_set_active<<<1, 32, 0, ctx->stream>>>(ctx->ctl, nrep, 0);
   ++ctx->launches;
+  if (opt->grid_basis) {   // the occupied orbitals themselves are the propagated state
+    rc = gridprop_setup(ctx);
+    if (rc) return rc;
+  }
   if (opt->precision == RMGTD_PREC_MIXED) {
     // reference state of the mixed path: the float64 set-up state (all replicas start in it)
     const size_t fsz = sizeof(float) * Ng;
@@ -665,6 +685,18 @@ int rmgtd_create(const rmgtd_system* sys, const rmgtd_options* opt_in, rmgtd_ctx
     return set_error(nullptr, RMGTD_EINVAL, "invalid options");
   if (opt.precision != RMGTD_PREC_FP64 && opt.precision != RMGTD_PREC_MIXED)
     return set_error(nullptr, RMGTD_EINVAL, "unknown precision");
+  if (opt.magnus_order == 0) opt.magnus_order = 1;
+  if (opt.magnus_order != 1 && opt.magnus_order != 2)
+    return set_error(nullptr, RMGTD_EINVAL, "magnus_order must be 1 or 2");
+  if (opt.nonorthogonal && (opt.orthonormalize || opt.subspace_scf > 0 || opt.magnus_order != 1))
+    return set_error(nullptr, RMGTD_EINVAL,
+                     "nonorthogonal needs orthonormalize = 0, subspace_scf = 0 and magnus_order 1");
+  if (opt.grid_basis &&
+      (sys->nvirt != 0 || opt.precision != RMGTD_PREC_FP64 || opt.magnus_order != 1 ||
+       opt.nonorthogonal || opt.subspace_scf > 0))
+    return set_error(nullptr, RMGTD_EINVAL,
+                     "grid_basis needs nvirt = 0, FP64, magnus_order 1, nonorthogonal 0 and "
+                     "subspace_scf 0");
   rmgtd_ctx* ctx = new rmgtd_ctx();
   int rc = create_impl(sys, &opt, ctx);
   if (rc != RMGTD_OK) {
@@ -692,11 +724,18 @@ int rmgtd_kick(rmgtd_ctx* ctx, int rep, int axis, double kappa) {
   if (!ctx) return set_error(nullptr, RMGTD_EINVAL, "ctx is NULL");
   if (rep < 0 || rep >= ctx->nrep || axis < 0 || axis > 2)
     return set_error(ctx, RMGTD_EINVAL, "kick: bad replica or axis");
+  if (ctx->opt.grid_basis) return gridprop_kick(ctx, rep, axis, kappa);
   const long NN = (long)ctx->N * ctx->N;
   RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream));
   const double* Mq = ctx->M + axis * NN;
-  int rc = eldyn(ctx, Mq, Mq, 0, kappa, ctx->S0 + rep * NN, ctx->A0 + rep * NN,
-                 ctx->S1 + rep * NN, ctx->A1 + rep * NN, nullptr, nullptr, rep, 1);
+  int rc = RMGTD_OK;
+  if (ctx->opt.nonorthogonal) {   // Omega = -i kappa S^-1 M_q
+    rc = nonorth_kick_matrix(ctx, axis);
+    if (rc) return rc;
+    Mq = ctx->Gm;
+  }
+  rc = eldyn(ctx, Mq, Mq, 0, kappa, ctx->S0 + rep * NN, ctx->A0 + rep * NN,
+             ctx->S1 + rep * NN, ctx->A1 + rep * NN, nullptr, nullptr, rep, 1);
   if (rc) return rc;
   RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->S0 + rep * NN, ctx->S1 + rep * NN, sizeof(double) * NN,
                                   cudaMemcpyDeviceToDevice, ctx->stream));
@@ -709,11 +748,15 @@ int rmgtd_kick(rmgtd_ctx* ctx, int rep, int axis, double kappa) {
 
 // One SCF pass of Algorithm 1 (lines 14-26) for every active replica.
 static int enqueue_pass(rmgtd_ctx* ctx, cudaGraphConditionalHandle cond, int use_cond) {
-  const long NN = (long)ctx->N * ctx->N;
   ph_begin(ctx, PH_ELDYN);
-  int rc = eldyn(ctx, ctx->H0, ctx->H1, NN, ctx->opt.dt, ctx->S0, ctx->A0, ctx->S1, ctx->A1,
-                 ctx->ctl, ctx->ctl, 0, ctx->nrep, ctx->mixed ? ctx->shat32 : nullptr,
-                 ctx->fld_on ? ctx->fld_ebar : nullptr);
+  // Omega's matrices: Hbar (+ the field), or S^-1 (Hbar + V) in a non-orthogonal basis, and
+  // the Omega_2 term
+  const double *Ha, *Hb, *febar, *D;
+  long hstride;
+  int rc = magnus_prepare(ctx, &Ha, &Hb, &hstride, &febar, &D);
+  if (!rc)
+    rc = eldyn(ctx, Ha, Hb, hstride, ctx->opt.dt, ctx->S0, ctx->A0, ctx->S1, ctx->A1, ctx->ctl,
+               ctx->ctl, 0, ctx->nrep, ctx->mixed ? ctx->shat32 : nullptr, febar, D);
   ph_end(ctx);
   if (rc) return rc;
   rc = dft_eval(ctx, ctx->S1, ctx->ctl, ctx->errbits);
@@ -874,6 +917,13 @@ int rmgtd_step(rmgtd_ctx* ctx, int nsteps, rmgtd_stats* stats) {
   if (!ctx) return set_error(nullptr, RMGTD_EINVAL, "ctx is NULL");
   if (nsteps < 0) return set_error(ctx, RMGTD_EINVAL, "nsteps < 0");
   if (ctx->in_batch) return set_error(ctx, RMGTD_ESTATE, "context belongs to a batch: step the batch");
+  if (ctx->opt.grid_basis) {   // host-driven steps of the orbitals on the grid
+    for (int i = 0; i < nsteps; ++i) {
+      const int rc = gridprop_step(ctx, stats ? stats + (long)i * ctx->nrep : nullptr);
+      if (rc) return rc;
+    }
+    return RMGTD_OK;
+  }
   if (ctx->opt.use_graph && !ctx->step_exec) {
     int rc = build_step_graph(ctx);
     if (rc) return rc;
@@ -909,6 +959,7 @@ int rmgtd_step(rmgtd_ctx* ctx, int nsteps, rmgtd_stats* stats) {
 int rmgtd_autotune(rmgtd_ctx* ctx, int choice[4]) {
   if (!ctx) return set_error(nullptr, RMGTD_EINVAL, "ctx is NULL");
   if (ctx->in_batch) return set_error(ctx, RMGTD_ESTATE, "autotune: context belongs to a batch");
+  if (ctx->opt.grid_basis) return set_error(ctx, RMGTD_ESTATE, "autotune: grid-basis context");
   const int nrep = ctx->nrep;
   const long Ng = ctx->Ng, NN = (long)ctx->N * ctx->N;
   RMGTD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
@@ -1088,6 +1139,7 @@ int rmgtd_batch_create(rmgtd_ctx* const* ctxs, int n, rmgtd_batch** out) {
   for (int i = 0; i < n; ++i) {
     if (!ctxs[i]) return set_error(nullptr, RMGTD_EINVAL, "batch_create: NULL context");
     if (ctxs[i]->in_batch) return set_error(nullptr, RMGTD_EINVAL, "batch_create: context already in a batch");
+    if (ctxs[i]->opt.grid_basis) return set_error(nullptr, RMGTD_ESTATE, "batch_create: grid-basis context");
     if (ctxs[i]->stream != ctxs[0]->stream)
       return set_error(nullptr, RMGTD_EINVAL, "batch_create: contexts must share one stream");
     for (int j = 0; j < i; ++j)
@@ -1229,6 +1281,7 @@ int rmgtd_profile_counters(rmgtd_ctx* ctx, long long* hartree_solves,
 int rmgtd_attach_net(rmgtd_ctx* ctx, rmgtd_net* net) {
   if (!ctx) return set_error(nullptr, RMGTD_EINVAL, "ctx is NULL");
   if (ctx->in_batch) return set_error(ctx, RMGTD_ESTATE, "attach_net: context belongs to a batch");
+  if (ctx->opt.grid_basis) return set_error(ctx, RMGTD_ESTATE, "attach_net: grid-basis context");
   if (net) {
     int nx, ny, nz;
     net_grid_points(net, &nx, &ny, &nz);
@@ -1283,7 +1336,8 @@ int rmgtd_get_field(rmgtd_ctx* ctx, int which, int rep, double* dev_out) {
 int rmgtd_density(rmgtd_ctx* ctx, int rep, double* rho_host) {
   if (!ctx) return set_error(nullptr, RMGTD_EINVAL, "ctx is NULL");
   if (rep < 0 || rep >= ctx->nrep || !rho_host) return set_error(ctx, RMGTD_EINVAL, "density: bad arguments");
-  int rc = rho_dev(ctx, ctx->S0, ctx->rho, nullptr, ctx->nrep);
+  int rc = ctx->opt.grid_basis ? gridprop_observables(ctx)
+                               : rho_dev(ctx, ctx->S0, ctx->rho, nullptr, ctx->nrep);
   if (rc) return rc;
   RMGTD_CUDA(ctx, cudaMemcpyAsync(rho_host, ctx->rho + (long)rep * ctx->Ng, sizeof(double) * ctx->Ng,
                                   cudaMemcpyDeviceToHost, ctx->stream));
@@ -1303,6 +1357,12 @@ static int fetch_obs(rmgtd_ctx* ctx) {
 int rmgtd_dipole(rmgtd_ctx* ctx, int rep, double mu[3]) {
   if (!ctx) return set_error(nullptr, RMGTD_EINVAL, "ctx is NULL");
   if (rep < 0 || rep >= ctx->nrep || !mu) return set_error(ctx, RMGTD_EINVAL, "dipole: bad arguments");
+  if (ctx->opt.grid_basis) {
+    const int rc = gridprop_observables(ctx);
+    if (rc) return rc;
+    gridprop_read(ctx, rep, mu, nullptr, nullptr);
+    return RMGTD_OK;
+  }
   int rc = fetch_obs(ctx);
   if (rc) return rc;
   for (int d = 0; d < 3; ++d) mu[d] = ctx->obs_host[8 * rep + d];
@@ -1312,6 +1372,12 @@ int rmgtd_dipole(rmgtd_ctx* ctx, int rep, double mu[3]) {
 int rmgtd_energy(rmgtd_ctx* ctx, int rep, double* E) {
   if (!ctx) return set_error(nullptr, RMGTD_EINVAL, "ctx is NULL");
   if (rep < 0 || rep >= ctx->nrep || !E) return set_error(ctx, RMGTD_EINVAL, "energy: bad arguments");
+  if (ctx->opt.grid_basis) {
+    const int rc = gridprop_observables(ctx);
+    if (rc) return rc;
+    gridprop_read(ctx, rep, nullptr, E, nullptr);
+    return RMGTD_OK;
+  }
   int rc = mixed_fields64(ctx);
   if (rc) return rc;
   rc = fetch_obs(ctx);
@@ -1342,6 +1408,7 @@ static double* matrix_ptr(rmgtd_ctx* ctx, int which, int rep, bool* shared) {
 
 int rmgtd_get_matrix(rmgtd_ctx* ctx, int which, int rep, double* host_out) {
   if (!ctx) return set_error(nullptr, RMGTD_EINVAL, "ctx is NULL");
+  if (ctx->opt.grid_basis) return set_error(ctx, RMGTD_ESTATE, "get_matrix: grid-basis context (no P)");
   if (rep < 0 || rep >= ctx->nrep || !host_out) return set_error(ctx, RMGTD_EINVAL, "get_matrix: bad arguments");
   bool shared;
   double* p = matrix_ptr(ctx, which, rep, &shared);
@@ -1354,6 +1421,7 @@ int rmgtd_get_matrix(rmgtd_ctx* ctx, int which, int rep, double* host_out) {
 
 int rmgtd_set_matrix(rmgtd_ctx* ctx, int which, int rep, const double* host_in) {
   if (!ctx) return set_error(nullptr, RMGTD_EINVAL, "ctx is NULL");
+  if (ctx->opt.grid_basis) return set_error(ctx, RMGTD_ESTATE, "set_matrix: grid-basis context (no P)");
   if (rep < 0 || rep >= ctx->nrep || !host_in) return set_error(ctx, RMGTD_EINVAL, "set_matrix: bad arguments");
   bool shared;
   double* p = matrix_ptr(ctx, which, rep, &shared);
@@ -1489,6 +1557,7 @@ static const uint64_t kMagic = 0x32444d54474d52ull;  // "RMGTD2"
 int rmgtd_save(rmgtd_ctx* ctx, const char* path) {
   if (!ctx) return set_error(nullptr, RMGTD_EINVAL, "ctx is NULL");
   if (!path) return set_error(ctx, RMGTD_EINVAL, "save: path is NULL");
+  if (ctx->opt.grid_basis) return set_error(ctx, RMGTD_ESTATE, "save: grid-basis context");
   const long NN = (long)ctx->N * ctx->N;
   const size_t mcount = (size_t)NN * ctx->nrep, gcount = (size_t)ctx->Ng * ctx->nrep;
   std::vector<double> buf(4 * mcount + gcount);
@@ -1543,6 +1612,7 @@ int rmgtd_save(rmgtd_ctx* ctx, const char* path) {
 int rmgtd_load(rmgtd_ctx* ctx, const char* path) {
   if (!ctx) return set_error(nullptr, RMGTD_EINVAL, "ctx is NULL");
   if (!path) return set_error(ctx, RMGTD_EINVAL, "load: path is NULL");
+  if (ctx->opt.grid_basis) return set_error(ctx, RMGTD_ESTATE, "load: grid-basis context");
   FILE* fp = fopen(path, "rb");
   if (!fp) return set_error(ctx, RMGTD_EINVAL, std::string("load: cannot open ") + path);
   uint64_t magic = 0;

@@ -700,6 +700,10 @@ struct EldynArgs {
   // E(t_j) and E(t_j + dt) (Algorithm 1's V_{j-1} + V_j in Omega)
   const double* fM;       // [3][N*N] dipole matrices
   const double* febar;    // [rep][3]
+  // second-order Magnus term (NULL: none): Omega = -i tau (Hbar + i D), D = (tau/12)[H_0, H_1]
+  // real antisymmetric per replica (stride N*N), so the series multiplies by the Hermitian
+  // K = Hbar + i D: T1 = Im(K dP) = Hbar A + D S, T2 = Re(K dP) = Hbar S - D A
+  const double* D;
 };
 
 // the field's contribution to Hbar at element o of replica rep (0 without a field)
@@ -710,7 +714,7 @@ __device__ __forceinline__ double field_term(const EldynArgs& a, int rep, long o
   return e[0] * a.fM[o] + e[1] * a.fM[NN + o] + e[2] * a.fM[2 * NN + o];
 }
 
-template <int TS, int NT>
+template <int TS, int NT, bool WD>
 __global__ void __launch_bounds__(NT) k_eldyn(EldynArgs a) {
   constexpr int KC = 32;
   constexpr int TSP = TS + 1;
@@ -724,6 +728,9 @@ __global__ void __launch_bounds__(NT) k_eldyn(EldynArgs a) {
   double* Si = Aj + KC * TSP;
   double* Sj = Si + KC * TSP;
   double* Tt = Sj + KC * TSP;        // [4][TS][TSP]
+  double* Di = Tt + 4 * TS * TSP;    // [TS][KC+1] rows of D (only with the Omega_2 term)
+  double* Dj = Di + TS * (KC + 1);
+  constexpr bool wd = WD;   // with the Omega_2 term (a.D != NULL)
   __shared__ double sh[32];
   __shared__ int conv[32];
   __shared__ int all_done;
@@ -796,6 +803,11 @@ __global__ void __launch_bounds__(NT) k_eldyn(EldynArgs a) {
           }
           Hi[r * (KC + 1) + kk] = hi;
           Hj[r * (KC + 1) + kk] = hj;
+          if (wd) {
+            const double* Dr = a.D + rep * NN;
+            Di[r * (KC + 1) + kk] = (kg < N && ri < N) ? Dr[(long)ri * N + kg] : 0.0;
+            Dj[r * (KC + 1) + kk] = (kg < N && rj < N) ? Dr[(long)rj * N + kg] : 0.0;
+          }
         }
         for (int e = tid; e < KC * TS; e += NT) {
           const int kk = e / TS, b = e % TS;
@@ -832,6 +844,17 @@ __global__ void __launch_bounds__(NT) k_eldyn(EldynArgs a) {
           for (int kk = 0; kk < KC; kk += 2) {
             s0 = fma(Hx[ra * (KC + 1) + kk], Dx[kk * TSP + cb], s0);
             s1 = fma(Hx[ra * (KC + 1) + kk + 1], Dx[(kk + 1) * TSP + cb], s1);
+          }
+          if (wd) {   // + D S (q = 0, 1) or - D A (q = 2, 3)
+            const double* Dd = (q == 0 || q == 2) ? Di : Dj;
+            const double* Dy = (q == 0) ? Sj : (q == 1) ? Si : (q == 2) ? Aj : Ai;
+            double d0 = 0.0, d1 = 0.0;
+#pragma unroll 8
+            for (int kk = 0; kk < KC; kk += 2) {
+              d0 = fma(Dd[ra * (KC + 1) + kk], Dy[kk * TSP + cb], d0);
+              d1 = fma(Dd[ra * (KC + 1) + kk + 1], Dy[(kk + 1) * TSP + cb], d1);
+            }
+            s1 += (q < 2) ? (d0 + d1) : -(d0 + d1);
           }
           acc[u] = s0 + s1;
         }
@@ -911,18 +934,19 @@ __global__ void __launch_bounds__(NT) k_eldyn(EldynArgs a) {
   }
 }
 
-template <int TS, int NT>
-static int launch_eldyn_ts(rmgtd_ctx* ctx, EldynArgs& a) {
+template <int TS, int NT, bool WD>
+static int launch_eldyn_tsd(rmgtd_ctx* ctx, EldynArgs& a) {
   const int KC = 32;
-  const size_t smem = sizeof(double) * (2 * TS * (KC + 1) + 4 * KC * (TS + 1) + 4 * TS * (TS + 1));
-  static bool attr_set = false;
-  if (!attr_set) {
-    RMGTD_CUDA(ctx, cudaFuncSetAttribute(k_eldyn<TS, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  const size_t smem = sizeof(double) * (2 * TS * (KC + 1) + 4 * KC * (TS + 1) + 4 * TS * (TS + 1) +
+                                        (a.D ? 2 * TS * (KC + 1) : 0));
+  static size_t attr_set = 0;
+  if (attr_set < smem) {
+    RMGTD_CUDA(ctx, cudaFuncSetAttribute(k_eldyn<TS, NT, WD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem));
-    attr_set = true;
+    attr_set = smem;
   }
   int per_sm = 0;
-  RMGTD_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_eldyn<TS, NT>, NT, smem));
+  RMGTD_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_eldyn<TS, NT, WD>, NT, smem));
   if (per_sm < 1) return set_error(ctx, RMGTD_ECUDA, "commutator kernel does not fit on an SM");
   const int T = (a.N + TS - 1) / TS;
   const int total = T * (T + 1) / 2 * a.nrep;
@@ -942,9 +966,14 @@ static int launch_eldyn_ts(rmgtd_ctx* ctx, EldynArgs& a) {
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  RMGTD_CUDA(ctx, cudaLaunchKernelExC(&cfg, (const void*)k_eldyn<TS, NT>, args));
+  RMGTD_CUDA(ctx, cudaLaunchKernelExC(&cfg, (const void*)k_eldyn<TS, NT, WD>, args));
   ++ctx->launches;
   return RMGTD_OK;
+}
+
+template <int TS, int NT>
+static int launch_eldyn_ts(rmgtd_ctx* ctx, EldynArgs& a) {
+  return a.D ? launch_eldyn_tsd<TS, NT, true>(ctx, a) : launch_eldyn_tsd<TS, NT, false>(ctx, a);
 }
 
 // Commutator series of one replica on one thread-block cluster (N <= 64).  The C CTAs of the
@@ -957,7 +986,7 @@ static int launch_eldyn_ts(rmgtd_ctx* ctx, EldynArgs& a) {
 // and the replicas' clusters never wait on one another.
 namespace cg = cooperative_groups;
 
-template <int C>
+template <int C, bool WD>
 __global__ void __launch_bounds__(256, 1) k_eldyn_cluster(EldynArgs a) {
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
@@ -979,6 +1008,8 @@ __global__ void __launch_bounds__(256, 1) k_eldyn_cluster(EldynArgs a) {
   double* S1r = T2 + rows * N;       // [rows][N] running P_1
   double* A1r = S1r + rows * N;
   unsigned long long* mx = reinterpret_cast<unsigned long long*>(A1r + rows * N);  // [C]
+  double* Dr = reinterpret_cast<double*>(mx + C);   // [rows][N] rows of D (Omega_2 only)
+  constexpr bool wd = WD;
   __shared__ unsigned long long shm[8];
   __shared__ double c_sh;
 
@@ -995,6 +1026,7 @@ __global__ void __launch_bounds__(256, 1) k_eldyn_cluster(EldynArgs a) {
     Hr[e] = 0.5 * (Ha[o] + Hb[o]) + field_term(a, a.rep0 + rep, o);
     S1r[e] = S0[o];
     A1r[e] = A0[o];
+    if (wd) Dr[e] = a.D[rep * NN + o];
   }
   __syncthreads();
 
@@ -1027,6 +1059,13 @@ __global__ void __launch_bounds__(256, 1) k_eldyn_cluster(EldynArgs a) {
           const double* h = Hr + ii * N;
           const int m0 = hf ? half : 0, m1 = hf ? N : half;
           for (int m = m0; m < m1; ++m) sp = fma(h[m], X[m * N + j], sp);
+          if (wd) {   // + D S (T1) or - D A (T2)
+            const double* X2 = q ? Af : Sf;
+            const double* dr = Dr + ii * N;
+            double sd = 0.0;
+            for (int m = m0; m < m1; ++m) sd = fma(dr[m], X2[m * N + j], sd);
+            sp += q ? -sd : sd;
+          }
         }
         sp += __shfl_xor_sync(0xffffffffu, sp, 1);
         if (o < nout && hf == 0) (q ? T2 : T1)[e] = sp;
@@ -1111,6 +1150,7 @@ __global__ void __launch_bounds__(256, 1) k_eldyn_cluster(EldynArgs a) {
 
 template <int C>
 static int launch_eldyn_cluster(rmgtd_ctx* ctx, EldynArgs& a, size_t smem) {
+  const void* fn = a.D ? (const void*)k_eldyn_cluster<C, true> : (const void*)k_eldyn_cluster<C, false>;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(C, a.nrep);
   cfg.blockDim = dim3(256);
@@ -1124,14 +1164,14 @@ static int launch_eldyn_cluster(rmgtd_ctx* ctx, EldynArgs& a, size_t smem) {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   void* args[] = {&a};
-  RMGTD_CUDA(ctx, cudaLaunchKernelExC(&cfg, (const void*)k_eldyn_cluster<C>, args));
+  RMGTD_CUDA(ctx, cudaLaunchKernelExC(&cfg, fn, args));
   ++ctx->launches;
   return RMGTD_OK;
 }
 
-static size_t eldyn_cluster_smem(int N, int C) {
+static size_t eldyn_cluster_smem(int N, int C, bool with_d = false) {
   const int rows = (N + C - 1) / C;
-  return sizeof(double) * (2 * (size_t)N * N + 5 * (size_t)rows * N) +
+  return sizeof(double) * (2 * (size_t)N * N + (with_d ? 6 : 5) * (size_t)rows * N) +
          sizeof(unsigned long long) * C;
 }
 
@@ -1141,21 +1181,34 @@ static int eldyn_cluster_size(rmgtd_ctx* ctx) {
   if (ctx->eldyn_cluster >= 0) return ctx->eldyn_cluster;
   ctx->eldyn_cluster = 0;
   for (int C : {16, 8}) {
-    const size_t smem = eldyn_cluster_smem(ctx->N, C);
-    const void* fn = C == 16 ? (const void*)k_eldyn_cluster<16> : (const void*)k_eldyn_cluster<8>;
-    if (C == 16 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
-                       cudaSuccess) {
-      cudaGetLastError();
-      continue;
+    // both variants (with and without the Omega_2 rows) get the attributes; the probe uses the
+    // larger one
+    const size_t smem = eldyn_cluster_smem(ctx->N, C, true);
+    const void* fns[2] = {C == 16 ? (const void*)k_eldyn_cluster<16, false>
+                                  : (const void*)k_eldyn_cluster<8, false>,
+                          C == 16 ? (const void*)k_eldyn_cluster<16, true>
+                                  : (const void*)k_eldyn_cluster<8, true>};
+    const void* fn = fns[1];
+    bool ok = true;
+    for (const void* f : fns) {
+      if (C == 16 && cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+                         cudaSuccess) {
+        ok = false;
+        break;
+      }
+      cudaFuncAttributes fa;
+      if (cudaFuncGetAttributes(&fa, f) != cudaSuccess) {
+        ok = false;
+        break;
+      }
+      if ((size_t)fa.maxDynamicSharedSizeBytes < smem &&
+          cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+              cudaSuccess) {
+        ok = false;
+        break;
+      }
     }
-    cudaFuncAttributes fa;
-    if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) {
-      cudaGetLastError();
-      continue;
-    }
-    if ((size_t)fa.maxDynamicSharedSizeBytes < smem &&
-        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess) {
+    if (!ok) {
       cudaGetLastError();
       continue;
     }
@@ -1182,11 +1235,13 @@ static int eldyn_cluster_size(rmgtd_ctx* ctx) {
 
 int eldyn(rmgtd_ctx* ctx, const double* Ha, const double* Hb, long hstride, double tau,
           const double* S0, const double* A0, double* S1, double* A1, const RepCtl* ctl_in,
-          RepCtl* ctl_out, int rep0, int nreps, float* shat_out, const double* febar) {
+          RepCtl* ctl_out, int rep0, int nreps, float* shat_out, const double* febar,
+          const double* D) {
   if (nreps > 32) return set_error(ctx, RMGTD_EINVAL, "at most 32 replicas per expansion");
   EldynArgs a;
   a.fM = ctx->M;
   a.febar = febar;
+  a.D = D;
   a.N = ctx->N;
   a.nrep = nreps;
   a.rep0 = rep0;
@@ -1218,8 +1273,8 @@ int eldyn(rmgtd_ctx* ctx, const double* Ha, const double* Hb, long hstride, doub
       a.shat = shat_out;
       ctx->shat_fresh = 1;   // the density pass that follows skips k_shat32
     }
-    if (C == 16) return launch_eldyn_cluster<16>(ctx, a, eldyn_cluster_smem(ctx->N, 16));
-    if (C == 8) return launch_eldyn_cluster<8>(ctx, a, eldyn_cluster_smem(ctx->N, 8));
+    if (C == 16) return launch_eldyn_cluster<16>(ctx, a, eldyn_cluster_smem(ctx->N, 16, D));
+    if (C == 8) return launch_eldyn_cluster<8>(ctx, a, eldyn_cluster_smem(ctx->N, 8, D));
     ctx->shat_fresh = 0;
   }
   // GB300's float64 units (~2 FMA per clock and SM) bound the series: pick the tile size
@@ -1361,7 +1416,8 @@ int scf_control(rmgtd_ctx* ctx, const unsigned long long* errbits,
 }
 
 // ebar[r] = (E_r(t_k) + E_r(t_k + dt)) / 2 for the step that starts after k completed steps
-// (samples E_r(j dt), j < nsamp[r]; zero past them)
+// (samples E_r(j dt), j < nsamp[r]; zero past them), followed by the end values
+// ebar[3 nrep + 6 r + q] = E_r(t_k), ebar[3 nrep + 6 r + 3 + q] = E_r(t_k + dt) (Omega_2)
 __global__ void k_field_ebar(int nrep, int cap, const double* __restrict__ samples,
                              const int* __restrict__ nsamp, const long long* __restrict__ step_dev,
                              double* __restrict__ ebar) {
@@ -1373,6 +1429,8 @@ __global__ void k_field_ebar(int nrep, int cap, const double* __restrict__ sampl
   const double e0 = k < nsamp[r] ? E[3 * k + q] : 0.0;
   const double e1 = k + 1 < nsamp[r] ? E[3 * (k + 1) + q] : 0.0;
   ebar[t] = 0.5 * (e0 + e1);
+  ebar[3 * nrep + 6 * r + q] = e0;
+  ebar[3 * nrep + 6 * r + 3 + q] = e1;
 }
 
 int field_begin(rmgtd_ctx* ctx) {

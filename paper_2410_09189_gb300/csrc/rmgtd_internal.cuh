@@ -243,8 +243,33 @@ struct rmgtd_ctx {
   int fld_cap = 0;
   double* fld_samples = nullptr;
   int* fld_nsamp = nullptr;
-  double* fld_ebar = nullptr;
+  double* fld_ebar = nullptr;   // [nrep][3] mean, then [nrep][6] end values E(t_k), E(t_k + dt)
   std::vector<std::vector<double>> fld_host;
+  // non-orthogonal basis (opt.nonorthogonal): S^-1; the pass's S^-1 (Hbar + V) per replica;
+  // second-order Magnus term (opt.magnus_order 2): D per replica; both: [nrep][N*N]
+  double* Sinv = nullptr;
+  double* Gm = nullptr;
+  double* Dm = nullptr;
+  double* Hx0 = nullptr;        // scratch [nrep][N*N] x 2: H_0 + V_0, H_1 + V_1 (Omega_2)
+  double* Hx1 = nullptr;
+  // propagation on the grid (opt.grid_basis): occupied orbitals [nrep][2][N][Ng] (planar
+  // complex), the series' sum, term and H term; potentials V_0, V_-1, V_1, Vbar [nrep][Ng];
+  // the step's mean field [nrep][3]; active flags; Gram / Cholesky scratch [3][N*N];
+  // observable partials
+  double* gp_psi = nullptr;
+  double* gp_psi1 = nullptr;
+  double* gp_t = nullptr;
+  double* gp_ht = nullptr;
+  double* gp_v0 = nullptr;
+  double* gp_vm1 = nullptr;
+  double* gp_v1 = nullptr;
+  double* gp_vbar = nullptr;
+  double* gp_ebar = nullptr;
+  int* gp_active = nullptr;
+  double* gp_gram = nullptr;
+  double* gp_obs = nullptr;
+  std::vector<double> gp_obs_host;
+  long long gp_steps = 0;
   long long* step_dev = nullptr;
 
   // learned seed of the SCF loop (attached network; buffers allocated at attach)
@@ -419,10 +444,29 @@ int add_fields(rmgtd_ctx* ctx, const double* a, const double* b, double* out, lo
 // phi32t <- phi32 in 32-point tiles (layout above)
 int tile_orbitals(rmgtd_ctx* ctx);
 // febar (may be NULL): [nrep][3] field of the step, Hbar += sum_q febar[r][q] M_q
+// D (may be NULL): [nreps][N*N] real antisymmetric Omega_2 / tau per replica (pre-offset like
+// Ha), the series then multiplies by Hbar + i D
 int eldyn(rmgtd_ctx* ctx, const double* Ha, const double* Hb, long hstride, double tau,
           const double* S0, const double* A0, double* S1, double* A1, const RepCtl* ctl_in,
           RepCtl* ctl_out, int rep0, int nreps,
-          float* shat_out = nullptr, const double* febar = nullptr);
+          float* shat_out = nullptr, const double* febar = nullptr, const double* D = nullptr);
+// k_magnus.cu: the non-orthogonal basis and the second-order Magnus term
+// set-up of the non-orthogonal basis: Sinv = S^-1 and P_0 = L^-T diag(f) L^-1 for every replica
+int nonorth_setup(rmgtd_ctx* ctx);
+// per SCF pass, before the series: G = S^-1 (Hbar + V) into ctx->Gm (non-orthogonal basis) and
+// D = (dt/12)[H_0 + V_0, H_1 + V_1] into ctx->Dm (Omega_2); *Ha/*Hb/*hstride/*febar/*D are the
+// arguments the series then takes
+int magnus_prepare(rmgtd_ctx* ctx, const double** Ha, const double** Hb, long* hstride,
+                   const double** febar, const double** D);
+// G = S^-1 M_axis into ctx->Gm for a kick in the non-orthogonal basis
+int nonorth_kick_matrix(rmgtd_ctx* ctx, int axis);
+// k_gridprop.cu: propagation of the occupied orbitals on the grid (opt.grid_basis)
+int gridprop_setup(rmgtd_ctx* ctx);
+int gridprop_kick(rmgtd_ctx* ctx, int rep, int axis, double kappa);
+// one time step of every replica; st (may be NULL): nrep entries
+int gridprop_step(rmgtd_ctx* ctx, rmgtd_stats* st);
+int gridprop_observables(rmgtd_ctx* ctx);
+void gridprop_read(const rmgtd_ctx* ctx, int rep, double* d3, double* E, double* ne);
 // the step's mean field ebar from the samples (no-op without a field)
 int field_begin(rmgtd_ctx* ctx);
 int step_begin(rmgtd_ctx* ctx);
@@ -435,6 +479,9 @@ int step_end(rmgtd_ctx* ctx);
 int observables(rmgtd_ctx* ctx);
 int subspace_update(rmgtd_ctx* ctx, double alpha, double* err_dev);
 int orthonormalize(rmgtd_ctx* ctx);
+// in-place lower Cholesky factor of the N x N matrix S (one block; status <- EINVAL when a
+// pivot is not positive)
+__global__ void k_cholesky(int N, double* __restrict__ S, int* status);
 // k_poisson.cu
 int setup_multigrid(rmgtd_ctx* ctx);
 int poisson_red_cap(int num_sms, int red_blocks);

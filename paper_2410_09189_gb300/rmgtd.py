@@ -61,6 +61,8 @@ class COptions(ctypes.Structure):
         ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", ctypes.c_void_p),
         ("subspace_scf", ctypes.c_int), ("subspace_mix", ctypes.c_double),
         ("subspace_tol", ctypes.c_double), ("mixed_poisson_tol", ctypes.c_double),
+        ("magnus_order", ctypes.c_int), ("nonorthogonal", ctypes.c_int),
+        ("grid_basis", ctypes.c_int),
     ]
 
 
@@ -132,6 +134,8 @@ def load_library(path: Optional[str] = None):
         "rmgtd_selftest_barrier_timeout": (i, [vp, ctypes.c_uint, _c_int_p]),
         "rmgtd_get_hartree_preconditioner": (i, [vp, _c_int_p]),
         "rmgtd_set_field": (i, [vp, i, _c_double_p, i]),
+        "rmgtd_spectrum": (i, [_c_double_p, i, ctypes.c_long, d, d, d, _c_double_p, i,
+                               _c_double_p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -159,7 +163,8 @@ class Context:
                  poisson_max_iter: int = 200, use_graph: bool = True,
                  stream: Optional[int] = None, torch_alloc: bool = True,
                  subspace_scf: int = 0, subspace_mix: float = 0.3, subspace_tol: float = 1e-10,
-                 mixed_poisson_tol: float = 0.0):
+                 mixed_poisson_tol: float = 0.0, magnus_order: int = 1,
+                 nonorthogonal: bool = False, grid_basis: bool = False):
         import torch
 
         lib = load_library()
@@ -215,6 +220,11 @@ class Context:
         opt.subspace_scf, opt.subspace_mix = int(subspace_scf), float(subspace_mix)
         opt.subspace_tol = float(subspace_tol)
         opt.mixed_poisson_tol = float(mixed_poisson_tol)
+        opt.magnus_order = int(magnus_order)
+        opt.nonorthogonal = 1 if nonorthogonal else 0
+        opt.grid_basis = 1 if grid_basis else 0
+        if nonorthogonal:
+            opt.orthonormalize = 0
         if stream is None:
             stream = torch.cuda.current_stream().cuda_stream
         self.stream = int(stream)
@@ -542,3 +552,17 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def spectrum(dipole, dt: float, kappa: float, gamma: float, omega) -> np.ndarray:
+    """Dipole strength function S(omega) of the kicked runs (rmgtd_spectrum): `dipole` is
+    (nq, nt), row q the component along the kick of the run kicked along q."""
+    lib = load_library()
+    d = np.ascontiguousarray(np.atleast_2d(np.asarray(dipole, dtype=np.float64)))
+    om = np.ascontiguousarray(np.asarray(omega, dtype=np.float64).reshape(-1))
+    out = np.empty(om.size, dtype=np.float64)
+    rc = lib.rmgtd_spectrum(_dptr(d), int(d.shape[0]), int(d.shape[1]), float(dt), float(kappa),
+                            float(gamma), _dptr(om), int(om.size), _dptr(out))
+    if rc != OK:
+        raise RmgtdError(rc, lib.rmgtd_last_error(None).decode())
+    return out
