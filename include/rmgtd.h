@@ -144,7 +144,10 @@ typedef struct {
                               basis's H_new - H_1 is diagonal); after the loop a float64
                               Cholesky re-orthonormalisation.  The kick is the phase
                               e^{-i kappa q}.  phi0 holds the occupied orbitals: nvirt = 0,
-                              precision FP64, magnus_order 1, nonorthogonal 0, subspace_scf 0.
+                              magnus_order 1, nonorthogonal 0, subspace_scf 0.  Precision FP64:
+                              every step in float64; MIXED: the series terms in float32 (the
+                              orbitals, their sum, the fields and the re-orthonormalisation
+                              stay float64).
                               rmgtd_kick / set_field / step / dipole / energy / density act on
                               the orbitals (stats: passes, terms of the orbital series,
                               H_err = max|V_new - V_1|); the matrix, save / load, batch,

@@ -582,7 +582,7 @@ static int create_impl(const rmgtd_system* sys, const rmgtd_options* opt, rmgtd_
     rc = gridprop_setup(ctx);
     if (rc) return rc;
   }
-  if (opt->precision == RMGTD_PREC_MIXED) {
+  if (opt->precision == RMGTD_PREC_MIXED && !opt->grid_basis) {
     // reference state of the mixed path: the float64 set-up state (all replicas start in it)
     const size_t fsz = sizeof(float) * Ng;
     ctx->phi32 = (float*)A(fsz * N);
@@ -692,11 +692,9 @@ int rmgtd_create(const rmgtd_system* sys, const rmgtd_options* opt_in, rmgtd_ctx
     return set_error(nullptr, RMGTD_EINVAL,
                      "nonorthogonal needs orthonormalize = 0, subspace_scf = 0 and magnus_order 1");
   if (opt.grid_basis &&
-      (sys->nvirt != 0 || opt.precision != RMGTD_PREC_FP64 || opt.magnus_order != 1 ||
-       opt.nonorthogonal || opt.subspace_scf > 0))
+      (sys->nvirt != 0 || opt.magnus_order != 1 || opt.nonorthogonal || opt.subspace_scf > 0))
     return set_error(nullptr, RMGTD_EINVAL,
-                     "grid_basis needs nvirt = 0, FP64, magnus_order 1, nonorthogonal 0 and "
-                     "subspace_scf 0");
+                     "grid_basis needs nvirt = 0, magnus_order 1, nonorthogonal 0 and subspace_scf 0");
   rmgtd_ctx* ctx = new rmgtd_ctx();
   int rc = create_impl(sys, &opt, ctx);
   if (rc != RMGTD_OK) {
@@ -922,7 +920,7 @@ int rmgtd_step(rmgtd_ctx* ctx, int nsteps, rmgtd_stats* stats) {
       const int rc = gridprop_step(ctx, stats ? stats + (long)i * ctx->nrep : nullptr);
       if (rc) return rc;
     }
-    return RMGTD_OK;
+    return ph_flush(ctx);
   }
   if (ctx->opt.use_graph && !ctx->step_exec) {
     int rc = build_step_graph(ctx);

@@ -251,13 +251,14 @@ __global__ void k_kb_project(const T* __restrict__ x, int ncols, long Ng, int nx
   const int p = blockIdx.x, j = blockIdx.y;
   const int x0 = box[6 * p], y0 = box[6 * p + 1], z0 = box[6 * p + 2];
   const int bx = box[6 * p + 3], by = box[6 * p + 4], bz = box[6 * p + 5];
-  const long nb = (long)bx * by * bz;
+  const int nb = bx * by * bz, bxy = bx * by;   // a box holds fewer than 2^31 points
   const double* b = val + off[p];
   const T* xc = x + (long)j * Ng;
   __shared__ double sh[32];
   double sr = 0.0, si = 0.0;
-  for (long e = threadIdx.x; e < nb; e += blockDim.x) {
-    const long g = ((long)(z0 + e / ((long)bx * by)) * ny + (y0 + (e / bx) % by)) * nx + x0 + e % bx;
+  for (int e = threadIdx.x; e < nb; e += blockDim.x) {
+    const int ez = e / bxy, exy = e - ez * bxy, ey = exy / bx, ex = exy - ey * bx;
+    const long g = ((long)(z0 + ez) * ny + (y0 + ey)) * nx + x0 + ex;
     const T xv = xc[g];
     if constexpr (sizeof(T) == 2 * sizeof(typename Elem<T>::S)) {
       sr += b[e] * (double)xv.x;
@@ -281,15 +282,15 @@ __global__ void k_kb_apply(T* __restrict__ out, int ncols, long Ng, int nx, int 
                            const double* __restrict__ Ekb, const double* __restrict__ coef) {
   const int x0 = box[6 * p], y0 = box[6 * p + 1], z0 = box[6 * p + 2];
   const int bx = box[6 * p + 3], by = box[6 * p + 4], bz = box[6 * p + 5];
-  const long nb = (long)bx * by * bz;
+  const int nb = bx * by * bz, bxy = bx * by;
   const double* b = val + off[p];
   const int j = blockIdx.y;
   const double cr = Ekb[p] * coef[(2L * j) * nproj + p];
   const double ci = Ekb[p] * coef[(2L * j + 1) * nproj + p];
   T* oc = out + (long)j * Ng;
-  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < nb;
-       e += (long)gridDim.x * blockDim.x) {
-    const long g = ((long)(z0 + e / ((long)bx * by)) * ny + (y0 + (e / bx) % by)) * nx + x0 + e % bx;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nb; e += gridDim.x * blockDim.x) {
+    const int ez = e / bxy, exy = e - ez * bxy, ey = exy / bx, ex = exy - ey * bx;
+    const long g = ((long)(z0 + ez) * ny + (y0 + ey)) * nx + x0 + ex;
     if constexpr (sizeof(T) == 2 * sizeof(typename Elem<T>::S)) {
       T o = oc[g];
       o.x += (typename Elem<T>::S)(cr * b[e]);
@@ -341,6 +342,23 @@ static int apply_h_t(rmgtd_ctx* ctx, const T* x, T* hx, int ncols, const double*
       RMGTD_LAUNCH(ctx, "k_kb_apply");
     }
   }
+  return RMGTD_OK;
+}
+
+int kb_project_cols(rmgtd_ctx* ctx, const void* x, int ncols, int dtype, double* coef) {
+  const int np = ctx->nproj;
+  if (np == 0 || ncols == 0) return RMGTD_OK;
+  const dim3 grid(np, ncols);
+  if (dtype == RMGTD_F64)
+    k_kb_project<double><<<grid, kThreads, 0, ctx->stream>>>(
+        (const double*)x, ncols, ctx->Ng, ctx->nx, ctx->ny, ctx->pbox, ctx->poff, ctx->pval, ctx->h3, coef);
+  else if (dtype == RMGTD_F32)
+    k_kb_project<float><<<grid, kThreads, 0, ctx->stream>>>(
+        (const float*)x, ncols, ctx->Ng, ctx->nx, ctx->ny, ctx->pbox, ctx->poff, ctx->pval, ctx->h3, coef);
+  else
+    return set_error(ctx, RMGTD_EINVAL, "kb_project_cols: real columns only");
+  ++ctx->launches;
+  RMGTD_LAUNCH(ctx, "k_kb_project");
   return RMGTD_OK;
 }
 

@@ -7,13 +7,18 @@
 // re-orthonormalisation in float64.  The kick is the pointwise phase e^{-i kappa q}.
 //
 // Layout: per replica the orbitals are planar complex, [2][nocc][Ng] (real plane, then
-// imaginary plane), so the real stencil / KB operator applies to both planes as 2 nocc real
-// columns.  Float64 throughout; the host drives the term and pass loops (one small read-back
-// per term for the stopping test).
+// imaginary plane).  The state psi, the series' sum psi_1, the potentials and the
+// re-orthonormalisation are float64; the series terms are float64 (FP64 path) or float32
+// (mixed path: the terms of a smooth orbital shrink fast, and a term's float32 rounding is
+// carried forward by the remaining, unitary, series, so the sum keeps ~1e-7 of |psi|).  One
+// fused kernel per term: the 12th-order stencil of both planes, the potential, the KB part
+// from per-point projector lists, the update psi_1 += t and the stopping maximum.  The host
+// drives the term and pass loops (one small read-back per term for the stopping test).
 #include <cstring>
 #include <utility>
 
 #include "rmgtd_internal.cuh"
+#include "tc_common.cuh"
 
 namespace rmgtd {
 
@@ -59,40 +64,345 @@ __global__ void k_gp_extrap(const double* __restrict__ a, const double* __restri
     out[e] = 2.0 * a[e] - b[e];
 }
 
-// vbar_r = (V0_r + V1_r)/2 + sum_q ebar_rq q
-__global__ void k_gp_vbar(const double* __restrict__ v0, const double* __restrict__ v1,
-                          const double* __restrict__ ebar, double* __restrict__ vbar, long Ng,
-                          int nx, int ny, int nz, double h) {
+// vtot_r = V_ion + (V0_r + V1_r)/2 + sum_q ebar_rq q, in the terms' precision
+template <typename T>
+__global__ void k_gp_vtot(const double* __restrict__ vion, const double* __restrict__ v0,
+                          const double* __restrict__ v1, const double* __restrict__ ebar,
+                          T* __restrict__ vtot, long Ng, int nx, int ny, int nz, double h) {
   const int r = blockIdx.y;
   const double ex = ebar[3 * r], ey = ebar[3 * r + 1], ez = ebar[3 * r + 2];
   for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < Ng; g += (long)gridDim.x * blockDim.x) {
     const long o = r * Ng + g;
-    double v = 0.5 * (v0[o] + v1[o]);
+    double v = vion[g] + 0.5 * (v0[o] + v1[o]);
     if (ex != 0.0 || ey != 0.0 || ez != 0.0)
       v += ex * coord_of(g, 0, nx, ny, nz, h) + ey * coord_of(g, 1, nx, ny, nz, h) +
            ez * coord_of(g, 2, nx, ny, nz, h);
-    vbar[o] = v;
+    vtot[o] = (T)v;
   }
 }
 
-// one series term on one replica: t <- (-i c) Ht, psi1 += t, errbits <- max |t|^2
-__global__ void k_gp_term(const double* __restrict__ Ht, double* __restrict__ t,
-                          double* __restrict__ psi1, long plane, double c,
-                          unsigned long long* __restrict__ errbits) {
-  __shared__ double sh[32];
-  double emax = 0.0;
-  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < plane;
+// start of a pass for the active replicas: psi_1 = psi, t = psi (in the terms' precision)
+template <typename T>
+__global__ void k_gp_start(const double* __restrict__ psi, double* __restrict__ psi1,
+                           T* __restrict__ t, long rplane, const int* __restrict__ active) {
+  const int r = blockIdx.y;
+  if (!active[r]) return;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < rplane;
        e += (long)gridDim.x * blockDim.x) {
-    const double hr = Ht[e], hi = Ht[plane + e];
-    const double tr = c * hi, ti = -c * hr;   // -i c (hr + i hi)
-    t[e] = tr;
-    t[plane + e] = ti;
-    psi1[e] += tr;
-    psi1[plane + e] += ti;
-    emax = fmax(emax, tr * tr + ti * ti);
+    const long o = r * rplane + e;
+    psi1[o] = psi[o];
+    t[o] = (T)psi[o];
+  }
+}
+
+// One term of the orbital series for orbital n of replica r over a z-range:
+//   t_out = (-i c) (T + V + V_NL) t_in,  psi_1 += t_out,  errbits_r <- max |t_out|^2,
+// c = dt / k.  Block BX x BY over an x-y tile, marching along z with each thread's z-column
+// (both planes) in registers; the x-y neighbourhood of every plane staged in shared memory
+// with a 6-point halo (zero outside the grid: Dirichlet ghosts).  The KB part reads the
+// point's projector list (E_p beta_p(r)) and the projections of t_in.
+template <typename T, int BX, int BY>
+__global__ void __launch_bounds__(BX * BY)
+k_gp_term_fused(const T* __restrict__ tin, T* __restrict__ tout, double* __restrict__ psi1,
+                const T* __restrict__ vtot, const int* __restrict__ kb_row,
+                const int* __restrict__ kb_p, const double* __restrict__ kb_val,
+                const double* __restrict__ coef, int np, int nocc, int nx, int ny, int nz,
+                int zchunk, int nzc, double cscale, double c, const int* __restrict__ sact,
+                unsigned long long* __restrict__ errbits) {
+  constexpr int R = kFdRadius;
+  constexpr int TX = BX + 2 * R, TY = BY + 2 * R;
+  __shared__ T sre[TY][TX];
+  __shared__ T sim[TY][TX];
+  __shared__ double sh[32];
+  const int col = blockIdx.z / nzc;   // rep * nocc + n
+  const int rep = col / nocc, n = col - rep * nocc;
+  if (!sact[rep]) return;             // uniform over the block
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
+  const int z0 = (blockIdx.z % nzc) * zchunk, z1 = min(nz, z0 + zchunk);
+  const int ix = blockIdx.x * BX + tx, iy = blockIdx.y * BY + ty;
+  const bool in_xy = ix < nx && iy < ny;
+  const long plane = (long)nx * ny, Ng = plane * nz, oplane = (long)nocc * Ng;
+  const long base = (long)rep * 2 * oplane + (long)n * Ng;
+  const T* xr = tin + base;
+  const T* xi = xr + oplane;
+  T* yr = tout + base;
+  T* yi = yr + oplane;
+  double* pr = psi1 + base;
+  double* pim = pr + oplane;
+  const T* v = vtot + (long)rep * Ng;
+  const double* cre = coef + (long)(2 * (rep * 2 * nocc + n)) * np;          // column re
+  const double* cim = coef + (long)(2 * (rep * 2 * nocc + nocc + n)) * np;   // column im
+  T cm[R + 1];
+#pragma unroll
+  for (int m = 1; m <= R; ++m) cm[m] = (T)(fd_coef(m) * cscale);
+  const T c0 = (T)(3.0 * fd_coef(0) * cscale);
+  T qr[2 * R + 1], qi[2 * R + 1];
+#pragma unroll
+  for (int k = 0; k < 2 * R; ++k) {
+    const int z = z0 - R + k;
+    const bool ok = in_xy && z >= 0 && z < nz;
+    const long g = (long)z * plane + (long)iy * nx + ix;
+    qr[k] = ok ? xr[g] : (T)0;
+    qi[k] = ok ? xi[g] : (T)0;
+  }
+  double emax = 0.0;
+  for (int z = z0; z < z1; ++z) {
+    {
+      const int zz = z + R;
+      const bool ok = in_xy && zz < nz;
+      const long g = (long)zz * plane + (long)iy * nx + ix;
+      qr[2 * R] = ok ? xr[g] : (T)0;
+      qi[2 * R] = ok ? xi[g] : (T)0;
+    }
+    for (int e = tid; e < TX * TY; e += BX * BY) {
+      const int ly = e / TX, lx = e - ly * TX;
+      const int gx = blockIdx.x * BX + lx - R, gy = blockIdx.y * BY + ly - R;
+      const bool corner = (lx < R || lx >= BX + R) && (ly < R || ly >= BY + R);
+      T a = (T)0, b = (T)0;
+      if (!corner && gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
+        const long g = (long)z * plane + (long)gy * nx + gx;
+        a = xr[g];
+        b = xi[g];
+      }
+      sre[ly][lx] = a;
+      sim[ly][lx] = b;
+    }
+    __syncthreads();
+    if (in_xy) {
+      const long g = (long)z * plane + (long)iy * nx + ix;
+      T ar = c0 * qr[R], ai = c0 * qi[R];
+#pragma unroll
+      for (int m = 1; m <= R; ++m) {
+        const T sr = (sre[ty + R][tx + R + m] + sre[ty + R][tx + R - m]) +
+                     (sre[ty + R + m][tx + R] + sre[ty + R - m][tx + R]) + (qr[R + m] + qr[R - m]);
+        const T si = (sim[ty + R][tx + R + m] + sim[ty + R][tx + R - m]) +
+                     (sim[ty + R + m][tx + R] + sim[ty + R - m][tx + R]) + (qi[R + m] + qi[R - m]);
+        ar = fma(cm[m], sr, ar);
+        ai = fma(cm[m], si, ai);
+      }
+      const T vv = v[g];
+      ar = fma(vv, qr[R], ar);
+      ai = fma(vv, qi[R], ai);
+      if (kb_row) {
+        double kr = 0.0, ki = 0.0;
+        for (int e = kb_row[g]; e < kb_row[g + 1]; ++e) {
+          const int p = kb_p[e];
+          const double w = kb_val[e];
+          kr = fma(w, cre[p], kr);
+          ki = fma(w, cim[p], ki);
+        }
+        ar += (T)kr;
+        ai += (T)ki;
+      }
+      const T nr = (T)c * ai, ni = -(T)c * ar;   // -i c (ar + i ai)
+      yr[g] = nr;
+      yi[g] = ni;
+      pr[g] += (double)nr;
+      pim[g] += (double)ni;
+      emax = fmax(emax, (double)nr * (double)nr + (double)ni * (double)ni);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 2 * R; ++k) {
+      qr[k] = qr[k + 1];
+      qi[k] = qi[k + 1];
+    }
   }
   emax = block_max(emax, sh);
-  if (threadIdx.x == 0) atomic_max_nonneg(errbits, emax);
+  if (tid == 0) atomic_max_nonneg(&errbits[rep], emax);
+}
+
+// The same term with the x-y tiles streamed by TMA: thread 0 keeps kGtS planes of the chunk
+// in flight, each a pair of tiles (real, imaginary) of (BX + 16) x (BY + 12) points starting at
+// (x0 - 8, y0 - 6) -- the x start rounded down to a 16-byte boundary -- with zero fill outside
+// the grid (the Dirichlet ghosts).  Each thread's z-column stays in registers, refilled by a
+// coalesced load issued one plane ahead.  One block barrier per plane; waits are bounded
+// (status <- ETIMEOUT, the copies in flight are waited for before the block leaves).
+constexpr int kGtS = 6;     // planes in flight
+constexpr int kGtXO = 8;    // x offset of the interior in a tile
+
+template <typename T, int BX, int BY>
+__host__ __device__ constexpr int gt_tile_elems() {
+  return (BY + 2 * kFdRadius) * (BX + 2 * kGtXO);
+}
+
+template <typename T, int BX, int BY>
+__host__ __device__ constexpr size_t gt_smem_bytes() {
+  return sizeof(T) * 2 * gt_tile_elems<T, BX, BY>() * kGtS + sizeof(uint64_t) * kGtS + 1024;
+}
+
+template <typename T, int BX, int BY>
+__global__ void __launch_bounds__(BX * BY)
+k_gp_term_tma(const __grid_constant__ CUtensorMap tm_in, const T* __restrict__ tin,
+              T* __restrict__ tout, double* __restrict__ psi1, const T* __restrict__ vtot,
+              const int* __restrict__ kb_row, const int* __restrict__ kb_p,
+              const double* __restrict__ kb_val, const double* __restrict__ coef, int np, int nocc,
+              int nx, int ny, int nz, int zchunk, int nzc, double cscale, double c,
+              const int* __restrict__ sact, unsigned long long* __restrict__ errbits,
+              int* __restrict__ status) {
+  constexpr int R = kFdRadius;
+  constexpr int TW = BX + 2 * kGtXO;            // tile row length
+  constexpr int TE = gt_tile_elems<T, BX, BY>();
+  constexpr uint32_t kBytes = 2u * TE * sizeof(T);
+  extern __shared__ unsigned char gt_raw[];
+  unsigned char* gt_smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(gt_raw) + 1023) & ~(uintptr_t)1023);
+  T* tiles = reinterpret_cast<T*>(gt_smem);     // [kGtS][2][BY + 2R][TW]
+  uint64_t* full = reinterpret_cast<uint64_t*>(gt_smem + sizeof(T) * 2 * TE * kGtS);
+  __shared__ double sh[32];
+  const int col = blockIdx.z / nzc;   // rep * nocc + n
+  const int rep = col / nocc, n = col - rep * nocc;
+  if (!sact[rep]) return;             // uniform over the block, before any barrier
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
+  const int z0 = (blockIdx.z % nzc) * zchunk, z1 = min(nz, z0 + zchunk), nzb = z1 - z0;
+  const int ix = blockIdx.x * BX + tx, iy = blockIdx.y * BY + ty;
+  const bool in_xy = ix < nx && iy < ny;
+  const long plane = (long)nx * ny, Ng = plane * nz, oplane = (long)nocc * Ng;
+  const long base = (long)rep * 2 * oplane + (long)n * Ng;
+  const int cre_col = rep * 2 * nocc + n, cim_col = cre_col + nocc;   // tensor-map columns
+  const int xs = blockIdx.x * BX - kGtXO, ys = blockIdx.y * BY - R;
+  if (tid == 0) {
+    for (int s = 0; s < kGtS; ++s) tc::mbar_init(&full[s], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    for (int i = 0; i < min(kGtS, nzb); ++i) {
+      T* dst = tiles + (size_t)i * 2 * TE;
+      const uint32_t bar = tc::saddr(&full[i]);
+      tc::mbar_expect_tx(bar, kBytes);
+      tc::tma_load_4d(tc::saddr(dst), &tm_in, xs, ys, z0 + i, cre_col, bar);
+      tc::tma_load_4d(tc::saddr(dst + TE), &tm_in, xs, ys, z0 + i, cim_col, bar);
+    }
+  }
+  const T* xr = tin + base;
+  const T* xi = xr + oplane;
+  T* yr = tout + base;
+  T* yi = yr + oplane;
+  double* pr = psi1 + base;
+  double* pim = pr + oplane;
+  const T* v = vtot + (long)rep * Ng;
+  const double* cre = coef + (long)(2 * cre_col) * np;
+  const double* cim = coef + (long)(2 * cim_col) * np;
+  T cm[R + 1];
+#pragma unroll
+  for (int m = 1; m <= R; ++m) cm[m] = (T)(fd_coef(m) * cscale);
+  const T c0 = (T)(3.0 * fd_coef(0) * cscale);
+  const long gxy = (long)iy * nx + ix;
+  T qr[2 * R + 1], qi[2 * R + 1];
+#pragma unroll
+  for (int k = 0; k < 2 * R; ++k) {   // planes z0 - R .. z0 + R - 1 of the column
+    const int z = z0 - R + k;
+    const bool okz = in_xy && z >= 0 && z < nz;
+    qr[k] = okz ? xr[(long)z * plane + gxy] : (T)0;
+    qi[k] = okz ? xi[(long)z * plane + gxy] : (T)0;
+  }
+  T nr_next, ni_next;   // plane z + R, loaded one iteration ahead
+  {
+    const int z = z0 + R;
+    const bool okz = in_xy && z < nz;
+    nr_next = okz ? xr[(long)z * plane + gxy] : (T)0;
+    ni_next = okz ? xi[(long)z * plane + gxy] : (T)0;
+  }
+  // the point's psi_1, potential and KB list range, loaded one plane ahead
+  double p1r = 0.0, p1i = 0.0;
+  T vv = (T)0;
+  int kb0 = 0, kb1 = 0;
+  if (in_xy) {
+    const long g = (long)z0 * plane + gxy;
+    p1r = pr[g];
+    p1i = pim[g];
+    vv = v[g];
+    if (kb_row) {
+      kb0 = kb_row[g];
+      kb1 = kb_row[g + 1];
+    }
+  }
+  __syncthreads();   // barriers initialised before anyone waits
+  const int lx = tx + kGtXO, ly = ty + R;
+  T emax = (T)0;
+  bool ok = true;
+  int i = 0;
+  for (; i < nzb; ++i) {
+    qr[2 * R] = nr_next;
+    qi[2 * R] = ni_next;
+    const double c_p1r = p1r, c_p1i = p1i;
+    const T c_vv = vv;
+    const int c_kb0 = kb0, c_kb1 = kb1;
+    {   // next plane's column value and point data
+      const int z = z0 + i + R + 1;
+      const bool okz = in_xy && z < nz;
+      nr_next = okz ? xr[(long)z * plane + gxy] : (T)0;
+      ni_next = okz ? xi[(long)z * plane + gxy] : (T)0;
+      if (in_xy && i + 1 < nzb) {
+        const long g = (long)(z0 + i + 1) * plane + gxy;
+        p1r = pr[g];
+        p1i = pim[g];
+        vv = v[g];
+        if (kb_row) {
+          kb0 = kb_row[g];
+          kb1 = kb_row[g + 1];
+        }
+      }
+    }
+    if (!tc::mbar_wait(&full[i % kGtS], (i / kGtS) & 1)) ok = false;
+    const T* tr = tiles + (size_t)(i % kGtS) * 2 * TE;
+    const T* ti = tr + TE;
+    if (in_xy && ok) {
+      const long g = (long)(z0 + i) * plane + gxy;
+      T ar = c0 * qr[R], ai = c0 * qi[R];
+#pragma unroll
+      for (int m = 1; m <= R; ++m) {
+        const T sr = (tr[ly * TW + lx + m] + tr[ly * TW + lx - m]) +
+                     (tr[(ly + m) * TW + lx] + tr[(ly - m) * TW + lx]) + (qr[R + m] + qr[R - m]);
+        const T si = (ti[ly * TW + lx + m] + ti[ly * TW + lx - m]) +
+                     (ti[(ly + m) * TW + lx] + ti[(ly - m) * TW + lx]) + (qi[R + m] + qi[R - m]);
+        ar = fma(cm[m], sr, ar);
+        ai = fma(cm[m], si, ai);
+      }
+      ar = fma(c_vv, qr[R], ar);
+      ai = fma(c_vv, qi[R], ai);
+      if (c_kb1 > c_kb0) {
+        double kr = 0.0, ki = 0.0;
+        for (int e = c_kb0; e < c_kb1; ++e) {
+          const int p = kb_p[e];
+          const double w = kb_val[e];
+          kr = fma(w, cre[p], kr);
+          ki = fma(w, cim[p], ki);
+        }
+        ar += (T)kr;
+        ai += (T)ki;
+      }
+      const T nr = (T)c * ai, ni = -(T)c * ar;   // -i c (ar + i ai)
+      yr[g] = nr;
+      yi[g] = ni;
+      pr[g] = c_p1r + (double)nr;
+      pim[g] = c_p1i + (double)ni;
+      emax = fmax(emax, nr * nr + ni * ni);   // in the terms' precision (a stopping test)
+    }
+    // every thread is done with slot i % kGtS (or a wait gave up)
+    if (__syncthreads_or(!ok)) break;
+    if (tid == 0 && i + kGtS < nzb) {   // refill the slot with plane i + kGtS
+      const int j = i + kGtS;
+      T* dst = tiles + (size_t)(j % kGtS) * 2 * TE;
+      const uint32_t bar = tc::saddr(&full[j % kGtS]);
+      tc::mbar_expect_tx(bar, kBytes);
+      tc::tma_load_4d(tc::saddr(dst), &tm_in, xs, ys, z0 + j, cre_col, bar);
+      tc::tma_load_4d(tc::saddr(dst + TE), &tm_in, xs, ys, z0 + j, cim_col, bar);
+    }
+#pragma unroll
+    for (int k = 0; k < 2 * R; ++k) {
+      qr[k] = qr[k + 1];
+      qi[k] = qi[k + 1];
+    }
+  }
+  if (i < nzb) {   // gave up: wait (bounded) for every issued copy, then leave
+    if (tid == 0) {
+      atomicCAS(status, 0, (int)RMGTD_ETIMEOUT);
+      const int issued = min(nzb, i + kGtS);
+      for (int w = 0; w < issued; ++w) tc::mbar_wait(&full[w % kGtS], (w / kGtS) & 1);
+    }
+    return;
+  }
+  const double bm = block_max((double)emax, sh);
+  if (tid == 0) atomic_max_nonneg(&errbits[rep], bm);
 }
 
 // rho_r = sum_n f_n |psi_n|^2
@@ -190,6 +500,143 @@ __global__ void k_gp_fsubst(int nocc, long Ng, const double* __restrict__ lre,
   }
 }
 
+// Gram G_nm = sum_g psi_n conj(psi_m) of a few orbitals (n <= m pairs): every block stages
+// kZgP points of all orbitals (both planes) in shared memory and each thread accumulates its
+// pairs over the block's chunks; per-block partials [block][pair][2], reduced in a fixed order.
+constexpr int kZgP = 32, kZgMaxPairsPerThread = 10, kZgThreads = 256;
+constexpr int kZgMaxN = 64;   // 2080 pairs <= 256 x 10 and 2 x 64 x 32 doubles of staging
+
+__global__ void __launch_bounds__(kZgThreads)
+k_gp_zgram_partial(int nocc, long Ng, const double* __restrict__ re, const double* __restrict__ im,
+                   double* __restrict__ part) {
+  __shared__ double sr[kZgMaxN][kZgP];
+  __shared__ double si[kZgMaxN][kZgP];
+  const int npairs = nocc * (nocc + 1) / 2;
+  double ar[kZgMaxPairsPerThread], ai[kZgMaxPairsPerThread];
+  int pn[kZgMaxPairsPerThread], pm[kZgMaxPairsPerThread];
+#pragma unroll
+  for (int u = 0; u < kZgMaxPairsPerThread; ++u) {
+    ar[u] = ai[u] = 0.0;
+    int q = threadIdx.x + u * kZgThreads, n = 0;
+    while (q >= nocc - n && n < nocc) {   // pair index -> (n, m), n <= m
+      q -= nocc - n;
+      ++n;
+    }
+    pn[u] = n;
+    pm[u] = n + q;
+  }
+  for (long c0 = blockIdx.x * (long)kZgP; c0 < Ng; c0 += (long)gridDim.x * kZgP) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < nocc * kZgP; e += kZgThreads) {
+      const int n = e / kZgP, p = e - n * kZgP;
+      const long g = c0 + p;
+      sr[n][p] = g < Ng ? re[(long)n * Ng + g] : 0.0;
+      si[n][p] = g < Ng ? im[(long)n * Ng + g] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < kZgMaxPairsPerThread; ++u) {
+      if (threadIdx.x + u * kZgThreads >= npairs) break;
+      const int n = pn[u], m = pm[u];
+      double xr = ar[u], xi = ai[u];
+      for (int p = 0; p < kZgP; ++p) {
+        xr = fma(sr[n][p], sr[m][p], fma(si[n][p], si[m][p], xr));
+        xi = fma(si[n][p], sr[m][p], -fma(sr[n][p], si[m][p], -xi));
+      }
+      ar[u] = xr;
+      ai[u] = xi;
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < kZgMaxPairsPerThread; ++u) {
+    const int q = threadIdx.x + u * kZgThreads;
+    if (q >= npairs) break;
+    part[((long)blockIdx.x * npairs + q) * 2] = ar[u];
+    part[((long)blockIdx.x * npairs + q) * 2 + 1] = ai[u];
+  }
+}
+
+// G = scale * sum over blocks (fixed order), full Hermitian (gre, gim) from the n <= m pairs
+__global__ void k_gp_zgram_reduce(int nocc, int nblk, const double* __restrict__ part, double scale,
+                                  double* __restrict__ gre, double* __restrict__ gim) {
+  const int npairs = nocc * (nocc + 1) / 2;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < npairs; q += gridDim.x * blockDim.x) {
+    int n = 0, r = q;
+    while (r >= nocc - n) {
+      r -= nocc - n;
+      ++n;
+    }
+    const int m = n + r;
+    double xr = 0.0, xi = 0.0;
+    for (int b = 0; b < nblk; ++b) {
+      xr += part[((long)b * npairs + q) * 2];
+      xi += part[((long)b * npairs + q) * 2 + 1];
+    }
+    gre[(long)n * nocc + m] = scale * xr;
+    gim[(long)n * nocc + m] = scale * xi;
+    gre[(long)m * nocc + n] = scale * xr;
+    gim[(long)m * nocc + n] = -scale * xi;
+  }
+}
+
+// X = L^-1 of the complex lower Cholesky factor (one block; thread j solves L x = e_j)
+__global__ void k_ztri_inverse(int N, const double* __restrict__ lre, const double* __restrict__ lim,
+                               double* __restrict__ xre, double* __restrict__ xim) {
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    for (int i = 0; i < j; ++i) {
+      xre[(long)i * N + j] = 0.0;
+      xim[(long)i * N + j] = 0.0;
+    }
+    for (int i = j; i < N; ++i) {
+      double sr = (i == j) ? 1.0 : 0.0, si = 0.0;
+      for (int k = j; k < i; ++k) {
+        const double ar = lre[(long)i * N + k], ai = lim[(long)i * N + k];
+        const double br = xre[(long)k * N + j], bi = xim[(long)k * N + j];
+        sr -= ar * br - ai * bi;
+        si -= ar * bi + ai * br;
+      }
+      const double d = lre[(long)i * N + i];   // real positive pivot
+      xre[(long)i * N + j] = sr / d;
+      xim[(long)i * N + j] = si / d;
+    }
+  }
+}
+
+// psi_out_n = sum_{m <= n} X_nm psi_in_m per grid point, the point's orbitals in registers
+template <int MAXN>
+__global__ void __launch_bounds__(256)
+k_gp_xapply(int nocc, long Ng, const double* __restrict__ xre, const double* __restrict__ xim,
+            const double* __restrict__ in, double* __restrict__ out) {
+  __shared__ double sxr[MAXN * MAXN], sxi[MAXN * MAXN];
+  for (int e = threadIdx.x; e < nocc * nocc; e += blockDim.x) {
+    sxr[e] = xre[e];
+    sxi[e] = xim[e];
+  }
+  __syncthreads();
+  const long plane = (long)nocc * Ng;
+  for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < Ng; g += (long)gridDim.x * blockDim.x) {
+    double yr[MAXN], yi[MAXN];
+#pragma unroll
+    for (int m = 0; m < MAXN; ++m) {
+      yr[m] = m < nocc ? in[(long)m * Ng + g] : 0.0;
+      yi[m] = m < nocc ? in[plane + (long)m * Ng + g] : 0.0;
+    }
+#pragma unroll
+    for (int n = 0; n < MAXN; ++n) {
+      if (n >= nocc) break;
+      double sr = 0.0, si = 0.0;
+#pragma unroll
+      for (int m = 0; m <= n; ++m) {
+        const double ar = sxr[n * nocc + m], ai = sxi[n * nocc + m];
+        sr = fma(ar, yr[m], fma(-ai, yi[m], sr));
+        si = fma(ar, yi[m], fma(ai, yr[m], si));
+      }
+      out[(long)n * Ng + g] = sr;
+      out[plane + (long)n * Ng + g] = si;
+    }
+  }
+}
+
 // per replica: [d_x, d_y, d_z, E_core, E_H, E_xc, N_e] partial sums over blocks (fixed order)
 constexpr int kGpObs = 7;
 __global__ void k_gp_obs(const double* __restrict__ psi, const double* __restrict__ hpsi,
@@ -229,29 +676,154 @@ int gp_blocks(rmgtd_ctx* ctx, long n) {
   return (int)std::max<long>(1, std::min<long>(ceil_div(n, 256), 4L * ctx->num_sms));
 }
 
+constexpr int kGpBX = 32, kGpBY = 8, kGpZ = 16, kGtZ = 32;
+
+// tensor maps of the two term buffers for the TMA kernel: 4-D {nx, ny, nz, columns}, box
+// {BX + 16, BY + 12, 1, 1}, zero fill outside; only when a row of x is a whole number of
+// 16-byte units (then every stride is)
+template <typename T>
+bool gp_encode_term_maps(rmgtd_ctx* ctx) {
+  const EncodeTiledFn f = tensor_map_encoder();
+  if (!f || ((long)ctx->nx * sizeof(T)) % 16 != 0) return false;
+  if (cudaFuncSetAttribute(k_gp_term_tma<T, kGpBX, kGpBY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)gt_smem_bytes<T, kGpBX, kGpBY>()) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  const cuuint64_t cols = 2ull * ctx->N * ctx->nrep;
+  const cuuint64_t dims[4] = {(cuuint64_t)ctx->nx, (cuuint64_t)ctx->ny, (cuuint64_t)ctx->nz, cols};
+  const cuuint64_t strides[3] = {(cuuint64_t)ctx->nx * sizeof(T),
+                                 (cuuint64_t)ctx->nx * ctx->ny * sizeof(T),
+                                 (cuuint64_t)ctx->Ng * sizeof(T)};
+  const cuuint32_t box[4] = {(cuuint32_t)(kGpBX + 2 * kGtXO), (cuuint32_t)(kGpBY + 2 * kFdRadius), 1, 1};
+  const cuuint32_t es[4] = {1, 1, 1, 1};
+  const CUtensorMapDataType dt =
+      sizeof(T) == sizeof(double) ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  for (int b = 0; b < 2; ++b) {
+    void* base = b == 0 ? ctx->gp_ta : ctx->gp_tb;
+    void* map = b == 0 ? (void*)ctx->gp_tm_a : (void*)ctx->gp_tm_b;
+    if (f(reinterpret_cast<CUtensorMap*>(map), dt, 4, base, dims, strides, box, es,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+  }
+  return true;
+}
+
+int gp_zgram_blocks(rmgtd_ctx* ctx) {
+  return (int)std::max<long>(1, std::min<long>(ceil_div(ctx->Ng, kZgP), 4L * ctx->num_sms));
+}
+
+// the mixed path's series terms are float32
+bool gp_f32(const rmgtd_ctx* ctx) { return ctx->opt.precision == RMGTD_PREC_MIXED; }
+
+// one series term for every replica whose series is running: tout = (-i dt/k) Hbar tin,
+// psi_1 += tout, errbits <- max|tout|^2 (the KB projections of tin first)
+template <typename T>
+int gp_term(rmgtd_ctx* ctx, const T* tin, T* tout, double c) {
+  const int N = ctx->N, nrep = ctx->nrep;
+  const int dtype = sizeof(T) == sizeof(double) ? RMGTD_F64 : RMGTD_F32;
+  int rc = kb_project_cols(ctx, tin, 2 * N * nrep, dtype, ctx->gp_coef);   // one block per column
+  if (rc) return rc;                                                       // and projector
+  if (ctx->gp_tma) {   // x-y tiles by TMA from the term's tensor map
+    const CUtensorMap* tm = reinterpret_cast<const CUtensorMap*>(
+        (const void*)tin == ctx->gp_ta ? ctx->gp_tm_a : ctx->gp_tm_b);
+    const int nzc = ceil_div(ctx->nz, kGtZ);
+    const dim3 grid(ceil_div(ctx->nx, kGpBX), ceil_div(ctx->ny, kGpBY), nrep * N * nzc);
+    k_gp_term_tma<T, kGpBX, kGpBY><<<grid, dim3(kGpBX, kGpBY), gt_smem_bytes<T, kGpBX, kGpBY>(),
+                                      ctx->stream>>>(
+        *tm, tin, tout, ctx->gp_psi1, (const T*)ctx->gp_vtot, ctx->gp_kb_row, ctx->gp_kb_p,
+        ctx->gp_kb_val, ctx->gp_coef, ctx->nproj, N, ctx->nx, ctx->ny, ctx->nz, kGtZ, nzc,
+        -0.5 / (ctx->h * ctx->h), c, ctx->gp_sact, ctx->errbits, ctx->status);
+    ++ctx->launches;
+    RMGTD_LAUNCH(ctx, "k_gp_term_tma");
+    return RMGTD_OK;
+  }
+  const int nzc = ceil_div(ctx->nz, kGpZ);
+  const dim3 grid(ceil_div(ctx->nx, kGpBX), ceil_div(ctx->ny, kGpBY), nrep * N * nzc);
+  k_gp_term_fused<T, kGpBX, kGpBY><<<grid, dim3(kGpBX, kGpBY), 0, ctx->stream>>>(
+      tin, tout, ctx->gp_psi1, (const T*)ctx->gp_vtot, ctx->gp_kb_row, ctx->gp_kb_p,
+      ctx->gp_kb_val, ctx->gp_coef, ctx->nproj, N, ctx->nx, ctx->ny, ctx->nz, kGpZ, nzc,
+      -0.5 / (ctx->h * ctx->h), c, ctx->gp_sact, ctx->errbits);
+  ++ctx->launches;
+  RMGTD_LAUNCH(ctx, "k_gp_term_fused");
+  return RMGTD_OK;
+}
+
+// KB lists by grid point (CSR) from the projector boxes: entry (p, E_p beta_p(r)) for every
+// projector whose box holds the point
+int gp_build_kb_lists(rmgtd_ctx* ctx) {
+  const int np = ctx->nproj;
+  const long Ng = ctx->Ng;
+  const long long nval = ctx->h_poff[np];
+  std::vector<double> val(nval);
+  RMGTD_CUDA(ctx, cudaMemcpy(val.data(), ctx->pval, sizeof(double) * nval, cudaMemcpyDeviceToHost));
+  std::vector<int> cnt(Ng + 1, 0);
+  auto point = [&](int p, long long e) {
+    const int* b = &ctx->h_pbox[6 * p];
+    const long long bxy = (long long)b[3] * b[4];
+    const long long z = b[2] + e / bxy, y = b[1] + (e / b[3]) % b[4], x = b[0] + e % b[3];
+    return (long)((z * ctx->ny + y) * ctx->nx + x);
+  };
+  for (int p = 0; p < np; ++p)
+    for (long long e = 0; e < ctx->h_poff[p + 1] - ctx->h_poff[p]; ++e) ++cnt[point(p, e) + 1];
+  for (long g = 0; g < Ng; ++g) cnt[g + 1] += cnt[g];
+  if ((long long)cnt[Ng] != nval) return set_error(ctx, RMGTD_EINVAL, "KB lists: box count mismatch");
+  std::vector<int> pos(cnt.begin(), cnt.end() - 1), pidx(nval);
+  std::vector<double> w(nval);
+  for (int p = 0; p < np; ++p)
+    for (long long e = 0; e < ctx->h_poff[p + 1] - ctx->h_poff[p]; ++e) {
+      const int k = pos[point(p, e)]++;
+      pidx[k] = p;
+      w[k] = ctx->h_Ekb[p] * val[ctx->h_poff[p] + e];
+    }
+  ctx->gp_kb_row = (int*)dev_alloc(ctx, sizeof(int) * (Ng + 1));
+  ctx->gp_kb_p = (int*)dev_alloc(ctx, sizeof(int) * std::max<long long>(nval, 1));
+  ctx->gp_kb_val = (double*)dev_alloc(ctx, sizeof(double) * std::max<long long>(nval, 1));
+  if (!ctx->gp_kb_row || !ctx->gp_kb_p || !ctx->gp_kb_val)
+    return set_error(ctx, RMGTD_ENOMEM, "KB lists");
+  RMGTD_CUDA(ctx, cudaMemcpy(ctx->gp_kb_row, cnt.data(), sizeof(int) * (Ng + 1), cudaMemcpyHostToDevice));
+  RMGTD_CUDA(ctx, cudaMemcpy(ctx->gp_kb_p, pidx.data(), sizeof(int) * nval, cudaMemcpyHostToDevice));
+  RMGTD_CUDA(ctx, cudaMemcpy(ctx->gp_kb_val, w.data(), sizeof(double) * nval, cudaMemcpyHostToDevice));
+  return RMGTD_OK;
+}
+
 }  // namespace
 
 int gridprop_setup(rmgtd_ctx* ctx) {
   const int nocc = ctx->N, nrep = ctx->nrep;
   const long Ng = ctx->Ng, plane = (long)nocc * Ng;
   const size_t psz = sizeof(double) * 2 * plane * nrep;
+  const size_t tsz = gp_f32(ctx) ? sizeof(float) : sizeof(double);
   ctx->gp_psi = (double*)dev_alloc(ctx, psz);
   ctx->gp_psi1 = (double*)dev_alloc(ctx, psz);
-  ctx->gp_t = (double*)dev_alloc(ctx, psz);
   ctx->gp_ht = (double*)dev_alloc(ctx, psz);
+  ctx->gp_ta = dev_alloc(ctx, tsz * 2 * plane * nrep);
+  ctx->gp_tb = dev_alloc(ctx, tsz * 2 * plane * nrep);
   const size_t vsz = sizeof(double) * Ng * nrep;
   ctx->gp_v0 = (double*)dev_alloc(ctx, vsz);
   ctx->gp_vm1 = (double*)dev_alloc(ctx, vsz);
   ctx->gp_v1 = (double*)dev_alloc(ctx, vsz);
-  ctx->gp_vbar = (double*)dev_alloc(ctx, vsz);
+  ctx->gp_vtot = dev_alloc(ctx, tsz * Ng * nrep);
   ctx->gp_ebar = (double*)dev_alloc(ctx, sizeof(double) * 3 * nrep);
   ctx->gp_active = (int*)dev_alloc(ctx, sizeof(int) * nrep);
-  ctx->gp_gram = (double*)dev_alloc(ctx, sizeof(double) * 3 * (size_t)nocc * nocc);
+  ctx->gp_sact = (int*)dev_alloc(ctx, sizeof(int) * nrep);
+  ctx->gp_coef = (double*)dev_alloc(ctx, sizeof(double) * 2 * std::max(ctx->nproj, 1) * 2L * nocc * nrep);
+  ctx->gp_gram = (double*)dev_alloc(ctx, sizeof(double) * 5 * (size_t)nocc * nocc);
+  if (nocc <= kZgMaxN)
+    ctx->gp_zpart = (double*)dev_alloc(
+        ctx, sizeof(double) * 2 * (size_t)gp_zgram_blocks(ctx) * (nocc * (nocc + 1) / 2));
   ctx->gp_obs = (double*)dev_alloc(ctx, sizeof(double) * kGpObs * nrep * 4L * ctx->num_sms);
-  if (!ctx->gp_psi || !ctx->gp_psi1 || !ctx->gp_t || !ctx->gp_ht || !ctx->gp_v0 || !ctx->gp_vm1 ||
-      !ctx->gp_v1 || !ctx->gp_vbar || !ctx->gp_ebar || !ctx->gp_active || !ctx->gp_gram ||
-      !ctx->gp_obs)
+  if (!ctx->gp_psi || !ctx->gp_psi1 || !ctx->gp_ht || !ctx->gp_ta || !ctx->gp_tb || !ctx->gp_v0 ||
+      !ctx->gp_vm1 || !ctx->gp_v1 || !ctx->gp_vtot || !ctx->gp_ebar || !ctx->gp_active ||
+      !ctx->gp_sact || !ctx->gp_coef || !ctx->gp_gram || !ctx->gp_obs ||
+      (nocc <= kZgMaxN && !ctx->gp_zpart))
     return set_error(ctx, RMGTD_ENOMEM, "grid propagation buffers");
+  if (ctx->nproj > 0) {
+    const int rc = gp_build_kb_lists(ctx);
+    if (rc) return rc;
+  }
+  ctx->gp_tma = gp_f32(ctx) ? gp_encode_term_maps<float>(ctx) : gp_encode_term_maps<double>(ctx);
   k_gp_init<<<gp_blocks(ctx, plane), 256, 0, ctx->stream>>>(ctx->phi, plane, nrep, ctx->gp_psi);
   ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_gp_init");
@@ -275,17 +847,24 @@ int gridprop_kick(rmgtd_ctx* ctx, int rep, int axis, double kappa) {
 // fields of the orbitals `psi` for every replica: rho, V_H, V_xc, eps_xc, V_Hxc (ctx arrays)
 static int gp_fields(rmgtd_ctx* ctx, const double* psi) {
   const long Ng = ctx->Ng;
+  ph_begin(ctx, PH_RHO);
   k_gp_density<<<dim3(gp_blocks(ctx, Ng), ctx->nrep), 256, 0, ctx->stream>>>(psi, ctx->f_dev, ctx->N,
                                                                             Ng, ctx->rho);
   ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_gp_density");
+  ph_end(ctx);
   int rc = RMGTD_OK;
   if (ctx->hartree_xc) {
+    ph_begin(ctx, PH_HARTREE);
     rc = hartree_coop(ctx, ctx->rho, ctx->vh, nullptr, 0, ctx->nrep, 0);
+    ph_end(ctx);
     if (rc) return rc;
   }
-  return launch_lda(ctx, ctx->rho, ctx->hartree_xc ? ctx->vh : nullptr, 0, ctx->vxc, ctx->exc,
-                    ctx->vhxc, nullptr, Ng, nullptr, ctx->nrep, Ng, ctx->hartree_xc);
+  ph_begin(ctx, PH_XC);
+  rc = launch_lda(ctx, ctx->rho, ctx->hartree_xc ? ctx->vh : nullptr, 0, ctx->vxc, ctx->exc,
+                  ctx->vhxc, nullptr, Ng, nullptr, ctx->nrep, Ng, ctx->hartree_xc);
+  ph_end(ctx);
+  return rc;
 }
 
 static int read_max(rmgtd_ctx* ctx, const unsigned long long* bits, int n, std::vector<double>& out) {
@@ -308,32 +887,108 @@ static int gp_orthonormalize(rmgtd_ctx* ctx, int r) {
   const long plane = (long)N * ctx->Ng, NN = (long)N * N;
   const double* re = ctx->gp_psi1 + 2 * r * plane;
   const double* im = re + plane;
+  double* out = ctx->gp_psi + 2 * r * plane;
   double* gre = ctx->gp_gram;
   double* gim = gre + NN;
   double* y = gim + NN;
-  // G_nm = h^3 sum psi_n conj(psi_m): Re = R R^T + I I^T, Im = Y - Y^T with Y = I R^T
-  int rc = gram(ctx, re, re, nullptr, 0, 1, ctx->h3, nullptr, gre, nullptr, nullptr, 1, nullptr);
-  if (!rc) rc = gram(ctx, im, im, nullptr, 0, 1, ctx->h3, gre, gre, nullptr, nullptr, 1, nullptr);
-  if (!rc) rc = gram(ctx, im, re, nullptr, 0, 1, ctx->h3, nullptr, y, nullptr, nullptr, 0, nullptr);
-  if (rc) return rc;
-  k_gp_antisym<<<gp_blocks(ctx, NN), 256, 0, ctx->stream>>>(N, y, gim);
-  ++ctx->launches;
-  RMGTD_LAUNCH(ctx, "k_gp_antisym");
+  double* xre = y + NN;
+  double* xim = xre + NN;
+  // G_nm = h^3 sum psi_n conj(psi_m)
+  if (N <= kZgMaxN) {
+    const int nblk = gp_zgram_blocks(ctx);
+    k_gp_zgram_partial<<<nblk, kZgThreads, 0, ctx->stream>>>(N, ctx->Ng, re, im, ctx->gp_zpart);
+    ++ctx->launches;
+    RMGTD_LAUNCH(ctx, "k_gp_zgram_partial");
+    k_gp_zgram_reduce<<<gp_blocks(ctx, (long)N * (N + 1) / 2), 256, 0, ctx->stream>>>(
+        N, nblk, ctx->gp_zpart, ctx->h3, gre, gim);
+    ++ctx->launches;
+    RMGTD_LAUNCH(ctx, "k_gp_zgram_reduce");
+  } else {   // Re = R R^T + I I^T, Im = Y - Y^T with Y = I R^T (the tiled float64 Gram)
+    int rc = gram(ctx, re, re, nullptr, 0, 1, ctx->h3, nullptr, gre, nullptr, nullptr, 1, nullptr);
+    if (!rc) rc = gram(ctx, im, im, nullptr, 0, 1, ctx->h3, gre, gre, nullptr, nullptr, 1, nullptr);
+    if (!rc) rc = gram(ctx, im, re, nullptr, 0, 1, ctx->h3, nullptr, y, nullptr, nullptr, 0, nullptr);
+    if (rc) return rc;
+    k_gp_antisym<<<gp_blocks(ctx, NN), 256, 0, ctx->stream>>>(N, y, gim);
+    ++ctx->launches;
+    RMGTD_LAUNCH(ctx, "k_gp_antisym");
+  }
   k_zcholesky<<<1, 1024, 0, ctx->stream>>>(N, gre, gim, ctx->status);
   ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_zcholesky");
-  k_gp_fsubst<<<gp_blocks(ctx, ctx->Ng), 256, 0, ctx->stream>>>(N, ctx->Ng, gre, gim, re,
-                                                               ctx->gp_psi + 2 * r * plane);
-  ++ctx->launches;
-  RMGTD_LAUNCH(ctx, "k_gp_fsubst");
+  if (N <= 32) {   // psi <- X psi1 with X = L^-1, the point's orbitals in registers
+    k_ztri_inverse<<<1, 1024, 0, ctx->stream>>>(N, gre, gim, xre, xim);
+    ++ctx->launches;
+    RMGTD_LAUNCH(ctx, "k_ztri_inverse");
+    if (N <= 16)
+      k_gp_xapply<16><<<gp_blocks(ctx, ctx->Ng), 256, 0, ctx->stream>>>(N, ctx->Ng, xre, xim, re, out);
+    else
+      k_gp_xapply<32><<<gp_blocks(ctx, ctx->Ng), 256, 0, ctx->stream>>>(N, ctx->Ng, xre, xim, re, out);
+    ++ctx->launches;
+    RMGTD_LAUNCH(ctx, "k_gp_xapply");
+  } else {
+    k_gp_fsubst<<<gp_blocks(ctx, ctx->Ng), 256, 0, ctx->stream>>>(N, ctx->Ng, gre, gim, re, out);
+    ++ctx->launches;
+    RMGTD_LAUNCH(ctx, "k_gp_fsubst");
+  }
   return RMGTD_OK;
 }
 
-int gridprop_step(rmgtd_ctx* ctx, rmgtd_stats* st) {
-  const int nrep = ctx->nrep, N = ctx->N;
-  const long Ng = ctx->Ng, plane = (long)N * Ng;
-  const double dt = ctx->opt.dt;
+// the orbital series of every active replica for one pass: psi_1 = sum of the terms (tmax,
+// tsum, status per replica)
+template <typename T>
+static int gp_series(rmgtd_ctx* ctx, const std::vector<int>& active, std::vector<int>& status,
+                     std::vector<int>& tmax, std::vector<int>& tsum) {
+  const int nrep = ctx->nrep;
+  const long Ng = ctx->Ng, rplane = 2L * ctx->N * Ng;
   const double thr2 = ctx->opt.dP_thrs * ctx->opt.dP_thrs;
+  k_gp_vtot<T><<<dim3(gp_blocks(ctx, Ng), nrep), 256, 0, ctx->stream>>>(
+      ctx->vion, ctx->gp_v0, ctx->gp_v1, ctx->gp_ebar, (T*)ctx->gp_vtot, Ng, ctx->nx, ctx->ny,
+      ctx->nz, ctx->h);
+  ++ctx->launches;
+  RMGTD_LAUNCH(ctx, "k_gp_vtot");
+  T* ta = (T*)ctx->gp_ta;
+  T* tb = (T*)ctx->gp_tb;
+  k_gp_start<T><<<dim3(gp_blocks(ctx, rplane), nrep), 256, 0, ctx->stream>>>(
+      ctx->gp_psi, ctx->gp_psi1, ta, rplane, ctx->gp_active);
+  ++ctx->launches;
+  RMGTD_LAUNCH(ctx, "k_gp_start");
+  std::vector<int> series(active);
+  std::vector<double> m;
+  for (int k = 1;; ++k) {
+    RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->gp_sact, series.data(), sizeof(int) * nrep,
+                                    cudaMemcpyHostToDevice, ctx->stream));
+    RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->errbits, 0, sizeof(unsigned long long) * nrep, ctx->stream));
+    int rc = gp_term<T>(ctx, ta, tb, ctx->opt.dt / k);
+    if (rc) return rc;
+    rc = read_max(ctx, ctx->errbits, nrep, m);
+    if (rc) return rc;
+    std::swap(ta, tb);
+    bool more = false;
+    for (int r = 0; r < nrep; ++r) {
+      if (!series[r]) continue;
+      if (!(m[r] <= 1e300)) {
+        status[r] = RMGTD_EDIVERGED;
+        series[r] = 0;
+      } else if (m[r] <= thr2) {
+        series[r] = 0;
+      } else if (k >= ctx->opt.max_terms) {
+        status[r] = RMGTD_ENOTCONVERGED;
+        series[r] = 0;
+      } else {
+        more = true;
+      }
+      if (!series[r]) {
+        tmax[r] = std::max(tmax[r], k);
+        tsum[r] += k;
+      }
+    }
+    if (!more) return RMGTD_OK;
+  }
+}
+
+int gridprop_step(rmgtd_ctx* ctx, rmgtd_stats* st) {
+  const int nrep = ctx->nrep;
+  const long Ng = ctx->Ng;
   RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream));
   // the step's mean field per replica from the host samples E(j dt) (zero past them)
   {
@@ -360,62 +1015,15 @@ int gridprop_step(rmgtd_ctx* ctx, rmgtd_stats* st) {
   for (int pass = 1; pass <= ctx->opt.max_scf && any; ++pass) {
     RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->gp_active, active.data(), sizeof(int) * nrep,
                                     cudaMemcpyHostToDevice, ctx->stream));
-    k_gp_vbar<<<dim3(gp_blocks(ctx, Ng), nrep), 256, 0, ctx->stream>>>(
-        ctx->gp_v0, ctx->gp_v1, ctx->gp_ebar, ctx->gp_vbar, Ng, ctx->nx, ctx->ny, ctx->nz, ctx->h);
-    ++ctx->launches;
-    RMGTD_LAUNCH(ctx, "k_gp_vbar");
-    // the orbital series of every active replica
-    std::vector<int> series(nrep, 0);
-    for (int r = 0; r < nrep; ++r) {
-      if (!active[r]) continue;
-      series[r] = 1;
-      const size_t b = sizeof(double) * 2 * plane;
-      RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->gp_psi1 + 2 * r * plane, ctx->gp_psi + 2 * r * plane, b,
-                                      cudaMemcpyDeviceToDevice, ctx->stream));
-      RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->gp_t + 2 * r * plane, ctx->gp_psi + 2 * r * plane, b,
-                                      cudaMemcpyDeviceToDevice, ctx->stream));
-    }
-    int k = 0;
-    for (bool more = true; more;) {
-      ++k;
-      RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->errbits, 0, sizeof(unsigned long long) * nrep, ctx->stream));
-      for (int r = 0; r < nrep; ++r) {
-        if (!series[r]) continue;
-        int rc = apply_h_dev(ctx, ctx->gp_t + 2 * r * plane, ctx->gp_ht + 2 * r * plane, 2 * N,
-                             RMGTD_F64, ctx->gp_vbar + r * Ng);
-        if (rc) return rc;
-        k_gp_term<<<gp_blocks(ctx, plane), 256, 0, ctx->stream>>>(
-            ctx->gp_ht + 2 * r * plane, ctx->gp_t + 2 * r * plane, ctx->gp_psi1 + 2 * r * plane,
-            plane, dt / k, ctx->errbits + r);
-        ++ctx->launches;
-        RMGTD_LAUNCH(ctx, "k_gp_term");
-      }
-      int rc = read_max(ctx, ctx->errbits, nrep, m);
-      if (rc) return rc;
-      more = false;
-      for (int r = 0; r < nrep; ++r) {
-        if (!series[r]) continue;
-        if (!(m[r] <= 1e300)) {
-          status[r] = RMGTD_EDIVERGED;
-          series[r] = 0;
-        } else if (m[r] <= thr2) {
-          series[r] = 0;
-        } else if (k >= ctx->opt.max_terms) {
-          status[r] = RMGTD_ENOTCONVERGED;
-          series[r] = 0;
-        } else {
-          more = true;
-        }
-        if (!series[r]) {
-          tmax[r] = std::max(tmax[r], k);
-          tsum[r] += k;
-        }
-      }
-    }
+    ph_begin(ctx, PH_ELDYN);   // the orbital series takes the commutator series' place
+    int rc = gp_f32(ctx) ? gp_series<float>(ctx, active, status, tmax, tsum)
+                         : gp_series<double>(ctx, active, status, tmax, tsum);
+    ph_end(ctx);
+    if (rc) return rc;
     for (int r = 0; r < nrep; ++r)
       if (status[r]) active[r] = 0;
     // V_new of the propagated orbitals; H_err = max|V_new - V_1|
-    int rc = gp_fields(ctx, ctx->gp_psi1);
+    rc = gp_fields(ctx, ctx->gp_psi1);
     if (rc) return rc;
     RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->gp_active, active.data(), sizeof(int) * nrep,
                                     cudaMemcpyHostToDevice, ctx->stream));
@@ -461,10 +1069,12 @@ int gridprop_step(rmgtd_ctx* ctx, rmgtd_stats* st) {
     return set_error(ctx, first, "grid propagation step " + std::to_string(ctx->gp_steps) +
                                      " failed with status " + std::to_string(first));
   }
+  ph_begin(ctx, PH_OTHER);
   for (int r = 0; r < nrep; ++r) {
     int rc = gp_orthonormalize(ctx, r);
     if (rc) return rc;
   }
+  ph_end(ctx);
   int cst = 0;
   RMGTD_CUDA(ctx, cudaMemcpyAsync(&cst, ctx->status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   // V_-1 <- V_0, V_0 <- V_1 (rotate the buffers)

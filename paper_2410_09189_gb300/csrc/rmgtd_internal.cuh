@@ -253,22 +253,32 @@ struct rmgtd_ctx {
   double* Hx0 = nullptr;        // scratch [nrep][N*N] x 2: H_0 + V_0, H_1 + V_1 (Omega_2)
   double* Hx1 = nullptr;
   // propagation on the grid (opt.grid_basis): occupied orbitals [nrep][2][N][Ng] (planar
-  // complex), the series' sum, term and H term; potentials V_0, V_-1, V_1, Vbar [nrep][Ng];
-  // the step's mean field [nrep][3]; active flags; Gram / Cholesky scratch [3][N*N];
+  // complex) and the series' sum, float64; potentials V_0, V_-1, V_1 [nrep][Ng];
+  // the step's mean field [nrep][3]; active flags; Gram / Cholesky / inverse scratch [5][N*N];
   // observable partials
   double* gp_psi = nullptr;
   double* gp_psi1 = nullptr;
-  double* gp_t = nullptr;
-  double* gp_ht = nullptr;
+  double* gp_ht = nullptr;      // H_core psi scratch of the observables
   double* gp_v0 = nullptr;
   double* gp_vm1 = nullptr;
   double* gp_v1 = nullptr;
-  double* gp_vbar = nullptr;
   double* gp_ebar = nullptr;
   int* gp_active = nullptr;
   double* gp_gram = nullptr;
+  double* gp_zpart = nullptr;   // per-block partials of the small complex Gram
   double* gp_obs = nullptr;
   std::vector<double> gp_obs_host;
+  void* gp_ta = nullptr;        // series terms in the path's precision (float64 / float32),
+  void* gp_tb = nullptr;        // double-buffered [nrep][2][N][Ng]
+  void* gp_vtot = nullptr;      // V_ion + Vbar + Ebar.q in that precision [nrep][Ng]
+  int* gp_sact = nullptr;       // [nrep] replicas whose series is still running
+  double* gp_coef = nullptr;    // KB projections of the current term [nrep][2N][2][nproj]
+  alignas(64) unsigned char gp_tm_a[128] = {};   // tensor maps of the two term buffers
+  alignas(64) unsigned char gp_tm_b[128] = {};
+  int gp_tma = 0;               // the term kernel streams its tiles by TMA
+  int* gp_kb_row = nullptr;     // KB lists by grid point: CSR row offsets [Ng + 1],
+  int* gp_kb_p = nullptr;       // projector index and E_p beta_p(r) of each entry
+  double* gp_kb_val = nullptr;
   long long gp_steps = 0;
   long long* step_dev = nullptr;
 
@@ -408,6 +418,8 @@ inline int ceil_div(long a, long b) { return (int)((a + b - 1) / b); }
 // ---- launchers -------------------------------------------------------------------------
 void dev_free(rmgtd_ctx* ctx, void* p);
 double* kb_coef_buffer(rmgtd_ctx* ctx, int ncols);
+// KB projections coef[(2 j) np + p] = h^3 <beta_p, x_j> of ncols real columns (F64 or F32)
+int kb_project_cols(rmgtd_ctx* ctx, const void* x, int ncols, int dtype, double* coef);
 // k_grid.cu
 int launch_vion(rmgtd_ctx* ctx, const double* pos_dev, const double* Z_dev,
                 const double* rc_dev, int natoms);
