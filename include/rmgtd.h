@@ -377,6 +377,13 @@ int rmgtd_net_get_params(rmgtd_net* net, float* theta_host);
 /* Feature scales s_0..s_2 and output scale s_out (positive, finite). */
 int rmgtd_net_set_scales(rmgtd_net* net, const double in_scales[3], double out_scale);
 int rmgtd_net_get_scales(rmgtd_net* net, double in_scales[3], double* out_scale);
+/* Weight file of the network (host file IO): tag "RMGTDNET", uint32 version 1, uint32 0,
+ * int64 parameter count, float64 scales s_0, s_1, s_2, s_out, then the float32 parameters,
+ * little-endian.  save writes the current parameters and scales; load checks the tag,
+ * version and count (RMGTD_EINVAL otherwise, or for non-finite values) and replaces both
+ * (Adam restarts). */
+int rmgtd_net_save(rmgtd_net* net, const char* path);
+int rmgtd_net_load(rmgtd_net* net, const char* path);
 /* One sample's features x_dev [3][Ng] (float32) from three float64 densities, and its target
  * t_dev [Ng] from three float64 potentials V_{t+dt}, V_t, V_{t-dt} (all device pointers). */
 int rmgtd_net_features(rmgtd_net* net, const double* rho_t, const double* rho_tm1,
@@ -400,6 +407,11 @@ int rmgtd_net_adam(rmgtd_net* net, double lr);
  * context's and its max_batch must be >= nrep.  The density history restarts (no history:
  * rho_{t-dt} = rho_{t-2dt} = rho_t).  Errors: RMGTD_EINVAL. */
 int rmgtd_attach_net(rmgtd_ctx* ctx, rmgtd_net* net);
+/* Create a network on the context's grid and stream (max_batch = nrep), load the weight
+ * file `path` (rmgtd_net_load) and attach it: the learned seed shipped with a run.  The
+ * caller owns *net_out (detach with rmgtd_attach_net(ctx, NULL) before rmgtd_net_destroy).
+ * Errors: those of the three calls; nothing is attached on failure. */
+int rmgtd_surrogate_load(rmgtd_ctx* ctx, const char* path, rmgtd_net** net_out);
 
 /* Fields of replica `rep` of the current state copied to a device array of Ng doubles:
  * which = 0 rho, 1 V_H + V_xc (of the last DFT evaluation). */

@@ -430,10 +430,9 @@ static int create_impl(const rmgtd_system* sys, const rmgtd_options* opt, rmgtd_
   ctx->done_steps = (int*)A(sizeof(int));
   ctx->step_dev = (long long*)A(sizeof(long long));
   ctx->fld_ebar = (double*)A(sizeof(double) * 9 * nrep);
-  if (opt->nonorthogonal || opt->magnus_order == 2) {
-    ctx->Hx0 = (double*)A(msz * nrep);
-    ctx->Hx1 = (double*)A(msz * nrep);
-  }
+  // Omega's scratch: Hbar + V of a field step, H_0 + V_0 / H_1 + V_1 of Omega_2
+  ctx->Hx0 = (double*)A(msz * nrep);
+  if (opt->nonorthogonal || opt->magnus_order == 2) ctx->Hx1 = (double*)A(msz * nrep);
   if (opt->nonorthogonal) {
     ctx->Sinv = (double*)A(msz);
     ctx->Gm = (double*)A(msz * nrep);
@@ -1273,6 +1272,23 @@ int rmgtd_profile_counters(rmgtd_ctx* ctx, long long* hartree_solves,
   RMGTD_CUDA(ctx, cudaMemcpy(kx, ctx->kexec, sizeof(kx), cudaMemcpyDeviceToHost));
   if (hartree_solves) *hartree_solves = (long long)kx[2];
   if (hartree_iterations) *hartree_iterations = (long long)kx[3];
+  return RMGTD_OK;
+}
+
+int rmgtd_surrogate_load(rmgtd_ctx* ctx, const char* path, rmgtd_net** net_out) {
+  if (!ctx || !path || !net_out) return set_error(ctx, RMGTD_EINVAL, "surrogate_load: NULL argument");
+  *net_out = nullptr;
+  rmgtd_net* net = nullptr;
+  int rc = rmgtd_net_create(ctx->nx, ctx->ny, ctx->nz, ctx->nrep, ctx->stream, &net);
+  if (rc) return set_error(ctx, rc, std::string("surrogate_load: ") + rmgtd_last_error(nullptr));
+  rc = rmgtd_net_load(net, path);
+  if (!rc) rc = rmgtd_attach_net(ctx, net);
+  if (rc) {
+    const std::string msg = ctx->err.empty() ? rmgtd_last_error(nullptr) : ctx->err;
+    rmgtd_net_destroy(net);
+    return set_error(ctx, rc, "surrogate_load: " + msg);
+  }
+  *net_out = net;
   return RMGTD_OK;
 }
 

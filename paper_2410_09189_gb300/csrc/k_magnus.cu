@@ -217,6 +217,17 @@ int magnus_prepare(rmgtd_ctx* ctx, const double** Ha, const double** Hb, long* h
   return RMGTD_OK;
 }
 
+int hbar_with_field(rmgtd_ctx* ctx, const double* Ha, const double* Hb, long hstride,
+                    const double* febar, int rep0, int nreps, double* out) {
+  const int N = ctx->N;
+  const long NN = (long)N * N;
+  k_hx_form<<<elementwise_blocks(ctx, NN * nreps), 256, 0, ctx->stream>>>(
+      N, nreps, Ha, Hb, hstride, ctx->M, febar + 3 * rep0, 0, out, nullptr);
+  ++ctx->launches;
+  RMGTD_LAUNCH(ctx, "k_hx_form");
+  return RMGTD_OK;
+}
+
 int nonorth_kick_matrix(rmgtd_ctx* ctx, int axis) {
   const long NN = (long)ctx->N * ctx->N;
   return launch_pair(ctx, 1, 1.0, ctx->Sinv, 0, ctx->M + axis * NN, 0, 0.0, nullptr, 0, nullptr, 0,

@@ -794,12 +794,9 @@ __global__ void __launch_bounds__(NT) k_eldyn(EldynArgs a) {
           const int ri = I * TS + r, rj = J * TS + r;
           double hi = 0.0, hj = 0.0;
           if (kg < N) {
-            if (ri < N)
-              hi = 0.5 * (Ha[(long)ri * N + kg] + Hb[(long)ri * N + kg]) +
-                   field_term(a, a.rep0 + rep, (long)ri * N + kg);
-            if (rj < N)
-              hj = 0.5 * (Ha[(long)rj * N + kg] + Hb[(long)rj * N + kg]) +
-                   field_term(a, a.rep0 + rep, (long)rj * N + kg);
+            // (the caller forms Hbar + V beforehand when a field is on: febar is NULL here)
+            if (ri < N) hi = 0.5 * (Ha[(long)ri * N + kg] + Hb[(long)ri * N + kg]);
+            if (rj < N) hj = 0.5 * (Ha[(long)rj * N + kg] + Hb[(long)rj * N + kg]);
           }
           Hi[r * (KC + 1) + kk] = hi;
           Hj[r * (KC + 1) + kk] = hj;
@@ -1276,6 +1273,14 @@ int eldyn(rmgtd_ctx* ctx, const double* Ha, const double* Hb, long hstride, doub
     if (C == 16) return launch_eldyn_cluster<16>(ctx, a, eldyn_cluster_smem(ctx->N, 16, D));
     if (C == 8) return launch_eldyn_cluster<8>(ctx, a, eldyn_cluster_smem(ctx->N, 8, D));
     ctx->shat_fresh = 0;
+  }
+  if (a.febar) {   // the cooperative kernel reads plain matrices: Hbar + V into Hx0 first
+    if (!ctx->Hx0) return set_error(ctx, RMGTD_EINVAL, "eldyn: field without its scratch");
+    int rc = hbar_with_field(ctx, Ha, Hb, hstride, a.febar, rep0, nreps, ctx->Hx0);
+    if (rc) return rc;
+    a.Ha = a.Hb = ctx->Hx0;
+    a.hstride = (long)ctx->N * ctx->N;
+    a.febar = nullptr;
   }
   // GB300's float64 units (~2 FMA per clock and SM) bound the series: pick the tile size
   // whose symmetric tile pairs spread the work of a term most evenly over the SMs (the most

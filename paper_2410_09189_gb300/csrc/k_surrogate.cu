@@ -25,6 +25,9 @@
 #include <vector>
 
 #include "fastdiv.h"
+#include <cstdio>
+#include <cstring>
+
 #include "rmgtd_internal.cuh"
 
 namespace rmgtd {
@@ -684,6 +687,53 @@ int rmgtd_net_adam(rmgtd_net* n, double lr) {
                                                           (float)lr, bc1, bc2, n->wbf);
   NET_LAUNCH("k_adam");
   return RMGTD_OK;
+}
+
+// Weight file: 8-byte tag "RMGTDNET", uint32 version 1, uint32 reserved 0, int64 parameter
+// count, float64 feature scales s_0..s_2 and output scale, then the float32 parameters; all
+// little-endian as written by the host.
+static const char kNetTag[8] = {'R', 'M', 'G', 'T', 'D', 'N', 'E', 'T'};
+
+int rmgtd_net_save(rmgtd_net* n, const char* path) {
+  if (!n || !path) return net_err(RMGTD_EINVAL, "net_save: NULL argument");
+  std::vector<float> theta(kParams);
+  int rc = rmgtd_net_get_params(n, theta.data());
+  if (rc) return rc;
+  FILE* fp = fopen(path, "wb");
+  if (!fp) return net_err(RMGTD_EINVAL, std::string("net_save: cannot open ") + path);
+  const uint32_t ver = 1, res = 0;
+  const int64_t count = kParams;
+  const double sc[4] = {n->in_scale[0], n->in_scale[1], n->in_scale[2], n->out_scale};
+  bool ok = fwrite(kNetTag, 1, 8, fp) == 8 && fwrite(&ver, 4, 1, fp) == 1 &&
+            fwrite(&res, 4, 1, fp) == 1 && fwrite(&count, 8, 1, fp) == 1 &&
+            fwrite(sc, 8, 4, fp) == 4 &&
+            fwrite(theta.data(), sizeof(float), kParams, fp) == (size_t)kParams;
+  ok = (fclose(fp) == 0) && ok;
+  return ok ? RMGTD_OK : net_err(RMGTD_EINVAL, std::string("net_save: write failed: ") + path);
+}
+
+int rmgtd_net_load(rmgtd_net* n, const char* path) {
+  if (!n || !path) return net_err(RMGTD_EINVAL, "net_load: NULL argument");
+  FILE* fp = fopen(path, "rb");
+  if (!fp) return net_err(RMGTD_EINVAL, std::string("net_load: cannot open ") + path);
+  char tag[8];
+  uint32_t ver = 0, res = 0;
+  int64_t count = 0;
+  double sc[4];
+  std::vector<float> theta(kParams);
+  bool ok = fread(tag, 1, 8, fp) == 8 && memcmp(tag, kNetTag, 8) == 0 && fread(&ver, 4, 1, fp) == 1 &&
+            ver == 1 && fread(&res, 4, 1, fp) == 1 && fread(&count, 8, 1, fp) == 1 &&
+            count == kParams && fread(sc, 8, 4, fp) == 4 &&
+            fread(theta.data(), sizeof(float), kParams, fp) == (size_t)kParams;
+  char extra;
+  ok = ok && fread(&extra, 1, 1, fp) == 0;   // nothing after the parameters
+  fclose(fp);
+  if (!ok) return net_err(RMGTD_EINVAL, std::string("net_load: not a weight file of this network: ") + path);
+  for (float t : theta)
+    if (!isfinite(t)) return net_err(RMGTD_EINVAL, "net_load: non-finite parameter");
+  int rc = rmgtd_net_set_scales(n, sc, sc[3]);
+  if (rc) return rc;
+  return rmgtd_net_set_params(n, theta.data());
 }
 
 }  // extern "C"

@@ -470,6 +470,9 @@ int nonorth_setup(rmgtd_ctx* ctx);
 // arguments the series then takes
 int magnus_prepare(rmgtd_ctx* ctx, const double** Ha, const double** Hb, long* hstride,
                    const double** febar, const double** D);
+// out_r = (Ha_r + Hb_r)/2 + sum_q febar[rep0 + r][q] M_q for nreps replicas (stride hstride)
+int hbar_with_field(rmgtd_ctx* ctx, const double* Ha, const double* Hb, long hstride,
+                    const double* febar, int rep0, int nreps, double* out);
 // G = S^-1 M_axis into ctx->Gm for a kick in the non-orthogonal basis
 int nonorth_kick_matrix(rmgtd_ctx* ctx, int axis);
 // k_gridprop.cu: propagation of the occupied orbitals on the grid (opt.grid_basis)

@@ -133,6 +133,9 @@ def load_library(path: Optional[str] = None):
                                    ctypes.POINTER(ctypes.c_longlong)]),
         "rmgtd_selftest_barrier_timeout": (i, [vp, ctypes.c_uint, _c_int_p]),
         "rmgtd_get_hartree_preconditioner": (i, [vp, _c_int_p]),
+        "rmgtd_net_save": (i, [vp, ctypes.c_char_p]),
+        "rmgtd_net_load": (i, [vp, ctypes.c_char_p]),
+        "rmgtd_surrogate_load": (i, [vp, ctypes.c_char_p, ctypes.POINTER(vp)]),
         "rmgtd_set_field": (i, [vp, i, _c_double_p, i]),
         "rmgtd_spectrum": (i, [_c_double_p, i, ctypes.c_long, d, d, d, _c_double_p, i,
                                _c_double_p]),
@@ -336,6 +339,21 @@ class Context:
         self._net = net
         self._check(self._lib.rmgtd_attach_net(self._ctx, net._net if net is not None else None))
 
+    def surrogate_load(self, path: str) -> "Net":
+        """Create a network on this grid, load the weight file and attach it
+        (rmgtd_surrogate_load); returns the attached network."""
+        handle = ctypes.c_void_p()
+        self._check(self._lib.rmgtd_surrogate_load(self._ctx, os.fsencode(path), ctypes.byref(handle)))
+        net = Net.__new__(Net)
+        net._lib = self._lib
+        net.n = tuple(int(v) for v in self.sys.n)
+        net.Ng = self.Ng
+        net.max_batch = self.nrep
+        net.P = int(self._lib.rmgtd_net_num_params())
+        net._net = handle
+        self._net = net
+        return net
+
     def field_into(self, which: int, rep: int, dev_ptr: int):
         """Copy rho (FIELD_RHO) or V_H + V_xc (FIELD_VHXC) of replica `rep` to device memory."""
         self._check(self._lib.rmgtd_get_field(self._ctx, int(which), int(rep), ctypes.c_void_p(dev_ptr)))
@@ -463,6 +481,14 @@ class Net:
     def _check(self, rc: int):
         if rc != OK:
             raise RmgtdError(rc, self._lib.rmgtd_last_error(None).decode())
+
+    def save(self, path: str):
+        """Write the parameters and scales to a weight file (rmgtd_net_save)."""
+        self._check(self._lib.rmgtd_net_save(self._net, os.fsencode(path)))
+
+    def load(self, path: str):
+        """Read parameters and scales from a weight file (rmgtd_net_load)."""
+        self._check(self._lib.rmgtd_net_load(self._net, os.fsencode(path)))
 
     def close(self):
         if getattr(self, "_net", None) and self._net.value:

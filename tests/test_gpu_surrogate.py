@@ -183,6 +183,47 @@ def test_attach_rejects_mismatched_network(lib, small_ground_state):
     ctx.close()
 
 
+def test_weight_file_round_trip_and_surrogate_load(lib, small_ground_state, tmp_path):
+    """rmgtd_net_save / rmgtd_net_load restore parameters and scales bit for bit;
+    rmgtd_surrogate_load attaches a network from the file that steps exactly like the same
+    network attached by hand; a corrupted file is refused with nothing attached."""
+    s, gs = small_ground_state
+    rng = np.random.default_rng(5)
+    net = lib.Net(s.n, max_batch=2)
+    theta = (1e-3 * rng.standard_normal(net.P)).astype(np.float32)
+    net.set_params(theta)
+    net.set_scales([0.5, 2e-6, 3e-7], 4e-6)
+    path = tmp_path / "seed.rmgtdnet"
+    net.save(str(path))
+    other = lib.Net(s.n, max_batch=1)
+    other.load(str(path))
+    assert np.array_equal(other.params(), theta)
+    s_other, o_other = other.scales()
+    s_net, o_net = net.scales()
+    assert np.array_equal(s_other, s_net) and o_other == o_net
+    runs = []
+    for how in ("attach", "file"):
+        ctx = lib.Context(s, gs["phi"], nrep=2, H_thrs=1e-9, dP_thrs=1e-12, use_graph=True)
+        ctx.kick(0, 2, s.kappa)
+        ctx.kick(1, 0, s.kappa)
+        if how == "attach":
+            ctx.attach_net(net)
+        else:
+            ctx.surrogate_load(str(path))
+        ctx.step(6)
+        runs.append(np.array([ctx.dipole(r) for r in range(2)]))
+        ctx.attach_net(None)
+        ctx.close()
+    assert np.array_equal(runs[0], runs[1])
+    bad = tmp_path / "bad.rmgtdnet"
+    bad.write_bytes(path.read_bytes()[:-4])
+    ctx = lib.Context(s, gs["phi"], nrep=1, use_graph=False)
+    with pytest.raises(lib.RmgtdError) as ei:
+        ctx.surrogate_load(str(bad))
+    assert ei.value.code == lib.EINVAL
+    ctx.close()
+
+
 def test_trained_network_saves_scf_passes(lib, small_ground_state, tmp_path):
     """Train on the first 3/4 of a kicked trajectory (the library's kernels only), then
     continue the propagation with and without the learned seed from the same state: fewer
