@@ -152,6 +152,16 @@ typedef struct {
                               the orbitals (stats: passes, terms of the orbital series,
                               H_err = max|V_new - V_1|); the matrix, save / load, batch,
                               autotune and network calls return RMGTD_ESTATE. */
+  int ground_state_scf;    /* > 0: before the set-up, up to this many SCF iterations of the
+                              Kohn-Sham ground state on the GPU (Algorithm 1 lines 1-3) from the
+                              orthonormalised phi0: Chebyshev-filtered subspace iteration on
+                              N + max(4, N/8) orbitals (degree 12 per iteration, Rayleigh-Ritz),
+                              Pulay-mixed density (history 6, mixing 0.4); phi0 is replaced by the
+                              N lowest Kohn-Sham orbitals (ascending energies).  Requires
+                              orthonormalize = 1, nonorthogonal = 0, N + buffer <= 1024.
+                              RMGTD_ENOTCONVERGED if the cap is reached. */
+  double ground_state_tol; /* stop when max|rho_out - rho_in| and the largest Ritz residual
+                              max|H phi_n - eps_n phi_n| (n < N) are below it (0: 1e-8) */
 } rmgtd_options;
 
 /* Per-step, per-replica statistics written by rmgtd_step. */
@@ -221,6 +231,12 @@ int rmgtd_kick(rmgtd_ctx* ctx, int rep, int axis, double kappa);
  * NULL) receives nsteps * nrep entries, step-major.  Returns the first non-OK replica
  * status; on failure the state of the last completed step is kept. */
 int rmgtd_step(rmgtd_ctx* ctx, int nsteps, rmgtd_stats* stats);
+
+/* Result of the ground-state SCF (opt.ground_state_scf): iterations, final max|rho_out -
+ * rho_in|, largest Ritz residual, and the N orbital energies (eps may be NULL).  Errors:
+ * RMGTD_ESTATE when the context was created without it. */
+int rmgtd_ground_state_info(rmgtd_ctx* ctx, int* iterations, double* drho, double* residual,
+                            double* eps);
 
 /* Dipole strength function of the kicked runs (Section 4: the spectrum is the sum of the
  * Fourier transforms of mu_x(t), mu_y(t), mu_z(t) of the runs kicked along x, y and z).

@@ -326,6 +326,8 @@ void rmgtd_default_options(rmgtd_options* o) {
   o->magnus_order = 1;
   o->nonorthogonal = 0;
   o->grid_basis = 0;
+  o->ground_state_scf = 0;
+  o->ground_state_tol = 1e-8;
 }
 
 const char* rmgtd_last_error(const rmgtd_ctx* ctx) {
@@ -502,6 +504,10 @@ static int create_impl(const rmgtd_system* sys, const rmgtd_options* opt, rmgtd_
 
   if (opt->orthonormalize) {
     rc = orthonormalize(ctx);
+    if (rc) return rc;
+  }
+  if (opt->ground_state_scf > 0) {   // the Kohn-Sham ground state replaces phi0
+    rc = ground_state_scf(ctx);
     if (rc) return rc;
   }
   rc = gram(ctx, ctx->phi, ctx->phi, nullptr, 0, 1, ctx->h3, nullptr, ctx->Smat, nullptr, nullptr,
@@ -690,6 +696,8 @@ int rmgtd_create(const rmgtd_system* sys, const rmgtd_options* opt_in, rmgtd_ctx
   if (opt.nonorthogonal && (opt.orthonormalize || opt.subspace_scf > 0 || opt.magnus_order != 1))
     return set_error(nullptr, RMGTD_EINVAL,
                      "nonorthogonal needs orthonormalize = 0, subspace_scf = 0 and magnus_order 1");
+  if (opt.ground_state_scf < 0 || (opt.ground_state_scf > 0 && (!opt.orthonormalize || opt.nonorthogonal)))
+    return set_error(nullptr, RMGTD_EINVAL, "ground_state_scf needs orthonormalize = 1 and nonorthogonal 0");
   if (opt.grid_basis &&
       (sys->nvirt != 0 || opt.magnus_order != 1 || opt.nonorthogonal || opt.subspace_scf > 0))
     return set_error(nullptr, RMGTD_EINVAL,
@@ -1526,6 +1534,18 @@ int rmgtd_set_field(rmgtd_ctx* ctx, int rep, const double* E_xyz, int nsamp) {
     ctx->step_graph = nullptr;
   }
   ctx->fld_on = on;
+  return RMGTD_OK;
+}
+
+int rmgtd_ground_state_info(rmgtd_ctx* ctx, int* iterations, double* drho, double* residual,
+                            double* eps) {
+  if (!ctx) return set_error(nullptr, RMGTD_EINVAL, "ctx is NULL");
+  if (ctx->opt.ground_state_scf <= 0)
+    return set_error(ctx, RMGTD_ESTATE, "ground_state_info: created without the ground-state SCF");
+  if (iterations) *iterations = ctx->gs_iters;
+  if (drho) *drho = ctx->gs_err;
+  if (residual) *residual = ctx->gs_resid;
+  if (eps) std::copy(ctx->gs_eps.begin(), ctx->gs_eps.end(), eps);
   return RMGTD_OK;
 }
 

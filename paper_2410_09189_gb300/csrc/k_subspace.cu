@@ -6,6 +6,7 @@
 #include <math.h>
 
 #include "rmgtd_internal.cuh"
+#include "jacobi.cuh"
 
 namespace rmgtd {
 
@@ -1565,71 +1566,7 @@ k_subspace_update(int N, const double* __restrict__ H, double* __restrict__ S,
     V[e] = ((e / N) == (e % N)) ? 1.0 : 0.0;
   }
   __syncthreads();
-  const int n2 = N + (N & 1);
-  const int np = n2 / 2;
-  for (int sweep = 0; sweep < 40; ++sweep) {
-    double off = 0.0, tot = 0.0;
-    for (long e = tid; e < NN; e += nt) {
-      const double a = A[e];
-      tot += a * a;
-      if ((e / N) != (e % N)) off += a * a;
-    }
-    off = block_sum(off, sh);
-    __syncthreads();
-    tot = block_sum(tot, sh);
-    if (tid == 0) stop = (off <= 1e-28 * tot) ? 1.0 : 0.0;
-    __syncthreads();
-    if (stop != 0.0) break;
-    for (int r = 0; r < n2 - 1; ++r) {
-      for (int i = tid; i < np; i += nt) {
-        const int a0 = (i == 0) ? 0 : ((i - 1 + r) % (n2 - 1)) + 1;
-        const int b0 = ((n2 - 2 - i + r) % (n2 - 1)) + 1;
-        int p = min(a0, b0), q = max(a0, b0);
-        double c = 1.0, sn = 0.0;
-        if (q < N) {
-          const double apq = A[(long)p * N + q];
-          if (fabs(apq) > 1e-300) {
-            const double tau = (A[(long)q * N + q] - A[(long)p * N + p]) / (2.0 * apq);
-            double t;
-            if (fabs(tau) > 1e150)
-              t = 0.5 / tau;
-            else
-              t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-            c = 1.0 / sqrt(1.0 + t * t);
-            sn = t * c;
-          }
-        } else {
-          p = q = -1;
-        }
-        pp[i] = p;
-        qq[i] = q;
-        cc[i] = c;
-        ss[i] = sn;
-      }
-      __syncthreads();
-      for (long e = tid; e < (long)np * N; e += nt) {  // rows: A <- J^T A
-        const int i = (int)(e / N), k = (int)(e % N);
-        const int p = pp[i], q = qq[i];
-        if (p < 0) continue;
-        const double ap = A[(long)p * N + k], aq = A[(long)q * N + k];
-        A[(long)p * N + k] = cc[i] * ap - ss[i] * aq;
-        A[(long)q * N + k] = ss[i] * ap + cc[i] * aq;
-      }
-      __syncthreads();
-      for (long e = tid; e < (long)np * N; e += nt) {  // columns: A <- A J, V <- V J
-        const int i = (int)(e / N), k = (int)(e % N);
-        const int p = pp[i], q = qq[i];
-        if (p < 0) continue;
-        const double ap = A[(long)k * N + p], aq = A[(long)k * N + q];
-        A[(long)k * N + p] = cc[i] * ap - ss[i] * aq;
-        A[(long)k * N + q] = ss[i] * ap + cc[i] * aq;
-        const double vp = V[(long)k * N + p], vq = V[(long)k * N + q];
-        V[(long)k * N + p] = cc[i] * vp - ss[i] * vq;
-        V[(long)k * N + q] = ss[i] * vp + cc[i] * vq;
-      }
-      __syncthreads();
-    }
-  }
+  jacobi_sweeps(N, A, V, pp, qq, cc, ss, sh, &stop);
   if (tid == 0) {  // ascending eigenvalue order (insertion sort, N <= 1024)
     for (int i = 0; i < N; ++i) ord[i] = i;
     for (int i = 1; i < N; ++i) {
@@ -1705,6 +1642,13 @@ __global__ void k_forward_subst(int N, long Ng, const double* __restrict__ L,
     y[(long)i * Ng + g] = s / L[(long)i * N + i];
   }
   for (int i = 0; i < N; ++i) phi[(long)i * Ng + g] = y[(long)i * Ng + g];
+}
+
+int forward_subst(rmgtd_ctx* ctx, int N, const double* L, double* X, double* work) {
+  k_forward_subst<<<ceil_div(ctx->Ng, 128), 128, 0, ctx->stream>>>(N, ctx->Ng, L, X, work);
+  ++ctx->launches;
+  RMGTD_LAUNCH(ctx, "k_forward_subst");
+  return RMGTD_OK;
 }
 
 int orthonormalize(rmgtd_ctx* ctx) {

@@ -280,6 +280,11 @@ struct rmgtd_ctx {
   int* gp_kb_p = nullptr;       // projector index and E_p beta_p(r) of each entry
   double* gp_kb_val = nullptr;
   long long gp_steps = 0;
+  // ground state on the device (opt.ground_state_scf): orbital energies, SCF iterations,
+  // final density change and largest Ritz residual
+  std::vector<double> gs_eps;
+  int gs_iters = 0;
+  double gs_err = 0.0, gs_resid = 0.0;
   long long* step_dev = nullptr;
 
   // learned seed of the SCF loop (attached network; buffers allocated at attach)
@@ -494,6 +499,11 @@ int step_end(rmgtd_ctx* ctx);
 int observables(rmgtd_ctx* ctx);
 int subspace_update(rmgtd_ctx* ctx, double alpha, double* err_dev);
 int orthonormalize(rmgtd_ctx* ctx);
+// X <- L^-1 X for N columns of length Ng (L lower, row-major); work: N * Ng doubles
+int forward_subst(rmgtd_ctx* ctx, int N, const double* L, double* X, double* work);
+// k_groundstate.cu: SCF ground state of the Kohn-Sham orbitals from ctx->phi (orthonormal),
+// replacing ctx->phi by the N lowest eigenvectors of H[rho] (opt.ground_state_scf > 0)
+int ground_state_scf(rmgtd_ctx* ctx);
 // in-place lower Cholesky factor of the N x N matrix S (one block; status <- EINVAL when a
 // pivot is not positive)
 __global__ void k_cholesky(int N, double* __restrict__ S, int* status);

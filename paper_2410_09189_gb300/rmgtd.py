@@ -62,7 +62,8 @@ class COptions(ctypes.Structure):
         ("subspace_scf", ctypes.c_int), ("subspace_mix", ctypes.c_double),
         ("subspace_tol", ctypes.c_double), ("mixed_poisson_tol", ctypes.c_double),
         ("magnus_order", ctypes.c_int), ("nonorthogonal", ctypes.c_int),
-        ("grid_basis", ctypes.c_int),
+        ("grid_basis", ctypes.c_int), ("ground_state_scf", ctypes.c_int),
+        ("ground_state_tol", ctypes.c_double),
     ]
 
 
@@ -136,6 +137,7 @@ def load_library(path: Optional[str] = None):
         "rmgtd_net_save": (i, [vp, ctypes.c_char_p]),
         "rmgtd_net_load": (i, [vp, ctypes.c_char_p]),
         "rmgtd_surrogate_load": (i, [vp, ctypes.c_char_p, ctypes.POINTER(vp)]),
+        "rmgtd_ground_state_info": (i, [vp, ctypes.POINTER(i), _c_double_p, _c_double_p, _c_double_p]),
         "rmgtd_set_field": (i, [vp, i, _c_double_p, i]),
         "rmgtd_spectrum": (i, [_c_double_p, i, ctypes.c_long, d, d, d, _c_double_p, i,
                                _c_double_p]),
@@ -167,7 +169,8 @@ class Context:
                  stream: Optional[int] = None, torch_alloc: bool = True,
                  subspace_scf: int = 0, subspace_mix: float = 0.3, subspace_tol: float = 1e-10,
                  mixed_poisson_tol: float = 0.0, magnus_order: int = 1,
-                 nonorthogonal: bool = False, grid_basis: bool = False):
+                 nonorthogonal: bool = False, grid_basis: bool = False,
+                 ground_state_scf: int = 0, ground_state_tol: float = 1e-8):
         import torch
 
         lib = load_library()
@@ -226,6 +229,8 @@ class Context:
         opt.magnus_order = int(magnus_order)
         opt.nonorthogonal = 1 if nonorthogonal else 0
         opt.grid_basis = 1 if grid_basis else 0
+        opt.ground_state_scf = int(ground_state_scf)
+        opt.ground_state_tol = float(ground_state_tol)
         if nonorthogonal:
             opt.orthonormalize = 0
         if stream is None:
@@ -286,6 +291,17 @@ class Context:
         self.close()
 
     # --- ABI -----------------------------------------------------------------------------
+    def ground_state_info(self):
+        """(iterations, max|rho_out - rho_in|, largest Ritz residual, orbital energies) of the
+        ground-state SCF run at creation (rmgtd_ground_state_info)."""
+        it = ctypes.c_int()
+        d, r = ctypes.c_double(), ctypes.c_double()
+        eps = np.empty(self.N)
+        self._check(self._lib.rmgtd_ground_state_info(
+            self._ctx, ctypes.byref(it), ctypes.cast(ctypes.byref(d), _c_double_p),
+            ctypes.cast(ctypes.byref(r), _c_double_p), _dptr(eps)))
+        return int(it.value), float(d.value), float(r.value), eps
+
     def set_field(self, rep: int, E):
         """Samples E[j] = (E_x, E_y, E_z)(j dt) of replica `rep`'s external field
         (rmgtd_set_field); an empty array clears it."""
