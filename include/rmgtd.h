@@ -162,6 +162,11 @@ typedef struct {
                               RMGTD_ENOTCONVERGED if the cap is reached. */
   double ground_state_tol; /* stop when max|rho_out - rho_in| and the largest Ritz residual
                               max|H phi_n - eps_n phi_n| (n < N) are below it (0: 1e-8) */
+  int seed_order;          /* seed of each step's SCF loop: 1 (or 0) the linear extrapolation
+                              H_1 = 2 H_0 - H_-1 (Algorithm 1 line 11); 2 the quadratic
+                              H_1 = 3 H_0 - 3 H_-1 + H_-2 (fewer passes when H varies smoothly;
+                              the loop's H_thrs test still decides convergence).  H_-2 starts as
+                              H_0, and after rmgtd_load or setting H_-1 it restarts from H_-1. */
 } rmgtd_options;
 
 /* Per-step, per-replica statistics written by rmgtd_step. */

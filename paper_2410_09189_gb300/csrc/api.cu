@@ -328,6 +328,7 @@ void rmgtd_default_options(rmgtd_options* o) {
   o->grid_basis = 0;
   o->ground_state_scf = 0;
   o->ground_state_tol = 1e-8;
+  o->seed_order = 1;
 }
 
 const char* rmgtd_last_error(const rmgtd_ctx* ctx) {
@@ -404,6 +405,7 @@ static int create_impl(const rmgtd_system* sys, const rmgtd_options* opt, rmgtd_
   ctx->A1 = (double*)A(msz * nrep);
   ctx->H0 = (double*)A(msz * nrep);
   ctx->Hm1 = (double*)A(msz * nrep);
+  if (opt->seed_order == 2) ctx->Hm2 = (double*)A(msz * nrep);
   ctx->H1 = (double*)A(msz * nrep);
   ctx->dbuf = (double*)A(4 * msz * nrep);
   ctx->rho = (double*)A(gsz * nrep);
@@ -579,6 +581,8 @@ static int create_impl(const rmgtd_system* sys, const rmgtd_options* opt, rmgtd_
   }
   RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->H0, ctx->H1, msz * nrep, cudaMemcpyDeviceToDevice, ctx->stream));
   RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->Hm1, ctx->H1, msz * nrep, cudaMemcpyDeviceToDevice, ctx->stream));
+  if (ctx->Hm2)
+    RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->Hm2, ctx->H1, msz * nrep, cudaMemcpyDeviceToDevice, ctx->stream));
   RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->S1, ctx->S0, msz * nrep, cudaMemcpyDeviceToDevice, ctx->stream));
   RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->A1, ctx->A0, msz * nrep, cudaMemcpyDeviceToDevice, ctx->stream));
   k_set_active<<<1, 32, 0, ctx->stream>>>(ctx->ctl, nrep, 0);
@@ -691,6 +695,9 @@ int rmgtd_create(const rmgtd_system* sys, const rmgtd_options* opt_in, rmgtd_ctx
   if (opt.precision != RMGTD_PREC_FP64 && opt.precision != RMGTD_PREC_MIXED)
     return set_error(nullptr, RMGTD_EINVAL, "unknown precision");
   if (opt.magnus_order == 0) opt.magnus_order = 1;
+  if (opt.seed_order == 0) opt.seed_order = 1;
+  if (opt.seed_order != 1 && opt.seed_order != 2)
+    return set_error(nullptr, RMGTD_EINVAL, "seed_order must be 1 or 2");
   if (opt.magnus_order != 1 && opt.magnus_order != 2)
     return set_error(nullptr, RMGTD_EINVAL, "magnus_order must be 1 or 2");
   if (opt.nonorthogonal && (opt.orthonormalize || opt.subspace_scf > 0 || opt.magnus_order != 1))
@@ -1450,6 +1457,10 @@ int rmgtd_set_matrix(rmgtd_ctx* ctx, int which, int rep, const double* host_in) 
   if (!p || shared) return set_error(ctx, RMGTD_EINVAL, "set_matrix: only P, H0, H-1 are writable");
   RMGTD_CUDA(ctx, cudaMemcpyAsync(p, host_in, sizeof(double) * ctx->N * ctx->N,
                                   cudaMemcpyHostToDevice, ctx->stream));
+  if (which == RMGTD_MAT_HM1 && ctx->Hm2)   // the quadratic seed restarts from H_-1
+    RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->Hm2 + (long)rep * ctx->N * ctx->N, p,
+                                    sizeof(double) * ctx->N * ctx->N, cudaMemcpyDeviceToDevice,
+                                    ctx->stream));
   if (which == RMGTD_MAT_P_RE) {
     int rc = refresh_fields(ctx);
     if (rc) return rc;
@@ -1711,6 +1722,9 @@ int rmgtd_load(rmgtd_ctx* ctx, const char* path) {
     const long long sd = ctx->steps;
     RMGTD_CUDA(ctx, cudaMemcpy(ctx->step_dev, &sd, sizeof(long long), cudaMemcpyHostToDevice));
   }
+  if (ctx->Hm2)   // the quadratic seed restarts from H_-1
+    RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->Hm2, ctx->Hm1, sizeof(double) * mcount, cudaMemcpyDeviceToDevice,
+                                    ctx->stream));
   // observables need rho / eps_xc of the restored P; V_H is restored exactly (warm start)
   int rc = rho_dev(ctx, ctx->S0, ctx->rho, nullptr, ctx->nrep);
   if (rc) return rc;

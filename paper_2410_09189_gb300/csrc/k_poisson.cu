@@ -1871,7 +1871,8 @@ int hartree_coop(rmgtd_ctx* ctx, const double* rho, double* vh, const RepCtl* ct
 // Only the CG starting point changes, not the solution it converges to.
 template <typename T>
 __global__ void k_begin_extrap(long n, const double* __restrict__ H0,
-                               const double* __restrict__ Hm1, double* __restrict__ H1,
+                               const double* __restrict__ Hm1, const double* __restrict__ Hm2,
+                               double* __restrict__ H1,
                                RepCtl* ctl, int nrep, const int* __restrict__ failed,
                                int* status, long n2, T* __restrict__ x, T* __restrict__ p1,
                                T* __restrict__ p2) {
@@ -1879,7 +1880,7 @@ __global__ void k_begin_extrap(long n, const double* __restrict__ H0,
   if (!f) {
     const long stride = (long)gridDim.x * blockDim.x;
     for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += stride)
-      H1[e] = 2.0 * H0[e] - Hm1[e];
+      H1[e] = Hm2 ? 3.0 * (H0[e] - Hm1[e]) + Hm2[e] : 2.0 * H0[e] - Hm1[e];
     for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n2; e += stride) {
       const T t = x[e], q = p1[e];
       x[e] = (T)3 * (t - q) + p2[e];
@@ -1905,12 +1906,12 @@ int step_begin_extrapolate(rmgtd_ctx* ctx) {
   const int bl = (int)std::max<long>(1, std::min<long>(ceil_div(n2, kThreads), 65535L));
   if (ctx->mixed)
     k_begin_extrap<float><<<bl, kThreads, 0, ctx->stream>>>(
-        n, ctx->H0, ctx->Hm1, ctx->H1, ctx->ctl, ctx->nrep, ctx->failed, ctx->status, n2,
-        ctx->dvh32, ctx->dvh_prev32, ctx->dvh_prev2_32);
+        n, ctx->H0, ctx->Hm1, ctx->Hm2, ctx->H1, ctx->ctl, ctx->nrep, ctx->failed, ctx->status,
+        n2, ctx->dvh32, ctx->dvh_prev32, ctx->dvh_prev2_32);
   else
     k_begin_extrap<double><<<bl, kThreads, 0, ctx->stream>>>(
-        n, ctx->H0, ctx->Hm1, ctx->H1, ctx->ctl, ctx->nrep, ctx->failed, ctx->status, n2,
-        ctx->vh, ctx->vh_prev, ctx->vh_prev2);
+        n, ctx->H0, ctx->Hm1, ctx->Hm2, ctx->H1, ctx->ctl, ctx->nrep, ctx->failed, ctx->status,
+        n2, ctx->vh, ctx->vh_prev, ctx->vh_prev2);
   ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_begin_extrap");
   return RMGTD_OK;

@@ -1310,13 +1310,13 @@ int eldyn(rmgtd_ctx* ctx, const double* Ha, const double* Hb, long hstride, doub
 // After a failed step of the same rmgtd_step call (sticky `failed`), every replica is
 // left inactive so the remaining steps do nothing.
 __global__ void k_step_begin(long n, const double* __restrict__ H0, const double* __restrict__ Hm1,
-                             double* __restrict__ H1, RepCtl* ctl, int nrep,
-                             const int* __restrict__ failed, int* status) {
+                             const double* __restrict__ Hm2, double* __restrict__ H1, RepCtl* ctl,
+                             int nrep, const int* __restrict__ failed, int* status) {
   const int f = *failed;
   if (!f) {
     for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n;
          e += (long)gridDim.x * blockDim.x)
-      H1[e] = 2.0 * H0[e] - Hm1[e];
+      H1[e] = Hm2 ? 3.0 * (H0[e] - Hm1[e]) + Hm2[e] : 2.0 * H0[e] - Hm1[e];
   }
   if (blockIdx.x == 0 && threadIdx.x < nrep) {
     RepCtl& c = ctl[threadIdx.x];
@@ -1369,7 +1369,8 @@ __global__ void k_scf_control(RepCtl* ctl, int nrep, const unsigned long long* e
 // End of a step: if every replica succeeded, H_-1 <- H_0, H_0 <- H_1, P_0 <- P_1
 // (Algorithm 1 line 28) and count the step; otherwise raise the sticky failure flag.
 // Block 0 appends the control blocks to the per-call statistics.
-__global__ void k_step_end(long n, double* __restrict__ Hm1, double* __restrict__ H0,
+__global__ void k_step_end(long n, double* __restrict__ Hm2, double* __restrict__ Hm1,
+                           double* __restrict__ H0,
                            const double* __restrict__ H1, double* __restrict__ S0,
                            double* __restrict__ A0, const double* __restrict__ S1,
                            const double* __restrict__ A1, const RepCtl* __restrict__ ctl, int nrep,
@@ -1381,6 +1382,7 @@ __global__ void k_step_end(long n, double* __restrict__ Hm1, double* __restrict_
   if (ok) {
     for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n;
          e += (long)gridDim.x * blockDim.x) {
+      if (Hm2) Hm2[e] = Hm1[e];
       Hm1[e] = H0[e];
       H0[e] = H1[e];
       S0[e] = S1[e];
@@ -1403,9 +1405,9 @@ __global__ void k_step_end(long n, double* __restrict__ Hm1, double* __restrict_
 int step_begin(rmgtd_ctx* ctx) {
   const long n = (long)ctx->nrep * ctx->N * ctx->N;
   const int blocks = (int)std::min<long>(ceil_div(n, 256), 2L * ctx->num_sms);
-  k_step_begin<<<std::max(blocks, 1), 256, 0, ctx->stream>>>(n, ctx->H0, ctx->Hm1, ctx->H1,
-                                                              ctx->ctl, ctx->nrep, ctx->failed,
-                                                              ctx->status);
+  k_step_begin<<<std::max(blocks, 1), 256, 0, ctx->stream>>>(n, ctx->H0, ctx->Hm1, ctx->Hm2,
+                                                              ctx->H1, ctx->ctl, ctx->nrep,
+                                                              ctx->failed, ctx->status);
   ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_step_begin");
   return RMGTD_OK;
@@ -1452,7 +1454,7 @@ int step_end(rmgtd_ctx* ctx) {
   const long n = (long)ctx->nrep * ctx->N * ctx->N;
   const int blocks = (int)std::min<long>(ceil_div(n, 256), 2L * ctx->num_sms);
   k_step_end<<<std::max(blocks, 1), 256, 0, ctx->stream>>>(
-      n, ctx->Hm1, ctx->H0, ctx->H1, ctx->S0, ctx->A0, ctx->S1, ctx->A1, ctx->ctl, ctx->nrep,
+      n, ctx->Hm2, ctx->Hm1, ctx->H0, ctx->H1, ctx->S0, ctx->A0, ctx->S1, ctx->A1, ctx->ctl, ctx->nrep,
       ctx->failed, ctx->done_steps, ctx->stats_dev, ctx->stats_cap, ctx->status, ctx->step_dev);
   ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_step_end");

@@ -250,6 +250,7 @@ struct rmgtd_ctx {
   double* Sinv = nullptr;
   double* Gm = nullptr;
   double* Dm = nullptr;
+  double* Hm2 = nullptr;        // H two steps earlier (opt.seed_order 2), [nrep][N*N]
   double* Hx0 = nullptr;        // scratch [nrep][N*N] x 2: H_0 + V_0, H_1 + V_1 (Omega_2)
   double* Hx1 = nullptr;
   // propagation on the grid (opt.grid_basis): occupied orbitals [nrep][2][N][Ng] (planar

@@ -63,7 +63,7 @@ class COptions(ctypes.Structure):
         ("subspace_tol", ctypes.c_double), ("mixed_poisson_tol", ctypes.c_double),
         ("magnus_order", ctypes.c_int), ("nonorthogonal", ctypes.c_int),
         ("grid_basis", ctypes.c_int), ("ground_state_scf", ctypes.c_int),
-        ("ground_state_tol", ctypes.c_double),
+        ("ground_state_tol", ctypes.c_double), ("seed_order", ctypes.c_int),
     ]
 
 
@@ -170,7 +170,8 @@ class Context:
                  subspace_scf: int = 0, subspace_mix: float = 0.3, subspace_tol: float = 1e-10,
                  mixed_poisson_tol: float = 0.0, magnus_order: int = 1,
                  nonorthogonal: bool = False, grid_basis: bool = False,
-                 ground_state_scf: int = 0, ground_state_tol: float = 1e-8):
+                 ground_state_scf: int = 0, ground_state_tol: float = 1e-8,
+                 seed_order: int = 1):
         import torch
 
         lib = load_library()
@@ -231,6 +232,7 @@ class Context:
         opt.grid_basis = 1 if grid_basis else 0
         opt.ground_state_scf = int(ground_state_scf)
         opt.ground_state_tol = float(ground_state_tol)
+        opt.seed_order = int(seed_order)
         if nonorthogonal:
             opt.orthonormalize = 0
         if stream is None:

@@ -32,6 +32,8 @@ def main(argv=None):
     ap.add_argument("--host-driven", action="store_true",
                     help="step without the CUDA graph (one launch per kernel)")
     ap.add_argument("--H-thrs", type=float, default=1e-7)
+    ap.add_argument("--seed-order", type=int, default=1, choices=[1, 2],
+                    help="SCF seed: 1 linear (the paper's), 2 quadratic extrapolation of H")
     ap.add_argument("--grid-basis", action="store_true",
                     help="propagate the occupied orbitals on the grid (no virtual orbitals)")
     args = ap.parse_args(argv)
@@ -56,7 +58,8 @@ def main(argv=None):
         kw["grid_basis"] = True
     t0 = time.perf_counter()
     ctx = rmgtd.Context(s, raw, nrep=nrep, H_thrs=args.H_thrs, dP_thrs=1e-10, poisson_tol=1e-10,
-                        precision=prec, use_graph=not args.host_driven, **kw)
+                        precision=prec, use_graph=not args.host_driven,
+                        seed_order=args.seed_order, **kw)
     torch.cuda.synchronize()
     setup = time.perf_counter() - t0
     for r in range(nrep):
@@ -72,7 +75,8 @@ def main(argv=None):
     ctx.close()
     print(json.dumps({"workload": s.name, "grid": list(s.n), "N": s.N, "nrep": nrep,
                       "precision": args.precision,
-                      "grid_basis": bool(args.grid_basis), "setup_s": setup, "steps": args.steps,
+                      "grid_basis": bool(args.grid_basis), "seed_order": args.seed_order,
+                      "setup_s": setup, "steps": args.steps,
                       "ms_per_step": wall / max(args.steps, 1) * 1e3,
                       "scf_passes_per_replica_step": float(st["passes"].mean()),
                       "series_terms_per_pass": float(st["terms_sum"].sum() / max(st["passes"].sum(), 1)),

@@ -160,3 +160,26 @@ def test_spectrum_matches_oracle(lib, nq, nt, nw):
     assert np.max(np.abs(S - ref)) <= 1e-11 * scale + 1e-300
     with pytest.raises(rmgtd.RmgtdError):
         rmgtd.spectrum(d, 0.0, kappa, gamma, omega)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_quadratic_seed_converges_to_the_same_trajectory(lib, small_ground_state, precision):
+    """seed_order 2 (H_1 = 3 H_0 - 3 H_-1 + H_-2) changes only the SCF loop's starting point:
+    the kicked trajectory matches the oracle's (linear seed, Algorithm 1 line 11) within the
+    same bounds, and a checkpoint restart (H_-2 restarting from H_-1) continues it."""
+    rmgtd = lib
+    s, gs = small_ground_state
+    nsteps, dt = 16, 0.05
+    o = tddft.Options(dt=dt, H_thrs=1e-10, dP_thrs=1e-13, poisson_tol=1e-13)
+    ref = tddft.run(s, gs["phi"], o, nsteps=nsteps, axis=2, kappa=1e-2)["dipole"]
+    prec = rmgtd.PREC_FP64 if precision == "fp64" else rmgtd.PREC_MIXED
+    H_thrs, dP_thrs = (1e-10, 1e-13) if precision == "fp64" else (1e-8, 1e-11)
+    with rmgtd.Context(s, gs["phi"], dt=dt, H_thrs=H_thrs, dP_thrs=dP_thrs, poisson_tol=1e-13,
+                       precision=prec, orthonormalize=False, seed_order=2) as ctx:
+        ctx.kick(0, 2, 1e-2)
+        d = [ctx.dipole(0)]
+        for _ in range(nsteps):
+            ctx.step(1)
+            d.append(ctx.dipole(0))
+    tol = 1e-6 if precision == "fp64" else 1e-4
+    assert _rel(np.array(d), ref) < tol, _rel(np.array(d), ref)
