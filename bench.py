@@ -828,21 +828,27 @@ def _surrogate_path(rmgtd, r, nsteps, world):
 
 def run_batch8(args):
     """The batched workload: eight clusters (20-150 atoms, 48^3-96^3), three kicks each,
-    stepped by one CUDA graph per time step (rmgtd_batch), against the same contexts stepped
-    one after another; mixed path, launch configurations from the autotuner."""
+    stepped by one CUDA graph per time step (rmgtd_batch, the clusters back to back: the
+    line's value), against the contexts stepped one after another and against the graph with
+    every cluster on its own share of the SMs on a parallel branch (shares in proportion to
+    the clusters' solo step times); mixed path, launch configurations from the autotuner; all
+    variants step the same window of the trajectory."""
     import torch
     torch.cuda.set_device(0)
     import __graft_entry__
     __graft_entry__.build()
     from paper_2410_09189_gb300 import inputs, rmgtd
 
-    def make():
+    systems = [inputs.cluster(i) for i in range(8)]
+    n_sms = torch.cuda.get_device_properties(0).multi_processor_count
+
+    def make(budget=None):
         out = []
-        for i in range(8):
-            s = inputs.cluster(i)
+        for i, s in enumerate(systems):
             raw = inputs.smooth_random_orbitals(s).reshape(s.N, s.Ng)
             c = rmgtd.Context(s, raw, nrep=3, H_thrs=1e-7, dP_thrs=1e-10, poisson_tol=1e-10,
-                              precision=rmgtd.PREC_MIXED, use_graph=True)
+                              precision=rmgtd.PREC_MIXED, use_graph=True,
+                              sm_budget=0 if budget is None else int(budget[i]))
             for a in range(3):
                 c.kick(a, a, 1e-3)
             out.append(c)
@@ -853,6 +859,23 @@ def run_batch8(args):
     setup_s = time.perf_counter() - t0
     choices = [c.autotune() for c in ctxs]
     stream = torch.cuda.current_stream()
+    # SM budgets of the concurrent variant: shares of the SMs in proportion to each cluster's
+    # own step time on the whole GPU (at least 4 SMs), summing to at most the SM count --
+    # latency-bound small systems lose little on few SMs, bandwidth-bound large ones need many
+    solo_ms = []
+    for c in ctxs:
+        c.step(2)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        c.step(5)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        solo_ms.append(e0.elapsed_time(e1) / 5)
+    work = np.array(solo_ms)
+    budgets = np.maximum(4, np.floor(n_sms * work / work.sum())).astype(int)
+    while budgets.sum() > n_sms:
+        budgets[int(np.argmax(budgets))] -= 1
 
     def timed(step_all):
         for _ in range(args.warmup):
@@ -878,12 +901,26 @@ def run_batch8(args):
     batch = rmgtd.Batch(ctxs)
     bat_ms, bat_st = timed(lambda k: batch.step(k))
     batch.close()
-    for pth in paths:
-        os.remove(pth)
-    os.rmdir(tmpdir)
     passes = float(np.mean([st["passes"].mean() for st in bat_st]))
     for c in ctxs:
         c.close()
+    # the concurrent variant: the same states in contexts sized to their SM budgets, one graph
+    # per step with a parallel branch per cluster
+    t0 = time.perf_counter()
+    cctx = make(budgets)
+    setup_c = time.perf_counter() - t0
+    cchoices = [c.autotune() for c in cctx]
+    for c, pth in zip(cctx, paths):
+        c.load(pth)
+    cbatch = rmgtd.Batch(cctx)
+    con_ms, con_st = timed(lambda k: cbatch.step(k))
+    cbatch.close()
+    con_passes = float(np.mean([st["passes"].mean() for st in con_st]))
+    for c in cctx:
+        c.close()
+    for pth in paths:
+        os.remove(pth)
+    os.rmdir(tmpdir)
     grid_pts = sum(inputs.cluster(i).Ng * inputs.cluster(i).N for i in range(8))
     out = {"metric": "batched RT-TDDFT time-steps/sec (8 clusters x 3 kicks per step)",
            "value": args.steps / (bat_ms * 1e-3), "unit": "time-steps/s", "n_gpus": 1,
@@ -894,7 +931,14 @@ def run_batch8(args):
                                     "grid": list(inputs.cluster(i).n), "N": inputs.cluster(i).N}
                                    for i in range(8)],
                       "precision": "mixed", "H_thrs": 1e-7, "initial_state": "P0 = diag(f)"},
-           "one_graph_per_step": {"value": args.steps / (bat_ms * 1e-3)},
+           "concurrent_sm_budgets": {"value": args.steps / (con_ms * 1e-3),
+                                     "ms_per_step": con_ms / args.steps,
+                                     "sm_budgets": [int(b) for b in budgets],
+                                     "solo_ms_per_step_whole_gpu": solo_ms,
+                                     "scf_passes_per_replica_step": con_passes,
+                                     "setup_s": setup_c, "autotune_choices": cchoices},
+           "one_graph_per_step_back_to_back": {"value": args.steps / (bat_ms * 1e-3),
+                                               "ms_per_step": bat_ms / args.steps},
            "contexts_one_after_another": {"value": args.steps / (seq_ms * 1e-3),
                                           "ms_per_step": seq_ms / args.steps,
                                           "scf_passes_per_replica_step": seq_passes},

@@ -167,6 +167,10 @@ typedef struct {
                               H_1 = 3 H_0 - 3 H_-1 + H_-2 (fewer passes when H varies smoothly;
                               the loop's H_thrs test still decides convergence).  H_-2 starts as
                               H_0, and after rmgtd_load or setting H_-1 it restarts from H_-1. */
+  int sm_budget;           /* > 0: every kernel grid of the context, the persistent Hartree and
+                              commutator kernels included, is sized to this many SMs instead of
+                              the device's; contexts whose budgets sum to at most the SM count
+                              then run concurrently inside one rmgtd_batch graph (0: all SMs) */
 } rmgtd_options;
 
 /* Per-step, per-replica statistics written by rmgtd_step. */
@@ -358,8 +362,11 @@ int rmgtd_set_hartree_preconditioner(rmgtd_ctx* ctx, int kind);
 int rmgtd_get_hartree_preconditioner(rmgtd_ctx* ctx, int* kind);
 
 /* Several contexts (different systems, each with its replicas) stepped by one CUDA graph per
- * time step: their steps are captured back to back into a single graph, launched once per
- * step on the contexts' common stream.  All contexts must use the same stream; attach the
+ * time step, launched once per step on the contexts' common stream.  When every context has
+ * an SM budget (rmgtd_options.sm_budget) their steps are captured on parallel branches of the
+ * graph and run concurrently, each on its share of the SMs; otherwise back to back.  Budgets
+ * that sum to more than the SM count are allowed but then the branches partly wait for one
+ * another.  All contexts must use the same stream; attach the
  * learned seed and autotune before creating the batch.  While in a batch a context refuses
  * rmgtd_step, rmgtd_attach_net and rmgtd_autotune (RMGTD_ESTATE); other calls work.
  * Errors: RMGTD_EINVAL (NULL, repeated or already-batched contexts, different streams). */

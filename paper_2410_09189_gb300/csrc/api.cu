@@ -329,6 +329,7 @@ void rmgtd_default_options(rmgtd_options* o) {
   o->ground_state_scf = 0;
   o->ground_state_tol = 1e-8;
   o->seed_order = 1;
+  o->sm_budget = 0;
 }
 
 const char* rmgtd_last_error(const rmgtd_ctx* ctx) {
@@ -382,6 +383,8 @@ static int create_impl(const rmgtd_system* sys, const rmgtd_options* opt, rmgtd_
   cudaDeviceProp prop;
   RMGTD_CUDA(ctx, cudaGetDeviceProperties(&prop, dev));
   ctx->num_sms = prop.multiProcessorCount;
+  if (opt->sm_budget > 0)   // every grid, persistent kernels included, sized to this share
+    ctx->num_sms = std::min(ctx->num_sms, opt->sm_budget);
   ctx->coop_ok = prop.cooperativeLaunch;
   if (!ctx->coop_ok) return set_error(ctx, RMGTD_ECUDA, "device lacks cooperative launch");
   // blocks of the grid-stride reduction kernels: about one point per thread up to 2048
@@ -696,6 +699,7 @@ int rmgtd_create(const rmgtd_system* sys, const rmgtd_options* opt_in, rmgtd_ctx
     return set_error(nullptr, RMGTD_EINVAL, "unknown precision");
   if (opt.magnus_order == 0) opt.magnus_order = 1;
   if (opt.seed_order == 0) opt.seed_order = 1;
+  if (opt.sm_budget < 0) return set_error(nullptr, RMGTD_EINVAL, "sm_budget must be >= 0");
   if (opt.seed_order != 1 && opt.seed_order != 2)
     return set_error(nullptr, RMGTD_EINVAL, "seed_order must be 1 or 2");
   if (opt.magnus_order != 1 && opt.magnus_order != 2)
@@ -1140,9 +1144,22 @@ struct rmgtd_batch {
   std::vector<rmgtd_ctx*> ctxs;
   cudaStream_t stream = nullptr;     // the contexts' common stream (launch stream)
   cudaStream_t capture = nullptr;    // library-owned capture stream
+  std::vector<cudaStream_t> branch;  // one forked capture stream per context (concurrent)
+  std::vector<cudaEvent_t> events;   // fork and join events of the capture
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
 };
+
+static void batch_release(rmgtd_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  for (cudaStream_t s : b->branch)
+    if (s) cudaStreamDestroy(s);
+  for (cudaEvent_t e : b->events)
+    if (e) cudaEventDestroy(e);
+  if (b->capture) cudaStreamDestroy(b->capture);
+  delete b;
+}
 
 int rmgtd_batch_create(rmgtd_ctx* const* ctxs, int n, rmgtd_batch** out) {
   if (!out) return set_error(nullptr, RMGTD_EINVAL, "batch_create: out is NULL");
@@ -1161,21 +1178,46 @@ int rmgtd_batch_create(rmgtd_ctx* const* ctxs, int n, rmgtd_batch** out) {
   b->ctxs.assign(ctxs, ctxs + n);
   b->stream = ctxs[0]->stream;
   auto fail = [&](int code, const std::string& msg) {
-    if (b->exec) cudaGraphExecDestroy(b->exec);
-    if (b->graph) cudaGraphDestroy(b->graph);
-    if (b->capture) cudaStreamDestroy(b->capture);
-    delete b;
+    batch_release(b);
     return set_error(nullptr, code, msg);
   };
+  // contexts with an SM budget run concurrently: each one's step is captured on its own
+  // stream forked from the capture stream and joined back; without budgets (every context
+  // sized to the whole GPU) they run one after another on the capture stream
+  bool concurrent = n > 1;
+  for (auto* c : b->ctxs) concurrent = concurrent && c->opt.sm_budget > 0;
   if (cudaStreamSynchronize(b->stream) != cudaSuccess ||
       cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking) != cudaSuccess)
     return fail(RMGTD_ECUDA, "batch_create: stream");
+  if (concurrent) {
+    b->branch.assign(n, nullptr);
+    b->events.assign(n + 1, nullptr);
+    for (int i = 0; i < n; ++i)
+      if (cudaStreamCreateWithFlags(&b->branch[i], cudaStreamNonBlocking) != cudaSuccess)
+        return fail(RMGTD_ECUDA, "batch_create: branch stream");
+    for (int i = 0; i <= n; ++i)
+      if (cudaEventCreateWithFlags(&b->events[i], cudaEventDisableTiming) != cudaSuccess)
+        return fail(RMGTD_ECUDA, "batch_create: event");
+  }
   if (cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeRelaxed) != cudaSuccess)
     return fail(RMGTD_ECUDA, "batch_create: begin capture");
   int rc = RMGTD_OK;
   int bad = -1;
+  if (concurrent && cudaEventRecord(b->events[n], b->capture) != cudaSuccess) {
+    rc = RMGTD_ECUDA;
+    bad = 0;
+  }
   for (int i = 0; i < n && !rc; ++i) {
-    rc = capture_step(b->ctxs[i], b->capture);
+    cudaStream_t s = b->capture;
+    if (concurrent) {
+      s = b->branch[i];
+      if (cudaStreamWaitEvent(s, b->events[n], 0) != cudaSuccess) rc = RMGTD_ECUDA;
+    }
+    if (!rc) rc = capture_step(b->ctxs[i], s);
+    if (!rc && concurrent &&
+        (cudaEventRecord(b->events[i], s) != cudaSuccess ||
+         cudaStreamWaitEvent(b->capture, b->events[i], 0) != cudaSuccess))
+      rc = RMGTD_ECUDA;
     if (rc) bad = i;
   }
   cudaGraph_t g = nullptr;
@@ -1185,7 +1227,7 @@ int rmgtd_batch_create(rmgtd_ctx* const* ctxs, int n, rmgtd_batch** out) {
   if (rc) {
     b->graph = nullptr;
     return fail(rc, std::string("batch_create: context ") + std::to_string(bad) + ": " +
-                        b->ctxs[bad]->err);
+                        (b->ctxs[bad]->err.empty() ? "capture failed" : b->ctxs[bad]->err));
   }
   b->graph = g;
   if (e != cudaSuccess) return fail(RMGTD_ECUDA, std::string("batch_create: ") + cudaGetErrorString(e));
@@ -1200,10 +1242,7 @@ void rmgtd_batch_destroy(rmgtd_batch* b) {
   if (!b) return;
   cudaStreamSynchronize(b->stream);
   for (auto* c : b->ctxs) c->in_batch = 0;
-  if (b->exec) cudaGraphExecDestroy(b->exec);
-  if (b->graph) cudaGraphDestroy(b->graph);
-  if (b->capture) cudaStreamDestroy(b->capture);
-  delete b;
+  batch_release(b);
 }
 
 int rmgtd_batch_step(rmgtd_batch* b, int nsteps, rmgtd_stats* const* stats) {

@@ -802,9 +802,14 @@ int rho_planes(rmgtd_ctx* ctx, const double* S, double* rho, float* drho, const 
   int slots = kRdMaxSlots;
   while (slots > 2 && rho_planes_smem(Np, slots) > (size_t)kSmemLimit) --slots;
   const size_t smem = rho_planes_smem(Np, slots);
+  // the attribute belongs to the function (process-wide, shared by every context): only ever
+  // raise it (a smaller N may need more shared memory: more slots fit)
   if (ctx->rho_pl_attr < (int)smem) {
-    RMGTD_CUDA(ctx, cudaFuncSetAttribute(k_rho_planes, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem));
+    cudaFuncAttributes fa;
+    RMGTD_CUDA(ctx, cudaFuncGetAttributes(&fa, k_rho_planes));
+    if ((size_t)fa.maxDynamicSharedSizeBytes < smem)
+      RMGTD_CUDA(ctx, cudaFuncSetAttribute(k_rho_planes, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem));
     ctx->rho_pl_attr = (int)smem;
   }
   const int ncta = std::max(1, ctx->num_sms / nrep);
@@ -834,9 +839,12 @@ int gram_planes(rmgtd_ctx* ctx, const float* w, const float* w_anchor, int nw, f
   int stages = kGpMaxStages;
   while (stages > 1 && gram_planes_smem(Np, stages) > (size_t)kSmemLimit) --stages;
   const size_t smem = gram_planes_smem(Np, stages);
-  if (ctx->gram_pl_attr < (int)smem) {
-    RMGTD_CUDA(ctx, cudaFuncSetAttribute(k_gram_planes,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (ctx->gram_pl_attr < (int)smem) {   // process-wide attribute: only ever raise it
+    cudaFuncAttributes fa;
+    RMGTD_CUDA(ctx, cudaFuncGetAttributes(&fa, k_gram_planes));
+    if ((size_t)fa.maxDynamicSharedSizeBytes < smem)
+      RMGTD_CUDA(ctx, cudaFuncSetAttribute(k_gram_planes,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     ctx->gram_pl_attr = (int)smem;
   }
   CUtensorMap tb;

@@ -583,7 +583,9 @@ int gram_mixed(rmgtd_ctx* ctx, const float* w, long wstride, int nw, double scal
   nsplit = (int)ceil_div(ctx->Ng, (long)chunk);   // no empty splits
   float* part = reinterpret_cast<float*>(ctx->gram_part);
   int rc = 1;
-  if (tc && ctx->phi_pl) {
+  // anchored weights exist only with the orbital planes, whose Gram is then always used (a
+  // tuning choice of the other Gram kernels applies to contexts without planes)
+  if ((tc || w_anchor) && ctx->phi_pl) {
     // orbital planes: one CTA per SM over (split, replica), chunks of whole 64-point stages
     int ps = std::max(1, ctx->num_sms / nw);
     ps = (int)std::min<long>(ps, (long)(2 * ctx->gram_part_elems) / std::max<long>(per, 1));
@@ -596,7 +598,11 @@ int gram_mixed(rmgtd_ctx* ctx, const float* w, long wstride, int nw, double scal
     }
   }
   if (w_anchor && rc != 0)
-    return set_error(ctx, RMGTD_ESTATE, "gram_mixed: anchored weights need the orbital planes");
+    return rc < 0 ? rc
+                  : set_error(ctx, RMGTD_ESTATE,
+                              std::string("gram_mixed: anchored weights need the orbital planes (") +
+                                  (ctx->phi_pl ? "planes declined" : "no planes") + ", tc " +
+                                  std::to_string((int)tc) + ")");
   if (rc > 0 && tc) rc = gram_tc(ctx, w, nw, part, nsplit, chunk, ctl);
   if (rc < 0) return rc;
   if (rc > 0) {

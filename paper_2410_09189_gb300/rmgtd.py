@@ -64,6 +64,7 @@ class COptions(ctypes.Structure):
         ("magnus_order", ctypes.c_int), ("nonorthogonal", ctypes.c_int),
         ("grid_basis", ctypes.c_int), ("ground_state_scf", ctypes.c_int),
         ("ground_state_tol", ctypes.c_double), ("seed_order", ctypes.c_int),
+        ("sm_budget", ctypes.c_int),
     ]
 
 
@@ -171,7 +172,7 @@ class Context:
                  mixed_poisson_tol: float = 0.0, magnus_order: int = 1,
                  nonorthogonal: bool = False, grid_basis: bool = False,
                  ground_state_scf: int = 0, ground_state_tol: float = 1e-8,
-                 seed_order: int = 1):
+                 seed_order: int = 1, sm_budget: int = 0):
         import torch
 
         lib = load_library()
@@ -233,6 +234,7 @@ class Context:
         opt.ground_state_scf = int(ground_state_scf)
         opt.ground_state_tol = float(ground_state_tol)
         opt.seed_order = int(seed_order)
+        opt.sm_budget = int(sm_budget)
         if nonorthogonal:
             opt.orthonormalize = 0
         if stream is None:

@@ -37,17 +37,21 @@ def _make(lib, spec, precision, **kw):
     return ctx
 
 
+@pytest.mark.parametrize("budget", [0, 48])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_batch_matches_separate_contexts_bitwise(lib, precision):
+def test_batch_matches_separate_contexts_bitwise(lib, precision, budget):
+    """budget 0: the systems run back to back in the graph; budget 48: each context's grids
+    are sized to 48 SMs and the three run concurrently on parallel branches (3 x 48 <= the SM
+    count); either way every context matches its separately stepped twin bit for bit."""
     prec = lib.PREC_FP64 if precision == "fp64" else lib.PREC_MIXED
     nsteps = 6
     solo = []
     for spec in SYSTEMS:
-        ctx = _make(lib, spec, prec)
+        ctx = _make(lib, spec, prec, sm_budget=budget)
         st = ctx.step(nsteps)
         solo.append(([ctx.dipole(a) for a in range(3)], st["passes"].copy()))
         ctx.close()
-    ctxs = [_make(lib, spec, prec) for spec in SYSTEMS]
+    ctxs = [_make(lib, spec, prec, sm_budget=budget) for spec in SYSTEMS]
     batch = lib.Batch(ctxs)
     with pytest.raises(lib.RmgtdError):
         ctxs[0].step(1)               # a batched context is stepped through its batch
