@@ -409,6 +409,10 @@ static int create_impl(const rmgtd_system* sys, const rmgtd_options* opt, rmgtd_
   ctx->H0 = (double*)A(msz * nrep);
   ctx->Hm1 = (double*)A(msz * nrep);
   if (opt->seed_order == 2) ctx->Hm2 = (double*)A(msz * nrep);
+  if (opt->precision == RMGTD_PREC_MIXED && !opt->grid_basis && N > 64) {
+    ctx->hbar32 = (float*)A(sizeof(float) * NN * nrep);
+    ctx->dbuf32 = (float*)A(sizeof(float) * 4 * NN * nrep);
+  }
   ctx->H1 = (double*)A(msz * nrep);
   ctx->dbuf = (double*)A(4 * msz * nrep);
   ctx->rho = (double*)A(gsz * nrep);
@@ -772,7 +776,8 @@ static int enqueue_pass(rmgtd_ctx* ctx, cudaGraphConditionalHandle cond, int use
   int rc = magnus_prepare(ctx, &Ha, &Hb, &hstride, &febar, &D);
   if (!rc)
     rc = eldyn(ctx, Ha, Hb, hstride, ctx->opt.dt, ctx->S0, ctx->A0, ctx->S1, ctx->A1, ctx->ctl,
-               ctx->ctl, 0, ctx->nrep, ctx->mixed ? ctx->shat32 : nullptr, febar, D);
+               ctx->ctl, 0, ctx->nrep, ctx->mixed ? ctx->shat32 : nullptr, febar, D,
+               ctx->mixed != 0);
   ph_end(ctx);
   if (rc) return rc;
   rc = dft_eval(ctx, ctx->S1, ctx->ctl, ctx->errbits);

@@ -707,6 +707,12 @@ struct EldynArgs {
   // E(t_j) and E(t_j + dt) (Algorithm 1's V_{j-1} + V_j in Omega)
   const double* fM;       // [3][N*N] dipole matrices
   const double* febar;    // [rep][3]
+  // float32 tail (mixed path, cooperative kernel): terms k >= kf from hbar32 = Hbar in float32
+  // and the previous term in float32 (dbuf32 [rep][2][2][N*N]); P_1 stays float64.  kf = 0:
+  // every term in float64
+  int kf;
+  const float* hbar32;
+  float* dbuf32;
   // second-order Magnus term (NULL: none): Omega = -i tau (Hbar + i D), D = (tau/12)[H_0, H_1]
   // real antisymmetric per replica (stride N*N), so the series multiplies by the Hermitian
   // K = Hbar + i D: T1 = Im(K dP) = Hbar A + D S, T2 = Re(K dP) = Hbar S - D A
@@ -721,7 +727,7 @@ __device__ __forceinline__ double field_term(const EldynArgs& a, int rep, long o
   return e[0] * a.fM[o] + e[1] * a.fM[NN + o] + e[2] * a.fM[2 * NN + o];
 }
 
-template <int TS, int NT, bool WD>
+template <int TS, int NT, bool WD, bool FT>
 __global__ void __launch_bounds__(NT) k_eldyn(EldynArgs a) {
   constexpr int KC = 32;
   constexpr int TSP = TS + 1;
@@ -738,6 +744,12 @@ __global__ void __launch_bounds__(NT) k_eldyn(EldynArgs a) {
   double* Di = Tt + 4 * TS * TSP;    // [TS][KC+1] rows of D (only with the Omega_2 term)
   double* Dj = Di + TS * (KC + 1);
   constexpr bool wd = WD;   // with the Omega_2 term (a.D != NULL)
+  float* fHi = reinterpret_cast<float*>(Hi);   // float32 views of the tiles (float32 tail)
+  float* fHj = reinterpret_cast<float*>(Hj);
+  float* fAi = reinterpret_cast<float*>(Ai);
+  float* fAj = reinterpret_cast<float*>(Aj);
+  float* fSi = reinterpret_cast<float*>(Si);
+  float* fSj = reinterpret_cast<float*>(Sj);
   __shared__ double sh[32];
   __shared__ int conv[32];
   __shared__ int all_done;
@@ -794,7 +806,62 @@ __global__ void __launch_bounds__(NT) k_eldyn(EldynArgs a) {
       double acc[OPT];
 #pragma unroll
       for (int u = 0; u < OPT; ++u) acc[u] = 0.0;
-      for (int k0 = 0; k0 < N; k0 += KC) {
+      const bool fk = FT && k >= a.kf;   // this term in float32
+      float* foS = FT ? a.dbuf32 + ((long)rep * 4 + (k & 1) * 2) * NN : nullptr;
+      float* foA = FT ? foS + NN : nullptr;
+      if (fk) {
+        // the previous term in float32 (the last float64 term also wrote its float32 copy)
+        const float* pS = a.dbuf32 + ((long)rep * 4 + ((k - 1) & 1) * 2) * NN;
+        const float* pA = pS + NN;
+        const float* Hf = a.hbar32 + rep * NN;
+        for (int k0 = 0; k0 < N; k0 += KC) {
+          for (int e = tid; e < TS * KC; e += NT) {
+            const int r = e / KC, kk = e % KC;
+            const int kg = k0 + kk;
+            const int ri = I * TS + r, rj = J * TS + r;
+            fHi[r * (KC + 1) + kk] = (kg < N && ri < N) ? Hf[(long)ri * N + kg] : 0.0f;
+            fHj[r * (KC + 1) + kk] = (kg < N && rj < N) ? Hf[(long)rj * N + kg] : 0.0f;
+          }
+          for (int e = tid; e < KC * TS; e += NT) {
+            const int kk = e / TS, b = e % TS;
+            const int kg = k0 + kk;
+            const int ci = I * TS + b, cj = J * TS + b;
+            float ai = 0.f, aj = 0.f, si = 0.f, sj = 0.f;
+            if (kg < N) {
+              if (ci < N) {
+                ai = pA[(long)kg * N + ci];
+                si = pS[(long)kg * N + ci];
+              }
+              if (cj < N) {
+                aj = pA[(long)kg * N + cj];
+                sj = pS[(long)kg * N + cj];
+              }
+            }
+            fAi[kk * TSP + b] = ai;
+            fAj[kk * TSP + b] = aj;
+            fSi[kk * TSP + b] = si;
+            fSj[kk * TSP + b] = sj;
+          }
+          __syncthreads();
+#pragma unroll
+          for (int u = 0; u < OPT; ++u) {
+            const int o = tid + NT * u;
+            const int q = o / (TS * TS), e = o % (TS * TS);
+            const int ra = e / TS, cb = e % TS;
+            const float* Hx = (q == 0 || q == 2) ? fHi : fHj;
+            const float* Dx = (q == 0) ? fAj : (q == 1) ? fAi : (q == 2) ? fSj : fSi;
+            float s0 = 0.f, s1 = 0.f;
+#pragma unroll 8
+            for (int kk = 0; kk < KC; kk += 2) {
+              s0 = fmaf(Hx[ra * (KC + 1) + kk], Dx[kk * TSP + cb], s0);
+              s1 = fmaf(Hx[ra * (KC + 1) + kk + 1], Dx[(kk + 1) * TSP + cb], s1);
+            }
+            acc[u] += (double)(s0 + s1);
+          }
+          __syncthreads();
+        }
+      }
+      for (int k0 = 0; k0 < (fk ? 0 : N); k0 += KC) {
         for (int e = tid; e < TS * KC; e += NT) {
           const int r = e / KC, kk = e % KC;
           const int kg = k0 + kk;
@@ -883,14 +950,26 @@ __global__ void __launch_bounds__(NT) k_eldyn(EldynArgs a) {
         const double ns = c * (t1ij + t1ji);
         const double na = -c * (t2ij - t2ji);
         const long o = (long)i * N + j;
-        oS[o] = ns;
-        oA[o] = na;
+        if (FT && k + 1 >= a.kf) {   // the next term reads this one in float32
+          foS[o] = (float)ns;
+          foA[o] = (float)na;
+        }
+        if (!fk) {
+          oS[o] = ns;
+          oA[o] = na;
+        }
         a.S1[rep * NN + o] += ns;
         a.A1[rep * NN + o] += na;
         if (I != J) {
           const long ot = (long)j * N + i;
-          oS[ot] = ns;
-          oA[ot] = -na;
+          if (FT && k + 1 >= a.kf) {
+            foS[ot] = (float)ns;
+            foA[ot] = (float)-na;
+          }
+          if (!fk) {
+            oS[ot] = ns;
+            oA[ot] = -na;
+          }
           a.S1[rep * NN + ot] += ns;
           a.A1[rep * NN + ot] -= na;
         }
@@ -938,19 +1017,19 @@ __global__ void __launch_bounds__(NT) k_eldyn(EldynArgs a) {
   }
 }
 
-template <int TS, int NT, bool WD>
+template <int TS, int NT, bool WD, bool FT>
 static int launch_eldyn_tsd(rmgtd_ctx* ctx, EldynArgs& a) {
   const int KC = 32;
   const size_t smem = sizeof(double) * (2 * TS * (KC + 1) + 4 * KC * (TS + 1) + 4 * TS * (TS + 1) +
                                         (a.D ? 2 * TS * (KC + 1) : 0));
   static size_t attr_set = 0;
   if (attr_set < smem) {
-    RMGTD_CUDA(ctx, cudaFuncSetAttribute(k_eldyn<TS, NT, WD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    RMGTD_CUDA(ctx, cudaFuncSetAttribute(k_eldyn<TS, NT, WD, FT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem));
     attr_set = smem;
   }
   int per_sm = 0;
-  RMGTD_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_eldyn<TS, NT, WD>, NT, smem));
+  RMGTD_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_eldyn<TS, NT, WD, FT>, NT, smem));
   if (per_sm < 1) return set_error(ctx, RMGTD_ECUDA, "commutator kernel does not fit on an SM");
   const int T = (a.N + TS - 1) / TS;
   const int total = T * (T + 1) / 2 * a.nrep;
@@ -970,14 +1049,26 @@ static int launch_eldyn_tsd(rmgtd_ctx* ctx, EldynArgs& a) {
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  RMGTD_CUDA(ctx, cudaLaunchKernelExC(&cfg, (const void*)k_eldyn<TS, NT, WD>, args));
+  RMGTD_CUDA(ctx, cudaLaunchKernelExC(&cfg, (const void*)k_eldyn<TS, NT, WD, FT>, args));
   ++ctx->launches;
   return RMGTD_OK;
 }
 
 template <int TS, int NT>
 static int launch_eldyn_ts(rmgtd_ctx* ctx, EldynArgs& a) {
-  return a.D ? launch_eldyn_tsd<TS, NT, true>(ctx, a) : launch_eldyn_tsd<TS, NT, false>(ctx, a);
+  if (a.D) return launch_eldyn_tsd<TS, NT, true, false>(ctx, a);
+  if (a.kf > 0) return launch_eldyn_tsd<TS, NT, false, true>(ctx, a);
+  return launch_eldyn_tsd<TS, NT, false, false>(ctx, a);
+}
+
+// Hbar in float32 for the float32 tail: out_r = (Ha_r + Hb_r)/2
+__global__ void k_hbar32(long NN, int nrep, const double* __restrict__ Ha, const double* __restrict__ Hb,
+                         long hstride, float* __restrict__ out) {
+  for (long x = blockIdx.x * (long)blockDim.x + threadIdx.x; x < NN * nrep;
+       x += (long)gridDim.x * blockDim.x) {
+    const long r = x / NN, o = x - r * NN;
+    out[x] = (float)(0.5 * (Ha[r * hstride + o] + Hb[r * hstride + o]));
+  }
 }
 
 // Commutator series of one replica on one thread-block cluster (N <= 64).  The C CTAs of the
@@ -1240,12 +1331,15 @@ static int eldyn_cluster_size(rmgtd_ctx* ctx) {
 int eldyn(rmgtd_ctx* ctx, const double* Ha, const double* Hb, long hstride, double tau,
           const double* S0, const double* A0, double* S1, double* A1, const RepCtl* ctl_in,
           RepCtl* ctl_out, int rep0, int nreps, float* shat_out, const double* febar,
-          const double* D) {
+          const double* D, bool f32_tail) {
   if (nreps > 32) return set_error(ctx, RMGTD_EINVAL, "at most 32 replicas per expansion");
   EldynArgs a;
   a.fM = ctx->M;
   a.febar = febar;
   a.D = D;
+  a.kf = 0;
+  a.hbar32 = nullptr;
+  a.dbuf32 = nullptr;
   a.N = ctx->N;
   a.nrep = nreps;
   a.rep0 = rep0;
@@ -1288,6 +1382,18 @@ int eldyn(rmgtd_ctx* ctx, const double* Ha, const double* Hb, long hstride, doub
     a.Ha = a.Hb = ctx->Hx0;
     a.hstride = (long)ctx->N * ctx->N;
     a.febar = nullptr;
+  }
+  if (f32_tail && !a.D && ctx->hbar32 && ctx->dbuf32) {
+    // terms from the third on in float32: a term is ~(tau |Hbar|)^k / k! of P, so its float32
+    // rounding stays far below dP_thrs of P; the running P_1 stays float64
+    const long NN = (long)ctx->N * ctx->N;
+    k_hbar32<<<(int)std::min<long>(ceil_div(NN * nreps, 256), 4L * ctx->num_sms), 256, 0, ctx->stream>>>(
+        NN, nreps, a.Ha, a.Hb, a.hstride, ctx->hbar32);
+    ++ctx->launches;
+    RMGTD_LAUNCH(ctx, "k_hbar32");
+    a.kf = 3;
+    a.hbar32 = ctx->hbar32;
+    a.dbuf32 = ctx->dbuf32;
   }
   // GB300's float64 units (~2 FMA per clock and SM) bound the series: pick the tile size
   // whose symmetric tile pairs spread the work of a term most evenly over the SMs (the most

@@ -251,6 +251,8 @@ struct rmgtd_ctx {
   double* Gm = nullptr;
   double* Dm = nullptr;
   double* Hm2 = nullptr;        // H two steps earlier (opt.seed_order 2), [nrep][N*N]
+  float* hbar32 = nullptr;      // mixed path, N > 64: Hbar in float32 [nrep][N*N] and the
+  float* dbuf32 = nullptr;      // float32 series terms [nrep][2][2][N*N] (the series' tail)
   double* Hx0 = nullptr;        // scratch [nrep][N*N] x 2: H_0 + V_0, H_1 + V_1 (Omega_2)
   double* Hx1 = nullptr;
   // propagation on the grid (opt.grid_basis): occupied orbitals [nrep][2][N][Ng] (planar
@@ -467,7 +469,8 @@ int tile_orbitals(rmgtd_ctx* ctx);
 int eldyn(rmgtd_ctx* ctx, const double* Ha, const double* Hb, long hstride, double tau,
           const double* S0, const double* A0, double* S1, double* A1, const RepCtl* ctl_in,
           RepCtl* ctl_out, int rep0, int nreps,
-          float* shat_out = nullptr, const double* febar = nullptr, const double* D = nullptr);
+          float* shat_out = nullptr, const double* febar = nullptr, const double* D = nullptr,
+          bool f32_tail = false);
 // k_magnus.cu: the non-orthogonal basis and the second-order Magnus term
 // set-up of the non-orthogonal basis: Sinv = S^-1 and P_0 = L^-T diag(f) L^-1 for every replica
 int nonorth_setup(rmgtd_ctx* ctx);
