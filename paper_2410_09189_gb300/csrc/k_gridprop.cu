@@ -12,8 +12,12 @@
 // (mixed path: the terms of a smooth orbital shrink fast, and a term's float32 rounding is
 // carried forward by the remaining, unitary, series, so the sum keeps ~1e-7 of |psi|).  One
 // fused kernel per term: the 12th-order stencil of both planes, the potential, the KB part
-// from per-point projector lists, the update psi_1 += t and the stopping maximum.  The host
-// drives the term and pass loops (one small read-back per term for the stopping test).
+// from per-point projector lists, the running sum and the stopping maximum.  With float64
+// terms the sum is psi_1 itself (psi_1 += t); with float32 terms it is a compensated float32
+// pair (hi + lo, the two-sum of Knuth) folded into psi_1 = psi + hi + lo once the series ends,
+// so that no float64 arithmetic is left in the term kernel (GB300's float64 pipe runs at 1/64
+// of its float32 rate).  The host drives the term and pass loops (one small read-back per
+// term for the stopping test).
 #include <cstring>
 #include <utility>
 
@@ -81,7 +85,29 @@ __global__ void k_gp_vtot(const double* __restrict__ vion, const double* __restr
   }
 }
 
-// start of a pass for the active replicas: psi_1 = psi, t = psi (in the terms' precision)
+// the stencil and series coefficients of one term in the terms' precision, formed on the
+// host and read by the kernels from their parameter space: cm[m] = a_m (-1/(2h^2)) for the
+// 12th-order Laplacian, c0 = 3 a_0 (-1/(2h^2)), c = dt / k.  (Formed in the kernels, the
+// float64 products would be recomputed for every plane where registers are short.)
+template <typename T>
+struct GpTermCoef {
+  T cm[kFdRadius + 1];
+  T c0;
+  T c;
+};
+
+template <typename T>
+GpTermCoef<T> gp_term_coef(double h, double c) {
+  GpTermCoef<T> k{};
+  const double cscale = -0.5 / (h * h);
+  for (int m = 1; m <= kFdRadius; ++m) k.cm[m] = (T)(fd_coef(m) * cscale);
+  k.c0 = (T)(3.0 * fd_coef(0) * cscale);
+  k.c = (T)c;
+  return k;
+}
+
+// start of a pass for the active replicas: t = psi (in the terms' precision) and, with
+// float64 terms, psi_1 = psi (psi1 null: float32 terms, whose sum starts at the first term)
 template <typename T>
 __global__ void k_gp_start(const double* __restrict__ psi, double* __restrict__ psi1,
                            T* __restrict__ t, long rplane, const int* __restrict__ active) {
@@ -90,24 +116,161 @@ __global__ void k_gp_start(const double* __restrict__ psi, double* __restrict__ 
   for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < rplane;
        e += (long)gridDim.x * blockDim.x) {
     const long o = r * rplane + e;
-    psi1[o] = psi[o];
+    if (psi1) psi1[o] = psi[o];
     t[o] = (T)psi[o];
   }
 }
 
+// s + e = a + b exactly, s = fl(a + b) (Knuth's two-sum: six additions, no branch)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bp = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
+}
+
+// the series' running sum at element o: float64 terms add to psi_1; float32 terms to the
+// pair (hi at o, lo at o + lo_off) by a two-sum, the first term setting it
+__device__ __forceinline__ void series_add(double* a, long o, long, double v, bool) { a[o] += v; }
+__device__ __forceinline__ void series_add(float* a, long o, long lo_off, float v, bool first) {
+  if (first) {
+    a[o] = v;
+    a[o + lo_off] = 0.f;
+    return;
+  }
+  float s, e;
+  two_sum(a[o], v, s, e);
+  a[o] = s;
+  a[o + lo_off] += e;
+}
+
+// after term k: the stopping test of every running series on the device, so that the host
+// can queue several terms between read-backs.  ctl = [running][status][terms] per replica;
+// a series stops when max|t|^2 <= thr2 (converged), is not finite (diverged) or k reaches
+// the term limit; errbits is cleared for the next term.
+__global__ void k_gp_series_ctl(int nrep, int k, double thr2, int max_terms, int* __restrict__ ctl,
+                                unsigned long long* __restrict__ errbits) {
+  for (int r = threadIdx.x; r < nrep; r += blockDim.x) {
+    if (!ctl[r]) continue;
+    const double m = __longlong_as_double((long long)errbits[r]);
+    errbits[r] = 0ull;
+    int st = 0;
+    bool stop = true;
+    if (!(m <= 1e300)) st = RMGTD_EDIVERGED;
+    else if (m <= thr2) st = 0;
+    else if (k >= max_terms) st = RMGTD_ENOTCONVERGED;
+    else stop = false;
+    if (stop) {
+      ctl[r] = 0;
+      ctl[nrep + r] = st;
+      ctl[2 * nrep + r] = k;
+    }
+  }
+}
+
+// end of a float32 series for the active replicas: psi_1 = psi + (hi + lo)
+__global__ void k_gp_fold(const double* __restrict__ psi, const float* __restrict__ acc,
+                          long lo_off, double* __restrict__ psi1, long rplane,
+                          const int* __restrict__ active) {
+  const int r = blockIdx.y;
+  if (!active[r]) return;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < rplane;
+       e += (long)gridDim.x * blockDim.x) {
+    const long o = r * rplane + e;
+    psi1[o] = psi[o] + ((double)acc[o] + (double)acc[o + lo_off]);
+  }
+}
+
+// KB projections of the real columns j of x (the term planes): coef[j][p] =
+// h^3 sum_e beta_p(e) x_j(g_e) over projector p's box, g_e the box entry's grid index.
+// Block (p, group of kKbCols columns): each thread takes every blockDim-th entry, four at a
+// time (their indexes, values and the kKbCols column values all in flight together), and
+// keeps one sum per column: float64 columns in float64, float32 columns in compensated
+// float32 (Kahan); the block then reduces each column in float64 in a fixed order.  Columns
+// of replicas whose series has stopped are skipped (cols_per_rep columns per replica).
+constexpr int kKbCols = 4, kKbThreads = 1024;
+
+template <typename T>
+__global__ void __launch_bounds__(kKbThreads)
+k_gp_kb_project(const T* __restrict__ x, long Ng, int ncols, int cols_per_rep,
+                const int* __restrict__ sact, const long long* __restrict__ off,
+                const int* __restrict__ pt, const T* __restrict__ pv, double h3,
+                T* __restrict__ coef) {
+  const int p = blockIdx.x, np = gridDim.x, j0 = blockIdx.y * kKbCols;
+  const long long e0 = off[p];
+  const int nb = (int)(off[p + 1] - e0);
+  const int* ptp = pt + e0;
+  const T* pvp = pv + e0;
+  __shared__ double sh[kKbCols][kKbThreads / 32];
+  bool act[kKbCols], any = false;
+  const T* xc[kKbCols];
+#pragma unroll
+  for (int c = 0; c < kKbCols; ++c) {
+    const int j = min(j0 + c, ncols - 1);
+    act[c] = j0 + c < ncols && sact[j / cols_per_rep];
+    any = any || act[c];
+    xc[c] = x + (long)j * Ng;
+  }
+  if (!any) return;   // uniform over the block
+  T s[kKbCols], comp[kKbCols];
+#pragma unroll
+  for (int c = 0; c < kKbCols; ++c) s[c] = comp[c] = (T)0;
+  const int step = blockDim.x;
+  for (int e = threadIdx.x; e < nb; e += 4 * step) {
+    int g[4];
+    T b[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int eu = e + u * step;
+      g[u] = eu < nb ? ptp[eu] : 0;
+      b[u] = eu < nb ? pvp[eu] : (T)0;
+    }
+    T xv[kKbCols][4];
+#pragma unroll
+    for (int c = 0; c < kKbCols; ++c)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) xv[c][u] = act[c] ? xc[c][g[u]] : (T)0;
+#pragma unroll
+    for (int c = 0; c < kKbCols; ++c)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const T v = b[u] * xv[c][u];
+        if constexpr (sizeof(T) == sizeof(double)) {
+          s[c] += v;
+        } else {
+          const T y = v - comp[c], t = s[c] + y;
+          comp[c] = (t - s[c]) - y;
+          s[c] = t;
+        }
+      }
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int c = 0; c < kKbCols; ++c) {
+    const double v = warp_sum((double)s[c] - (double)comp[c]);
+    if (lane == 0) sh[c][w] = v;
+  }
+  __syncthreads();
+  if (w < kKbCols) {
+    const int c = w;
+    double v = lane < nw ? sh[c][lane] : 0.0;
+    v = warp_sum(v);
+    if (lane == 0 && j0 + c < ncols) coef[(long)(j0 + c) * np + p] = (T)(h3 * v);
+  }
+}
+
 // One term of the orbital series for orbital n of replica r over a z-range:
-//   t_out = (-i c) (T + V + V_NL) t_in,  psi_1 += t_out,  errbits_r <- max |t_out|^2,
-// c = dt / k.  Block BX x BY over an x-y tile, marching along z with each thread's z-column
+//   t_out = (-i c) (T + V + V_NL) t_in,  sum += t_out,  errbits_r <- max |t_out|^2,
+// c = dt / k (the sum: psi_1 for float64 terms, the float32 pair for float32 terms).  Block BX x BY over an x-y tile, marching along z with each thread's z-column
 // (both planes) in registers; the x-y neighbourhood of every plane staged in shared memory
 // with a 6-point halo (zero outside the grid: Dirichlet ghosts).  The KB part reads the
 // point's projector list (E_p beta_p(r)) and the projections of t_in.
 template <typename T, int BX, int BY>
 __global__ void __launch_bounds__(BX * BY)
-k_gp_term_fused(const T* __restrict__ tin, T* __restrict__ tout, double* __restrict__ psi1,
-                const T* __restrict__ vtot, const int* __restrict__ kb_row,
-                const int* __restrict__ kb_p, const double* __restrict__ kb_val,
-                const double* __restrict__ coef, int np, int nocc, int nx, int ny, int nz,
-                int zchunk, int nzc, double cscale, double c, const int* __restrict__ sact,
+k_gp_term_fused(const T* __restrict__ tin, T* __restrict__ tout, T* __restrict__ acc, long lo_off,
+                int first, const T* __restrict__ vtot, const int* __restrict__ kb_row,
+                const int* __restrict__ kb_p, const T* __restrict__ kb_w,
+                const T* __restrict__ coef, int np, int nocc, int nx, int ny, int nz,
+                int zchunk, int nzc, const GpTermCoef<T> kc, const int* __restrict__ sact,
                 unsigned long long* __restrict__ errbits) {
   constexpr int R = kFdRadius;
   constexpr int TX = BX + 2 * R, TY = BY + 2 * R;
@@ -127,15 +290,9 @@ k_gp_term_fused(const T* __restrict__ tin, T* __restrict__ tout, double* __restr
   const T* xi = xr + oplane;
   T* yr = tout + base;
   T* yi = yr + oplane;
-  double* pr = psi1 + base;
-  double* pim = pr + oplane;
   const T* v = vtot + (long)rep * Ng;
-  const double* cre = coef + (long)(2 * (rep * 2 * nocc + n)) * np;          // column re
-  const double* cim = coef + (long)(2 * (rep * 2 * nocc + nocc + n)) * np;   // column im
-  T cm[R + 1];
-#pragma unroll
-  for (int m = 1; m <= R; ++m) cm[m] = (T)(fd_coef(m) * cscale);
-  const T c0 = (T)(3.0 * fd_coef(0) * cscale);
+  const T* cre = coef + (long)(rep * 2 * nocc + n) * np;          // column re
+  const T* cim = coef + (long)(rep * 2 * nocc + nocc + n) * np;   // column im
   T qr[2 * R + 1], qi[2 * R + 1];
 #pragma unroll
   for (int k = 0; k < 2 * R; ++k) {
@@ -145,7 +302,7 @@ k_gp_term_fused(const T* __restrict__ tin, T* __restrict__ tout, double* __restr
     qr[k] = ok ? xr[g] : (T)0;
     qi[k] = ok ? xi[g] : (T)0;
   }
-  double emax = 0.0;
+  T emax = (T)0;
   for (int z = z0; z < z1; ++z) {
     {
       const int zz = z + R;
@@ -170,36 +327,36 @@ k_gp_term_fused(const T* __restrict__ tin, T* __restrict__ tout, double* __restr
     __syncthreads();
     if (in_xy) {
       const long g = (long)z * plane + (long)iy * nx + ix;
-      T ar = c0 * qr[R], ai = c0 * qi[R];
+      T ar = kc.c0 * qr[R], ai = kc.c0 * qi[R];
 #pragma unroll
       for (int m = 1; m <= R; ++m) {
         const T sr = (sre[ty + R][tx + R + m] + sre[ty + R][tx + R - m]) +
                      (sre[ty + R + m][tx + R] + sre[ty + R - m][tx + R]) + (qr[R + m] + qr[R - m]);
         const T si = (sim[ty + R][tx + R + m] + sim[ty + R][tx + R - m]) +
                      (sim[ty + R + m][tx + R] + sim[ty + R - m][tx + R]) + (qi[R + m] + qi[R - m]);
-        ar = fma(cm[m], sr, ar);
-        ai = fma(cm[m], si, ai);
+        ar = fma(kc.cm[m], sr, ar);
+        ai = fma(kc.cm[m], si, ai);
       }
       const T vv = v[g];
       ar = fma(vv, qr[R], ar);
       ai = fma(vv, qi[R], ai);
       if (kb_row) {
-        double kr = 0.0, ki = 0.0;
+        T kr = (T)0, ki = (T)0;
         for (int e = kb_row[g]; e < kb_row[g + 1]; ++e) {
           const int p = kb_p[e];
-          const double w = kb_val[e];
+          const T w = kb_w[e];
           kr = fma(w, cre[p], kr);
           ki = fma(w, cim[p], ki);
         }
-        ar += (T)kr;
-        ai += (T)ki;
+        ar += kr;
+        ai += ki;
       }
-      const T nr = (T)c * ai, ni = -(T)c * ar;   // -i c (ar + i ai)
+      const T nr = kc.c * ai, ni = -kc.c * ar;   // -i c (ar + i ai)
       yr[g] = nr;
       yi[g] = ni;
-      pr[g] += (double)nr;
-      pim[g] += (double)ni;
-      emax = fmax(emax, (double)nr * (double)nr + (double)ni * (double)ni);
+      series_add(acc, base + g, lo_off, nr, first);
+      series_add(acc, base + oplane + g, lo_off, ni, first);
+      emax = fmax(emax, nr * nr + ni * ni);   // in the terms' precision (a stopping test)
     }
     __syncthreads();
 #pragma unroll
@@ -208,8 +365,8 @@ k_gp_term_fused(const T* __restrict__ tin, T* __restrict__ tout, double* __restr
       qi[k] = qi[k + 1];
     }
   }
-  emax = block_max(emax, sh);
-  if (tid == 0) atomic_max_nonneg(&errbits[rep], emax);
+  const double bm = block_max((double)emax, sh);
+  if (tid == 0) atomic_max_nonneg(&errbits[rep], bm);
 }
 
 // The same term with the x-y tiles streamed by TMA: thread 0 keeps kGtS planes of the chunk
@@ -236,10 +393,11 @@ __global__ void __launch_bounds__(BX * BY)
 k_gp_term_tma(const __grid_constant__ CUtensorMap tm_in, const T* __restrict__ tin,
               T* __restrict__ tout, double* __restrict__ psi1, const T* __restrict__ vtot,
               const int* __restrict__ kb_row, const int* __restrict__ kb_p,
-              const double* __restrict__ kb_val, const double* __restrict__ coef, int np, int nocc,
-              int nx, int ny, int nz, int zchunk, int nzc, double cscale, double c,
+              const T* __restrict__ kb_w, const T* __restrict__ coef, int np, int nocc,
+              int nx, int ny, int nz, int zchunk, int nzc, const GpTermCoef<T> kc,
               const int* __restrict__ sact, unsigned long long* __restrict__ errbits,
               int* __restrict__ status) {
+  static_assert(sizeof(T) == sizeof(double), "float32 terms use k_gp_term_tma2");
   constexpr int R = kFdRadius;
   constexpr int TW = BX + 2 * kGtXO;            // tile row length
   constexpr int TE = gt_tile_elems<T, BX, BY>();
@@ -279,12 +437,8 @@ k_gp_term_tma(const __grid_constant__ CUtensorMap tm_in, const T* __restrict__ t
   double* pr = psi1 + base;
   double* pim = pr + oplane;
   const T* v = vtot + (long)rep * Ng;
-  const double* cre = coef + (long)(2 * cre_col) * np;
-  const double* cim = coef + (long)(2 * cim_col) * np;
-  T cm[R + 1];
-#pragma unroll
-  for (int m = 1; m <= R; ++m) cm[m] = (T)(fd_coef(m) * cscale);
-  const T c0 = (T)(3.0 * fd_coef(0) * cscale);
+  const T* cre = coef + (long)cre_col * np;
+  const T* cim = coef + (long)cim_col * np;
   const long gxy = (long)iy * nx + ix;
   T qr[2 * R + 1], qi[2 * R + 1];
 #pragma unroll
@@ -347,30 +501,30 @@ k_gp_term_tma(const __grid_constant__ CUtensorMap tm_in, const T* __restrict__ t
     const T* ti = tr + TE;
     if (in_xy && ok) {
       const long g = (long)(z0 + i) * plane + gxy;
-      T ar = c0 * qr[R], ai = c0 * qi[R];
+      T ar = kc.c0 * qr[R], ai = kc.c0 * qi[R];
 #pragma unroll
       for (int m = 1; m <= R; ++m) {
         const T sr = (tr[ly * TW + lx + m] + tr[ly * TW + lx - m]) +
                      (tr[(ly + m) * TW + lx] + tr[(ly - m) * TW + lx]) + (qr[R + m] + qr[R - m]);
         const T si = (ti[ly * TW + lx + m] + ti[ly * TW + lx - m]) +
                      (ti[(ly + m) * TW + lx] + ti[(ly - m) * TW + lx]) + (qi[R + m] + qi[R - m]);
-        ar = fma(cm[m], sr, ar);
-        ai = fma(cm[m], si, ai);
+        ar = fma(kc.cm[m], sr, ar);
+        ai = fma(kc.cm[m], si, ai);
       }
       ar = fma(c_vv, qr[R], ar);
       ai = fma(c_vv, qi[R], ai);
       if (c_kb1 > c_kb0) {
-        double kr = 0.0, ki = 0.0;
+        T kr = (T)0, ki = (T)0;
         for (int e = c_kb0; e < c_kb1; ++e) {
           const int p = kb_p[e];
-          const double w = kb_val[e];
+          const T w = kb_w[e];
           kr = fma(w, cre[p], kr);
           ki = fma(w, cim[p], ki);
         }
-        ar += (T)kr;
-        ai += (T)ki;
+        ar += kr;
+        ai += ki;
       }
-      const T nr = (T)c * ai, ni = -(T)c * ar;   // -i c (ar + i ai)
+      const T nr = kc.c * ai, ni = -kc.c * ar;   // -i c (ar + i ai)
       yr[g] = nr;
       yi[g] = ni;
       pr[g] = c_p1r + (double)nr;
@@ -398,6 +552,250 @@ k_gp_term_tma(const __grid_constant__ CUtensorMap tm_in, const T* __restrict__ t
       atomicCAS(status, 0, (int)RMGTD_ETIMEOUT);
       const int issued = min(nzb, i + kGtS);
       for (int w = 0; w < issued; ++w) tc::mbar_wait(&full[w % kGtS], (w / kGtS) & 1);
+    }
+    return;
+  }
+  const double bm = block_max((double)emax, sh);
+  if (tid == 0) atomic_max_nonneg(&errbits[rep], bm);
+}
+
+// The float32 term with two neighbouring x points per thread (vector shared loads): a block of
+// 32 x BY threads covers 64 x BY points; the tiles are (64 + 16) x (BY + 12) floats from
+// (x0 - 8, y0 - 6).  The x-neighbours of the pair come from 7 float2 loads of its row, the
+// y-neighbours from 12 float2 loads, the z-column is a register array of float2 pairs; psi_1
+// and the series' float32 pair (hi, lo) move as float2, as do V and the term.  Rows must be a
+// whole number of 16-byte units (nx % 4 == 0), so a pair is inside or outside the grid
+// together.  No float64 arithmetic: the KB lists and projections are float32 too.
+constexpr int kG2X = 64;   // points per block along x
+constexpr int kG2S = 4;    // planes in flight
+
+template <int BY>
+__host__ __device__ constexpr int gt2_tile_elems() {
+  return (BY + 2 * kFdRadius) * (kG2X + 2 * kGtXO);
+}
+
+template <int BY>
+__host__ __device__ constexpr size_t gt2_smem_bytes() {
+  return sizeof(float) * 2 * gt2_tile_elems<BY>() * kG2S + sizeof(uint64_t) * kG2S + 1024;
+}
+
+template <int BY>
+__global__ void __launch_bounds__(32 * BY)
+k_gp_term_tma2(const __grid_constant__ CUtensorMap tm_in, const float* __restrict__ tin,
+               float* __restrict__ tout, float* __restrict__ acc, long lo_off, int first,
+               const float* __restrict__ vtot, const int* __restrict__ kb_row,
+               const int* __restrict__ kb_p, const float* __restrict__ kb_w,
+               const float* __restrict__ coef, int np, int nocc,
+               int nx, int ny, int nz, int zchunk, int nzc, const GpTermCoef<float> kc,
+               const int* __restrict__ sact, unsigned long long* __restrict__ errbits,
+               int* __restrict__ status) {
+  constexpr int R = kFdRadius;
+  constexpr int TW = kG2X + 2 * kGtXO;
+  constexpr int TE = gt2_tile_elems<BY>();
+  constexpr uint32_t kBytes = 2u * TE * sizeof(float);
+  extern __shared__ unsigned char gt2_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(gt2_raw) + 1023) & ~(uintptr_t)1023);
+  float* tiles = reinterpret_cast<float*>(smem);   // [kG2S][2][BY + 2R][TW]
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + sizeof(float) * 2 * TE * kG2S);
+  __shared__ double sh[32];
+  const int col = blockIdx.z / nzc;
+  const int rep = col / nocc, n = col - rep * nocc;
+  if (!sact[rep]) return;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+  const int z0 = (blockIdx.z % nzc) * zchunk, z1 = min(nz, z0 + zchunk), nzb = z1 - z0;
+  const int ix = blockIdx.x * kG2X + 2 * tx, iy = blockIdx.y * BY + ty;
+  const bool in_xy = ix < nx && iy < ny;   // ix even, nx % 4 == 0: ix + 1 < nx too
+  const long plane = (long)nx * ny, Ng = plane * nz, oplane = (long)nocc * Ng;
+  const long base = (long)rep * 2 * oplane + (long)n * Ng;
+  const int cre_col = rep * 2 * nocc + n, cim_col = cre_col + nocc;
+  const int xs = blockIdx.x * kG2X - kGtXO, ys = blockIdx.y * BY - R;
+  if (tid == 0) {
+    for (int s = 0; s < kG2S; ++s) tc::mbar_init(&full[s], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    for (int i = 0; i < min(kG2S, nzb); ++i) {
+      float* dst = tiles + (size_t)i * 2 * TE;
+      const uint32_t bar = tc::saddr(&full[i]);
+      tc::mbar_expect_tx(bar, kBytes);
+      tc::tma_load_4d(tc::saddr(dst), &tm_in, xs, ys, z0 + i, cre_col, bar);
+      tc::tma_load_4d(tc::saddr(dst + TE), &tm_in, xs, ys, z0 + i, cim_col, bar);
+    }
+  }
+  const float* xr = tin + base;
+  const float* xi = xr + oplane;
+  float* yr = tout + base;
+  float* yi = yr + oplane;
+  float* hr = acc + base;          // the sum's hi and lo, real and imaginary
+  float* hi_ = hr + oplane;
+  float* lr = hr + lo_off;
+  float* li = hi_ + lo_off;
+  const float* v = vtot + (long)rep * Ng;
+  const float* cre = coef + (long)cre_col * np;
+  const float* cim = coef + (long)cim_col * np;
+  const long gxy = (long)iy * nx + ix;
+  float2 qr[2 * R + 1], qi[2 * R + 1];
+#pragma unroll
+  for (int k = 0; k < 2 * R; ++k) {
+    const int z = z0 - R + k;
+    const bool okz = in_xy && z >= 0 && z < nz;
+    qr[k] = okz ? *reinterpret_cast<const float2*>(xr + (long)z * plane + gxy) : make_float2(0.f, 0.f);
+    qi[k] = okz ? *reinterpret_cast<const float2*>(xi + (long)z * plane + gxy) : make_float2(0.f, 0.f);
+  }
+  float2 nr_next, ni_next;
+  {
+    const int z = z0 + R;
+    const bool okz = in_xy && z < nz;
+    nr_next = okz ? *reinterpret_cast<const float2*>(xr + (long)z * plane + gxy) : make_float2(0.f, 0.f);
+    ni_next = okz ? *reinterpret_cast<const float2*>(xi + (long)z * plane + gxy) : make_float2(0.f, 0.f);
+  }
+  const float2 zero2 = make_float2(0.f, 0.f);
+  float2 ahr = zero2, ahi = zero2, alr = zero2, ali = zero2;   // the sum, one plane ahead
+  float2 vv = zero2;
+  int kb0 = 0, kb1 = 0, kb2 = 0;
+  if (in_xy) {
+    const long g = (long)z0 * plane + gxy;
+    if (!first) {
+      ahr = *reinterpret_cast<const float2*>(hr + g);
+      ahi = *reinterpret_cast<const float2*>(hi_ + g);
+      alr = *reinterpret_cast<const float2*>(lr + g);
+      ali = *reinterpret_cast<const float2*>(li + g);
+    }
+    vv = *reinterpret_cast<const float2*>(v + g);
+    if (kb_row) {
+      kb0 = kb_row[g];
+      kb1 = kb_row[g + 1];
+      kb2 = kb_row[g + 2];
+    }
+  }
+  __syncthreads();
+  const int lx = 2 * tx + kGtXO, ly = ty + R;
+  float emax = 0.f;
+  bool ok = true;
+  int i = 0;
+  for (; i < nzb; ++i) {
+    qr[2 * R] = nr_next;
+    qi[2 * R] = ni_next;
+    const float2 c_ahr = ahr, c_ahi = ahi, c_alr = alr, c_ali = ali;
+    const float2 c_vv = vv;
+    const int c_kb0 = kb0, c_kb1 = kb1, c_kb2 = kb2;
+    {
+      const int z = z0 + i + R + 1;
+      const bool okz = in_xy && z < nz;
+      nr_next = okz ? *reinterpret_cast<const float2*>(xr + (long)z * plane + gxy) : zero2;
+      ni_next = okz ? *reinterpret_cast<const float2*>(xi + (long)z * plane + gxy) : zero2;
+      if (in_xy && i + 1 < nzb) {
+        const long g = (long)(z0 + i + 1) * plane + gxy;
+        if (!first) {
+          ahr = *reinterpret_cast<const float2*>(hr + g);
+          ahi = *reinterpret_cast<const float2*>(hi_ + g);
+          alr = *reinterpret_cast<const float2*>(lr + g);
+          ali = *reinterpret_cast<const float2*>(li + g);
+        }
+        vv = *reinterpret_cast<const float2*>(v + g);
+        if (kb_row) {
+          kb0 = kb_row[g];
+          kb1 = kb_row[g + 1];
+          kb2 = kb_row[g + 2];
+        }
+      }
+    }
+    if (!tc::mbar_wait(&full[i % kG2S], (i / kG2S) & 1)) ok = false;
+    const float* tr = tiles + (size_t)(i % kG2S) * 2 * TE;
+    const float* ti = tr + TE;
+    if (in_xy && ok) {
+      const long g = (long)(z0 + i) * plane + gxy;
+      // the row segment lx - 6 .. lx + 7 of both planes (7 float2 each)
+      float xr14[14], xi14[14];
+#pragma unroll
+      for (int k = 0; k < 7; ++k) {
+        const float2 a = *reinterpret_cast<const float2*>(tr + ly * TW + lx - R + 2 * k);
+        const float2 b = *reinterpret_cast<const float2*>(ti + ly * TW + lx - R + 2 * k);
+        xr14[2 * k] = a.x;
+        xr14[2 * k + 1] = a.y;
+        xi14[2 * k] = b.x;
+        xi14[2 * k + 1] = b.y;
+      }
+      // point 0 at xr14[R], point 1 at xr14[R + 1]
+      float ar0 = kc.c0 * qr[R].x, ar1 = kc.c0 * qr[R].y, ai0 = kc.c0 * qi[R].x, ai1 = kc.c0 * qi[R].y;
+#pragma unroll
+      for (int m = 1; m <= R; ++m) {
+        const float2 ur = *reinterpret_cast<const float2*>(tr + (ly + m) * TW + lx);
+        const float2 dr = *reinterpret_cast<const float2*>(tr + (ly - m) * TW + lx);
+        const float2 ui = *reinterpret_cast<const float2*>(ti + (ly + m) * TW + lx);
+        const float2 di = *reinterpret_cast<const float2*>(ti + (ly - m) * TW + lx);
+        const float sr0 = (xr14[R + m] + xr14[R - m]) + (ur.x + dr.x) + (qr[R + m].x + qr[R - m].x);
+        const float sr1 = (xr14[R + 1 + m] + xr14[R + 1 - m]) + (ur.y + dr.y) + (qr[R + m].y + qr[R - m].y);
+        const float si0 = (xi14[R + m] + xi14[R - m]) + (ui.x + di.x) + (qi[R + m].x + qi[R - m].x);
+        const float si1 = (xi14[R + 1 + m] + xi14[R + 1 - m]) + (ui.y + di.y) + (qi[R + m].y + qi[R - m].y);
+        ar0 = fmaf(kc.cm[m], sr0, ar0);
+        ar1 = fmaf(kc.cm[m], sr1, ar1);
+        ai0 = fmaf(kc.cm[m], si0, ai0);
+        ai1 = fmaf(kc.cm[m], si1, ai1);
+      }
+      ar0 = fmaf(c_vv.x, qr[R].x, ar0);
+      ar1 = fmaf(c_vv.y, qr[R].y, ar1);
+      ai0 = fmaf(c_vv.x, qi[R].x, ai0);
+      ai1 = fmaf(c_vv.y, qi[R].y, ai1);
+      if (c_kb2 > c_kb0) {
+        float kr0 = 0.f, ki0 = 0.f, kr1 = 0.f, ki1 = 0.f;
+        for (int e = c_kb0; e < c_kb1; ++e) {
+          const int p = kb_p[e];
+          const float w = kb_w[e];
+          kr0 = fmaf(w, cre[p], kr0);
+          ki0 = fmaf(w, cim[p], ki0);
+        }
+        for (int e = c_kb1; e < c_kb2; ++e) {
+          const int p = kb_p[e];
+          const float w = kb_w[e];
+          kr1 = fmaf(w, cre[p], kr1);
+          ki1 = fmaf(w, cim[p], ki1);
+        }
+        ar0 += kr0;
+        ai0 += ki0;
+        ar1 += kr1;
+        ai1 += ki1;
+      }
+      const float2 nr = make_float2(kc.c * ai0, kc.c * ai1), ni = make_float2(-kc.c * ar0, -kc.c * ar1);
+      *reinterpret_cast<float2*>(yr + g) = nr;
+      *reinterpret_cast<float2*>(yi + g) = ni;
+      if (first) {
+        *reinterpret_cast<float2*>(hr + g) = nr;
+        *reinterpret_cast<float2*>(hi_ + g) = ni;
+        *reinterpret_cast<float2*>(lr + g) = zero2;
+        *reinterpret_cast<float2*>(li + g) = zero2;
+      } else {
+        float2 sr, si, er, ei;
+        two_sum(c_ahr.x, nr.x, sr.x, er.x);
+        two_sum(c_ahr.y, nr.y, sr.y, er.y);
+        two_sum(c_ahi.x, ni.x, si.x, ei.x);
+        two_sum(c_ahi.y, ni.y, si.y, ei.y);
+        *reinterpret_cast<float2*>(hr + g) = sr;
+        *reinterpret_cast<float2*>(hi_ + g) = si;
+        *reinterpret_cast<float2*>(lr + g) = make_float2(c_alr.x + er.x, c_alr.y + er.y);
+        *reinterpret_cast<float2*>(li + g) = make_float2(c_ali.x + ei.x, c_ali.y + ei.y);
+      }
+      emax = fmaxf(emax, fmaxf(nr.x * nr.x + ni.x * ni.x, nr.y * nr.y + ni.y * ni.y));
+    }
+    if (__syncthreads_or(!ok)) break;
+    if (tid == 0 && i + kG2S < nzb) {
+      const int j = i + kG2S;
+      float* dst = tiles + (size_t)(j % kG2S) * 2 * TE;
+      const uint32_t bar = tc::saddr(&full[j % kG2S]);
+      tc::mbar_expect_tx(bar, kBytes);
+      tc::tma_load_4d(tc::saddr(dst), &tm_in, xs, ys, z0 + j, cre_col, bar);
+      tc::tma_load_4d(tc::saddr(dst + TE), &tm_in, xs, ys, z0 + j, cim_col, bar);
+    }
+#pragma unroll
+    for (int k = 0; k < 2 * R; ++k) {
+      qr[k] = qr[k + 1];
+      qi[k] = qi[k + 1];
+    }
+  }
+  if (i < nzb) {
+    if (tid == 0) {
+      atomicCAS(status, 0, (int)RMGTD_ETIMEOUT);
+      const int issued = min(nzb, i + kG2S);
+      for (int w = 0; w < issued; ++w) tc::mbar_wait(&full[w % kG2S], (w / kG2S) & 1);
     }
     return;
   }
@@ -685,17 +1083,24 @@ template <typename T>
 bool gp_encode_term_maps(rmgtd_ctx* ctx) {
   const EncodeTiledFn f = tensor_map_encoder();
   if (!f || ((long)ctx->nx * sizeof(T)) % 16 != 0) return false;
-  if (cudaFuncSetAttribute(k_gp_term_tma<T, kGpBX, kGpBY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)gt_smem_bytes<T, kGpBX, kGpBY>()) != cudaSuccess) {
+  cudaError_t e;
+  if constexpr (sizeof(T) == sizeof(float))   // the two-point float32 kernel: 64-wide tiles
+    e = cudaFuncSetAttribute(k_gp_term_tma2<kGpBY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)gt2_smem_bytes<kGpBY>());
+  else
+    e = cudaFuncSetAttribute(k_gp_term_tma<T, kGpBX, kGpBY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)gt_smem_bytes<T, kGpBX, kGpBY>());
+  if (e != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
+  const int bx = sizeof(T) == sizeof(float) ? kG2X : kGpBX;
   const cuuint64_t cols = 2ull * ctx->N * ctx->nrep;
   const cuuint64_t dims[4] = {(cuuint64_t)ctx->nx, (cuuint64_t)ctx->ny, (cuuint64_t)ctx->nz, cols};
   const cuuint64_t strides[3] = {(cuuint64_t)ctx->nx * sizeof(T),
                                  (cuuint64_t)ctx->nx * ctx->ny * sizeof(T),
                                  (cuuint64_t)ctx->Ng * sizeof(T)};
-  const cuuint32_t box[4] = {(cuuint32_t)(kGpBX + 2 * kGtXO), (cuuint32_t)(kGpBY + 2 * kFdRadius), 1, 1};
+  const cuuint32_t box[4] = {(cuuint32_t)(bx + 2 * kGtXO), (cuuint32_t)(kGpBY + 2 * kFdRadius), 1, 1};
   const cuuint32_t es[4] = {1, 1, 1, 1};
   const CUtensorMapDataType dt =
       sizeof(T) == sizeof(double) ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
@@ -720,38 +1125,62 @@ bool gp_f32(const rmgtd_ctx* ctx) { return ctx->opt.precision == RMGTD_PREC_MIXE
 // one series term for every replica whose series is running: tout = (-i dt/k) Hbar tin,
 // psi_1 += tout, errbits <- max|tout|^2 (the KB projections of tin first)
 template <typename T>
-int gp_term(rmgtd_ctx* ctx, const T* tin, T* tout, double c) {
+int gp_term(rmgtd_ctx* ctx, const T* tin, T* tout, double c, bool first) {
   const int N = ctx->N, nrep = ctx->nrep;
-  const int dtype = sizeof(T) == sizeof(double) ? RMGTD_F64 : RMGTD_F32;
-  int rc = kb_project_cols(ctx, tin, 2 * N * nrep, dtype, ctx->gp_coef);   // one block per column
-  if (rc) return rc;                                                       // and projector
+  if (ctx->nproj > 0) {   // one block per projector and group of real columns
+    const int ncols = 2 * N * nrep;
+    k_gp_kb_project<T><<<dim3(ctx->nproj, ceil_div(ncols, kKbCols)), kKbThreads, 0, ctx->stream>>>(
+        tin, ctx->Ng, ncols, 2 * N, ctx->gp_sact, ctx->poff, ctx->gp_kb_pt, (const T*)ctx->gp_pv,
+        ctx->h3, (T*)ctx->gp_coef);
+    ++ctx->launches;
+    RMGTD_LAUNCH(ctx, "k_gp_kb_project");
+  }
+  const T* kb_w = (const T*)ctx->gp_kb_w;
+  const T* coef = (const T*)ctx->gp_coef;
+  const long lo_off = 2L * N * ctx->Ng * nrep;
+  const GpTermCoef<T> kc = gp_term_coef<T>(ctx->h, c);
+  T* acc;
+  if constexpr (sizeof(T) == sizeof(float)) acc = ctx->gp_acc;
+  else acc = ctx->gp_psi1;
   if (ctx->gp_tma) {   // x-y tiles by TMA from the term's tensor map
     const CUtensorMap* tm = reinterpret_cast<const CUtensorMap*>(
         (const void*)tin == ctx->gp_ta ? ctx->gp_tm_a : ctx->gp_tm_b);
     const int nzc = ceil_div(ctx->nz, kGtZ);
-    const dim3 grid(ceil_div(ctx->nx, kGpBX), ceil_div(ctx->ny, kGpBY), nrep * N * nzc);
-    k_gp_term_tma<T, kGpBX, kGpBY><<<grid, dim3(kGpBX, kGpBY), gt_smem_bytes<T, kGpBX, kGpBY>(),
-                                      ctx->stream>>>(
-        *tm, tin, tout, ctx->gp_psi1, (const T*)ctx->gp_vtot, ctx->gp_kb_row, ctx->gp_kb_p,
-        ctx->gp_kb_val, ctx->gp_coef, ctx->nproj, N, ctx->nx, ctx->ny, ctx->nz, kGtZ, nzc,
-        -0.5 / (ctx->h * ctx->h), c, ctx->gp_sact, ctx->errbits, ctx->status);
-    ++ctx->launches;
-    RMGTD_LAUNCH(ctx, "k_gp_term_tma");
+    if constexpr (sizeof(T) == sizeof(float)) {
+      const dim3 grid(ceil_div(ctx->nx, kG2X), ceil_div(ctx->ny, kGpBY), nrep * N * nzc);
+      k_gp_term_tma2<kGpBY><<<grid, dim3(32, kGpBY), gt2_smem_bytes<kGpBY>(), ctx->stream>>>(
+          *tm, tin, tout, acc, lo_off, first ? 1 : 0, (const float*)ctx->gp_vtot, ctx->gp_kb_row,
+          ctx->gp_kb_p, kb_w, coef, ctx->nproj, N, ctx->nx, ctx->ny, ctx->nz, kGtZ, nzc,
+          kc, ctx->gp_sact, ctx->errbits, ctx->status);
+      ++ctx->launches;
+      RMGTD_LAUNCH(ctx, "k_gp_term_tma2");
+    } else {
+      const dim3 grid(ceil_div(ctx->nx, kGpBX), ceil_div(ctx->ny, kGpBY), nrep * N * nzc);
+      k_gp_term_tma<T, kGpBX, kGpBY><<<grid, dim3(kGpBX, kGpBY), gt_smem_bytes<T, kGpBX, kGpBY>(),
+                                        ctx->stream>>>(
+          *tm, tin, tout, acc, (const T*)ctx->gp_vtot, ctx->gp_kb_row, ctx->gp_kb_p,
+          kb_w, coef, ctx->nproj, N, ctx->nx, ctx->ny, ctx->nz, kGtZ, nzc,
+          kc, ctx->gp_sact, ctx->errbits, ctx->status);
+      ++ctx->launches;
+      RMGTD_LAUNCH(ctx, "k_gp_term_tma");
+    }
     return RMGTD_OK;
   }
   const int nzc = ceil_div(ctx->nz, kGpZ);
   const dim3 grid(ceil_div(ctx->nx, kGpBX), ceil_div(ctx->ny, kGpBY), nrep * N * nzc);
   k_gp_term_fused<T, kGpBX, kGpBY><<<grid, dim3(kGpBX, kGpBY), 0, ctx->stream>>>(
-      tin, tout, ctx->gp_psi1, (const T*)ctx->gp_vtot, ctx->gp_kb_row, ctx->gp_kb_p,
-      ctx->gp_kb_val, ctx->gp_coef, ctx->nproj, N, ctx->nx, ctx->ny, ctx->nz, kGpZ, nzc,
-      -0.5 / (ctx->h * ctx->h), c, ctx->gp_sact, ctx->errbits);
+      tin, tout, acc, lo_off, first ? 1 : 0, (const T*)ctx->gp_vtot, ctx->gp_kb_row,
+      ctx->gp_kb_p, kb_w, coef, ctx->nproj, N, ctx->nx, ctx->ny, ctx->nz, kGpZ, nzc,
+      kc, ctx->gp_sact, ctx->errbits);
   ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_gp_term_fused");
   return RMGTD_OK;
 }
 
 // KB lists by grid point (CSR) from the projector boxes: entry (p, E_p beta_p(r)) for every
-// projector whose box holds the point
+// projector whose box holds the point; the grid index of every box entry; weights and box
+// values in the terms' precision
+template <typename T>
 int gp_build_kb_lists(rmgtd_ctx* ctx) {
   const int np = ctx->nproj;
   const long Ng = ctx->Ng;
@@ -769,22 +1198,30 @@ int gp_build_kb_lists(rmgtd_ctx* ctx) {
     for (long long e = 0; e < ctx->h_poff[p + 1] - ctx->h_poff[p]; ++e) ++cnt[point(p, e) + 1];
   for (long g = 0; g < Ng; ++g) cnt[g + 1] += cnt[g];
   if ((long long)cnt[Ng] != nval) return set_error(ctx, RMGTD_EINVAL, "KB lists: box count mismatch");
-  std::vector<int> pos(cnt.begin(), cnt.end() - 1), pidx(nval);
-  std::vector<double> w(nval);
+  std::vector<int> pos(cnt.begin(), cnt.end() - 1), pidx(nval), pt(nval);
+  std::vector<T> w(nval), pv(nval);
   for (int p = 0; p < np; ++p)
     for (long long e = 0; e < ctx->h_poff[p + 1] - ctx->h_poff[p]; ++e) {
-      const int k = pos[point(p, e)]++;
+      const long g = point(p, e);
+      const int k = pos[g]++;
       pidx[k] = p;
-      w[k] = ctx->h_Ekb[p] * val[ctx->h_poff[p] + e];
+      w[k] = (T)(ctx->h_Ekb[p] * val[ctx->h_poff[p] + e]);
+      pt[ctx->h_poff[p] + e] = (int)g;
+      pv[ctx->h_poff[p] + e] = (T)val[ctx->h_poff[p] + e];
     }
+  const size_t n1 = std::max<long long>(nval, 1);
   ctx->gp_kb_row = (int*)dev_alloc(ctx, sizeof(int) * (Ng + 1));
-  ctx->gp_kb_p = (int*)dev_alloc(ctx, sizeof(int) * std::max<long long>(nval, 1));
-  ctx->gp_kb_val = (double*)dev_alloc(ctx, sizeof(double) * std::max<long long>(nval, 1));
-  if (!ctx->gp_kb_row || !ctx->gp_kb_p || !ctx->gp_kb_val)
+  ctx->gp_kb_p = (int*)dev_alloc(ctx, sizeof(int) * n1);
+  ctx->gp_kb_w = dev_alloc(ctx, sizeof(T) * n1);
+  ctx->gp_kb_pt = (int*)dev_alloc(ctx, sizeof(int) * n1);
+  ctx->gp_pv = dev_alloc(ctx, sizeof(T) * n1);
+  if (!ctx->gp_kb_row || !ctx->gp_kb_p || !ctx->gp_kb_w || !ctx->gp_kb_pt || !ctx->gp_pv)
     return set_error(ctx, RMGTD_ENOMEM, "KB lists");
   RMGTD_CUDA(ctx, cudaMemcpy(ctx->gp_kb_row, cnt.data(), sizeof(int) * (Ng + 1), cudaMemcpyHostToDevice));
   RMGTD_CUDA(ctx, cudaMemcpy(ctx->gp_kb_p, pidx.data(), sizeof(int) * nval, cudaMemcpyHostToDevice));
-  RMGTD_CUDA(ctx, cudaMemcpy(ctx->gp_kb_val, w.data(), sizeof(double) * nval, cudaMemcpyHostToDevice));
+  RMGTD_CUDA(ctx, cudaMemcpy(ctx->gp_kb_w, w.data(), sizeof(T) * nval, cudaMemcpyHostToDevice));
+  RMGTD_CUDA(ctx, cudaMemcpy(ctx->gp_kb_pt, pt.data(), sizeof(int) * nval, cudaMemcpyHostToDevice));
+  RMGTD_CUDA(ctx, cudaMemcpy(ctx->gp_pv, pv.data(), sizeof(T) * nval, cudaMemcpyHostToDevice));
   return RMGTD_OK;
 }
 
@@ -807,8 +1244,9 @@ int gridprop_setup(rmgtd_ctx* ctx) {
   ctx->gp_vtot = dev_alloc(ctx, tsz * Ng * nrep);
   ctx->gp_ebar = (double*)dev_alloc(ctx, sizeof(double) * 3 * nrep);
   ctx->gp_active = (int*)dev_alloc(ctx, sizeof(int) * nrep);
-  ctx->gp_sact = (int*)dev_alloc(ctx, sizeof(int) * nrep);
-  ctx->gp_coef = (double*)dev_alloc(ctx, sizeof(double) * 2 * std::max(ctx->nproj, 1) * 2L * nocc * nrep);
+  ctx->gp_sact = (int*)dev_alloc(ctx, sizeof(int) * 3 * nrep);
+  ctx->gp_coef = dev_alloc(ctx, tsz * std::max(ctx->nproj, 1) * 2L * nocc * nrep);
+  if (gp_f32(ctx)) ctx->gp_acc = (float*)ctx->gp_ht;   // hi + lo floats: the size of gp_ht
   ctx->gp_gram = (double*)dev_alloc(ctx, sizeof(double) * 5 * (size_t)nocc * nocc);
   if (nocc <= kZgMaxN)
     ctx->gp_zpart = (double*)dev_alloc(
@@ -820,7 +1258,7 @@ int gridprop_setup(rmgtd_ctx* ctx) {
       (nocc <= kZgMaxN && !ctx->gp_zpart))
     return set_error(ctx, RMGTD_ENOMEM, "grid propagation buffers");
   if (ctx->nproj > 0) {
-    const int rc = gp_build_kb_lists(ctx);
+    const int rc = gp_f32(ctx) ? gp_build_kb_lists<float>(ctx) : gp_build_kb_lists<double>(ctx);
     if (rc) return rc;
   }
   ctx->gp_tma = gp_f32(ctx) ? gp_encode_term_maps<float>(ctx) : gp_encode_term_maps<double>(ctx);
@@ -948,42 +1386,55 @@ static int gp_series(rmgtd_ctx* ctx, const std::vector<int>& active, std::vector
   RMGTD_LAUNCH(ctx, "k_gp_vtot");
   T* ta = (T*)ctx->gp_ta;
   T* tb = (T*)ctx->gp_tb;
+  constexpr bool f32 = sizeof(T) == sizeof(float);
   k_gp_start<T><<<dim3(gp_blocks(ctx, rplane), nrep), 256, 0, ctx->stream>>>(
-      ctx->gp_psi, ctx->gp_psi1, ta, rplane, ctx->gp_active);
+      ctx->gp_psi, f32 ? nullptr : ctx->gp_psi1, ta, rplane, ctx->gp_active);
   ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_gp_start");
-  std::vector<int> series(active);
-  std::vector<double> m;
-  for (int k = 1;; ++k) {
-    RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->gp_sact, series.data(), sizeof(int) * nrep,
-                                    cudaMemcpyHostToDevice, ctx->stream));
-    RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->errbits, 0, sizeof(unsigned long long) * nrep, ctx->stream));
-    int rc = gp_term<T>(ctx, ta, tb, ctx->opt.dt / k);
-    if (rc) return rc;
-    rc = read_max(ctx, ctx->errbits, nrep, m);
-    if (rc) return rc;
-    std::swap(ta, tb);
-    bool more = false;
-    for (int r = 0; r < nrep; ++r) {
-      if (!series[r]) continue;
-      if (!(m[r] <= 1e300)) {
-        status[r] = RMGTD_EDIVERGED;
-        series[r] = 0;
-      } else if (m[r] <= thr2) {
-        series[r] = 0;
-      } else if (k >= ctx->opt.max_terms) {
-        status[r] = RMGTD_ENOTCONVERGED;
-        series[r] = 0;
-      } else {
-        more = true;
-      }
-      if (!series[r]) {
-        tmax[r] = std::max(tmax[r], k);
-        tsum[r] += k;
-      }
+  // the terms in batches between read-backs of the device-side stopping test: the first
+  // batch as long as the last series less one, then two at a time (terms queued after a
+  // series has stopped return at once)
+  std::vector<int> ctl(3 * nrep, 0);
+  for (int r = 0; r < nrep; ++r) ctl[r] = active[r];
+  RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->gp_sact, ctl.data(), sizeof(int) * 3 * nrep,
+                                  cudaMemcpyHostToDevice, ctx->stream));
+  RMGTD_CUDA(ctx, cudaMemsetAsync(ctx->errbits, 0, sizeof(unsigned long long) * nrep, ctx->stream));
+  int batch = std::max(1, ctx->gp_terms_hint - 1);
+  for (int k = 1;;) {
+    for (int b = 0; b < batch; ++b, ++k) {
+      int rc = gp_term<T>(ctx, ta, tb, ctx->opt.dt / k, k == 1);
+      if (rc) return rc;
+      std::swap(ta, tb);
+      k_gp_series_ctl<<<1, 32, 0, ctx->stream>>>(nrep, k, thr2, ctx->opt.max_terms, ctx->gp_sact,
+                                                 ctx->errbits);
+      ++ctx->launches;
+      RMGTD_LAUNCH(ctx, "k_gp_series_ctl");
     }
-    if (!more) return RMGTD_OK;
+    RMGTD_CUDA(ctx, cudaMemcpyAsync(ctl.data(), ctx->gp_sact, sizeof(int) * 3 * nrep,
+                                    cudaMemcpyDeviceToHost, ctx->stream));
+    RMGTD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    bool more = false;
+    for (int r = 0; r < nrep; ++r) more = more || ctl[r];
+    if (!more) break;
+    batch = 2;
   }
+  int last = 0;
+  for (int r = 0; r < nrep; ++r) {
+    if (!active[r]) continue;
+    const int terms = ctl[2 * nrep + r];
+    if (ctl[nrep + r]) status[r] = ctl[nrep + r];
+    tmax[r] = std::max(tmax[r], terms);
+    tsum[r] += terms;
+    last = std::max(last, terms);
+  }
+  ctx->gp_terms_hint = last;
+  if (f32) {   // psi_1 = psi + hi + lo
+    k_gp_fold<<<dim3(gp_blocks(ctx, rplane), nrep), 256, 0, ctx->stream>>>(
+        ctx->gp_psi, ctx->gp_acc, rplane * nrep, ctx->gp_psi1, rplane, ctx->gp_active);
+    ++ctx->launches;
+    RMGTD_LAUNCH(ctx, "k_gp_fold");
+  }
+  return RMGTD_OK;
 }
 
 int gridprop_step(rmgtd_ctx* ctx, rmgtd_stats* st) {

@@ -274,14 +274,21 @@ struct rmgtd_ctx {
   void* gp_ta = nullptr;        // series terms in the path's precision (float64 / float32),
   void* gp_tb = nullptr;        // double-buffered [nrep][2][N][Ng]
   void* gp_vtot = nullptr;      // V_ion + Vbar + Ebar.q in that precision [nrep][Ng]
-  int* gp_sact = nullptr;       // [nrep] replicas whose series is still running
-  double* gp_coef = nullptr;    // KB projections of the current term [nrep][2N][2][nproj]
+  int* gp_sact = nullptr;       // [3][nrep]: replicas whose series is still running, then
+                                // each series' status and term count (set on the device)
+  int gp_terms_hint = 0;        // terms of the last series (the next one's first batch)
+  void* gp_coef = nullptr;      // KB projections of the current term, terms' precision
+                                // [nrep][2][N][nproj]
   alignas(64) unsigned char gp_tm_a[128] = {};   // tensor maps of the two term buffers
   alignas(64) unsigned char gp_tm_b[128] = {};
   int gp_tma = 0;               // the term kernel streams its tiles by TMA
   int* gp_kb_row = nullptr;     // KB lists by grid point: CSR row offsets [Ng + 1],
-  int* gp_kb_p = nullptr;       // projector index and E_p beta_p(r) of each entry
-  double* gp_kb_val = nullptr;
+  int* gp_kb_p = nullptr;       // projector index and E_p beta_p(r) of each entry (the
+  void* gp_kb_w = nullptr;      // latter in the terms' precision)
+  int* gp_kb_pt = nullptr;      // grid index of every projector-box entry [nval]
+  void* gp_pv = nullptr;        // projector-box values beta_p in the terms' precision [nval]
+  float* gp_acc = nullptr;      // float32 terms: the series' sum, hi then lo [2][nrep][2][N][Ng]
+                                // (shares the observables' scratch gp_ht: never live together)
   long long gp_steps = 0;
   // ground state on the device (opt.ground_state_scf): orbital energies, SCF iterations,
   // final density change and largest Ritz residual
