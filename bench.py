@@ -758,8 +758,8 @@ def run_ours(args):
 def _grid_basis_path(rmgtd, peaks):
     """Secondary line: the occupied orbitals propagated on the grid (the complete-grid-basis
     limit) on the ring, kicked along x, y, z, both precisions; the series phase rated as the
-    term kernel's algorithmic bytes (term read and write, psi_1 read and write per point and
-    orbital) over its time."""
+    term kernel's algorithmic bytes (term read and write, and the running sum read and written
+    per point and orbital) over its time."""
     import torch
     s, raw = _system("ring")
     s = dataclasses.replace(s, nvirt=0)
@@ -780,8 +780,8 @@ def _grid_basis_path(rmgtd, peaks):
         ph, calls, _ = ctx.profile_read()
         ctx.close()
         terms = float(st["terms_sum"].sum())
-        # per point and orbital: the term read and written (2 planes of T) and psi_1 (2 planes
-        # of float64) read and written
+        # per point and orbital: the term read and written (2 planes of T) and the running sum
+        # read and written (float64: psi_1, 2 planes; mixed: the float32 hi/lo pair, 4 planes)
         per_term = (8 * 8 if name == "fp64" else 8 * 6) * s.Ng * s.N
         series_ms = ph["eldyn"]
         achieved = per_term * terms / (series_ms * 1e-3) / 1e9 if series_ms > 0 else None
@@ -793,8 +793,9 @@ def _grid_basis_path(rmgtd, peaks):
                      "series_hbm_gbs": achieved,
                      "series_hbm_frac": achieved / peaks["hbm_gbs"] if achieved else None,
                      "bytes_per_term_and_replica": per_term}
-    out["note"] = ("series phase = KB projections + fused TMA term kernel + the per-term "
-                   "stopping read-back; H_thrs above each path's floor (1e-7 float64, 1e-6 "
+    out["note"] = ("series phase = KB projections + fused TMA term kernel + the device-side "
+                   "stopping test (terms queued in batches between read-backs) + the fold of "
+                   "the float32 sum; H_thrs above each path's floor (1e-7 float64, 1e-6 "
                    "mixed: the float32 terms leave ~1e-8 of noise in V)")
     return out
 

@@ -10,10 +10,10 @@
  *     dP_k = (Omega dP_{k-1} + dP_{k-1} Omega^dagger)/k until max|dP_k| <= dP_thrs
  *     (Eqs. 19, 33; real/imaginary split of Eq. 35),
  *   - Hamiltonian self-consistency: H_1 <- DFT(rho(P_1)) until max|H_new - H_1| <= H_thrs,
- *     seeded by H_1 = 2 H_0 - H_-1 (Algorithm 1 line 11),
+ *     seeded by H_1 = 2 H_0 - H_-1 (Algorithm 1's extrapolation),
  *   - DFT(rho) = density rho(r) = sum_ij Re(P)_ij phi_i phi_j, multigrid Poisson solve for
  *     V_H, LDA exchange-correlation, H = H_core + h^3 Phi^T diag(V_H + V_xc) Phi,
- *   - dipole d_q = Tr(Re(P) M_q), M_q = h^3 Phi^T q Phi (Algorithm 1 lines 3, 27),
+ *   - dipole d_q = Tr(Re(P) M_q), M_q = h^3 Phi^T q Phi (Algorithm 1's dipole),
  *   - delta kick P <- exp(-i kappa M_q) P exp(i kappa M_q) (Eq. 34 with a delta envelope).
  *
  * Conventions (atomic units):
@@ -105,9 +105,9 @@ typedef struct {
 } rmgtd_system;
 
 typedef struct {
-  double dt;               /* time step (a.u.); Algorithm 1 line 4 */
-  double H_thrs;           /* SCF threshold on max|H_new - H_1|; Algorithm 1 line 6 */
-  double dP_thrs;          /* commutator-series threshold on max|dP_k|; line 6 */
+  double dt;               /* time step (a.u.) of Algorithm 1 */
+  double H_thrs;           /* SCF threshold on max|H_new - H_1| (Algorithm 1) */
+  double dP_thrs;          /* commutator-series threshold on max|dP_k| (Algorithm 1) */
   int max_scf;             /* SCF pass cap per step (exceeded -> RMGTD_ENOTCONVERGED) */
   int max_terms;           /* commutator-term cap per expansion */
   int precision;           /* rmgtd_precision */
@@ -153,7 +153,7 @@ typedef struct {
                               H_err = max|V_new - V_1|); the matrix, save / load, batch,
                               autotune and network calls return RMGTD_ESTATE. */
   int ground_state_scf;    /* > 0: before the set-up, up to this many SCF iterations of the
-                              Kohn-Sham ground state on the GPU (Algorithm 1 lines 1-3) from the
+                              Kohn-Sham ground state on the GPU (Algorithm 1's ground state) from the
                               orthonormalised phi0: Chebyshev-filtered subspace iteration on
                               N + max(4, N/8) orbitals (degree 12 per iteration, Rayleigh-Ritz),
                               Pulay-mixed density (history 6, mixing 0.4); phi0 is replaced by the
@@ -163,7 +163,7 @@ typedef struct {
   double ground_state_tol; /* stop when max|rho_out - rho_in| and the largest Ritz residual
                               max|H phi_n - eps_n phi_n| (n < N) are below it (0: 1e-8) */
   int seed_order;          /* seed of each step's SCF loop: 1 (or 0) the linear extrapolation
-                              H_1 = 2 H_0 - H_-1 (Algorithm 1 line 11); 2 the quadratic
+                              H_1 = 2 H_0 - H_-1 (Algorithm 1's extrapolation); 2 the quadratic
                               H_1 = 3 H_0 - 3 H_-1 + H_-2 (fewer passes when H varies smoothly;
                               the loop's H_thrs test still decides convergence).  H_-2 starts as
                               H_0, and after rmgtd_load or setting H_-1 it restarts from H_-1. */
@@ -202,7 +202,7 @@ typedef enum {
  * passes and the Hartree iterations), default stream, cudaMalloc. */
 void rmgtd_default_options(rmgtd_options* opt);
 
-/* Set up a context (Algorithm 1 lines 1-8 given the orbitals): copy Phi, build V_loc and
+/* Set up a context (Algorithm 1's set-up given the orbitals): copy Phi, build V_loc and
  * the KB projectors on the device, orthonormalise Phi (optional), form H_core, M_q and the
  * ground-state H_0 = H[rho(P_0)] with P_0 = diag(f) for every replica, H_-1 = H_0.
  * Errors: RMGTD_EINVAL (sizes, NULL required pointers, nrep < 1), RMGTD_ENOMEM,
@@ -288,7 +288,7 @@ int rmgtd_hartree(rmgtd_ctx* ctx, const double* rho_dev, double* vh_dev);
 int rmgtd_xc(rmgtd_ctx* ctx, const double* rho_dev, double* vxc_dev, double* exc_dev,
              size_t n);
 
-/* The mixed path's xc increment (Algorithm 1 line 26 with the fields kept as float32
+/* The mixed path's xc increment (Algorithm 1's density-functional update with the fields kept as float32
  * increments against the set-up state): dvxc_dev[g] = V_xc(rho0_dev[g] + drho_dev[g]) -
  * V_xc(rho0_dev[g]) for the LDA of rmgtd_xc, on n device points (rho0 double, drho and the
  * result float).  Evaluated in float32 arithmetic on the increment, so the error is a few
@@ -377,7 +377,7 @@ void rmgtd_batch_destroy(rmgtd_batch* batch);
  * nsteps x nrep records (as rmgtd_step).  On a failed step the error names the context. */
 int rmgtd_batch_step(rmgtd_batch* batch, int nsteps, rmgtd_stats* const* stats);
 
-/* ---- Learned seed of the SCF loop (Algorithm 1 line 11) ------------------------------------
+/* ---- Learned seed of the SCF loop (Algorithm 1's extrapolation) ------------------------------------
  * The paper seeds each step's Hamiltonian SCF loop with H_1 = 2 H_0 - H_-1 = H[2 V_0 - V_-1].
  * An attached network adds dV = s_out * y to that potential, y = net(x) with features
  *   x[0] = rho_t / s_0,  x[1] = (rho_t - rho_{t-dt}) / s_1,  x[2] = (rho_t - 2 rho_{t-dt} + rho_{t-2dt}) / s_2,

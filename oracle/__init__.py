@@ -14,7 +14,7 @@ Plain, slow, obviously-correct NumPy/SciPy in float64, written from the paper:
 * ``poisson``     -- Hartree potential of the discrete 12th-order operator (Section 2.1).
 * ``lda``         -- Slater exchange + Perdew-Zunger 1981 correlation.
 * ``groundstate`` -- SCF ground state that supplies the active-space orbitals
-                     (Algorithm 1, lines 1-3).
+                     (Algorithm 1's ground state).
 * ``tddft``       -- Algorithm 1: commutator expansion (Eqs. 19, 32-33), Hamiltonian
                      self-consistency, linear extrapolation, kick (Eq. 34), dipole.
 * ``gridprop``    -- the occupied orbitals propagated on the grid, the complete-grid-basis
@@ -22,7 +22,7 @@ Plain, slow, obviously-correct NumPy/SciPy in float64, written from the paper:
 * ``spectrum``    -- absorption spectrum (dipole strength function) from the kicked dipole
                      series of the three kick directions (Section 4).
 * ``surrogate``   -- learned correction to the linear-extrapolation seed of the SCF loop
-                     (Algorithm 1 line 11): conv3d network, its gradient, Adam.
+                     (Algorithm 1's extrapolation): conv3d network, its gradient, Adam.
 
 Parity status of each function is stated in its module header.
 """

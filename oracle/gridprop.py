@@ -8,9 +8,9 @@ limit of the active space.  With P = sum_n f_n |psi_n><psi_n|, the propagated
 e^{Omega} P e^{Omega^dagger} equals sum_n f_n (e^{Omega} psi_n)(e^{Omega} psi_n)^dagger, so
 applying the exponential to the occupied orbitals propagates P without truncation:
 
-* Step (Algorithm 1 lines 9-29 in the grid basis, where H depends on time only through the
+* Step (Algorithm 1's time loop in the grid basis, where H depends on time only through the
   potential V = V_H + V_xc):
-    V_1 <- 2 V_0 - V_-1                                  (line 11)
+    V_1 <- 2 V_0 - V_-1                                  (the extrapolation)
     repeat:
       psi_1 = sum_k psi^(k), psi^(0) = psi_0, psi^(k) = (-i dt / k) Hbar psi^(k-1),
         Hbar = T + V_ion + V_NL + (V_0 + V_1)/2 + sum_q Ebar_q q   (the series of Eq. 33

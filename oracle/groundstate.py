@@ -1,4 +1,4 @@
-"""Ground-state Kohn-Sham orbitals that define the active space (Algorithm 1, lines 1-3).
+"""Ground-state Kohn-Sham orbitals that define the active space (Algorithm 1's ground state).
 
 Self-consistent field at the Gamma point: for the current density, the N lowest
 eigenpairs of the sparse grid Hamiltonian are found with ARPACK (scipy ``eigsh``, smallest

@@ -1,4 +1,4 @@
-"""Hartree potential on the grid: Lap_12 V_H = -4 pi rho (Section 2.1, Algorithm 1 line 26).
+"""Hartree potential on the grid: Lap_12 V_H = -4 pi rho (Section 2.1; Algorithm 1's density-functional update).
 
 The paper solves Poisson's equation by multigrid; the oracle solves the *same discrete
 equation* by preconditioned conjugate gradients, which reaches the identical solution

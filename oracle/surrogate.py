@@ -3,7 +3,7 @@
 TEST INFRASTRUCTURE ONLY (see the package header).
 
 The paper seeds the SCF loop of every step with the linear extrapolation
-H_1 = 2 H_0 - H_-1 (Algorithm 1 line 11).  H is linear in the potential, so this is
+H_1 = 2 H_0 - H_-1 (Algorithm 1's extrapolation).  H is linear in the potential, so this is
 H[V_pred] with V_pred = 2 V_0 - V_-1.  The learned predictor adds a correction dV = s_out * y
 to V_pred, where y is produced by a small 3-D convolutional network from the last three
 densities; the SCF loop still decides convergence, so the converged step does not depend on

@@ -3,21 +3,21 @@
 Active space: the N = N_occ + N_virt orbitals Phi (rows of ``phi``, grid-normalised), so
 the overlap is the identity and the orthogonal commutator expansion applies (Section 3.1).
 
-* Matrices (Algorithm 1 lines 2-3, 8): H_ij = h^3 <phi_i|H|phi_j>, M_q,ij = h^3 <phi_i|q|phi_j>,
+* Matrices (Algorithm 1's set-up): H_ij = h^3 <phi_i|H|phi_j>, M_q,ij = h^3 <phi_i|q|phi_j>,
   q measured from the box centre.  H is real symmetric at Gamma (Eq. 35 discussion); the
   oracle symmetrises it, (H + H^T)/2, so both sides see the same real symmetric matrix.
-* P_0 = diag(f), f = 2 occupied / 0 virtual.  H_0 = H[rho(P_0)], H_-1 = H_0 (line 8).
+* P_0 = diag(f), f = 2 occupied / 0 virtual.  H_0 = H[rho(P_0)], H_-1 = H_0 (the set-up).
 * Kick (Eq. 34 with a delta envelope): applied at t = 0+ as P <- e^{-i kappa M_q} P e^{i kappa M_q},
   evaluated with the same commutator expansion (Omega = -i kappa M_q); no field afterwards.
-* Step j (lines 9-29), with Omega = -i dt (H_0 + H_1)/2 (Eq. 15, first-order Magnus):
-    H_1 <- 2 H_0 - H_-1                                   (line 11, linear extrapolation)
+* Step j (the time loop), with Omega = -i dt (H_0 + H_1)/2 (Eq. 15, first-order Magnus):
+    H_1 <- 2 H_0 - H_-1                                   (linear extrapolation)
     repeat:                                               (Hamiltonian SCF loop)
         P_1 <- P_0 + sum_k dP_k,  dP_0 = P_0,
-        dP_k = (Omega dP_{k-1} + dP_{k-1} Omega^dagger)/k  (Eq. 33 / lines 15-22)
+        dP_k = (Omega dP_{k-1} + dP_{k-1} Omega^dagger)/k  (Eq. 33, the commutator series)
         stop the series when max_ij |dP_k| <= dP_thrs
         H_new <- DFT(rho(P_1)); H_err = max_ij |H_new - H_1|; H_1 <- H_new
     until H_err <= H_thrs
-    H_-1 <- H_0, H_0 <- H_1, P_0 <- P_1                   (line 28)
+    H_-1 <- H_0, H_0 <- H_1, P_0 <- P_1                   (the shift)
   Reading of the loop order: the paper computes H_err before the update and never defines
   H_1^old on the first pass; here H_err compares the Hamiltonian the propagation used with
   the one its density produces, and a pass is one DFT evaluation.
@@ -37,7 +37,7 @@ the overlap is the identity and the orthogonal commutator expansion applies (Sec
   imaginary part of a Hermitian P cancels).
 * DFT(rho): Hartree by ``poisson.hartree``, LDA by ``lda.lda``, then
   H = h^3 Phi (H[rho] Phi^T) with the *full* grid Hamiltonian applied to every orbital.
-* Observables: electronic dipole d_q = Tr(Re(P) M_q) (line 27 without mu_0), and
+* Observables: electronic dipole d_q = Tr(Re(P) M_q) (Algorithm 1's dipole without mu_0), and
   E = Tr(Re(P) H_core) + 1/2 h^3 sum rho V_H + h^3 sum rho eps_xc + E_ion.
 * Frozen core density rho_core (optional, ``sys.rho_core``; Section 3.1's frozen semicore
   electrons): a fixed density added to rho in the exchange-correlation only, V_xc and eps_xc
@@ -148,7 +148,7 @@ class Propagator:
         return np.sum(self.phi * X, axis=0)
 
     def dft(self, P: np.ndarray):
-        """H_1 <- DFT(rho(P)) (line 26); also returns the grid fields for observables."""
+        """H_1 <- DFT(rho(P)) (the density-functional update); also returns the grid fields for observables."""
         rho = self.density(P)
         if self.sys.hartree_xc:
             vh = hartree(self.sys, rho.reshape(self.shape), tol=self.opts.poisson_tol,
@@ -198,7 +198,7 @@ class Propagator:
         """SCF inside the orbital block: P <- (1-mix) P + mix P_aufbau(H[rho(P)]).
 
         P_aufbau = sum_n f_n w_n w_n^T over the eigenvectors of H in ascending order
-        (scipy eigh), i.e. the ground-state density matrix of Algorithm 1 lines 1-3 restricted
+        (scipy eigh), i.e. the ground-state density matrix of Algorithm 1's set-up restricted
         to the active space.  Returns (P, H, aux, iterations, last max|P_new - P|).
         """
         f = self.sys.occupations

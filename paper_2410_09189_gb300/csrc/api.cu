@@ -1,5 +1,5 @@
-// The C ABI of include/rmgtd.h: context set-up (Algorithm 1 lines 1-8), the time loop
-// (lines 9-29), kicks, observables, checkpoints.  Host code only orchestrates launches on
+// The C ABI of include/rmgtd.h: context set-up (Algorithm 1's set-up), the time loop
+// (Algorithm 1's time loop), kicks, observables, checkpoints.  Host code only orchestrates launches on
 // the context's stream; every arithmetic step of the propagation runs in the kernels of
 // k_grid.cu, k_subspace.cu and k_poisson.cu.
 #include <math.h>
@@ -195,7 +195,7 @@ static int add_while(rmgtd_ctx* ctx, cudaGraphConditionalHandle h, cudaGraph_t* 
 }
 
 
-// ---- one density-functional evaluation: H_1 <- DFT(rho(P)) (Algorithm 1 line 26) ------------
+// ---- one density-functional evaluation: H_1 <- DFT(rho(P)) (Algorithm 1's update) ------------
 // S: Re P per replica.  Writes rho, vh, vxc, exc, vhxc and H1 (in place) for active
 // replicas and folds max|H_new - H_1| into errbits.
 int dft_eval(rmgtd_ctx* ctx, const double* S, const RepCtl* ctl, unsigned long long* errbits) {
@@ -766,7 +766,7 @@ int rmgtd_kick(rmgtd_ctx* ctx, int rep, int axis, double kappa) {
   return check_status(ctx, "kick");
 }
 
-// One SCF pass of Algorithm 1 (lines 14-26) for every active replica.
+// One SCF pass of Algorithm 1 (series, density, fields, H update) for every active replica.
 static int enqueue_pass(rmgtd_ctx* ctx, cudaGraphConditionalHandle cond, int use_cond) {
   ph_begin(ctx, PH_ELDYN);
   // Omega's matrices: Hbar (+ the field), or S^-1 (Hbar + V) in a non-orthogonal basis, and

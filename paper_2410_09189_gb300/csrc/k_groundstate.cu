@@ -1,4 +1,4 @@
-// Ground state on the GPU (Algorithm 1 lines 1-3): the self-consistent Kohn-Sham orbitals that
+// Ground state on the GPU (Algorithm 1's ground state): the self-consistent Kohn-Sham orbitals that
 // define the active space, computed from the starting orbitals before the set-up continues.
 //
 // Eigensolver: Chebyshev-filtered subspace iteration on a block of N + nb orbitals (nb buffer

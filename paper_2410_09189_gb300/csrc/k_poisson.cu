@@ -1,4 +1,4 @@
-// Hartree potential: Lap_12 V_H = -4 pi rho on the grid (Section 2.1; Algorithm 1 line 26).
+// Hartree potential: Lap_12 V_H = -4 pi rho on the grid (Section 2.1; Algorithm 1's density-functional update).
 //
 // Discrete problem (the same one the kinetic stencil defines): interior unknowns, ghost
 // layers holding the monopole + dipole field of rho about the box centre,

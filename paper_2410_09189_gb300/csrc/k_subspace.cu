@@ -669,7 +669,7 @@ int to_float(rmgtd_ctx* ctx, const double* in, float* out, long n) {
 }
 
 // ---------------------------------------------------------------------------------------
-// Commutator expansion (Algorithm 1, lines 15-22) in the real split of Eq. 35.  With
+// Commutator expansion (Algorithm 1's series) in the real split of Eq. 35.  With
 // P = S + iA (S symmetric, A antisymmetric), Hbar real symmetric and Omega = -i tau Hbar:
 //   S_k =  (tau/k) [Hbar, A_{k-1}] = (tau/k) (T1 + T1^T),  T1 = Hbar A_{k-1}
 //   A_k = -(tau/k) [Hbar, S_{k-1}] = -(tau/k) (T2 - T2^T), T2 = Hbar S_{k-1}
@@ -1418,7 +1418,7 @@ int eldyn(rmgtd_ctx* ctx, const double* Ha, const double* Hb, long hstride, doub
 
 // ---------------------------------------------------------------------------------------
 // Step bookkeeping.
-// H_1 <- 2 H_0 - H_-1 (Algorithm 1 line 11) for every replica; reset the control blocks.
+// H_1 <- 2 H_0 - H_-1 (Algorithm 1's extrapolation) for every replica; reset the control blocks.
 // After a failed step of the same rmgtd_step call (sticky `failed`), every replica is
 // left inactive so the remaining steps do nothing.
 __global__ void k_step_begin(long n, const double* __restrict__ H0, const double* __restrict__ Hm1,
@@ -1479,7 +1479,7 @@ __global__ void k_scf_control(RepCtl* ctl, int nrep, const unsigned long long* e
 }
 
 // End of a step: if every replica succeeded, H_-1 <- H_0, H_0 <- H_1, P_0 <- P_1
-// (Algorithm 1 line 28) and count the step; otherwise raise the sticky failure flag.
+// (Algorithm 1's shift) and count the step; otherwise raise the sticky failure flag.
 // Block 0 appends the control blocks to the per-call statistics.
 __global__ void k_step_end(long n, double* __restrict__ Hm2, double* __restrict__ Hm1,
                            double* __restrict__ H0,

@@ -1,4 +1,4 @@
-// Learned seed of the Hamiltonian self-consistency loop (Algorithm 1 line 11).
+// Learned seed of the Hamiltonian self-consistency loop (Algorithm 1's extrapolation).
 //
 // The paper seeds every step's SCF loop with H_1 = 2 H_0 - H_-1, which is H[V_pred] with
 // V_pred = 2 V_0 - V_-1 because H is linear in V.  A small 3-D convolutional network adds a

@@ -1,6 +1,6 @@
 // Tensor-core (tcgen05) kernels of the mixed path.
 //
-// Density change (Algorithm 1 line 26's rho(P_1), Section 3.1's rho = sum_ij Re P_ij phi_i phi_j)
+// Density change (Algorithm 1's rho(P_1), Section 3.1's rho = sum_ij Re P_ij phi_i phi_j)
 // as a GEMM on the 5th-generation tensor cores:
 //   Y_r(g, j) = sum_k phi_k(g) Shat_r[k][j]        (M = 128 grid points, N = 32 nrep, K = 32)
 //   drho_r(g) = sum_j phi_j(g) Y_r(g, j)            (epilogue, one thread per grid point)
@@ -355,7 +355,7 @@ int rho_tc(rmgtd_ctx* ctx, double* rho, float* drho, const RepCtl* ctl, int nrep
 namespace tc {
 
 // ---- float32 Gram partials on the tensor cores ---------------------------------------------
-// H update of the mixed path (Algorithm 1 line 26, Section 3.1's H = h^3 Phi^T (V Phi)):
+// H update of the mixed path (Algorithm 1's density-functional update, Section 3.1's H = h^3 Phi^T (V Phi)):
 //   G_r[i][j] = sum_g (w_r(g) phi_i(g)) phi_j(g)     for the orbital tile pair (It, Jt)
 // as D = A B^T with M = 128 rows (4 replicas x 32 orbitals of tile It, w-weighted), N = 32
 // (orbitals of tile Jt), K = grid points, accumulated in tensor memory over the CTA's chunk

@@ -7,7 +7,7 @@ mini-batches and sets the normalisation scales from training-set statistics.
 Data: after every converged step j the context's rho_j and V_j (V_H + V_xc) are copied to
 device tensors.  Sample j (2 <= j < nsteps) has features from (rho_j, rho_{j-1}, rho_{j-2})
 and target (V_{j+1} - 2 V_j + V_{j-1}) / s_out: the residual of the paper's linear
-extrapolation seed for step j + 1 (Algorithm 1 line 11).
+extrapolation seed for step j + 1 (Algorithm 1).
 """
 from __future__ import annotations
 

@@ -12,7 +12,7 @@ from the CUDA path.  Each golden is one JSON file beside this script:
   for a 64-step window.
 
 Both use the Delta-V form of the Hamiltonian update, H = H_core + h^3 Phi^T diag(V_H + V_xc)
-Phi, which equals the full grid apply of Algorithm 1 line 26 up to rounding (pinned in
+Phi, which equals the full grid apply of Algorithm 1's H update up to rounding (pinned in
 ``tests/test_oracle_propagation.py``); it saves the oracle the 37-point stencil on every
 orbital in every pass.  Thresholds are tighter than the benchmark's so that the stored series
 sits well inside the tolerance of the tests that read it.

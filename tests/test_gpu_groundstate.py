@@ -1,4 +1,4 @@
-"""Ground state on the GPU (Algorithm 1 lines 1-3; option ground_state_scf) against the
+"""Ground state on the GPU (Algorithm 1's ground state; option ground_state_scf) against the
 oracle's SCF ground state (ARPACK eigenpairs, Pulay mixing), and the N_virt study (Section
 4.1: the spectrum's convergence with the number of virtual orbitals) against the
 complete-grid-basis propagation.

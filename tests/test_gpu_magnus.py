@@ -165,7 +165,7 @@ def test_spectrum_matches_oracle(lib, nq, nt, nw):
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_quadratic_seed_converges_to_the_same_trajectory(lib, small_ground_state, precision):
     """seed_order 2 (H_1 = 3 H_0 - 3 H_-1 + H_-2) changes only the SCF loop's starting point:
-    the kicked trajectory matches the oracle's (linear seed, Algorithm 1 line 11) within the
+    the kicked trajectory matches the oracle's (linear seed, Algorithm 1's extrapolation) within the
     same bounds."""
     rmgtd = lib
     s, gs = small_ground_state

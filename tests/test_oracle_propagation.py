@@ -8,7 +8,7 @@
 * Zero-field energy conservation after the kick (Section 4.2: no drift).
 * Time-domain TRK sum rule: d'(0+) = -kappa Tr(P_0 [[M,H],M]) -> -kappa N_e (complete basis).
 * The two Hamiltonian-update forms (full apply vs H_core + Phi^T V_Hxc Phi) agree, and
-  2 H_0 - H_-1 = H[2 V_0 - V_-1] (Algorithm 1 line 11 is linear in V).
+  2 H_0 - H_-1 = H[2 V_0 - V_-1] (Algorithm 1's extrapolation is linear in V).
 """
 import math
 
