@@ -166,7 +166,8 @@ typedef struct {
                               H_1 = 2 H_0 - H_-1 (Algorithm 1's extrapolation); 2 the quadratic
                               H_1 = 3 H_0 - 3 H_-1 + H_-2 (fewer passes when H varies smoothly;
                               the loop's H_thrs test still decides convergence).  H_-2 starts as
-                              H_0, and after rmgtd_load or setting H_-1 it restarts from H_-1. */
+                              H_0, and after rmgtd_load or setting H_-1 it restarts from H_-1.
+                              With grid_basis the same seeds act on the potential V. */
   int sm_budget;           /* > 0: every kernel grid of the context, the persistent Hartree and
                               commutator kernels included, is sized to this many SMs instead of
                               the device's; contexts whose budgets sum to at most the SM count

@@ -61,11 +61,12 @@ __global__ void k_gp_kick(double* __restrict__ psi, int nocc, long Ng, int nx, i
   }
 }
 
-// out = 2 a - b (V_1 <- 2 V_0 - V_-1, Algorithm 1's extrapolation on the potential)
+// out = 2 a - b (V_1 <- 2 V_0 - V_-1, Algorithm 1's extrapolation on the potential), or with
+// c (seed_order 2) the quadratic out = 3 a - 3 b + c (V_1 <- 3 V_0 - 3 V_-1 + V_-2)
 __global__ void k_gp_extrap(const double* __restrict__ a, const double* __restrict__ b,
-                            double* __restrict__ out, long n) {
+                            const double* __restrict__ c, double* __restrict__ out, long n) {
   for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x)
-    out[e] = 2.0 * a[e] - b[e];
+    out[e] = c ? 3.0 * (a[e] - b[e]) + c[e] : 2.0 * a[e] - b[e];
 }
 
 // vtot_r = V_ion + (V0_r + V1_r)/2 + sum_q ebar_rq q, in the terms' precision
@@ -1244,6 +1245,10 @@ int gridprop_setup(rmgtd_ctx* ctx) {
   const size_t vsz = sizeof(double) * Ng * nrep;
   ctx->gp_v0 = (double*)dev_alloc(ctx, vsz);
   ctx->gp_vm1 = (double*)dev_alloc(ctx, vsz);
+  if (ctx->opt.seed_order == 2) {
+    ctx->gp_vm2 = (double*)dev_alloc(ctx, vsz);
+    if (!ctx->gp_vm2) return set_error(ctx, RMGTD_ENOMEM, "grid propagation buffers");
+  }
   ctx->gp_v1 = (double*)dev_alloc(ctx, vsz);
   ctx->gp_vtot = dev_alloc(ctx, tsz * Ng * nrep);
   ctx->gp_ebar = (double*)dev_alloc(ctx, sizeof(double) * 3 * nrep);
@@ -1272,6 +1277,8 @@ int gridprop_setup(rmgtd_ctx* ctx) {
   // V_0 = V_-1 = V_H + V_xc of the starting density (computed by the set-up)
   RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->gp_v0, ctx->vhxc, vsz, cudaMemcpyDeviceToDevice, ctx->stream));
   RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->gp_vm1, ctx->vhxc, vsz, cudaMemcpyDeviceToDevice, ctx->stream));
+  if (ctx->gp_vm2)   // V_-2 = V_0 too: the first steps' quadratic seed is the linear one
+    RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->gp_vm2, ctx->vhxc, vsz, cudaMemcpyDeviceToDevice, ctx->stream));
   RMGTD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   return RMGTD_OK;
 }
@@ -1461,7 +1468,7 @@ int gridprop_step(rmgtd_ctx* ctx, rmgtd_stats* st) {
                                     cudaMemcpyHostToDevice, ctx->stream));
   }
   const int vb = gp_blocks(ctx, Ng * nrep);
-  k_gp_extrap<<<vb, 256, 0, ctx->stream>>>(ctx->gp_v0, ctx->gp_vm1, ctx->gp_v1, Ng * nrep);
+  k_gp_extrap<<<vb, 256, 0, ctx->stream>>>(ctx->gp_v0, ctx->gp_vm1, ctx->gp_vm2, ctx->gp_v1, Ng * nrep);
   ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_gp_extrap");
   std::vector<int> active(nrep, 1), passes(nrep, 0), tmax(nrep, 0), tsum(nrep, 0), status(nrep, 0);
@@ -1533,6 +1540,7 @@ int gridprop_step(rmgtd_ctx* ctx, rmgtd_stats* st) {
   int cst = 0;
   RMGTD_CUDA(ctx, cudaMemcpyAsync(&cst, ctx->status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   // V_-1 <- V_0, V_0 <- V_1 (rotate the buffers)
+  if (ctx->gp_vm2) std::swap(ctx->gp_vm2, ctx->gp_vm1);   // V_-2 <- V_-1
   std::swap(ctx->gp_vm1, ctx->gp_v0);
   std::swap(ctx->gp_v0, ctx->gp_v1);
   RMGTD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));

@@ -264,6 +264,7 @@ struct rmgtd_ctx {
   double* gp_ht = nullptr;      // H_core psi scratch of the observables
   double* gp_v0 = nullptr;
   double* gp_vm1 = nullptr;
+  double* gp_vm2 = nullptr;     // V_-2 (seed_order 2 only)
   double* gp_v1 = nullptr;
   double* gp_ebar = nullptr;
   int* gp_active = nullptr;

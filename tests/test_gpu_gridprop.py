@@ -6,6 +6,7 @@
   path, 1e-4 and 1e-6 of |E| with float32 series terms (mixed).
 * Ring on a ragged 20 x 22 x 24 grid (15 occupied orbitals, s-type KB projectors), kicked
   along x.
+* The quadratic potential seed (seed_order 2) against the oracle's linear one.
 * A series cap that cannot be met reports RMGTD_ENOTCONVERGED and keeps the state; the
   matrix calls are refused on a grid-basis context.
 """
@@ -121,6 +122,22 @@ def test_grid_basis_failure_and_refusals(lib, small_ground_state):
     with pytest.raises(rmgtd.RmgtdError) as ei:
         rmgtd.Context(s, gs["phi"], grid_basis=True, orthonormalize=False)   # nvirt > 0
     assert ei.value.code == rmgtd.EINVAL
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_quadratic_potential_seed_matches_oracle(lib, precision):
+    """seed_order 2 (V_1 = 3 V_0 - 3 V_-1 + V_-2) moves only the SCF loop's starting point:
+    the trajectory matches the oracle's (linear seed) within the same bounds."""
+    rmgtd = lib
+    s = dataclasses.replace(inputs.ring(n=32, h=0.6, nvirt=0), n=(20, 22, 24))
+    raw = inputs.smooth_random_orbitals(s).reshape(s.N, s.Ng)
+    psi0 = oham.orthonormalize(s, raw)
+    nsteps, dt = 8, 0.05
+    o = tddft.Options(dt=dt, H_thrs=1e-10, dP_thrs=1e-12, poisson_tol=1e-13)
+    ref = ogrid.run(s, psi0, s.occupations, o, nsteps=nsteps, axis=2, kappa=2e-2)
+    d, e = _gpu_run(rmgtd, s, psi0, nsteps, dt, {0: (2, 2e-2)}, {}, 1, precision, seed_order=2)
+    assert _rel(d[:, 0], ref["dipole"]) < _TOL[precision][0], _rel(d[:, 0], ref["dipole"])
+    assert np.max(np.abs(e[:, 0] - ref["energy"])) < _etol(precision, ref)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
