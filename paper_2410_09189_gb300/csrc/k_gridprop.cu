@@ -14,10 +14,11 @@
 // fused kernel per term: the 12th-order stencil of both planes, the potential, the KB part
 // from per-point projector lists, the running sum and the stopping maximum.  With float64
 // terms the sum is psi_1 itself (psi_1 += t); with float32 terms it is a compensated float32
-// pair (hi + lo, the two-sum of Knuth) folded into psi_1 = psi + hi + lo once the series ends,
-// so that no float64 arithmetic is left in the term kernel (GB300's float64 pipe runs at 1/64
-// of its float32 rate).  The host drives the term and pass loops (one small read-back per
-// term for the stopping test).
+// pair (hi + lo, the two-sum of Knuth), each pass's density is a float32 change on the float64
+// density of the step's psi, and psi_1 = psi + hi + lo is formed once, when the SCF loop
+// ends: no float64 arithmetic is left per term or per pass (GB300's float64 pipe runs at 1/64
+// of its float32 rate).  The host drives the pass loop and queues the terms in batches behind
+// a device-side stopping test.
 #include <cstring>
 #include <utility>
 
@@ -168,12 +169,12 @@ __global__ void k_gp_series_ctl(int nrep, int k, double thr2, int max_terms, int
   }
 }
 
-// end of a float32 series for the active replicas: psi_1 = psi + (hi + lo)
+// end of a step with float32 terms (every replica, active null): psi_1 = psi + (hi + lo)
 __global__ void k_gp_fold(const double* __restrict__ psi, const float* __restrict__ acc,
                           long lo_off, double* __restrict__ psi1, long rplane,
                           const int* __restrict__ active) {
   const int r = blockIdx.y;
-  if (!active[r]) return;
+  if (active && !active[r]) return;
   for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < rplane;
        e += (long)gridDim.x * blockDim.x) {
     const long o = r * rplane + e;
@@ -821,6 +822,33 @@ __global__ void k_gp_density(const double* __restrict__ psi, const double* __res
   }
 }
 
+// psi0f = psi in float32 (float32 terms: once per step, the first term's input)
+__global__ void k_gp_to_f32(const double* __restrict__ psi, float* __restrict__ out, long n) {
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x)
+    out[e] = (float)psi[e];
+}
+
+// float32 terms: rho_r = rho0_r + sum_n f_n (2 Re(conj(psi0_n) s_n) + |s_n|^2), the density of
+// psi_1 = psi_0 + s (s = the series' sum hi + lo, taken as hi: |lo| is below hi's rounding)
+// as a float32 change on the float64 density of psi_0; no float64 arithmetic per orbital
+__global__ void k_gp_drho(const float* __restrict__ psi0f, const float* __restrict__ hi,
+                          const float* __restrict__ fs, int nocc, long Ng,
+                          const double* __restrict__ rho0, double* __restrict__ rho) {
+  const int r = blockIdx.y;
+  const long plane = (long)nocc * Ng;
+  const float* p = psi0f + 2 * r * plane;
+  const float* h = hi + 2 * r * plane;
+  for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < Ng; g += (long)gridDim.x * blockDim.x) {
+    float d = 0.f;
+    for (int n = 0; n < nocc; ++n) {
+      const long o = (long)n * Ng + g;
+      const float pr = p[o], pi = p[plane + o], hr = h[o], hm = h[plane + o];
+      d = fmaf(fs[n], fmaf(2.f, fmaf(pr, hr, pi * hm), fmaf(hr, hr, hm * hm)), d);
+    }
+    rho[r * Ng + g] = rho0[r * Ng + g] + (double)d;
+  }
+}
+
 // errbits_r <- max |vnew - v1|; v1 <- vnew (replicas with active[r] = 0 untouched)
 __global__ void k_gp_verr(const double* __restrict__ vnew, double* __restrict__ v1, long Ng,
                           const int* __restrict__ active, unsigned long long* __restrict__ errbits) {
@@ -957,10 +985,13 @@ k_gp_zgram_partial(int nocc, long Ng, const double* __restrict__ re, const doubl
 }
 
 // G = scale * sum over blocks (fixed order), full Hermitian (gre, gim) from the n <= m pairs
+// one warp per pair (the lanes stride over the block partials, then a warp sum: a serial
+// loop over hundreds of partials per thread was latency-bound)
 __global__ void k_gp_zgram_reduce(int nocc, int nblk, const double* __restrict__ part, double scale,
                                   double* __restrict__ gre, double* __restrict__ gim) {
   const int npairs = nocc * (nocc + 1) / 2;
-  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < npairs; q += gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31, nwarp = (gridDim.x * blockDim.x) >> 5;
+  for (int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < npairs; q += nwarp) {
     int n = 0, r = q;
     while (r >= nocc - n) {
       r -= nocc - n;
@@ -968,14 +999,18 @@ __global__ void k_gp_zgram_reduce(int nocc, int nblk, const double* __restrict__
     }
     const int m = n + r;
     double xr = 0.0, xi = 0.0;
-    for (int b = 0; b < nblk; ++b) {
+    for (int b = lane; b < nblk; b += 32) {
       xr += part[((long)b * npairs + q) * 2];
       xi += part[((long)b * npairs + q) * 2 + 1];
     }
-    gre[(long)n * nocc + m] = scale * xr;
-    gim[(long)n * nocc + m] = scale * xi;
-    gre[(long)m * nocc + n] = scale * xr;
-    gim[(long)m * nocc + n] = -scale * xi;
+    xr = warp_sum(xr);
+    xi = warp_sum(xi);
+    if (lane == 0) {
+      gre[(long)n * nocc + m] = scale * xr;
+      gim[(long)n * nocc + m] = scale * xi;
+      gre[(long)m * nocc + n] = scale * xr;
+      gim[(long)m * nocc + n] = -scale * xi;
+    }
   }
 }
 
@@ -1078,7 +1113,7 @@ int gp_blocks(rmgtd_ctx* ctx, long n) {
 
 constexpr int kGpBX = 32, kGpBY = 8, kGpZ = 16, kGtZ = 32;
 
-// tensor maps of the two term buffers for the TMA kernel: 4-D {nx, ny, nz, columns}, box
+// tensor maps of the term buffers (and of psi0f) for the TMA kernel: 4-D {nx, ny, nz, columns}, box
 // {BX + 16, BY + 12, 1, 1}, zero fill outside; only when a row of x is a whole number of
 // 16-byte units (then every stride is)
 template <typename T>
@@ -1106,9 +1141,9 @@ bool gp_encode_term_maps(rmgtd_ctx* ctx) {
   const cuuint32_t es[4] = {1, 1, 1, 1};
   const CUtensorMapDataType dt =
       sizeof(T) == sizeof(double) ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-  for (int b = 0; b < 2; ++b) {
-    void* base = b == 0 ? ctx->gp_ta : ctx->gp_tb;
-    void* map = b == 0 ? (void*)ctx->gp_tm_a : (void*)ctx->gp_tm_b;
+  for (int b = 0; b < (ctx->gp_psi0f ? 3 : 2); ++b) {
+    void* base = b == 0 ? ctx->gp_ta : b == 1 ? ctx->gp_tb : (void*)ctx->gp_psi0f;
+    void* map = b == 0 ? (void*)ctx->gp_tm_a : b == 1 ? (void*)ctx->gp_tm_b : (void*)ctx->gp_tm_0;
     if (f(reinterpret_cast<CUtensorMap*>(map), dt, 4, base, dims, strides, box, es,
           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
@@ -1146,7 +1181,8 @@ int gp_term(rmgtd_ctx* ctx, const T* tin, T* tout, double c, bool first) {
   else acc = ctx->gp_psi1;
   if (ctx->gp_tma) {   // x-y tiles by TMA from the term's tensor map
     const CUtensorMap* tm = reinterpret_cast<const CUtensorMap*>(
-        (const void*)tin == ctx->gp_ta ? ctx->gp_tm_a : ctx->gp_tm_b);
+        (const void*)tin == ctx->gp_ta ? ctx->gp_tm_a
+        : (const void*)tin == ctx->gp_tb ? ctx->gp_tm_b : ctx->gp_tm_0);
     if constexpr (sizeof(T) == sizeof(float)) {
       // z split evenly into chunks of about kG2Z planes (more, shorter blocks fill the SMs'
       // two block slots better than 32-plane chunks: 16.0 vs 17.0 ms per step on the ring)
@@ -1255,7 +1291,16 @@ int gridprop_setup(rmgtd_ctx* ctx) {
   ctx->gp_active = (int*)dev_alloc(ctx, sizeof(int) * nrep);
   ctx->gp_sact = (int*)dev_alloc(ctx, sizeof(int) * 3 * nrep);
   ctx->gp_coef = dev_alloc(ctx, tsz * std::max(ctx->nproj, 1) * 2L * nocc * nrep);
-  if (gp_f32(ctx)) ctx->gp_acc = (float*)ctx->gp_ht;   // hi + lo floats: the size of gp_ht
+  if (gp_f32(ctx)) {
+    ctx->gp_acc = (float*)ctx->gp_ht;   // hi + lo floats: the size of gp_ht
+    ctx->gp_psi0f = (float*)dev_alloc(ctx, sizeof(float) * 2 * plane * nrep);
+    ctx->gp_rho0 = (double*)dev_alloc(ctx, sizeof(double) * Ng * nrep);
+    ctx->gp_f32occ = (float*)dev_alloc(ctx, sizeof(float) * nocc);
+    if (!ctx->gp_psi0f || !ctx->gp_rho0 || !ctx->gp_f32occ)
+      return set_error(ctx, RMGTD_ENOMEM, "grid propagation buffers");
+    std::vector<float> ff(ctx->f.begin(), ctx->f.begin() + nocc);
+    RMGTD_CUDA(ctx, cudaMemcpy(ctx->gp_f32occ, ff.data(), sizeof(float) * nocc, cudaMemcpyHostToDevice));
+  }
   ctx->gp_gram = (double*)dev_alloc(ctx, sizeof(double) * 5 * (size_t)nocc * nocc);
   if (nocc <= kZgMaxN)
     ctx->gp_zpart = (double*)dev_alloc(
@@ -1293,14 +1338,23 @@ int gridprop_kick(rmgtd_ctx* ctx, int rep, int axis, double kappa) {
   return RMGTD_OK;   // |psi|^2 unchanged: the fields stay as they are
 }
 
-// fields of the orbitals `psi` for every replica: rho, V_H, V_xc, eps_xc, V_Hxc (ctx arrays)
+// fields of the orbitals `psi` for every replica: rho, V_H, V_xc, eps_xc, V_Hxc (ctx arrays);
+// psi null (float32 terms): of the pass's psi_1 = psi0 + the series' sum, the density as a
+// float32 change on rho0
 static int gp_fields(rmgtd_ctx* ctx, const double* psi) {
   const long Ng = ctx->Ng;
   ph_begin(ctx, PH_RHO);
-  k_gp_density<<<dim3(gp_blocks(ctx, Ng), ctx->nrep), 256, 0, ctx->stream>>>(psi, ctx->f_dev, ctx->N,
-                                                                            Ng, ctx->rho);
-  ++ctx->launches;
-  RMGTD_LAUNCH(ctx, "k_gp_density");
+  if (psi) {
+    k_gp_density<<<dim3(gp_blocks(ctx, Ng), ctx->nrep), 256, 0, ctx->stream>>>(psi, ctx->f_dev, ctx->N,
+                                                                              Ng, ctx->rho);
+    ++ctx->launches;
+    RMGTD_LAUNCH(ctx, "k_gp_density");
+  } else {
+    k_gp_drho<<<dim3(gp_blocks(ctx, Ng), ctx->nrep), 256, 0, ctx->stream>>>(
+        ctx->gp_psi0f, ctx->gp_acc, ctx->gp_f32occ, ctx->N, Ng, ctx->gp_rho0, ctx->rho);
+    ++ctx->launches;
+    RMGTD_LAUNCH(ctx, "k_gp_drho");
+  }
   ph_end(ctx);
   int rc = RMGTD_OK;
   if (ctx->hartree_xc) {
@@ -1348,7 +1402,7 @@ static int gp_orthonormalize(rmgtd_ctx* ctx, int r) {
     k_gp_zgram_partial<<<nblk, kZgThreads, 0, ctx->stream>>>(N, ctx->Ng, re, im, ctx->gp_zpart);
     ++ctx->launches;
     RMGTD_LAUNCH(ctx, "k_gp_zgram_partial");
-    k_gp_zgram_reduce<<<gp_blocks(ctx, (long)N * (N + 1) / 2), 256, 0, ctx->stream>>>(
+    k_gp_zgram_reduce<<<gp_blocks(ctx, 32L * N * (N + 1) / 2), 256, 0, ctx->stream>>>(
         N, nblk, ctx->gp_zpart, ctx->h3, gre, gim);
     ++ctx->launches;
     RMGTD_LAUNCH(ctx, "k_gp_zgram_reduce");
@@ -1397,11 +1451,17 @@ static int gp_series(rmgtd_ctx* ctx, const std::vector<int>& active, std::vector
   RMGTD_LAUNCH(ctx, "k_gp_vtot");
   T* ta = (T*)ctx->gp_ta;
   T* tb = (T*)ctx->gp_tb;
-  constexpr bool f32 = sizeof(T) == sizeof(float);
-  k_gp_start<T><<<dim3(gp_blocks(ctx, rplane), nrep), 256, 0, ctx->stream>>>(
-      ctx->gp_psi, f32 ? nullptr : ctx->gp_psi1, ta, rplane, ctx->gp_active);
-  ++ctx->launches;
-  RMGTD_LAUNCH(ctx, "k_gp_start");
+  const T* tin = ta;   // the term's input and output (the first from psi)
+  T* tout = tb;
+  if constexpr (sizeof(T) == sizeof(float)) {   // the step's psi in float32, converted once
+    tin = ctx->gp_psi0f;
+    tout = ta;
+  } else {
+    k_gp_start<T><<<dim3(gp_blocks(ctx, rplane), nrep), 256, 0, ctx->stream>>>(
+        ctx->gp_psi, ctx->gp_psi1, ta, rplane, ctx->gp_active);
+    ++ctx->launches;
+    RMGTD_LAUNCH(ctx, "k_gp_start");
+  }
   // the terms in batches between read-backs of the device-side stopping test: the first
   // batch as long as the last series less one, then two at a time (terms queued after a
   // series has stopped return at once)
@@ -1413,9 +1473,10 @@ static int gp_series(rmgtd_ctx* ctx, const std::vector<int>& active, std::vector
   int batch = std::max(1, ctx->gp_terms_hint - 1);
   for (int k = 1;;) {
     for (int b = 0; b < batch; ++b, ++k) {
-      int rc = gp_term<T>(ctx, ta, tb, ctx->opt.dt / k, k == 1);
+      int rc = gp_term<T>(ctx, tin, tout, ctx->opt.dt / k, k == 1);
       if (rc) return rc;
-      std::swap(ta, tb);
+      tin = tout;
+      tout = tout == ta ? tb : ta;
       k_gp_series_ctl<<<1, 32, 0, ctx->stream>>>(nrep, k, thr2, ctx->opt.max_terms, ctx->gp_sact,
                                                  ctx->errbits);
       ++ctx->launches;
@@ -1439,12 +1500,6 @@ static int gp_series(rmgtd_ctx* ctx, const std::vector<int>& active, std::vector
     last = std::max(last, terms);
   }
   ctx->gp_terms_hint = last;
-  if (f32) {   // psi_1 = psi + hi + lo
-    k_gp_fold<<<dim3(gp_blocks(ctx, rplane), nrep), 256, 0, ctx->stream>>>(
-        ctx->gp_psi, ctx->gp_acc, rplane * nrep, ctx->gp_psi1, rplane, ctx->gp_active);
-    ++ctx->launches;
-    RMGTD_LAUNCH(ctx, "k_gp_fold");
-  }
   return RMGTD_OK;
 }
 
@@ -1471,6 +1526,18 @@ int gridprop_step(rmgtd_ctx* ctx, rmgtd_stats* st) {
   k_gp_extrap<<<vb, 256, 0, ctx->stream>>>(ctx->gp_v0, ctx->gp_vm1, ctx->gp_vm2, ctx->gp_v1, Ng * nrep);
   ++ctx->launches;
   RMGTD_LAUNCH(ctx, "k_gp_extrap");
+  const bool f32 = gp_f32(ctx);
+  const long rplane = 2L * ctx->N * Ng;
+  if (f32) {   // the step's psi in float32 and its density in float64, once per step
+    k_gp_to_f32<<<gp_blocks(ctx, rplane * nrep), 256, 0, ctx->stream>>>(ctx->gp_psi, ctx->gp_psi0f,
+                                                                         rplane * nrep);
+    ++ctx->launches;
+    RMGTD_LAUNCH(ctx, "k_gp_to_f32");
+    k_gp_density<<<dim3(gp_blocks(ctx, Ng), nrep), 256, 0, ctx->stream>>>(ctx->gp_psi, ctx->f_dev, ctx->N,
+                                                                         Ng, ctx->gp_rho0);
+    ++ctx->launches;
+    RMGTD_LAUNCH(ctx, "k_gp_density");
+  }
   std::vector<int> active(nrep, 1), passes(nrep, 0), tmax(nrep, 0), tsum(nrep, 0), status(nrep, 0);
   std::vector<double> herr(nrep, 0.0), m;
   bool any = true;
@@ -1478,14 +1545,14 @@ int gridprop_step(rmgtd_ctx* ctx, rmgtd_stats* st) {
     RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->gp_active, active.data(), sizeof(int) * nrep,
                                     cudaMemcpyHostToDevice, ctx->stream));
     ph_begin(ctx, PH_ELDYN);   // the orbital series takes the commutator series' place
-    int rc = gp_f32(ctx) ? gp_series<float>(ctx, active, status, tmax, tsum)
-                         : gp_series<double>(ctx, active, status, tmax, tsum);
+    int rc = f32 ? gp_series<float>(ctx, active, status, tmax, tsum)
+                 : gp_series<double>(ctx, active, status, tmax, tsum);
     ph_end(ctx);
     if (rc) return rc;
     for (int r = 0; r < nrep; ++r)
       if (status[r]) active[r] = 0;
     // V_new of the propagated orbitals; H_err = max|V_new - V_1|
-    rc = gp_fields(ctx, ctx->gp_psi1);
+    rc = gp_fields(ctx, f32 ? nullptr : ctx->gp_psi1);
     if (rc) return rc;
     RMGTD_CUDA(ctx, cudaMemcpyAsync(ctx->gp_active, active.data(), sizeof(int) * nrep,
                                     cudaMemcpyHostToDevice, ctx->stream));
@@ -1532,6 +1599,12 @@ int gridprop_step(rmgtd_ctx* ctx, rmgtd_stats* st) {
                                      " failed with status " + std::to_string(first));
   }
   ph_begin(ctx, PH_OTHER);
+  if (f32) {   // psi_1 = psi + hi + lo of every replica's last series
+    k_gp_fold<<<dim3(gp_blocks(ctx, rplane), nrep), 256, 0, ctx->stream>>>(
+        ctx->gp_psi, ctx->gp_acc, rplane * nrep, ctx->gp_psi1, rplane, nullptr);
+    ++ctx->launches;
+    RMGTD_LAUNCH(ctx, "k_gp_fold");
+  }
   for (int r = 0; r < nrep; ++r) {
     int rc = gp_orthonormalize(ctx, r);
     if (rc) return rc;

@@ -282,6 +282,11 @@ struct rmgtd_ctx {
                                 // [nrep][2][N][nproj]
   alignas(64) unsigned char gp_tm_a[128] = {};   // tensor maps of the two term buffers
   alignas(64) unsigned char gp_tm_b[128] = {};
+  alignas(64) unsigned char gp_tm_0[128] = {};   // and of gp_psi0f (float32 terms)
+  float* gp_psi0f = nullptr;    // float32 terms: the step's psi in float32 (the first term's
+                                // input, and the density change's reference) [nrep][2][N][Ng]
+  double* gp_rho0 = nullptr;    // float32 terms: rho of the step's psi [nrep][Ng]
+  float* gp_f32occ = nullptr;   // float32 terms: the occupations f [N] in float32
   int gp_tma = 0;               // the term kernel streams its tiles by TMA
   int* gp_kb_row = nullptr;     // KB lists by grid point: CSR row offsets [Ng + 1],
   int* gp_kb_p = nullptr;       // projector index and E_p beta_p(r) of each entry (the
