@@ -6,8 +6,11 @@ algebraic), the density sum_i f_i |phi_i|^2 is rebuilt and Pulay-mixed until it 
 changing.  Orbitals are returned grid-normalised (h^3 sum phi_i phi_j = delta_ij) with the
 sign fixed so that each orbital's largest-magnitude value is positive.
 
-Parity status: pinned indirectly (harmonic-oscillator eigenvalues, stationarity of
-P_0 = diag(f) under H_0 checked by the propagation tests).
+Pinned by (tests/test_oracle_groundstate.py): on a 576-point grid with a KB projector, a
+dense LAPACK diagonalisation of the whole grid Hamiltonian -- the independent-electron
+eigenpairs and occupied projector, the Kohn-Sham fixed point rho = rho(eig(H[rho])) with
+Hartree and LDA, and the stationarity and minimality of the Kohn-Sham energy under an
+occupied-virtual rotation; also the harmonic-oscillator eigenvalues.
 """
 from __future__ import annotations
 
