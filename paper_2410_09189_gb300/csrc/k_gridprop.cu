@@ -1037,17 +1037,31 @@ __global__ void k_ztri_inverse(int N, const double* __restrict__ lre, const doub
   }
 }
 
-// psi_out_n = sum_{m <= n} X_nm psi_in_m per grid point, the point's orbitals in registers
+// psi_out_n = sum_{m <= n} X_nm psi_in_m per grid point, the point's orbitals in registers.
+// X = L^-1 is the identity up to the series' departure from unitarity, so when every entry of
+// X - I is below kXSmall the kernel forms psi_out = psi_in + (X - I) psi_in with the correction
+// in float32 (its rounding, ~1e-7 of a correction below 1e-6 of |psi|, stays under 1e-13 of
+// |psi|): per orbital two conversions and one float64 add instead of 2(n + 1) complex float64
+// multiply-adds.  Otherwise the product is float64 throughout.
+constexpr double kXSmall = 1e-6;
+
 template <int MAXN>
 __global__ void __launch_bounds__(256)
 k_gp_xapply(int nocc, long Ng, const double* __restrict__ xre, const double* __restrict__ xim,
             const double* __restrict__ in, double* __restrict__ out) {
   __shared__ double sxr[MAXN * MAXN], sxi[MAXN * MAXN];
+  __shared__ float sfr[MAXN * MAXN], sfi[MAXN * MAXN];
+  bool big = false;
   for (int e = threadIdx.x; e < nocc * nocc; e += blockDim.x) {
+    const int n = e / nocc, m = e - n * nocc;
+    const double dr = xre[e] - (n == m ? 1.0 : 0.0), di = xim[e];
     sxr[e] = xre[e];
-    sxi[e] = xim[e];
+    sxi[e] = di;
+    sfr[e] = (float)dr;
+    sfi[e] = (float)di;
+    big = big || !(fabs(dr) <= kXSmall && fabs(di) <= kXSmall);
   }
-  __syncthreads();
+  big = __syncthreads_or(big);   // uniform over the block
   const long plane = (long)nocc * Ng;
   for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < Ng; g += (long)gridDim.x * blockDim.x) {
     double yr[MAXN], yi[MAXN];
@@ -1055,6 +1069,28 @@ k_gp_xapply(int nocc, long Ng, const double* __restrict__ xre, const double* __r
     for (int m = 0; m < MAXN; ++m) {
       yr[m] = m < nocc ? in[(long)m * Ng + g] : 0.0;
       yi[m] = m < nocc ? in[plane + (long)m * Ng + g] : 0.0;
+    }
+    if (!big) {
+      float fr[MAXN], fi[MAXN];
+#pragma unroll
+      for (int m = 0; m < MAXN; ++m) {
+        fr[m] = (float)yr[m];
+        fi[m] = (float)yi[m];
+      }
+#pragma unroll
+      for (int n = 0; n < MAXN; ++n) {
+        if (n >= nocc) break;
+        float sr = 0.f, si = 0.f;
+#pragma unroll
+        for (int m = 0; m <= n; ++m) {
+          const float ar = sfr[n * nocc + m], ai = sfi[n * nocc + m];
+          sr = fmaf(ar, fr[m], fmaf(-ai, fi[m], sr));
+          si = fmaf(ar, fi[m], fmaf(ai, fr[m], si));
+        }
+        out[(long)n * Ng + g] = yr[n] + (double)sr;
+        out[plane + (long)n * Ng + g] = yi[n] + (double)si;
+      }
+      continue;
     }
 #pragma unroll
     for (int n = 0; n < MAXN; ++n) {
