@@ -187,7 +187,8 @@ __global__ void k_gp_fold(const double* __restrict__ psi, const float* __restric
 // Block (p, group of kKbCols columns): each thread takes every blockDim-th entry, four at a
 // time (their indexes, values and the kKbCols column values all in flight together), and
 // keeps one sum per column: float64 columns in float64, float32 columns in compensated
-// float32 (Kahan); the block then reduces each column in float64 in a fixed order.  Columns
+// float32 (Kahan), summed across the warp as float32 pairs; the warps' sums are then added in
+// float64 in a fixed order.  Columns
 // of replicas whose series has stopped are skipped (cols_per_rep columns per replica).
 constexpr int kKbCols = 4, kKbThreads = 1024;
 
@@ -248,8 +249,22 @@ k_gp_kb_project(const T* __restrict__ x, long Ng, int ncols, int cols_per_rep,
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
   for (int c = 0; c < kKbCols; ++c) {
-    const double v = warp_sum((double)s[c] - (double)comp[c]);
-    if (lane == 0) sh[c][w] = v;
+    if constexpr (sizeof(T) == sizeof(double)) {
+      const double v = warp_sum(s[c]);
+      if (lane == 0) sh[c][w] = v;
+    } else {   // the warp's sum as a float32 pair (two-sum butterfly), float64 from lane 0
+      float hi = s[c], lo = -comp[c];
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, hi, off);
+        const float ol = __shfl_xor_sync(0xffffffffu, lo, off);
+        float t, e;
+        two_sum(hi, oh, t, e);
+        hi = t;
+        lo = __fadd_rn(__fadd_rn(lo, ol), e);
+      }
+      if (lane == 0) sh[c][w] = (double)hi + (double)lo;
+    }
   }
   __syncthreads();
   if (w < kKbCols) {

@@ -10,6 +10,9 @@ from the CUDA path.  Each golden is one JSON file beside this script:
 * ``icosa128_window.json`` -- the 147-atom icosahedron on its 128^3 grid (N = 148), started
   from P_0 = diag(f) of the orthonormalised seeded orbitals, kicked along z and propagated
   for a 64-step window.
+* ``ring64_grid_basis.json`` -- the ring's 15 occupied orbitals propagated on its 64^3 grid
+  (the complete-grid-basis limit, ``oracle/gridprop.py``), from the orthonormalised first 15
+  seeded orbitals, kicked along z, 20 steps, every step stored.
 
 Both use the Delta-V form of the Hamiltonian update, H = H_core + h^3 Phi^T diag(V_H + V_xc)
 Phi, which equals the full grid apply of Algorithm 1's H update up to rounding (pinned in
@@ -17,8 +20,8 @@ Phi, which equals the full grid apply of Algorithm 1's H update up to rounding (
 orbital in every pass.  Thresholds are tighter than the benchmark's so that the stored series
 sits well inside the tolerance of the tests that read it.
 
-Usage: ``python tests/golden/make_trajectory_goldens.py ring|icosa`` (minutes to an hour
-of CPU time each).
+Usage: ``python tests/golden/make_trajectory_goldens.py ring|icosa|grid`` (minutes to an
+hour of CPU time each).
 """
 from __future__ import annotations
 
@@ -34,13 +37,48 @@ ROOT = os.path.dirname(os.path.dirname(HERE))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-from oracle import hamiltonian as oham, tddft  # noqa: E402
+from oracle import gridprop, hamiltonian as oham, tddft  # noqa: E402
 from paper_2410_09189_gb300 import inputs  # noqa: E402
 
 RING = dict(name="ring64_three_kicks", nsteps=2000, record_every=5, H_thrs=1e-10, dP_thrs=1e-12,
             poisson_tol=1e-12, subspace_scf=600, subspace_mix=0.3, subspace_tol=1e-12)
 ICOSA = dict(name="icosa128_window", nsteps=64, record_every=1, H_thrs=1e-10, dP_thrs=1e-13,
              poisson_tol=1e-12)
+GRID = dict(name="ring64_grid_basis", nsteps=20, axis=2, H_thrs=1e-10, dP_thrs=1e-12,
+            poisson_tol=1e-12)
+
+
+def make_grid():
+    """The ring's occupied orbitals propagated on the grid (oracle/gridprop.py)."""
+    import dataclasses
+    cfg = GRID
+    s0 = inputs.ring()
+    s = dataclasses.replace(s0, nvirt=0)
+    raw = inputs.smooth_random_orbitals(s0).reshape(s0.N, s0.Ng)[:s.N]
+    psi0 = oham.orthonormalize(s, raw)
+    opts = tddft.Options(dt=s.dt, H_thrs=cfg["H_thrs"], dP_thrs=cfg["dP_thrs"],
+                         poisson_tol=cfg["poisson_tol"])
+    t0 = time.time()
+    out = gridprop.run(s, psi0, s.occupations, opts, nsteps=cfg["nsteps"], axis=cfg["axis"],
+                       kappa=s.kappa)
+    doc = {
+        "what": f"oracle grid propagation of the {s.name} workload's occupied orbitals (float64 CPU)",
+        "written_by": "tests/golden/make_trajectory_goldens.py (oracle/ only)",
+        "workload": {"name": s.name, "grid": list(s.n), "h": s.h, "nocc": s.nocc,
+                     "natoms": int(len(s.Z)), "nproj": s.nproj, "dt": s.dt, "kappa": s.kappa,
+                     "axis": cfg["axis"]},
+        "options": {k: v for k, v in cfg.items() if k != "name"},
+        "initial_state": "the orthonormalised first nocc seeded orbitals",
+        "step": list(range(cfg["nsteps"] + 1)),
+        "dipole": out["dipole"].tolist(), "energy": out["energy"].tolist(),
+        "electrons": out["electrons"].tolist(), "passes": out["passes"],
+        "cpu_seconds": time.time() - t0,
+    }
+    path = os.path.join(HERE, cfg["name"] + ".json")
+    with open(path + ".tmp", "w") as f:
+        json.dump(doc, f, indent=None, separators=(",", ":"))
+    os.replace(path + ".tmp", path)
+    print(f"wrote {path}", flush=True)
 
 
 def _trajectory(pr, st0, axis, kappa, nsteps, every, log):
@@ -120,4 +158,5 @@ def make(which: str):
 
 
 if __name__ == "__main__":
-    make(sys.argv[1] if len(sys.argv) > 1 else "ring")
+    which = sys.argv[1] if len(sys.argv) > 1 else "ring"
+    make_grid() if which == "grid" else make(which)

@@ -5,7 +5,9 @@ contractions, the Hartree solve on odd and long axes, and the failure paths.
   written by ``tests/golden/make_trajectory_goldens.py`` from ``oracle/`` alone):
   - the 147-atom icosahedron on its 128^3 grid (N = 148), 64-step window from P_0 = diag(f);
   - the 12-atom ring on its 64^3 grid (N = 30), three kicks, 2,000 steps from the ground state
-    inside the orbital block.
+    inside the orbital block;
+  - the ring's 15 occupied orbitals propagated on its 64^3 grid (the complete-grid-basis
+    limit), three kicked replicas as benchmarked, 20 steps of the z-kicked one.
   Dipole tolerance (reading of "relative": max_t |d - d_ref| / max_t |d_ref(t) - d_ref(0)|):
   1e-6 on the float64 path, 1e-4 on the mixed path, the targets the method states for each.
 * The bfloat16 hi/lo split of the orbital-plane contractions keeps each product to about
@@ -173,6 +175,40 @@ def test_ring_64_three_kicks_2000_steps_match_oracle(lib, precision):
         etol = 1e-8 * np.max(np.abs(e_ref)) if precision == "fp64" else 1e-6 * np.max(np.abs(e_ref))
         assert np.max(np.abs(e - e_ref)) < etol, (a, np.max(np.abs(e - e_ref)))
         assert abs(tr[a] - g["replicas"][a]["trace"][-1]) < 1e-9
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_ring_64_grid_basis_matches_oracle(lib, precision):
+    """The ring's 15 occupied orbitals propagated on its 64^3 grid with three kicked replicas
+    (the benchmark's grid-basis workload and launch configuration), 20 steps of the z-kicked
+    replica against the stored oracle run: dipole within 1e-6 / 1e-4 of its variation, and
+    energy."""
+    rmgtd = lib
+    g = _golden("ring64_grid_basis.json")
+    s0 = inputs.ring()
+    s = dataclasses.replace(s0, nvirt=0)
+    raw = inputs.smooth_random_orbitals(s0).reshape(s0.N, s0.Ng)[:s.N]
+    o = g["options"]
+    fp64 = precision == "fp64"
+    # the float32 terms leave ~1e-8 of noise in V: the mixed SCF stops above it
+    with rmgtd.Context(s, raw, dt=s.dt, H_thrs=o["H_thrs"] if fp64 else 1e-8,
+                       dP_thrs=o["dP_thrs"], poisson_tol=o["poisson_tol"], nrep=3,
+                       grid_basis=True,
+                       precision=rmgtd.PREC_FP64 if fp64 else rmgtd.PREC_MIXED) as ctx:
+        for a in range(3):
+            ctx.kick(a, a, s.kappa)
+        r = g["workload"]["axis"]
+        d, e = [ctx.dipole(r)], [ctx.energy(r)]
+        for _ in range(o["nsteps"]):
+            ctx.step(1)
+            d.append(ctx.dipole(r))
+            e.append(ctx.energy(r))
+    ref = np.array(g["dipole"])
+    err = _dipole_error(np.array(d), ref)
+    assert err < (1e-6 if fp64 else 1e-4), err
+    e_ref = np.array(g["energy"])
+    etol = (1e-8 if fp64 else 1e-6) * np.max(np.abs(e_ref))
+    assert np.max(np.abs(np.array(e) - e_ref)) < etol, np.max(np.abs(np.array(e) - e_ref))
 
 
 # ---- Hartree solve on odd and long axes ----------------------------------------------------------
