@@ -153,9 +153,10 @@ typedef struct {
                               H_err = max|V_new - V_1|); the matrix, save / load, batch,
                               autotune and network calls return RMGTD_ESTATE. */
   int ground_state_scf;    /* > 0: before the set-up, up to this many SCF iterations of the
-                              Kohn-Sham ground state on the GPU (Algorithm 1's ground state) from the
-                              orthonormalised phi0: Chebyshev-filtered subspace iteration on
-                              N + max(4, N/8) orbitals (degree 12 per iteration, Rayleigh-Ritz),
+                              Kohn-Sham ground state on the GPU (Algorithm 1's ground state)
+                              from the orthonormalised phi0: Chebyshev-filtered subspace
+                              iteration on N + max(4, N/8) orbitals (degree 12 per iteration,
+                              Rayleigh-Ritz),
                               Pulay-mixed density (history 6, mixing 0.4); phi0 is replaced by the
                               N lowest Kohn-Sham orbitals (ascending energies).  Requires
                               orthonormalize = 1, nonorthogonal = 0, N + buffer <= 1024.
@@ -289,10 +290,10 @@ int rmgtd_hartree(rmgtd_ctx* ctx, const double* rho_dev, double* vh_dev);
 int rmgtd_xc(rmgtd_ctx* ctx, const double* rho_dev, double* vxc_dev, double* exc_dev,
              size_t n);
 
-/* The mixed path's xc increment (Algorithm 1's density-functional update with the fields kept as float32
- * increments against the set-up state): dvxc_dev[g] = V_xc(rho0_dev[g] + drho_dev[g]) -
- * V_xc(rho0_dev[g]) for the LDA of rmgtd_xc, on n device points (rho0 double, drho and the
- * result float).  Evaluated in float32 arithmetic on the increment, so the error is a few
+/* The mixed path's xc increment (Algorithm 1's density-functional update, with the fields
+ * kept as float32 increments against the set-up state):
+ * dvxc_dev[g] = V_xc(rho0_dev[g] + drho_dev[g]) - V_xc(rho0_dev[g]) for the LDA of rmgtd_xc,
+ * on n device points (rho0 double, drho and the result float).  Evaluated in float32 arithmetic on the increment, so the error is a few
  * float32 units of the increment itself; points near the density floor or across r_s = 1 take
  * two float64 evaluations.  Arrays belong to the caller.  Errors: RMGTD_EINVAL. */
 int rmgtd_xc_increment(rmgtd_ctx* ctx, const double* rho0_dev, const float* drho_dev,
@@ -378,7 +379,7 @@ void rmgtd_batch_destroy(rmgtd_batch* batch);
  * nsteps x nrep records (as rmgtd_step).  On a failed step the error names the context. */
 int rmgtd_batch_step(rmgtd_batch* batch, int nsteps, rmgtd_stats* const* stats);
 
-/* ---- Learned seed of the SCF loop (Algorithm 1's extrapolation) ------------------------------------
+/* ---- Learned seed of the SCF loop (Algorithm 1's extrapolation) ---------------------------
  * The paper seeds each step's Hamiltonian SCF loop with H_1 = 2 H_0 - H_-1 = H[2 V_0 - V_-1].
  * An attached network adds dV = s_out * y to that potential, y = net(x) with features
  *   x[0] = rho_t / s_0,  x[1] = (rho_t - rho_{t-dt}) / s_1,  x[2] = (rho_t - 2 rho_{t-dt} + rho_{t-2dt}) / s_2,
