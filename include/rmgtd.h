@@ -156,9 +156,8 @@ typedef struct {
                               Kohn-Sham ground state on the GPU (Algorithm 1's ground state)
                               from the orthonormalised phi0: Chebyshev-filtered subspace
                               iteration on N + max(4, N/8) orbitals (degree 12 per iteration,
-                              Rayleigh-Ritz),
-                              Pulay-mixed density (history 6, mixing 0.4); phi0 is replaced by the
-                              N lowest Kohn-Sham orbitals (ascending energies).  Requires
+                              Rayleigh-Ritz), Pulay-mixed density (history 6, mixing 0.4); phi0
+                              is replaced by the N lowest Kohn-Sham orbitals (ascending energies).  Requires
                               orthonormalize = 1, nonorthogonal = 0, N + buffer <= 1024.
                               RMGTD_ENOTCONVERGED if the cap is reached. */
   double ground_state_tol; /* stop when max|rho_out - rho_in| and the largest Ritz residual
