@@ -386,7 +386,8 @@ k_gp_term_fused(const T* __restrict__ tin, T* __restrict__ tout, T* __restrict__
   if (tid == 0) atomic_max_nonneg(&errbits[rep], bm);
 }
 
-// The same term with the x-y tiles streamed by TMA: thread 0 keeps kGtS planes of the chunk
+// The same term (float64 terms; float32 terms use k_gp_term_tma2 below) with the x-y tiles
+// streamed by TMA: thread 0 keeps kGtS planes of the chunk
 // in flight, each a pair of tiles (real, imaginary) of (BX + 16) x (BY + 12) points starting at
 // (x0 - 8, y0 - 6) -- the x start rounded down to a 16-byte boundary -- with zero fill outside
 // the grid (the Dirichlet ghosts).  Each thread's z-column stays in registers, refilled by a
