@@ -568,8 +568,11 @@ k_gp_term_tma(const __grid_constant__ CUtensorMap tm_in, const T* __restrict__ t
   if (i < nzb) {   // gave up: wait (bounded) for every issued copy, then leave
     if (tid == 0) {
       atomicCAS(status, 0, (int)RMGTD_ETIMEOUT);
+      // the last copy of each slot (older planes' phases are past: waiting on their
+      // parity would only run out the limit)
       const int issued = min(nzb, i + kGtS);
-      for (int w = 0; w < issued; ++w) tc::mbar_wait(&full[w % kGtS], (w / kGtS) & 1);
+      for (int w = max(0, issued - kGtS); w < issued; ++w)
+        tc::mbar_wait(&full[w % kGtS], (w / kGtS) & 1);
     }
     return;
   }
@@ -583,7 +586,9 @@ k_gp_term_tma(const __grid_constant__ CUtensorMap tm_in, const T* __restrict__ t
 // y-neighbours from 12 float2 loads, the z-column is a register array of float2 pairs; psi_1
 // and the series' float32 pair (hi, lo) move as float2, as do V and the term.  Rows must be a
 // whole number of 16-byte units (nx % 4 == 0), so a pair is inside or outside the grid
-// together.  No float64 arithmetic: the KB lists and projections are float32 too.
+// together.  No float64 arithmetic: the KB lists and projections are float32 too.  No block
+// barrier per plane: each warp arrives on the slot's `empty` mbarrier when done with it, and
+// thread 0 refills the slot once all have (the warps run up to kG2S planes apart).
 constexpr int kG2X = 64;   // points per block along x
 constexpr int kG2S = 4;    // planes in flight
 constexpr int kG2Z = 12;   // z-planes per block, about
@@ -595,7 +600,7 @@ __host__ __device__ constexpr int gt2_tile_elems() {
 
 template <int BY>
 __host__ __device__ constexpr size_t gt2_smem_bytes() {
-  return sizeof(float) * 2 * gt2_tile_elems<BY>() * kG2S + sizeof(uint64_t) * kG2S + 1024;
+  return sizeof(float) * 2 * gt2_tile_elems<BY>() * kG2S + 2 * sizeof(uint64_t) * kG2S + 1024;
 }
 
 template <int BY>
@@ -617,6 +622,7 @@ k_gp_term_tma2(const __grid_constant__ CUtensorMap tm_in, const float* __restric
       (reinterpret_cast<uintptr_t>(gt2_raw) + 1023) & ~(uintptr_t)1023);
   float* tiles = reinterpret_cast<float*>(smem);   // [kG2S][2][BY + 2R][TW]
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + sizeof(float) * 2 * TE * kG2S);
+  uint64_t* empty = full + kG2S;   // all warps done with a slot (one arrival per warp)
   __shared__ double sh[32];
   const int col = blockIdx.z / nzc;
   const int rep = col / nocc, n = col - rep * nocc;
@@ -630,7 +636,10 @@ k_gp_term_tma2(const __grid_constant__ CUtensorMap tm_in, const float* __restric
   const int cre_col = rep * 2 * nocc + n, cim_col = cre_col + nocc;
   const int xs = blockIdx.x * kG2X - kGtXO, ys = blockIdx.y * BY - R;
   if (tid == 0) {
-    for (int s = 0; s < kG2S; ++s) tc::mbar_init(&full[s], 1);
+    for (int s = 0; s < kG2S; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], BY);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     for (int i = 0; i < min(kG2S, nzb); ++i) {
       float* dst = tiles + (size_t)i * 2 * TE;
@@ -690,8 +699,8 @@ k_gp_term_tma2(const __grid_constant__ CUtensorMap tm_in, const float* __restric
   const int lx = 2 * tx + kGtXO, ly = ty + R;
   float emax = 0.f;
   bool ok = true;
-  int i = 0;
-  for (; i < nzb; ++i) {
+  int issued = min(kG2S, nzb);   // planes whose copies thread 0 issued
+  for (int i = 0; i < nzb; ++i) {
     qr[2 * R] = nr_next;
     qi[2 * R] = ni_next;
     const float2 c_ahr = ahr, c_ahi = ahi, c_alr = alr, c_ali = ali;
@@ -718,7 +727,7 @@ k_gp_term_tma2(const __grid_constant__ CUtensorMap tm_in, const float* __restric
         }
       }
     }
-    if (!tc::mbar_wait(&full[i % kG2S], (i / kG2S) & 1)) ok = false;
+    if (ok && !tc::mbar_wait(&full[i % kG2S], (i / kG2S) & 1)) ok = false;
     const float* tr = tiles + (size_t)(i % kG2S) * 2 * TE;
     const float* ti = tr + TE;
     if (in_xy && ok) {
@@ -795,14 +804,22 @@ k_gp_term_tma2(const __grid_constant__ CUtensorMap tm_in, const float* __restric
       }
       emax = fmaxf(emax, fmaxf(nr.x * nr.x + ni.x * ni.x, nr.y * nr.y + ni.y * ni.y));
     }
-    if (__syncthreads_or(!ok)) break;
-    if (tid == 0 && i + kG2S < nzb) {
-      const int j = i + kG2S;
-      float* dst = tiles + (size_t)(j % kG2S) * 2 * TE;
-      const uint32_t bar = tc::saddr(&full[j % kG2S]);
-      tc::mbar_expect_tx(bar, kBytes);
-      tc::tma_load_4d(tc::saddr(dst), &tm_in, xs, ys, z0 + j, cre_col, bar);
-      tc::tma_load_4d(tc::saddr(dst + TE), &tm_in, xs, ys, z0 + j, cim_col, bar);
+    // this warp is done with slot i % kG2S; thread 0 refills it once every warp is
+    // (no block barrier: the warps run up to kG2S planes apart)
+    __syncwarp();
+    if ((tid & 31) == 0) tc::mbar_arrive(&empty[i % kG2S]);
+    if (tid == 0 && i + kG2S < nzb && ok) {
+      if (!tc::mbar_wait(&empty[i % kG2S], (i / kG2S) & 1)) {
+        ok = false;
+      } else {
+        const int j = i + kG2S;
+        float* dst = tiles + (size_t)(j % kG2S) * 2 * TE;
+        const uint32_t bar = tc::saddr(&full[j % kG2S]);
+        tc::mbar_expect_tx(bar, kBytes);
+        tc::tma_load_4d(tc::saddr(dst), &tm_in, xs, ys, z0 + j, cre_col, bar);
+        tc::tma_load_4d(tc::saddr(dst + TE), &tm_in, xs, ys, z0 + j, cim_col, bar);
+        issued = j + 1;
+      }
     }
 #pragma unroll
     for (int k = 0; k < 2 * R; ++k) {
@@ -810,11 +827,11 @@ k_gp_term_tma2(const __grid_constant__ CUtensorMap tm_in, const float* __restric
       qi[k] = qi[k + 1];
     }
   }
-  if (i < nzb) {
+  if (__syncthreads_or(!ok)) {   // a wait gave up: wait (bounded) for the copies in flight
     if (tid == 0) {
       atomicCAS(status, 0, (int)RMGTD_ETIMEOUT);
-      const int issued = min(nzb, i + kG2S);
-      for (int w = 0; w < issued; ++w) tc::mbar_wait(&full[w % kG2S], (w / kG2S) & 1);
+      for (int w = max(0, issued - kG2S); w < issued; ++w)
+        tc::mbar_wait(&full[w % kG2S], (w / kG2S) & 1);
     }
     return;
   }
