@@ -855,6 +855,19 @@ __global__ void k_gp_density(const double* __restrict__ psi, const double* __res
   }
 }
 
+// The first Hartree solve's guess at the start of a step: with a = V_H now (the last solve),
+// vh <- 3 a - 3 vh1 + vh2 (two earlier steps known), 2 a - vh1 (one), a (none): V_H one step
+// ahead to O(dt^3); then vh2 <- vh1, vh1 <- a.  The guess changes only the iteration count.
+__global__ void k_gp_vh_guess(double* __restrict__ vh, double* __restrict__ vh1,
+                              double* __restrict__ vh2, int hist, long n) {
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
+    const double a = vh[e], b = vh1[e];
+    vh[e] = hist >= 2 ? 3.0 * (a - b) + vh2[e] : hist == 1 ? 2.0 * a - b : a;
+    vh2[e] = b;
+    vh1[e] = a;
+  }
+}
+
 // psi0f = psi in float32 (float32 terms: once per step, the first term's input)
 __global__ void k_gp_to_f32(const double* __restrict__ psi, float* __restrict__ out, long n) {
   for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x)
@@ -1360,6 +1373,12 @@ int gridprop_setup(rmgtd_ctx* ctx) {
   ctx->gp_active = (int*)dev_alloc(ctx, sizeof(int) * nrep);
   ctx->gp_sact = (int*)dev_alloc(ctx, sizeof(int) * 3 * nrep);
   ctx->gp_coef = dev_alloc(ctx, tsz * std::max(ctx->nproj, 1) * 2L * nocc * nrep);
+  if (ctx->hartree_xc) {
+    ctx->gp_vh1 = (double*)dev_alloc(ctx, vsz);
+    ctx->gp_vh2 = (double*)dev_alloc(ctx, vsz);
+    if (!ctx->gp_vh1 || !ctx->gp_vh2) return set_error(ctx, RMGTD_ENOMEM, "grid propagation buffers");
+    ctx->gp_vh_hist = 0;
+  }
   if (gp_f32(ctx)) {
     ctx->gp_acc = (float*)ctx->gp_ht;   // hi + lo floats: the size of gp_ht
     ctx->gp_psi0f = (float*)dev_alloc(ctx, sizeof(float) * 2 * plane * nrep);
@@ -1597,6 +1616,13 @@ int gridprop_step(rmgtd_ctx* ctx, rmgtd_stats* st) {
   RMGTD_LAUNCH(ctx, "k_gp_extrap");
   const bool f32 = gp_f32(ctx);
   const long rplane = 2L * ctx->N * Ng;
+  if (ctx->hartree_xc) {   // the first solve's guess: V_H extrapolated one step ahead
+    k_gp_vh_guess<<<vb, 256, 0, ctx->stream>>>(ctx->vh, ctx->gp_vh1, ctx->gp_vh2, ctx->gp_vh_hist,
+                                               Ng * nrep);
+    ++ctx->launches;
+    RMGTD_LAUNCH(ctx, "k_gp_vh_guess");
+    ctx->gp_vh_hist = std::min(2, ctx->gp_vh_hist + 1);
+  }
   if (f32) {   // the step's psi in float32 and its density in float64, once per step
     k_gp_to_f32<<<gp_blocks(ctx, rplane * nrep), 256, 0, ctx->stream>>>(ctx->gp_psi, ctx->gp_psi0f,
                                                                          rplane * nrep);

@@ -265,6 +265,9 @@ struct rmgtd_ctx {
   double* gp_v0 = nullptr;
   double* gp_vm1 = nullptr;
   double* gp_vm2 = nullptr;     // V_-2 (seed_order 2 only)
+  double* gp_vh1 = nullptr;     // V_H at the start of the last two steps (the first Hartree
+  double* gp_vh2 = nullptr;     // solve's guess is their quadratic extrapolation)
+  int gp_vh_hist = 0;           // how many of them are set (0..2)
   double* gp_v1 = nullptr;
   double* gp_ebar = nullptr;
   int* gp_active = nullptr;
