@@ -67,3 +67,26 @@ def test_grid_propagation_keeps_orthonormal_orbitals():
     S = s.h ** 3 * psi.conj() @ psi.T
     assert np.max(np.abs(S - np.eye(3))) < 1e-12
     assert np.max(np.abs(r["electrons"] - 5.0)) < 1e-10
+
+
+def test_stored_grid_trajectory_starts_from_its_recipe():
+    """The stored full-size grid-basis run (tests/golden/ring64_grid_basis.json) starts where
+    its recipe says: the ring's orthonormalised first 15 seeded orbitals kicked along z; its
+    step-0 dipole and energy are the oracle's."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "ring64_grid_basis.json")
+    with open(path) as f:
+        g = json.load(f)
+    s0 = inputs.ring()
+    s = dataclasses.replace(s0, nvirt=0)
+    raw = inputs.smooth_random_orbitals(s0).reshape(s0.N, s0.Ng)[:s.N]
+    psi0 = ham.orthonormalize(s, raw)
+    o = g["options"]
+    opts = tddft.Options(dt=s.dt, H_thrs=o["H_thrs"], dP_thrs=o["dP_thrs"],
+                         poisson_tol=o["poisson_tol"])
+    gp = gridprop.GridPropagator(s, psi0, s.occupations, opts)
+    gp.kick(g["workload"]["axis"], s.kappa)
+    assert np.max(np.abs(gp.dipole() - np.array(g["dipole"][0]))) < 1e-12
+    assert abs(gp.energy() - g["energy"][0]) < 1e-9
+    assert len(g["dipole"]) == o["nsteps"] + 1
