@@ -1353,6 +1353,11 @@ int gp_build_kb_lists(rmgtd_ctx* ctx) {
 int gridprop_setup(rmgtd_ctx* ctx) {
   const int nocc = ctx->N, nrep = ctx->nrep;
   const long Ng = ctx->Ng, plane = (long)nocc * Ng;
+  // the term kernels take one block row per replica, orbital and z chunk (at least
+  // ceil(nz / kG2Z) chunks): the launch grid's z extent is at most 65535
+  if ((long)nrep * nocc * ceil_div(ctx->nz, std::min(kG2Z, kGpZ)) > 65535L)
+    return set_error(ctx, RMGTD_EINVAL,
+                     "grid_basis: replicas x orbitals x z chunks exceed the launch grid (65535)");
   const size_t psz = sizeof(double) * 2 * plane * nrep;
   const size_t tsz = gp_f32(ctx) ? sizeof(float) : sizeof(double);
   ctx->gp_psi = (double*)dev_alloc(ctx, psz);
