@@ -19,6 +19,11 @@ Workloads (units: bohr, hartree, atomic time units):
   minimum distance, Z=1 plus one s-type projector each, 128^3 grid at h=0.4,
   74 doubly occupied + 74 virtual orbitals: a metal-cluster stand-in for the paper's
   silver nanoparticles (Section 4.3).
+* ``cluster(i)`` -- the batched workload's eight random clusters (20-150 atoms, 48^3-96^3).
+* ``fcc_large`` -- the large workload: the 1,024 sites of an FCC lattice (nearest-neighbour
+  distance 5.4 bohr) nearest the box centre, jittered, Z=2 each with one s and three p
+  projectors, 192^3 grid at h=0.4, 1,024 doubly occupied + 1,024 virtual orbitals: the
+  stand-in for the paper's largest silver clusters (Section 4.3).
 
 Seeds are ``241009189 + 1000*workload_index + sub_index``.
 """
@@ -206,6 +211,38 @@ def cluster(index: int, natoms: Optional[int] = None, n: Optional[int] = None,
                   nocc=nocc, nvirt=nocc, kick_axes=(0, 1, 2), nsteps=200, seed=seed)
 
 
+def fcc_sites(nsites: int, nn: float = 5.4) -> np.ndarray:
+    """The `nsites` sites of an FCC lattice with nearest-neighbour distance `nn` (cube edge
+    a = nn * sqrt(2), a site at the origin) nearest the origin; equidistant sites are taken
+    in lexicographic order of (x, y, z), so the selection is deterministic."""
+    a = nn * math.sqrt(2.0)
+    m = int(math.ceil((nsites / 4.0) ** (1.0 / 3.0))) + 2
+    basis = np.array([[0.0, 0.0, 0.0], [0.0, 0.5, 0.5], [0.5, 0.0, 0.5], [0.5, 0.5, 0.0]])
+    r = np.arange(-m, m + 1, dtype=float)
+    cells = np.stack(np.meshgrid(r, r, r, indexing="ij"), axis=-1).reshape(-1, 3)
+    pts = (cells[:, None, :] + basis[None, :, :]).reshape(-1, 3) * a
+    d2 = np.round((pts * pts).sum(1), 9)
+    order = np.lexsort((pts[:, 2], pts[:, 1], pts[:, 0], d2))
+    return pts[order[:nsites]]
+
+
+def fcc_large(n: int = 192, h: float = 0.4, nsites: int = 1024, jitter: float = 0.1) -> System:
+    """The large workload: `fcc_sites(nsites)` each moved by N(0, jitter^2) per coordinate
+    (seeded), Z = 2 local wells (r_c = 0.5) with one s and three p KB projectors (x, y, z)
+    on every atom (r_c = 1.2, E_KB ~ U[0.5, 2] per projector), n^3 grid at h; two valence
+    electrons per atom: N_occ = nsites, N = 2 N_occ; kick along z, 200 steps."""
+    seed = SEED_BASE + 1000 * 5
+    rng = np.random.default_rng(seed)
+    pos = fcc_sites(nsites) + rng.normal(0.0, jitter, size=(nsites, 3))
+    atoms = np.repeat(np.arange(nsites, dtype=np.int32), 4)
+    pl = np.tile(np.array([0, 1, 1, 1], np.int32), nsites)
+    pm = np.tile(np.array([0, 0, 1, 2], np.int32), nsites)
+    ekb = rng.uniform(0.5, 2.0, size=4 * nsites)
+    return System("fcc_large", (n, n, n), h, pos, np.full(nsites, 2.0), np.full(nsites, 0.5),
+                  atoms, pl, pm, np.full(4 * nsites, 1.2), ekb, nocc=nsites, nvirt=nsites,
+                  kick_axes=(2,), nsteps=200, seed=seed)
+
+
 def harmonic(n: int = 32, h: float = 0.4, omega: float = 0.5, nvirt: int = 3) -> System:
     """Test mode: one doubly occupied orbital in V = 0.5*omega^2*r^2, no Hartree/xc."""
     pa, pl, pm, prc, ekb = _no_proj()
@@ -284,7 +321,8 @@ def random_grid(sys: System, seed: int, positive: bool = False) -> np.ndarray:
     return np.abs(x) if positive else x
 
 
-ALL = {"small": small, "ring": ring, "icosa": icosa, "harmonic": harmonic}
+ALL = {"small": small, "ring": ring, "icosa": icosa, "harmonic": harmonic,
+       "fcc_large": fcc_large}
 
 
 def by_name(name: str, **kw) -> System:
